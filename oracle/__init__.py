@@ -1,0 +1,180 @@
+"""FP64 CPU oracle for the plane-strain lattice Boltzmann method (arXiv:2301.00228).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow reference the CUDA
+library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it.  It shares no code with the
+CUDA path: the arithmetic lives in ``lbm_oracle.c`` (compiled with gcc,
+``-ffp-contract=off`` so results do not depend on FMA contraction), and this
+module only marshals arrays through ctypes.
+
+Parity status of each function is recorded in ``PINS`` below: every part of
+the time loop is pinned by a test against a closed form, an invariant, a
+hand-computed lattice or brute force, except the two readings listed as
+"parity unpinned" (they are pinned oracle-to-CUDA only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "lbm_oracle.c"
+_LIB = _HERE / "liblbm_oracle.so"
+
+# Which test pins which part of the oracle (file::test).
+PINS = {
+    "constants (Eq. conditions-parameters)": "tests/test_oracle_pins.py::test_constants_*",
+    "interior LBE = five-point leapfrog": "tests/test_oracle_pins.py::test_leapfrog_equivalence",
+    "discrete standing wave, phi/psi/u/v": "tests/test_oracle_pins.py::test_standing_wave_closed_form",
+    "wave speeds c_d, c_s": "tests/test_oracle_pins.py::test_wave_speeds",
+    "conservation (periodic)": "tests/test_oracle_pins.py::test_conservation_periodic",
+    "patch tests (Neumann cells, corners, Dirichlet)": "tests/test_oracle_pins.py::test_patch_*",
+    "Dirichlet target u*": "tests/test_oracle_pins.py::test_dirichlet_reaches_target",
+    "hand-computed 3x3 lattices": "tests/test_oracle_golden.py",
+    "convergence to continuum slab modes": "tests/test_oracle_pins.py::test_slab_convergence",
+    "linearity / mirror symmetry": "tests/test_oracle_pins.py::test_linearity, ::test_mirror_symmetry",
+    "synchronisation (Sec. 3.2)": "tests/test_oracle_pins.py::test_sync_*",
+    "rectangle boundary helper": "tests/test_oracle_pins.py::test_rect_bc_*",
+}
+# Readings with no pin against the paper itself.
+PARITY_UNPINNED = (
+    "initial first moments from du/dt (reading R9): no paper value; pinned oracle-to-CUDA only",
+    "consistency-error magnitude of Fig. 9 (4.3e-12): lattice resolution not given",
+)
+
+UX, UY, VX, VY, PHI, PSI, F_PHI, F_PSI, ERR, AX, AY = range(11)
+
+
+def build(force: bool = False) -> Path:
+    """Compile lbm_oracle.c into a shared library beside it (gcc, FP64, OpenMP)."""
+    if _LIB.exists() and not force and _LIB.stat().st_mtime >= _SRC.stat().st_mtime:
+        return _LIB
+    tmp = _LIB.with_suffix(f".so.{os.getpid()}")
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-Wall", "-o", str(tmp), str(_SRC), "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("lam", ctypes.c_double), ("mu", ctypes.c_double), ("rho", ctypes.c_double),
+                ("dh", ctypes.c_double), ("a0_phi", ctypes.c_double),
+                ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("bc_feq_mode", ctypes.c_int32), ("sync_every", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(str(_LIB))
+        vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+        L.ora_create.restype = vp
+        L.ora_create.argtypes = [ctypes.POINTER(_Params), vp, vp]
+        L.ora_destroy.argtypes = [vp]
+        L.ora_constants.argtypes = [vp, dp]
+        L.ora_init.argtypes = [vp, vp, vp, vp, vp]
+        L.ora_step.argtypes = [vp, ctypes.c_int64]
+        L.ora_sync.argtypes = [vp]
+        L.ora_read.argtypes = [vp, ctypes.c_int32, vp]
+        L.ora_steps_done.restype = ctypes.c_int64
+        L.ora_steps_done.argtypes = [vp]
+        L.ora_rect_bc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                  ctypes.c_double, vp, vp, vp, vp]
+        L.ora_set_threads.argtypes = [ctypes.c_int32]
+        L.ora_get_threads.restype = ctypes.c_int32
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    lib().ora_set_threads(int(n))
+
+
+def rect_bc(nx, ny, edge_type, edge_value, periodic_x=False, periodic_y=False, dh=1.0):
+    """Node types and boundary values of a rectangle (edges: bottom, right, top, left)."""
+    et = np.ascontiguousarray(edge_type, dtype=np.int32).reshape(4)
+    ev = np.ascontiguousarray(edge_value, dtype=np.float64).reshape(8)
+    nt = np.zeros((ny, nx), np.uint8)
+    bv = np.zeros((ny, nx, 2), np.float64)
+    rc = lib().ora_rect_bc(nx, ny, int(periodic_x), int(periodic_y), float(dh), _ptr(et), _ptr(ev),
+                           _ptr(nt), _ptr(bv))
+    if rc != 0:
+        raise ValueError("invalid rectangle boundary description")
+    return nt, bv
+
+
+class OracleLattice:
+    """One lattice of the FP64 oracle."""
+
+    def __init__(self, nx, ny, lam, mu, rho=1.0, dh=1.0, a0_phi=0.9999, periodic_x=False,
+                 periodic_y=False, node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0):
+        self.nx, self.ny = int(nx), int(ny)
+        p = _Params(self.nx, self.ny, lam, mu, rho, dh, a0_phi, int(periodic_x), int(periodic_y),
+                    int(bc_feq_mode), int(sync_every))
+        if node_type is None:
+            node_type = np.zeros((ny, nx), np.uint8)
+        self._nt = np.ascontiguousarray(node_type, dtype=np.uint8)
+        self._bv = None if bc_value is None else np.ascontiguousarray(bc_value, dtype=np.float64)
+        self._h = lib().ora_create(ctypes.byref(p), _ptr(self._nt), _ptr(self._bv))
+        if not self._h:
+            raise ValueError("oracle rejected the lattice description")
+        c = np.zeros(6)
+        lib().ora_constants(self._h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self.cd, self.cs, self.a_phi, self.a_psi, self.a0_psi, self.dt = (float(x) for x in c)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().ora_destroy(h)
+            self._h = None
+
+    def init(self, ux0, uy0, vx0=None, vy0=None):
+        a = [np.ascontiguousarray(x, dtype=np.float64) if x is not None else None
+             for x in (ux0, uy0, vx0, vy0)]
+        if lib().ora_init(self._h, *[_ptr(x) for x in a]) != 0:
+            raise ValueError("non-finite initial data")
+        return self
+
+    def step(self, n=1):
+        if lib().ora_step(self._h, int(n)) != 0:
+            raise RuntimeError("oracle step failed")
+        return self
+
+    def sync(self):
+        lib().ora_sync(self._h)
+        return self
+
+    @property
+    def steps(self):
+        return int(lib().ora_steps_done(self._h))
+
+    def read(self, field):
+        planes = 5 if field in (F_PHI, F_PSI) else 1
+        out = np.zeros((planes, self.ny, self.nx), np.float64)
+        if lib().ora_read(self._h, int(field), _ptr(out)) != 0:
+            raise ValueError("bad field id")
+        return out if planes == 5 else out[0]
+
+    def fields(self):
+        return {name: self.read(fid) for name, fid in
+                (("ux", UX), ("uy", UY), ("vx", VX), ("vy", VY), ("phi", PHI), ("psi", PSI))}
+
+
+if __name__ == "__main__":
+    build(force="--force" in sys.argv)
+    print(_LIB)

@@ -1,0 +1,633 @@
+/*
+ * FP64 CPU oracle for the plane-strain lattice Boltzmann method of
+ * arXiv:2301.00228 (Schlueter, Yan, Faust, Mueller & Mueller).
+ *
+ * TEST INFRASTRUCTURE ONLY: the plain, slow reference for the CUDA library.
+ * It is loaded by the test suite, the smoke check and the CPU-baseline leg of
+ * the benchmark, and by nothing else.  It shares no code with the CUDA path.
+ *
+ * Every time step runs the blocks of the algorithm summary (Fig. 3) in the
+ * paper's order, one full-lattice pass per block, no fusion:
+ *   1. moments phi, psi of both population sets           Eq. interpretation
+ *   2. acceleration at interior points                     Eq. navier
+ *   3. acceleration at Neumann / Dirichlet points          Eq. acc_neumann,
+ *                                                          Eq. acc_dirichlet
+ *   4. explicit Newmark integration of u                   Eq. integration
+ *   5. boundary phi, psi from finite differences of the
+ *      new u, boundary populations reset                   Eq. psi_phi_at_bound,
+ *                                                          Eq. correction-f
+ *   6. LBE into interior points, with the time-averaged
+ *      state for boundary sources                          Eq. LBE, Eq. LBE_mod
+ *   7. every l-th step, synchronisation                    Sec. 3.2
+ *
+ * Readings where the paper is silent, garbled or inconsistent:
+ *   R1  c_s = sqrt(mu/rho) (the text after Eq. wave-navier prints lambda;
+ *       Sec. 4 states c_s/c_d = 1/sqrt(3), true for mu only at lambda = mu).
+ *   R2  Fig. 3 initialises phi with the curl; phi is the divergence,
+ *       Eq. phi-psi.
+ *   R3  The interior acceleration is c_d^2 grad(phi) - c_s^2 curl(psi e_z)
+ *       (Eq. navier); Fig. 3 drops the curl.
+ *   R4  Finite differences are central where both neighbours exist (or wrap
+ *       periodically) and one-sided three-point (second order) otherwise;
+ *       the paper only states "second order accurate" (Sec. 3.1.2).
+ *   R5  The segment length l_kr that Sec. 3.1.1 defines multiplies each
+ *       stress term in Eq. acc_neumann (the printed sum omits it).
+ *   R6  Rectangle cells: the square of side dh around a boundary point
+ *       clipped to the body; faces towards each existing neighbour.
+ *   R7  J(x_k, t) in Eq. correction-f is the first moment of the populations
+ *       stored at x_k at time t.  Boundary points receive no LBE output, so
+ *       their populations are only ever set by Eq. correction-f.
+ *   R8  Eq. LBE_mod: with bc_feq_mode 0 the equilibrium is evaluated from the
+ *       moments of the averaged state f-hat; with mode 1 from f(x_k, t) as
+ *       printed.
+ *   R9  With du/dt(x,0) given, the first moments start at J_phi = -v and
+ *       J_psi = (-v_y, v_x), from d(phi)/dt = -div J_phi (the zeroth-moment
+ *       balance of the LBE) and d(phi)/dt = div v.  All inputs at rest give
+ *       J = 0.
+ *   R10 tau = dt/2 in both Eq. LBE and Eq. LBE_mod (so dt/tau = 1/tau = 2).
+ *   R11 The Newmark update is used as printed (gamma = 1 for the velocity).
+ *   R12 Dirichlet u* is constant in time, so u*(t) and u*(t+dt) coincide.
+ */
+#include "lbm_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* D2Q5 lattice directions e_alpha; the velocities are c^alpha = c e_alpha
+ * with c = dh/dt (Sec. 3, velocity set). */
+static const int EX[5] = {0, 1, 0, -1, 0};
+static const int EY[5] = {0, 0, 1, 0, -1};
+
+struct ora_lattice {
+    ora_params p;
+    double cd, cs, a_phi, a_psi, a0_psi, dt, c;
+    uint8_t* type;        /* [ny*nx] */
+    double* bc;           /* [ny*nx*2] */
+    double* f[2][5];      /* populations at t: set 0 = phi, set 1 = psi */
+    double* fn[2][5];     /* populations at t + dt */
+    double* fc[2][5];     /* post-collision populations */
+    double *ux, *uy, *vx, *vy;      /* u, du/dt at t */
+    double *ux1, *uy1, *vx1, *vy1;  /* u, du/dt at t + dt */
+    double* s[2];         /* phi, psi at t */
+    double *ax, *ay;      /* acceleration at t */
+    int64_t steps;
+    int initialised;
+};
+
+static int32_t g_threads = 1;
+
+void ora_set_threads(int32_t n) { g_threads = n > 0 ? n : 1; }
+int32_t ora_get_threads(void) { return g_threads; }
+
+static long at(const ora_lattice* L, int i, int j) { return (long)j * L->p.nx + i; }
+
+/* Weights a_0, a of one population set (Eq. feq, Eq. feq_req). */
+static double w0_of(const ora_lattice* L, int set) { return set == 0 ? L->p.a0_phi : L->a0_psi; }
+static double w_of(const ora_lattice* L, int set) { return set == 0 ? L->a_phi : L->a_psi; }
+
+/* A point is a boundary lattice point when one of its four neighbours lies
+ * outside a non-periodic edge. */
+static int is_boundary(const ora_lattice* L, int i, int j) {
+    if (!L->p.periodic_x && (i == 0 || i == L->p.nx - 1)) return 1;
+    if (!L->p.periodic_y && (j == 0 || j == L->p.ny - 1)) return 1;
+    return 0;
+}
+
+/* Neighbour of (i,j) in direction (di,dj); 0 if it lies outside the body. */
+static int neighbour(const ora_lattice* L, int i, int j, int di, int dj, int* oi, int* oj) {
+    int ni = i + di, nj = j + dj;
+    if (ni < 0 || ni >= L->p.nx) {
+        if (!L->p.periodic_x) return 0;
+        ni = (ni + L->p.nx) % L->p.nx;
+    }
+    if (nj < 0 || nj >= L->p.ny) {
+        if (!L->p.periodic_y) return 0;
+        nj = (nj + L->p.ny) % L->p.ny;
+    }
+    *oi = ni;
+    *oj = nj;
+    return 1;
+}
+
+/* Second-order finite differences (reading R4). */
+static double d_dx(const ora_lattice* L, const double* g, int i, int j) {
+    int nx = L->p.nx;
+    double h = L->p.dh;
+    if (L->p.periodic_x)
+        return (g[at(L, (i + 1) % nx, j)] - g[at(L, (i - 1 + nx) % nx, j)]) / (2.0 * h);
+    if (i > 0 && i < nx - 1) return (g[at(L, i + 1, j)] - g[at(L, i - 1, j)]) / (2.0 * h);
+    if (i == 0) return (-3.0 * g[at(L, 0, j)] + 4.0 * g[at(L, 1, j)] - g[at(L, 2, j)]) / (2.0 * h);
+    return (3.0 * g[at(L, nx - 1, j)] - 4.0 * g[at(L, nx - 2, j)] + g[at(L, nx - 3, j)]) / (2.0 * h);
+}
+
+static double d_dy(const ora_lattice* L, const double* g, int i, int j) {
+    int ny = L->p.ny;
+    double h = L->p.dh;
+    if (L->p.periodic_y)
+        return (g[at(L, i, (j + 1) % ny)] - g[at(L, i, (j - 1 + ny) % ny)]) / (2.0 * h);
+    if (j > 0 && j < ny - 1) return (g[at(L, i, j + 1)] - g[at(L, i, j - 1)]) / (2.0 * h);
+    if (j == 0) return (-3.0 * g[at(L, i, 0)] + 4.0 * g[at(L, i, 1)] - g[at(L, i, 2)]) / (2.0 * h);
+    return (3.0 * g[at(L, i, ny - 1)] - 4.0 * g[at(L, i, ny - 2)] + g[at(L, i, ny - 3)]) / (2.0 * h);
+}
+
+/* Divergence and curl of u by finite differences (Eq. phi-psi). */
+static double fd_div(const ora_lattice* L, const double* ux, const double* uy, int i, int j) {
+    return d_dx(L, ux, i, j) + d_dy(L, uy, i, j);
+}
+static double fd_curl(const ora_lattice* L, const double* ux, const double* uy, int i, int j) {
+    return d_dx(L, uy, i, j) - d_dy(L, ux, i, j);
+}
+
+/* Cauchy stress by finite differences of Eq. strain inserted in Eq. hooke:
+ * sig = {sigma_xx, sigma_yy, sigma_xy}. */
+static void stress(const ora_lattice* L, const double* ux, const double* uy, int i, int j, double sig[3]) {
+    double exx = d_dx(L, ux, i, j);
+    double eyy = d_dy(L, uy, i, j);
+    double exy = 0.5 * (d_dy(L, ux, i, j) + d_dx(L, uy, i, j));
+    double tr = exx + eyy;
+    sig[0] = L->p.lambda * tr + 2.0 * L->p.mu * exx;
+    sig[1] = L->p.lambda * tr + 2.0 * L->p.mu * eyy;
+    sig[2] = 2.0 * L->p.mu * exy;
+}
+
+/* Equilibrium of Eq. feq for direction alpha, given s and J = sum c^alpha f^alpha. */
+static double f_eq(const ora_lattice* L, int set, int alpha, double s, double jx, double jy) {
+    const double b = 1.0; /* Eq. feq_req */
+    if (alpha == 0) return w0_of(L, set) * s;
+    double cax = L->c * EX[alpha], cay = L->c * EY[alpha];
+    return w_of(L, set) * s + b * (cax * jx + cay * jy) / (2.0 * L->c * L->c);
+}
+
+/* Zeroth and first moments of five populations (Eq. interpretation, Eq. feq). */
+static void moments(const ora_lattice* L, const double g[5], double* s, double* jx, double* jy) {
+    double m0 = 0.0, mx = 0.0, my = 0.0;
+    for (int a = 0; a < 5; ++a) {
+        m0 += g[a];
+        mx += L->c * EX[a] * g[a];
+        my += L->c * EY[a] * g[a];
+    }
+    *s = m0;
+    *jx = mx;
+    *jy = my;
+}
+
+static void gather(double* const fs[5], long k, double g[5]) {
+    for (int a = 0; a < 5; ++a) g[a] = fs[a][k];
+}
+
+/* ---------------------------------------------------------------- create */
+
+static double* alloc0(long n) { return (double*)calloc((size_t)n, sizeof(double)); }
+
+ora_lattice* ora_create(const ora_params* p, const uint8_t* node_type, const double* bc_value) {
+    if (!p || p->nx < 3 || p->ny < 3) return NULL;
+    if (!(p->mu > 0.0) || !(p->rho > 0.0) || !(p->lambda + 2.0 * p->mu > 0.0) || !(p->dh > 0.0)) return NULL;
+    if (!(p->a0_phi >= 0.0 && p->a0_phi < 1.0)) return NULL;
+    if (p->bc_feq_mode != 0 && p->bc_feq_mode != 1) return NULL;
+    if (p->sync_every < 0) return NULL;
+    ora_lattice* L = (ora_lattice*)calloc(1, sizeof(ora_lattice));
+    if (!L) return NULL;
+    L->p = *p;
+    /* Wave speeds after Eq. wave-navier (reading R1). */
+    L->cd = sqrt((p->lambda + 2.0 * p->mu) / p->rho);
+    L->cs = sqrt(p->mu / p->rho);
+    /* Eq. feq_req: a_0 + 4a = 1; Eq. conditions-parameters for a_psi, dt. */
+    L->a_phi = (1.0 - p->a0_phi) / 4.0;
+    L->a_psi = (L->cs * L->cs) / (L->cd * L->cd) * L->a_phi;
+    L->a0_psi = 1.0 - 4.0 * L->a_psi;
+    L->dt = p->dh / L->cd * sqrt(2.0 * L->a_phi);
+    L->c = p->dh / L->dt;
+    long n = (long)p->nx * p->ny;
+    L->type = (uint8_t*)calloc((size_t)n, 1);
+    L->bc = alloc0(2 * n);
+    for (int set = 0; set < 2; ++set) {
+        for (int a = 0; a < 5; ++a) {
+            L->f[set][a] = alloc0(n);
+            L->fn[set][a] = alloc0(n);
+            L->fc[set][a] = alloc0(n);
+        }
+        L->s[set] = alloc0(n);
+    }
+    L->ux = alloc0(n); L->uy = alloc0(n); L->vx = alloc0(n); L->vy = alloc0(n);
+    L->ux1 = alloc0(n); L->uy1 = alloc0(n); L->vx1 = alloc0(n); L->vy1 = alloc0(n);
+    L->ax = alloc0(n); L->ay = alloc0(n);
+    for (int j = 0; j < p->ny; ++j) {
+        for (int i = 0; i < p->nx; ++i) {
+            long k = at(L, i, j);
+            uint8_t t = node_type ? node_type[k] : 0;
+            int bnd = is_boundary(L, i, j);
+            if (t > 2 || (bnd && t == 0) || (!bnd && t != 0)) {
+                ora_destroy(L);
+                return NULL;
+            }
+            L->type[k] = t;
+            if (bc_value) {
+                L->bc[2 * k] = bc_value[2 * k];
+                L->bc[2 * k + 1] = bc_value[2 * k + 1];
+            }
+        }
+    }
+    return L;
+}
+
+void ora_destroy(ora_lattice* L) {
+    if (!L) return;
+    free(L->type);
+    free(L->bc);
+    for (int set = 0; set < 2; ++set) {
+        for (int a = 0; a < 5; ++a) {
+            free(L->f[set][a]);
+            free(L->fn[set][a]);
+            free(L->fc[set][a]);
+        }
+        free(L->s[set]);
+    }
+    free(L->ux); free(L->uy); free(L->vx); free(L->vy);
+    free(L->ux1); free(L->uy1); free(L->vx1); free(L->vy1);
+    free(L->ax); free(L->ay);
+    free(L);
+}
+
+void ora_constants(const ora_lattice* L, double out[6]) {
+    out[0] = L->cd;
+    out[1] = L->cs;
+    out[2] = L->a_phi;
+    out[3] = L->a_psi;
+    out[4] = L->a0_psi;
+    out[5] = L->dt;
+}
+
+int64_t ora_steps_done(const ora_lattice* L) { return L->steps; }
+
+/* ------------------------------------------------------------------ init */
+
+int ora_init(ora_lattice* L, const double* ux0, const double* uy0, const double* vx0, const double* vy0) {
+    int nx = L->p.nx, ny = L->p.ny;
+    long n = (long)nx * ny;
+    for (long k = 0; k < n; ++k) {
+        if (!isfinite(ux0[k]) || !isfinite(uy0[k])) return -1;
+        if (vx0 && (!isfinite(vx0[k]) || !isfinite(vy0[k]))) return -1;
+    }
+    memcpy(L->ux, ux0, (size_t)n * sizeof(double));
+    memcpy(L->uy, uy0, (size_t)n * sizeof(double));
+    if (vx0) {
+        memcpy(L->vx, vx0, (size_t)n * sizeof(double));
+        memcpy(L->vy, vy0, (size_t)n * sizeof(double));
+    } else {
+        memset(L->vx, 0, (size_t)n * sizeof(double));
+        memset(L->vy, 0, (size_t)n * sizeof(double));
+    }
+    /* Fig. 3, initialisation: phi = div u, psi = curl u by finite differences,
+     * then f = f_eq (Eq. feq); first moments from reading R9. */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = at(L, i, j);
+            double phi = fd_div(L, L->ux, L->uy, i, j);
+            double psi = fd_curl(L, L->ux, L->uy, i, j);
+            double jphi_x = -L->vx[k], jphi_y = -L->vy[k];
+            double jpsi_x = -L->vy[k], jpsi_y = L->vx[k];
+            for (int a = 0; a < 5; ++a) {
+                L->f[0][a][k] = f_eq(L, 0, a, phi, jphi_x, jphi_y);
+                L->f[1][a][k] = f_eq(L, 1, a, psi, jpsi_x, jpsi_y);
+            }
+        }
+    }
+    L->steps = 0;
+    L->initialised = 1;
+    return 0;
+}
+
+/* ---------------------------------------------------------- accelerations */
+
+/* Interior points: Eq. navier with finite differences (reading R3). */
+static void accel_interior(const ora_lattice* L, int i, int j, double* ax, double* ay) {
+    double dphi_dx = d_dx(L, L->s[0], i, j), dphi_dy = d_dy(L, L->s[0], i, j);
+    double dpsi_dx = d_dx(L, L->s[1], i, j), dpsi_dy = d_dy(L, L->s[1], i, j);
+    double cd2 = L->cd * L->cd, cs2 = L->cs * L->cs;
+    /* curl(psi e_z) = (d psi/dy, -d psi/dx) */
+    *ax = cd2 * dphi_dx - cs2 * dpsi_dy;
+    *ay = cd2 * dphi_dy + cs2 * dpsi_dx;
+}
+
+/* Neumann points: momentum balance of the boundary cell, Eq.
+ * contBalanceOfMomentum simplified to Eq. acc_neumann (readings R5, R6). */
+static void accel_neumann(const ora_lattice* L, int i, int j, double* ax, double* ay) {
+    long k = at(L, i, j);
+    double half = 0.5 * L->p.dh;
+    int ti, tj;
+    int has_w = neighbour(L, i, j, -1, 0, &ti, &tj);
+    int has_e = neighbour(L, i, j, 1, 0, &ti, &tj);
+    int has_s = neighbour(L, i, j, 0, -1, &ti, &tj);
+    int has_n = neighbour(L, i, j, 0, 1, &ti, &tj);
+    /* Cell: square of side dh centred on x_k, clipped to the body. */
+    double wx = (has_w ? half : 0.0) + (has_e ? half : 0.0);
+    double wy = (has_s ? half : 0.0) + (has_n ? half : 0.0);
+    double vol = wx * wy;
+    double sk[3];
+    stress(L, L->ux, L->uy, i, j, sk);
+    /* External part: integral of t* over dC_ext, supplied per point. */
+    double fx = L->bc[2 * k], fy = L->bc[2 * k + 1];
+    /* Internal part: one face per neighbour r, normal n_kr pointing to r,
+     * length l_kr, stress sigma_kr = (sigma_k + sigma_r)/2. */
+    for (int a = 1; a < 5; ++a) {
+        int ri, rj;
+        if (!neighbour(L, i, j, EX[a], EY[a], &ri, &rj)) continue;
+        double sr[3];
+        stress(L, L->ux, L->uy, ri, rj, sr);
+        double sxx = 0.5 * (sk[0] + sr[0]);
+        double syy = 0.5 * (sk[1] + sr[1]);
+        double sxy = 0.5 * (sk[2] + sr[2]);
+        double nx_ = (double)EX[a], ny_ = (double)EY[a];
+        double len = (EX[a] != 0) ? wy : wx;
+        fx += (sxx * nx_ + sxy * ny_) * len;
+        fy += (sxy * nx_ + syy * ny_) * len;
+    }
+    *ax = fx / (L->p.rho * vol);
+    *ay = fy / (L->p.rho * vol);
+}
+
+/* Dirichlet points: Eq. acc_dirichlet (reading R12). */
+static void accel_dirichlet(const ora_lattice* L, int i, int j, double* ax, double* ay) {
+    long k = at(L, i, j);
+    double dt = L->dt;
+    *ax = 2.0 / (dt * dt) * (L->bc[2 * k] - L->ux[k]) - 2.0 / dt * L->vx[k];
+    *ay = 2.0 / (dt * dt) * (L->bc[2 * k + 1] - L->uy[k]) - 2.0 / dt * L->vy[k];
+}
+
+/* Moments phi, psi of the current populations (Eq. interpretation). */
+static void compute_moments(ora_lattice* L) {
+    int nx = L->p.nx, ny = L->p.ny;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = at(L, i, j);
+            for (int set = 0; set < 2; ++set) {
+                double g[5], s, jx, jy;
+                gather(L->f[set], k, g);
+                moments(L, g, &s, &jx, &jy);
+                L->s[set][k] = s;
+            }
+        }
+    }
+}
+
+static void compute_accelerations(ora_lattice* L) {
+    int nx = L->p.nx, ny = L->p.ny;
+    /* Fig. 3: interior first ... */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            if (L->type[at(L, i, j)] == 0) accel_interior(L, i, j, &L->ax[at(L, i, j)], &L->ay[at(L, i, j)]);
+    /* ... then boundary points. */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = at(L, i, j);
+            if (L->type[k] == 1) accel_neumann(L, i, j, &L->ax[k], &L->ay[k]);
+            else if (L->type[k] == 2) accel_dirichlet(L, i, j, &L->ax[k], &L->ay[k]);
+        }
+    }
+}
+
+/* -------------------------------------------------------------- one step */
+
+static void swap_ptr(double** a, double** b) {
+    double* t = *a;
+    *a = *b;
+    *b = t;
+}
+
+/* Sec. 3.2: phi, psi from finite differences of u everywhere, then the
+ * populations from Eq. correction-f with the current first moments. */
+static void synchronise(ora_lattice* L) {
+    int nx = L->p.nx, ny = L->p.ny;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = at(L, i, j);
+            double snew[2];
+            snew[0] = fd_div(L, L->ux, L->uy, i, j);
+            snew[1] = fd_curl(L, L->ux, L->uy, i, j);
+            for (int set = 0; set < 2; ++set) {
+                double g[5], s, jx, jy;
+                gather(L->f[set], k, g);
+                moments(L, g, &s, &jx, &jy);
+                for (int a = 0; a < 5; ++a) L->fn[set][a][k] = f_eq(L, set, a, snew[set], jx, jy);
+            }
+        }
+    }
+    for (int set = 0; set < 2; ++set)
+        for (int a = 0; a < 5; ++a) swap_ptr(&L->f[set][a], &L->fn[set][a]);
+}
+
+static void one_step(ora_lattice* L) {
+    int nx = L->p.nx, ny = L->p.ny;
+    double dt = L->dt;
+
+    /* Block 1: moments at t. */
+    compute_moments(L);
+
+    /* Blocks 2-3: accelerations at t. */
+    compute_accelerations(L);
+
+    /* Block 4: Newmark, Eq. integration, at every point. */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = at(L, i, j);
+            L->ux1[k] = L->ux[k] + dt * L->vx[k] + dt * dt / 2.0 * L->ax[k];
+            L->uy1[k] = L->uy[k] + dt * L->vy[k] + dt * dt / 2.0 * L->ay[k];
+            L->vx1[k] = L->vx[k] + dt * L->ax[k];
+            L->vy1[k] = L->vy[k] + dt * L->ay[k];
+        }
+    }
+
+    /* Block 5: boundary phi, psi from the new u (Eq. psi_phi_at_bound) and
+     * boundary populations from Eq. correction-f (reading R7). */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = at(L, i, j);
+            if (L->type[k] == 0) continue;
+            double snew[2];
+            snew[0] = fd_div(L, L->ux1, L->uy1, i, j);
+            snew[1] = fd_curl(L, L->ux1, L->uy1, i, j);
+            for (int set = 0; set < 2; ++set) {
+                double g[5], s, jx, jy;
+                gather(L->f[set], k, g);
+                moments(L, g, &s, &jx, &jy);
+                for (int a = 0; a < 5; ++a) L->fn[set][a][k] = f_eq(L, set, a, snew[set], jx, jy);
+            }
+        }
+    }
+
+    /* Block 6a: collision at every source point.  Boundary sources collide the
+     * time-averaged state f-tilde (Eq. LBE_mod); all others collide f(x,t)
+     * (Eq. LBE).  tau = dt/2 (reading R10). */
+    const double dt_over_tau = 2.0;
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = at(L, i, j);
+            int bnd = L->type[k] != 0;
+            for (int set = 0; set < 2; ++set) {
+                double fold[5], fhat[5], s, jx, jy;
+                gather(L->f[set], k, fold);
+                for (int a = 0; a < 5; ++a)
+                    fhat[a] = bnd ? 0.5 * (L->fn[set][a][k] + fold[a]) : fold[a];
+                if (bnd && L->p.bc_feq_mode == 1) moments(L, fold, &s, &jx, &jy);
+                else moments(L, fhat, &s, &jx, &jy);
+                for (int a = 0; a < 5; ++a) {
+                    double feq = f_eq(L, set, a, s, jx, jy);
+                    L->fc[set][a][k] = fhat[a] - dt_over_tau * (fhat[a] - feq);
+                }
+            }
+        }
+    }
+
+    /* Block 6b: streaming into interior points only; boundary points keep the
+     * values of block 5. */
+#pragma omp parallel for num_threads(g_threads) schedule(static)
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = at(L, i, j);
+            if (L->type[k] != 0) continue;
+            for (int a = 0; a < 5; ++a) {
+                int si = i, sj = j;
+                neighbour(L, i, j, -EX[a], -EY[a], &si, &sj); /* interior: always exists */
+                long ks = at(L, si, sj);
+                L->fn[0][a][k] = L->fc[0][a][ks];
+                L->fn[1][a][k] = L->fc[1][a][ks];
+            }
+        }
+    }
+
+    /* t -> t + dt */
+    for (int set = 0; set < 2; ++set)
+        for (int a = 0; a < 5; ++a) swap_ptr(&L->f[set][a], &L->fn[set][a]);
+    swap_ptr(&L->ux, &L->ux1);
+    swap_ptr(&L->uy, &L->uy1);
+    swap_ptr(&L->vx, &L->vx1);
+    swap_ptr(&L->vy, &L->vy1);
+    L->steps += 1;
+
+    /* Block 7: synchronisation every l-th step (Sec. 3.2). */
+    if (L->p.sync_every > 0 && L->steps % L->p.sync_every == 0) synchronise(L);
+}
+
+int ora_step(ora_lattice* L, int64_t n) {
+    if (!L->initialised || n < 0) return -1;
+    for (int64_t t = 0; t < n; ++t) one_step(L);
+    return 0;
+}
+
+int ora_sync(ora_lattice* L) {
+    if (!L->initialised) return -1;
+    synchronise(L);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ read */
+
+int ora_read(ora_lattice* L, int32_t field, double* dst) {
+    int nx = L->p.nx, ny = L->p.ny;
+    long n = (long)nx * ny;
+    switch (field) {
+    case ORA_UX: memcpy(dst, L->ux, (size_t)n * sizeof(double)); return 0;
+    case ORA_UY: memcpy(dst, L->uy, (size_t)n * sizeof(double)); return 0;
+    case ORA_VX: memcpy(dst, L->vx, (size_t)n * sizeof(double)); return 0;
+    case ORA_VY: memcpy(dst, L->vy, (size_t)n * sizeof(double)); return 0;
+    case ORA_PHI:
+    case ORA_PSI: {
+        compute_moments(L);
+        memcpy(dst, L->s[field == ORA_PHI ? 0 : 1], (size_t)n * sizeof(double));
+        return 0;
+    }
+    case ORA_F_PHI:
+    case ORA_F_PSI: {
+        int set = field == ORA_F_PHI ? 0 : 1;
+        for (int a = 0; a < 5; ++a) memcpy(dst + a * n, L->f[set][a], (size_t)n * sizeof(double));
+        return 0;
+    }
+    case ORA_ERR: {
+        /* Consistency error e(x,t) of Sec. 4. */
+        compute_moments(L);
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                long k = at(L, i, j);
+                double d_psi = L->s[1][k] - fd_curl(L, L->ux, L->uy, i, j);
+                double d_phi = L->s[0][k] - fd_div(L, L->ux, L->uy, i, j);
+                dst[k] = sqrt(d_psi * d_psi + d_phi * d_phi);
+            }
+        }
+        return 0;
+    }
+    case ORA_AX:
+    case ORA_AY: {
+        compute_moments(L);
+        compute_accelerations(L);
+        memcpy(dst, field == ORA_AX ? L->ax : L->ay, (size_t)n * sizeof(double));
+        return 0;
+    }
+    default: return -1;
+    }
+}
+
+/* ------------------------------------------------------ rectangle helper */
+
+int ora_rect_bc(int32_t nx, int32_t ny, int32_t periodic_x, int32_t periodic_y, double dh,
+                const int32_t edge_type[4], const double edge_value[8], uint8_t* node_type,
+                double* bc_value) {
+    if (nx < 3 || ny < 3 || !(dh > 0.0)) return -1;
+    /* edges: 0 bottom (j = 0), 1 right (i = nx-1), 2 top (j = ny-1), 3 left (i = 0) */
+    for (int e = 0; e < 4; ++e) {
+        int active = (e == 0 || e == 2) ? !periodic_y : !periodic_x;
+        if (active && edge_type[e] != 1 && edge_type[e] != 2) return -1;
+    }
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = (long)j * nx + i;
+            int on[4];
+            on[0] = !periodic_y && j == 0;
+            on[1] = !periodic_x && i == nx - 1;
+            on[2] = !periodic_y && j == ny - 1;
+            on[3] = !periodic_x && i == 0;
+            int n_on = on[0] + on[1] + on[2] + on[3];
+            node_type[k] = 0;
+            bc_value[2 * k] = 0.0;
+            bc_value[2 * k + 1] = 0.0;
+            if (n_on == 0) continue;
+            int n_dir = 0;
+            for (int e = 0; e < 4; ++e) n_dir += on[e] && edge_type[e] == 2;
+            if (n_dir > 0) {
+                /* Dirichlet dominates; the mean of the prescribed u* at a
+                 * Dirichlet-Dirichlet corner. */
+                node_type[k] = 2;
+                for (int e = 0; e < 4; ++e) {
+                    if (on[e] && edge_type[e] == 2) {
+                        bc_value[2 * k] += edge_value[2 * e] / n_dir;
+                        bc_value[2 * k + 1] += edge_value[2 * e + 1] / n_dir;
+                    }
+                }
+            } else {
+                /* Neumann: F = sum over the external faces of t* times the face
+                 * length; an edge point has one face of length dh, a corner two
+                 * of length dh/2. */
+                node_type[k] = 1;
+                double len = n_on == 1 ? dh : 0.5 * dh;
+                for (int e = 0; e < 4; ++e) {
+                    if (on[e]) {
+                        bc_value[2 * k] += edge_value[2 * e] * len;
+                        bc_value[2 * k + 1] += edge_value[2 * e + 1] * len;
+                    }
+                }
+            }
+        }
+    }
+    return 0;
+}

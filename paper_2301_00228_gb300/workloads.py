@@ -1,0 +1,192 @@
+"""Seeded synthetic inputs for the plane-strain LBM.
+
+This module only draws and samples initial displacement fields and boundary
+descriptions.  It contains none of the method's arithmetic, so both the CUDA
+path and the CPU oracle can take their inputs from it.
+
+Recipes (lattice units, dh = 1):
+
+* Gaussian pulses of dilatation or rotation are given through the exactly
+  irrotational / solenoidal displacement fields
+  ``u = A sigma^2 (1 - exp(-r^2 / (2 sigma^2))) / r`` along ``e_r`` (pure
+  dilatation, div u = A exp(-r^2/(2 sigma^2)), curl u = 0) or along
+  ``e_theta`` (pure rotation), sampled at the lattice points, u = 0 at r = 0.
+* Plane waves on periodic lattices use integer wave numbers (m, n) so that
+  they are periodic; the dilatational part points along k, the shear part
+  along k rotated by 90 degrees.  Started at rest they are standing waves.
+* Random rectangles draw each edge Dirichlet or Neumann with values in
+  U(-1e-3, 1e-3)^2 and lambda/mu from U(0.5, 4) with mu = rho = 1.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+NEUMANN, DIRICHLET = 1, 2
+EDGES = ("bottom", "right", "top", "left")
+
+
+def pulse_displacement(nx, ny, cx, cy, sigma, amp, kind="dilatation", dh=1.0):
+    """Displacement of one Gaussian pulse centred at (cx, cy) (lattice coordinates)."""
+    x = (np.arange(nx, dtype=np.float64) - cx) * dh
+    y = (np.arange(ny, dtype=np.float64) - cy) * dh
+    X, Y = np.meshgrid(x, y)
+    r = np.hypot(X, Y)
+    s = sigma * dh
+    with np.errstate(invalid="ignore", divide="ignore"):
+        g = amp * s * s * (-np.expm1(-r * r / (2.0 * s * s))) / r
+        g = np.where(r > 0.0, g / np.where(r > 0.0, r, 1.0), 0.0)  # g(r)/r
+    if kind == "dilatation":
+        return g * X, g * Y
+    if kind == "rotation":
+        return -g * Y, g * X
+    raise ValueError(kind)
+
+
+def plane_wave_displacement(nx, ny, m, n, amp_d, amp_s):
+    """u = amp_d khat sin(k.x) + amp_s khat_perp sin(k.x), k = 2 pi (m/nx, n/ny)."""
+    kx, ky = 2.0 * math.pi * m / nx, 2.0 * math.pi * n / ny
+    kn = math.hypot(kx, ky)
+    ex, ey = kx / kn, ky / kn
+    x = np.arange(nx, dtype=np.float64)
+    y = np.arange(ny, dtype=np.float64)
+    X, Y = np.meshgrid(x, y)
+    ph = np.sin(kx * X + ky * Y)
+    ux = (amp_d * ex - amp_s * ey) * ph
+    uy = (amp_d * ey + amp_s * ex) * ph
+    return ux, uy
+
+
+def pick_wave_numbers(size, wavelength, rng):
+    """Integer (m, n) whose |k| is nearest 2 pi / wavelength, at a random angle."""
+    target = size / wavelength
+    theta = rng.uniform(0.0, 2.0 * math.pi)
+    m = int(round(target * math.cos(theta)))
+    n = int(round(target * math.sin(theta)))
+    best = None
+    for dm in range(-2, 3):
+        for dn in range(-2, 3):
+            mm, nn = m + dm, n + dn
+            if mm == 0 and nn == 0:
+                continue
+            err = abs(math.hypot(mm, nn) - target) + 1e-3 * abs(math.atan2(nn, mm) - theta)
+            if best is None or err < best[0]:
+                best = (err, mm, nn)
+    return best[1], best[2]
+
+
+@dataclass
+class Domain:
+    """A rectangular solve: sizes, material, boundary description, initial u."""
+    nx: int
+    ny: int
+    lam: float
+    mu: float
+    rho: float = 1.0
+    a0_phi: float = 0.9999
+    periodic_x: bool = False
+    periodic_y: bool = False
+    edge_type: tuple = (NEUMANN, NEUMANN, NEUMANN, NEUMANN)
+    edge_value: tuple = ((0.0, 0.0),) * 4
+    pulses: list = field(default_factory=list)     # (cx, cy, sigma, amp, kind)
+    wave: tuple | None = None                      # (m, n, amp_d, amp_s)
+    steps: int = 0
+
+    def displacement(self):
+        ux = np.zeros((self.ny, self.nx))
+        uy = np.zeros((self.ny, self.nx))
+        for (cx, cy, sg, amp, kind) in self.pulses:
+            dx, dy = pulse_displacement(self.nx, self.ny, cx, cy, sg, amp, kind)
+            ux += dx
+            uy += dy
+        if self.wave is not None:
+            dx, dy = plane_wave_displacement(self.nx, self.ny, *self.wave)
+            ux += dx
+            uy += dy
+        return ux, uy
+
+    def edge_arrays(self):
+        return (np.asarray(self.edge_type, np.int32),
+                np.asarray(self.edge_value, np.float64).reshape(4, 2))
+
+
+def square_64():
+    """64 x 64, lambda = mu = rho = 1, left edge clamped (u* = 0), others
+    traction-free, centred dilatation pulse sigma = 4 cells, amplitude 1e-3,
+    1000 steps."""
+    return Domain(64, 64, 1.0, 1.0, edge_type=(NEUMANN, NEUMANN, NEUMANN, DIRICHLET),
+                  pulses=[(31.5, 31.5, 4.0, 1e-3, "dilatation")], steps=1000)
+
+
+def periodic_waves(size=1024, seed=2, wavelength=64.0, amp=1e-3, steps=10000):
+    """Periodic size x size lattice, lambda/mu = 2, superposed dilatational and
+    shear standing plane waves along a seeded direction."""
+    rng = np.random.default_rng(seed)
+    m, n = pick_wave_numbers(size, wavelength, rng)
+    return Domain(size, size, 2.0, 1.0, periodic_x=True, periodic_y=True,
+                  wave=(m, n, amp, amp), steps=steps)
+
+
+def random_rectangle(rng, side_lo=64, side_hi=512, steps=2000, sigma=4.0, amp=1e-3):
+    """One rectangle of the mixed-size batch: sides U{lo..hi}, random edges,
+    lambda/mu in U(0.5, 4), one pulse at a random point."""
+    nx = int(rng.integers(side_lo, side_hi + 1))
+    ny = int(rng.integers(side_lo, side_hi + 1))
+    et = tuple(int(x) for x in rng.choice([NEUMANN, DIRICHLET], size=4))
+    ev = tuple((float(a), float(b)) for a, b in rng.uniform(-1e-3, 1e-3, size=(4, 2)))
+    lam = float(rng.uniform(0.5, 4.0))
+    cx = float(rng.integers(0, nx))
+    cy = float(rng.integers(0, ny))
+    kind = "dilatation" if rng.random() < 0.5 else "rotation"
+    return Domain(nx, ny, lam, 1.0, edge_type=et, edge_value=ev,
+                  pulses=[(cx, cy, sigma, amp, kind)], steps=steps)
+
+
+def mixed_batch(count=256, seed=3, side_lo=64, side_hi=512, steps=2000):
+    rng = np.random.default_rng(seed)
+    return [random_rectangle(rng, side_lo, side_hi, steps) for _ in range(count)]
+
+
+def many_pulses(size=8192, seed=4, count=32, steps=5000, amp=1e-3):
+    """size x size, lambda/mu = 3, clamped bottom edge, traction-free others,
+    32 random dilatation/rotation pulses with sigma in U(8, 64)."""
+    rng = np.random.default_rng(seed)
+    pulses = []
+    for _ in range(count):
+        kind = "dilatation" if rng.random() < 0.5 else "rotation"
+        sg = float(rng.uniform(8.0, 64.0))
+        cx, cy = (float(v) for v in rng.uniform(0, size - 1, size=2))
+        pulses.append((cx, cy, sg, amp, kind))
+    return Domain(size, size, 3.0, 1.0, edge_type=(DIRICHLET, NEUMANN, NEUMANN, NEUMANN),
+                  pulses=pulses, steps=steps)
+
+
+def crop(domain: Domain, x0, y0, w, h):
+    """A w x h window of ``domain`` with the same boundary types on its edges and
+    the pulses whose centres fall inside (re-centred)."""
+    pulses = [(cx - x0, cy - y0, sg, amp, kind) for (cx, cy, sg, amp, kind) in domain.pulses
+              if x0 <= cx < x0 + w and y0 <= cy < y0 + h]
+    return Domain(w, h, domain.lam, domain.mu, domain.rho, domain.a0_phi,
+                  edge_type=domain.edge_type, edge_value=domain.edge_value, pulses=pulses,
+                  steps=domain.steps)
+
+
+def poisson_requests(count=10000, seed=5, rate_hz=1.0, side_lo=128, side_hi=2048,
+                     steps_lo=500, steps_hi=20000):
+    """Arrival times and domains of the serving stream: Poisson arrivals, sides
+    log-uniform, step counts uniform, boundaries and materials as random_rectangle."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, size=count))
+    out = []
+    for k in range(count):
+        nx = int(round(math.exp(rng.uniform(math.log(side_lo), math.log(side_hi)))))
+        ny = int(round(math.exp(rng.uniform(math.log(side_lo), math.log(side_hi)))))
+        d = random_rectangle(rng, 3, 3)  # draws edges, material, pulse kind
+        d.nx, d.ny = nx, ny
+        d.pulses = [(float(rng.integers(0, nx)), float(rng.integers(0, ny)), 4.0, 1e-3,
+                     d.pulses[0][4])]
+        d.steps = int(rng.integers(steps_lo, steps_hi + 1))
+        out.append((float(t[k]), d))
+    return out

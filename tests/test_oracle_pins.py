@@ -1,0 +1,460 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own code: closed forms of the
+discrete scheme derived on paper, continuum solutions, invariants, patch
+tests and brute force.  None of them re-types an oracle formula.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2301_00228_gb300 import workloads as W
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+def periodic_lattice(nx, ny, lam=2.0, mu=1.0, rho=1.0, a0=0.6, **kw):
+    return O.OracleLattice(nx, ny, lam, mu, rho, a0_phi=a0, periodic_x=True, periodic_y=True, **kw)
+
+
+# --------------------------------------------------------------- constants
+
+def test_constants_wave_speed_ratio():
+    """Sec. 4 fixes c_s/c_d = 1/sqrt(3) for its examples; with c_d = sqrt((lambda+2mu)/rho)
+    and c_s = sqrt(mu/rho) that is lambda = mu."""
+    lat = periodic_lattice(8, 8, lam=1.0, mu=1.0, rho=2.5, a0=0.9999)
+    assert lat.cs / lat.cd == pytest.approx(1.0 / math.sqrt(3.0), rel=1e-14)
+    assert lat.cd == pytest.approx(math.sqrt(3.0 / 2.5), rel=1e-14)
+
+
+def test_constants_parameter_rules():
+    """Eq. feq_req and Eq. conditions-parameters: a0 + 4a = 1 for both sets, one time step
+    for both wave speeds, CFL c_d dt/dh <= 1."""
+    for lam, mu, a0 in ((1.0, 1.0, 0.9999), (3.0, 0.7, 0.5), (0.5, 2.0, 0.0)):
+        lat = O.OracleLattice(6, 5, lam, mu, 1.3, dh=0.25, a0_phi=a0, periodic_x=True, periodic_y=True)
+        assert a0 + 4 * lat.a_phi == pytest.approx(1.0, abs=1e-15)
+        assert lat.a0_psi + 4 * lat.a_psi == pytest.approx(1.0, abs=1e-15)
+        assert lat.a0_psi >= 0.0
+        dt_phi = 0.25 / lat.cd * math.sqrt(2 * lat.a_phi)
+        dt_psi = 0.25 / lat.cs * math.sqrt(2 * lat.a_psi)
+        assert lat.dt == pytest.approx(dt_phi, rel=1e-14)
+        assert lat.dt == pytest.approx(dt_psi, rel=1e-14)
+        assert lat.cd * lat.dt / 0.25 <= 1.0
+
+
+# ---------------------------------------------------- interior = leapfrog
+
+def test_leapfrog_equivalence():
+    """With tau = dt/2 and J = 0 initially, the interior LBE is the five-point leapfrog
+    s^{n+1} = 2 s^n - s^{n-1} + 2a (sum of 4 neighbours - 4 s^n), s^1 = s^0 + a(...)
+    (a property of the D2Q5 wave model; derived by eliminating the populations)."""
+    rng = np.random.default_rng(11)
+    nx, ny = 24, 20
+    ux0, uy0 = rng.standard_normal((2, ny, nx)) * 1e-3
+    lat = periodic_lattice(nx, ny, lam=2.0, mu=1.0, a0=0.55)
+    lat.init(ux0, uy0)
+    s0 = {"phi": lat.read(O.PHI), "psi": lat.read(O.PSI)}
+    a = {"phi": lat.a_phi, "psi": lat.a_psi}
+
+    def lap(g):
+        return np.roll(g, 1, 0) + np.roll(g, -1, 0) + np.roll(g, 1, 1) + np.roll(g, -1, 1) - 4 * g
+
+    lf = {k: [s0[k], s0[k] + a[k] * lap(s0[k])] for k in s0}
+    for n in range(2, 41):
+        for k in lf:
+            lf[k].append(2 * lf[k][-1] - lf[k][-2] + 2 * a[k] * lap(lf[k][-1]))
+    for n in range(1, 41):
+        lat.step(1)
+        for k, fid in (("phi", O.PHI), ("psi", O.PSI)):
+            scale = np.abs(s0[k]).max()
+            assert np.abs(lat.read(fid) - lf[k][n]).max() <= 1e-12 * scale, (k, n)
+
+
+# ----------------------------------------------- discrete standing wave
+
+def standing_wave_expected(nx, ny, m, n, amp_d, amp_s, lam, mu, rho, a_phi, a_psi, dt, steps):
+    """Closed form of the scheme for a periodic plane wave started at rest.
+
+    u0 = A sin(k.x).  Central differences of sin/cos give
+        phi0 = Phi cos(k.x),  Phi = A_x sin kx + A_y sin ky,
+        psi0 = Psi cos(k.x),  Psi = A_y sin kx - A_x sin ky,
+    the leapfrog gives phi_n = Phi cos(n w_phi) cos(k.x) with cos w = 1 - 2a(2 - cos kx - cos ky),
+    the acceleration c_d^2 grad phi - c_s^2 curl(psi e_z) is sin(k.x) (P C_phi(n) + Q C_psi(n)),
+    and the Newmark recurrences are summed as scalar sequences.
+    """
+    kx, ky = 2 * math.pi * m / nx, 2 * math.pi * n / ny
+    kn = math.hypot(kx, ky)
+    ex, ey = kx / kn, ky / kn
+    Ax, Ay = amp_d * ex - amp_s * ey, amp_d * ey + amp_s * ex
+    Phi = Ax * math.sin(kx) + Ay * math.sin(ky)
+    Psi = Ay * math.sin(kx) - Ax * math.sin(ky)
+    cd2, cs2 = (lam + 2 * mu) / rho, mu / rho
+    K = 2 - math.cos(kx) - math.cos(ky)
+    w_phi = math.acos(1 - 2 * a_phi * K)
+    w_psi = math.acos(1 - 2 * a_psi * K)
+    # d/dx cos(k.x) -> -sin(k.x) sin kx ; d/dy -> -sin(k.x) sin ky
+    P = np.array([-cd2 * Phi * math.sin(kx), -cd2 * Phi * math.sin(ky)])
+    Q = np.array([cs2 * Psi * math.sin(ky), -cs2 * Psi * math.sin(kx)])
+    Ut = np.array([Ax, Ay], dtype=float)
+    Vt = np.zeros(2)
+    for q in range(steps):
+        acc = P * math.cos(q * w_phi) + Q * math.cos(q * w_psi)
+        Ut = Ut + dt * Vt + 0.5 * dt * dt * acc
+        Vt = Vt + dt * acc
+    X, Y = np.meshgrid(np.arange(nx), np.arange(ny))
+    ph = kx * X + ky * Y
+    return {
+        "phi": Phi * math.cos(steps * w_phi) * np.cos(ph),
+        "psi": Psi * math.cos(steps * w_psi) * np.cos(ph),
+        "ux": Ut[0] * np.sin(ph), "uy": Ut[1] * np.sin(ph),
+        "vx": Vt[0] * np.sin(ph), "vy": Vt[1] * np.sin(ph),
+    }
+
+
+@pytest.mark.parametrize("m,n,amp_d,amp_s", [(2, 1, 1e-3, 0.0), (1, 3, 0.0, 1e-3), (3, 2, 1e-3, -7e-4)])
+def test_standing_wave_closed_form(m, n, amp_d, amp_s):
+    nx, ny, lam, mu, rho, steps = 48, 40, 2.0, 1.0, 1.0, 300
+    lat = periodic_lattice(nx, ny, lam, mu, rho, a0=0.6)
+    ux0, uy0 = W.plane_wave_displacement(nx, ny, m, n, amp_d, amp_s)
+    lat.init(ux0, uy0).step(steps)
+    ex = standing_wave_expected(nx, ny, m, n, amp_d, amp_s, lam, mu, rho, lat.a_phi, lat.a_psi,
+                                lat.dt, steps)
+    got = lat.fields()
+    groups = (("phi", "psi"), ("ux", "uy"), ("vx", "vy"))
+    for g in groups:
+        scale = max(np.abs(ex[k]).max() for k in g)
+        for k in g:
+            assert np.abs(got[k] - ex[k]).max() <= 1e-11 * scale, k
+
+
+@pytest.mark.parametrize("field,speed", [("phi", "cd"), ("psi", "cs")])
+def test_wave_speeds(field, speed):
+    """The discrete frequency of a long plane wave gives the paper's wave speeds
+    c_d = sqrt((lambda+2mu)/rho), c_s = sqrt(mu/rho) within the O((k dh)^2) dispersion."""
+    nx, ny, lam, mu, rho = 256, 3, 3.0, 1.0, 1.7
+    lat = O.OracleLattice(nx, ny, lam, mu, rho, a0_phi=0.99, periodic_x=True, periodic_y=True)
+    k = 2 * math.pi * 4 / nx
+    if field == "phi":
+        ux0, uy0 = W.plane_wave_displacement(nx, ny, 4, 0, 1e-3, 0.0)
+        fid = O.PHI
+    else:
+        ux0, uy0 = W.plane_wave_displacement(nx, ny, 4, 0, 0.0, 1e-3)
+        fid = O.PSI
+    lat.init(ux0, uy0)
+    s0 = lat.read(fid)[1]
+    i0 = int(np.argmax(np.abs(s0)))
+    series = [s0[i0]]
+    for _ in range(400):
+        lat.step(1)
+        series.append(lat.read(fid)[1, i0])
+    series = np.array(series) / series[0]
+    # least-squares fit of cos(w n) over a frequency scan, refined
+    ns = np.arange(len(series))
+    ws = np.linspace(1e-4, 0.2, 20001)
+    err = [np.sum((series - np.cos(w * ns)) ** 2) for w in ws]
+    w = ws[int(np.argmin(err))]
+    c_meas = w / (k * lat.dt)
+    c_ref = math.sqrt((lam + 2 * mu) / rho) if speed == "cd" else math.sqrt(mu / rho)
+    assert abs(c_meas / c_ref - 1) < 3e-3
+
+
+# ------------------------------------------------------------ conservation
+
+def test_conservation_periodic():
+    """Periodic lattice: sum phi, sum psi and sum J are invariants of the LBE
+    (sum_alpha of 2 f_eq - f is s, its first moment is J); sum du/dt is invariant
+    because central differences telescope; sum u grows by dt * sum du/dt."""
+    rng = np.random.default_rng(5)
+    nx, ny = 32, 24
+    ux0, uy0, vx0, vy0 = rng.standard_normal((4, ny, nx)) * 1e-3
+    lat = periodic_lattice(nx, ny, lam=1.5, mu=0.8, a0=0.7)
+    lat.init(ux0, uy0, vx0, vy0)
+
+    def totals():
+        fphi, fpsi = lat.read(O.F_PHI), lat.read(O.F_PSI)
+        c = 1.0 / lat.dt
+        return (fphi.sum(), fpsi.sum(), c * (fphi[1] - fphi[3]).sum(), c * (fphi[2] - fphi[4]).sum(),
+                c * (fpsi[1] - fpsi[3]).sum(), c * (fpsi[2] - fpsi[4]).sum(),
+                lat.read(O.VX).sum(), lat.read(O.VY).sum())
+
+    t0 = totals()
+    sx0, sy0 = lat.read(O.UX).sum(), lat.read(O.UY).sum()
+    lat.step(100)
+    t1 = totals()
+    for a, b in zip(t0, t1):
+        assert abs(a - b) <= 1e-13 * nx * ny * 1e-3 * max(1.0, 1.0 / lat.dt)
+    assert lat.read(O.UX).sum() == pytest.approx(sx0 + 100 * lat.dt * t0[6], abs=1e-12)
+    assert lat.read(O.UY).sum() == pytest.approx(sy0 + 100 * lat.dt * t0[7], abs=1e-12)
+
+
+# -------------------------------------------------------------- patch tests
+
+def linear_field(nx, ny, G, d=(0.0, 0.0)):
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    return d[0] + G[0][0] * X + G[0][1] * Y, d[1] + G[1][0] * X + G[1][1] * Y
+
+
+def hooke(G, lam, mu):
+    """sigma for the uniform displacement gradient G (Eq. strain in Eq. hooke)."""
+    eps = 0.5 * (np.array(G) + np.array(G).T)
+    return lam * np.trace(eps) * np.eye(2) + 2 * mu * eps
+
+
+def assert_static(lat, ux0, uy0, steps=60, tol=1e-13):
+    lat.step(steps)
+    scale = max(np.abs(ux0).max(), np.abs(uy0).max(), 1e-3)
+    assert np.abs(lat.read(O.UX) - ux0).max() <= tol * scale
+    assert np.abs(lat.read(O.UY) - uy0).max() <= tol * scale
+    assert np.abs(lat.read(O.VX)).max() <= tol * scale / lat.dt
+    assert np.abs(lat.read(O.VY)).max() <= tol * scale / lat.dt
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_patch_rigid_motions(mode):
+    """Rigid translation and infinitesimal rigid rotation of a traction-free body stay at rest."""
+    nx, ny = 12, 9
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 1, 1), np.zeros(8))
+    for G, d in (([[0, 0], [0, 0]], (3e-4, -2e-4)), ([[0, -5e-4], [5e-4, 0]], (0.0, 0.0))):
+        ux0, uy0 = linear_field(nx, ny, G, d)
+        lat = O.OracleLattice(nx, ny, 1.3, 0.9, a0_phi=0.8, node_type=nt, bc_value=bv, bc_feq_mode=mode)
+        lat.init(ux0, uy0)
+        assert_static(lat, ux0, uy0)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_patch_uniform_strain_neumann(mode):
+    """A uniform displacement gradient with tractions t* = sigma n on every edge is an
+    equilibrium: finite differences are exact on linear fields and the traction of a
+    constant stress over a closed cell sums to zero, corners included."""
+    nx, ny, lam, mu = 11, 8, 2.0, 0.7
+    G = [[4e-4, 1.5e-4], [-0.5e-4, -2e-4]]
+    sig = hooke(G, lam, mu)
+    normals = ((0, -1), (1, 0), (0, 1), (-1, 0))  # bottom, right, top, left
+    ev = np.concatenate([sig @ np.array(n, float) for n in normals])
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 1, 1), ev)
+    ux0, uy0 = linear_field(nx, ny, G, (1e-4, 0.0))
+    lat = O.OracleLattice(nx, ny, lam, mu, a0_phi=0.9, node_type=nt, bc_value=bv, bc_feq_mode=mode)
+    lat.init(ux0, uy0)
+    assert_static(lat, ux0, uy0)
+
+
+def test_patch_uniform_strain_mixed():
+    """The same equilibrium with the left edge and its corners held by Dirichlet values."""
+    nx, ny, lam, mu = 9, 10, 1.0, 1.0
+    G = [[-3e-4, 2e-4], [1e-4, 5e-4]]
+    sig = hooke(G, lam, mu)
+    normals = ((0, -1), (1, 0), (0, 1), (-1, 0))
+    ev = np.concatenate([sig @ np.array(n, float) for n in normals])
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 1, 2), ev)
+    ux0, uy0 = linear_field(nx, ny, G)
+    dmask = nt == 2
+    bv[dmask, 0] = ux0[dmask]
+    bv[dmask, 1] = uy0[dmask]
+    assert dmask[:, 0].all() and dmask.sum() == ny
+    lat = O.OracleLattice(nx, ny, lam, mu, a0_phi=0.9999, node_type=nt, bc_value=bv)
+    lat.init(ux0, uy0)
+    assert_static(lat, ux0, uy0)
+
+
+def test_dirichlet_reaches_target():
+    """Eq. acc_dirichlet is chosen so that Eq. integration lands on u* after every step."""
+    rng = np.random.default_rng(3)
+    nx, ny = 10, 7
+    ev = rng.uniform(-1e-3, 1e-3, 8)
+    nt, bv = O.rect_bc(nx, ny, (2, 2, 2, 2), ev)
+    ux0, uy0 = rng.standard_normal((2, ny, nx)) * 1e-3
+    lat = O.OracleLattice(nx, ny, 1.0, 1.0, a0_phi=0.9, node_type=nt, bc_value=bv)
+    lat.init(ux0, uy0)
+    d = nt == 2
+    for _ in range(5):
+        lat.step(1)
+        assert np.abs(lat.read(O.UX)[d] - bv[d, 0]).max() <= 1e-15
+        assert np.abs(lat.read(O.UY)[d] - bv[d, 1]).max() <= 1e-15
+    # corner of two Dirichlet edges: mean of the two prescribed values (corner reading)
+    assert bv[0, 0, 0] == pytest.approx(0.5 * (ev[0] + ev[6]))
+
+
+# ------------------------------------------------------ continuum convergence
+
+def slab_error(N, kind, a0, sync_every, ny=3, rho=1.0):
+    """Slab 0 <= x <= L, periodic in y, first standing mode of the continuum solution
+    of Eq. navier1: traction-free edges (u = A cos(pi x/L) along x for the dilatational
+    wave, along y for the shear wave) or clamped edges (u_x = A sin(pi x/L))."""
+    L = N - 1
+    et = (2, 2, 2, 2) if kind == "clamped" else (1, 1, 1, 1)
+    nt, bv = O.rect_bc(N, ny, et, np.zeros(8), periodic_y=True)
+    lat = O.OracleLattice(N, ny, 1.0, 1.0, rho, a0_phi=a0, periodic_y=True, node_type=nt,
+                          bc_value=bv, sync_every=sync_every)
+    X = np.arange(N)[None, :] * np.ones((ny, 1))
+    k = math.pi / L
+    A = 1e-3
+    if kind == "free_d":
+        base, c, fid = np.cos(k * X), lat.cd, O.UX
+        lat.init(A * base, 0 * X)
+    elif kind == "free_s":
+        base, c, fid = np.cos(k * X), lat.cs, O.UY
+        lat.init(0 * X, A * base)
+    else:
+        base, c, fid = np.sin(k * X), lat.cd, O.UX
+        lat.init(A * base, 0 * X)
+    steps = int(round(0.5 * (2 * math.pi / (c * k)) / lat.dt))
+    lat.step(steps)
+    exact = A * base * math.cos(c * k * steps * lat.dt)
+    return np.abs(lat.read(fid) - exact).max() / A
+
+
+@pytest.mark.parametrize("kind,a0,sync,rho", [("free_d", 0.99, 1, 1.0), ("free_s", 0.99, 1, 1.0),
+                                              ("free_d", 0.99, 1, 2.5), ("clamped", 0.5, 0, 1.0)])
+def test_slab_convergence(kind, a0, sync, rho):
+    """Half a period of the first slab mode converges to the continuum solution at first
+    order in dh (the printed Newmark update is first order in the velocity).  Traction-free
+    edges need the synchronisation of Sec. 3.2 (here every step); clamped edges do not."""
+    sizes = (33, 65, 129) if kind == "clamped" else (17, 33, 65)
+    errs = [slab_error(N, kind, a0, sync, rho=rho) for N in sizes]
+    assert errs[-1] < 3e-2
+    for a, b in zip(errs, errs[1:]):
+        assert a / b > 1.7
+
+
+# ------------------------------------------------------ linearity, symmetry
+
+def test_linearity():
+    """The scheme is linear in (u0, v0) for homogeneous boundary data."""
+    nx, ny = 20, 16
+    nt, bv = O.rect_bc(nx, ny, (2, 1, 1, 2), np.zeros(8))
+    u1 = W.pulse_displacement(nx, ny, 7.0, 8.0, 3.0, 1e-3, "dilatation")
+    u2 = W.pulse_displacement(nx, ny, 12.0, 6.0, 2.5, 7e-4, "rotation")
+
+    def run(ux, uy):
+        lat = O.OracleLattice(nx, ny, 1.7, 1.0, a0_phi=0.9, node_type=nt, bc_value=bv)
+        return lat.init(ux, uy).step(40).fields()
+
+    a, b = run(*u1), run(*u2)
+    c = run(u1[0] + u2[0], u1[1] + u2[1])
+    for k in c:
+        scale = np.abs(c[k]).max()
+        assert np.abs(c[k] - a[k] - b[k]).max() <= 1e-12 * scale, k
+
+
+def test_mirror_symmetry():
+    """A pulse centred on a mirror line of a symmetric problem keeps the mirror symmetry."""
+    nx, ny = 21, 15
+    nt, bv = O.rect_bc(nx, ny, (1, 2, 1, 2), np.zeros(8))
+    ux0, uy0 = W.pulse_displacement(nx, ny, 10.0, 7.0, 3.0, 1e-3, "dilatation")
+    lat = O.OracleLattice(nx, ny, 1.0, 1.0, a0_phi=0.8, node_type=nt, bc_value=bv)
+    f = lat.init(ux0, uy0).step(60).fields()
+    s = np.abs(f["ux"]).max()
+    assert np.abs(f["ux"] + f["ux"][:, ::-1]).max() <= 1e-13 * s
+    assert np.abs(f["ux"] - f["ux"][::-1, :]).max() <= 1e-13 * s
+    assert np.abs(f["uy"] - f["uy"][:, ::-1]).max() <= 1e-13 * s
+    assert np.abs(f["uy"] + f["uy"][::-1, :]).max() <= 1e-13 * s
+    assert np.abs(f["phi"] - f["phi"][:, ::-1]).max() <= 1e-13 * np.abs(f["phi"]).max()
+
+
+# -------------------------------------------------------------- synchronise
+
+def test_sync_restores_consistency():
+    """After the synchronisation of Sec. 3.2 the consistency error e of Sec. 4 vanishes and
+    the first moments are unchanged."""
+    nx, ny = 18, 14
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 2, 1), np.zeros(8))
+    ux0, uy0 = W.pulse_displacement(nx, ny, 9.0, 6.0, 2.0, 1e-3, "rotation")
+    lat = O.OracleLattice(nx, ny, 1.0, 1.0, a0_phi=0.7, node_type=nt, bc_value=bv)
+    lat.init(ux0, uy0).step(25)
+    assert lat.read(O.ERR).max() > 1e-9
+    f0 = lat.read(O.F_PHI)
+    lat.sync()
+    assert lat.read(O.ERR).max() <= 1e-17
+    f1 = lat.read(O.F_PHI)
+    assert np.abs((f1[1] - f1[3]) - (f0[1] - f0[3])).max() <= 1e-18
+
+
+def test_sync_every_matches_manual():
+    nx, ny = 12, 10
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 1, 1), np.zeros(8))
+    u = W.pulse_displacement(nx, ny, 5.0, 5.0, 2.0, 1e-3, "dilatation")
+    a = O.OracleLattice(nx, ny, 1.0, 1.0, a0_phi=0.8, node_type=nt, bc_value=bv, sync_every=4).init(*u)
+    b = O.OracleLattice(nx, ny, 1.0, 1.0, a0_phi=0.8, node_type=nt, bc_value=bv).init(*u)
+    a.step(12)
+    for _ in range(3):
+        b.step(4).sync()
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_initial_state_consistent():
+    """Fig. 3 initialises phi, psi by finite differences of u, so e(x, 0) = 0."""
+    nx, ny = 15, 13
+    nt, bv = O.rect_bc(nx, ny, (2, 1, 1, 1), np.zeros(8))
+    u = W.pulse_displacement(nx, ny, 6.0, 7.0, 2.0, 1e-3, "dilatation")
+    lat = O.OracleLattice(nx, ny, 1.0, 1.0, node_type=nt, bc_value=bv).init(*u)
+    assert lat.read(O.ERR).max() <= 1e-15 * 1e-3
+
+
+def test_init_polynomial_exact():
+    """Second-order differences (central and one-sided) are exact on quadratics, so the
+    initial phi, psi equal the analytic divergence and curl everywhere, edges included."""
+    nx, ny = 7, 6
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 1, 1), np.zeros(8))
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    ux = 1e-4 * (X * X - 2 * X * Y + 3 * Y)
+    uy = 1e-4 * (0.5 * Y * Y + X * Y - X)
+    lat = O.OracleLattice(nx, ny, 1.0, 1.0, node_type=nt, bc_value=bv).init(ux, uy)
+    div = 1e-4 * ((2 * X - 2 * Y) + (Y + X))
+    curl = 1e-4 * ((Y - 1) - (-2 * X + 3))
+    assert np.abs(lat.read(O.PHI) - div).max() <= 1e-17
+    assert np.abs(lat.read(O.PSI) - curl).max() <= 1e-17
+
+
+def test_consistency_error_peaks_at_second_row():
+    """Sec. 4 (tension example, Fig. 9): under a traction on the top and bottom edges the
+    consistency error appears at the 'second row' points of the loaded edges.  The
+    magnitude 4.3e-12 printed there cannot be reproduced (resolution not given)."""
+    nx = ny = 33
+    s0 = 5e-3
+    ev = np.array([0, -s0, 0, 0, 0, s0, 0, 0], float)  # bottom -sigma0 e_y, top +sigma0 e_y
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 1, 1), ev)
+    lat = O.OracleLattice(nx, ny, 1.0, 1.0, a0_phi=0.9999, node_type=nt, bc_value=bv)
+    lat.init(np.zeros((ny, nx)), np.zeros((ny, nx))).step(3)
+    e = lat.read(O.ERR)
+    j, i = np.unravel_index(int(np.argmax(e)), e.shape)
+    assert j in (1, ny - 2)
+
+
+# ------------------------------------------------------------ rect helper
+
+def test_rect_bc_types_and_values():
+    nx, ny = 5, 4
+    ev = np.array([1, 2, 3, 4, 5, 6, 7, 8], float)  # bottom, right, top, left
+    nt, bv = O.rect_bc(nx, ny, (1, 2, 1, 1), ev, dh=0.5)
+    expected_types = np.array([
+        [1, 1, 1, 1, 2],
+        [1, 0, 0, 0, 2],
+        [1, 0, 0, 0, 2],
+        [1, 1, 1, 1, 2]], np.uint8)
+    assert np.array_equal(nt, expected_types)
+    # Neumann edge point: t* times dh
+    assert np.allclose(bv[0, 2], [0.5, 1.0])
+    # Neumann-Neumann corner (bottom-left): half faces of both edges
+    assert np.allclose(bv[0, 0], [0.25 * 1 + 0.25 * 7, 0.25 * 2 + 0.25 * 8])
+    # Dirichlet right edge dominates its corners: u* of the right edge
+    assert np.allclose(bv[0, 4], [3, 4]) and np.allclose(bv[3, 4], [3, 4])
+    assert np.allclose(bv[1, 1], [0, 0])
+
+
+def test_rect_bc_periodic():
+    nt, bv = O.rect_bc(6, 5, (2, 0, 1, 0), np.array([1, 1, 0, 0, 2, 2, 0, 0.]), periodic_x=True)
+    assert (nt[0] == 2).all() and (nt[-1] == 1).all() and (nt[1:-1] == 0).all()
+    assert np.allclose(bv[-1], [2, 2])
+
+
+def test_rejects_bad_masks():
+    nt, bv = O.rect_bc(6, 5, (1, 1, 1, 1), np.zeros(8))
+    nt[2, 2] = 1
+    with pytest.raises(ValueError):
+        O.OracleLattice(6, 5, 1.0, 1.0, node_type=nt, bc_value=bv)
+    with pytest.raises(ValueError):
+        O.OracleLattice(2, 5, 1.0, 1.0, periodic_x=True, periodic_y=True)
