@@ -1,0 +1,184 @@
+/*
+ * lbps.h -- C ABI of the GB300 plane-strain lattice Boltzmann solver.
+ *
+ * Method: Schlueter, Yan, Faust, Mueller & Mueller, "A Lattice Boltzmann
+ * Method for Elastic Solids Under Plane Strain Deformation",
+ * arXiv:2301.00228.  The calls follow the paper's statement of the problem
+ * (Sec. 2: a body with Dirichlet data u* and Neumann data t* on its edges)
+ * and its algorithm summary (Fig. 3: build the lattice, initialise, run the
+ * time loop, read fields).  Every time step runs on the GPU in hand-written
+ * sm_103a CUDA kernels; nothing here falls back to the host.
+ *
+ * Conventions
+ *   - Host arrays are row-major [ny][nx], x fastest, FP64 unless stated.
+ *   - The caller owns every buffer it passes; the library copies what it
+ *     needs during the call and keeps no pointer to caller host memory.
+ *   - Device memory: lbps_create either allocates it (device_mem == NULL)
+ *     or lives in a caller-provided device block of lbps_state_bytes()
+ *     bytes that must outlive the lattice (e.g. a torch tensor).
+ *   - Every call returns LBPS_OK (0) or a negative LBPS_ERR_* code.  No call
+ *     aborts, prints or throws.  lbps_strerror() names the code.
+ *   - Work is enqueued on params.cuda_stream (a cudaStream_t; NULL means
+ *     the legacy default stream).  Calls that take host buffers synchronise
+ *     the stream before returning; *_async / *_device calls do not.
+ *   - Units are the caller's; the configurations used by the tests take
+ *     lattice units (dh = 1).
+ */
+#ifndef LBPS_H
+#define LBPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBPS_OK 0
+#define LBPS_ERR_INVALID (-1)   /* bad argument, size, mask or parameter      */
+#define LBPS_ERR_OOM (-2)       /* device allocation failed / block too small */
+#define LBPS_ERR_CUDA (-3)      /* a CUDA runtime call or launch failed       */
+#define LBPS_ERR_NONFINITE (-4) /* the state became non-finite (instability)  */
+#define LBPS_ERR_TIMEOUT (-5)   /* a bounded device wait gave up              */
+#define LBPS_ERR_STATE (-6)     /* call out of order (e.g. step before init)  */
+
+/* Node types of the boundary mask (Sec. 2, Fig. 1). */
+#define LBPS_INTERIOR 0
+#define LBPS_NEUMANN 1          /* traction t* prescribed: Eq. acc_neumann    */
+#define LBPS_DIRICHLET 2        /* displacement u* prescribed: Eq. acc_dirichlet */
+
+/* Storage of the populations (Eq. interpretation).  u and du/dt are FP64 in
+ * every format. */
+#define LBPS_STORAGE_F32 0      /* FP32 populations, FP32 arithmetic          */
+#define LBPS_STORAGE_F64 1      /* FP64 populations, FP64 arithmetic          */
+
+/* Fields for lbps_read / lbps_read_device. */
+#define LBPS_UX 0               /* displacement u_x                            */
+#define LBPS_UY 1
+#define LBPS_VX 2               /* velocity du_x/dt                            */
+#define LBPS_VY 3
+#define LBPS_PHI 4              /* dilatation phi = sum_alpha f_phi^alpha      */
+#define LBPS_PSI 5              /* rotation psi = sum_alpha f_psi^alpha        */
+#define LBPS_F_PHI 6            /* the 5 phi populations, [5][ny][nx]          */
+#define LBPS_F_PSI 7            /* the 5 psi populations, [5][ny][nx]          */
+#define LBPS_CONSISTENCY 8      /* error measure e(x,t) of Sec. 4              */
+
+typedef struct lbps_params {
+    int32_t nx, ny;             /* lattice points along x, y; each >= 3       */
+    double lambda, mu, rho;     /* Lame constants, density (Sec. 2);
+                                   mu > 0, rho > 0, lambda + 2 mu > 0          */
+    double dh;                  /* lattice spacing Delta h > 0 (Sec. 3)       */
+    double a0_phi;              /* rest weight a_{0,phi} in [0, 1) of Eq. feq;
+                                   the paper's examples use 0.9999 (Sec. 4)   */
+    int32_t periodic_x;         /* 1: x wraps around, no boundary along x     */
+    int32_t periodic_y;
+    int32_t bc_feq_mode;        /* Eq. LBE_mod equilibrium: 0 = moments of the
+                                   averaged state f-hat, 1 = moments of
+                                   f(x_k, t)                                   */
+    int32_t sync_every;         /* l of Sec. 3.2 (0 = no synchronisation)     */
+    int32_t storage;            /* LBPS_STORAGE_*                              */
+    void* cuda_stream;          /* cudaStream_t for all work of this lattice  */
+} lbps_params;
+
+typedef struct lbps_lattice lbps_lattice; /* opaque, library-owned */
+
+/* Name of an error code (static string). */
+const char* lbps_strerror(int code);
+
+/* Rectangle helper (Sec. 2, Fig. 1; boundary cells of Sec. 3.1.1).
+ * Fills node_type[ny][nx] and bc_value[ny][nx][2] for a rectangle whose four
+ * edges (order: bottom y=0, right x=nx-1, top y=ny-1, left x=0) are each
+ * Neumann or Dirichlet.  edge_value[2e], [2e+1]: u* of a Dirichlet edge, or
+ * traction t* (force per unit length) of a Neumann edge, which is integrated
+ * over each boundary cell's external faces (Eq. acc_neumann): dh at an edge
+ * point, dh/2 per edge at a corner.  At corners Dirichlet dominates; two
+ * Dirichlet edges give the mean u*.  Edges of periodic directions are
+ * ignored.  Returns LBPS_ERR_INVALID for sides < 3 or an edge type other
+ * than 1 or 2 on a non-periodic edge. */
+int lbps_rect_bc(int32_t nx, int32_t ny, int32_t periodic_x, int32_t periodic_y, double dh,
+                 const int32_t edge_type[4], const double edge_value[8],
+                 uint8_t* node_type, double* bc_value);
+
+/* Device bytes that lbps_create needs for this lattice (two state copies,
+ * boundary tables and reduction scratch). */
+int lbps_state_bytes(const lbps_params* params, size_t* bytes);
+
+/* Build the lattice (Fig. 3, preprocessing).
+ * node_type[ny][nx]: LBPS_INTERIOR inside, LBPS_NEUMANN or LBPS_DIRICHLET on
+ * the outer ring of every non-periodic direction (exactly there), or NULL for
+ * a fully periodic lattice.  bc_value[ny][nx][2]: u* at Dirichlet points, the
+ * integrated external force F = int_{dC_ext} t* da at Neumann points (Eq.
+ * acc_neumann); NULL means zero.  device_mem: NULL to let the library
+ * allocate, or a device block of at least lbps_state_bytes() bytes, 256-byte
+ * aligned, owned by the caller.  On success *out owns the lattice. */
+int lbps_create(const lbps_params* params, const uint8_t* node_type, const double* bc_value,
+                void* device_mem, size_t device_bytes, lbps_lattice** out);
+
+/* Initialisation (Fig. 3; Sec. 3 before Eq. integration): u(x,0), du/dt(x,0)
+ * from host arrays [ny][nx]; phi, psi by finite differences of u; the
+ * populations at equilibrium (Eq. feq).  vx0/vy0 may both be NULL (body at
+ * rest); otherwise the first moments start at J_phi = -v, J_psi = (-v_y, v_x).
+ * Rejects non-finite input with LBPS_ERR_INVALID.  Synchronises. */
+int lbps_init(lbps_lattice* lat, const double* ux0, const double* uy0,
+              const double* vx0, const double* vy0);
+
+/* As lbps_init with device arrays [ny][nx]; asynchronous, no finiteness check. */
+int lbps_init_device(lbps_lattice* lat, const double* d_ux0, const double* d_uy0,
+                     const double* d_vx0, const double* d_vy0);
+
+/* Time loop of Fig. 3, n iterations: accelerations (Eq. navier,
+ * acc_neumann, acc_dirichlet), Newmark (Eq. integration), boundary reset
+ * (Eq. psi_phi_at_bound, correction-f), LBE with the averaged boundary state
+ * (Eq. LBE, LBE_mod), and every sync_every-th step the synchronisation of
+ * Sec. 3.2.  Enqueues the work, then waits for the stream and returns
+ * LBPS_ERR_NONFINITE if any update produced a non-finite value. */
+int lbps_step(lbps_lattice* lat, int64_t n);
+
+/* As lbps_step without the final wait and check (use lbps_check later). */
+int lbps_step_async(lbps_lattice* lat, int64_t n);
+
+/* Waits for the stream; LBPS_ERR_NONFINITE if the state went non-finite
+ * since creation. */
+int lbps_check(lbps_lattice* lat);
+
+/* Periodic synchronisation of Sec. 3.2 applied now to the current state. */
+int lbps_sync(lbps_lattice* lat);
+
+/* Copy a field to host memory as FP64 [ny][nx] (populations: [5][ny][nx]).
+ * count is the capacity of dst in doubles.  Synchronises. */
+int lbps_read(lbps_lattice* lat, int32_t field, double* dst, size_t count);
+
+/* As lbps_read into device memory; asynchronous. */
+int lbps_read_device(lbps_lattice* lat, int32_t field, double* d_dst, size_t count);
+
+/* FP64 reductions over the lattice for one scalar field (LBPS_UX ..
+ * LBPS_PSI, LBPS_CONSISTENCY): out[0] = sum (x - ref)^2, out[1] = sum ref^2,
+ * out[2] = sum x, out[3] = max |x|.  d_ref is a device array [ny][nx] or
+ * NULL (ref = 0).  Deterministic order.  Synchronises. */
+int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out[4]);
+
+/* Derived constants (Eq. conditions-parameters): out[0] c_d, out[1] c_s,
+ * out[2] a_phi, out[3] a_psi, out[4] a_{0,psi}, out[5] Delta t; and the
+ * number of completed time steps. */
+int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done);
+
+/* Per-kernel timing for roofline reports.  enable != 0 starts recording a
+ * CUDA event before and after every kernel launch of the time loop on the
+ * lattice's stream (the two kernels of a step stay back to back); 0 stops.
+ * lbps_profile_read waits for the stream and returns, since recording
+ * started: out[0] total milliseconds in the bulk (interior) kernel, out[1]
+ * its launches, out[2] total milliseconds in the boundary kernel, out[3] its
+ * launches; then clears the record. */
+int lbps_profile(lbps_lattice* lat, int32_t enable);
+int lbps_profile_read(lbps_lattice* lat, double out[4]);
+
+/* Switch the stream used by later calls. */
+int lbps_set_stream(lbps_lattice* lat, void* cuda_stream);
+
+/* Release the lattice and any device memory the library allocated. */
+void lbps_destroy(lbps_lattice* lat);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBPS_H */

@@ -45,7 +45,11 @@
  *       balance of the LBE) and d(phi)/dt = div v.  All inputs at rest give
  *       J = 0.
  *   R10 tau = dt/2 in both Eq. LBE and Eq. LBE_mod (so dt/tau = 1/tau = 2).
- *   R11 The Newmark update is used as printed (gamma = 1 for the velocity).
+ *   R11 The Newmark update is used as printed: beta = 0 and gamma = 0 (the
+ *       velocity takes the acceleration at t only).  It is first order, and
+ *       modes whose acceleration feeds back on u (boundary points) grow by
+ *       about 1 + (omega dt)^2 / 4 per step, which is why small a_phi (the
+ *       paper's a_{0,phi} = 0.9999, Sec. 4) is needed for stability.
  *   R12 Dirichlet u* is constant in time, so u*(t) and u*(t+dt) coincide.
  */
 #include "lbm_oracle.h"

@@ -1,0 +1,577 @@
+// C ABI of the plane-strain LBM library (declarations and contracts in
+// include/lbps.h).  Host-side work only: validation, the rectangle helper,
+// the device memory layout, and enqueueing the kernels of lbps_kernels.cu.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbps.h"
+#include "lbps_launch.h"
+
+using lbps::BNode;
+using lbps::Consts;
+using lbps::Geo;
+using lbps::KC;
+using lbps::View;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStagingMax = size_t(8) << 20;  // host read/write staging, bytes
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    Geo g;
+    size_t elem;        // bytes per population value
+    size_t f_bytes;     // 10 population planes, aligned
+    size_t u_bytes;     // 4 FP64 planes, aligned
+    size_t copy_bytes;
+    size_t off_copy[2];
+    size_t off_bn, off_part, off_out, off_flag, off_staging;
+    size_t staging_bytes;
+    size_t total;
+    int nb;
+};
+
+bool finite_positive(double x) { return std::isfinite(x) && x > 0.0; }
+
+int validate_params(const lbps_params* p) {
+    if (!p) return LBPS_ERR_INVALID;
+    if (p->nx < 3 || p->ny < 3 || p->nx > (1 << 24) || p->ny > (1 << 24)) return LBPS_ERR_INVALID;
+    if (!finite_positive(p->mu) || !finite_positive(p->rho) || !std::isfinite(p->lambda)) return LBPS_ERR_INVALID;
+    if (!(p->lambda + 2.0 * p->mu > 0.0) || !finite_positive(p->dh)) return LBPS_ERR_INVALID;
+    if (!(p->a0_phi >= 0.0 && p->a0_phi < 1.0)) return LBPS_ERR_INVALID;
+    if (p->bc_feq_mode != 0 && p->bc_feq_mode != 1) return LBPS_ERR_INVALID;
+    if (p->sync_every < 0) return LBPS_ERR_INVALID;
+    if (p->storage != LBPS_STORAGE_F32 && p->storage != LBPS_STORAGE_F64) return LBPS_ERR_INVALID;
+    if ((p->periodic_x != 0 && p->periodic_x != 1) || (p->periodic_y != 0 && p->periodic_y != 1))
+        return LBPS_ERR_INVALID;
+    return LBPS_OK;
+}
+
+Layout make_layout(const lbps_params* p) {
+    Layout L{};
+    L.g.nx = p->nx;
+    L.g.ny = p->ny;
+    L.g.px = (p->nx + 31) / 32 * 32;
+    L.g.periodic_x = p->periodic_x;
+    L.g.periodic_y = p->periodic_y;
+    L.g.plane = (size_t)L.g.px * (size_t)p->ny;
+    L.elem = p->storage == LBPS_STORAGE_F64 ? 8 : 4;
+    L.f_bytes = align_up(10 * L.g.plane * L.elem);
+    L.u_bytes = align_up(4 * L.g.plane * 8);
+    L.copy_bytes = L.f_bytes + L.u_bytes;
+    L.nb = lbps::perim_count(L.g);
+    size_t off = 0;
+    L.off_copy[0] = off;
+    off += L.copy_bytes;
+    L.off_copy[1] = off;
+    off += L.copy_bytes;
+    L.off_bn = off;
+    off += align_up((size_t)L.nb * sizeof(BNode));
+    L.off_part = off;
+    off += align_up((size_t)lbps::kNormBlocks * 4 * sizeof(double));
+    L.off_out = off;
+    off += kAlign;
+    L.off_flag = off;
+    off += kAlign;
+    size_t dense = 5 * (size_t)p->nx * (size_t)p->ny * sizeof(double);
+    L.staging_bytes = align_up(dense < kStagingMax ? dense : kStagingMax);
+    L.off_staging = off;
+    off += L.staging_bytes;
+    L.total = off;
+    return L;
+}
+
+template <typename T>
+KC<T> make_kc(double a_phi, double a_psi, double cd2, double cs2, double dh) {
+    KC<T> k;
+    double a[2] = {a_phi, a_psi};
+    for (int s = 0; s < 2; ++s) {
+        T at = (T)a[s];
+        T a0t = (T)(1.0 - 4.0 * (double)at);
+        k.a[s] = at;
+        k.two_a[s] = (T)2 * at;
+        k.eight_a[s] = (T)8 * at;
+        k.two_a0[s] = (T)2 * a0t;
+    }
+    k.cd2h = (T)(cd2 * 0.5 / dh);
+    k.cs2h = (T)(cs2 * 0.5 / dh);
+    return k;
+}
+
+}  // namespace
+
+struct lbps_lattice {
+    lbps_params p;
+    Layout L;
+    Consts c;
+    KC<float> kf;
+    KC<double> kd;
+    double cd, cs, a_phi, a_psi, a0_psi;
+    cudaStream_t st;
+    char* mem;
+    bool owns;
+    int cur;            // copy holding time t
+    int64_t steps;
+    bool initialised;
+    // per-kernel event timing (lbps_profile)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<int> ev_kind;   // per recorded pair: 0 bulk, 1 boundary
+
+    template <typename T>
+    View<T> view(int q) const {
+        View<T> v;
+        v.f = reinterpret_cast<T*>(mem + L.off_copy[q]);
+        v.u = reinterpret_cast<double*>(mem + L.off_copy[q] + L.f_bytes);
+        return v;
+    }
+    const BNode* bn() const { return reinterpret_cast<const BNode*>(mem + L.off_bn); }
+    unsigned* flag() const { return reinterpret_cast<unsigned*>(mem + L.off_flag); }
+    double* partials() const { return reinterpret_cast<double*>(mem + L.off_part); }
+    double* out4() const { return reinterpret_cast<double*>(mem + L.off_out); }
+    double* staging() const { return reinterpret_cast<double*>(mem + L.off_staging); }
+    bool f64() const { return p.storage == LBPS_STORAGE_F64; }
+};
+
+namespace {
+
+int cuda_ok(cudaError_t e) { return e == cudaSuccess ? LBPS_OK : LBPS_ERR_CUDA; }
+
+// Next free event of the profiling pool (created on demand).
+cudaEvent_t next_event(lbps_lattice* lat) {
+    if (lat->ev_used == lat->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        lat->ev_pool.push_back(e);
+    }
+    return lat->ev_pool[lat->ev_used++];
+}
+
+// Records an event on the stream when profiling; the pair (start, end) of a
+// kernel is two consecutive pool entries.
+cudaError_t prof_mark(lbps_lattice* lat) {
+    if (!lat->prof) return cudaSuccess;
+    cudaEvent_t e = next_event(lat);
+    if (!e) return cudaErrorMemoryAllocation;
+    return cudaEventRecord(e, lat->st);
+}
+
+int run_step(lbps_lattice* lat) {
+    int a = lat->cur, b = lat->cur ^ 1;
+    cudaError_t e = cudaSuccess;
+    if (lat->L.nb > 0) {
+        e = prof_mark(lat);
+        if (e == cudaSuccess) {
+            if (lat->f64())
+                e = lbps::launch_boundary<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(a), lat->view<double>(b),
+                                                  lat->bn(), lat->L.nb, lat->flag(), lat->st);
+            else
+                e = lbps::launch_boundary<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(a), lat->view<float>(b),
+                                                 lat->bn(), lat->L.nb, lat->flag(), lat->st);
+        }
+        if (e == cudaSuccess) e = prof_mark(lat);
+        if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(1);
+    }
+    if (e == cudaSuccess) e = prof_mark(lat);
+    if (e == cudaSuccess) {
+        if (lat->f64())
+            e = lbps::launch_bulk<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(a), lat->view<double>(b),
+                                          lat->flag(), lat->st);
+        else
+            e = lbps::launch_bulk<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(a), lat->view<float>(b),
+                                         lat->flag(), lat->st);
+    }
+    if (e == cudaSuccess) e = prof_mark(lat);
+    if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(0);
+    if (e != cudaSuccess) return LBPS_ERR_CUDA;
+    lat->cur = b;
+    lat->steps += 1;
+    return LBPS_OK;
+}
+
+int run_sync(lbps_lattice* lat) {
+    cudaError_t e;
+    if (lat->f64())
+        e = lbps::launch_sync<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(lat->cur), lat->st);
+    else
+        e = lbps::launch_sync<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(lat->cur), lat->st);
+    return cuda_ok(e);
+}
+
+int run_init_kernel(lbps_lattice* lat) {
+    cudaError_t e;
+    if (lat->f64())
+        e = lbps::launch_init<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(lat->cur), nullptr, nullptr,
+                                      nullptr, nullptr, lat->st);
+    else
+        e = lbps::launch_init<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(lat->cur), nullptr, nullptr,
+                                     nullptr, nullptr, lat->st);
+    return cuda_ok(e);
+}
+
+// Copy four [ny][nx] arrays (v may be null) into the pitched u planes of the
+// current copy, then run the initialisation kernel.
+int init_from(lbps_lattice* lat, const double* ux0, const double* uy0, const double* vx0, const double* vy0,
+              cudaMemcpyKind kind) {
+    const Geo& g = lat->L.g;
+    double* u = lat->view<float>(lat->cur).u;  // u planes sit at the same place for both storages
+    if (lat->f64()) u = lat->view<double>(lat->cur).u;
+    size_t dp = (size_t)g.px * sizeof(double), sp = (size_t)g.nx * sizeof(double);
+    const double* src[4] = {ux0, uy0, vx0, vy0};
+    for (int q = 0; q < 4; ++q) {
+        double* dst = u + (size_t)q * g.plane;
+        cudaError_t e = src[q] ? cudaMemcpy2DAsync(dst, dp, src[q], sp, sp, g.ny, kind, lat->st)
+                               : cudaMemset2DAsync(dst, dp, 0, sp, g.ny, lat->st);
+        if (e != cudaSuccess) return LBPS_ERR_CUDA;
+    }
+    if (cudaMemsetAsync(lat->flag(), 0, sizeof(unsigned), lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
+    int rc = run_init_kernel(lat);
+    if (rc != LBPS_OK) return rc;
+    lat->steps = 0;
+    lat->initialised = true;
+    return LBPS_OK;
+}
+
+size_t field_count(const lbps_lattice* lat, int32_t field) {
+    size_t n = (size_t)lat->p.nx * (size_t)lat->p.ny;
+    return (field == LBPS_F_PHI || field == LBPS_F_PSI) ? 5 * n : n;
+}
+
+bool valid_field(int32_t f) { return f >= LBPS_UX && f <= LBPS_CONSISTENCY; }
+
+int extract_rows(lbps_lattice* lat, int32_t field, int j0, int rows, double* dst) {
+    cudaError_t e;
+    if (lat->f64())
+        e = lbps::launch_extract_rows<double>(lat->L.g, lat->c, lat->view<double>(lat->cur), field, j0, rows, dst,
+                                              lat->st);
+    else
+        e = lbps::launch_extract_rows<float>(lat->L.g, lat->c, lat->view<float>(lat->cur), field, j0, rows, dst,
+                                             lat->st);
+    return cuda_ok(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbps_strerror(int code) {
+    switch (code) {
+    case LBPS_OK: return "ok";
+    case LBPS_ERR_INVALID: return "invalid argument";
+    case LBPS_ERR_OOM: return "out of device memory";
+    case LBPS_ERR_CUDA: return "CUDA error";
+    case LBPS_ERR_NONFINITE: return "state became non-finite";
+    case LBPS_ERR_TIMEOUT: return "device wait timed out";
+    case LBPS_ERR_STATE: return "call out of order";
+    default: return "unknown error";
+    }
+}
+
+int lbps_rect_bc(int32_t nx, int32_t ny, int32_t periodic_x, int32_t periodic_y, double dh,
+                 const int32_t edge_type[4], const double edge_value[8], uint8_t* node_type, double* bc_value) {
+    if (nx < 3 || ny < 3 || !finite_positive(dh) || !edge_type || !edge_value || !node_type || !bc_value)
+        return LBPS_ERR_INVALID;
+    // edges: 0 bottom (j = 0), 1 right (i = nx-1), 2 top (j = ny-1), 3 left (i = 0)
+    for (int e = 0; e < 4; ++e) {
+        bool active = (e == 0 || e == 2) ? !periodic_y : !periodic_x;
+        if (active && edge_type[e] != LBPS_NEUMANN && edge_type[e] != LBPS_DIRICHLET) return LBPS_ERR_INVALID;
+        if (active && (!std::isfinite(edge_value[2 * e]) || !std::isfinite(edge_value[2 * e + 1])))
+            return LBPS_ERR_INVALID;
+    }
+    for (int32_t j = 0; j < ny; ++j) {
+        for (int32_t i = 0; i < nx; ++i) {
+            size_t k = (size_t)j * nx + i;
+            bool on[4] = {!periodic_y && j == 0, !periodic_x && i == nx - 1, !periodic_y && j == ny - 1,
+                          !periodic_x && i == 0};
+            int n_on = 0, n_dir = 0;
+            for (int e = 0; e < 4; ++e) {
+                n_on += on[e];
+                n_dir += on[e] && edge_type[e] == LBPS_DIRICHLET;
+            }
+            double vx = 0.0, vy = 0.0;
+            uint8_t t = LBPS_INTERIOR;
+            if (n_dir > 0) {
+                // Dirichlet dominates; mean u* where two Dirichlet edges meet.
+                t = LBPS_DIRICHLET;
+                for (int e = 0; e < 4; ++e)
+                    if (on[e] && edge_type[e] == LBPS_DIRICHLET) {
+                        vx += edge_value[2 * e] / n_dir;
+                        vy += edge_value[2 * e + 1] / n_dir;
+                    }
+            } else if (n_on > 0) {
+                // Integrated traction over the external faces of the cell.
+                t = LBPS_NEUMANN;
+                double len = n_on == 1 ? dh : 0.5 * dh;
+                for (int e = 0; e < 4; ++e)
+                    if (on[e]) {
+                        vx += edge_value[2 * e] * len;
+                        vy += edge_value[2 * e + 1] * len;
+                    }
+            }
+            node_type[k] = t;
+            bc_value[2 * k] = vx;
+            bc_value[2 * k + 1] = vy;
+        }
+    }
+    return LBPS_OK;
+}
+
+int lbps_state_bytes(const lbps_params* params, size_t* bytes) {
+    int rc = validate_params(params);
+    if (rc != LBPS_OK) return rc;
+    if (!bytes) return LBPS_ERR_INVALID;
+    *bytes = make_layout(params).total;
+    return LBPS_OK;
+}
+
+int lbps_create(const lbps_params* params, const uint8_t* node_type, const double* bc_value, void* device_mem,
+                size_t device_bytes, lbps_lattice** out) {
+    if (!out) return LBPS_ERR_INVALID;
+    *out = nullptr;
+    int rc = validate_params(params);
+    if (rc != LBPS_OK) return rc;
+    Layout L = make_layout(params);
+    const Geo& g = L.g;
+    // Boundary list in perimeter order, checked against the mask.
+    std::vector<BNode> bn((size_t)L.nb);
+    std::vector<char> seen((size_t)L.nb, 0);
+    for (int j = 0; j < g.ny; ++j) {
+        for (int i = 0; i < g.nx; ++i) {
+            size_t k = (size_t)j * g.nx + i;
+            int t = node_type ? node_type[k] : LBPS_INTERIOR;
+            bool bnd = lbps::is_boundary(i, j, g);
+            if (!bnd) {
+                if (t != LBPS_INTERIOR) return LBPS_ERR_INVALID;
+                continue;
+            }
+            if (t != LBPS_NEUMANN && t != LBPS_DIRICHLET) return LBPS_ERR_INVALID;
+            double bx = bc_value ? bc_value[2 * k] : 0.0, by = bc_value ? bc_value[2 * k + 1] : 0.0;
+            if (!std::isfinite(bx) || !std::isfinite(by)) return LBPS_ERR_INVALID;
+            int q = lbps::perim_index(i, j, g);
+            if (q < 0 || q >= L.nb || seen[q]) return LBPS_ERR_INVALID;
+            seen[q] = 1;
+            bn[q] = BNode{i, j, t, 0, bx, by};
+        }
+    }
+    lbps_lattice* lat = new (std::nothrow) lbps_lattice();
+    if (!lat) return LBPS_ERR_OOM;
+    lat->p = *params;
+    lat->L = L;
+    lat->st = reinterpret_cast<cudaStream_t>(params->cuda_stream);
+    if (device_mem) {
+        if (device_bytes < L.total || (reinterpret_cast<uintptr_t>(device_mem) % kAlign) != 0) {
+            delete lat;
+            return LBPS_ERR_OOM;
+        }
+        lat->mem = static_cast<char*>(device_mem);
+        lat->owns = false;
+    } else {
+        if (cudaMalloc(&lat->mem, L.total) != cudaSuccess) {
+            cudaGetLastError();
+            delete lat;
+            return LBPS_ERR_OOM;
+        }
+        lat->owns = true;
+    }
+    // Derived constants, Eq. feq_req and Eq. conditions-parameters.
+    double lam = params->lambda, mu = params->mu, rho = params->rho, dh = params->dh;
+    lat->cd = std::sqrt((lam + 2.0 * mu) / rho);
+    lat->cs = std::sqrt(mu / rho);
+    lat->a_phi = (1.0 - params->a0_phi) / 4.0;
+    lat->a_psi = (lat->cs * lat->cs) / (lat->cd * lat->cd) * lat->a_phi;
+    lat->a0_psi = 1.0 - 4.0 * lat->a_psi;
+    double dt = dh / lat->cd * std::sqrt(2.0 * lat->a_phi);
+    Consts& c = lat->c;
+    c.dt = dt;
+    c.half_dt2 = 0.5 * dt * dt;
+    c.lam = lam;
+    c.mu = mu;
+    c.rho = rho;
+    c.dh = dh;
+    c.inv2h = 0.5 / dh;
+    c.cd2 = lat->cd * lat->cd;
+    c.cs2 = lat->cs * lat->cs;
+    c.a[0] = lat->a_phi;
+    c.a[1] = lat->a_psi;
+    c.a0[0] = params->a0_phi;
+    c.a0[1] = lat->a0_psi;
+    c.bc_feq_mode = params->bc_feq_mode;
+    lat->kf = make_kc<float>(lat->a_phi, lat->a_psi, c.cd2, c.cs2, dh);
+    lat->kd = make_kc<double>(lat->a_phi, lat->a_psi, c.cd2, c.cs2, dh);
+    lat->cur = 0;
+    lat->steps = 0;
+    lat->initialised = false;
+    cudaError_t e = cudaMemsetAsync(lat->mem, 0, L.total, lat->st);
+    if (e == cudaSuccess && L.nb > 0)
+        e = cudaMemcpyAsync(lat->mem + L.off_bn, bn.data(), bn.size() * sizeof(BNode), cudaMemcpyHostToDevice,
+                            lat->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+    if (e != cudaSuccess) {
+        lbps_destroy(lat);
+        return LBPS_ERR_CUDA;
+    }
+    *out = lat;
+    return LBPS_OK;
+}
+
+int lbps_init(lbps_lattice* lat, const double* ux0, const double* uy0, const double* vx0, const double* vy0) {
+    if (!lat || !ux0 || !uy0 || (!vx0) != (!vy0)) return LBPS_ERR_INVALID;
+    size_t n = (size_t)lat->p.nx * (size_t)lat->p.ny;
+    for (size_t k = 0; k < n; ++k) {
+        if (!std::isfinite(ux0[k]) || !std::isfinite(uy0[k])) return LBPS_ERR_INVALID;
+        if (vx0 && (!std::isfinite(vx0[k]) || !std::isfinite(vy0[k]))) return LBPS_ERR_INVALID;
+    }
+    int rc = init_from(lat, ux0, uy0, vx0, vy0, cudaMemcpyHostToDevice);
+    if (rc != LBPS_OK) return rc;
+    return cuda_ok(cudaStreamSynchronize(lat->st));
+}
+
+int lbps_init_device(lbps_lattice* lat, const double* d_ux0, const double* d_uy0, const double* d_vx0,
+                     const double* d_vy0) {
+    if (!lat || !d_ux0 || !d_uy0 || (!d_vx0) != (!d_vy0)) return LBPS_ERR_INVALID;
+    return init_from(lat, d_ux0, d_uy0, d_vx0, d_vy0, cudaMemcpyDeviceToDevice);
+}
+
+int lbps_step_async(lbps_lattice* lat, int64_t n) {
+    if (!lat || n < 0) return LBPS_ERR_INVALID;
+    if (!lat->initialised) return LBPS_ERR_STATE;
+    for (int64_t s = 0; s < n; ++s) {
+        int rc = run_step(lat);
+        if (rc != LBPS_OK) return rc;
+        if (lat->p.sync_every > 0 && lat->steps % lat->p.sync_every == 0) {
+            rc = run_sync(lat);
+            if (rc != LBPS_OK) return rc;
+        }
+    }
+    return LBPS_OK;
+}
+
+int lbps_check(lbps_lattice* lat) {
+    if (!lat) return LBPS_ERR_INVALID;
+    unsigned flag = 0;
+    cudaError_t e = cudaMemcpyAsync(&flag, lat->flag(), sizeof(unsigned), cudaMemcpyDeviceToHost, lat->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+    if (e != cudaSuccess) return LBPS_ERR_CUDA;
+    return flag ? LBPS_ERR_NONFINITE : LBPS_OK;
+}
+
+int lbps_step(lbps_lattice* lat, int64_t n) {
+    int rc = lbps_step_async(lat, n);
+    if (rc != LBPS_OK) return rc;
+    return lbps_check(lat);
+}
+
+int lbps_sync(lbps_lattice* lat) {
+    if (!lat) return LBPS_ERR_INVALID;
+    if (!lat->initialised) return LBPS_ERR_STATE;
+    return run_sync(lat);
+}
+
+int lbps_read_device(lbps_lattice* lat, int32_t field, double* d_dst, size_t count) {
+    if (!lat || !d_dst || !valid_field(field)) return LBPS_ERR_INVALID;
+    if (!lat->initialised) return LBPS_ERR_STATE;
+    if (count < field_count(lat, field)) return LBPS_ERR_INVALID;
+    return extract_rows(lat, field, 0, lat->p.ny, d_dst);
+}
+
+int lbps_read(lbps_lattice* lat, int32_t field, double* dst, size_t count) {
+    if (!lat || !dst || !valid_field(field)) return LBPS_ERR_INVALID;
+    if (!lat->initialised) return LBPS_ERR_STATE;
+    if (count < field_count(lat, field)) return LBPS_ERR_INVALID;
+    const Geo& g = lat->L.g;
+    size_t nx = (size_t)g.nx, n = nx * (size_t)g.ny;
+    int planes = (field == LBPS_F_PHI || field == LBPS_F_PSI) ? 5 : 1;
+    size_t row_bytes = (size_t)planes * nx * sizeof(double);
+    int chunk = (int)(lat->L.staging_bytes / row_bytes);
+    if (chunk < 1) return LBPS_ERR_INVALID;
+    double* stg = lat->staging();
+    for (int j0 = 0; j0 < g.ny; j0 += chunk) {
+        int rows = g.ny - j0 < chunk ? g.ny - j0 : chunk;
+        int rc = extract_rows(lat, field, j0, rows, stg);
+        if (rc != LBPS_OK) return rc;
+        for (int q = 0; q < planes; ++q) {
+            cudaError_t e = cudaMemcpyAsync(dst + (size_t)q * n + (size_t)j0 * nx, stg + (size_t)q * rows * nx,
+                                            (size_t)rows * nx * sizeof(double), cudaMemcpyDeviceToHost, lat->st);
+            if (e != cudaSuccess) return LBPS_ERR_CUDA;
+        }
+        if (cudaStreamSynchronize(lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
+    }
+    return LBPS_OK;
+}
+
+int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out[4]) {
+    if (!lat || !out) return LBPS_ERR_INVALID;
+    if (!(field >= LBPS_UX && field <= LBPS_PSI) && field != LBPS_CONSISTENCY) return LBPS_ERR_INVALID;
+    if (!lat->initialised) return LBPS_ERR_STATE;
+    cudaError_t e;
+    if (lat->f64())
+        e = lbps::launch_norms<double>(lat->L.g, lat->c, lat->view<double>(lat->cur), field, d_ref, lat->partials(),
+                                       lat->out4(), lat->st);
+    else
+        e = lbps::launch_norms<float>(lat->L.g, lat->c, lat->view<float>(lat->cur), field, d_ref, lat->partials(),
+                                      lat->out4(), lat->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, lat->out4(), 4 * sizeof(double), cudaMemcpyDeviceToHost, lat->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+    return cuda_ok(e);
+}
+
+int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done) {
+    if (!lat) return LBPS_ERR_INVALID;
+    if (out) {
+        out[0] = lat->cd;
+        out[1] = lat->cs;
+        out[2] = lat->a_phi;
+        out[3] = lat->a_psi;
+        out[4] = lat->a0_psi;
+        out[5] = lat->c.dt;
+    }
+    if (steps_done) *steps_done = lat->steps;
+    return LBPS_OK;
+}
+
+int lbps_profile(lbps_lattice* lat, int32_t enable) {
+    if (!lat) return LBPS_ERR_INVALID;
+    lat->prof = enable != 0;
+    return LBPS_OK;
+}
+
+int lbps_profile_read(lbps_lattice* lat, double out[4]) {
+    if (!lat || !out) return LBPS_ERR_INVALID;
+    if (cudaStreamSynchronize(lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
+    for (int q = 0; q < 4; ++q) out[q] = 0.0;
+    for (size_t r = 0; r < lat->ev_kind.size(); ++r) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, lat->ev_pool[2 * r], lat->ev_pool[2 * r + 1]) != cudaSuccess)
+            return LBPS_ERR_CUDA;
+        int k = lat->ev_kind[r];
+        out[2 * k] += ms;
+        out[2 * k + 1] += 1.0;
+    }
+    lat->ev_kind.clear();
+    lat->ev_used = 0;
+    return LBPS_OK;
+}
+
+int lbps_set_stream(lbps_lattice* lat, void* cuda_stream) {
+    if (!lat) return LBPS_ERR_INVALID;
+    lat->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    lat->p.cuda_stream = cuda_stream;
+    return LBPS_OK;
+}
+
+void lbps_destroy(lbps_lattice* lat) {
+    if (!lat) return;
+    if (lat->owns && lat->mem) {
+        cudaStreamSynchronize(lat->st);
+        cudaFree(lat->mem);
+    }
+    for (cudaEvent_t e : lat->ev_pool) cudaEventDestroy(e);
+    delete lat;
+}
+
+}  // extern "C"

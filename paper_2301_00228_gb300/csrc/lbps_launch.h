@@ -1,0 +1,40 @@
+// Host-side launchers of the LBM kernels (defined in lbps_kernels.cu).
+#pragma once
+
+#include "lbps_device.cuh"
+
+namespace lbps {
+
+template <typename T>
+cudaError_t launch_init(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, const double* ux0,
+                        const double* uy0, const double* vx0, const double* vy0, cudaStream_t st);
+
+// One time step A (time t) -> B (time t + dt) is launch_boundary followed by
+// launch_bulk on the same stream.
+template <typename T>
+cudaError_t launch_boundary(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B,
+                            const BNode* bn, int nb, unsigned* flag, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, unsigned* flag,
+                        cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_sync(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, cudaStream_t st);
+
+// Dense FP64 copy of one field (ids of lbps.h).
+template <typename T>
+cudaError_t launch_extract(const Geo& g, const Consts& c, View<T> A, int field, double* dst, cudaStream_t st);
+
+// Rows [j0, j0 + rows) only, into a dense [rows][nx] (x5 for populations) buffer.
+template <typename T>
+cudaError_t launch_extract_rows(const Geo& g, const Consts& c, View<T> A, int field, int j0, int rows,
+                                double* dst, cudaStream_t st);
+
+// FP64 reductions of one scalar field against an optional reference;
+// partials: scratch of at least kNormBlocks * 4 doubles.
+constexpr int kNormBlocks = 1024;
+template <typename T>
+cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, const double* ref,
+                         double* partials, double* out4, cudaStream_t st);
+
+}  // namespace lbps

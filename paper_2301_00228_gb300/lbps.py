@@ -1,0 +1,294 @@
+"""Thin ctypes binding of the C ABI in include/lbps.h.
+
+The functions ``lbps_*`` here have the names and arguments of the C entry
+points and only marshal arguments; every step of the time loop runs in the
+CUDA kernels of liblbps.so.  There is no host fallback: if the library is
+missing, importing this module raises.  PyTorch supplies device memory (the
+lattice state lives in a torch uint8 tensor) and the CUDA stream.
+
+``Lattice`` is the convenience wrapper used by the tests and the benchmark.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "liblbps.so"
+
+LBPS_OK = 0
+LBPS_ERR_INVALID = -1
+LBPS_ERR_OOM = -2
+LBPS_ERR_CUDA = -3
+LBPS_ERR_NONFINITE = -4
+LBPS_ERR_TIMEOUT = -5
+LBPS_ERR_STATE = -6
+
+LBPS_INTERIOR, LBPS_NEUMANN, LBPS_DIRICHLET = 0, 1, 2
+LBPS_STORAGE_F32, LBPS_STORAGE_F64 = 0, 1
+LBPS_UX, LBPS_UY, LBPS_VX, LBPS_VY, LBPS_PHI, LBPS_PSI, LBPS_F_PHI, LBPS_F_PSI, LBPS_CONSISTENCY = range(9)
+FIELDS = {"ux": LBPS_UX, "uy": LBPS_UY, "vx": LBPS_VX, "vy": LBPS_VY, "phi": LBPS_PHI, "psi": LBPS_PSI,
+          "f_phi": LBPS_F_PHI, "f_psi": LBPS_F_PSI, "consistency": LBPS_CONSISTENCY}
+STORAGES = {"f32": LBPS_STORAGE_F32, "f64": LBPS_STORAGE_F64}
+
+
+class lbps_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("lambda_", ctypes.c_double), ("mu", ctypes.c_double), ("rho", ctypes.c_double),
+                ("dh", ctypes.c_double), ("a0_phi", ctypes.c_double),
+                ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("bc_feq_mode", ctypes.c_int32), ("sync_every", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+
+
+class LbpsError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {lbps_strerror(code)} ({code})" if what else lbps_strerror(code))
+
+
+def _load():
+    if not _LIB_PATH.exists():
+        raise ImportError(f"CUDA library {_LIB_PATH.name} is not built; run __graft_entry__.build()")
+    L = ctypes.CDLL(str(_LIB_PATH))
+    vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "lbps_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "lbps_rect_bc": (ctypes.c_int, [i32, i32, i32, i32, ctypes.c_double, vp, vp, vp, vp]),
+        "lbps_state_bytes": (ctypes.c_int, [P(lbps_params), P(sz)]),
+        "lbps_create": (ctypes.c_int, [P(lbps_params), vp, vp, vp, sz, P(vp)]),
+        "lbps_init": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "lbps_init_device": (ctypes.c_int, [vp, vp, vp, vp, vp]),
+        "lbps_step": (ctypes.c_int, [vp, i64]),
+        "lbps_step_async": (ctypes.c_int, [vp, i64]),
+        "lbps_check": (ctypes.c_int, [vp]),
+        "lbps_sync": (ctypes.c_int, [vp]),
+        "lbps_read": (ctypes.c_int, [vp, i32, vp, sz]),
+        "lbps_read_device": (ctypes.c_int, [vp, i32, vp, sz]),
+        "lbps_norms": (ctypes.c_int, [vp, i32, vp, vp]),
+        "lbps_info": (ctypes.c_int, [vp, vp, P(i64)]),
+        "lbps_profile": (ctypes.c_int, [vp, i32]),
+        "lbps_profile_read": (ctypes.c_int, [vp, vp]),
+        "lbps_set_stream": (ctypes.c_int, [vp, vp]),
+        "lbps_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+_lib = _load()
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _check(rc, what):
+    if rc != LBPS_OK:
+        raise LbpsError(rc, what)
+
+
+# ---- C entry points under their own names ---------------------------------
+
+def lbps_strerror(code):
+    return _lib.lbps_strerror(int(code)).decode()
+
+
+def lbps_rect_bc(nx, ny, periodic_x, periodic_y, dh, edge_type, edge_value):
+    et = np.ascontiguousarray(edge_type, np.int32).reshape(4)
+    ev = np.ascontiguousarray(edge_value, np.float64).reshape(8)
+    nt = np.zeros((ny, nx), np.uint8)
+    bv = np.zeros((ny, nx, 2), np.float64)
+    _check(_lib.lbps_rect_bc(nx, ny, int(periodic_x), int(periodic_y), float(dh), _p(et), _p(ev), _p(nt), _p(bv)),
+           "lbps_rect_bc")
+    return nt, bv
+
+
+def lbps_state_bytes(params):
+    n = ctypes.c_size_t(0)
+    _check(_lib.lbps_state_bytes(ctypes.byref(params), ctypes.byref(n)), "lbps_state_bytes")
+    return int(n.value)
+
+
+def lbps_create(params, node_type, bc_value, device_ptr, device_bytes):
+    h = ctypes.c_void_p()
+    _check(_lib.lbps_create(ctypes.byref(params), _p(node_type), _p(bc_value),
+                            ctypes.c_void_p(device_ptr) if device_ptr else None, device_bytes, ctypes.byref(h)),
+           "lbps_create")
+    return h
+
+
+def lbps_init(h, ux0, uy0, vx0=None, vy0=None):
+    _check(_lib.lbps_init(h, _p(ux0), _p(uy0), _p(vx0), _p(vy0)), "lbps_init")
+
+
+def lbps_init_device(h, d_ux0, d_uy0, d_vx0=0, d_vy0=0):
+    _check(_lib.lbps_init_device(h, ctypes.c_void_p(d_ux0), ctypes.c_void_p(d_uy0),
+                                 ctypes.c_void_p(d_vx0) if d_vx0 else None,
+                                 ctypes.c_void_p(d_vy0) if d_vy0 else None), "lbps_init_device")
+
+
+def lbps_step(h, n):
+    return _lib.lbps_step(h, int(n))
+
+
+def lbps_step_async(h, n):
+    return _lib.lbps_step_async(h, int(n))
+
+
+def lbps_check(h):
+    return _lib.lbps_check(h)
+
+
+def lbps_sync(h):
+    _check(_lib.lbps_sync(h), "lbps_sync")
+
+
+def lbps_read(h, field, dst):
+    _check(_lib.lbps_read(h, int(field), _p(dst), dst.size), "lbps_read")
+    return dst
+
+
+def lbps_read_device(h, field, d_dst, count):
+    _check(_lib.lbps_read_device(h, int(field), ctypes.c_void_p(d_dst), int(count)), "lbps_read_device")
+
+
+def lbps_norms(h, field, d_ref=0):
+    out = np.zeros(4, np.float64)
+    _check(_lib.lbps_norms(h, int(field), ctypes.c_void_p(d_ref) if d_ref else None, _p(out)), "lbps_norms")
+    return out
+
+
+def lbps_info(h):
+    out = np.zeros(6, np.float64)
+    steps = ctypes.c_int64(0)
+    _check(_lib.lbps_info(h, _p(out), ctypes.byref(steps)), "lbps_info")
+    return out, int(steps.value)
+
+
+def lbps_profile(h, enable):
+    _check(_lib.lbps_profile(h, int(bool(enable))), "lbps_profile")
+
+
+def lbps_profile_read(h):
+    out = np.zeros(4, np.float64)
+    _check(_lib.lbps_profile_read(h, _p(out)), "lbps_profile_read")
+    return out
+
+
+def lbps_set_stream(h, stream_ptr):
+    _check(_lib.lbps_set_stream(h, ctypes.c_void_p(stream_ptr) if stream_ptr else None), "lbps_set_stream")
+
+
+def lbps_destroy(h):
+    _lib.lbps_destroy(h)
+
+
+# ---- convenience wrapper --------------------------------------------------
+
+class Lattice:
+    """One lattice on the current CUDA device, its state in a torch tensor."""
+
+    def __init__(self, nx, ny, lam, mu, rho=1.0, dh=1.0, a0_phi=0.9999, periodic_x=False, periodic_y=False,
+                 node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0, storage="f32", stream=None):
+        import torch
+
+        self.nx, self.ny = int(nx), int(ny)
+        self._torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.params = lbps_params(self.nx, self.ny, lam, mu, rho, dh, a0_phi, int(periodic_x), int(periodic_y),
+                                  int(bc_feq_mode), int(sync_every), STORAGES[storage],
+                                  ctypes.c_void_p(self.stream.cuda_stream))
+        self.nbytes = lbps_state_bytes(self.params)
+        with torch.cuda.stream(self.stream):
+            self._mem = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        nt = None if node_type is None else np.ascontiguousarray(node_type, np.uint8)
+        bv = None if bc_value is None else np.ascontiguousarray(bc_value, np.float64)
+        self._h = lbps_create(self.params, nt, bv, self._mem.data_ptr(), self.nbytes)
+        c, _ = lbps_info(self._h)
+        self.cd, self.cs, self.a_phi, self.a_psi, self.a0_psi, self.dt = (float(x) for x in c)
+
+    @classmethod
+    def rectangle(cls, nx, ny, lam, mu, edge_type, edge_value, periodic_x=False, periodic_y=False, dh=1.0, **kw):
+        nt, bv = lbps_rect_bc(nx, ny, periodic_x, periodic_y, dh, edge_type, edge_value)
+        return cls(nx, ny, lam, mu, dh=dh, periodic_x=periodic_x, periodic_y=periodic_y, node_type=nt,
+                   bc_value=bv, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            lbps_destroy(self._h)
+            self._h = None
+            self._mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, ux0, uy0, vx0=None, vy0=None):
+        torch = self._torch
+        if isinstance(ux0, torch.Tensor):
+            t = [None if x is None else x.contiguous().to(torch.float64) for x in (ux0, uy0, vx0, vy0)]
+            self._init_keep = t
+            lbps_init_device(self._h, t[0].data_ptr(), t[1].data_ptr(), t[2].data_ptr() if t[2] is not None else 0,
+                             t[3].data_ptr() if t[3] is not None else 0)
+        else:
+            a = [None if x is None else np.ascontiguousarray(x, np.float64) for x in (ux0, uy0, vx0, vy0)]
+            lbps_init(self._h, *a)
+        return self
+
+    def step(self, n=1):
+        rc = lbps_step(self._h, n)
+        if rc != LBPS_OK:
+            raise LbpsError(rc, "lbps_step")
+        return self
+
+    def step_async(self, n=1):
+        rc = lbps_step_async(self._h, n)
+        if rc != LBPS_OK:
+            raise LbpsError(rc, "lbps_step_async")
+        return self
+
+    def check(self):
+        return lbps_check(self._h)
+
+    def sync(self):
+        lbps_sync(self._h)
+        return self
+
+    @property
+    def steps(self):
+        return lbps_info(self._h)[1]
+
+    def read(self, field):
+        fid = FIELDS[field] if isinstance(field, str) else int(field)
+        planes = 5 if fid in (LBPS_F_PHI, LBPS_F_PSI) else 1
+        out = np.zeros((planes, self.ny, self.nx), np.float64)
+        lbps_read(self._h, fid, out)
+        return out if planes == 5 else out[0]
+
+    def read_device(self, field, out=None):
+        torch = self._torch
+        fid = FIELDS[field] if isinstance(field, str) else int(field)
+        planes = 5 if fid in (LBPS_F_PHI, LBPS_F_PSI) else 1
+        if out is None:
+            out = torch.empty((planes, self.ny, self.nx), dtype=torch.float64, device="cuda")
+        lbps_read_device(self._h, fid, out.data_ptr(), out.numel())
+        return out if planes == 5 else out[0]
+
+    def norms(self, field, ref=None):
+        fid = FIELDS[field] if isinstance(field, str) else int(field)
+        if ref is not None:
+            ref = ref.contiguous()
+            return lbps_norms(self._h, fid, ref.data_ptr())
+        return lbps_norms(self._h, fid)
+
+    def fields(self):
+        return {k: self.read(k) for k in ("ux", "uy", "vx", "vy", "phi", "psi")}

@@ -28,10 +28,11 @@ NEUMANN, DIRICHLET = 1, 2
 EDGES = ("bottom", "right", "top", "left")
 
 
-def pulse_displacement(nx, ny, cx, cy, sigma, amp, kind="dilatation", dh=1.0):
-    """Displacement of one Gaussian pulse centred at (cx, cy) (lattice coordinates)."""
-    x = (np.arange(nx, dtype=np.float64) - cx) * dh
-    y = (np.arange(ny, dtype=np.float64) - cy) * dh
+def pulse_displacement(nx, ny, cx, cy, sigma, amp, kind="dilatation", dh=1.0, x0=0, y0=0):
+    """Displacement of one Gaussian pulse centred at (cx, cy) (lattice coordinates),
+    sampled on the nx x ny window whose first point is (x0, y0)."""
+    x = (np.arange(x0, x0 + nx, dtype=np.float64) - cx) * dh
+    y = (np.arange(y0, y0 + ny, dtype=np.float64) - cy) * dh
     X, Y = np.meshgrid(x, y)
     r = np.hypot(X, Y)
     s = sigma * dh
@@ -94,17 +95,47 @@ class Domain:
     wave: tuple | None = None                      # (m, n, amp_d, amp_s)
     steps: int = 0
 
-    def displacement(self):
-        ux = np.zeros((self.ny, self.nx))
-        uy = np.zeros((self.ny, self.nx))
+    def displacement(self, window=None):
+        """u(x, 0) on the whole lattice, or on window = (x0, y0, w, h)."""
+        x0, y0, w, h = window if window is not None else (0, 0, self.nx, self.ny)
+        ux = np.zeros((h, w))
+        uy = np.zeros((h, w))
         for (cx, cy, sg, amp, kind) in self.pulses:
-            dx, dy = pulse_displacement(self.nx, self.ny, cx, cy, sg, amp, kind)
+            dx, dy = pulse_displacement(w, h, cx, cy, sg, amp, kind, x0=x0, y0=y0)
             ux += dx
             uy += dy
         if self.wave is not None:
+            if window is not None:
+                raise ValueError("plane waves are sampled on the whole lattice")
             dx, dy = plane_wave_displacement(self.nx, self.ny, *self.wave)
             ux += dx
             uy += dy
+        return ux, uy
+
+    def displacement_torch(self, device="cuda"):
+        """u(x, 0) as FP64 torch tensors on ``device`` (same recipe as displacement())."""
+        import torch
+
+        x = torch.arange(self.nx, dtype=torch.float64, device=device)
+        y = torch.arange(self.ny, dtype=torch.float64, device=device)
+        ux = torch.zeros((self.ny, self.nx), dtype=torch.float64, device=device)
+        uy = torch.zeros_like(ux)
+        for (cx, cy, sg, amp, kind) in self.pulses:
+            X = (x - cx)[None, :]
+            Y = (y - cy)[:, None]
+            r = torch.hypot(X, Y)
+            g = amp * sg * sg * (-torch.expm1(-r * r / (2.0 * sg * sg)))
+            g = torch.where(r > 0, g / torch.where(r > 0, r * r, torch.ones_like(r)), torch.zeros_like(r))
+            if kind == "dilatation":
+                ux += g * X
+                uy += g * Y
+            else:
+                ux -= g * Y
+                uy += g * X
+        if self.wave is not None:
+            dx, dy = plane_wave_displacement(self.nx, self.ny, *self.wave)
+            ux += torch.from_numpy(dx).to(device)
+            uy += torch.from_numpy(dy).to(device)
         return ux, uy
 
     def edge_arrays(self):

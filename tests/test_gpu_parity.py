@@ -1,0 +1,378 @@
+"""Parity of the CUDA time loop with the FP64 oracle, through the C ABI.
+
+Tolerances: FP64 population storage must match the oracle to round-off
+(relative L2 <= 1e-10 per field); FP32 storage within relative L2 <= 1e-5 per
+field.  Relative L2 is taken per field against max(||ref||, 1e-2 ||ref group||)
+where the groups are (ux, uy), (vx, vy), (phi, psi), so a field that is zero
+by symmetry is compared on the scale of its partner.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import hand_cases as H
+from paper_2301_00228_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GROUPS = (("ux", "uy"), ("vx", "vy"), ("phi", "psi"))
+TOL = {"f64": 1e-10, "f32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def L():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2301_00228_gb300 import lbps
+    return lbps
+
+
+def rel_errors(got, ref):
+    out = {}
+    for g in GROUPS:
+        gn = np.sqrt(sum(np.linalg.norm(ref[k]) ** 2 for k in g))
+        for k in g:
+            den = max(np.linalg.norm(ref[k]), 1e-2 * gn, 1e-300)
+            out[k] = float(np.linalg.norm(got[k] - ref[k]) / den)
+    return out
+
+
+def assert_parity(got, ref, tol, what=""):
+    errs = rel_errors(got, ref)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, (what, bad, errs)
+    return errs
+
+
+# ------------------------------------------------------------ hand cases
+
+def _gpu_factory(L, storage):
+    def make(case, mode):
+        c = H.load()["common"]
+        return L.Lattice.rectangle(c["nx"], c["ny"], c["lambda"], c["mu"], case["edges"]["type"],
+                                   H.edge_values(case), rho=c["rho"], a0_phi=c["a0_phi"], bc_feq_mode=mode,
+                                   storage=storage)
+    return make
+
+
+def _gpu_read(lat, field, alpha):
+    if field in ("f_phi", "f_psi"):
+        return lat.read(field)[alpha]
+    return lat.read(field)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-6)])
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name", [c["name"] for c in H.load()["cases"]])
+def test_hand_cases(L, name, mode, storage, tol):
+    g = H.load()
+    case = next(c for c in g["cases"] if c["name"] == name)
+    make = _gpu_factory(L, storage)
+    dt = make(case, mode).dt
+    fails = H.run_case(case, g["common"], mode, make, _gpu_read, dt, tol)
+    assert not fails, fails
+
+
+# ------------------------------------------------------- mixed rectangles
+
+def mixed_case(seed, nx, ny, periodic=(0, 0), a0=0.99, mode=0, sync=0, steps=200):
+    rng = np.random.default_rng(seed)
+    et = tuple(int(x) for x in rng.choice([1, 2], 4))
+    ev = rng.uniform(-2e-4, 2e-4, 8)
+    lam = float(rng.uniform(0.5, 4.0))
+    cx, cy = float(rng.uniform(0, nx - 1)), float(rng.uniform(0, ny - 1))
+    kind = "dilatation" if seed % 2 else "rotation"
+    ux, uy = W.pulse_displacement(nx, ny, cx, cy, max(1.5, min(nx, ny) / 8), 1e-3, kind)
+    return dict(nx=nx, ny=ny, et=et, ev=ev, lam=lam, px=periodic[0], py=periodic[1], a0=a0, mode=mode,
+                sync=sync, steps=steps, ux=ux, uy=uy)
+
+
+MIXED = [
+    mixed_case(1, 67, 45),
+    mixed_case(2, 130, 97, a0=0.9999, steps=300),
+    mixed_case(3, 67, 45, mode=1),
+    mixed_case(4, 96, 64, sync=7),
+    mixed_case(5, 70, 41, periodic=(1, 0)),
+    mixed_case(6, 41, 70, periodic=(0, 1), mode=1),
+    mixed_case(7, 64, 48, periodic=(1, 1), a0=0.9),
+    mixed_case(8, 3, 3, steps=50),
+    mixed_case(9, 3, 11, steps=80),
+    mixed_case(10, 13, 3, steps=80, mode=1),
+    mixed_case(11, 33, 17, a0=0.5, steps=20),
+]
+
+
+def run_oracle(cs):
+    nt, bv = O.rect_bc(cs["nx"], cs["ny"], cs["et"], cs["ev"], periodic_x=cs["px"], periodic_y=cs["py"])
+    lat = O.OracleLattice(cs["nx"], cs["ny"], cs["lam"], 1.0, a0_phi=cs["a0"], periodic_x=cs["px"],
+                          periodic_y=cs["py"], node_type=nt, bc_value=bv, bc_feq_mode=cs["mode"],
+                          sync_every=cs["sync"])
+    return lat.init(cs["ux"], cs["uy"]).step(cs["steps"]).fields()
+
+
+def run_gpu(L, cs, storage):
+    lat = L.Lattice.rectangle(cs["nx"], cs["ny"], cs["lam"], 1.0, cs["et"], cs["ev"], periodic_x=cs["px"],
+                              periodic_y=cs["py"], a0_phi=cs["a0"], bc_feq_mode=cs["mode"], sync_every=cs["sync"],
+                              storage=storage)
+    f = lat.init(cs["ux"], cs["uy"]).step(cs["steps"]).fields()
+    lat.close()
+    return f
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("k", range(len(MIXED)))
+def test_mixed_rectangles(L, k, storage):
+    cs = MIXED[k]
+    assert_parity(run_gpu(L, cs, storage), run_oracle(cs), TOL[storage], (k, storage))
+
+
+# ------------------------------------------------- the 64 x 64 problem
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_square_64_1000_steps(L, storage):
+    """64 x 64, left edge clamped, others traction-free, centred dilatation pulse
+    sigma = 4, lambda = mu = rho = 1, a_{0,phi} = 0.9999, 1000 steps."""
+    d = W.square_64()
+    ev = np.asarray(d.edge_value, float).ravel()
+    ux, uy = d.displacement()
+    nt, bv = O.rect_bc(64, 64, d.edge_type, ev)
+    ref = O.OracleLattice(64, 64, 1.0, 1.0, node_type=nt, bc_value=bv).init(ux, uy).step(d.steps).fields()
+    lat = L.Lattice.rectangle(64, 64, 1.0, 1.0, d.edge_type, ev, storage=storage)
+    got = lat.init(ux, uy).step(d.steps).fields()
+    assert_parity(got, ref, TOL[storage])
+
+
+# ------------------------------------------- full size: periodic waves
+
+def test_periodic_waves_full_size(L):
+    """1024 x 1024 periodic, lambda/mu = 2, superposed dilatational and shear standing
+    waves (wavelength 64), 10^4 FP32 steps, against the closed form of the scheme."""
+    from test_oracle_pins import standing_wave_expected
+
+    d = W.periodic_waves()
+    m, n, amp_d, amp_s = d.wave
+    lat = L.Lattice(d.nx, d.ny, d.lam, d.mu, periodic_x=True, periodic_y=True, storage="f32")
+    ux, uy = d.displacement()
+    lat.init(ux, uy).step(d.steps)
+    ex = standing_wave_expected(d.nx, d.ny, m, n, amp_d, amp_s, d.lam, d.mu, d.rho, lat.a_phi, lat.a_psi, lat.dt,
+                                d.steps)
+    errs = assert_parity(lat.fields(), ex, TOL["f32"])
+    print("periodic 1024^2 x 1e4 steps rel-L2:", errs)
+
+
+# ---------------------------------------- full size: sampled windows
+
+def test_many_pulses_full_size_sampled(L):
+    """8192 x 8192, lambda/mu = 3, clamped bottom, 32 pulses (the largest single-GPU
+    lattice), in the benchmark's launch configuration.  One step widens the domain of
+    dependence by at most 5 points (a second-row point reads the reset state of its
+    boundary neighbour, whose differences of the new u reach 2 points and whose
+    boundary accelerations reach 2 more), so the oracle on a window of radius
+    5 S + 16 around a sample reproduces the 13 x 13 points around it."""
+    d = W.many_pulses(steps=24)
+    S = d.steps
+    R = 5 * S + 16
+    ev = np.asarray(d.edge_value, float).ravel()
+    lat = L.Lattice.rectangle(d.nx, d.ny, d.lam, d.mu, d.edge_type, ev, storage="f32")
+    ux_d, uy_d = d.displacement_torch("cuda")
+    lat.init(ux_d, uy_d).step(S)
+    del ux_d, uy_d
+    got = {k: lat.read_device(k) for k in ("ux", "uy", "phi", "psi")}
+    samples = [(0, 0), (d.nx - 1, 0), (4000, 0), (0, 5000), (d.nx - 1, 3000), (2000, d.ny - 1),
+               (d.nx - 1, d.ny - 1), (4100, 4100)]
+    rng = np.random.default_rng(44)
+    samples += [tuple(int(v) for v in rng.integers(0, d.nx, 2)) for _ in range(3)]
+    for (si, sj) in samples:
+        x0, x1 = max(0, si - R), min(d.nx, si + R + 1)
+        y0, y1 = max(0, sj - R), min(d.ny, sj + R + 1)
+        w, h = x1 - x0, y1 - y0
+        ux, uy = d.displacement(window=(x0, y0, w, h))
+        # crop edges that are real edges keep their type; cut edges get traction-free
+        et = [d.edge_type[0] if y0 == 0 else 1, d.edge_type[1] if x1 == d.nx else 1,
+              d.edge_type[2] if y1 == d.ny else 1, d.edge_type[3] if x0 == 0 else 1]
+        nt, bv = O.rect_bc(w, h, et, ev)
+        ref = O.OracleLattice(w, h, d.lam, d.mu, node_type=nt, bc_value=bv).init(ux, uy).step(S).fields()
+        r = 6
+        wx0, wx1 = max(0, si - r), min(d.nx, si + r + 1)
+        wy0, wy1 = max(0, sj - r), min(d.ny, sj + r + 1)
+        g = {k: got[k][wy0:wy1, wx0:wx1].cpu().numpy() for k in got}
+        e = {k: ref[k][wy0 - y0:wy1 - y0, wx0 - x0:wx1 - x0] for k in got}
+        for k in ("ux", "uy", "phi", "psi"):
+            scale = max(np.abs(e["ux"]).max(), np.abs(e["uy"]).max()) if k in ("ux", "uy") else \
+                max(np.abs(e["phi"]).max(), np.abs(e["psi"]).max())
+            assert np.abs(g[k] - e[k]).max() <= 2e-6 * scale + 1e-18, ((si, sj), k)
+
+
+# ----------------------------------------------------------- edge cases
+
+def _small(L, **kw):
+    args = dict(nx=20, ny=17, lam=1.0, mu=1.0, edge_type=(1, 2, 1, 1), edge_value=np.zeros(8))
+    args.update(kw)
+    return L.Lattice.rectangle(args.pop("nx"), args.pop("ny"), args.pop("lam"), args.pop("mu"),
+                               args.pop("edge_type"), args.pop("edge_value"), **args)
+
+
+def test_zero_steps_is_init(L):
+    ux, uy = W.pulse_displacement(20, 17, 9.0, 8.0, 2.0, 1e-3, "rotation")
+    lat = _small(L, storage="f64").init(ux, uy).step(0)
+    nt, bv = O.rect_bc(20, 17, (1, 2, 1, 1), np.zeros(8))
+    ref = O.OracleLattice(20, 17, 1.0, 1.0, node_type=nt, bc_value=bv).init(ux, uy)
+    assert_parity(lat.fields(), ref.fields(), 1e-13)
+    assert np.abs(lat.read("f_psi") - ref.read(O.F_PSI)).max() <= 1e-18
+    assert lat.steps == 0
+
+
+def test_invalid_inputs_rejected(L):
+    nt, bv = L.lbps_rect_bc(10, 8, 0, 0, 1.0, (1, 1, 1, 1), np.zeros(8))
+    bad = nt.copy()
+    bad[3, 3] = 1  # interior point marked as boundary
+    with pytest.raises(L.LbpsError) as e:
+        L.Lattice(10, 8, 1.0, 1.0, node_type=bad, bc_value=bv)
+    assert e.value.code == L.LBPS_ERR_INVALID
+    bad = nt.copy()
+    bad[0, 4] = 0  # boundary point left interior
+    with pytest.raises(L.LbpsError):
+        L.Lattice(10, 8, 1.0, 1.0, node_type=bad, bc_value=bv)
+    bv2 = bv.copy()
+    bv2[0, 0, 0] = np.nan
+    with pytest.raises(L.LbpsError):
+        L.Lattice(10, 8, 1.0, 1.0, node_type=nt, bc_value=bv2)
+    with pytest.raises(L.LbpsError):
+        L.Lattice(10, 8, 1.0, 1.0)  # bounded lattice without a mask
+    with pytest.raises(L.LbpsError):
+        L.Lattice(10, 8, 1.0, -1.0, periodic_x=True, periodic_y=True)
+
+
+def test_call_order_and_capacity(L):
+    lat = _small(L)
+    assert L.lbps_step(lat._h, 1) == L.LBPS_ERR_STATE
+    with pytest.raises(L.LbpsError) as e:
+        lat.read("ux")
+    assert e.value.code == L.LBPS_ERR_STATE
+    ux = np.zeros((17, 20))
+    lat.init(ux, ux)
+    small = np.zeros(10)
+    assert L._lib.lbps_read(lat._h, L.LBPS_UX, L._p(small), small.size) == L.LBPS_ERR_INVALID
+    assert L._lib.lbps_read(lat._h, 42, L._p(small), small.size) == L.LBPS_ERR_INVALID
+    assert L.lbps_step(lat._h, -1) == L.LBPS_ERR_INVALID
+    bad = ux.copy()
+    bad[2, 2] = np.inf
+    with pytest.raises(L.LbpsError):
+        lat.init(bad, ux)
+
+
+def test_nonfinite_state_reported(L):
+    """A displacement of 1e300 overflows FP32 populations; the step reports it."""
+    ux = np.full((17, 20), 1e300)
+    lat = _small(L, storage="f32").init(ux, np.zeros_like(ux))
+    assert L.lbps_step(lat._h, 3) == L.LBPS_ERR_NONFINITE
+    assert lat.check() == L.LBPS_ERR_NONFINITE
+    lat.init(np.zeros_like(ux), np.zeros_like(ux))  # re-initialising clears the flag
+    assert L.lbps_step(lat._h, 3) == L.LBPS_OK
+
+
+def test_norms_match_host(L):
+    ux, uy = W.pulse_displacement(50, 37, 20.0, 20.0, 4.0, 1e-3, "dilatation")
+    lat = L.Lattice.rectangle(50, 37, 2.0, 1.0, (2, 1, 1, 1), np.zeros(8), a0_phi=0.99).init(ux, uy).step(30)
+    for name in ("ux", "uy", "phi", "psi", "consistency"):
+        x = lat.read(name)
+        ref = torch.from_numpy(np.sin(np.arange(x.size)).reshape(x.shape) * 1e-3).cuda()
+        n = lat.norms(name, ref)
+        r = ref.cpu().numpy()
+        assert n[0] == pytest.approx(((x - r) ** 2).sum(), rel=1e-12)
+        assert n[1] == pytest.approx((r ** 2).sum(), rel=1e-12)
+        assert abs(n[2] - x.sum()) <= 1e-12 * np.abs(x).sum() + 1e-300
+        assert n[3] == np.abs(x).max()
+        n0 = lat.norms(name)
+        assert n0[0] == pytest.approx((x ** 2).sum(), rel=1e-12) and n0[1] == 0.0
+
+
+def test_consistency_and_populations_match_oracle(L):
+    nx, ny = 31, 26
+    ux, uy = W.pulse_displacement(nx, ny, 12.0, 10.0, 3.0, 1e-3, "rotation")
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 2, 1), np.zeros(8))
+    ref = O.OracleLattice(nx, ny, 1.0, 1.0, a0_phi=0.99, node_type=nt, bc_value=bv).init(ux, uy).step(40)
+    lat = L.Lattice.rectangle(nx, ny, 1.0, 1.0, (1, 1, 2, 1), np.zeros(8), a0_phi=0.99, storage="f64")
+    lat.init(ux, uy).step(40)
+    e_ref = ref.read(O.ERR)
+    assert np.abs(lat.read("consistency") - e_ref).max() <= 1e-10 * e_ref.max()
+    for f, fid in (("f_phi", O.F_PHI), ("f_psi", O.F_PSI)):
+        r = ref.read(fid)
+        assert np.abs(lat.read(f) - r).max() <= 1e-10 * np.abs(r).max()
+
+
+def test_sync_matches_oracle(L):
+    nx, ny = 40, 30
+    ux, uy = W.pulse_displacement(nx, ny, 15.0, 12.0, 3.0, 1e-3, "dilatation")
+    nt, bv = O.rect_bc(nx, ny, (2, 1, 1, 1), np.zeros(8))
+    ref = O.OracleLattice(nx, ny, 1.5, 1.0, a0_phi=0.99, node_type=nt, bc_value=bv).init(ux, uy).step(13).sync()
+    for storage in ("f64", "f32"):
+        lat = L.Lattice.rectangle(nx, ny, 1.5, 1.0, (2, 1, 1, 1), np.zeros(8), a0_phi=0.99, storage=storage)
+        lat.init(ux, uy).step(13).sync()
+        assert_parity(lat.fields(), ref.fields(), TOL[storage])
+        assert lat.read("consistency").max() <= (1e-15 if storage == "f64" else 1e-10)
+
+
+def test_device_init_equals_host_init(L):
+    ux, uy = W.pulse_displacement(40, 33, 15.0, 12.0, 3.0, 1e-3, "dilatation")
+    vx, vy = 1e-4 * uy, -1e-4 * ux
+    a = _small(L, nx=40, ny=33, storage="f64").init(ux, uy, vx, vy).step(11)
+    t = [torch.from_numpy(x).cuda() for x in (ux, uy, vx, vy)]
+    b = _small(L, nx=40, ny=33, storage="f64").init(*t).step(11)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    nt, bv = O.rect_bc(40, 33, (1, 2, 1, 1), np.zeros(8))
+    ref = O.OracleLattice(40, 33, 1.0, 1.0, node_type=nt, bc_value=bv).init(ux, uy, vx, vy).step(11)
+    assert_parity(fa, ref.fields(), TOL["f64"])
+
+
+def test_library_owned_memory(L):
+    """device_mem = NULL: the library allocates and frees the state itself."""
+    p = L.lbps_params(24, 20, 1.0, 1.0, 1.0, 1.0, 0.99, 1, 1, 0, 0, L.LBPS_STORAGE_F32, None)
+    h = L.lbps_create(p, None, None, 0, 0)
+    ux, uy = W.pulse_displacement(24, 20, 10.0, 9.0, 2.0, 1e-3, "dilatation")
+    L.lbps_init(h, np.ascontiguousarray(ux), np.ascontiguousarray(uy))
+    assert L.lbps_step(h, 10) == L.LBPS_OK
+    out = np.zeros((20, 24))
+    L.lbps_read(h, L.LBPS_UX, out)
+    L.lbps_destroy(h)
+    ref = O.OracleLattice(24, 20, 1.0, 1.0, a0_phi=0.99, periodic_x=True, periodic_y=True).init(ux, uy).step(10)
+    r = ref.read(O.UX)
+    assert np.linalg.norm(out - r) <= 1e-5 * np.linalg.norm(r)
+
+
+def test_chunked_host_read(L):
+    """Host reads larger than the staging buffer go through it in row blocks."""
+    nx, ny = 640, 420
+    d = W.Domain(nx, ny, 1.0, 1.0, pulses=[(300.0, 200.0, 20.0, 1e-3, "rotation")])
+    lat = L.Lattice.rectangle(nx, ny, 1.0, 1.0, (1, 1, 1, 1), np.zeros(8), a0_phi=0.99)
+    lat.init(*d.displacement()).step(5)
+    for f in ("f_phi", "psi", "uy"):
+        h = lat.read(f)
+        dv = lat.read_device(f).cpu().numpy()
+        assert np.array_equal(h, dv), f
+
+
+def test_two_streams_independent(L):
+    """Two lattices on two streams, stepped interleaved, give their solo results."""
+    cs1, cs2 = MIXED[0], MIXED[3]
+    solo1, solo2 = run_gpu(L, cs1, "f32"), run_gpu(L, cs2, "f32")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def mk(cs, st):
+        return L.Lattice.rectangle(cs["nx"], cs["ny"], cs["lam"], 1.0, cs["et"], cs["ev"], a0_phi=cs["a0"],
+                                   bc_feq_mode=cs["mode"], sync_every=cs["sync"], storage="f32", stream=st)
+
+    a, b = mk(cs1, s1), mk(cs2, s2)
+    a.init(cs1["ux"], cs1["uy"])
+    b.init(cs2["ux"], cs2["uy"])
+    for _ in range(max(cs1["steps"], cs2["steps"]) // 10):
+        if a.steps < cs1["steps"]:
+            a.step_async(10)
+        if b.steps < cs2["steps"]:
+            b.step_async(10)
+    assert a.check() == 0 and b.check() == 0
+    fa, fb = a.fields(), b.fields()
+    for k in solo1:
+        assert np.array_equal(fa[k], solo1[k]) and np.array_equal(fb[k], solo2[k]), k
