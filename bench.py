@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark of the plane-strain LBM time loop on GB300.
+
+One benchmark step is one time step of the whole method (Fig. 3): boundary
+accelerations and reset, interior accelerations, Newmark, and the LBE for both
+population sets, over the full lattice.  Default workload: the 8192 x 8192
+lattice with lambda/mu = 3, a clamped bottom edge, traction-free other edges
+and 32 seeded Gaussian dilatation/rotation pulses, FP32 populations, FP64
+displacement (its state, 9.7 GB, is far larger than L2).
+
+Prints one JSON line (rank 0).  Metric: two-field lattice updates per second
+(GLUPS = lattice points x time steps / s / 1e9), whole job.
+  --impl reference  times the FP64 CPU oracle on the host cores instead
+                    (bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+if str(ROOT) not in sys.path:
+    sys.path.insert(0, str(ROOT))
+
+METRIC = "two-field GLUPS"
+UNIT = "GLUPS"
+BYTES_PER_UPDATE = {"f32": 2 * (10 * 4 + 4 * 8), "f64": 2 * (10 * 8 + 4 * 8)}
+
+
+# ----------------------------------------------------------------- helpers
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(local_seconds, local_units, world, reduce_max, reduce_sum):
+    """Whole-job throughput: units summed over ranks / slowest rank's time."""
+    t = reduce_max(local_seconds)
+    u = reduce_sum(local_units)
+    return u / t, t, u
+
+
+def workload(name, size=None):
+    """(config name, Domain) of a workload recipe."""
+    from paper_2301_00228_gb300 import workloads as W
+
+    if name == "pulses":
+        size = size or 8192
+        return f"pulses_{size}", W.many_pulses(size=size)
+    if name == "waves":
+        size = size or 1024
+        return f"waves_{size}", W.periodic_waves(size=size)
+    if name == "square":
+        return "square_64", W.square_64()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def describe(d):
+    bc = {1: "N", 2: "D"}
+    edges = "periodic" if d.periodic_x and d.periodic_y else "".join(bc[e] for e in d.edge_type)
+    return {"nx": d.nx, "ny": d.ny, "lambda_over_mu": d.lam / d.mu, "a0_phi": d.a0_phi,
+            "edges_bottom_right_top_left": edges, "pulses": len(d.pulses), "wave": d.wave}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm_sorted = sorted(sm)
+        return {"sm_mhz": sm_sorted[len(sm) // 2], "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    src = (ROOT / "paper_2301_00228_gb300" / "csrc" / "lbps_kernels.cu").read_bytes()
+    src += (ROOT / "paper_2301_00228_gb300" / "csrc" / "lbps_device.cuh").read_bytes()
+    return hashlib.sha256(src).hexdigest()[:16]
+
+
+def ncu_traffic(workload_name, storage):
+    """DRAM bytes per bulk-kernel launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    f = ROOT / "profiles" / f"bulk_kernel_{workload_name}_{storage}.md"
+    if not f.exists():
+        return None
+    text = f.read_text()
+    h = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    b = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", text)
+    if not h or not b or h.group(1) != kernel_source_hash():
+        return None
+    return float(b.group(1))
+
+
+# ------------------------------------------------------------ CPU oracle
+
+def oracle_sample(d, target_seconds=15.0, side=1024):
+    """Time the FP64 oracle on a side x side crop of the workload (bottom-left
+    corner, same edge types) for as many steps as fill about target_seconds."""
+    import numpy as np
+    import oracle as O
+    from paper_2301_00228_gb300 import workloads as W
+
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    side_x, side_y = min(side, d.nx), min(side, d.ny)
+    if d.periodic_x and d.periodic_y:
+        c = W.Domain(side_x, side_y, d.lam, d.mu, d.rho, d.a0_phi, periodic_x=True, periodic_y=True)
+        m, n, ad, as_ = d.wave
+        ux, uy = W.plane_wave_displacement(side_x, side_y, max(1, round(m * side_x / d.nx)),
+                                           round(n * side_y / d.ny), ad, as_)
+        nt = bv = None
+    else:
+        c = W.crop(d, 0, 0, side_x, side_y)
+        ux, uy = d.displacement(window=(0, 0, side_x, side_y))
+        et = [d.edge_type[0], 1, 1, d.edge_type[3]]
+        nt, bv = O.rect_bc(side_x, side_y, et, np.asarray(d.edge_value, float).ravel())
+    lat = O.OracleLattice(side_x, side_y, c.lam, c.mu, c.rho, a0_phi=c.a0_phi, periodic_x=c.periodic_x,
+                          periodic_y=c.periodic_y, node_type=nt, bc_value=bv)
+    lat.init(ux, uy)
+    t0 = time.perf_counter()
+    lat.step(2)
+    per = (time.perf_counter() - t0) / 2
+    steps = max(2, int(target_seconds / max(per, 1e-9)))
+    t0 = time.perf_counter()
+    lat.step(steps)
+    dt = time.perf_counter() - t0
+    glups = side_x * side_y * steps / dt / 1e9
+    return {"value": glups, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{side_x}x{side_y} corner crop of the workload (same material, edges of the "
+                      f"corner kept), {steps} FP64 steps in {dt:.1f} s"}, dt, steps
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    wname, d = workload(args.workload, args.size)
+    secs = []
+    for _ in range(args.warmup):
+        oracle_sample(d, target_seconds=2.0)
+    vals = []
+    cb = None
+    for _ in range(args.steps):
+        cb, dt, _ = oracle_sample(d, target_seconds=args.ref_seconds)
+        vals.append(cb["value"])
+        secs.append(dt)
+    value = sum(vals) / len(vals)
+    cb["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wname, **describe(d)},
+            "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU for the default arm")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2301_00228_gb300 import lbps
+
+    wname, d = workload(args.workload, args.size)
+    et = d.edge_type
+    ev = np.asarray(d.edge_value, float).ravel()
+    stream = torch.cuda.current_stream()
+    mk = dict(a0_phi=d.a0_phi, storage=args.storage, sync_every=args.sync_every)
+    if d.periodic_x and d.periodic_y:
+        lat = lbps.Lattice(d.nx, d.ny, d.lam, d.mu, d.rho, periodic_x=True, periodic_y=True, **mk)
+    else:
+        lat = lbps.Lattice.rectangle(d.nx, d.ny, d.lam, d.mu, et, ev, **mk)
+    ux, uy = d.displacement_torch("cuda")
+    lat.init(ux, uy)
+    torch.cuda.synchronize()
+
+    # warm-up
+    lat.step(args.warmup)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    lbps.lbps_profile(lat._h, 1)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc = lbps.lbps_step_async(lat._h, args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clock = clocks.stop()
+    if rc != 0:
+        raise SystemExit(f"step failed: {lbps.lbps_strerror(rc)}")
+    if lat.check() != 0:
+        raise SystemExit("state became non-finite")
+    prof = lbps.lbps_profile_read(lat._h)
+    lbps.lbps_profile(lat._h, 0)
+    seconds = e0.elapsed_time(e1) / 1000.0
+    units = d.nx * d.ny * args.steps
+
+    if dist is not None:
+        def rmax(x):
+            t = torch.tensor([x], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+
+        def rsum(x):
+            t = torch.tensor([x], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+            return float(t.item())
+    else:
+        rmax = rsum = float
+    value_ups, t_max, units_all = aggregate(seconds, units, world, rmax, rsum)
+    value = value_ups / 1e9
+
+    # roofline of the dominant (bulk) kernel
+    bulk_ms, bulk_n, bnd_ms, bnd_n = (float(x) for x in prof)
+    interior = (d.nx - (0 if d.periodic_x else 2)) * (d.ny - (0 if d.periodic_y else 2))
+    alg_bytes = interior * BYTES_PER_UPDATE[args.storage]
+    bulk_avg_s = bulk_ms / max(bulk_n, 1) / 1000.0
+    peak, peak_kind = measured_peaks()
+    achieved = alg_bytes / bulk_avg_s / 1e9
+    traffic = ncu_traffic(wname, args.storage)
+    total_kernel_ms = bulk_ms + bnd_ms
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "bulk_kernel", "peak_source": peak_kind,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": bulk_avg_s * 1000.0,
+                "share_of_step_kernel_time": bulk_ms / total_kernel_ms if total_kernel_ms else None,
+                "boundary_kernel_avg_ms": bnd_ms / max(bnd_n, 1)}
+    gpu_launches = int(bulk_n + bnd_n) + (args.steps // args.sync_every if args.sync_every else 0)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pin_ux = torch.empty((d.ny, d.nx), dtype=torch.float64, pin_memory=True)
+        pin_uy = torch.empty_like(pin_ux)
+        pin_ux.copy_(ux.cpu())
+        pin_uy.copy_(uy.cpu())
+        out_x = torch.empty_like(pin_ux)
+        out_y = torch.empty_like(pin_ux)
+        barrier()
+        t0 = time.perf_counter()
+        lbps.lbps_init(lat._h, pin_ux.numpy(), pin_uy.numpy())
+        rc = lbps.lbps_step(lat._h, args.e2e_steps)
+        lbps.lbps_read(lat._h, lbps.LBPS_UX, out_x.numpy())
+        lbps.lbps_read(lat._h, lbps.LBPS_UY, out_y.numpy())
+        t1 = time.perf_counter()
+        barrier()
+        if rc != 0:
+            raise SystemExit(f"e2e step failed: {lbps.lbps_strerror(rc)}")
+        e2e_ups, _, _ = aggregate(t1 - t0, d.nx * d.ny * args.e2e_steps, world, rmax, rsum)
+        e2e = {"value": e2e_ups / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * d.nx * d.ny * 8, "d2h_bytes_per_step": 2 * d.nx * d.ny * 8,
+               "step": f"one solve: lbps_init from pinned host u0, lbps_step({args.e2e_steps}), "
+                       f"lbps_read of u_x and u_y into pinned host memory"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _, _ = oracle_sample(d, target_seconds=args.ref_seconds)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+                "config": {"workload": wname, **describe(d), "storage": args.storage,
+                           "displacement": "f64", "sync_every": args.sync_every,
+                           "l2": "state larger than L2" if alg_bytes > 1.3e8 else "state fits L2",
+                           "replicas_per_gpu": 1},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "clocks": clock}
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="pulses", choices=["pulses", "waves", "square"])
+    ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")
+    ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--sync-every", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

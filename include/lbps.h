@@ -162,6 +162,25 @@ int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out
  * number of completed time steps. */
 int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done);
 
+/* The CUDA runtime error code (a cudaError_t value) of the most recent
+ * step, check or initialisation of this lattice that returned
+ * LBPS_ERR_CUDA; 0 if none. */
+int lbps_last_cuda_error(const lbps_lattice* lat);
+
+/* Diagnostics of a checked build (compiled with LBPS_CHECKED): every device
+ * access of the time-loop kernels is checked against the lattice's device
+ * block and for alignment, and the first violation is recorded instead of
+ * performed.  Returns 1 and out[0] = source line, out[1] = address of that
+ * first violation (0, 0 if none) in a checked build; returns 0 and zeros in
+ * a normal build.  Waits for the device. */
+int lbps_check_report(uint64_t out[2]);
+
+/* Launch shape of the interior kernel (performance only; results are
+ * bit-identical for every setting).  variant 0..3 selects the register budget
+ * (0: 6 blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8); rows_per_warp
+ * (1..4096) the number of rows each warp marches over.  Defaults: 0, 32. */
+int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);
+
 /* Per-kernel timing for roofline reports.  enable != 0 starts recording a
  * CUDA event before and after every kernel launch of the time loop on the
  * lattice's stream (the two kernels of a step stay back to back); 0 stops.

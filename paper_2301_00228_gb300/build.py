@@ -39,16 +39,21 @@ def _stale(outp: Path, deps) -> bool:
     return any(d.stat().st_mtime > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> Path:
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, checked: bool = False) -> Path:
+    """Compile liblbps.so; checked=True builds liblbps_checked.so with every
+    kernel memory access range- and alignment-checked (LBPS_CHECKED)."""
     BUILD.mkdir(exist_ok=True)
     headers = list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) + list(INCLUDE.glob("*.h"))
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(INCLUDE), "-I", str(CSRC)]
     if ptxas_info:
         flags += ["-Xptxas", "-v"]
+    if checked:
+        flags += ["-DLBPS_CHECKED"]
+    lib = PKG / ("liblbps_checked.so" if checked else "liblbps.so")
     procs = []
     objs = []
     for src in sources():
-        obj = BUILD / (src.stem + ".o")
+        obj = BUILD / (src.stem + ("_checked" if checked else "") + ".o")
         objs.append(obj)
         if force or ptxas_info or _stale(obj, [src] + headers):
             cmd = [nvcc()] + flags + ["-c", str(src), "-o", str(obj)]
@@ -64,14 +69,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             failed.append(src.name)
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(failed))
-    if force or procs or _stale(LIB, objs):
-        tmp = LIB.with_suffix(f".so.{os.getpid()}")
+    if force or procs or _stale(lib, objs):
+        tmp = lib.with_suffix(f".so.{os.getpid()}")
         cmd = [nvcc()] + ARCH + ["-shared", "-o", str(tmp)] + [str(o) for o in objs]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv)
-    print(LIB)
+    out = build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv,
+                checked="--checked" in sys.argv)
+    print(out)

@@ -29,7 +29,7 @@ struct Layout {
     size_t u_bytes;     // 4 FP64 planes, aligned
     size_t copy_bytes;
     size_t off_copy[2];
-    size_t off_bn, off_part, off_out, off_flag, off_staging;
+    size_t off_bn, off_edge, off_part, off_out, off_flag, off_staging;
     size_t staging_bytes;
     size_t total;
     int nb;
@@ -71,6 +71,8 @@ Layout make_layout(const lbps_params* p) {
     off += L.copy_bytes;
     L.off_bn = off;
     off += align_up((size_t)L.nb * sizeof(BNode));
+    L.off_edge = off;
+    off += align_up(2 * (size_t)L.nb * L.elem);
     L.off_part = off;
     off += align_up((size_t)lbps::kNormBlocks * 4 * sizeof(double));
     L.off_out = off;
@@ -115,6 +117,8 @@ struct lbps_lattice {
     char* mem;
     bool owns;
     int cur;            // copy holding time t
+    lbps::Tuning tuning;  // bulk-kernel launch shape
+    int last_cuda = 0;    // cudaError_t of the last failing CUDA call
     int64_t steps;
     bool initialised;
     // per-kernel event timing (lbps_profile)
@@ -131,6 +135,8 @@ struct lbps_lattice {
         return v;
     }
     const BNode* bn() const { return reinterpret_cast<const BNode*>(mem + L.off_bn); }
+    template <typename T>
+    T* edge() const { return reinterpret_cast<T*>(mem + L.off_edge); }
     unsigned* flag() const { return reinterpret_cast<unsigned*>(mem + L.off_flag); }
     double* partials() const { return reinterpret_cast<double*>(mem + L.off_part); }
     double* out4() const { return reinterpret_cast<double*>(mem + L.off_out); }
@@ -169,10 +175,10 @@ int run_step(lbps_lattice* lat) {
         if (e == cudaSuccess) {
             if (lat->f64())
                 e = lbps::launch_boundary<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(a), lat->view<double>(b),
-                                                  lat->bn(), lat->L.nb, lat->flag(), lat->st);
+                                                  lat->bn(), lat->L.nb, lat->edge<double>(), lat->flag(), lat->st);
             else
                 e = lbps::launch_boundary<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(a), lat->view<float>(b),
-                                                 lat->bn(), lat->L.nb, lat->flag(), lat->st);
+                                                 lat->bn(), lat->L.nb, lat->edge<float>(), lat->flag(), lat->st);
         }
         if (e == cudaSuccess) e = prof_mark(lat);
         if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(1);
@@ -181,14 +187,17 @@ int run_step(lbps_lattice* lat) {
     if (e == cudaSuccess) {
         if (lat->f64())
             e = lbps::launch_bulk<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(a), lat->view<double>(b),
-                                          lat->flag(), lat->st);
+                                          lat->edge<double>(), lat->L.nb, lat->flag(), lat->st, lat->tuning);
         else
             e = lbps::launch_bulk<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(a), lat->view<float>(b),
-                                         lat->flag(), lat->st);
+                                         lat->edge<float>(), lat->L.nb, lat->flag(), lat->st, lat->tuning);
     }
     if (e == cudaSuccess) e = prof_mark(lat);
     if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(0);
-    if (e != cudaSuccess) return LBPS_ERR_CUDA;
+    if (e != cudaSuccess) {
+        lat->last_cuda = (int)e;
+        return LBPS_ERR_CUDA;
+    }
     lat->cur = b;
     lat->steps += 1;
     return LBPS_OK;
@@ -407,6 +416,7 @@ int lbps_create(const lbps_params* params, const uint8_t* node_type, const doubl
     lat->steps = 0;
     lat->initialised = false;
     cudaError_t e = cudaMemsetAsync(lat->mem, 0, L.total, lat->st);
+    if (e == cudaSuccess) e = lbps::set_check_range(lat->mem, L.total, lat->st);
     if (e == cudaSuccess && L.nb > 0)
         e = cudaMemcpyAsync(lat->mem + L.off_bn, bn.data(), bn.size() * sizeof(BNode), cudaMemcpyHostToDevice,
                             lat->st);
@@ -428,7 +438,9 @@ int lbps_init(lbps_lattice* lat, const double* ux0, const double* uy0, const dou
     }
     int rc = init_from(lat, ux0, uy0, vx0, vy0, cudaMemcpyHostToDevice);
     if (rc != LBPS_OK) return rc;
-    return cuda_ok(cudaStreamSynchronize(lat->st));
+    cudaError_t e = cudaStreamSynchronize(lat->st);
+    if (e != cudaSuccess) lat->last_cuda = (int)e;
+    return cuda_ok(e);
 }
 
 int lbps_init_device(lbps_lattice* lat, const double* d_ux0, const double* d_uy0, const double* d_vx0,
@@ -456,7 +468,10 @@ int lbps_check(lbps_lattice* lat) {
     unsigned flag = 0;
     cudaError_t e = cudaMemcpyAsync(&flag, lat->flag(), sizeof(unsigned), cudaMemcpyDeviceToHost, lat->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
-    if (e != cudaSuccess) return LBPS_ERR_CUDA;
+    if (e != cudaSuccess) {
+        lat->last_cuda = (int)e;
+        return LBPS_ERR_CUDA;
+    }
     return flag ? LBPS_ERR_NONFINITE : LBPS_OK;
 }
 
@@ -531,6 +546,25 @@ int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done) {
         out[5] = lat->c.dt;
     }
     if (steps_done) *steps_done = lat->steps;
+    return LBPS_OK;
+}
+
+int lbps_last_cuda_error(const lbps_lattice* lat) { return lat ? lat->last_cuda : 0; }
+
+int lbps_check_report(uint64_t out[2]) {
+    if (!out) return LBPS_ERR_INVALID;
+    unsigned long long r[2] = {0, 0};
+    int rc = lbps::check_report(r);
+    out[0] = r[0];
+    out[1] = r[1];
+    return rc < 0 ? LBPS_ERR_CUDA : rc;
+}
+
+int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp) {
+    if (!lat || variant < 0 || variant >= lbps::kTuningVariants || rows_per_warp < 1 || rows_per_warp > 4096)
+        return LBPS_ERR_INVALID;
+    lat->tuning.variant = variant;
+    lat->tuning.rows_per_warp = rows_per_warp;
     return LBPS_OK;
 }
 

@@ -8,6 +8,36 @@
 
 namespace lbps {
 
+// Global-memory accessors of the kernels.  In a build with LBPS_CHECKED
+// defined, every access is checked against the lattice's device block and
+// for alignment; the first violation is recorded (source line and address)
+// and the access is skipped, so a bad index shows up as a report instead of
+// a fault.  Without LBPS_CHECKED they are plain loads and stores.
+#ifdef LBPS_CHECKED
+__device__ const char* g_chk_lo;
+__device__ const char* g_chk_hi;
+__device__ unsigned long long g_chk_line;
+__device__ unsigned long long g_chk_addr;
+template <typename P>
+__device__ __forceinline__ bool chk_ok(const P* p, int line) {
+    const char* c = reinterpret_cast<const char*>(p);
+    bool ok = c >= g_chk_lo && c + sizeof(P) <= g_chk_hi && (reinterpret_cast<uintptr_t>(c) % sizeof(P)) == 0;
+    if (!ok && atomicCAS(&g_chk_line, 0ull, (unsigned long long)line) == 0ull)
+        g_chk_addr = reinterpret_cast<unsigned long long>(c);
+    return ok;
+}
+#define LBPS_LDG(p) (::lbps::chk_ok((p), __LINE__) ? __ldg(p) : decltype(__ldg(p))(0))
+#define LBPS_LD(p) (::lbps::chk_ok((p), __LINE__) ? *(p) : decltype(+*(p))(0))
+#define LBPS_ST(p, v)                                      \
+    do {                                                  \
+        if (::lbps::chk_ok((p), __LINE__)) *(p) = (v);    \
+    } while (0)
+#else
+#define LBPS_LDG(p) __ldg(p)
+#define LBPS_LD(p) (*(p))
+#define LBPS_ST(p, v) (*(p) = (v))
+#endif
+
 // Lattice geometry.  Planes are pitched: row j of a plane starts at j * px.
 struct Geo {
     int nx, ny;
@@ -120,7 +150,7 @@ __device__ inline double ddx(const double* __restrict__ g, size_t stride, int i,
     Sten s = stencil(i, G.nx, G.periodic_x);
     const double* r = g + (size_t)j * stride;
     double acc = 0.0;
-    for (int q = 0; q < s.n; ++q) acc = fma_rn(s.w[q], r[wrap(i + s.d[q], G.nx)], acc);
+    for (int q = 0; q < s.n; ++q) acc = fma_rn(s.w[q], LBPS_LD(&r[wrap(i + s.d[q], G.nx)]), acc);
     return mul_rn(acc, inv2h);
 }
 
@@ -128,7 +158,7 @@ __device__ inline double ddy(const double* __restrict__ g, size_t stride, int i,
                              double inv2h) {
     Sten s = stencil(j, G.ny, G.periodic_y);
     double acc = 0.0;
-    for (int q = 0; q < s.n; ++q) acc = fma_rn(s.w[q], g[(size_t)wrap(j + s.d[q], G.ny) * stride + i], acc);
+    for (int q = 0; q < s.n; ++q) acc = fma_rn(s.w[q], LBPS_LD(&g[(size_t)wrap(j + s.d[q], G.ny) * stride + i]), acc);
     return mul_rn(acc, inv2h);
 }
 

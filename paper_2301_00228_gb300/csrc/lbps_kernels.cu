@@ -27,7 +27,7 @@ enum {
 };
 
 template <typename T>
-__device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+__device__ __forceinline__ T ld(const T* p) { return LBPS_LDG(p); }
 
 // Sum of the five populations of one set at pitched offset p.
 template <typename T>
@@ -44,11 +44,11 @@ __device__ __forceinline__ void store_feq(T* __restrict__ f, size_t plane, size_
                                           double a, double s, double jx, double jy) {
     T* b = f + (size_t)set * 5 * plane + p;
     double as = a * s;
-    b[0] = (T)(a0 * s);
-    b[plane] = (T)(as + 0.5 * jx);
-    b[2 * plane] = (T)(as + 0.5 * jy);
-    b[3 * plane] = (T)(as - 0.5 * jx);
-    b[4 * plane] = (T)(as - 0.5 * jy);
+    LBPS_ST(&b[0], (T)(a0 * s));
+    LBPS_ST(&b[plane], (T)(as + 0.5 * jx));
+    LBPS_ST(&b[2 * plane], (T)(as + 0.5 * jy));
+    LBPS_ST(&b[3 * plane], (T)(as - 0.5 * jx));
+    LBPS_ST(&b[4 * plane], (T)(as - 0.5 * jy));
 }
 
 // ------------------------------------------------------------------ init
@@ -65,7 +65,7 @@ __global__ void init_kernel(Geo g, Consts c, View<T> A) {
     size_t p = (size_t)j * g.px + i;
     double phi = ddx(ux, g.px, i, j, g, c.inv2h) + ddy(uy, g.px, i, j, g, c.inv2h);
     double psi = ddx(uy, g.px, i, j, g, c.inv2h) - ddy(ux, g.px, i, j, g, c.inv2h);
-    double vx = A.u[2 * g.plane + p], vy = A.u[3 * g.plane + p];
+    double vx = LBPS_LD(&A.u[2 * g.plane + p]), vy = LBPS_LD(&A.u[3 * g.plane + p]);
     // First moments from du/dt (J_phi = -v, J_psi = (-v_y, v_x)), in lattice
     // units Jbar = J dt / dh.
     double q = c.dt / c.dh;
@@ -131,15 +131,17 @@ __device__ inline void accel_at(const Geo& g, const Consts& c, const KC<T>& k, c
     const double* uy = A.u + g.plane;
     size_t p = (size_t)j * g.px + i;
     if (is_boundary(i, j, g)) {
-        BNode b = bn[perim_index(i, j, g)];
-        if (b.type == DIRICHLET) {
+        const BNode* bp = &bn[perim_index(i, j, g)];
+        const int btype = LBPS_LD(&bp->type);
+        const double bx = LBPS_LD(&bp->bx), by = LBPS_LD(&bp->by);
+        if (btype == DIRICHLET) {
             const double* vx = A.u + 2 * g.plane;
             const double* vy = A.u + 3 * g.plane;
             double two_dt2 = 2.0 / (c.dt * c.dt), two_dt = 2.0 / c.dt;
-            ax = two_dt2 * (b.bx - ux[p]) - two_dt * vx[p];
-            ay = two_dt2 * (b.by - uy[p]) - two_dt * vy[p];
+            ax = two_dt2 * (bx - LBPS_LD(&ux[p])) - two_dt * LBPS_LD(&vx[p]);
+            ay = two_dt2 * (by - LBPS_LD(&uy[p])) - two_dt * LBPS_LD(&vy[p]);
         } else {
-            accel_neumann(g, c, ux, uy, i, j, b.bx, b.by, ax, ay);
+            accel_neumann(g, c, ux, uy, i, j, bx, by, ax, ay);
         }
         return;
     }
@@ -158,16 +160,52 @@ __device__ inline void unew_at(const Geo& g, const Consts& c, const KC<T>& k, co
     double ax, ay;
     accel_at(g, c, k, A, bn, i, j, ax, ay);
     size_t p = (size_t)j * g.px + i;
-    newmark(A.u[p], A.u[2 * g.plane + p], ax, c, ux1, vx1);
-    newmark(A.u[g.plane + p], A.u[3 * g.plane + p], ay, c, uy1, vy1);
+    newmark(LBPS_LD(&A.u[p]), LBPS_LD(&A.u[2 * g.plane + p]), ax, c, ux1, vx1);
+    newmark(LBPS_LD(&A.u[g.plane + p]), LBPS_LD(&A.u[3 * g.plane + p]), ay, c, uy1, vy1);
+}
+
+// Value streamed out of a boundary source (Eq. LBE_mod).  f-hat is the mean
+// of the stored (A) and reset (B) populations of the source; the
+// equilibrium is taken from f-hat (mode 0) or from f(x_k, t) (mode 1).
+// ALPHA is the direction of travel (1..4), OPP its reverse.
+template <int ALPHA, int OPP, typename T>
+__device__ inline T stream_from_boundary(const T* __restrict__ fa, const T* __restrict__ fb, size_t plane,
+                                         const KC<T>& k, int set, int mode) {
+    T a5[5], h5[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        a5[q] = ld(fa + q * plane);
+        h5[q] = mul_rn((T)0.5, add_rn(a5[q], LBPS_LD(&fb[q * plane])));
+    }
+    if (mode == 0) {
+        T sh = sum5(h5[0], h5[1], h5[2], h5[3], h5[4]);
+        return fma_rn(k.two_a[set], sh, -h5[OPP]);  // 2 f_eq(f-hat) - f-hat = 2 a s-hat - f-hat^opp
+    }
+    T sa = sum5(a5[0], a5[1], a5[2], a5[3], a5[4]);
+    T ej = sub_rn(a5[ALPHA], a5[OPP]);              // e_alpha . Jbar(x_k, t)
+    return sub_rn(add_rn(mul_rn(k.two_a[set], sa), ej), h5[ALPHA]);
+}
+
+// Direction (1..4, D2Q5 numbering) from boundary point (i, j) towards its one
+// interior neighbour, or 0 when it has none (corners, and points whose inward
+// neighbour is itself on the boundary).
+__device__ inline int inward_dir(int i, int j, const Geo& g) {
+    bool l = !g.periodic_x && i == 0, r = !g.periodic_x && i == g.nx - 1;
+    bool b = !g.periodic_y && j == 0, t = !g.periodic_y && j == g.ny - 1;
+    if ((l || r) && (b || t)) return 0;  // corner
+    if (l) return 1;                      // +x
+    if (r) return 3;                      // -x
+    if (b) return 2;                      // +y
+    return 4;                             // -y (t)
 }
 
 template <typename T>
 __global__ void __launch_bounds__(128) boundary_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
-                                                       const BNode* __restrict__ bn, int nb, unsigned* flag) {
+                                                       const BNode* __restrict__ bn, int nb, T* __restrict__ edge,
+                                                       unsigned* flag) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
-    int i = bn[b].i, j = bn[b].j;
+    int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
     size_t p = (size_t)j * g.px + i;
     double ux1, uy1, vx1, vy1;
     unew_at(g, c, k, A, bn, i, j, ux1, uy1, vx1, vy1);
@@ -188,99 +226,183 @@ __global__ void __launch_bounds__(128) boundary_kernel(Geo g, Consts c, KC<T> k,
     }
     double phi = mul_rn(dux_dx, c.inv2h) + mul_rn(duy_dy, c.inv2h);
     double psi = mul_rn(duy_dx, c.inv2h) - mul_rn(dux_dy, c.inv2h);
-    // Eq. correction-f with J(x_k, t) of the stored populations.
+    // Eq. correction-f with J(x_k, t) of the stored populations, then the value
+    // this point streams into its interior neighbour (Eq. LBE_mod).
+    const int dir = inward_dir(i, j, g);
+#pragma unroll
     for (int set = 0; set < 2; ++set) {
         const T* fa = A.f + (size_t)set * 5 * g.plane + p;
+        const T* fb = B.f + (size_t)set * 5 * g.plane + p;
         double jx = (double)ld(fa + g.plane) - (double)ld(fa + 3 * g.plane);
         double jy = (double)ld(fa + 2 * g.plane) - (double)ld(fa + 4 * g.plane);
         store_feq(B.f, g.plane, p, set, c.a0[set], c.a[set], set == 0 ? phi : psi, jx, jy);
+        T v = (T)0;
+        switch (dir) {
+        case 1: v = stream_from_boundary<1, 3>(fa, fb, g.plane, k, set, c.bc_feq_mode); break;
+        case 2: v = stream_from_boundary<2, 4>(fa, fb, g.plane, k, set, c.bc_feq_mode); break;
+        case 3: v = stream_from_boundary<3, 1>(fa, fb, g.plane, k, set, c.bc_feq_mode); break;
+        case 4: v = stream_from_boundary<4, 2>(fa, fb, g.plane, k, set, c.bc_feq_mode); break;
+        default: break;
+        }
+        if (dir != 0) LBPS_ST(&edge[(size_t)set * nb + b], v);
     }
-    B.u[p] = ux1;
-    B.u[g.plane + p] = uy1;
-    B.u[2 * g.plane + p] = vx1;
-    B.u[3 * g.plane + p] = vy1;
+    LBPS_ST(&B.u[p], ux1);
+    LBPS_ST(&B.u[g.plane + p], uy1);
+    LBPS_ST(&B.u[2 * g.plane + p], vx1);
+    LBPS_ST(&B.u[3 * g.plane + p], vy1);
     if (!isfinite((T)phi + (T)psi)) atomicOr(flag, 1u);
 }
 
 // ---------------------------------------------------------------- bulk
 
-// Value streamed out of a boundary source (Eq. LBE_mod).  f-hat is the mean
-// of the stored (A) and reset (B) populations of the source; the
-// equilibrium is taken from f-hat (mode 0) or from f(x_k, t) (mode 1).
-// alpha is the direction of travel (1..4), opp its reverse.
-template <typename T>
-__device__ inline T stream_from_boundary(const T* __restrict__ fa, const T* __restrict__ fb, size_t plane,
-                                         int alpha, int opp, const KC<T>& k, int set, int mode) {
-    T a5[5], h5[5];
-#pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        a5[q] = ld(fa + q * plane);
-        h5[q] = mul_rn((T)0.5, add_rn(a5[q], ld(fb + q * plane)));
-    }
-    if (mode == 0) {
-        T sh = sum5(h5[0], h5[1], h5[2], h5[3], h5[4]);
-        return fma_rn(k.two_a[set], sh, -h5[opp]);  // 2 f_eq(f-hat) - f-hat = 2 a s-hat - f-hat^opp
-    }
-    T sa = sum5(a5[0], a5[1], a5[2], a5[3], a5[4]);
-    T ej = sub_rn(a5[alpha], a5[opp]);              // e_alpha . Jbar(x_k, t)
-    return sub_rn(add_rn(mul_rn(k.two_a[set], sa), ej), h5[alpha]);
-}
+// Bulk kernel: each warp owns a strip of kStripCols output columns and marches
+// along y over kRowsPerWarp rows.  Lane l holds column xs - 1 + l, so lanes 0
+// and 31 are halo lanes whose values reach their neighbours by shuffles; the
+// rows above and below stay in registers, and the populations are prefetched
+// two rows ahead.  Every lattice point's 14 words are read once per launch
+// (plus the two halo columns and two halo rows of each strip).
+constexpr int kStripCols = 30;
+constexpr int kWarpsPerBlock = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(256) bulk_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
-                                                   unsigned* flag) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int j = blockIdx.y * blockDim.y + threadIdx.y;
-    bool active = i < g.nx && j < g.ny && !is_boundary(i, j, g);
-    bool bad = false;
-    if (active) {
-        int iw = wrap(i - 1, g.nx), ie = wrap(i + 1, g.nx), js = wrap(j - 1, g.ny), jn = wrap(j + 1, g.ny);
-        size_t p = (size_t)j * g.px + i;
-        size_t pw = (size_t)j * g.px + iw, pe = (size_t)j * g.px + ie;
-        size_t ps = (size_t)js * g.px + i, pn = (size_t)jn * g.px + i;
-        bool bw = is_boundary(iw, j, g), be = is_boundary(ie, j, g);
-        bool bs = is_boundary(i, js, g), bnb = is_boundary(i, jn, g);
-        T sW[2], sE[2], sS[2], sN[2];
-        T out[2][5];
+__device__ __forceinline__ void load_row(const T* __restrict__ F, size_t plane, size_t p, bool ok, T (&f)[2][5]) {
 #pragma unroll
-        for (int set = 0; set < 2; ++set) {
-            const T* F = A.f + (size_t)set * 5 * g.plane;
-            const T* FB = B.f + (size_t)set * 5 * g.plane;
-            const size_t P = g.plane;
-            // rest population: 2 a0 s - f0 = f0 + (2 a0 m - 8 a f0), m = moving sum
-            T f0 = ld(F + p);
-            T m = add_rn(add_rn(ld(F + P + p), ld(F + 2 * P + p)), add_rn(ld(F + 3 * P + p), ld(F + 4 * P + p)));
-            out[set][0] = add_rn(f0, fma_rn(k.two_a0[set], m, -mul_rn(k.eight_a[set], f0)));
-            // moving populations: f^alpha(x) = 2 a s(x - e_alpha) - f^opp(x - e_alpha)
-            sW[set] = moment0(A.f, P, pw, set);
-            sE[set] = moment0(A.f, P, pe, set);
-            sS[set] = moment0(A.f, P, ps, set);
-            sN[set] = moment0(A.f, P, pn, set);
-            out[set][1] = bw ? stream_from_boundary(F + pw, FB + pw, P, 1, 3, k, set, c.bc_feq_mode)
-                             : fma_rn(k.two_a[set], sW[set], -ld(F + 3 * P + pw));
-            out[set][3] = be ? stream_from_boundary(F + pe, FB + pe, P, 3, 1, k, set, c.bc_feq_mode)
-                             : fma_rn(k.two_a[set], sE[set], -ld(F + P + pe));
-            out[set][2] = bs ? stream_from_boundary(F + ps, FB + ps, P, 2, 4, k, set, c.bc_feq_mode)
-                             : fma_rn(k.two_a[set], sS[set], -ld(F + 4 * P + ps));
-            out[set][4] = bnb ? stream_from_boundary(F + pn, FB + pn, P, 4, 2, k, set, c.bc_feq_mode)
-                              : fma_rn(k.two_a[set], sN[set], -ld(F + 2 * P + pn));
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) f[s][q] = ok ? ld(F + (size_t)(s * 5 + q) * plane + p) : (T)0;
+}
+
+__device__ __forceinline__ void load_uv(const double* __restrict__ U, size_t plane, size_t p, bool ok,
+                                        double (&u)[4]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[q] = ok ? ld(U + (size_t)q * plane + p) : 0.0;
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
+                                                   const T* __restrict__ edge, int nb, unsigned* flag,
+                                                   int rows_per_warp) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int xs = warp * kStripCols;
+    if (xs >= g.nx) return;  // whole warp
+    const int xl = xs - 1 + lane;
+    const bool col_ok = g.periodic_x ? (xl <= g.nx) : (xl >= 0 && xl < g.nx);
+    const int col = col_ok ? wrap(xl, g.nx) : 0;
+    const bool out_lane = lane >= 1 && lane <= kStripCols && xl < g.nx &&
+                          (g.periodic_x || (xl > 0 && xl < g.nx - 1));
+    const bool bsrc_w = !g.periodic_x && xl == 1;           // west source on the boundary
+    const bool bsrc_e = !g.periodic_x && xl == g.nx - 2;    // east source on the boundary
+    const int j0 = blockIdx.y * rows_per_warp;
+    const int j1 = min(j0 + rows_per_warp, g.ny);
+    const size_t P = g.plane;
+
+    auto row_ok = [&](int j) { return g.periodic_y || (j >= 0 && j < g.ny); };
+    auto row_of = [&](int j) { return g.periodic_y ? wrap(j, g.ny) : j; };
+    // Offsets are formed only for rows inside the lattice (rows outside are
+    // clamped; their loads are masked), so no address ever leaves the planes
+    // even where a masked load is issued unconditionally.
+    auto at = [&](int j) { return (size_t)min(max(row_of(j), 0), g.ny - 1) * (size_t)g.px + (size_t)col; };
+
+    T Ps[2], Pf4[2];                          // row j - 1: moment and f^4
+    T Cf[2][5], Cs[2], Cm[2];                 // row j
+    T Nf[2][5];                               // row j + 1
+    T Qf[2][5];                               // row j + 2 (in flight)
+    double Cu[4], Nu[4];
+    {
+        T t[2][5];
+        load_row(A.f, P, at(j0 - 1), col_ok && row_ok(j0 - 1), t);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            Ps[s] = sum5(t[s][0], t[s][1], t[s][2], t[s][3], t[s][4]);
+            Pf4[s] = t[s][4];
         }
-        double ax, ay;
-        accel_interior<T>(sW[0], sE[0], sS[0], sN[0], sW[1], sE[1], sS[1], sN[1], k, ax, ay);
-        double ux1, uy1, vx1, vy1;
-        newmark(ld(A.u + p), ld(A.u + 2 * g.plane + p), ax, c, ux1, vx1);
-        newmark(ld(A.u + g.plane + p), ld(A.u + 3 * g.plane + p), ay, c, uy1, vy1);
-#pragma unroll
-        for (int set = 0; set < 2; ++set)
-#pragma unroll
-            for (int q = 0; q < 5; ++q) B.f[((size_t)set * 5 + q) * g.plane + p] = out[set][q];
-        B.u[p] = ux1;
-        B.u[g.plane + p] = uy1;
-        B.u[2 * g.plane + p] = vx1;
-        B.u[3 * g.plane + p] = vy1;
-        bad = !isfinite(out[0][0] + out[1][0]);
     }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+    load_row(A.f, P, at(j0), col_ok, Cf);
+    load_row(A.f, P, at(j0 + 1), col_ok && row_ok(j0 + 1), Nf);
+    load_uv(A.u, P, at(j0), out_lane, Cu);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        Cm[s] = add_rn(add_rn(Cf[s][1], Cf[s][2]), add_rn(Cf[s][3], Cf[s][4]));
+        Cs[s] = add_rn(Cf[s][0], Cm[s]);
+    }
+    bool bad = false;
+    for (int j = j0; j < j1; ++j) {
+        // prefetch: populations two rows ahead, u and du/dt one row ahead
+        load_row(A.f, P, at(j + 2), col_ok && row_ok(j + 2) && j + 2 <= j1, Qf);
+        load_uv(A.u, P, at(j + 1), out_lane && j + 1 < j1, Nu);
+        T Nm[2], Ns[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            Nm[s] = add_rn(add_rn(Nf[s][1], Nf[s][2]), add_rn(Nf[s][3], Nf[s][4]));
+            Ns[s] = add_rn(Nf[s][0], Nm[s]);
+        }
+        const bool row_interior = g.periodic_y || (j > 0 && j < g.ny - 1);
+        if (row_interior) {  // warp-uniform
+            const bool bsrc_s = !g.periodic_y && j == 1;
+            const bool bsrc_n = !g.periodic_y && j == g.ny - 2;
+            T sW[2], sE[2], out[2][5];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                sW[s] = __shfl_up_sync(FULL, Cs[s], 1);
+                sE[s] = __shfl_down_sync(FULL, Cs[s], 1);
+                T f3W = __shfl_up_sync(FULL, Cf[s][3], 1);
+                T f1E = __shfl_down_sync(FULL, Cf[s][1], 1);
+                // rest population: 2 a0 s - f0 = f0 + (2 a0 m - 8 a f0)
+                out[s][0] = add_rn(Cf[s][0], fma_rn(k.two_a0[s], Cm[s], -mul_rn(k.eight_a[s], Cf[s][0])));
+                // moving populations: f^alpha(x) = 2 a s(x - e_alpha) - f^opp(x - e_alpha)
+                out[s][1] = fma_rn(k.two_a[s], sW[s], -f3W);
+                out[s][3] = fma_rn(k.two_a[s], sE[s], -f1E);
+                out[s][2] = fma_rn(k.two_a[s], Ps[s], -Pf4[s]);
+                out[s][4] = fma_rn(k.two_a[s], Ns[s], -Nf[s][2]);
+            }
+            if (out_lane) {
+                if (bsrc_w | bsrc_e | bsrc_s | bsrc_n) {
+                    // second-row points: boundary sources stream the value the boundary
+                    // kernel derived from their averaged state (Eq. LBE_mod)
+                    const int jr = row_of(j);
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const T* e = edge + (size_t)s * nb;
+                        if (bsrc_w) out[s][1] = ld(e + perim_index(col - 1, jr, g));
+                        if (bsrc_e) out[s][3] = ld(e + perim_index(col + 1, jr, g));
+                        if (bsrc_s) out[s][2] = ld(e + perim_index(col, jr - 1, g));
+                        if (bsrc_n) out[s][4] = ld(e + perim_index(col, jr + 1, g));
+                    }
+                }
+                double ax, ay;
+                accel_interior<T>(sW[0], sE[0], Ps[0], Ns[0], sW[1], sE[1], Ps[1], Ns[1], k, ax, ay);
+                double u1[4];
+                newmark(Cu[0], Cu[2], ax, c, u1[0], u1[2]);
+                newmark(Cu[1], Cu[3], ay, c, u1[1], u1[3]);
+                const size_t p = at(j);
+#pragma unroll
+                for (int s = 0; s < 2; ++s)
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) LBPS_ST(&B.f[(size_t)(s * 5 + q) * P + p], out[s][q]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) LBPS_ST(&B.u[(size_t)q * P + p], u1[q]);
+                bad |= !isfinite(out[0][0] + out[1][0]);
+            }
+        }
+        // shift the row window
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            Ps[s] = Cs[s];
+            Pf4[s] = Cf[s][4];
+            Cs[s] = Ns[s];
+            Cm[s] = Nm[s];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                Cf[s][q] = Nf[s][q];
+                Nf[s][q] = Qf[s][q];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) Cu[q] = Nu[q];
+    }
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(flag, 1u);
 }
 
 // ------------------------------------------------------------------ sync
@@ -423,6 +545,37 @@ dim3 grid2d(int nx, int ny, dim3 blk) { return dim3((nx + blk.x - 1) / blk.x, (n
 
 // ------------------------------------------------------------- launchers
 
+cudaError_t set_check_range(const void* base, size_t bytes, cudaStream_t st) {
+#ifdef LBPS_CHECKED
+    const char* lo = static_cast<const char*>(base);
+    const char* hi = lo + bytes;
+    unsigned long long zero = 0;
+    cudaError_t e = cudaMemcpyToSymbolAsync(g_chk_lo, &lo, sizeof(lo), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_chk_hi, &hi, sizeof(hi), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_chk_line, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_chk_addr, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+#else
+    (void)base;
+    (void)bytes;
+    (void)st;
+    return cudaSuccess;
+#endif
+}
+
+int check_report(unsigned long long out[2]) {
+#ifdef LBPS_CHECKED
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(&out[0], g_chk_line, sizeof(out[0])) != cudaSuccess) return -1;
+    if (cudaMemcpyFromSymbol(&out[1], g_chk_addr, sizeof(out[1])) != cudaSuccess) return -1;
+    return 1;
+#else
+    out[0] = out[1] = 0;
+    return 0;
+#endif
+}
+
 template <typename T>
 cudaError_t launch_init(const Geo& g, const Consts& c, const KC<T>&, View<T> A, const double*, const double*,
                         const double*, const double*, cudaStream_t st) {
@@ -433,16 +586,23 @@ cudaError_t launch_init(const Geo& g, const Consts& c, const KC<T>&, View<T> A, 
 
 template <typename T>
 cudaError_t launch_boundary(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, const BNode* bn,
-                            int nb, unsigned* flag, cudaStream_t st) {
-    if (nb > 0) boundary_kernel<T><<<(nb + 127) / 128, 128, 0, st>>>(g, c, k, A, B, bn, nb, flag);
+                            int nb, T* edge, unsigned* flag, cudaStream_t st) {
+    if (nb > 0) boundary_kernel<T><<<(nb + 127) / 128, 128, 0, st>>>(g, c, k, A, B, bn, nb, edge, flag);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, unsigned* flag,
-                        cudaStream_t st) {
-    dim3 blk(32, 8);
-    bulk_kernel<T><<<grid2d(g.nx, g.ny, blk), blk, 0, st>>>(g, c, k, A, B, flag);
+cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, const T* edge, int nb,
+                        unsigned* flag, cudaStream_t st, const Tuning& tu) {
+    int warps = (g.nx + kStripCols - 1) / kStripCols;
+    dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, (g.ny + tu.rows_per_warp - 1) / tu.rows_per_warp);
+    dim3 blk(32 * kWarpsPerBlock);
+    switch (tu.variant) {
+    case 0: bulk_kernel<T, 6><<<grid, blk, 0, st>>>(g, c, k, A, B, edge, nb, flag, tu.rows_per_warp); break;
+    case 1: bulk_kernel<T, 5><<<grid, blk, 0, st>>>(g, c, k, A, B, edge, nb, flag, tu.rows_per_warp); break;
+    case 2: bulk_kernel<T, 4><<<grid, blk, 0, st>>>(g, c, k, A, B, edge, nb, flag, tu.rows_per_warp); break;
+    default: bulk_kernel<T, 8><<<grid, blk, 0, st>>>(g, c, k, A, B, edge, nb, flag, tu.rows_per_warp); break;
+    }
     return cudaGetLastError();
 }
 
@@ -481,9 +641,9 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, co
     template cudaError_t launch_init<T>(const Geo&, const Consts&, const KC<T>&, View<T>, const double*,      \
                                         const double*, const double*, const double*, cudaStream_t);          \
     template cudaError_t launch_boundary<T>(const Geo&, const Consts&, const KC<T>&, View<T>, View<T>,        \
-                                            const BNode*, int, unsigned*, cudaStream_t);                      \
-    template cudaError_t launch_bulk<T>(const Geo&, const Consts&, const KC<T>&, View<T>, View<T>, unsigned*, \
-                                        cudaStream_t);                                                        \
+                                            const BNode*, int, T*, unsigned*, cudaStream_t);                  \
+    template cudaError_t launch_bulk<T>(const Geo&, const Consts&, const KC<T>&, View<T>, View<T>, const T*,  \
+                                        int, unsigned*, cudaStream_t, const Tuning&);                         \
     template cudaError_t launch_sync<T>(const Geo&, const Consts&, const KC<T>&, View<T>, cudaStream_t);     \
     template cudaError_t launch_extract<T>(const Geo&, const Consts&, View<T>, int, double*, cudaStream_t);  \
     template cudaError_t launch_extract_rows<T>(const Geo&, const Consts&, View<T>, int, int, int, double*,   \

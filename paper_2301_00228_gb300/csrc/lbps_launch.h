@@ -11,12 +11,22 @@ cudaError_t launch_init(const Geo& g, const Consts& c, const KC<T>& k, View<T> A
 
 // One time step A (time t) -> B (time t + dt) is launch_boundary followed by
 // launch_bulk on the same stream.
+// edge[set * nb + b]: value boundary point b streams into its interior
+// neighbour (written by launch_boundary, read by launch_bulk).
 template <typename T>
 cudaError_t launch_boundary(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B,
-                            const BNode* bn, int nb, unsigned* flag, cudaStream_t st);
+                            const BNode* bn, int nb, T* edge, unsigned* flag, cudaStream_t st);
+// Launch shape of the bulk kernel: variant selects the register budget (0: 6
+// blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8), rows_per_warp the height of
+// the strip each warp marches over.  Results do not depend on either.
+struct Tuning {
+    int variant = 0;
+    int rows_per_warp = 32;
+};
+constexpr int kTuningVariants = 4;
 template <typename T>
-cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, unsigned* flag,
-                        cudaStream_t st);
+cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, const T* edge, int nb,
+                        unsigned* flag, cudaStream_t st, const Tuning& tu);
 
 template <typename T>
 cudaError_t launch_sync(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, cudaStream_t st);
@@ -36,5 +46,11 @@ constexpr int kNormBlocks = 1024;
 template <typename T>
 cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, const double* ref,
                          double* partials, double* out4, cudaStream_t st);
+
+// Checked builds (LBPS_CHECKED): the device block every kernel access must
+// stay inside, and the first violation seen (source line, address); both are
+// no-ops returning 0 in normal builds.
+cudaError_t set_check_range(const void* base, size_t bytes, cudaStream_t st);
+int check_report(unsigned long long out[2]);
 
 }  // namespace lbps

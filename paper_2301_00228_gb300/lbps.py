@@ -11,11 +11,14 @@ lattice state lives in a torch uint8 tensor) and the CUDA stream.
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 import numpy as np
 
-_LIB_PATH = Path(__file__).resolve().parent / "liblbps.so"
+# LBPS_CHECKED=1 selects the range-checked build (liblbps_checked.so).
+_LIB_PATH = Path(__file__).resolve().parent / (
+    "liblbps_checked.so" if os.environ.get("LBPS_CHECKED") == "1" else "liblbps.so")
 
 LBPS_OK = 0
 LBPS_ERR_INVALID = -1
@@ -43,9 +46,13 @@ class lbps_params(ctypes.Structure):
 
 
 class LbpsError(RuntimeError):
-    def __init__(self, code, what=""):
+    def __init__(self, code, what="", cuda_code=0):
         self.code = code
-        super().__init__(f"{what}: {lbps_strerror(code)} ({code})" if what else lbps_strerror(code))
+        self.cuda_code = cuda_code
+        msg = f"{lbps_strerror(code)} ({code})"
+        if cuda_code:
+            msg += f", cudaError {cuda_code}"
+        super().__init__(f"{what}: {msg}" if what else msg)
 
 
 def _load():
@@ -69,6 +76,9 @@ def _load():
         "lbps_read_device": (ctypes.c_int, [vp, i32, vp, sz]),
         "lbps_norms": (ctypes.c_int, [vp, i32, vp, vp]),
         "lbps_info": (ctypes.c_int, [vp, vp, P(i64)]),
+        "lbps_check_report": (ctypes.c_int, [vp]),
+        "lbps_last_cuda_error": (ctypes.c_int, [vp]),
+        "lbps_set_tuning": (ctypes.c_int, [vp, i32, i32]),
         "lbps_profile": (ctypes.c_int, [vp, i32]),
         "lbps_profile_read": (ctypes.c_int, [vp, vp]),
         "lbps_set_stream": (ctypes.c_int, [vp, vp]),
@@ -171,6 +181,18 @@ def lbps_info(h):
     return out, int(steps.value)
 
 
+def lbps_check_report():
+    out = np.zeros(2, np.uint64)
+    rc = _lib.lbps_check_report(_p(out))
+    if rc < 0:
+        raise LbpsError(rc, "lbps_check_report")
+    return rc, int(out[0]), int(out[1])
+
+
+def lbps_set_tuning(h, variant, rows_per_warp):
+    _check(_lib.lbps_set_tuning(h, int(variant), int(rows_per_warp)), "lbps_set_tuning")
+
+
 def lbps_profile(h, enable):
     _check(_lib.lbps_profile(h, int(bool(enable))), "lbps_profile")
 
@@ -247,13 +269,13 @@ class Lattice:
     def step(self, n=1):
         rc = lbps_step(self._h, n)
         if rc != LBPS_OK:
-            raise LbpsError(rc, "lbps_step")
+            raise LbpsError(rc, "lbps_step", _lib.lbps_last_cuda_error(self._h))
         return self
 
     def step_async(self, n=1):
         rc = lbps_step_async(self._h, n)
         if rc != LBPS_OK:
-            raise LbpsError(rc, "lbps_step_async")
+            raise LbpsError(rc, "lbps_step_async", _lib.lbps_last_cuda_error(self._h))
         return self
 
     def check(self):

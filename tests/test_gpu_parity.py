@@ -376,3 +376,26 @@ def test_two_streams_independent(L):
     fa, fb = a.fields(), b.fields()
     for k in solo1:
         assert np.array_equal(fa[k], solo1[k]) and np.array_equal(fb[k], solo2[k]), k
+
+
+def test_tunings_bit_identical(L):
+    """Every launch shape of the interior kernel gives the same bits (ragged strip
+    and row counts included)."""
+    cs = mixed_case(21, 97, 83, steps=40)
+    ref = None
+    for variant in range(4):
+        for rows in (1, 7, 64, 4096):
+            lat = L.Lattice.rectangle(cs["nx"], cs["ny"], cs["lam"], 1.0, cs["et"], cs["ev"], a0_phi=cs["a0"],
+                                      storage="f32")
+            L.lbps_set_tuning(lat._h, variant, rows)
+            f = lat.init(cs["ux"], cs["uy"]).step(cs["steps"]).fields()
+            lat.close()
+            if ref is None:
+                ref = f
+                assert_parity(f, run_oracle(cs), TOL["f32"])
+            for k in f:
+                assert np.array_equal(f[k], ref[k]), (variant, rows, k)
+    small = L.Lattice(8, 8, 1.0, 1.0, periodic_x=True, periodic_y=True)
+    for bad in ((4, 64), (-1, 64), (0, 0), (0, 5000)):
+        with pytest.raises(L.LbpsError):
+            L.lbps_set_tuning(small._h, *bad)
