@@ -157,6 +157,30 @@ int lbps_read_device(lbps_lattice* lat, int32_t field, double* d_dst, size_t cou
  * NULL (ref = 0).  Deterministic order.  Synchronises. */
 int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out[4]);
 
+/* lbps_norms without any allocation.  The paper has no counterpart: this is
+ * a service routine for callers that cannot call cudaMalloc or cudaFree,
+ * such as a serving loop that keeps all device memory in its own pool under a
+ * fixed budget (an allocation behind its back breaks that accounting or
+ * fails), or a latency-sensitive loop that must not stall on cudaFree, which
+ * waits for the device.
+ * Computes out[0] = sum (x - ref)^2, out[1] = sum ref^2, out[2] = sum x,
+ * out[3] = max |x| over d_x[0..n) and d_ref[0..n) (device FP64 arrays the
+ * caller owns; d_ref may be NULL for ref = 0), on cuda_stream (NULL = legacy
+ * default stream), then waits for that stream and writes out (host).
+ * Scratch: a fixed device array inside the library (2 MiB + 32 B per device
+ * that loads it, held until the process exits), so n may be at most
+ * LBPS_NOALLOC_MAX_POINTS; larger n returns LBPS_ERR_INVALID before any
+ * device work.  The first call on a device looks up the array's address with
+ * that device current; make that first call before any stream capture.  All
+ * calls on a device share the array: calls whose work overlaps on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * Each call overwrites every scratch slot it reads, so nothing in it needs
+ * clearing between calls.  Calls no cudaMalloc, cudaFree or other allocating
+ * routine. */
+#define LBPS_NOALLOC_MAX_BLOCKS 65536
+#define LBPS_NOALLOC_MAX_POINTS ((size_t)LBPS_NOALLOC_MAX_BLOCKS * 4096)
+int lbps_norms_noalloc(const double* d_x, const double* d_ref, size_t n, void* cuda_stream, double out[4]);
+
 /* Derived constants (Eq. conditions-parameters): out[0] c_d, out[1] c_s,
  * out[2] a_phi, out[3] a_psi, out[4] a_{0,psi}, out[5] Delta t; and the
  * number of completed time steps. */

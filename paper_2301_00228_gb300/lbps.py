@@ -75,6 +75,7 @@ def _load():
         "lbps_read": (ctypes.c_int, [vp, i32, vp, sz]),
         "lbps_read_device": (ctypes.c_int, [vp, i32, vp, sz]),
         "lbps_norms": (ctypes.c_int, [vp, i32, vp, vp]),
+        "lbps_norms_noalloc": (ctypes.c_int, [vp, vp, sz, vp, vp]),
         "lbps_info": (ctypes.c_int, [vp, vp, P(i64)]),
         "lbps_check_report": (ctypes.c_int, [vp]),
         "lbps_last_cuda_error": (ctypes.c_int, [vp]),
@@ -171,6 +172,19 @@ def lbps_read_device(h, field, d_dst, count):
 def lbps_norms(h, field, d_ref=0):
     out = np.zeros(4, np.float64)
     _check(_lib.lbps_norms(h, int(field), ctypes.c_void_p(d_ref) if d_ref else None, _p(out)), "lbps_norms")
+    return out
+
+
+LBPS_NOALLOC_MAX_POINTS = 65536 * 4096
+
+
+def lbps_norms_noalloc(d_x, d_ref, n, stream_ptr=0):
+    """FP64 norms of caller-owned device arrays without any allocation (the
+    scratch is a fixed array inside the library; see include/lbps.h)."""
+    out = np.zeros(4, np.float64)
+    _check(_lib.lbps_norms_noalloc(ctypes.c_void_p(d_x), ctypes.c_void_p(d_ref) if d_ref else None, int(n),
+                                   ctypes.c_void_p(stream_ptr) if stream_ptr else None, _p(out)),
+           "lbps_norms_noalloc")
     return out
 
 
