@@ -225,6 +225,76 @@ def run_reference(args):
 
 # ------------------------------------------------------------------ GPU arm
 
+def run_batch(args):
+    """256 seeded rectangles (sides U{64..512}, random edges and lambda/mu), all
+    advanced as one batch; compared with stepping the same lattices one at a time."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2301_00228_gb300 import lbps
+    from paper_2301_00228_gb300 import workloads as W
+
+    ds = W.mixed_batch(count=args.batch_count)
+    lats = []
+    for d in ds:
+        lat = lbps.Lattice.rectangle(d.nx, d.ny, d.lam, d.mu, d.edge_type, np.asarray(d.edge_value, float).ravel(),
+                                     a0_phi=d.a0_phi, storage=args.storage)
+        lat.init(*d.displacement())
+        lats.append(lat)
+    points = sum(d.nx * d.ny for d in ds)
+    interior = sum((d.nx - 2) * (d.ny - 2) for d in ds)
+    b = lbps.Batch(lats)
+    variant, rows, tuned_ms = b.tune(repeats=5)
+    stream = torch.cuda.current_stream()
+    b.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    clock = clocks.stop()
+    if b.check() != 0:
+        raise SystemExit("state became non-finite")
+    seconds = e0.elapsed_time(e1) / 1000.0
+    value = points * args.steps / seconds / 1e9
+    # the same lattices stepped one at a time (same kernels, one lattice per launch)
+    loop_steps = max(2, args.steps // 10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for lat in lats:
+        lbps.lbps_step_async(lat._h, loop_steps)
+    torch.cuda.synchronize()
+    loop_s = time.perf_counter() - t0
+    loop_value = points * loop_steps / loop_s / 1e9
+    peak, peak_kind = measured_peaks()
+    step_s = seconds / args.steps
+    achieved = interior * BYTES_PER_UPDATE[args.storage] / step_s / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * step_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": f"mixed_batch_{len(ds)}", "domains": len(ds), "sides": "U{64..512}",
+                       "points": points, "storage": args.storage, "l2": "state larger than L2",
+                       "tuned": {"variant": variant, "rows_per_warp": rows, "ms_per_step": tuned_ms}},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "whole batched step",
+                         "peak_source": peak_kind},
+            "one_at_a_time": {"value": loop_value, "unit": UNIT, "steps": loop_steps,
+                              "speedup_of_batch": value / loop_value},
+            "gpu_launches": 2 * args.steps, "clocks": clock}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    for lat in lats:
+        lat.close()
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -365,7 +435,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="pulses", choices=["pulses", "waves", "square"])
+    ap.add_argument("--workload", default="pulses", choices=["pulses", "waves", "square", "batch"])
+    ap.add_argument("--batch-count", type=int, default=256, help="domains of the batch workload")
     ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
     ap.add_argument("--sync-every", type=int, default=0)
@@ -377,6 +448,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

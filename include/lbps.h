@@ -181,6 +181,48 @@ int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out
 #define LBPS_NOALLOC_MAX_POINTS ((size_t)LBPS_NOALLOC_MAX_BLOCKS * 4096)
 int lbps_norms_noalloc(const double* d_x, const double* d_ref, size_t n, void* cuda_stream, double out[4]);
 
+/* ---- Batches: many lattices of different sizes, materials and edges
+ * advanced together.  Each time step is one launch of the boundary kernel
+ * over the boundary points of every lattice and one launch of the interior
+ * kernel over a work list of strips of every lattice (the same per-point
+ * arithmetic as lbps_step, so every lattice gets the same bits as when
+ * stepped alone).  Pairs of steps are captured once into a CUDA graph and
+ * replayed.  The paper has no counterpart; this serves many solves at once. */
+typedef struct lbps_batch lbps_batch; /* opaque, library-owned */
+
+/* lats[count]: distinct, initialised lattices, all FP32 or all FP64, with
+ * sync_every == 0.  The batch keeps the pointers (not the lattices): destroy
+ * the batch before any of its lattices.  cuda_stream: stream for the batch's
+ * work (NULL: a blocking stream of the batch's own, ordered with the legacy
+ * default stream).  Allocates a small device block for descriptors and work
+ * lists (cudaMalloc). */
+int lbps_batch_create(lbps_lattice* const* lats, int32_t count, void* cuda_stream, lbps_batch** out);
+
+/* Advance every lattice of the batch by n steps (asynchronous; the work is
+ * ordered after work queued on each lattice's stream, and later work on those
+ * streams is ordered after it).  A lattice stepped on its own meanwhile is
+ * picked up where it is. */
+int lbps_batch_step(lbps_batch* b, int64_t n);
+
+/* Waits; LBPS_ERR_NONFINITE if any lattice of the batch went non-finite. */
+int lbps_batch_check(lbps_batch* b);
+
+/* Launch shape of the batch's interior kernel (as lbps_set_tuning;
+ * rows_per_warp 8..4096).  Results do not depend on it. */
+int lbps_batch_set_tuning(lbps_batch* b, int32_t variant, int32_t rows_per_warp);
+
+/* Autotuner: times one step for each launch shape (variants 0..2 x rows
+ * 8, 16, 32, 64, 128), repeats times each, keeps the fastest and reports
+ * it.  Leaves every lattice's state unchanged (a step is a pure function of
+ * the copy it reads; the timed steps only rewrite the same next state). */
+int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* rows_per_warp,
+                    double* ms_per_step);
+
+/* cudaError_t of the batch's last failing CUDA call (0 if none). */
+int lbps_batch_last_cuda_error(const lbps_batch* b);
+
+void lbps_batch_destroy(lbps_batch* b);
+
 /* Derived constants (Eq. conditions-parameters): out[0] c_d, out[1] c_s,
  * out[2] a_phi, out[3] a_psi, out[4] a_{0,psi}, out[5] Delta t; and the
  * number of completed time steps. */

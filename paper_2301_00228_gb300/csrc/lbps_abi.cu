@@ -8,11 +8,13 @@
 
 #include "lbps.h"
 #include "lbps_launch.h"
+#include "lbps_state.h"
 
 using lbps::BNode;
 using lbps::Consts;
 using lbps::Geo;
 using lbps::KC;
+using lbps::Layout;
 using lbps::View;
 
 namespace {
@@ -22,18 +24,7 @@ constexpr size_t kStagingMax = size_t(8) << 20;  // host read/write staging, byt
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-struct Layout {
-    Geo g;
-    size_t elem;        // bytes per population value
-    size_t f_bytes;     // 10 population planes, aligned
-    size_t u_bytes;     // 4 FP64 planes, aligned
-    size_t copy_bytes;
-    size_t off_copy[2];
-    size_t off_bn, off_edge, off_part, off_out, off_flag, off_staging;
-    size_t staging_bytes;
-    size_t total;
-    int nb;
-};
+
 
 bool finite_positive(double x) { return std::isfinite(x) && x > 0.0; }
 
@@ -106,43 +97,7 @@ KC<T> make_kc(double a_phi, double a_psi, double cd2, double cs2, double dh) {
 
 }  // namespace
 
-struct lbps_lattice {
-    lbps_params p;
-    Layout L;
-    Consts c;
-    KC<float> kf;
-    KC<double> kd;
-    double cd, cs, a_phi, a_psi, a0_psi;
-    cudaStream_t st;
-    char* mem;
-    bool owns;
-    int cur;            // copy holding time t
-    lbps::Tuning tuning;  // bulk-kernel launch shape
-    int last_cuda = 0;    // cudaError_t of the last failing CUDA call
-    int64_t steps;
-    bool initialised;
-    // per-kernel event timing (lbps_profile)
-    bool prof = false;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-    std::vector<int> ev_kind;   // per recorded pair: 0 bulk, 1 boundary
 
-    template <typename T>
-    View<T> view(int q) const {
-        View<T> v;
-        v.f = reinterpret_cast<T*>(mem + L.off_copy[q]);
-        v.u = reinterpret_cast<double*>(mem + L.off_copy[q] + L.f_bytes);
-        return v;
-    }
-    const BNode* bn() const { return reinterpret_cast<const BNode*>(mem + L.off_bn); }
-    template <typename T>
-    T* edge() const { return reinterpret_cast<T*>(mem + L.off_edge); }
-    unsigned* flag() const { return reinterpret_cast<unsigned*>(mem + L.off_flag); }
-    double* partials() const { return reinterpret_cast<double*>(mem + L.off_part); }
-    double* out4() const { return reinterpret_cast<double*>(mem + L.off_out); }
-    double* staging() const { return reinterpret_cast<double*>(mem + L.off_staging); }
-    bool f64() const { return p.storage == LBPS_STORAGE_F64; }
-};
 
 namespace {
 

@@ -1,0 +1,342 @@
+// Batches of lattices (lbps_batch_* in include/lbps.h): every lattice of a
+// batch advances by one launch of the boundary kernel and one launch of the
+// interior kernel per time step, driven by device-side work lists; pairs of
+// steps are captured once in a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbps.h"
+#include "lbps_launch.h"
+#include "lbps_state.h"
+
+using lbps::BndTask;
+using lbps::BulkTask;
+using lbps::DomDesc;
+
+struct lbps_batch {
+    std::vector<lbps_lattice*> lats;
+    bool f64 = false;
+    cudaStream_t st = nullptr;    // stream the graph runs on
+    bool own_stream = false;
+    char* mem = nullptr;          // descriptors | boundary tasks | bulk tasks
+    size_t mem_bytes = 0;
+    size_t off_bnd = 0, off_bulk = 0;
+    int nbnd = 0, nbulk = 0;
+    int variant = 0, rows = 32;
+    std::vector<int> uploaded_cur;
+    cudaGraphExec_t graph = nullptr;
+    cudaEvent_t order = nullptr;  // orders the batch stream with the lattices' streams
+    int last_cuda = 0;
+};
+
+namespace {
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+template <typename T>
+DomDesc<T> make_desc(const lbps_lattice* lat) {
+    DomDesc<T> d;
+    d.g = lat->L.g;
+    d.c = lat->c;
+    if constexpr (sizeof(T) == 8)
+        d.k = lat->kd;
+    else
+        d.k = lat->kf;
+    d.v[0] = lat->view<T>(0);
+    d.v[1] = lat->view<T>(1);
+    d.bn = lat->bn();
+    d.edge = lat->edge<T>();
+    d.flag = lat->flag();
+    d.nb = lat->L.nb;
+    d.cur = lat->cur;
+    return d;
+}
+
+size_t desc_bytes(const lbps_batch* b) {
+    return b->f64 ? sizeof(DomDesc<double>) : sizeof(DomDesc<float>);
+}
+
+std::vector<BulkTask> bulk_tasks(const lbps_batch* b, int rows) {
+    std::vector<BulkTask> t;
+    for (int d = 0; d < (int)b->lats.size(); ++d) {
+        const lbps::Geo& g = b->lats[d]->L.g;
+        for (int xs = 0; xs < g.nx; xs += lbps::kBatchStripCols)
+            for (int j0 = 0; j0 < g.ny; j0 += rows) t.push_back(BulkTask{d, xs, j0, std::min(j0 + rows, g.ny)});
+    }
+    return t;
+}
+
+int fail(lbps_batch* b, cudaError_t e) {
+    b->last_cuda = (int)e;
+    return LBPS_ERR_CUDA;
+}
+
+// (Re)builds the bulk work list for b->rows and the descriptors, in a device
+// block sized for the largest work list the tuner may ask for.
+int upload(lbps_batch* b) {
+    std::vector<BulkTask> bt = bulk_tasks(b, b->rows);
+    std::vector<BndTask> nt;
+    for (int d = 0; d < (int)b->lats.size(); ++d)
+        for (int q = 0; q < b->lats[d]->L.nb; ++q) nt.push_back(BndTask{d, q});
+    std::vector<char> host(b->off_bnd + nt.size() * sizeof(BndTask));
+    size_t db = desc_bytes(b);
+    for (int d = 0; d < (int)b->lats.size(); ++d) {
+        if (b->f64) {
+            DomDesc<double> x = make_desc<double>(b->lats[d]);
+            std::memcpy(host.data() + d * db, &x, db);
+        } else {
+            DomDesc<float> x = make_desc<float>(b->lats[d]);
+            std::memcpy(host.data() + d * db, &x, db);
+        }
+        b->uploaded_cur[d] = b->lats[d]->cur;
+    }
+    std::memcpy(host.data() + b->off_bnd, nt.data(), nt.size() * sizeof(BndTask));
+    cudaError_t e = cudaMemcpyAsync(b->mem, host.data(), host.size(), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->mem + b->off_bulk, bt.data(), bt.size() * sizeof(BulkTask), cudaMemcpyHostToDevice,
+                            b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return fail(b, e);
+    b->nbnd = (int)nt.size();
+    b->nbulk = (int)bt.size();
+    return LBPS_OK;
+}
+
+// One time step of every lattice: parity 0 reads v[cur], parity 1 v[cur ^ 1].
+cudaError_t launch_step(lbps_batch* b, int parity) {
+    cudaError_t e;
+    if (b->f64) {
+        const DomDesc<double>* dd = reinterpret_cast<const DomDesc<double>*>(b->mem);
+        e = lbps::launch_boundary_batch<double>(dd, reinterpret_cast<const BndTask*>(b->mem + b->off_bnd), b->nbnd,
+                                                parity, b->st);
+        if (e == cudaSuccess)
+            e = lbps::launch_bulk_batch<double>(dd, reinterpret_cast<const BulkTask*>(b->mem + b->off_bulk), b->nbulk,
+                                                parity, b->variant, b->st);
+    } else {
+        const DomDesc<float>* dd = reinterpret_cast<const DomDesc<float>*>(b->mem);
+        e = lbps::launch_boundary_batch<float>(dd, reinterpret_cast<const BndTask*>(b->mem + b->off_bnd), b->nbnd,
+                                               parity, b->st);
+        if (e == cudaSuccess)
+            e = lbps::launch_bulk_batch<float>(dd, reinterpret_cast<const BulkTask*>(b->mem + b->off_bulk), b->nbulk,
+                                               parity, b->variant, b->st);
+    }
+    return e;
+}
+
+void drop_graph(lbps_batch* b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+// Captures two steps (parity 0 then 1) as one graph.
+int capture(lbps_batch* b) {
+    drop_graph(b);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(b, e);
+    cudaError_t e1 = launch_step(b, 0);
+    if (e1 == cudaSuccess) e1 = launch_step(b, 1);
+    e = cudaStreamEndCapture(b->st, &g);
+    if (e1 != cudaSuccess) e = e1;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return fail(b, e);
+    }
+    return LBPS_OK;
+}
+
+// Refreshes the descriptors if any lattice was stepped on its own since the
+// last upload (its current copy moved).
+int refresh(lbps_batch* b) {
+    for (size_t d = 0; d < b->lats.size(); ++d)
+        if (b->lats[d]->cur != b->uploaded_cur[d]) return upload(b);
+    return LBPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbps_batch_create(lbps_lattice* const* lats, int32_t count, void* cuda_stream, lbps_batch** out) {
+    if (!out || !lats || count < 1) return LBPS_ERR_INVALID;
+    *out = nullptr;
+    bool f64 = lats[0] && lats[0]->f64();
+    for (int32_t d = 0; d < count; ++d) {
+        const lbps_lattice* l = lats[d];
+        if (!l) return LBPS_ERR_INVALID;
+        if (!l->initialised) return LBPS_ERR_STATE;
+        if (l->f64() != f64 || l->p.sync_every != 0) return LBPS_ERR_INVALID;
+        for (int32_t q = 0; q < d; ++q)
+            if (lats[q] == l) return LBPS_ERR_INVALID;
+    }
+    lbps_batch* b = new (std::nothrow) lbps_batch();
+    if (!b) return LBPS_ERR_OOM;
+    b->lats.assign(lats, lats + count);
+    b->uploaded_cur.assign(count, -1);
+    b->f64 = f64;
+    if (cuda_stream) {
+        b->st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    } else {
+        // The legacy default stream cannot be captured; a blocking stream of
+        // our own stays ordered with it.
+        if (cudaStreamCreate(&b->st) != cudaSuccess) {
+            delete b;
+            return LBPS_ERR_CUDA;
+        }
+        b->own_stream = true;
+    }
+    if (cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming) != cudaSuccess) {
+        lbps_batch_destroy(b);
+        return LBPS_ERR_CUDA;
+    }
+    // Work lists: the bulk list is largest for the smallest tile height the
+    // tuner tries (8 rows).
+    size_t max_bulk = bulk_tasks(b, 8).size();
+    size_t nbnd = 0;
+    for (auto* l : b->lats) nbnd += (size_t)l->L.nb;
+    b->off_bnd = align256((size_t)count * desc_bytes(b));
+    b->off_bulk = align256(b->off_bnd + nbnd * sizeof(BndTask));
+    b->mem_bytes = b->off_bulk + std::max<size_t>(max_bulk, 1) * sizeof(BulkTask);
+    if (cudaMalloc(&b->mem, b->mem_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        lbps_batch_destroy(b);
+        return LBPS_ERR_OOM;
+    }
+    int rc = upload(b);
+    if (rc != LBPS_OK) {
+        lbps_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBPS_OK;
+}
+
+int lbps_batch_set_tuning(lbps_batch* b, int32_t variant, int32_t rows_per_warp) {
+    if (!b || variant < 0 || variant >= lbps::kTuningVariants || rows_per_warp < 8 || rows_per_warp > 4096)
+        return LBPS_ERR_INVALID;
+    b->variant = variant;
+    b->rows = rows_per_warp;
+    drop_graph(b);
+    return upload(b);
+}
+
+int lbps_batch_step(lbps_batch* b, int64_t n) {
+    if (!b || n < 0) return LBPS_ERR_INVALID;
+    if (n == 0) return LBPS_OK;
+    // start after the work already queued on the lattices' own streams
+    for (auto* l : b->lats) {
+        if (l->st == b->st) continue;
+        cudaError_t e = cudaEventRecord(b->order, l->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->order, 0);
+        if (e != cudaSuccess) return fail(b, e);
+    }
+    int rc = refresh(b);
+    if (rc != LBPS_OK) return rc;
+    if (n >= 2 && !b->graph) {
+        rc = capture(b);
+        if (rc != LBPS_OK) return rc;
+    }
+    for (int64_t q = 0; q + 1 < n; q += 2) {
+        cudaError_t e = cudaGraphLaunch(b->graph, b->st);
+        if (e != cudaSuccess) return fail(b, e);
+    }
+    if (n & 1) {
+        cudaError_t e = launch_step(b, 0);
+        if (e != cudaSuccess) return fail(b, e);
+    }
+    // later work on the lattices' own streams starts after these steps
+    cudaError_t e = cudaEventRecord(b->order, b->st);
+    for (auto* l : b->lats)
+        if (e == cudaSuccess && l->st != b->st) e = cudaStreamWaitEvent(l->st, b->order, 0);
+    if (e != cudaSuccess) return fail(b, e);
+    for (auto* l : b->lats) {
+        l->steps += n;
+        l->cur ^= (int)(n & 1);
+    }
+    return LBPS_OK;
+}
+
+int lbps_batch_check(lbps_batch* b) {
+    if (!b) return LBPS_ERR_INVALID;
+    std::vector<unsigned> flags(b->lats.size(), 0);
+    cudaError_t e = cudaSuccess;
+    for (size_t d = 0; d < b->lats.size() && e == cudaSuccess; ++d)
+        e = cudaMemcpyAsync(&flags[d], b->lats[d]->flag(), sizeof(unsigned), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return fail(b, e);
+    for (unsigned f : flags)
+        if (f) return LBPS_ERR_NONFINITE;
+    return LBPS_OK;
+}
+
+int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* rows_per_warp, double* ms_per_step) {
+    if (!b || repeats < 1) return LBPS_ERR_INVALID;
+    int rc = refresh(b);
+    if (rc != LBPS_OK) return rc;
+    const int rows_c[] = {8, 16, 32, 64, 128};
+    const int var_c[] = {0, 1, 2};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(b, cudaGetLastError());
+    float best = -1.0f;
+    int bv = b->variant, br = b->rows;
+    for (int r : rows_c) {
+        b->rows = r;
+        drop_graph(b);
+        rc = upload(b);
+        if (rc != LBPS_OK) break;
+        for (int v : var_c) {
+            b->variant = v;
+            // A step is a pure function of the copy it reads, so repeating the
+            // parity-0 step rewrites the same next state: timing it leaves the
+            // lattices where they were.
+            cudaError_t e = launch_step(b, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->st);
+            for (int q = 0; q < repeats && e == cudaSuccess; ++q) e = launch_step(b, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                rc = fail(b, e);
+                break;
+            }
+            ms /= repeats;
+            if (best < 0.0f || ms < best) {
+                best = ms;
+                bv = v;
+                br = r;
+            }
+        }
+        if (rc != LBPS_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LBPS_OK) return rc;
+    b->variant = bv;
+    b->rows = br;
+    drop_graph(b);
+    rc = upload(b);
+    if (rc != LBPS_OK) return rc;
+    if (variant) *variant = bv;
+    if (rows_per_warp) *rows_per_warp = br;
+    if (ms_per_step) *ms_per_step = best;
+    return LBPS_OK;
+}
+
+int lbps_batch_last_cuda_error(const lbps_batch* b) { return b ? b->last_cuda : 0; }
+
+void lbps_batch_destroy(lbps_batch* b) {
+    if (!b) return;
+    if (b->st) cudaStreamSynchronize(b->st);
+    drop_graph(b);
+    if (b->mem) cudaFree(b->mem);
+    if (b->order) cudaEventDestroy(b->order);
+    if (b->own_stream) cudaStreamDestroy(b->st);
+    delete b;
+}
+
+}  // extern "C"

@@ -199,12 +199,13 @@ __device__ inline int inward_dir(int i, int j, const Geo& g) {
     return 4;                             // -y (t)
 }
 
+// Boundary point b of the perimeter list: accelerations, Newmark, reset and
+// the value streamed into its interior neighbour.  Returns true if the reset
+// state is non-finite.
 template <typename T>
-__global__ void __launch_bounds__(128) boundary_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
-                                                       const BNode* __restrict__ bn, int nb, T* __restrict__ edge,
-                                                       unsigned* flag) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
+__device__ __forceinline__ bool boundary_point(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
+                                               const View<T>& B, const BNode* __restrict__ bn, int nb,
+                                               T* __restrict__ edge, int b) {
     int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
     size_t p = (size_t)j * g.px + i;
     double ux1, uy1, vx1, vy1;
@@ -250,7 +251,16 @@ __global__ void __launch_bounds__(128) boundary_kernel(Geo g, Consts c, KC<T> k,
     LBPS_ST(&B.u[g.plane + p], uy1);
     LBPS_ST(&B.u[2 * g.plane + p], vx1);
     LBPS_ST(&B.u[3 * g.plane + p], vy1);
-    if (!isfinite((T)phi + (T)psi)) atomicOr(flag, 1u);
+    return !isfinite((T)phi + (T)psi);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) boundary_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
+                                                       const BNode* __restrict__ bn, int nb, T* __restrict__ edge,
+                                                       unsigned* flag) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    if (boundary_point(g, c, k, A, B, bn, nb, edge, b)) atomicOr(flag, 1u);
 }
 
 // ---------------------------------------------------------------- bulk
@@ -278,15 +288,15 @@ __device__ __forceinline__ void load_uv(const double* __restrict__ U, size_t pla
     for (int q = 0; q < 4; ++q) u[q] = ok ? ld(U + (size_t)q * plane + p) : 0.0;
 }
 
-template <typename T, int MINB>
-__global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
-                                                   const T* __restrict__ edge, int nb, unsigned* flag,
-                                                   int rows_per_warp) {
+// One warp's strip: output columns [xs, xs + kStripCols) of rows [j0, j1).
+// Returns true in lanes that produced a non-finite value.  All 32 lanes of
+// the warp must call it together (warp shuffles).
+template <typename T>
+__device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
+                                           const View<T>& B, const T* __restrict__ edge, int nb, int xs, int j0,
+                                           int j1) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int xs = warp * kStripCols;
-    if (xs >= g.nx) return;  // whole warp
     const int xl = xs - 1 + lane;
     const bool col_ok = g.periodic_x ? (xl <= g.nx) : (xl >= 0 && xl < g.nx);
     const int col = col_ok ? wrap(xl, g.nx) : 0;
@@ -294,8 +304,6 @@ __global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KC<T> 
                           (g.periodic_x || (xl > 0 && xl < g.nx - 1));
     const bool bsrc_w = !g.periodic_x && xl == 1;           // west source on the boundary
     const bool bsrc_e = !g.periodic_x && xl == g.nx - 2;    // east source on the boundary
-    const int j0 = blockIdx.y * rows_per_warp;
-    const int j1 = min(j0 + rows_per_warp, g.ny);
     const size_t P = g.plane;
 
     auto row_ok = [&](int j) { return g.periodic_y || (j >= 0 && j < g.ny); };
@@ -402,7 +410,60 @@ __global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KC<T> 
 #pragma unroll
         for (int q = 0; q < 4; ++q) Cu[q] = Nu[q];
     }
-    if (__any_sync(FULL, bad) && lane == 0) atomicOr(flag, 1u);
+    return bad;
+}
+
+template <typename T, int MINB>
+__global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
+                                                   const T* __restrict__ edge, int nb, unsigned* flag,
+                                                   int rows_per_warp) {
+    const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int xs = warp * kStripCols;
+    if (xs >= g.nx) return;  // whole warp
+    const int j0 = blockIdx.y * rows_per_warp;
+    const int j1 = min(j0 + rows_per_warp, g.ny);
+    bool bad = bulk_strip(g, c, k, A, B, edge, nb, xs, j0, j1);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+// --------------------------------------------------------------- batches
+
+// One thread per boundary point of every lattice in the batch.
+template <typename T>
+__global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<T>* __restrict__ dd,
+                                                             const BndTask* __restrict__ tasks, int ntasks,
+                                                             int parity) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntasks) return;
+    const BndTask tk = tasks[t];
+    const DomDesc<T>& d = dd[tk.dom];
+    const int a = d.cur ^ parity;
+    if (boundary_point(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.edge, tk.b)) atomicOr(d.flag, 1u);
+}
+
+// One warp per strip task of every lattice in the batch.
+template <typename T, int MINB>
+__global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<T>* __restrict__ dd,
+                                                               const BulkTask* __restrict__ tasks, int ntasks,
+                                                               int parity) {
+    // Each warp copies its lattice's descriptor into shared memory, from where
+    // the strip code reloads fields as it needs them (instead of holding them
+    // in registers).
+    __shared__ DomDesc<T> sd[kWarpsPerBlock];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int w = blockIdx.x * kWarpsPerBlock + wid;
+    if (w >= ntasks) return;  // whole warp
+    const BulkTask tk = tasks[w];
+    {
+        const unsigned* src = reinterpret_cast<const unsigned*>(dd + tk.dom);
+        unsigned* dst = reinterpret_cast<unsigned*>(sd + wid);
+        for (int q = lane; q < (int)(sizeof(DomDesc<T>) / 4); q += 32) dst[q] = src[q];
+        __syncwarp();
+    }
+    const DomDesc<T>& d = sd[wid];
+    const int a = d.cur ^ parity;
+    bool bad = bulk_strip(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.edge, d.nb, tk.xs, tk.j0, tk.j1);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.flag, 1u);
 }
 
 // ------------------------------------------------------------------ sync
@@ -545,6 +606,27 @@ dim3 grid2d(int nx, int ny, dim3 blk) { return dim3((nx + blk.x - 1) / blk.x, (n
 
 // ------------------------------------------------------------- launchers
 
+template <typename T>
+cudaError_t launch_boundary_batch(const DomDesc<T>* dd, const BndTask* tasks, int ntasks, int parity,
+                                  cudaStream_t st) {
+    if (ntasks > 0) boundary_batch_kernel<T><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bulk_batch(const DomDesc<T>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
+                              cudaStream_t st) {
+    if (ntasks <= 0) return cudaGetLastError();
+    dim3 grid((ntasks + kWarpsPerBlock - 1) / kWarpsPerBlock), blk(32 * kWarpsPerBlock);
+    switch (variant) {
+    case 0: bulk_batch_kernel<T, 6><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 1: bulk_batch_kernel<T, 5><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 2: bulk_batch_kernel<T, 4><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    default: bulk_batch_kernel<T, 8><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t set_check_range(const void* base, size_t bytes, cudaStream_t st) {
 #ifdef LBPS_CHECKED
     const char* lo = static_cast<const char*>(base);
@@ -653,5 +735,10 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, co
 
 LBPS_INSTANTIATE(float)
 LBPS_INSTANTIATE(double)
+
+template cudaError_t launch_boundary_batch<float>(const DomDesc<float>*, const BndTask*, int, int, cudaStream_t);
+template cudaError_t launch_boundary_batch<double>(const DomDesc<double>*, const BndTask*, int, int, cudaStream_t);
+template cudaError_t launch_bulk_batch<float>(const DomDesc<float>*, const BulkTask*, int, int, int, cudaStream_t);
+template cudaError_t launch_bulk_batch<double>(const DomDesc<double>*, const BulkTask*, int, int, int, cudaStream_t);
 
 }  // namespace lbps

@@ -47,6 +47,40 @@ template <typename T>
 cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, const double* ref,
                          double* partials, double* out4, cudaStream_t st);
 
+// ---- batches: many lattices advanced by one launch of each kernel per step
+
+// Everything the kernels need about one lattice of a batch.  v[cur] holds the
+// state at the start of a batch step pair; a step with parity p reads
+// v[cur ^ p] and writes v[cur ^ p ^ 1].
+template <typename T>
+struct DomDesc {
+    Geo g;
+    Consts c;
+    KC<T> k;
+    View<T> v[2];
+    const BNode* bn;
+    T* edge;
+    unsigned* flag;
+    int nb;
+    int cur;
+};
+
+struct BulkTask {  // one warp: output columns [xs, xs + 30) of rows [j0, j1) of lattice dom
+    int dom, xs, j0, j1;
+};
+
+struct BndTask {   // one thread: boundary point b of lattice dom
+    int dom, b;
+};
+
+constexpr int kBatchStripCols = 30;  // output columns per warp task
+
+template <typename T>
+cudaError_t launch_boundary_batch(const DomDesc<T>* dd, const BndTask* tasks, int ntasks, int parity, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bulk_batch(const DomDesc<T>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
+                              cudaStream_t st);
+
 // Checked builds (LBPS_CHECKED): the device block every kernel access must
 // stay inside, and the first violation seen (source line, address); both are
 // no-ops returning 0 in normal builds.

@@ -84,6 +84,13 @@ def _load():
         "lbps_profile_read": (ctypes.c_int, [vp, vp]),
         "lbps_set_stream": (ctypes.c_int, [vp, vp]),
         "lbps_destroy": (None, [vp]),
+        "lbps_batch_create": (ctypes.c_int, [vp, i32, vp, P(vp)]),
+        "lbps_batch_step": (ctypes.c_int, [vp, i64]),
+        "lbps_batch_check": (ctypes.c_int, [vp]),
+        "lbps_batch_set_tuning": (ctypes.c_int, [vp, i32, i32]),
+        "lbps_batch_tune": (ctypes.c_int, [vp, i32, P(i32), P(i32), P(ctypes.c_double)]),
+        "lbps_batch_last_cuda_error": (ctypes.c_int, [vp]),
+        "lbps_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -328,3 +335,71 @@ class Lattice:
 
     def fields(self):
         return {k: self.read(k) for k in ("ux", "uy", "vx", "vy", "phi", "psi")}
+
+
+# ---- batches -----------------------------------------------------------------
+
+def lbps_batch_create(handles, stream_ptr=0):
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    b = ctypes.c_void_p()
+    _check(_lib.lbps_batch_create(arr, len(handles), ctypes.c_void_p(stream_ptr) if stream_ptr else None,
+                                  ctypes.byref(b)), "lbps_batch_create")
+    return b
+
+
+def lbps_batch_step(b, n):
+    return _lib.lbps_batch_step(b, int(n))
+
+
+def lbps_batch_check(b):
+    return _lib.lbps_batch_check(b)
+
+
+def lbps_batch_set_tuning(b, variant, rows_per_warp):
+    _check(_lib.lbps_batch_set_tuning(b, int(variant), int(rows_per_warp)), "lbps_batch_set_tuning")
+
+
+def lbps_batch_tune(b, repeats=3):
+    v, r, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0)
+    _check(_lib.lbps_batch_tune(b, int(repeats), ctypes.byref(v), ctypes.byref(r), ctypes.byref(ms)),
+           "lbps_batch_tune")
+    return int(v.value), int(r.value), float(ms.value)
+
+
+def lbps_batch_destroy(b):
+    _lib.lbps_batch_destroy(b)
+
+
+class Batch:
+    """Lattices advanced together (one launch per kernel per step, graphs)."""
+
+    def __init__(self, lattices, stream=None):
+        self.lattices = list(lattices)
+        self.stream = stream
+        self._h = lbps_batch_create([l._h for l in self.lattices], stream.cuda_stream if stream is not None else 0)
+
+    def step(self, n=1):
+        rc = lbps_batch_step(self._h, n)
+        if rc != LBPS_OK:
+            raise LbpsError(rc, "lbps_batch_step", _lib.lbps_batch_last_cuda_error(self._h))
+        return self
+
+    def check(self):
+        return lbps_batch_check(self._h)
+
+    def tune(self, repeats=3):
+        return lbps_batch_tune(self._h, repeats)
+
+    def set_tuning(self, variant, rows_per_warp):
+        lbps_batch_set_tuning(self._h, variant, rows_per_warp)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lbps_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,128 @@
+"""Batches: many lattices advanced by one launch per kernel per step.
+
+Every lattice of a batch must end bit-for-bit where it ends when stepped on
+its own (same per-point arithmetic), whatever the mix, the step counts, the
+launch shape or interleaved single steps; and agree with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2301_00228_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2301_00228_gb300 import lbps
+    return lbps
+
+
+def domains(seed, count, lo=3, hi=150, periodic=True):
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        nx, ny = (int(v) for v in rng.integers(lo, hi + 1, 2))
+        px = bool(periodic and q % 5 == 3)
+        py = bool(periodic and q % 7 == 5)
+        et = tuple(int(x) for x in rng.choice([1, 2], 4))
+        ev = rng.uniform(-2e-4, 2e-4, 8)
+        lam = float(rng.uniform(0.5, 4.0))
+        a0 = float(rng.choice([0.99, 0.9999]))
+        kind = "dilatation" if q % 2 else "rotation"
+        ux, uy = W.pulse_displacement(nx, ny, float(rng.uniform(0, nx - 1)), float(rng.uniform(0, ny - 1)),
+                                      max(1.5, min(nx, ny) / 6), 1e-3, kind)
+        out.append(dict(nx=nx, ny=ny, px=px, py=py, et=et, ev=ev, lam=lam, a0=a0, ux=ux, uy=uy))
+    return out
+
+
+def make(L, d, storage):
+    lat = L.Lattice.rectangle(d["nx"], d["ny"], d["lam"], 1.0, d["et"], d["ev"], periodic_x=d["px"],
+                              periodic_y=d["py"], a0_phi=d["a0"], storage=storage)
+    return lat.init(d["ux"], d["uy"])
+
+
+def assert_same(a, b, what):
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), (what, k)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64"])
+def test_batch_equals_single(L, storage):
+    ds = domains(7, 14)
+    solo = [make(L, d, storage).step(37) for d in ds]
+    lats = [make(L, d, storage) for d in ds]
+    b = L.Batch(lats)
+    b.step(10).step(27)
+    assert b.check() == 0
+    for q, (x, y) in enumerate(zip(lats, solo)):
+        assert x.steps == 37
+        assert_same(x, y, (storage, q))
+    b.close()
+
+
+def test_batch_tuning_and_interleaved_single_steps(L):
+    ds = domains(8, 9, lo=20, hi=120)
+    solo = [make(L, d, "f32").step(30) for d in ds]
+    lats = [make(L, d, "f32") for d in ds]
+    b = L.Batch(lats)
+    v, r, ms = b.tune(repeats=2)
+    assert 0 <= v <= 2 and r in (8, 16, 32, 64, 128) and ms > 0
+    b.step(9)
+    lats[2].step(1)        # one lattice stepped on its own in between
+    lats[5].step(2)
+    b.step(5)
+    lats[2].step(15)       # catch up to 30 steps for every lattice
+    lats[5].step(14)
+    for q in (0, 1, 3, 4, 6, 7, 8):
+        lats[q].step(16)
+    for q, (x, y) in enumerate(zip(lats, solo)):
+        assert x.steps == 30
+        assert_same(x, y, q)
+    for variant in range(3):
+        b.set_tuning(variant, 8)
+    b.close()
+
+
+def test_batch_against_oracle(L):
+    ds = domains(9, 5, lo=12, hi=60, periodic=False)
+    lats = [make(L, d, "f64") for d in ds]
+    b = L.Batch(lats)
+    b.step(41)
+    for d, lat in zip(ds, lats):
+        nt, bv = O.rect_bc(d["nx"], d["ny"], d["et"], d["ev"])
+        ref = O.OracleLattice(d["nx"], d["ny"], d["lam"], 1.0, a0_phi=d["a0"], node_type=nt, bc_value=bv)
+        ref.init(d["ux"], d["uy"]).step(41)
+        got, want = lat.fields(), ref.fields()
+        for k in ("ux", "uy", "phi", "psi"):
+            scale = max(np.abs(want["ux"]).max(), np.abs(want["uy"]).max()) if k[0] == "u" else \
+                max(np.abs(want["phi"]).max(), np.abs(want["psi"]).max())
+            assert np.abs(got[k] - want[k]).max() <= 1e-10 * scale, k
+    b.close()
+
+
+def test_batch_rejects_and_reports(L):
+    ds = domains(10, 3, lo=10, hi=30, periodic=False)
+    a, c = make(L, ds[0], "f32"), make(L, ds[1], "f64")
+    with pytest.raises(L.LbpsError):
+        L.Batch([a, c])                       # mixed storage
+    with pytest.raises(L.LbpsError):
+        L.Batch([a, a])                       # the same lattice twice
+    s = L.Lattice.rectangle(10, 10, 1.0, 1.0, (1, 1, 1, 1), np.zeros(8), sync_every=5).init(
+        np.zeros((10, 10)), np.zeros((10, 10)))
+    with pytest.raises(L.LbpsError):
+        L.Batch([a, s])                       # synchronisation is per lattice only
+    u = L.Lattice.rectangle(10, 10, 1.0, 1.0, (1, 1, 1, 1), np.zeros(8))
+    with pytest.raises(L.LbpsError) as e:
+        L.Batch([u])                          # not initialised
+    assert e.value.code == L.LBPS_ERR_STATE
+    big = np.full((ds[2]["ny"], ds[2]["nx"]), 1e300)
+    bad = L.Lattice.rectangle(ds[2]["nx"], ds[2]["ny"], 1.0, 1.0, (1, 2, 1, 1), np.zeros(8)).init(big, 0 * big)
+    b = L.Batch([a, bad])
+    b.step(3)
+    assert b.check() == L.LBPS_ERR_NONFINITE
+    assert a.check() == 0
+    b.close()
