@@ -295,6 +295,65 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: a Poisson stream of solves (sides log-uniform 128..2048, steps
+    U{500..20000}, edges and lambda/mu as in the mixed batch) at 0.8 x the
+    capacity of a one-solve-at-a-time loop, served by continuous batching and
+    by that loop; latency = completion - arrival."""
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2301_00228_gb300 import serve as S
+    from paper_2301_00228_gb300 import workloads as W
+
+    # capacity of the one-at-a-time loop, from a sample of the same recipe
+    sample = [S.Request(i, 0.0, d, d.steps)
+              for i, (_, d) in enumerate(W.poisson_requests(count=args.serve_sample, seed=55, rate_hz=1.0))]
+    prep = {r.rid: r.domain.displacement() for r in sample}
+    S.serve_one_at_a_time(sample[:1], prepared=prep)  # warm-up
+    t0 = time.perf_counter()
+    base = S.serve_one_at_a_time(sample, prepared=prep)
+    service = (time.perf_counter() - t0) / len(sample)
+    rate = args.rate_factor / service
+    reqs = [S.Request(i, t, d, d.steps)
+            for i, (t, d) in enumerate(W.poisson_requests(count=args.requests, seed=5, rate_hz=rate))]
+    prepared = {r.rid: r.domain.displacement() for r in reqs}
+    work = sum(r.domain.nx * r.domain.ny * r.steps for r in reqs)
+    budget = int(args.budget_gb * (1 << 30))
+    served = S.serve_batched(reqs, budget, prepared=prepared, max_chunk=args.max_chunk)
+    small = S.serve_batched(reqs, int(args.small_budget_gb * (1 << 30)), prepared=prepared,
+                            max_chunk=args.max_chunk) if args.small_budget_gb > 0 else None
+    loop = S.serve_one_at_a_time(reqs, prepared=prepared)
+    sv, lp = served.summary(), loop.summary()
+    line = {"metric": "served solves/s", "value": sv["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+            "steps": len(reqs), "warmup": 1, "ms_per_step": 1000.0 * served.makespan / len(reqs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"serve_poisson_{len(reqs)}", "requests": len(reqs), "sides": "log-U 128..2048",
+                       "steps": "U{500..20000}", "rate_hz": rate, "rate_factor": args.rate_factor,
+                       "loop_service_s_mean": service, "budget_gb": args.budget_gb,
+                       "lattice_updates": work},
+            "served": {**sv, "glups": work / served.makespan / 1e9},
+            "one_at_a_time": {**lp, "glups": work / loop.makespan / 1e9},
+            "speedup_solves_per_s": sv["solves_per_s"] / lp["solves_per_s"],
+            "p99_latency_ratio": lp["p99_latency_s"] / sv["p99_latency_s"]}
+    if small is not None:
+        line["served_small_budget"] = {**small.summary(), "budget_gb": args.small_budget_gb}
+    # capacity: the first requests all arriving at once (throughput, no idle time)
+    burst = [S.Request(r.rid, 0.0, r.domain, r.steps) for r in reqs[:args.burst]]
+    bwork = sum(r.domain.nx * r.domain.ny * r.steps for r in burst)
+    bs = S.serve_batched(burst, budget, prepared=prepared, max_chunk=args.max_chunk)
+    bl = S.serve_one_at_a_time(burst, prepared=prepared)
+    line["capacity_burst"] = {"requests": len(burst),
+                              "served_solves_per_s": bs.summary()["solves_per_s"],
+                              "loop_solves_per_s": bl.summary()["solves_per_s"],
+                              "served_glups": bwork / bs.makespan / 1e9, "loop_glups": bwork / bl.makespan / 1e9,
+                              "speedup": bl.makespan / bs.makespan, "served_max_active": bs.max_active}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -435,7 +494,14 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="pulses", choices=["pulses", "waves", "square", "batch"])
+    ap.add_argument("--workload", default="pulses", choices=["pulses", "waves", "square", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=64, help="serve: requests in the Poisson stream")
+    ap.add_argument("--serve-sample", type=int, default=6, help="serve: solves timed to set the arrival rate")
+    ap.add_argument("--rate-factor", type=float, default=0.8, help="serve: arrival rate / loop capacity")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device-memory admission budget")
+    ap.add_argument("--small-budget-gb", type=float, default=2.0, help="serve: second run with a small budget")
+    ap.add_argument("--max-chunk", type=int, default=500, help="serve: most steps between completions checks")
+    ap.add_argument("--burst", type=int, default=32, help="serve: requests arriving at once for the capacity run")
     ap.add_argument("--batch-count", type=int, default=256, help="domains of the batch workload")
     ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
@@ -450,6 +516,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_gpu(args)
 
 

@@ -1,0 +1,203 @@
+"""Continuous-batching serving of plane-strain LBM solves on one GPU.
+
+A request is one solve: a rectangle (sizes, material, edges, initial
+displacement) and a step count.  ``Server.run`` takes requests with arrival
+times and serves them as they arrive:
+
+* admission: a waiting request is admitted when the device memory its
+  lattice needs (``lbps_state_bytes``) fits in what the budget has left; its
+  populations then stay resident until it completes;
+* batching: all admitted solves advance together as one ``Batch`` (one launch
+  of each kernel per time step for all of them, CUDA graphs for step pairs),
+  in chunks no longer than the shortest remaining solve, so every solve stops
+  exactly at its step count;
+* completion: finished solves are read out (their u fields) and freed, and
+  the batch is rebuilt with the waiting requests that now fit.
+
+``serve_one_at_a_time`` is the plain baseline: the same kernels, one solve at
+a time in arrival order.  Both report per-request latency (completion minus
+arrival) and throughput.  A solve gets the same bits alone, in the batch, or
+in the baseline loop, because the batched kernels run the per-point
+arithmetic of the single-lattice ones.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import lbps
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds after the start of the run
+    domain: object          # workloads.Domain
+    steps: int
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    completed: float
+    ux: np.ndarray | None = None
+    uy: np.ndarray | None = None
+
+    @property
+    def latency(self):
+        return self.completed - self.arrival
+
+
+@dataclass
+class Report:
+    results: list = field(default_factory=list)
+    makespan: float = 0.0
+    chunks: int = 0
+    rebuilds: int = 0
+    max_active: int = 0
+    peak_bytes: int = 0
+
+    def summary(self):
+        lat = np.array([r.latency for r in self.results])
+        return {"solves": len(self.results), "solves_per_s": len(self.results) / self.makespan,
+                "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                "mean_latency_s": float(lat.mean()), "makespan_s": self.makespan, "chunks": self.chunks,
+                "batch_rebuilds": self.rebuilds, "max_active": self.max_active, "peak_state_bytes": self.peak_bytes}
+
+
+def _params(d, storage):
+    return lbps.lbps_params(d.nx, d.ny, d.lam, d.mu, d.rho, 1.0, d.a0_phi, int(d.periodic_x), int(d.periodic_y),
+                            0, 0, lbps.STORAGES[storage], None)
+
+
+def footprint(d, storage="f32"):
+    """Device bytes one solve holds while admitted."""
+    return lbps.lbps_state_bytes(_params(d, storage))
+
+
+def _lattice(d, storage, u0=None):
+    lat = lbps.Lattice.rectangle(d.nx, d.ny, d.lam, d.mu, d.edge_type, np.asarray(d.edge_value, float).ravel(),
+                                 periodic_x=d.periodic_x, periodic_y=d.periodic_y, a0_phi=d.a0_phi,
+                                 storage=storage)
+    ux, uy = u0 if u0 is not None else d.displacement()
+    return lat.init(ux, uy)
+
+
+class _Clock:
+    def __init__(self, clock):
+        self.clock = clock
+        self.t0 = clock()
+
+    def now(self):
+        return self.clock() - self.t0
+
+    def wait_until(self, t):
+        while True:
+            dt = t - self.now()
+            if dt <= 0:
+                return
+            time.sleep(min(dt, 0.01))
+
+
+def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fields=True, tuning=None,
+                  clock=time.perf_counter, prepared=None):
+    """Continuous batching.  ``prepared[rid]`` may hold (ux, uy) host arrays
+    computed beforehand (input generation kept out of the timed run)."""
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    for r in reqs:
+        if footprint(r.domain, storage) > budget_bytes:
+            raise ValueError(f"request {r.rid} needs more device memory than the whole budget")
+    clk = _Clock(clock)
+    rep = Report()
+    waiting, active = [], []     # active: [request, lattice, remaining, admitted]
+    nxt = 0
+    used = 0
+    batch = None
+    batch_members = ()
+    while nxt < len(reqs) or waiting or active:
+        now = clk.now()
+        while nxt < len(reqs) and reqs[nxt].arrival <= now:
+            waiting.append(reqs[nxt])
+            nxt += 1
+        # admit in arrival order while memory is left
+        while waiting:
+            need = footprint(waiting[0].domain, storage)
+            if used + need > budget_bytes:
+                break
+            r = waiting.pop(0)
+            u0 = prepared.get(r.rid) if prepared else None
+            active.append([r, _lattice(r.domain, storage, u0), r.steps, clk.now()])
+            used += need
+        rep.peak_bytes = max(rep.peak_bytes, used)
+        rep.max_active = max(rep.max_active, len(active))
+        if not active:
+            if nxt < len(reqs):
+                clk.wait_until(reqs[nxt].arrival)
+            continue
+        members = tuple(id(a[1]) for a in active)
+        if members != batch_members:
+            if batch is not None:
+                batch.close()
+            batch = lbps.Batch([a[1] for a in active])
+            if tuning is not None:
+                batch.set_tuning(*tuning)
+            batch_members = members
+            rep.rebuilds += 1
+        k = min(max_chunk, min(a[2] for a in active))
+        batch.step(k)
+        rc = batch.check()  # waits for the chunk
+        if rc != lbps.LBPS_OK:
+            raise lbps.LbpsError(rc, "serve: batch check")
+        rep.chunks += 1
+        done = [a for a in active if a[2] == k]
+        for a in active:
+            a[2] -= k
+        if done:
+            batch.close()
+            batch, batch_members = None, ()
+            for r, lat, _, admitted in done:
+                res = Result(r.rid, r.arrival, admitted, 0.0)
+                if keep_fields:
+                    res.ux, res.uy = lat.read("ux"), lat.read("uy")
+                else:
+                    lat.norms("ux")
+                res.completed = clk.now()
+                rep.results.append(res)
+                used -= footprint(r.domain, storage)
+                lat.close()
+            active = [a for a in active if a[2] > 0]
+    if batch is not None:
+        batch.close()
+    rep.makespan = clk.now()
+    rep.results.sort(key=lambda r: r.rid)
+    return rep
+
+
+def serve_one_at_a_time(requests, storage="f32", keep_fields=True, clock=time.perf_counter, prepared=None):
+    """Baseline: one solve at a time, in arrival order, with lbps_step."""
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    clk = _Clock(clock)
+    rep = Report()
+    for r in reqs:
+        clk.wait_until(r.arrival)
+        admitted = clk.now()
+        u0 = prepared.get(r.rid) if prepared else None
+        lat = _lattice(r.domain, storage, u0)
+        lat.step(r.steps)
+        res = Result(r.rid, r.arrival, admitted, 0.0)
+        if keep_fields:
+            res.ux, res.uy = lat.read("ux"), lat.read("uy")
+        else:
+            lat.norms("ux")
+        res.completed = clk.now()
+        rep.results.append(res)
+        rep.chunks += 1
+        lat.close()
+    rep.makespan = clk.now()
+    rep.max_active = 1
+    rep.results.sort(key=lambda r: r.rid)
+    return rep

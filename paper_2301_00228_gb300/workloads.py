@@ -204,20 +204,24 @@ def crop(domain: Domain, x0, y0, w, h):
                   steps=domain.steps)
 
 
-def poisson_requests(count=10000, seed=5, rate_hz=1.0, side_lo=128, side_hi=2048,
-                     steps_lo=500, steps_hi=20000):
-    """Arrival times and domains of the serving stream: Poisson arrivals, sides
-    log-uniform, step counts uniform, boundaries and materials as random_rectangle."""
+def poisson_requests(count=10000, seed=5, rate_hz=1.0, side_lo=128, side_hi=2048, steps_lo=500,
+                     steps_hi=20000):
+    """Arrival times and domains of a serving stream: Poisson arrivals at
+    rate_hz, sides log-uniform in [side_lo, side_hi] (independent nx, ny), step
+    counts uniform in [steps_lo, steps_hi], edges, lambda/mu and one pulse
+    drawn as in random_rectangle."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_hz, size=count))
     out = []
     for k in range(count):
         nx = int(round(math.exp(rng.uniform(math.log(side_lo), math.log(side_hi)))))
         ny = int(round(math.exp(rng.uniform(math.log(side_lo), math.log(side_hi)))))
-        d = random_rectangle(rng, 3, 3)  # draws edges, material, pulse kind
-        d.nx, d.ny = nx, ny
-        d.pulses = [(float(rng.integers(0, nx)), float(rng.integers(0, ny)), 4.0, 1e-3,
-                     d.pulses[0][4])]
-        d.steps = int(rng.integers(steps_lo, steps_hi + 1))
-        out.append((float(t[k]), d))
+        et = tuple(int(x) for x in rng.choice([NEUMANN, DIRICHLET], size=4))
+        ev = tuple((float(a), float(b)) for a, b in rng.uniform(-1e-3, 1e-3, size=(4, 2)))
+        lam = float(rng.uniform(0.5, 4.0))
+        kind = "dilatation" if rng.random() < 0.5 else "rotation"
+        pulse = (float(rng.integers(0, nx)), float(rng.integers(0, ny)), 4.0, 1e-3, kind)
+        steps = int(rng.integers(steps_lo, steps_hi + 1))
+        out.append((float(t[k]), Domain(nx, ny, lam, 1.0, edge_type=et, edge_value=ev, pulses=[pulse],
+                                        steps=steps)))
     return out
