@@ -286,7 +286,7 @@ def run_batch(args):
                          "peak_source": peak_kind},
             "one_at_a_time": {"value": loop_value, "unit": UNIT, "steps": loop_steps,
                               "speedup_of_batch": value / loop_value},
-            "gpu_launches": 2 * args.steps, "clocks": clock}
+            "gpu_launches": 4 * args.steps, "clocks": clock}
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()
@@ -439,8 +439,9 @@ def run_gpu(args):
                 "traffic": traffic, "kernel": "bulk_kernel", "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": bulk_avg_s * 1000.0,
                 "share_of_step_kernel_time": bulk_ms / total_kernel_ms if total_kernel_ms else None,
-                "boundary_kernel_avg_ms": bnd_ms / max(bnd_n, 1)}
-    gpu_launches = int(bulk_n + bnd_n) + (args.steps // args.sync_every if args.sync_every else 0)
+                "boundary_passes_ms_per_step": bnd_ms / args.steps}
+    bounded = not (d.periodic_x and d.periodic_y)
+    gpu_launches = int(bulk_n) * (4 if bounded else 1) + (args.steps // args.sync_every if args.sync_every else 0)
 
     # end to end through the C ABI with host buffers
     e2e = None

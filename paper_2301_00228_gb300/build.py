@@ -44,7 +44,11 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
     kernel memory access range- and alignment-checked (LBPS_CHECKED)."""
     BUILD.mkdir(exist_ok=True)
     headers = list(CSRC.glob("*.cuh")) + list(CSRC.glob("*.h")) + list(INCLUDE.glob("*.h"))
-    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", str(INCLUDE), "-I", str(CSRC)]
+    # -fmad=false: no compiler-chosen multiply-add contraction, so every kernel
+    # that evaluates a shared formula gets the same bits (the hot loops use
+    # explicit fused intrinsics where they want them).
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC", "-I", str(INCLUDE),
+                    "-I", str(CSRC)]
     if ptxas_info:
         flags += ["-Xptxas", "-v"]
     if checked:

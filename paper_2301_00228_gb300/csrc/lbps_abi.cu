@@ -62,8 +62,8 @@ Layout make_layout(const lbps_params* p) {
     off += L.copy_bytes;
     L.off_bn = off;
     off += align_up((size_t)L.nb * sizeof(BNode));
-    L.off_edge = off;
-    off += align_up(2 * (size_t)L.nb * L.elem);
+    L.off_sig = off;
+    off += align_up(2 * (size_t)L.nb * 3 * sizeof(double));
     L.off_part = off;
     off += align_up((size_t)lbps::kNormBlocks * 4 * sizeof(double));
     L.off_out = off;
@@ -122,33 +122,43 @@ cudaError_t prof_mark(lbps_lattice* lat) {
     return cudaEventRecord(e, lat->st);
 }
 
+// Boundary passes [pass_lo, pass_hi) of one step (0 stress, 1 Newmark, 2 reset).
+cudaError_t boundary_passes(lbps_lattice* lat, int a, int b, int pass_lo, int pass_hi) {
+    if (lat->L.nb == 0) return cudaSuccess;
+    cudaError_t e = prof_mark(lat);
+    if (e == cudaSuccess) {
+        if (lat->f64())
+            e = lbps::launch_boundary<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(a), lat->view<double>(b),
+                                              lat->bn(), lat->L.nb, lat->sig(), lat->flag(), lat->st, pass_lo,
+                                              pass_hi);
+        else
+            e = lbps::launch_boundary<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(a), lat->view<float>(b),
+                                             lat->bn(), lat->L.nb, lat->sig(), lat->flag(), lat->st, pass_lo,
+                                             pass_hi);
+    }
+    if (e == cudaSuccess) e = prof_mark(lat);
+    if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(1);
+    return e;
+}
+
+// One time step: boundary stress and Newmark passes, the interior kernel, then
+// the boundary reset (which reads the interior kernel's new u and overwrites
+// the populations streamed from boundary points).
 int run_step(lbps_lattice* lat) {
     int a = lat->cur, b = lat->cur ^ 1;
-    cudaError_t e = cudaSuccess;
-    if (lat->L.nb > 0) {
-        e = prof_mark(lat);
-        if (e == cudaSuccess) {
-            if (lat->f64())
-                e = lbps::launch_boundary<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(a), lat->view<double>(b),
-                                                  lat->bn(), lat->L.nb, lat->edge<double>(), lat->flag(), lat->st);
-            else
-                e = lbps::launch_boundary<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(a), lat->view<float>(b),
-                                                 lat->bn(), lat->L.nb, lat->edge<float>(), lat->flag(), lat->st);
-        }
-        if (e == cudaSuccess) e = prof_mark(lat);
-        if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(1);
-    }
+    cudaError_t e = boundary_passes(lat, a, b, 0, 2);
     if (e == cudaSuccess) e = prof_mark(lat);
     if (e == cudaSuccess) {
         if (lat->f64())
             e = lbps::launch_bulk<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(a), lat->view<double>(b),
-                                          lat->edge<double>(), lat->L.nb, lat->flag(), lat->st, lat->tuning);
+                                          lat->flag(), lat->st, lat->tuning);
         else
             e = lbps::launch_bulk<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(a), lat->view<float>(b),
-                                         lat->edge<float>(), lat->L.nb, lat->flag(), lat->st, lat->tuning);
+                                         lat->flag(), lat->st, lat->tuning);
     }
     if (e == cudaSuccess) e = prof_mark(lat);
     if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(0);
+    if (e == cudaSuccess) e = boundary_passes(lat, a, b, 2, 3);
     if (e != cudaSuccess) {
         lat->last_cuda = (int)e;
         return LBPS_ERR_CUDA;
@@ -364,6 +374,9 @@ int lbps_create(const lbps_params* params, const uint8_t* node_type, const doubl
     c.a[1] = lat->a_psi;
     c.a0[0] = params->a0_phi;
     c.a0[1] = lat->a0_psi;
+    c.two_dt2 = 2.0 / (dt * dt);
+    c.two_dt = 2.0 / dt;
+    c.inv_rho_dh2 = 1.0 / (rho * dh * dh);
     c.bc_feq_mode = params->bc_feq_mode;
     lat->kf = make_kc<float>(lat->a_phi, lat->a_psi, c.cd2, c.cs2, dh);
     lat->kd = make_kc<double>(lat->a_phi, lat->a_psi, c.cd2, c.cs2, dh);

@@ -47,7 +47,7 @@ DomDesc<T> make_desc(const lbps_lattice* lat) {
     d.v[0] = lat->view<T>(0);
     d.v[1] = lat->view<T>(1);
     d.bn = lat->bn();
-    d.edge = lat->edge<T>();
+    d.sig = lat->sig();
     d.flag = lat->flag();
     d.nb = lat->L.nb;
     d.cur = lat->cur;
@@ -105,22 +105,21 @@ int upload(lbps_batch* b) {
 }
 
 // One time step of every lattice: parity 0 reads v[cur], parity 1 v[cur ^ 1].
+// Boundary stress and Newmark passes, the interior kernel, boundary reset.
 cudaError_t launch_step(lbps_batch* b, int parity) {
+    const BndTask* bt = reinterpret_cast<const BndTask*>(b->mem + b->off_bnd);
+    const BulkTask* wt = reinterpret_cast<const BulkTask*>(b->mem + b->off_bulk);
     cudaError_t e;
     if (b->f64) {
         const DomDesc<double>* dd = reinterpret_cast<const DomDesc<double>*>(b->mem);
-        e = lbps::launch_boundary_batch<double>(dd, reinterpret_cast<const BndTask*>(b->mem + b->off_bnd), b->nbnd,
-                                                parity, b->st);
-        if (e == cudaSuccess)
-            e = lbps::launch_bulk_batch<double>(dd, reinterpret_cast<const BulkTask*>(b->mem + b->off_bulk), b->nbulk,
-                                                parity, b->variant, b->st);
+        e = lbps::launch_boundary_batch<double>(dd, bt, b->nbnd, parity, 0, 2, b->st);
+        if (e == cudaSuccess) e = lbps::launch_bulk_batch<double>(dd, wt, b->nbulk, parity, b->variant, b->st);
+        if (e == cudaSuccess) e = lbps::launch_boundary_batch<double>(dd, bt, b->nbnd, parity, 2, 3, b->st);
     } else {
         const DomDesc<float>* dd = reinterpret_cast<const DomDesc<float>*>(b->mem);
-        e = lbps::launch_boundary_batch<float>(dd, reinterpret_cast<const BndTask*>(b->mem + b->off_bnd), b->nbnd,
-                                               parity, b->st);
-        if (e == cudaSuccess)
-            e = lbps::launch_bulk_batch<float>(dd, reinterpret_cast<const BulkTask*>(b->mem + b->off_bulk), b->nbulk,
-                                               parity, b->variant, b->st);
+        e = lbps::launch_boundary_batch<float>(dd, bt, b->nbnd, parity, 0, 2, b->st);
+        if (e == cudaSuccess) e = lbps::launch_bulk_batch<float>(dd, wt, b->nbulk, parity, b->variant, b->st);
+        if (e == cudaSuccess) e = lbps::launch_boundary_batch<float>(dd, bt, b->nbnd, parity, 2, 3, b->st);
     }
     return e;
 }

@@ -53,6 +53,8 @@ struct Consts {
     double inv2h;               // 1 / (2 dh)
     double cd2, cs2;            // c_d^2, c_s^2 (c_s = sqrt(mu/rho))
     double a[2], a0[2];         // a_phi, a_psi ; a_{0,phi}, a_{0,psi}
+    double two_dt2, two_dt;     // 2 / dt^2, 2 / dt (Eq. acc_dirichlet)
+    double inv_rho_dh2;         // 1 / (rho dh^2); a boundary cell's 1 / (rho V_C) is 1, 2 or 4 times it
     int bc_feq_mode;            // Eq. LBE_mod reading
 };
 

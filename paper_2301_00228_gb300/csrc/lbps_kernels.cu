@@ -90,8 +90,9 @@ __device__ inline void stress_at(const Geo& g, const Consts& c, const double* ux
 // Eq. acc_neumann for the boundary cell of (i, j): the square of side dh
 // clipped to the rectangle; one face per existing neighbour r with normal
 // pointing to r, length l_kr, stress (sigma_k + sigma_r)/2; external force
-// F = int t* da supplied per point.
-__device__ inline void accel_neumann(const Geo& g, const Consts& c, const double* ux, const double* uy,
+// F = int t* da supplied per point.  The stresses come from the stress pass:
+// sig0[b] at boundary point b, sig1[b] at its interior neighbour.
+__device__ inline void accel_neumann(const Geo& g, const Consts& c, const double* __restrict__ sig, int nb, int b,
                                      int i, int j, double fx, double fy, double& ax, double& ay) {
     const int DX[4] = {1, 0, -1, 0};
     const int DY[4] = {0, 1, 0, -1};
@@ -104,12 +105,13 @@ __device__ inline void accel_neumann(const Geo& g, const Consts& c, const double
     double wx = (has[0] ? half : 0.0) + (has[2] ? half : 0.0);
     double wy = (has[1] ? half : 0.0) + (has[3] ? half : 0.0);
     double sk[3];
-    stress_at(g, c, ux, uy, i, j, sk);
+    for (int q = 0; q < 3; ++q) sk[q] = LBPS_LD(&sig[(size_t)b * 3 + q]);
     for (int d = 0; d < 4; ++d) {
         if (!has[d]) continue;
         int ri = wrap(i + DX[d], g.nx), rj = wrap(j + DY[d], g.ny);
+        size_t slot = is_boundary(ri, rj, g) ? (size_t)perim_index(ri, rj, g) : (size_t)nb + b;
         double sr[3];
-        stress_at(g, c, ux, uy, ri, rj, sr);
+        for (int q = 0; q < 3; ++q) sr[q] = LBPS_LD(&sig[slot * 3 + q]);
         double sxx = 0.5 * (sk[0] + sr[0]);
         double syy = 0.5 * (sk[1] + sr[1]);
         double sxy = 0.5 * (sk[2] + sr[2]);
@@ -117,51 +119,10 @@ __device__ inline void accel_neumann(const Geo& g, const Consts& c, const double
         fx += (sxx * DX[d] + sxy * DY[d]) * len;
         fy += (sxy * DX[d] + syy * DY[d]) * len;
     }
-    double m = c.rho * wx * wy;
-    ax = fx / m;
-    ay = fy / m;
-}
-
-// Acceleration at time t of any lattice point (interior: Eq. navier; boundary:
-// Eq. acc_neumann or Eq. acc_dirichlet).
-template <typename T>
-__device__ inline void accel_at(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
-                                const BNode* __restrict__ bn, int i, int j, double& ax, double& ay) {
-    const double* ux = A.u;
-    const double* uy = A.u + g.plane;
-    size_t p = (size_t)j * g.px + i;
-    if (is_boundary(i, j, g)) {
-        const BNode* bp = &bn[perim_index(i, j, g)];
-        const int btype = LBPS_LD(&bp->type);
-        const double bx = LBPS_LD(&bp->bx), by = LBPS_LD(&bp->by);
-        if (btype == DIRICHLET) {
-            const double* vx = A.u + 2 * g.plane;
-            const double* vy = A.u + 3 * g.plane;
-            double two_dt2 = 2.0 / (c.dt * c.dt), two_dt = 2.0 / c.dt;
-            ax = two_dt2 * (bx - LBPS_LD(&ux[p])) - two_dt * LBPS_LD(&vx[p]);
-            ay = two_dt2 * (by - LBPS_LD(&uy[p])) - two_dt * LBPS_LD(&vy[p]);
-        } else {
-            accel_neumann(g, c, ux, uy, i, j, bx, by, ax, ay);
-        }
-        return;
-    }
-    int iw = wrap(i - 1, g.nx), ie = wrap(i + 1, g.nx), js = wrap(j - 1, g.ny), jn = wrap(j + 1, g.ny);
-    size_t pw = (size_t)j * g.px + iw, pe = (size_t)j * g.px + ie;
-    size_t ps = (size_t)js * g.px + i, pn = (size_t)jn * g.px + i;
-    accel_interior<T>(moment0(A.f, g.plane, pw, 0), moment0(A.f, g.plane, pe, 0), moment0(A.f, g.plane, ps, 0),
-                      moment0(A.f, g.plane, pn, 0), moment0(A.f, g.plane, pw, 1), moment0(A.f, g.plane, pe, 1),
-                      moment0(A.f, g.plane, ps, 1), moment0(A.f, g.plane, pn, 1), k, ax, ay);
-}
-
-template <typename T>
-__device__ inline void unew_at(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
-                               const BNode* __restrict__ bn, int i, int j, double& ux1, double& uy1,
-                               double& vx1, double& vy1) {
-    double ax, ay;
-    accel_at(g, c, k, A, bn, i, j, ax, ay);
-    size_t p = (size_t)j * g.px + i;
-    newmark(LBPS_LD(&A.u[p]), LBPS_LD(&A.u[2 * g.plane + p]), ax, c, ux1, vx1);
-    newmark(LBPS_LD(&A.u[g.plane + p]), LBPS_LD(&A.u[3 * g.plane + p]), ay, c, uy1, vy1);
+    // 1 / (rho V_C): V_C = wx wy is dh^2, dh^2/2 or dh^2/4 (exact powers of two)
+    double inv_m = c.inv_rho_dh2 * ((has[0] && has[2]) ? 1.0 : 2.0) * ((has[1] && has[3]) ? 1.0 : 2.0);
+    ax = fx * inv_m;
+    ay = fy * inv_m;
 }
 
 // Value streamed out of a boundary source (Eq. LBE_mod).  f-hat is the mean
@@ -199,37 +160,89 @@ __device__ inline int inward_dir(int i, int j, const Geo& g) {
     return 4;                             // -y (t)
 }
 
-// Boundary point b of the perimeter list: accelerations, Newmark, reset and
-// the value streamed into its interior neighbour.  Returns true if the reset
-// state is non-finite.
+// The boundary work of a step runs in three passes over the perimeter list,
+// each one thread per boundary point b at (i, j):
+//   stress   sigma at b and at its interior neighbour (for Eq. acc_neumann);
+//   newmark  acceleration of b (Eq. acc_neumann or Eq. acc_dirichlet) and
+//            u(t + dt) at b;
+//   (the interior kernel runs here: u(t + dt) at every interior point)
+//   reset    phi, psi from differences of u(t + dt) (Eq. psi_phi_at_bound),
+//            populations by Eq. correction-f, and the value b streams into its
+//            interior neighbour (Eq. LBE_mod), written over the population the
+//            interior kernel put there.
+
+__device__ inline void boundary_stress(const Geo& g, const Consts& c, const double* ux, const double* uy,
+                                       const BNode* __restrict__ bn, int nb, double* __restrict__ sig, int b) {
+    int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
+    double s[3];
+    stress_at(g, c, ux, uy, i, j, s);
+    for (int q = 0; q < 3; ++q) LBPS_ST(&sig[(size_t)b * 3 + q], s[q]);
+    const int dir = inward_dir(i, j, g);
+    if (dir != 0) {
+        const int DX[5] = {0, 1, 0, -1, 0};
+        const int DY[5] = {0, 0, 1, 0, -1};
+        stress_at(g, c, ux, uy, i + DX[dir], j + DY[dir], s);
+        for (int q = 0; q < 3; ++q) LBPS_ST(&sig[((size_t)nb + b) * 3 + q], s[q]);
+    }
+}
+
 template <typename T>
-__device__ __forceinline__ bool boundary_point(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
-                                               const View<T>& B, const BNode* __restrict__ bn, int nb,
-                                               T* __restrict__ edge, int b) {
+__device__ inline void boundary_newmark(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
+                                        const View<T>& B, const BNode* __restrict__ bn, int nb,
+                                        const double* __restrict__ sig, int b) {
+    int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
+    const int btype = LBPS_LD(&bn[b].type);
+    const double bx = LBPS_LD(&bn[b].bx), by = LBPS_LD(&bn[b].by);
+    size_t p = (size_t)j * g.px + i;
+    const double* ux = A.u;
+    const double* uy = A.u + g.plane;
+    const double* vx = A.u + 2 * g.plane;
+    const double* vy = A.u + 3 * g.plane;
+    double ax, ay;
+    if (btype == DIRICHLET) {
+        ax = c.two_dt2 * (bx - LBPS_LD(&ux[p])) - c.two_dt * LBPS_LD(&vx[p]);
+        ay = c.two_dt2 * (by - LBPS_LD(&uy[p])) - c.two_dt * LBPS_LD(&vy[p]);
+    } else {
+        accel_neumann(g, c, sig, nb, b, i, j, bx, by, ax, ay);
+    }
+    double ux1, uy1, vx1, vy1;
+    newmark(LBPS_LD(&ux[p]), LBPS_LD(&vx[p]), ax, c, ux1, vx1);
+    newmark(LBPS_LD(&uy[p]), LBPS_LD(&vy[p]), ay, c, uy1, vy1);
+    LBPS_ST(&B.u[p], ux1);
+    LBPS_ST(&B.u[g.plane + p], uy1);
+    LBPS_ST(&B.u[2 * g.plane + p], vx1);
+    LBPS_ST(&B.u[3 * g.plane + p], vy1);
+}
+
+template <typename T>
+__device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
+                                      const View<T>& B, const BNode* __restrict__ bn, int b) {
     int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
     size_t p = (size_t)j * g.px + i;
-    double ux1, uy1, vx1, vy1;
-    unew_at(g, c, k, A, bn, i, j, ux1, uy1, vx1, vy1);
+    const double* ux1 = B.u;
+    const double* uy1 = B.u + g.plane;
     // Eq. psi_phi_at_bound: differences of u(t + dt) at (i, j).
     Sten sx = stencil(i, g.nx, g.periodic_x), sy = stencil(j, g.ny, g.periodic_y);
     double dux_dx = 0.0, duy_dx = 0.0, dux_dy = 0.0, duy_dy = 0.0;
     for (int q = 0; q < sx.n; ++q) {
-        double a1 = ux1, a2 = uy1, t1, t2;
-        if (sx.d[q] != 0) unew_at(g, c, k, A, bn, wrap(i + sx.d[q], g.nx), j, a1, a2, t1, t2);
-        dux_dx = fma_rn(sx.w[q], a1, dux_dx);
-        duy_dx = fma_rn(sx.w[q], a2, duy_dx);
+        size_t o = (size_t)j * g.px + wrap(i + sx.d[q], g.nx);
+        dux_dx = fma_rn(sx.w[q], LBPS_LD(&ux1[o]), dux_dx);
+        duy_dx = fma_rn(sx.w[q], LBPS_LD(&uy1[o]), duy_dx);
     }
     for (int q = 0; q < sy.n; ++q) {
-        double a1 = ux1, a2 = uy1, t1, t2;
-        if (sy.d[q] != 0) unew_at(g, c, k, A, bn, i, wrap(j + sy.d[q], g.ny), a1, a2, t1, t2);
-        dux_dy = fma_rn(sy.w[q], a1, dux_dy);
-        duy_dy = fma_rn(sy.w[q], a2, duy_dy);
+        size_t o = (size_t)wrap(j + sy.d[q], g.ny) * g.px + i;
+        dux_dy = fma_rn(sy.w[q], LBPS_LD(&ux1[o]), dux_dy);
+        duy_dy = fma_rn(sy.w[q], LBPS_LD(&uy1[o]), duy_dy);
     }
     double phi = mul_rn(dux_dx, c.inv2h) + mul_rn(duy_dy, c.inv2h);
     double psi = mul_rn(duy_dx, c.inv2h) - mul_rn(dux_dy, c.inv2h);
     // Eq. correction-f with J(x_k, t) of the stored populations, then the value
-    // this point streams into its interior neighbour (Eq. LBE_mod).
+    // this point streams into its interior neighbour (Eq. LBE_mod): population
+    // dir of that neighbour, replacing what the interior kernel wrote there.
     const int dir = inward_dir(i, j, g);
+    const int DX[5] = {0, 1, 0, -1, 0};
+    const int DY[5] = {0, 0, 1, 0, -1};
+    const size_t pin = dir ? (size_t)(j + DY[dir]) * g.px + (i + DX[dir]) : p;
 #pragma unroll
     for (int set = 0; set < 2; ++set) {
         const T* fa = A.f + (size_t)set * 5 * g.plane + p;
@@ -245,22 +258,31 @@ __device__ __forceinline__ bool boundary_point(const Geo& g, const Consts& c, co
         case 4: v = stream_from_boundary<4, 2>(fa, fb, g.plane, k, set, c.bc_feq_mode); break;
         default: break;
         }
-        if (dir != 0) LBPS_ST(&edge[(size_t)set * nb + b], v);
+        if (dir != 0) LBPS_ST(&B.f[((size_t)set * 5 + dir) * g.plane + pin], v);
     }
-    LBPS_ST(&B.u[p], ux1);
-    LBPS_ST(&B.u[g.plane + p], uy1);
-    LBPS_ST(&B.u[2 * g.plane + p], vx1);
-    LBPS_ST(&B.u[3 * g.plane + p], vy1);
     return !isfinite((T)phi + (T)psi);
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) boundary_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
-                                                       const BNode* __restrict__ bn, int nb, T* __restrict__ edge,
-                                                       unsigned* flag) {
+__global__ void __launch_bounds__(128) boundary_stress_kernel(Geo g, Consts c, View<T> A,
+                                                              const BNode* __restrict__ bn, int nb, double* sig) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    if (boundary_point(g, c, k, A, B, bn, nb, edge, b)) atomicOr(flag, 1u);
+    if (b < nb) boundary_stress(g, c, A.u, A.u + g.plane, bn, nb, sig, b);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) boundary_newmark_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
+                                                               const BNode* __restrict__ bn, int nb,
+                                                               const double* __restrict__ sig) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) boundary_newmark(g, c, k, A, B, bn, nb, sig, b);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) boundary_reset_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
+                                                             const BNode* __restrict__ bn, int nb, unsigned* flag) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb && boundary_reset(g, c, k, A, B, bn, b)) atomicOr(flag, 1u);
 }
 
 // ---------------------------------------------------------------- bulk
@@ -293,8 +315,7 @@ __device__ __forceinline__ void load_uv(const double* __restrict__ U, size_t pla
 // the warp must call it together (warp shuffles).
 template <typename T>
 __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
-                                           const View<T>& B, const T* __restrict__ edge, int nb, int xs, int j0,
-                                           int j1) {
+                                           const View<T>& B, int xs, int j0, int j1) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int xl = xs - 1 + lane;
@@ -302,8 +323,6 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
     const int col = col_ok ? wrap(xl, g.nx) : 0;
     const bool out_lane = lane >= 1 && lane <= kStripCols && xl < g.nx &&
                           (g.periodic_x || (xl > 0 && xl < g.nx - 1));
-    const bool bsrc_w = !g.periodic_x && xl == 1;           // west source on the boundary
-    const bool bsrc_e = !g.periodic_x && xl == g.nx - 2;    // east source on the boundary
     const size_t P = g.plane;
 
     auto row_ok = [&](int j) { return g.periodic_y || (j >= 0 && j < g.ny); };
@@ -348,8 +367,6 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
         }
         const bool row_interior = g.periodic_y || (j > 0 && j < g.ny - 1);
         if (row_interior) {  // warp-uniform
-            const bool bsrc_s = !g.periodic_y && j == 1;
-            const bool bsrc_n = !g.periodic_y && j == g.ny - 2;
             T sW[2], sE[2], out[2][5];
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
@@ -360,25 +377,13 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
                 // rest population: 2 a0 s - f0 = f0 + (2 a0 m - 8 a f0)
                 out[s][0] = add_rn(Cf[s][0], fma_rn(k.two_a0[s], Cm[s], -mul_rn(k.eight_a[s], Cf[s][0])));
                 // moving populations: f^alpha(x) = 2 a s(x - e_alpha) - f^opp(x - e_alpha)
+                // (for sources on the boundary the reset pass overwrites them)
                 out[s][1] = fma_rn(k.two_a[s], sW[s], -f3W);
                 out[s][3] = fma_rn(k.two_a[s], sE[s], -f1E);
                 out[s][2] = fma_rn(k.two_a[s], Ps[s], -Pf4[s]);
                 out[s][4] = fma_rn(k.two_a[s], Ns[s], -Nf[s][2]);
             }
             if (out_lane) {
-                if (bsrc_w | bsrc_e | bsrc_s | bsrc_n) {
-                    // second-row points: boundary sources stream the value the boundary
-                    // kernel derived from their averaged state (Eq. LBE_mod)
-                    const int jr = row_of(j);
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const T* e = edge + (size_t)s * nb;
-                        if (bsrc_w) out[s][1] = ld(e + perim_index(col - 1, jr, g));
-                        if (bsrc_e) out[s][3] = ld(e + perim_index(col + 1, jr, g));
-                        if (bsrc_s) out[s][2] = ld(e + perim_index(col, jr - 1, g));
-                        if (bsrc_n) out[s][4] = ld(e + perim_index(col, jr + 1, g));
-                    }
-                }
                 double ax, ay;
                 accel_interior<T>(sW[0], sE[0], Ps[0], Ns[0], sW[1], sE[1], Ps[1], Ns[1], k, ax, ay);
                 double u1[4];
@@ -415,30 +420,35 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
 
 template <typename T, int MINB>
 __global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
-                                                   const T* __restrict__ edge, int nb, unsigned* flag,
-                                                   int rows_per_warp) {
+                                                   unsigned* flag, int rows_per_warp) {
     const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int xs = warp * kStripCols;
     if (xs >= g.nx) return;  // whole warp
     const int j0 = blockIdx.y * rows_per_warp;
     const int j1 = min(j0 + rows_per_warp, g.ny);
-    bool bad = bulk_strip(g, c, k, A, B, edge, nb, xs, j0, j1);
+    bool bad = bulk_strip(g, c, k, A, B, xs, j0, j1);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
 // --------------------------------------------------------------- batches
 
-// One thread per boundary point of every lattice in the batch.
+// The three boundary passes over the boundary points of every lattice in the
+// batch (one thread per point).
 template <typename T>
 __global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<T>* __restrict__ dd,
                                                              const BndTask* __restrict__ tasks, int ntasks,
-                                                             int parity) {
+                                                             int parity, int pass) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntasks) return;
     const BndTask tk = tasks[t];
     const DomDesc<T>& d = dd[tk.dom];
     const int a = d.cur ^ parity;
-    if (boundary_point(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.edge, tk.b)) atomicOr(d.flag, 1u);
+    if (pass == 0)
+        boundary_stress(d.g, d.c, d.v[a].u, d.v[a].u + d.g.plane, d.bn, d.nb, d.sig, tk.b);
+    else if (pass == 1)
+        boundary_newmark(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.sig, tk.b);
+    else if (boundary_reset(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, tk.b))
+        atomicOr(d.flag, 1u);
 }
 
 // One warp per strip task of every lattice in the batch.
@@ -462,7 +472,7 @@ __global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<T>*
     }
     const DomDesc<T>& d = sd[wid];
     const int a = d.cur ^ parity;
-    bool bad = bulk_strip(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.edge, d.nb, tk.xs, tk.j0, tk.j1);
+    bool bad = bulk_strip(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], tk.xs, tk.j0, tk.j1);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.flag, 1u);
 }
 
@@ -607,9 +617,11 @@ dim3 grid2d(int nx, int ny, dim3 blk) { return dim3((nx + blk.x - 1) / blk.x, (n
 // ------------------------------------------------------------- launchers
 
 template <typename T>
-cudaError_t launch_boundary_batch(const DomDesc<T>* dd, const BndTask* tasks, int ntasks, int parity,
-                                  cudaStream_t st) {
-    if (ntasks > 0) boundary_batch_kernel<T><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity);
+cudaError_t launch_boundary_batch(const DomDesc<T>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
+                                  int pass_hi, cudaStream_t st) {
+    if (ntasks > 0)
+        for (int pass = pass_lo; pass < pass_hi; ++pass)
+            boundary_batch_kernel<T><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity, pass);
     return cudaGetLastError();
 }
 
@@ -668,22 +680,29 @@ cudaError_t launch_init(const Geo& g, const Consts& c, const KC<T>&, View<T> A, 
 
 template <typename T>
 cudaError_t launch_boundary(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, const BNode* bn,
-                            int nb, T* edge, unsigned* flag, cudaStream_t st) {
-    if (nb > 0) boundary_kernel<T><<<(nb + 127) / 128, 128, 0, st>>>(g, c, k, A, B, bn, nb, edge, flag);
+                            int nb, double* sig, unsigned* flag, cudaStream_t st, int pass_lo, int pass_hi) {
+    if (nb > 0) {
+        const int blocks = (nb + 127) / 128;
+        for (int pass = pass_lo; pass < pass_hi; ++pass) {
+            if (pass == 0) boundary_stress_kernel<T><<<blocks, 128, 0, st>>>(g, c, A, bn, nb, sig);
+            if (pass == 1) boundary_newmark_kernel<T><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb, sig);
+            if (pass == 2) boundary_reset_kernel<T><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb, flag);
+        }
+    }
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, const T* edge, int nb,
-                        unsigned* flag, cudaStream_t st, const Tuning& tu) {
+cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, unsigned* flag,
+                        cudaStream_t st, const Tuning& tu) {
     int warps = (g.nx + kStripCols - 1) / kStripCols;
     dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, (g.ny + tu.rows_per_warp - 1) / tu.rows_per_warp);
     dim3 blk(32 * kWarpsPerBlock);
     switch (tu.variant) {
-    case 0: bulk_kernel<T, 6><<<grid, blk, 0, st>>>(g, c, k, A, B, edge, nb, flag, tu.rows_per_warp); break;
-    case 1: bulk_kernel<T, 5><<<grid, blk, 0, st>>>(g, c, k, A, B, edge, nb, flag, tu.rows_per_warp); break;
-    case 2: bulk_kernel<T, 4><<<grid, blk, 0, st>>>(g, c, k, A, B, edge, nb, flag, tu.rows_per_warp); break;
-    default: bulk_kernel<T, 8><<<grid, blk, 0, st>>>(g, c, k, A, B, edge, nb, flag, tu.rows_per_warp); break;
+    case 0: bulk_kernel<T, 6><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    case 1: bulk_kernel<T, 5><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    case 2: bulk_kernel<T, 4><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    default: bulk_kernel<T, 8><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
     }
     return cudaGetLastError();
 }
@@ -723,9 +742,9 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, co
     template cudaError_t launch_init<T>(const Geo&, const Consts&, const KC<T>&, View<T>, const double*,      \
                                         const double*, const double*, const double*, cudaStream_t);          \
     template cudaError_t launch_boundary<T>(const Geo&, const Consts&, const KC<T>&, View<T>, View<T>,        \
-                                            const BNode*, int, T*, unsigned*, cudaStream_t);                  \
-    template cudaError_t launch_bulk<T>(const Geo&, const Consts&, const KC<T>&, View<T>, View<T>, const T*,  \
-                                        int, unsigned*, cudaStream_t, const Tuning&);                         \
+                                            const BNode*, int, double*, unsigned*, cudaStream_t, int, int);   \
+    template cudaError_t launch_bulk<T>(const Geo&, const Consts&, const KC<T>&, View<T>, View<T>, unsigned*, \
+                                        cudaStream_t, const Tuning&);                                         \
     template cudaError_t launch_sync<T>(const Geo&, const Consts&, const KC<T>&, View<T>, cudaStream_t);     \
     template cudaError_t launch_extract<T>(const Geo&, const Consts&, View<T>, int, double*, cudaStream_t);  \
     template cudaError_t launch_extract_rows<T>(const Geo&, const Consts&, View<T>, int, int, int, double*,   \
@@ -736,8 +755,10 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, co
 LBPS_INSTANTIATE(float)
 LBPS_INSTANTIATE(double)
 
-template cudaError_t launch_boundary_batch<float>(const DomDesc<float>*, const BndTask*, int, int, cudaStream_t);
-template cudaError_t launch_boundary_batch<double>(const DomDesc<double>*, const BndTask*, int, int, cudaStream_t);
+template cudaError_t launch_boundary_batch<float>(const DomDesc<float>*, const BndTask*, int, int, int, int,
+                                                  cudaStream_t);
+template cudaError_t launch_boundary_batch<double>(const DomDesc<double>*, const BndTask*, int, int, int, int,
+                                                   cudaStream_t);
 template cudaError_t launch_bulk_batch<float>(const DomDesc<float>*, const BulkTask*, int, int, int, cudaStream_t);
 template cudaError_t launch_bulk_batch<double>(const DomDesc<double>*, const BulkTask*, int, int, int, cudaStream_t);
 

@@ -9,13 +9,13 @@ template <typename T>
 cudaError_t launch_init(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, const double* ux0,
                         const double* uy0, const double* vx0, const double* vy0, cudaStream_t st);
 
-// One time step A (time t) -> B (time t + dt) is launch_boundary followed by
-// launch_bulk on the same stream.
-// edge[set * nb + b]: value boundary point b streams into its interior
-// neighbour (written by launch_boundary, read by launch_bulk).
+// One time step A (time t) -> B (time t + dt) on one stream: boundary passes
+// 0-1 (stress, Newmark), launch_bulk, boundary pass 2 (reset).  sig: scratch
+// of 2 * nb * 3 doubles (stresses of the boundary cells).
 template <typename T>
 cudaError_t launch_boundary(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B,
-                            const BNode* bn, int nb, T* edge, unsigned* flag, cudaStream_t st);
+                            const BNode* bn, int nb, double* sig, unsigned* flag, cudaStream_t st, int pass_lo,
+                            int pass_hi);
 // Launch shape of the bulk kernel: variant selects the register budget (0: 6
 // blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8), rows_per_warp the height of
 // the strip each warp marches over.  Results do not depend on either.
@@ -25,8 +25,8 @@ struct Tuning {
 };
 constexpr int kTuningVariants = 4;
 template <typename T>
-cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, const T* edge, int nb,
-                        unsigned* flag, cudaStream_t st, const Tuning& tu);
+cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, unsigned* flag,
+                        cudaStream_t st, const Tuning& tu);
 
 template <typename T>
 cudaError_t launch_sync(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, cudaStream_t st);
@@ -59,7 +59,7 @@ struct DomDesc {
     KC<T> k;
     View<T> v[2];
     const BNode* bn;
-    T* edge;
+    double* sig;
     unsigned* flag;
     int nb;
     int cur;
@@ -76,7 +76,8 @@ struct BndTask {   // one thread: boundary point b of lattice dom
 constexpr int kBatchStripCols = 30;  // output columns per warp task
 
 template <typename T>
-cudaError_t launch_boundary_batch(const DomDesc<T>* dd, const BndTask* tasks, int ntasks, int parity, cudaStream_t st);
+cudaError_t launch_boundary_batch(const DomDesc<T>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
+                                  int pass_hi, cudaStream_t st);
 template <typename T>
 cudaError_t launch_bulk_batch(const DomDesc<T>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
                               cudaStream_t st);

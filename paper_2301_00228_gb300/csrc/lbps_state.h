@@ -17,7 +17,7 @@ struct Layout {
     size_t u_bytes;     // 4 FP64 planes, aligned
     size_t copy_bytes;
     size_t off_copy[2];
-    size_t off_bn, off_edge, off_part, off_out, off_flag, off_staging;
+    size_t off_bn, off_sig, off_part, off_out, off_flag, off_staging;
     size_t staging_bytes;
     size_t total;
     int nb;
@@ -54,8 +54,7 @@ struct lbps_lattice {
         return v;
     }
     const lbps::BNode* bn() const { return reinterpret_cast<const lbps::BNode*>(mem + L.off_bn); }
-    template <typename T>
-    T* edge() const { return reinterpret_cast<T*>(mem + L.off_edge); }
+    double* sig() const { return reinterpret_cast<double*>(mem + L.off_sig); }
     unsigned* flag() const { return reinterpret_cast<unsigned*>(mem + L.off_flag); }
     double* partials() const { return reinterpret_cast<double*>(mem + L.off_part); }
     double* out4() const { return reinterpret_cast<double*>(mem + L.off_out); }
