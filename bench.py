@@ -12,6 +12,11 @@ Prints one JSON line (rank 0).  Metric: two-field lattice updates per second
 (GLUPS = lattice points x time steps / s / 1e9), whole job.
   --impl reference  times the FP64 CPU oracle on the host cores instead
                     (bounded sample of the same workload).
+  --storage bf16|f16  populations in the 16-bit formats (FP32 moments, 16-bit
+                    non-equilibrium sums); dtype stays the arithmetic type.
+  --precision       adds the relative L2 error of FP32, BF16 and FP16 storage
+                    against the FP64 oracle on a 1024^2 crop rerun (5000
+                    steps; about a minute of oracle time on the host cores).
 """
 from __future__ import annotations
 
@@ -33,7 +38,11 @@ if str(ROOT) not in sys.path:
 
 METRIC = "two-field GLUPS"
 UNIT = "GLUPS"
-BYTES_PER_UPDATE = {"f32": 2 * (10 * 4 + 4 * 8), "f64": 2 * (10 * 8 + 4 * 8)}
+# algorithmic bytes per interior update: read + write of the populations and
+# of u, du/dt (FP64); the 16-bit formats hold per set f^0, Jx, Jy in FP32 and
+# two 16-bit non-equilibrium sums
+BYTES_PER_UPDATE = {"f32": 2 * (10 * 4 + 4 * 8), "f64": 2 * (10 * 8 + 4 * 8),
+                    "bf16": 2 * (6 * 4 + 4 * 2 + 4 * 8), "f16": 2 * (6 * 4 + 4 * 2 + 4 * 8)}
 
 
 # ----------------------------------------------------------------- helpers
@@ -197,6 +206,48 @@ def oracle_sample(d, target_seconds=15.0, side=1024):
                       f"corner kept), {steps} FP64 steps in {dt:.1f} s"}, dt, steps
 
 
+def precision_report(d, side, steps):
+    """Relative L2 per field of every storage format against the FP64 oracle
+    on a side x side stand-alone crop of the workload (the window with the
+    most pulse centres; the workload's edge types on its edges; the pulses
+    centred inside), run for the given number of steps."""
+    import numpy as np
+    import oracle as O
+    from paper_2301_00228_gb300 import lbps
+    from paper_2301_00228_gb300 import workloads as W
+
+    x0, y0 = W.busiest_crop(d, side)
+    c = W.crop(d, x0, y0, side, side)
+    ux, uy = c.displacement()
+    ev = np.asarray(c.edge_value, float).ravel()
+    fields = ("ux", "uy", "phi", "psi")
+    got = {}
+    for st in ("f32", "bf16", "f16"):
+        lat = lbps.Lattice.rectangle(side, side, c.lam, c.mu, c.edge_type, ev, a0_phi=c.a0_phi, storage=st)
+        lat.init(ux, uy).step(steps)
+        got[st] = ({k: lat.read(k) for k in fields}, lat.scale_exp)
+        lat.close()
+    O.set_threads(os.cpu_count() or 1)
+    nt, bv = O.rect_bc(side, side, c.edge_type, ev)
+    t0 = time.perf_counter()
+    ref = O.OracleLattice(side, side, c.lam, c.mu, c.rho, a0_phi=c.a0_phi, node_type=nt, bc_value=bv)
+    ref.init(ux, uy).step(steps)
+    secs = time.perf_counter() - t0
+    rf = ref.fields()
+    out = {}
+    for st, (g, e) in got.items():
+        errs = {}
+        for grp in (("ux", "uy"), ("phi", "psi")):
+            gn = np.sqrt(sum(np.linalg.norm(rf[k]) ** 2 for k in grp))
+            for k in grp:
+                den = max(np.linalg.norm(rf[k]), 1e-2 * gn, 1e-300)
+                errs[k] = float(np.linalg.norm(g[k] - rf[k]) / den)
+        out[st] = {"rel_l2": errs, "max": max(errs.values()), "scale_exp": e,
+                   "bytes_per_update": BYTES_PER_UPDATE[st]}
+    return {"crop": f"{side}x{side} at ({x0}, {y0})", "pulses": len(c.pulses), "steps": steps,
+            "a0_phi": c.a0_phi, "oracle_seconds": secs, "oracle_threads": os.cpu_count() or 1, "formats": out}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -277,7 +328,7 @@ def run_batch(args):
     achieved = interior * BYTES_PER_UPDATE[args.storage] / step_s / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * step_s, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if args.storage == "f64" else "f32", "data": "synthetic",
             "config": {"workload": f"mixed_batch_{len(ds)}", "domains": len(ds), "sides": "U{64..512}",
                        "points": points, "storage": args.storage, "l2": "state larger than L2",
                        "tuned": {"variant": variant, "rows_per_warp": rows, "ms_per_step": tuned_ms}},
@@ -471,17 +522,23 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = oracle_sample(d, target_seconds=args.ref_seconds)
+    precision = None
+    if rank == 0 and args.precision and not (d.periodic_x and d.periodic_y):
+        precision = precision_report(d, args.precision_side, args.precision_steps)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.storage == "f64" else "f32",
+                "data": "synthetic",
                 "config": {"workload": wname, **describe(d), "storage": args.storage,
                            "displacement": "f64", "sync_every": args.sync_every,
                            "l2": "state larger than L2" if alg_bytes > 1.3e8 else "state fits L2",
                            "replicas_per_gpu": 1},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clock}
+        if precision is not None:
+            line["precision"] = precision
         print(json.dumps(line), flush=True)
     lat.close()
     if dist is not None:
@@ -505,7 +562,11 @@ def main(argv=None):
     ap.add_argument("--burst", type=int, default=32, help="serve: requests arriving at once for the capacity run")
     ap.add_argument("--batch-count", type=int, default=256, help="domains of the batch workload")
     ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16", "f16"])
+    ap.add_argument("--precision", action="store_true",
+                    help="pulses: add rel-L2 of every storage format against the FP64 oracle on a crop rerun")
+    ap.add_argument("--precision-side", type=int, default=1024)
+    ap.add_argument("--precision-steps", type=int, default=5000)
     ap.add_argument("--sync-every", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1000)
     ap.add_argument("--ref-seconds", type=float, default=15.0)

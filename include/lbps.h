@@ -48,9 +48,17 @@ extern "C" {
 #define LBPS_DIRICHLET 2        /* displacement u* prescribed: Eq. acc_dirichlet */
 
 /* Storage of the populations (Eq. interpretation).  u and du/dt are FP64 in
- * every format. */
+ * every format.  The 16-bit formats store, per set, the conserved moments
+ * f^0, Jx = f^1 - f^3, Jy = f^2 - f^4 in FP32 and the two pair sums'
+ * deviations from equilibrium (Eq. feq), Nx = f^1 + f^3 - 2 (a/a_0) f^0 and
+ * Ny = f^2 + f^4 - 2 (a/a_0) f^0, in 16 bits multiplied by 2^scale_exp and
+ * rounded to nearest; arithmetic is FP32.  32 bytes per point per state copy
+ * instead of 40 (FP32).  They reject lattices 3 points wide along a
+ * non-periodic axis (LBPS_ERR_INVALID). */
 #define LBPS_STORAGE_F32 0      /* FP32 populations, FP32 arithmetic          */
 #define LBPS_STORAGE_F64 1      /* FP64 populations, FP64 arithmetic          */
+#define LBPS_STORAGE_BF16 2     /* FP32 moments + bfloat16 Nx, Ny             */
+#define LBPS_STORAGE_F16 3      /* FP32 moments + IEEE half Nx, Ny            */
 
 /* Fields for lbps_read / lbps_read_device. */
 #define LBPS_UX 0               /* displacement u_x                            */
@@ -77,6 +85,12 @@ typedef struct lbps_params {
                                    f(x_k, t)                                   */
     int32_t sync_every;         /* l of Sec. 3.2 (0 = no synchronisation)     */
     int32_t storage;            /* LBPS_STORAGE_*                              */
+    int32_t pop_scale_exp;      /* 16-bit storage: the exponent e of 2^e that
+                                   Nx, Ny are stored times, |e| <= 100; 0 =
+                                   chosen by each init so that the size of J
+                                   the initial state and boundary values imply
+                                   lands near 2^10 (Nx, Ny are smaller; half's
+                                   limit is 65504).  Ignored for FP32 / FP64.  */
     void* cuda_stream;          /* cudaStream_t for all work of this lattice  */
 } lbps_params;
 
@@ -118,11 +132,14 @@ int lbps_create(const lbps_params* params, const uint8_t* node_type, const doubl
  * from host arrays [ny][nx]; phi, psi by finite differences of u; the
  * populations at equilibrium (Eq. feq).  vx0/vy0 may both be NULL (body at
  * rest); otherwise the first moments start at J_phi = -v, J_psi = (-v_y, v_x).
- * Rejects non-finite input with LBPS_ERR_INVALID.  Synchronises. */
+ * Rejects non-finite input with LBPS_ERR_INVALID.  Synchronises.  With
+ * 16-bit storage and pop_scale_exp 0, the storage scale is chosen here from a
+ * device reduction over the initial state (lbps_scale_exp reports it). */
 int lbps_init(lbps_lattice* lat, const double* ux0, const double* uy0,
               const double* vx0, const double* vy0);
 
-/* As lbps_init with device arrays [ny][nx]; asynchronous, no finiteness check. */
+/* As lbps_init with device arrays [ny][nx]; asynchronous, no finiteness check
+ * (except that an automatic 16-bit scale choice waits for its reduction). */
 int lbps_init_device(lbps_lattice* lat, const double* d_ux0, const double* d_uy0,
                      const double* d_vx0, const double* d_vy0);
 
@@ -211,9 +228,9 @@ int lbps_batch_check(lbps_batch* b);
  * rows_per_warp 8..4096).  Results do not depend on it. */
 int lbps_batch_set_tuning(lbps_batch* b, int32_t variant, int32_t rows_per_warp);
 
-/* Autotuner: times one step for each launch shape (variants 0..2 x rows
- * 8, 16, 32, 64, 128), repeats times each, keeps the fastest and reports
- * it.  Leaves every lattice's state unchanged (a step is a pure function of
+/* Autotuner: times one step for each launch shape (variants 0, 1, 2, 4, 5,
+ * 6 x rows 8, 16, 32, 64, 128), repeats times each, keeps the fastest and
+ * reports it.  Leaves every lattice's state unchanged (a step is a pure function of
  * the copy it reads; the timed steps only rewrite the same next state). */
 int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* rows_per_warp,
                     double* ms_per_step);
@@ -227,6 +244,12 @@ void lbps_batch_destroy(lbps_batch* b);
  * out[2] a_phi, out[3] a_psi, out[4] a_{0,psi}, out[5] Delta t; and the
  * number of completed time steps. */
 int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done);
+
+/* The exponent e of the 16-bit storage scale in use (Nx, Ny are stored
+ * times 2^e; fixed by pop_scale_exp or chosen by the last init); 0 for FP32
+ * and FP64 storage.  The paper stores populations in full precision; the
+ * compressed formats are this library's. */
+int lbps_scale_exp(const lbps_lattice* lat, int32_t* exp);
 
 /* The CUDA runtime error code (a cudaError_t value) of the most recent
  * step, check or initialisation of this lattice that returned
@@ -243,17 +266,20 @@ int lbps_check_report(uint64_t out[2]);
 
 /* Launch shape of the interior kernel (performance only; results are
  * bit-identical for every setting).  variant 0..3 selects the register budget
- * (0: 6 blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8); rows_per_warp
- * (1..4096) the number of rows each warp marches over.  Defaults: 0, 32. */
+ * (0: 6 blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8) with u, du/dt loaded
+ * two rows ahead; 4..7 the same budgets loading them one row ahead.
+ * rows_per_warp (1..4096) is the number of rows each warp marches over.
+ * Defaults: 0, 32. */
 int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);
 
-/* Per-kernel timing for roofline reports.  enable != 0 starts recording a
- * CUDA event before and after every kernel launch of the time loop on the
- * lattice's stream (the two kernels of a step stay back to back); 0 stops.
- * lbps_profile_read waits for the stream and returns, since recording
- * started: out[0] total milliseconds in the bulk (interior) kernel, out[1]
- * its launches, out[2] total milliseconds in the boundary kernel, out[3] its
- * launches; then clears the record. */
+/* Per-kernel timing for roofline reports.  enable != 0 starts recording CUDA
+ * events on the lattice's stream around the interior kernel of every step
+ * and around each group of boundary passes (stress + Newmark before it,
+ * reset after it); 0 stops.  lbps_profile_read waits for the stream and
+ * returns, since recording started: out[0] total milliseconds in the bulk
+ * (interior) kernel, out[1] its launches, out[2] total milliseconds in the
+ * boundary passes, out[3] the number of timed boundary groups (two per
+ * step); then clears the record. */
 int lbps_profile(lbps_lattice* lat, int32_t enable);
 int lbps_profile_read(lbps_lattice* lat, double out[4]);
 

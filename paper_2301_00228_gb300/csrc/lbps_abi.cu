@@ -1,6 +1,7 @@
 // C ABI of the plane-strain LBM library (declarations and contracts in
 // include/lbps.h).  Host-side work only: validation, the rectangle helper,
 // the device memory layout, and enqueueing the kernels of lbps_kernels.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -24,8 +25,6 @@ constexpr size_t kStagingMax = size_t(8) << 20;  // host read/write staging, byt
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-
-
 bool finite_positive(double x) { return std::isfinite(x) && x > 0.0; }
 
 int validate_params(const lbps_params* p) {
@@ -36,8 +35,15 @@ int validate_params(const lbps_params* p) {
     if (!(p->a0_phi >= 0.0 && p->a0_phi < 1.0)) return LBPS_ERR_INVALID;
     if (p->bc_feq_mode != 0 && p->bc_feq_mode != 1) return LBPS_ERR_INVALID;
     if (p->sync_every < 0) return LBPS_ERR_INVALID;
-    if (p->storage != LBPS_STORAGE_F32 && p->storage != LBPS_STORAGE_F64) return LBPS_ERR_INVALID;
+    if (p->storage < LBPS_STORAGE_F32 || p->storage > LBPS_STORAGE_F16) return LBPS_ERR_INVALID;
+    if (p->pop_scale_exp < -100 || p->pop_scale_exp > 100) return LBPS_ERR_INVALID;
     if ((p->periodic_x != 0 && p->periodic_x != 1) || (p->periodic_y != 0 && p->periodic_y != 1))
+        return LBPS_ERR_INVALID;
+    // 16-bit storage rewrites a population pair as a whole; on a lattice 3 points
+    // wide along a non-periodic axis two boundary sources stream into the same
+    // pair of one point, which that cannot express.
+    if ((p->storage == LBPS_STORAGE_BF16 || p->storage == LBPS_STORAGE_F16) &&
+        ((!p->periodic_x && p->nx == 3) || (!p->periodic_y && p->ny == 3)))
         return LBPS_ERR_INVALID;
     return LBPS_OK;
 }
@@ -50,8 +56,9 @@ Layout make_layout(const lbps_params* p) {
     L.g.periodic_x = p->periodic_x;
     L.g.periodic_y = p->periodic_y;
     L.g.plane = (size_t)L.g.px * (size_t)p->ny;
-    L.elem = p->storage == LBPS_STORAGE_F64 ? 8 : 4;
-    L.f_bytes = align_up(10 * L.g.plane * L.elem);
+    const size_t per_point =
+        lbps::with_policy(p->storage, [](auto pol) { return (size_t)decltype(pol)::kBytesPerPoint; });
+    L.f_bytes = align_up(L.g.plane * per_point);
     L.u_bytes = align_up(4 * L.g.plane * 8);
     L.copy_bytes = L.f_bytes + L.u_bytes;
     L.nb = lbps::perim_count(L.g);
@@ -92,12 +99,13 @@ KC<T> make_kc(double a_phi, double a_psi, double cd2, double cs2, double dh) {
     }
     k.cd2h = (T)(cd2 * 0.5 / dh);
     k.cs2h = (T)(cs2 * 0.5 / dh);
+    for (int s = 0; s < 2; ++s) k.r[s] = (T)(a[s] / (1.0 - 4.0 * a[s]));
+    k.scale = (T)1;
+    k.inv_scale = (T)1;
     return k;
 }
 
 }  // namespace
-
-
 
 namespace {
 
@@ -126,16 +134,13 @@ cudaError_t prof_mark(lbps_lattice* lat) {
 cudaError_t boundary_passes(lbps_lattice* lat, int a, int b, int pass_lo, int pass_hi) {
     if (lat->L.nb == 0) return cudaSuccess;
     cudaError_t e = prof_mark(lat);
-    if (e == cudaSuccess) {
-        if (lat->f64())
-            e = lbps::launch_boundary<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(a), lat->view<double>(b),
-                                              lat->bn(), lat->L.nb, lat->sig(), lat->flag(), lat->st, pass_lo,
-                                              pass_hi);
-        else
-            e = lbps::launch_boundary<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(a), lat->view<float>(b),
-                                             lat->bn(), lat->L.nb, lat->sig(), lat->flag(), lat->st, pass_lo,
-                                             pass_hi);
-    }
+    if (e == cudaSuccess)
+        e = lbps::with_policy(lat->p.storage, [&](auto pol) {
+            using P = decltype(pol);
+            return lbps::launch_boundary<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(a), lat->view<P>(b),
+                                            lat->bn(), lat->L.nb, lat->sig(), lat->flag(), lat->st, pass_lo,
+                                            pass_hi);
+        });
     if (e == cudaSuccess) e = prof_mark(lat);
     if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(1);
     return e;
@@ -148,14 +153,12 @@ int run_step(lbps_lattice* lat) {
     int a = lat->cur, b = lat->cur ^ 1;
     cudaError_t e = boundary_passes(lat, a, b, 0, 2);
     if (e == cudaSuccess) e = prof_mark(lat);
-    if (e == cudaSuccess) {
-        if (lat->f64())
-            e = lbps::launch_bulk<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(a), lat->view<double>(b),
-                                          lat->flag(), lat->st, lat->tuning);
-        else
-            e = lbps::launch_bulk<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(a), lat->view<float>(b),
-                                         lat->flag(), lat->st, lat->tuning);
-    }
+    if (e == cudaSuccess)
+        e = lbps::with_policy(lat->p.storage, [&](auto pol) {
+            using P = decltype(pol);
+            return lbps::launch_bulk<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(a), lat->view<P>(b),
+                                        lat->flag(), lat->st, lat->tuning);
+        });
     if (e == cudaSuccess) e = prof_mark(lat);
     if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(0);
     if (e == cudaSuccess) e = boundary_passes(lat, a, b, 2, 3);
@@ -169,23 +172,49 @@ int run_step(lbps_lattice* lat) {
 }
 
 int run_sync(lbps_lattice* lat) {
-    cudaError_t e;
-    if (lat->f64())
-        e = lbps::launch_sync<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(lat->cur), lat->st);
-    else
-        e = lbps::launch_sync<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(lat->cur), lat->st);
+    cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
+        using P = decltype(pol);
+        return lbps::launch_sync<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(lat->cur), lat->st);
+    });
     return cuda_ok(e);
 }
 
 int run_init_kernel(lbps_lattice* lat) {
-    cudaError_t e;
-    if (lat->f64())
-        e = lbps::launch_init<double>(lat->L.g, lat->c, lat->kd, lat->view<double>(lat->cur), nullptr, nullptr,
-                                      nullptr, nullptr, lat->st);
-    else
-        e = lbps::launch_init<float>(lat->L.g, lat->c, lat->kf, lat->view<float>(lat->cur), nullptr, nullptr,
-                                     nullptr, nullptr, lat->st);
+    cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
+        using P = decltype(pol);
+        return lbps::launch_init<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(lat->cur), lat->st);
+    });
     return cuda_ok(e);
+}
+
+// 16-bit storage: the scale 2^e of the stored Nx, Ny, fixed by the
+// parameters or chosen from the initial state (already in the u planes of the
+// current copy) and the boundary values.
+int choose_scale(lbps_lattice* lat) {
+    int e = lat->p.pop_scale_exp;
+    if (e == 0) {
+        unsigned* word = reinterpret_cast<unsigned*>(lat->out4());
+        unsigned bits = 0;
+        cudaError_t ce = cudaMemsetAsync(word, 0, sizeof(unsigned), lat->st);
+        if (ce == cudaSuccess)
+            ce = lbps::launch_scale_probe(lat->L.g, lat->c, lat->u(lat->cur), std::sqrt(2.0 * lat->a_phi), word,
+                                          lat->st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(&bits, word, sizeof(bits), cudaMemcpyDeviceToHost, lat->st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(lat->st);
+        if (ce != cudaSuccess) {
+            lat->last_cuda = (int)ce;
+            return LBPS_ERR_CUDA;
+        }
+        float probe;
+        std::memcpy(&probe, &bits, sizeof(probe));
+        double m = std::max((double)probe, lat->bc_est);
+        if (m > 0.0 && std::isfinite(m)) e = 10 - (int)std::ceil(std::log2(m));
+        e = std::min(100, std::max(-100, e));
+    }
+    lat->scale_exp = e;
+    lat->kf.scale = std::ldexp(1.0f, e);
+    lat->kf.inv_scale = std::ldexp(1.0f, -e);
+    return LBPS_OK;
 }
 
 // Copy four [ny][nx] arrays (v may be null) into the pitched u planes of the
@@ -193,8 +222,7 @@ int run_init_kernel(lbps_lattice* lat) {
 int init_from(lbps_lattice* lat, const double* ux0, const double* uy0, const double* vx0, const double* vy0,
               cudaMemcpyKind kind) {
     const Geo& g = lat->L.g;
-    double* u = lat->view<float>(lat->cur).u;  // u planes sit at the same place for both storages
-    if (lat->f64()) u = lat->view<double>(lat->cur).u;
+    double* u = lat->u(lat->cur);
     size_t dp = (size_t)g.px * sizeof(double), sp = (size_t)g.nx * sizeof(double);
     const double* src[4] = {ux0, uy0, vx0, vy0};
     for (int q = 0; q < 4; ++q) {
@@ -204,9 +232,14 @@ int init_from(lbps_lattice* lat, const double* ux0, const double* uy0, const dou
         if (e != cudaSuccess) return LBPS_ERR_CUDA;
     }
     if (cudaMemsetAsync(lat->flag(), 0, sizeof(unsigned), lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
+    if (lat->neq16()) {
+        int rc = choose_scale(lat);
+        if (rc != LBPS_OK) return rc;
+    }
     int rc = run_init_kernel(lat);
     if (rc != LBPS_OK) return rc;
     lat->steps = 0;
+    lat->gen += 1;
     lat->initialised = true;
     return LBPS_OK;
 }
@@ -219,13 +252,11 @@ size_t field_count(const lbps_lattice* lat, int32_t field) {
 bool valid_field(int32_t f) { return f >= LBPS_UX && f <= LBPS_CONSISTENCY; }
 
 int extract_rows(lbps_lattice* lat, int32_t field, int j0, int rows, double* dst) {
-    cudaError_t e;
-    if (lat->f64())
-        e = lbps::launch_extract_rows<double>(lat->L.g, lat->c, lat->view<double>(lat->cur), field, j0, rows, dst,
-                                              lat->st);
-    else
-        e = lbps::launch_extract_rows<float>(lat->L.g, lat->c, lat->view<float>(lat->cur), field, j0, rows, dst,
-                                             lat->st);
+    cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
+        using P = decltype(pol);
+        return lbps::launch_extract_rows<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(lat->cur), field, j0,
+                                            rows, dst, lat->st);
+    });
     return cuda_ok(e);
 }
 
@@ -378,6 +409,14 @@ int lbps_create(const lbps_params* params, const uint8_t* node_type, const doubl
     c.two_dt = 2.0 / dt;
     c.inv_rho_dh2 = 1.0 / (rho * dh * dh);
     c.bc_feq_mode = params->bc_feq_mode;
+    // Strain scale the boundary values impose (|u*| / dh at Dirichlet points,
+    // |F| / (dh mu) at Neumann points), for the 16-bit scale estimate.
+    double eps = 0.0;
+    for (const BNode& q : bn) {
+        double m = std::max(std::fabs(q.bx), std::fabs(q.by));
+        eps = std::max(eps, q.type == LBPS_DIRICHLET ? m / dh : m / (dh * mu));
+    }
+    lat->bc_est = std::sqrt(2.0 * lat->a_phi) * eps;
     lat->kf = make_kc<float>(lat->a_phi, lat->a_psi, c.cd2, c.cs2, dh);
     lat->kd = make_kc<double>(lat->a_phi, lat->a_psi, c.cd2, c.cs2, dh);
     lat->cur = 0;
@@ -491,13 +530,11 @@ int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out
     if (!lat || !out) return LBPS_ERR_INVALID;
     if (!(field >= LBPS_UX && field <= LBPS_PSI) && field != LBPS_CONSISTENCY) return LBPS_ERR_INVALID;
     if (!lat->initialised) return LBPS_ERR_STATE;
-    cudaError_t e;
-    if (lat->f64())
-        e = lbps::launch_norms<double>(lat->L.g, lat->c, lat->view<double>(lat->cur), field, d_ref, lat->partials(),
-                                       lat->out4(), lat->st);
-    else
-        e = lbps::launch_norms<float>(lat->L.g, lat->c, lat->view<float>(lat->cur), field, d_ref, lat->partials(),
-                                      lat->out4(), lat->st);
+    cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
+        using P = decltype(pol);
+        return lbps::launch_norms<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(lat->cur), field, d_ref,
+                                     lat->partials(), lat->out4(), lat->st);
+    });
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, lat->out4(), 4 * sizeof(double), cudaMemcpyDeviceToHost, lat->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
     return cuda_ok(e);
@@ -514,6 +551,12 @@ int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done) {
         out[5] = lat->c.dt;
     }
     if (steps_done) *steps_done = lat->steps;
+    return LBPS_OK;
+}
+
+int lbps_scale_exp(const lbps_lattice* lat, int32_t* exp) {
+    if (!lat || !exp) return LBPS_ERR_INVALID;
+    *exp = lat->neq16() ? lat->scale_exp : 0;
     return LBPS_OK;
 }
 

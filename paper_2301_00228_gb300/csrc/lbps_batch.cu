@@ -17,7 +17,7 @@ using lbps::DomDesc;
 
 struct lbps_batch {
     std::vector<lbps_lattice*> lats;
-    bool f64 = false;
+    int32_t storage = LBPS_STORAGE_F32;
     cudaStream_t st = nullptr;    // stream the graph runs on
     bool own_stream = false;
     char* mem = nullptr;          // descriptors | boundary tasks | bulk tasks
@@ -26,6 +26,7 @@ struct lbps_batch {
     int nbnd = 0, nbulk = 0;
     int variant = 0, rows = 32;
     std::vector<int> uploaded_cur;
+    std::vector<int64_t> uploaded_gen;
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t order = nullptr;  // orders the batch stream with the lattices' streams
     int last_cuda = 0;
@@ -35,17 +36,14 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-template <typename T>
-DomDesc<T> make_desc(const lbps_lattice* lat) {
-    DomDesc<T> d;
+template <typename P>
+DomDesc<P> make_desc(const lbps_lattice* lat) {
+    DomDesc<P> d;
     d.g = lat->L.g;
     d.c = lat->c;
-    if constexpr (sizeof(T) == 8)
-        d.k = lat->kd;
-    else
-        d.k = lat->kf;
-    d.v[0] = lat->view<T>(0);
-    d.v[1] = lat->view<T>(1);
+    d.k = lat->kc<P>();
+    d.v[0] = lat->view<P>(0);
+    d.v[1] = lat->view<P>(1);
     d.bn = lat->bn();
     d.sig = lat->sig();
     d.flag = lat->flag();
@@ -55,7 +53,7 @@ DomDesc<T> make_desc(const lbps_lattice* lat) {
 }
 
 size_t desc_bytes(const lbps_batch* b) {
-    return b->f64 ? sizeof(DomDesc<double>) : sizeof(DomDesc<float>);
+    return lbps::with_policy(b->storage, [](auto pol) { return sizeof(DomDesc<decltype(pol)>); });
 }
 
 std::vector<BulkTask> bulk_tasks(const lbps_batch* b, int rows) {
@@ -83,14 +81,13 @@ int upload(lbps_batch* b) {
     std::vector<char> host(b->off_bnd + nt.size() * sizeof(BndTask));
     size_t db = desc_bytes(b);
     for (int d = 0; d < (int)b->lats.size(); ++d) {
-        if (b->f64) {
-            DomDesc<double> x = make_desc<double>(b->lats[d]);
+        lbps::with_policy(b->storage, [&](auto pol) {
+            auto x = make_desc<decltype(pol)>(b->lats[d]);
             std::memcpy(host.data() + d * db, &x, db);
-        } else {
-            DomDesc<float> x = make_desc<float>(b->lats[d]);
-            std::memcpy(host.data() + d * db, &x, db);
-        }
+            return 0;
+        });
         b->uploaded_cur[d] = b->lats[d]->cur;
+        b->uploaded_gen[d] = b->lats[d]->gen;
     }
     std::memcpy(host.data() + b->off_bnd, nt.data(), nt.size() * sizeof(BndTask));
     cudaError_t e = cudaMemcpyAsync(b->mem, host.data(), host.size(), cudaMemcpyHostToDevice, b->st);
@@ -109,19 +106,14 @@ int upload(lbps_batch* b) {
 cudaError_t launch_step(lbps_batch* b, int parity) {
     const BndTask* bt = reinterpret_cast<const BndTask*>(b->mem + b->off_bnd);
     const BulkTask* wt = reinterpret_cast<const BulkTask*>(b->mem + b->off_bulk);
-    cudaError_t e;
-    if (b->f64) {
-        const DomDesc<double>* dd = reinterpret_cast<const DomDesc<double>*>(b->mem);
-        e = lbps::launch_boundary_batch<double>(dd, bt, b->nbnd, parity, 0, 2, b->st);
-        if (e == cudaSuccess) e = lbps::launch_bulk_batch<double>(dd, wt, b->nbulk, parity, b->variant, b->st);
-        if (e == cudaSuccess) e = lbps::launch_boundary_batch<double>(dd, bt, b->nbnd, parity, 2, 3, b->st);
-    } else {
-        const DomDesc<float>* dd = reinterpret_cast<const DomDesc<float>*>(b->mem);
-        e = lbps::launch_boundary_batch<float>(dd, bt, b->nbnd, parity, 0, 2, b->st);
-        if (e == cudaSuccess) e = lbps::launch_bulk_batch<float>(dd, wt, b->nbulk, parity, b->variant, b->st);
-        if (e == cudaSuccess) e = lbps::launch_boundary_batch<float>(dd, bt, b->nbnd, parity, 2, 3, b->st);
-    }
-    return e;
+    return lbps::with_policy(b->storage, [&](auto pol) {
+        using P = decltype(pol);
+        const DomDesc<P>* dd = reinterpret_cast<const DomDesc<P>*>(b->mem);
+        cudaError_t e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 0, 2, b->st);
+        if (e == cudaSuccess) e = lbps::launch_bulk_batch<P>(dd, wt, b->nbulk, parity, b->variant, b->st);
+        if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 2, 3, b->st);
+        return e;
+    });
 }
 
 void drop_graph(lbps_batch* b) {
@@ -148,11 +140,13 @@ int capture(lbps_batch* b) {
     return LBPS_OK;
 }
 
-// Refreshes the descriptors if any lattice was stepped on its own since the
-// last upload (its current copy moved).
+// Refreshes the descriptors if any lattice was stepped on its own (its
+// current copy moved) or initialised again (its 16-bit scale may have
+// changed) since the last upload.  The graph reads the descriptors from
+// device memory, so it stays valid.
 int refresh(lbps_batch* b) {
     for (size_t d = 0; d < b->lats.size(); ++d)
-        if (b->lats[d]->cur != b->uploaded_cur[d]) return upload(b);
+        if (b->lats[d]->cur != b->uploaded_cur[d] || b->lats[d]->gen != b->uploaded_gen[d]) return upload(b);
     return LBPS_OK;
 }
 
@@ -163,12 +157,12 @@ extern "C" {
 int lbps_batch_create(lbps_lattice* const* lats, int32_t count, void* cuda_stream, lbps_batch** out) {
     if (!out || !lats || count < 1) return LBPS_ERR_INVALID;
     *out = nullptr;
-    bool f64 = lats[0] && lats[0]->f64();
+    const int32_t storage = lats[0] ? lats[0]->p.storage : LBPS_STORAGE_F32;
     for (int32_t d = 0; d < count; ++d) {
         const lbps_lattice* l = lats[d];
         if (!l) return LBPS_ERR_INVALID;
         if (!l->initialised) return LBPS_ERR_STATE;
-        if (l->f64() != f64 || l->p.sync_every != 0) return LBPS_ERR_INVALID;
+        if (l->p.storage != storage || l->p.sync_every != 0) return LBPS_ERR_INVALID;
         for (int32_t q = 0; q < d; ++q)
             if (lats[q] == l) return LBPS_ERR_INVALID;
     }
@@ -176,7 +170,8 @@ int lbps_batch_create(lbps_lattice* const* lats, int32_t count, void* cuda_strea
     if (!b) return LBPS_ERR_OOM;
     b->lats.assign(lats, lats + count);
     b->uploaded_cur.assign(count, -1);
-    b->f64 = f64;
+    b->uploaded_gen.assign(count, -1);
+    b->storage = storage;
     if (cuda_stream) {
         b->st = reinterpret_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -277,7 +272,7 @@ int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* r
     int rc = refresh(b);
     if (rc != LBPS_OK) return rc;
     const int rows_c[] = {8, 16, 32, 64, 128};
-    const int var_c[] = {0, 1, 2};
+    const int var_c[] = {0, 1, 2, 4, 5, 6};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(b, cudaGetLastError());
     float best = -1.0f;

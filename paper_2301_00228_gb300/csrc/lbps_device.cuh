@@ -4,6 +4,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbps {
@@ -66,13 +68,15 @@ struct KC {
     T two_a0[2];                // 2 a_0
     T eight_a[2];               // 8 a = 2 (1 - a_0)
     T cd2h, cs2h;               // c_d^2 / (2 dh), c_s^2 / (2 dh)
+    T r[2];                     // a / a_0 (16-bit storage: equilibrium pair sum 2 r f^0)
+    T scale, inv_scale;         // 2^e, 2^-e applied to the stored 16-bit Nx, Ny
 };
 
-// One state copy: 10 population planes (phi^0..phi^4, psi^0..psi^4) of type T
+// One state copy: the population planes (layout set by the storage policy P)
 // and 4 FP64 planes (u_x, u_y, v_x, v_y).
-template <typename T>
+template <typename P>
 struct View {
-    T* f;
+    typename P::Base* f;
     double* u;
 };
 
@@ -186,5 +190,244 @@ template <typename T>
 __device__ __forceinline__ T sum5(T f0, T f1, T f2, T f3, T f4) {
     return add_rn(f0, add_rn(add_rn(f1, f2), add_rn(f3, f4)));
 }
+
+// ---- population storage policies
+//
+// PopDirect<T>: the five populations of each set as 10 planes of T (FP32 or
+// FP64), arithmetic in T.
+// PopNeq16<H>: per set the conserved moments in FP32 and the non-equilibrium
+// part in 16 bits (H = __half or __nv_bfloat16), arithmetic in FP32.  The
+// five populations of a set map one-to-one to f^0, the lattice first moment
+// (Jx, Jy) = (f^1 - f^3, f^2 - f^4) and the pair sums f^1 + f^3, f^2 + f^4;
+// at equilibrium (Eq. feq) each pair sum is 2 a s = 2 (a / a_0) f^0, so
+//   Nx = f^1 + f^3 - 2 r f^0,  Ny = f^2 + f^4 - 2 r f^0   (r = a / a_0)
+// vanish there and carry only the non-equilibrium part.  f^0, Jx, Jy are
+// stored in FP32, Nx, Ny in H multiplied by 2^e.  Decoding:
+//   f^1 = r f^0 + (Nx + Jx) / 2,  f^3 = r f^0 + (Nx - Jx) / 2  (and y).
+// The first moment stays FP32 because with the small time steps of Sec. 4
+// (a_0 near 1) every rounding of J acts as a momentum kick whose effect on
+// phi grows with time; the pair sums do not have that effect.  Layout per
+// copy: f^0, Jx, Jy of phi, the same of psi (6 FP32 planes), then two planes
+// of 32-bit words, (Nx of phi | Nx of psi << 16) and the same for Ny, so every
+// access is a 4-byte one; 32 bytes per point instead of 40.
+//
+// Besides per-set loads and stores, each policy writes a whole point
+// (store_point, both sets) and one streamed population of both sets
+// (store1_both), the forms the interior kernel and the boundary reset use.
+
+template <typename T>
+struct PopDirect {
+    using V = T;
+    using Base = T;
+    static constexpr int kBytesPerPoint = 10 * (int)sizeof(T);
+    struct Raw {
+        T f[2][5];
+    };
+    __device__ __forceinline__ static void load_raw(const T* __restrict__ f, size_t plane, size_t p, bool ok,
+                                                    Raw& r) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) r.f[s][q] = ok ? LBPS_LDG(f + (size_t)(s * 5 + q) * plane + p) : (T)0;
+    }
+    __device__ __forceinline__ static void decode(const Raw& r, int s, const KC<T>&, T (&x)[5]) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) x[q] = r.f[s][q];
+    }
+    __device__ __forceinline__ static void load5(const T* __restrict__ f, size_t plane, size_t p, int s,
+                                                 const KC<T>&, T (&x)[5]) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) x[q] = LBPS_LD(f + (size_t)(s * 5 + q) * plane + p);
+    }
+    __device__ __forceinline__ static void store5(T* __restrict__ f, size_t plane, size_t p, int s, const T (&x)[5],
+                                                  const KC<T>&) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) LBPS_ST(f + (size_t)(s * 5 + q) * plane + p, x[q]);
+    }
+    __device__ __forceinline__ static void store_point(T* __restrict__ f, size_t plane, size_t p,
+                                                       const T (&x)[2][5], const KC<T>& k) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) store5(f, plane, p, s, x[s], k);
+    }
+    // One moving population alpha (1..4) of both sets.
+    __device__ __forceinline__ static void store1_both(T* __restrict__ f, size_t plane, size_t p, int alpha,
+                                                       const T (&v)[2], const KC<T>&) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) LBPS_ST(f + (size_t)(s * 5 + alpha) * plane + p, v[s]);
+    }
+    // The stored populations of set s, widened to FP64 (field output).
+    __device__ __forceinline__ static void load5d(const T* __restrict__ f, size_t plane, size_t p, int s,
+                                                  const KC<T>&, double (&x)[5]) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) x[q] = (double)LBPS_LD(f + (size_t)(s * 5 + q) * plane + p);
+    }
+    // Equilibrium of Eq. feq for s and the lattice first moment (jx, jy) (FP64 in).
+    __device__ __forceinline__ static void store_eq(T* __restrict__ f, size_t plane, size_t p, int s, double a0,
+                                                    double a, double sv, double jx, double jy, const KC<T>&) {
+        T* b = f + (size_t)s * 5 * plane + p;
+        double as = a * sv;
+        LBPS_ST(&b[0], (T)(a0 * sv));
+        LBPS_ST(&b[plane], (T)(as + 0.5 * jx));
+        LBPS_ST(&b[2 * plane], (T)(as + 0.5 * jy));
+        LBPS_ST(&b[3 * plane], (T)(as - 0.5 * jx));
+        LBPS_ST(&b[4 * plane], (T)(as - 0.5 * jy));
+    }
+};
+
+template <typename H>
+__device__ __forceinline__ float h2f(H v);
+template <>
+__device__ __forceinline__ float h2f<__half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float h2f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename H>
+__device__ __forceinline__ H f2h(float v);
+template <>
+__device__ __forceinline__ __half f2h<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 f2h<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+// 16-bit value <-> its bits (the low or high half of a packed word)
+template <typename H>
+__device__ __forceinline__ float bits2f(unsigned b);
+template <>
+__device__ __forceinline__ float bits2f<__half>(unsigned b) { return __half2float(__ushort_as_half((unsigned short)b)); }
+template <>
+__device__ __forceinline__ float bits2f<__nv_bfloat16>(unsigned b) {
+    return __bfloat162float(__ushort_as_bfloat16((unsigned short)b));
+}
+template <typename H>
+__device__ __forceinline__ unsigned f2bits(float v);
+template <>
+__device__ __forceinline__ unsigned f2bits<__half>(float v) { return __half_as_ushort(__float2half_rn(v)); }
+template <>
+__device__ __forceinline__ unsigned f2bits<__nv_bfloat16>(float v) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+template <typename H>
+struct PopNeq16 {
+    using V = float;
+    using Base = float;
+    static constexpr int kBytesPerPoint = 6 * 4 + 2 * 4;
+    struct Raw {
+        float m[2][3];   // f^0, Jx, Jy of each set
+        unsigned w[2];   // packed Nx, Ny words (scaled)
+    };
+    __device__ __forceinline__ static const unsigned* words(const float* f, size_t plane) {
+        return reinterpret_cast<const unsigned*>(f + 6 * plane);
+    }
+    __device__ __forceinline__ static unsigned* words(float* f, size_t plane) {
+        return reinterpret_cast<unsigned*>(f + 6 * plane);
+    }
+    __device__ __forceinline__ static float half_of(unsigned w, int s, const KC<float>& k) {
+        return mul_rn(bits2f<H>(s ? (w >> 16) : (w & 0xffffu)), k.inv_scale);
+    }
+    // populations from the moments of one set
+    __device__ __forceinline__ static void expand(float f0, float jx, float jy, float nx, float ny, float r,
+                                                  float (&x)[5]) {
+        const float rf0 = mul_rn(r, f0);
+        x[0] = f0;
+        x[1] = fma_rn(0.5f, add_rn(nx, jx), rf0);
+        x[3] = fma_rn(0.5f, sub_rn(nx, jx), rf0);
+        x[2] = fma_rn(0.5f, add_rn(ny, jy), rf0);
+        x[4] = fma_rn(0.5f, sub_rn(ny, jy), rf0);
+    }
+    __device__ __forceinline__ static unsigned enc_n(float pair_sum, float f0, float r, float scale) {
+        return f2bits<H>(mul_rn(fma_rn(-2.0f * r, f0, pair_sum), scale));
+    }
+    __device__ __forceinline__ static void load_raw(const float* __restrict__ f, size_t plane, size_t p, bool ok,
+                                                    Raw& r) {
+        const unsigned* w = words(f, plane);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) r.m[s][q] = ok ? LBPS_LDG(f + (size_t)(s * 3 + q) * plane + p) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) r.w[q] = ok ? LBPS_LDG(w + (size_t)q * plane + p) : 0u;
+    }
+    __device__ __forceinline__ static void decode(const Raw& r, int s, const KC<float>& k, float (&x)[5]) {
+        expand(r.m[s][0], r.m[s][1], r.m[s][2], half_of(r.w[0], s, k), half_of(r.w[1], s, k), k.r[s], x);
+    }
+    __device__ __forceinline__ static void load5(const float* __restrict__ f, size_t plane, size_t p, int s,
+                                                 const KC<float>& k, float (&x)[5]) {
+        const unsigned* w = words(f, plane);
+        float m[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) m[q] = LBPS_LD(f + (size_t)(s * 3 + q) * plane + p);
+        expand(m[0], m[1], m[2], half_of(LBPS_LD(w + p), s, k), half_of(LBPS_LD(w + plane + p), s, k), k.r[s], x);
+    }
+    // The same in FP64 (field output).
+    __device__ __forceinline__ static void load5d(const float* __restrict__ f, size_t plane, size_t p, int s,
+                                                  const KC<float>& k, double (&x)[5]) {
+        const unsigned* w = words(f, plane);
+        double f0 = LBPS_LD(f + (size_t)(s * 3) * plane + p);
+        double jx = LBPS_LD(f + (size_t)(s * 3 + 1) * plane + p);
+        double jy = LBPS_LD(f + (size_t)(s * 3 + 2) * plane + p);
+        unsigned wx = LBPS_LD(w + p), wy = LBPS_LD(w + plane + p);
+        double nx = (double)bits2f<H>(s ? (wx >> 16) : (wx & 0xffffu)) * (double)k.inv_scale;
+        double ny = (double)bits2f<H>(s ? (wy >> 16) : (wy & 0xffffu)) * (double)k.inv_scale;
+        double rf0 = (double)k.r[s] * f0;
+        x[0] = f0;
+        x[1] = rf0 + 0.5 * (nx + jx);
+        x[3] = rf0 + 0.5 * (nx - jx);
+        x[2] = rf0 + 0.5 * (ny + jy);
+        x[4] = rf0 + 0.5 * (ny - jy);
+    }
+    __device__ __forceinline__ static void store_point(float* __restrict__ f, size_t plane, size_t p,
+                                                       const float (&x)[2][5], const KC<float>& k) {
+        unsigned wx = 0, wy = 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            LBPS_ST(f + (size_t)(s * 3) * plane + p, x[s][0]);
+            LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, sub_rn(x[s][1], x[s][3]));
+            LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, sub_rn(x[s][2], x[s][4]));
+            wx |= enc_n(add_rn(x[s][1], x[s][3]), x[s][0], k.r[s], k.scale) << (16 * s);
+            wy |= enc_n(add_rn(x[s][2], x[s][4]), x[s][0], k.r[s], k.scale) << (16 * s);
+        }
+        unsigned* w = words(f, plane);
+        LBPS_ST(w + p, wx);
+        LBPS_ST(w + plane + p, wy);
+    }
+    // One moving population alpha (1..4) of both sets: the pair partner keeps
+    // its value, so the pair's J and N are rewritten together.  Both sets'
+    // N of a pair share one word, so the call owns that word; the library
+    // rejects lattices 3 points wide along a non-periodic axis, the only shape
+    // where two boundary sources stream into the same pair of one point.
+    __device__ __forceinline__ static void store1_both(float* __restrict__ f, size_t plane, size_t p, int alpha,
+                                                       const float (&v)[2], const KC<float>& k) {
+        const int ax = (alpha == 1 || alpha == 3) ? 0 : 1;        // 0: x pair, 1: y pair
+        const bool plus = alpha <= 2;                              // alpha = 1, 2: J = v - partner
+        unsigned* wp = words(f, plane) + (size_t)ax * plane + p;
+        const unsigned w = LBPS_LD(wp);
+        unsigned out = 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            float* jp = f + (size_t)(s * 3 + 1 + ax) * plane + p;
+            const float f0 = LBPS_LD(f + (size_t)(s * 3) * plane + p);
+            const float j = LBPS_LD(jp);
+            const float nn = half_of(w, s, k);
+            const float rf0 = mul_rn(k.r[s], f0);
+            const float partner = plus ? fma_rn(0.5f, sub_rn(nn, j), rf0) : fma_rn(0.5f, add_rn(nn, j), rf0);
+            LBPS_ST(jp, plus ? sub_rn(v[s], partner) : sub_rn(partner, v[s]));
+            out |= enc_n(add_rn(v[s], partner), f0, k.r[s], k.scale) << (16 * s);
+        }
+        LBPS_ST(wp, out);
+    }
+    // Equilibrium of Eq. feq for set s: J = (jx, jy) (rounded to FP32), the
+    // pair sums' deviation 2 a s - 2 r f^0 formed in FP64 from the stored f^0,
+    // written into the set's halves of both words.
+    __device__ __forceinline__ static void store_eq(float* __restrict__ f, size_t plane, size_t p, int s, double a0,
+                                                    double a, double sv, double jx, double jy, const KC<float>& k) {
+        float f0 = (float)(a0 * sv);
+        LBPS_ST(f + (size_t)(s * 3) * plane + p, f0);
+        LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, (float)jx);
+        LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, (float)jy);
+        unsigned short nv =
+            (unsigned short)f2bits<H>((float)((2.0 * a * sv - 2.0 * (double)k.r[s] * (double)f0) * (double)k.scale));
+        unsigned short* h = reinterpret_cast<unsigned short*>(words(f, plane));
+        LBPS_ST(h + 2 * p + s, nv);
+        LBPS_ST(h + 2 * (plane + p) + s, nv);
+    }
+};
 
 }  // namespace lbps

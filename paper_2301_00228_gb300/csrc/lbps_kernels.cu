@@ -1,20 +1,24 @@
 // CUDA kernels of the plane-strain lattice Boltzmann time loop
 // (arXiv:2301.00228, algorithm summary of Fig. 3), sm_103a.
 //
-// One time step is two launches on the same stream:
-//   boundary_kernel  one thread per boundary point: acceleration by Eq.
-//                    acc_neumann / acc_dirichlet, Newmark (Eq. integration),
-//                    phi, psi from differences of the new u (Eq.
-//                    psi_phi_at_bound; the new u of the few stencil points is
-//                    recomputed locally), populations by Eq. correction-f.
-//                    Writes u, du/dt and the populations of boundary points
-//                    of copy B.
-//   bulk_kernel      every other point: interior acceleration (Eq. navier),
-//                    Newmark, and the pull form of the LBE (Eq. LBE) with the
-//                    time-averaged state of boundary sources (Eq. LBE_mod),
-//                    which it reads from copy B.  Memory-bound stencil: reads
-//                    copy A once, writes copy B once.
-// Copies A (time t) and B (time t + dt) swap after each step.
+// One time step is four launches on one stream:
+//   boundary stress   sigma at every boundary point and its interior
+//                     neighbour (Eq. strain, Eq. hooke), for Eq. acc_neumann;
+//   boundary newmark  acceleration of each boundary point (Eq. acc_neumann or
+//                     Eq. acc_dirichlet) and u, du/dt at t + dt (Eq.
+//                     integration);
+//   bulk              every interior point: acceleration (Eq. navier),
+//                     Newmark, and the pull form of the LBE (Eq. LBE).
+//                     Memory-bound stencil: reads copy A once, writes copy B
+//                     once;
+//   boundary reset    phi, psi at boundary points from differences of the new
+//                     u (Eq. psi_phi_at_bound), their populations by Eq.
+//                     correction-f, and the value each streams into its
+//                     interior neighbour (Eq. LBE_mod).
+// Copies A (time t) and B (time t + dt) swap after each step.  Every kernel is
+// a template over the population storage policy (lbps_device.cuh): FP32 or
+// FP64 planes, or FP32 moments (f^0, J) with the non-equilibrium pair sums in
+// 16 bits.
 #include "lbps_launch.h"
 
 namespace lbps {
@@ -29,34 +33,12 @@ enum {
 template <typename T>
 __device__ __forceinline__ T ld(const T* p) { return LBPS_LDG(p); }
 
-// Sum of the five populations of one set at pitched offset p.
-template <typename T>
-__device__ __forceinline__ T moment0(const T* __restrict__ f, size_t plane, size_t p, int set) {
-    const T* b = f + (size_t)set * 5 * plane + p;
-    return sum5(ld(b), ld(b + plane), ld(b + 2 * plane), ld(b + 3 * plane), ld(b + 4 * plane));
-}
-
-// Equilibrium of Eq. feq for s and the lattice first moment Jbar = J / c
-// (c cancels: c^alpha . J / (2 c^2) = e_alpha . Jbar / 2), written to plane
-// set of copy V at offset p.
-template <typename T>
-__device__ __forceinline__ void store_feq(T* __restrict__ f, size_t plane, size_t p, int set, double a0,
-                                          double a, double s, double jx, double jy) {
-    T* b = f + (size_t)set * 5 * plane + p;
-    double as = a * s;
-    LBPS_ST(&b[0], (T)(a0 * s));
-    LBPS_ST(&b[plane], (T)(as + 0.5 * jx));
-    LBPS_ST(&b[2 * plane], (T)(as + 0.5 * jy));
-    LBPS_ST(&b[3 * plane], (T)(as - 0.5 * jx));
-    LBPS_ST(&b[4 * plane], (T)(as - 0.5 * jy));
-}
-
 // ------------------------------------------------------------------ init
 
 // Fig. 3 initialisation: phi = div u, psi = curl u by finite differences of
-// u(x, 0) (already copied into copy A), populations at equilibrium.
-template <typename T>
-__global__ void init_kernel(Geo g, Consts c, View<T> A) {
+// u(x, 0) (already copied into copy A), populations at equilibrium (Eq. feq).
+template <typename P>
+__global__ void init_kernel(Geo g, Consts c, KCof<P> k, View<P> A) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
@@ -67,10 +49,42 @@ __global__ void init_kernel(Geo g, Consts c, View<T> A) {
     double psi = ddx(uy, g.px, i, j, g, c.inv2h) - ddy(ux, g.px, i, j, g, c.inv2h);
     double vx = LBPS_LD(&A.u[2 * g.plane + p]), vy = LBPS_LD(&A.u[3 * g.plane + p]);
     // First moments from du/dt (J_phi = -v, J_psi = (-v_y, v_x)), in lattice
-    // units Jbar = J dt / dh.
+    // units Jbar = J dt / dh (c cancels: c^alpha . J / (2 c^2) = e_alpha . Jbar / 2).
     double q = c.dt / c.dh;
-    store_feq(A.f, g.plane, p, 0, c.a0[0], c.a[0], phi, -vx * q, -vy * q);
-    store_feq(A.f, g.plane, p, 1, c.a0[1], c.a[1], psi, -vy * q, vx * q);
+    P::store_eq(A.f, g.plane, p, 0, c.a0[0], c.a[0], phi, -vx * q, -vy * q, k);
+    P::store_eq(A.f, g.plane, p, 1, c.a0[1], c.a[1], psi, -vy * q, vx * q, k);
+}
+
+// Size of the lattice first moment J that the initial state implies, for the
+// choice of the 16-bit storage scale (the stored non-equilibrium sums are
+// smaller): per
+// point sqrt(2 a_phi) max(|phi|, |psi|) + (|v_x| + |v_y|) dt / dh (a plane
+// wave has |Jbar| = sqrt(2 a_phi) |phi| for the dilatation; the shear part is
+// smaller by c_s / c_d).  Maximum over the lattice into *out (FP32 bits of a
+// non-negative value, which order like unsigned integers).
+__global__ void scale_probe_kernel(Geo g, Consts c, const double* __restrict__ u, double sq, unsigned* out) {
+    __shared__ float sh[256];
+    int t = threadIdx.y * blockDim.x + threadIdx.x;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    float est = 0.0f;
+    if (i < g.nx && j < g.ny) {
+        const double* ux = u;
+        const double* uy = u + g.plane;
+        size_t p = (size_t)j * g.px + i;
+        double phi = ddx(ux, g.px, i, j, g, c.inv2h) + ddy(uy, g.px, i, j, g, c.inv2h);
+        double psi = ddx(uy, g.px, i, j, g, c.inv2h) - ddy(ux, g.px, i, j, g, c.inv2h);
+        double v = fabs(LBPS_LD(&u[2 * g.plane + p])) + fabs(LBPS_LD(&u[3 * g.plane + p]));
+        double e = sq * fmax(fabs(phi), fabs(psi)) + v * c.dt / c.dh;
+        est = isfinite(e) ? (float)e : 3.0e38f;
+    }
+    sh[t] = est;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) sh[t] = fmaxf(sh[t], sh[t + w]);
+        __syncthreads();
+    }
+    if (t == 0) atomicMax(out, __float_as_uint(sh[0]));
 }
 
 // ------------------------------------------------------------- boundary
@@ -126,24 +140,20 @@ __device__ inline void accel_neumann(const Geo& g, const Consts& c, const double
 }
 
 // Value streamed out of a boundary source (Eq. LBE_mod).  f-hat is the mean
-// of the stored (A) and reset (B) populations of the source; the
-// equilibrium is taken from f-hat (mode 0) or from f(x_k, t) (mode 1).
-// ALPHA is the direction of travel (1..4), OPP its reverse.
-template <int ALPHA, int OPP, typename T>
-__device__ inline T stream_from_boundary(const T* __restrict__ fa, const T* __restrict__ fb, size_t plane,
-                                         const KC<T>& k, int set, int mode) {
-    T a5[5], h5[5];
+// of the stored (a5, copy A) and reset (b5, copy B) populations of the
+// source; the equilibrium is taken from f-hat (mode 0) or from f(x_k, t)
+// (mode 1).  ALPHA is the direction of travel (1..4), OPP its reverse.
+template <int ALPHA, int OPP, typename V>
+__device__ inline V stream_from_boundary(const V (&a5)[5], const V (&b5)[5], const KC<V>& k, int set, int mode) {
+    V h5[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        a5[q] = ld(fa + q * plane);
-        h5[q] = mul_rn((T)0.5, add_rn(a5[q], LBPS_LD(&fb[q * plane])));
-    }
+    for (int q = 0; q < 5; ++q) h5[q] = mul_rn((V)0.5, add_rn(a5[q], b5[q]));
     if (mode == 0) {
-        T sh = sum5(h5[0], h5[1], h5[2], h5[3], h5[4]);
+        V sh = sum5(h5[0], h5[1], h5[2], h5[3], h5[4]);
         return fma_rn(k.two_a[set], sh, -h5[OPP]);  // 2 f_eq(f-hat) - f-hat = 2 a s-hat - f-hat^opp
     }
-    T sa = sum5(a5[0], a5[1], a5[2], a5[3], a5[4]);
-    T ej = sub_rn(a5[ALPHA], a5[OPP]);              // e_alpha . Jbar(x_k, t)
+    V sa = sum5(a5[0], a5[1], a5[2], a5[3], a5[4]);
+    V ej = sub_rn(a5[ALPHA], a5[OPP]);              // e_alpha . Jbar(x_k, t)
     return sub_rn(add_rn(mul_rn(k.two_a[set], sa), ej), h5[ALPHA]);
 }
 
@@ -186,9 +196,9 @@ __device__ inline void boundary_stress(const Geo& g, const Consts& c, const doub
     }
 }
 
-template <typename T>
-__device__ inline void boundary_newmark(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
-                                        const View<T>& B, const BNode* __restrict__ bn, int nb,
+template <typename P>
+__device__ inline void boundary_newmark(const Geo& g, const Consts& c, const View<P>& A, const View<P>& B,
+                                        const BNode* __restrict__ bn, int nb,
                                         const double* __restrict__ sig, int b) {
     int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
     const int btype = LBPS_LD(&bn[b].type);
@@ -214,9 +224,10 @@ __device__ inline void boundary_newmark(const Geo& g, const Consts& c, const KC<
     LBPS_ST(&B.u[3 * g.plane + p], vy1);
 }
 
-template <typename T>
-__device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
-                                      const View<T>& B, const BNode* __restrict__ bn, int b) {
+template <typename P>
+__device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& A,
+                                      const View<P>& B, const BNode* __restrict__ bn, int b) {
+    using V = typename P::V;
     int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
     size_t p = (size_t)j * g.px + i;
     const double* ux1 = B.u;
@@ -243,43 +254,46 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KC<T>
     const int DX[5] = {0, 1, 0, -1, 0};
     const int DY[5] = {0, 0, 1, 0, -1};
     const size_t pin = dir ? (size_t)(j + DY[dir]) * g.px + (i + DX[dir]) : p;
+    V v[2] = {(V)0, (V)0};
 #pragma unroll
     for (int set = 0; set < 2; ++set) {
-        const T* fa = A.f + (size_t)set * 5 * g.plane + p;
-        const T* fb = B.f + (size_t)set * 5 * g.plane + p;
-        double jx = (double)ld(fa + g.plane) - (double)ld(fa + 3 * g.plane);
-        double jy = (double)ld(fa + 2 * g.plane) - (double)ld(fa + 4 * g.plane);
-        store_feq(B.f, g.plane, p, set, c.a0[set], c.a[set], set == 0 ? phi : psi, jx, jy);
-        T v = (T)0;
-        switch (dir) {
-        case 1: v = stream_from_boundary<1, 3>(fa, fb, g.plane, k, set, c.bc_feq_mode); break;
-        case 2: v = stream_from_boundary<2, 4>(fa, fb, g.plane, k, set, c.bc_feq_mode); break;
-        case 3: v = stream_from_boundary<3, 1>(fa, fb, g.plane, k, set, c.bc_feq_mode); break;
-        case 4: v = stream_from_boundary<4, 2>(fa, fb, g.plane, k, set, c.bc_feq_mode); break;
-        default: break;
+        V a5[5];
+        P::load5(A.f, g.plane, p, set, k, a5);
+        double jx = (double)a5[1] - (double)a5[3];
+        double jy = (double)a5[2] - (double)a5[4];
+        P::store_eq(B.f, g.plane, p, set, c.a0[set], c.a[set], set == 0 ? phi : psi, jx, jy, k);
+        if (dir != 0) {
+            V b5[5];
+            P::load5(B.f, g.plane, p, set, k, b5);  // the reset values just stored
+            switch (dir) {
+            case 1: v[set] = stream_from_boundary<1, 3>(a5, b5, k, set, c.bc_feq_mode); break;
+            case 2: v[set] = stream_from_boundary<2, 4>(a5, b5, k, set, c.bc_feq_mode); break;
+            case 3: v[set] = stream_from_boundary<3, 1>(a5, b5, k, set, c.bc_feq_mode); break;
+            default: v[set] = stream_from_boundary<4, 2>(a5, b5, k, set, c.bc_feq_mode); break;
+            }
         }
-        if (dir != 0) LBPS_ST(&B.f[((size_t)set * 5 + dir) * g.plane + pin], v);
     }
-    return !isfinite((T)phi + (T)psi);
+    if (dir != 0) P::store1_both(B.f, g.plane, pin, dir, v, k);
+    return !isfinite((V)phi + (V)psi);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) boundary_stress_kernel(Geo g, Consts c, View<T> A,
+template <typename P>
+__global__ void __launch_bounds__(128) boundary_stress_kernel(Geo g, Consts c, View<P> A,
                                                               const BNode* __restrict__ bn, int nb, double* sig) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nb) boundary_stress(g, c, A.u, A.u + g.plane, bn, nb, sig, b);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) boundary_newmark_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
+template <typename P>
+__global__ void __launch_bounds__(128) boundary_newmark_kernel(Geo g, Consts c, View<P> A, View<P> B,
                                                                const BNode* __restrict__ bn, int nb,
                                                                const double* __restrict__ sig) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb) boundary_newmark(g, c, k, A, B, bn, nb, sig, b);
+    if (b < nb) boundary_newmark(g, c, A, B, bn, nb, sig, b);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) boundary_reset_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
+template <typename P>
+__global__ void __launch_bounds__(128) boundary_reset_kernel(Geo g, Consts c, KCof<P> k, View<P> A, View<P> B,
                                                              const BNode* __restrict__ bn, int nb, unsigned* flag) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nb && boundary_reset(g, c, k, A, B, bn, b)) atomicOr(flag, 1u);
@@ -291,17 +305,17 @@ __global__ void __launch_bounds__(128) boundary_reset_kernel(Geo g, Consts c, KC
 // along y over kRowsPerWarp rows.  Lane l holds column xs - 1 + l, so lanes 0
 // and 31 are halo lanes whose values reach their neighbours by shuffles; the
 // rows above and below stay in registers, and the populations are prefetched
-// two rows ahead.  Every lattice point's 14 words are read once per launch
-// (plus the two halo columns and two halo rows of each strip).
+// two rows ahead (in their stored form, decoded when the row window shifts).
+// Every lattice point's words are read once per launch (plus the two halo
+// columns and two halo rows of each strip).
 constexpr int kStripCols = 30;
 constexpr int kWarpsPerBlock = 4;
 
-template <typename T>
-__device__ __forceinline__ void load_row(const T* __restrict__ F, size_t plane, size_t p, bool ok, T (&f)[2][5]) {
+template <typename P>
+__device__ __forceinline__ void decode_row(const typename P::Raw& r, const KCof<P>& k,
+                                           typename P::V (&f)[2][5]) {
 #pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int q = 0; q < 5; ++q) f[s][q] = ok ? ld(F + (size_t)(s * 5 + q) * plane + p) : (T)0;
+    for (int s = 0; s < 2; ++s) P::decode(r, s, k, f[s]);
 }
 
 __device__ __forceinline__ void load_uv(const double* __restrict__ U, size_t plane, size_t p, bool ok,
@@ -312,10 +326,12 @@ __device__ __forceinline__ void load_uv(const double* __restrict__ U, size_t pla
 
 // One warp's strip: output columns [xs, xs + kStripCols) of rows [j0, j1).
 // Returns true in lanes that produced a non-finite value.  All 32 lanes of
-// the warp must call it together (warp shuffles).
-template <typename T>
-__device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const KC<T>& k, const View<T>& A,
-                                           const View<T>& B, int xs, int j0, int j1) {
+// the warp must call it together (warp shuffles).  UVD: how many rows ahead u
+// and du/dt are prefetched (1 or 2; the populations always 2).
+template <typename P, int UVD>
+__device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& A,
+                                           const View<P>& B, int xs, int j0, int j1) {
+    using V = typename P::V;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int xl = xs - 1 + lane;
@@ -323,7 +339,7 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
     const int col = col_ok ? wrap(xl, g.nx) : 0;
     const bool out_lane = lane >= 1 && lane <= kStripCols && xl < g.nx &&
                           (g.periodic_x || (xl > 0 && xl < g.nx - 1));
-    const size_t P = g.plane;
+    const size_t PL = g.plane;
 
     auto row_ok = [&](int j) { return g.periodic_y || (j >= 0 && j < g.ny); };
     auto row_of = [&](int j) { return g.periodic_y ? wrap(j, g.ny) : j; };
@@ -332,23 +348,27 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
     // even where a masked load is issued unconditionally.
     auto at = [&](int j) { return (size_t)min(max(row_of(j), 0), g.ny - 1) * (size_t)g.px + (size_t)col; };
 
-    T Ps[2], Pf4[2];                          // row j - 1: moment and f^4
-    T Cf[2][5], Cs[2], Cm[2];                 // row j
-    T Nf[2][5];                               // row j + 1
-    T Qf[2][5];                               // row j + 2 (in flight)
-    double Cu[4], Nu[4];
+    V Ps[2], Pf4[2];                          // row j - 1: moment and f^4
+    V Cf[2][5], Cs[2], Cm[2];                 // row j
+    V Nf[2][5];                               // row j + 1
+    typename P::Raw Qr;                       // row j + 2 (in flight, stored form)
+    double Cu[4], Nu[4], Qu[4];               // u, du/dt of rows j, j + 1, j + 2
     {
-        T t[2][5];
-        load_row(A.f, P, at(j0 - 1), col_ok && row_ok(j0 - 1), t);
+        V t[2][5];
+        P::load_raw(A.f, PL, at(j0 - 1), col_ok && row_ok(j0 - 1), Qr);
+        decode_row<P>(Qr, k, t);
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             Ps[s] = sum5(t[s][0], t[s][1], t[s][2], t[s][3], t[s][4]);
             Pf4[s] = t[s][4];
         }
     }
-    load_row(A.f, P, at(j0), col_ok, Cf);
-    load_row(A.f, P, at(j0 + 1), col_ok && row_ok(j0 + 1), Nf);
-    load_uv(A.u, P, at(j0), out_lane, Cu);
+    P::load_raw(A.f, PL, at(j0), col_ok, Qr);
+    decode_row<P>(Qr, k, Cf);
+    P::load_raw(A.f, PL, at(j0 + 1), col_ok && row_ok(j0 + 1), Qr);
+    decode_row<P>(Qr, k, Nf);
+    load_uv(A.u, PL, at(j0), out_lane, Cu);
+    if (UVD == 2) load_uv(A.u, PL, at(j0 + 1), out_lane && j0 + 1 < j1, Nu);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         Cm[s] = add_rn(add_rn(Cf[s][1], Cf[s][2]), add_rn(Cf[s][3], Cf[s][4]));
@@ -357,9 +377,12 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
     bool bad = false;
     for (int j = j0; j < j1; ++j) {
         // prefetch: populations two rows ahead, u and du/dt one row ahead
-        load_row(A.f, P, at(j + 2), col_ok && row_ok(j + 2) && j + 2 <= j1, Qf);
-        load_uv(A.u, P, at(j + 1), out_lane && j + 1 < j1, Nu);
-        T Nm[2], Ns[2];
+        P::load_raw(A.f, PL, at(j + 2), col_ok && row_ok(j + 2) && j + 2 <= j1, Qr);
+        if (UVD == 2)
+            load_uv(A.u, PL, at(j + 2), out_lane && j + 2 < j1, Qu);
+        else
+            load_uv(A.u, PL, at(j + 1), out_lane && j + 1 < j1, Nu);
+        V Nm[2], Ns[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             Nm[s] = add_rn(add_rn(Nf[s][1], Nf[s][2]), add_rn(Nf[s][3], Nf[s][4]));
@@ -367,13 +390,13 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
         }
         const bool row_interior = g.periodic_y || (j > 0 && j < g.ny - 1);
         if (row_interior) {  // warp-uniform
-            T sW[2], sE[2], out[2][5];
+            V sW[2], sE[2], out[2][5];
 #pragma unroll
             for (int s = 0; s < 2; ++s) {
                 sW[s] = __shfl_up_sync(FULL, Cs[s], 1);
                 sE[s] = __shfl_down_sync(FULL, Cs[s], 1);
-                T f3W = __shfl_up_sync(FULL, Cf[s][3], 1);
-                T f1E = __shfl_down_sync(FULL, Cf[s][1], 1);
+                V f3W = __shfl_up_sync(FULL, Cf[s][3], 1);
+                V f1E = __shfl_down_sync(FULL, Cf[s][1], 1);
                 // rest population: 2 a0 s - f0 = f0 + (2 a0 m - 8 a f0)
                 out[s][0] = add_rn(Cf[s][0], fma_rn(k.two_a0[s], Cm[s], -mul_rn(k.eight_a[s], Cf[s][0])));
                 // moving populations: f^alpha(x) = 2 a s(x - e_alpha) - f^opp(x - e_alpha)
@@ -385,17 +408,14 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
             }
             if (out_lane) {
                 double ax, ay;
-                accel_interior<T>(sW[0], sE[0], Ps[0], Ns[0], sW[1], sE[1], Ps[1], Ns[1], k, ax, ay);
+                accel_interior<V>(sW[0], sE[0], Ps[0], Ns[0], sW[1], sE[1], Ps[1], Ns[1], k, ax, ay);
                 double u1[4];
                 newmark(Cu[0], Cu[2], ax, c, u1[0], u1[2]);
                 newmark(Cu[1], Cu[3], ay, c, u1[1], u1[3]);
                 const size_t p = at(j);
+                P::store_point(B.f, PL, p, out, k);
 #pragma unroll
-                for (int s = 0; s < 2; ++s)
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) LBPS_ST(&B.f[(size_t)(s * 5 + q) * P + p], out[s][q]);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) LBPS_ST(&B.u[(size_t)q * P + p], u1[q]);
+                for (int q = 0; q < 4; ++q) LBPS_ST(&B.u[(size_t)q * PL + p], u1[q]);
                 bad |= !isfinite(out[0][0] + out[1][0]);
             }
         }
@@ -407,26 +427,27 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
             Cs[s] = Ns[s];
             Cm[s] = Nm[s];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                Cf[s][q] = Nf[s][q];
-                Nf[s][q] = Qf[s][q];
-            }
+            for (int q = 0; q < 5; ++q) Cf[s][q] = Nf[s][q];
         }
+        decode_row<P>(Qr, k, Nf);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) Cu[q] = Nu[q];
+        for (int q = 0; q < 4; ++q) {
+            Cu[q] = Nu[q];
+            if (UVD == 2) Nu[q] = Qu[q];
+        }
     }
     return bad;
 }
 
-template <typename T, int MINB>
-__global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KC<T> k, View<T> A, View<T> B,
-                                                   unsigned* flag, int rows_per_warp) {
+template <typename P, int MINB, int UVD>
+__global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KCof<P> k, View<P> A, View<P> B,
+                                                         unsigned* flag, int rows_per_warp) {
     const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int xs = warp * kStripCols;
     if (xs >= g.nx) return;  // whole warp
     const int j0 = blockIdx.y * rows_per_warp;
     const int j1 = min(j0 + rows_per_warp, g.ny);
-    bool bad = bulk_strip(g, c, k, A, B, xs, j0, j1);
+    bool bad = bulk_strip<P, UVD>(g, c, k, A, B, xs, j0, j1);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
@@ -434,32 +455,32 @@ __global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KC<T> 
 
 // The three boundary passes over the boundary points of every lattice in the
 // batch (one thread per point).
-template <typename T>
-__global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<T>* __restrict__ dd,
+template <typename P>
+__global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<P>* __restrict__ dd,
                                                              const BndTask* __restrict__ tasks, int ntasks,
                                                              int parity, int pass) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntasks) return;
     const BndTask tk = tasks[t];
-    const DomDesc<T>& d = dd[tk.dom];
+    const DomDesc<P>& d = dd[tk.dom];
     const int a = d.cur ^ parity;
     if (pass == 0)
         boundary_stress(d.g, d.c, d.v[a].u, d.v[a].u + d.g.plane, d.bn, d.nb, d.sig, tk.b);
     else if (pass == 1)
-        boundary_newmark(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.sig, tk.b);
+        boundary_newmark(d.g, d.c, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.sig, tk.b);
     else if (boundary_reset(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, tk.b))
         atomicOr(d.flag, 1u);
 }
 
 // One warp per strip task of every lattice in the batch.
-template <typename T, int MINB>
-__global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<T>* __restrict__ dd,
+template <typename P, int MINB, int UVD>
+__global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<P>* __restrict__ dd,
                                                                const BulkTask* __restrict__ tasks, int ntasks,
                                                                int parity) {
     // Each warp copies its lattice's descriptor into shared memory, from where
     // the strip code reloads fields as it needs them (instead of holding them
     // in registers).
-    __shared__ DomDesc<T> sd[kWarpsPerBlock];
+    __shared__ DomDesc<P> sd[kWarpsPerBlock];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int w = blockIdx.x * kWarpsPerBlock + wid;
     if (w >= ntasks) return;  // whole warp
@@ -467,12 +488,12 @@ __global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<T>*
     {
         const unsigned* src = reinterpret_cast<const unsigned*>(dd + tk.dom);
         unsigned* dst = reinterpret_cast<unsigned*>(sd + wid);
-        for (int q = lane; q < (int)(sizeof(DomDesc<T>) / 4); q += 32) dst[q] = src[q];
+        for (int q = lane; q < (int)(sizeof(DomDesc<P>) / 4); q += 32) dst[q] = src[q];
         __syncwarp();
     }
-    const DomDesc<T>& d = sd[wid];
+    const DomDesc<P>& d = sd[wid];
     const int a = d.cur ^ parity;
-    bool bad = bulk_strip(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], tk.xs, tk.j0, tk.j1);
+    bool bad = bulk_strip<P, UVD>(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], tk.xs, tk.j0, tk.j1);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.flag, 1u);
 }
 
@@ -480,8 +501,9 @@ __global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<T>*
 
 // Sec. 3.2: phi, psi from differences of u at every point, populations by
 // Eq. correction-f with the current first moments.  In place.
-template <typename T>
-__global__ void sync_kernel(Geo g, Consts c, View<T> A) {
+template <typename P>
+__global__ void sync_kernel(Geo g, Consts c, KCof<P> k, View<P> A) {
+    using V = typename P::V;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= g.nx || j >= g.ny) return;
@@ -492,37 +514,40 @@ __global__ void sync_kernel(Geo g, Consts c, View<T> A) {
     s[0] = ddx(ux, g.px, i, j, g, c.inv2h) + ddy(uy, g.px, i, j, g, c.inv2h);
     s[1] = ddx(uy, g.px, i, j, g, c.inv2h) - ddy(ux, g.px, i, j, g, c.inv2h);
     for (int set = 0; set < 2; ++set) {
-        const T* fa = A.f + (size_t)set * 5 * g.plane + p;
-        double jx = (double)fa[g.plane] - (double)fa[3 * g.plane];
-        double jy = (double)fa[2 * g.plane] - (double)fa[4 * g.plane];
-        store_feq(A.f, g.plane, p, set, c.a0[set], c.a[set], s[set], jx, jy);
+        V f[5];
+        P::load5(A.f, g.plane, p, set, k, f);
+        double jx = (double)f[1] - (double)f[3];
+        double jy = (double)f[2] - (double)f[4];
+        P::store_eq(A.f, g.plane, p, set, c.a0[set], c.a[set], s[set], jx, jy, k);
     }
 }
 
 // ---------------------------------------------------------------- fields
 
-template <typename T>
-__device__ inline double moment0_fp64(const T* f, size_t plane, size_t p, int set) {
-    const T* b = f + (size_t)set * 5 * plane + p;
-    return (double)b[0] + (((double)b[plane] + (double)b[2 * plane]) + ((double)b[3 * plane] + (double)b[4 * plane]));
+template <typename P>
+__device__ inline double moment0_fp64(const View<P>& A, size_t plane, size_t p, int set, const KCof<P>& k) {
+    double b[5];
+    P::load5d(A.f, plane, p, set, k, b);
+    return b[0] + ((b[1] + b[2]) + (b[3] + b[4]));
 }
 
 // Scalar field value at (i, j).
-template <typename T>
-__device__ inline double field_value(const Geo& g, const Consts& c, const View<T>& A, int field, int i, int j) {
+template <typename P>
+__device__ inline double field_value(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& A, int field,
+                                     int i, int j) {
     size_t p = (size_t)j * g.px + i;
     switch (field) {
     case FLD_UX: case FLD_UY: case FLD_VX: case FLD_VY: return A.u[(size_t)field * g.plane + p];
-    case FLD_PHI: return moment0_fp64(A.f, g.plane, p, 0);
-    case FLD_PSI: return moment0_fp64(A.f, g.plane, p, 1);
+    case FLD_PHI: return moment0_fp64(A, g.plane, p, 0, k);
+    case FLD_PSI: return moment0_fp64(A, g.plane, p, 1, k);
     default: {
         // consistency error e(x, t) of Sec. 4
         const double* ux = A.u;
         const double* uy = A.u + g.plane;
         double div = ddx(ux, g.px, i, j, g, c.inv2h) + ddy(uy, g.px, i, j, g, c.inv2h);
         double curl = ddx(uy, g.px, i, j, g, c.inv2h) - ddy(ux, g.px, i, j, g, c.inv2h);
-        double e1 = moment0_fp64(A.f, g.plane, p, 1) - curl;
-        double e0 = moment0_fp64(A.f, g.plane, p, 0) - div;
+        double e1 = moment0_fp64(A, g.plane, p, 1, k) - curl;
+        double e0 = moment0_fp64(A, g.plane, p, 0, k) - div;
         return sqrt(e1 * e1 + e0 * e0);
     }
     }
@@ -530,8 +555,8 @@ __device__ inline double field_value(const Geo& g, const Consts& c, const View<T
 
 // Dense FP64 copy of rows [j0, j0 + rows) of a field.  Population fields
 // write 5 consecutive [rows][nx] blocks.
-template <typename T>
-__global__ void extract_kernel(Geo g, Consts c, View<T> A, int field, int j0, int rows, double* dst) {
+template <typename P>
+__global__ void extract_kernel(Geo g, Consts c, KCof<P> k, View<P> A, int field, int j0, int rows, double* dst) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int jr = blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= g.nx || jr >= rows) return;
@@ -541,18 +566,21 @@ __global__ void extract_kernel(Geo g, Consts c, View<T> A, int field, int j0, in
         int set = field == FLD_FPHI ? 0 : 1;
         size_t p = (size_t)j * g.px + i;
         size_t blk = (size_t)rows * g.nx;
-        for (int q = 0; q < 5; ++q) dst[q * blk + d] = (double)A.f[((size_t)set * 5 + q) * g.plane + p];
+        double f[5];
+        P::load5d(A.f, g.plane, p, set, k, f);
+        for (int q = 0; q < 5; ++q) dst[q * blk + d] = f[q];
         return;
     }
-    dst[d] = field_value(g, c, A, field, i, j);
+    dst[d] = field_value<P>(g, c, k, A, field, i, j);
 }
 
 // --------------------------------------------------------------- norms
 
 constexpr int kNormThreads = 256;
 
-template <typename T>
-__global__ void __launch_bounds__(kNormThreads) norms_partial_kernel(Geo g, Consts c, View<T> A, int field,
+template <typename P>
+__global__ void __launch_bounds__(kNormThreads) norms_partial_kernel(Geo g, Consts c, KCof<P> k, View<P> A,
+                                                                     int field,
                                                                      const double* __restrict__ ref,
                                                                      double* partials) {
     __shared__ double sh[4][kNormThreads];
@@ -560,7 +588,7 @@ __global__ void __launch_bounds__(kNormThreads) norms_partial_kernel(Geo g, Cons
     size_t n = (size_t)g.nx * g.ny;
     for (size_t d = (size_t)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += (size_t)gridDim.x * blockDim.x) {
         int i = (int)(d % g.nx), j = (int)(d / g.nx);
-        double x = field_value(g, c, A, field, i, j);
+        double x = field_value<P>(g, c, k, A, field, i, j);
         double r = ref ? ref[d] : 0.0;
         double e = x - r;
         s0 += e * e;
@@ -616,25 +644,29 @@ dim3 grid2d(int nx, int ny, dim3 blk) { return dim3((nx + blk.x - 1) / blk.x, (n
 
 // ------------------------------------------------------------- launchers
 
-template <typename T>
-cudaError_t launch_boundary_batch(const DomDesc<T>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
+template <typename P>
+cudaError_t launch_boundary_batch(const DomDesc<P>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
                                   int pass_hi, cudaStream_t st) {
     if (ntasks > 0)
         for (int pass = pass_lo; pass < pass_hi; ++pass)
-            boundary_batch_kernel<T><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity, pass);
+            boundary_batch_kernel<P><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity, pass);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_bulk_batch(const DomDesc<T>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
+template <typename P>
+cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
                               cudaStream_t st) {
     if (ntasks <= 0) return cudaGetLastError();
     dim3 grid((ntasks + kWarpsPerBlock - 1) / kWarpsPerBlock), blk(32 * kWarpsPerBlock);
     switch (variant) {
-    case 0: bulk_batch_kernel<T, 6><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    case 1: bulk_batch_kernel<T, 5><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    case 2: bulk_batch_kernel<T, 4><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    default: bulk_batch_kernel<T, 8><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 0: bulk_batch_kernel<P, 6, 2><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 1: bulk_batch_kernel<P, 5, 2><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 2: bulk_batch_kernel<P, 4, 2><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 3: bulk_batch_kernel<P, 8, 2><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 4: bulk_batch_kernel<P, 6, 1><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 5: bulk_batch_kernel<P, 5, 1><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 6: bulk_batch_kernel<P, 4, 1><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    default: bulk_batch_kernel<P, 8, 1><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
     }
     return cudaGetLastError();
 }
@@ -670,96 +702,97 @@ int check_report(unsigned long long out[2]) {
 #endif
 }
 
-template <typename T>
-cudaError_t launch_init(const Geo& g, const Consts& c, const KC<T>&, View<T> A, const double*, const double*,
-                        const double*, const double*, cudaStream_t st) {
+cudaError_t launch_scale_probe(const Geo& g, const Consts& c, const double* u, double sq, unsigned* out,
+                               cudaStream_t st) {
     dim3 blk(32, 8);
-    init_kernel<T><<<grid2d(g.nx, g.ny, blk), blk, 0, st>>>(g, c, A);
+    scale_probe_kernel<<<grid2d(g.nx, g.ny, blk), blk, 0, st>>>(g, c, u, sq, out);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_boundary(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, const BNode* bn,
+template <typename P>
+cudaError_t launch_init(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, cudaStream_t st) {
+    dim3 blk(32, 8);
+    init_kernel<P><<<grid2d(g.nx, g.ny, blk), blk, 0, st>>>(g, c, k, A);
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t launch_boundary(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, const BNode* bn,
                             int nb, double* sig, unsigned* flag, cudaStream_t st, int pass_lo, int pass_hi) {
     if (nb > 0) {
         const int blocks = (nb + 127) / 128;
         for (int pass = pass_lo; pass < pass_hi; ++pass) {
-            if (pass == 0) boundary_stress_kernel<T><<<blocks, 128, 0, st>>>(g, c, A, bn, nb, sig);
-            if (pass == 1) boundary_newmark_kernel<T><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb, sig);
-            if (pass == 2) boundary_reset_kernel<T><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb, flag);
+            if (pass == 0) boundary_stress_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, bn, nb, sig);
+            if (pass == 1) boundary_newmark_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, B, bn, nb, sig);
+            if (pass == 2) boundary_reset_kernel<P><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb, flag);
         }
     }
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, unsigned* flag,
+template <typename P>
+cudaError_t launch_bulk(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, unsigned* flag,
                         cudaStream_t st, const Tuning& tu) {
     int warps = (g.nx + kStripCols - 1) / kStripCols;
     dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, (g.ny + tu.rows_per_warp - 1) / tu.rows_per_warp);
     dim3 blk(32 * kWarpsPerBlock);
     switch (tu.variant) {
-    case 0: bulk_kernel<T, 6><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
-    case 1: bulk_kernel<T, 5><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
-    case 2: bulk_kernel<T, 4><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
-    default: bulk_kernel<T, 8><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    case 0: bulk_kernel<P, 6, 2><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    case 1: bulk_kernel<P, 5, 2><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    case 2: bulk_kernel<P, 4, 2><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    case 3: bulk_kernel<P, 8, 2><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    case 4: bulk_kernel<P, 6, 1><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    case 5: bulk_kernel<P, 5, 1><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    case 6: bulk_kernel<P, 4, 1><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
+    default: bulk_kernel<P, 8, 1><<<grid, blk, 0, st>>>(g, c, k, A, B, flag, tu.rows_per_warp); break;
     }
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_sync(const Geo& g, const Consts& c, const KC<T>&, View<T> A, cudaStream_t st) {
+template <typename P>
+cudaError_t launch_sync(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, cudaStream_t st) {
     dim3 blk(32, 8);
-    sync_kernel<T><<<grid2d(g.nx, g.ny, blk), blk, 0, st>>>(g, c, A);
+    sync_kernel<P><<<grid2d(g.nx, g.ny, blk), blk, 0, st>>>(g, c, k, A);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_extract_rows(const Geo& g, const Consts& c, View<T> A, int field, int j0, int rows, double* dst,
-                                cudaStream_t st) {
+template <typename P>
+cudaError_t launch_extract_rows(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, int field, int j0,
+                                int rows, double* dst, cudaStream_t st) {
     dim3 blk(32, 8);
-    extract_kernel<T><<<grid2d(g.nx, rows, blk), blk, 0, st>>>(g, c, A, field, j0, rows, dst);
+    extract_kernel<P><<<grid2d(g.nx, rows, blk), blk, 0, st>>>(g, c, k, A, field, j0, rows, dst);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_extract(const Geo& g, const Consts& c, View<T> A, int field, double* dst, cudaStream_t st) {
-    return launch_extract_rows<T>(g, c, A, field, 0, g.ny, dst, st);
-}
-
-template <typename T>
-cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, const double* ref, double* partials,
-                         double* out4, cudaStream_t st) {
+template <typename P>
+cudaError_t launch_norms(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, int field, const double* ref,
+                         double* partials, double* out4, cudaStream_t st) {
     size_t n = (size_t)g.nx * g.ny;
     int nblk = (int)((n + kNormThreads - 1) / kNormThreads);
     if (nblk > kNormBlocks) nblk = kNormBlocks;
-    norms_partial_kernel<T><<<nblk, kNormThreads, 0, st>>>(g, c, A, field, ref, partials);
+    norms_partial_kernel<P><<<nblk, kNormThreads, 0, st>>>(g, c, k, A, field, ref, partials);
     norms_final_kernel<<<1, kNormThreads, 0, st>>>(partials, nblk, out4);
     return cudaGetLastError();
 }
 
-#define LBPS_INSTANTIATE(T)                                                                                   \
-    template cudaError_t launch_init<T>(const Geo&, const Consts&, const KC<T>&, View<T>, const double*,      \
-                                        const double*, const double*, const double*, cudaStream_t);          \
-    template cudaError_t launch_boundary<T>(const Geo&, const Consts&, const KC<T>&, View<T>, View<T>,        \
+#define LBPS_INSTANTIATE(P)                                                                                   \
+    template cudaError_t launch_init<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, cudaStream_t);  \
+    template cudaError_t launch_boundary<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>,      \
                                             const BNode*, int, double*, unsigned*, cudaStream_t, int, int);   \
-    template cudaError_t launch_bulk<T>(const Geo&, const Consts&, const KC<T>&, View<T>, View<T>, unsigned*, \
-                                        cudaStream_t, const Tuning&);                                         \
-    template cudaError_t launch_sync<T>(const Geo&, const Consts&, const KC<T>&, View<T>, cudaStream_t);     \
-    template cudaError_t launch_extract<T>(const Geo&, const Consts&, View<T>, int, double*, cudaStream_t);  \
-    template cudaError_t launch_extract_rows<T>(const Geo&, const Consts&, View<T>, int, int, int, double*,   \
-                                                cudaStream_t);                                                \
-    template cudaError_t launch_norms<T>(const Geo&, const Consts&, View<T>, int, const double*, double*,    \
-                                         double*, cudaStream_t);
+    template cudaError_t launch_bulk<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>,          \
+                                        unsigned*, cudaStream_t, const Tuning&);                              \
+    template cudaError_t launch_sync<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, cudaStream_t);  \
+    template cudaError_t launch_extract_rows<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, int, int, \
+                                                int, double*, cudaStream_t);                                  \
+    template cudaError_t launch_norms<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, int,            \
+                                         const double*, double*, double*, cudaStream_t);                     \
+    template cudaError_t launch_boundary_batch<P>(const DomDesc<P>*, const BndTask*, int, int, int, int,      \
+                                                  cudaStream_t);                                              \
+    template cudaError_t launch_bulk_batch<P>(const DomDesc<P>*, const BulkTask*, int, int, int, cudaStream_t);
 
-LBPS_INSTANTIATE(float)
-LBPS_INSTANTIATE(double)
-
-template cudaError_t launch_boundary_batch<float>(const DomDesc<float>*, const BndTask*, int, int, int, int,
-                                                  cudaStream_t);
-template cudaError_t launch_boundary_batch<double>(const DomDesc<double>*, const BndTask*, int, int, int, int,
-                                                   cudaStream_t);
-template cudaError_t launch_bulk_batch<float>(const DomDesc<float>*, const BulkTask*, int, int, int, cudaStream_t);
-template cudaError_t launch_bulk_batch<double>(const DomDesc<double>*, const BulkTask*, int, int, int, cudaStream_t);
+LBPS_INSTANTIATE(PopDirect<float>)
+LBPS_INSTANTIATE(PopDirect<double>)
+LBPS_INSTANTIATE(PopNeq16<__nv_bfloat16>)
+LBPS_INSTANTIATE(PopNeq16<__half>)
 
 }  // namespace lbps

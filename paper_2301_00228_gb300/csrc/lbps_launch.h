@@ -5,46 +5,60 @@
 
 namespace lbps {
 
-template <typename T>
-cudaError_t launch_init(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, const double* ux0,
-                        const double* uy0, const double* vx0, const double* vy0, cudaStream_t st);
+template <typename P>
+using KCof = KC<typename P::V>;
+
+// The storage policies the library is built for (lbps_device.cuh), by
+// LBPS_STORAGE_* code.
+using PolF32 = PopDirect<float>;
+using PolF64 = PopDirect<double>;
+using PolBF16 = PopNeq16<__nv_bfloat16>;
+using PolF16 = PopNeq16<__half>;
+
+// Largest per-point estimate of |J| (scale_probe_kernel): FP32 bits
+// of a non-negative value, atomically maxed into *out (zero it first).
+cudaError_t launch_scale_probe(const Geo& g, const Consts& c, const double* u, double sq, unsigned* out,
+                               cudaStream_t st);
+
+template <typename P>
+cudaError_t launch_init(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, cudaStream_t st);
 
 // One time step A (time t) -> B (time t + dt) on one stream: boundary passes
 // 0-1 (stress, Newmark), launch_bulk, boundary pass 2 (reset).  sig: scratch
 // of 2 * nb * 3 doubles (stresses of the boundary cells).
-template <typename T>
-cudaError_t launch_boundary(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B,
+template <typename P>
+cudaError_t launch_boundary(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B,
                             const BNode* bn, int nb, double* sig, unsigned* flag, cudaStream_t st, int pass_lo,
                             int pass_hi);
 // Launch shape of the bulk kernel: variant selects the register budget (0: 6
-// blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8), rows_per_warp the height of
-// the strip each warp marches over.  Results do not depend on either.
+// blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8) with u, du/dt prefetched two
+// rows ahead like the populations; variants 4..7 the same budgets with u,
+// du/dt one row ahead (fewer registers, less memory in flight).
+// rows_per_warp is the height of the strip each warp marches over.  Results
+// do not depend on either.
 struct Tuning {
     int variant = 0;
     int rows_per_warp = 32;
 };
-constexpr int kTuningVariants = 4;
-template <typename T>
-cudaError_t launch_bulk(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, View<T> B, unsigned* flag,
+constexpr int kTuningVariants = 8;
+template <typename P>
+cudaError_t launch_bulk(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, unsigned* flag,
                         cudaStream_t st, const Tuning& tu);
 
-template <typename T>
-cudaError_t launch_sync(const Geo& g, const Consts& c, const KC<T>& k, View<T> A, cudaStream_t st);
+template <typename P>
+cudaError_t launch_sync(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, cudaStream_t st);
 
-// Dense FP64 copy of one field (ids of lbps.h).
-template <typename T>
-cudaError_t launch_extract(const Geo& g, const Consts& c, View<T> A, int field, double* dst, cudaStream_t st);
-
-// Rows [j0, j0 + rows) only, into a dense [rows][nx] (x5 for populations) buffer.
-template <typename T>
-cudaError_t launch_extract_rows(const Geo& g, const Consts& c, View<T> A, int field, int j0, int rows,
-                                double* dst, cudaStream_t st);
+// Rows [j0, j0 + rows) of one field (ids of lbps.h) into a dense FP64
+// [rows][nx] (x5 for populations) buffer.
+template <typename P>
+cudaError_t launch_extract_rows(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, int field, int j0,
+                                int rows, double* dst, cudaStream_t st);
 
 // FP64 reductions of one scalar field against an optional reference;
 // partials: scratch of at least kNormBlocks * 4 doubles.
 constexpr int kNormBlocks = 1024;
-template <typename T>
-cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, const double* ref,
+template <typename P>
+cudaError_t launch_norms(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, int field, const double* ref,
                          double* partials, double* out4, cudaStream_t st);
 
 // ---- batches: many lattices advanced by one launch of each kernel per step
@@ -52,12 +66,12 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, View<T> A, int field, co
 // Everything the kernels need about one lattice of a batch.  v[cur] holds the
 // state at the start of a batch step pair; a step with parity p reads
 // v[cur ^ p] and writes v[cur ^ p ^ 1].
-template <typename T>
+template <typename P>
 struct DomDesc {
     Geo g;
     Consts c;
-    KC<T> k;
-    View<T> v[2];
+    KCof<P> k;
+    View<P> v[2];
     const BNode* bn;
     double* sig;
     unsigned* flag;
@@ -75,11 +89,11 @@ struct BndTask {   // one thread: boundary point b of lattice dom
 
 constexpr int kBatchStripCols = 30;  // output columns per warp task
 
-template <typename T>
-cudaError_t launch_boundary_batch(const DomDesc<T>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
+template <typename P>
+cudaError_t launch_boundary_batch(const DomDesc<P>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
                                   int pass_hi, cudaStream_t st);
-template <typename T>
-cudaError_t launch_bulk_batch(const DomDesc<T>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
+template <typename P>
+cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
                               cudaStream_t st);
 
 // Checked builds (LBPS_CHECKED): the device block every kernel access must

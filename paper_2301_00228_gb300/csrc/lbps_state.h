@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include "lbps.h"
@@ -12,8 +13,7 @@ namespace lbps {
 // Placement of everything in a lattice's device block.
 struct Layout {
     Geo g;
-    size_t elem;        // bytes per population value
-    size_t f_bytes;     // 10 population planes, aligned
+    size_t f_bytes;     // population planes (layout of the storage policy), aligned
     size_t u_bytes;     // 4 FP64 planes, aligned
     size_t copy_bytes;
     size_t off_copy[2];
@@ -22,6 +22,17 @@ struct Layout {
     size_t total;
     int nb;
 };
+
+// Calls fn with a value of the storage policy type of an LBPS_STORAGE_* code.
+template <typename Fn>
+auto with_policy(int32_t storage, Fn&& fn) {
+    switch (storage) {
+    case LBPS_STORAGE_F64: return fn(PolF64{});
+    case LBPS_STORAGE_BF16: return fn(PolBF16{});
+    case LBPS_STORAGE_F16: return fn(PolF16{});
+    default: return fn(PolF32{});
+    }
+}
 
 }  // namespace lbps
 
@@ -32,6 +43,9 @@ struct lbps_lattice {
     lbps::KC<float> kf;
     lbps::KC<double> kd;
     double cd, cs, a_phi, a_psi, a0_psi;
+    double bc_est = 0.0;  // boundary values' share of the 16-bit scale estimate
+    int scale_exp = 0;    // 16-bit storage: Nx, Ny are stored times 2^scale_exp
+    int64_t gen = 0;      // incremented by every init (batches re-read descriptors)
     cudaStream_t st;
     char* mem;
     bool owns;
@@ -46,12 +60,20 @@ struct lbps_lattice {
     size_t ev_used = 0;
     std::vector<int> ev_kind;   // per recorded pair: 0 bulk, 1 boundary
 
-    template <typename T>
-    lbps::View<T> view(int q) const {
-        lbps::View<T> v;
-        v.f = reinterpret_cast<T*>(mem + L.off_copy[q]);
-        v.u = reinterpret_cast<double*>(mem + L.off_copy[q] + L.f_bytes);
+    template <typename P>
+    lbps::View<P> view(int q) const {
+        lbps::View<P> v;
+        v.f = reinterpret_cast<typename P::Base*>(mem + L.off_copy[q]);
+        v.u = u(q);
         return v;
+    }
+    double* u(int q) const { return reinterpret_cast<double*>(mem + L.off_copy[q] + L.f_bytes); }
+    template <typename P>
+    const lbps::KCof<P>& kc() const {
+        if constexpr (std::is_same<typename P::V, double>::value)
+            return kd;
+        else
+            return kf;
     }
     const lbps::BNode* bn() const { return reinterpret_cast<const lbps::BNode*>(mem + L.off_bn); }
     double* sig() const { return reinterpret_cast<double*>(mem + L.off_sig); }
@@ -59,5 +81,5 @@ struct lbps_lattice {
     double* partials() const { return reinterpret_cast<double*>(mem + L.off_part); }
     double* out4() const { return reinterpret_cast<double*>(mem + L.off_out); }
     double* staging() const { return reinterpret_cast<double*>(mem + L.off_staging); }
-    bool f64() const { return p.storage == LBPS_STORAGE_F64; }
+    bool neq16() const { return p.storage == LBPS_STORAGE_BF16 || p.storage == LBPS_STORAGE_F16; }
 };

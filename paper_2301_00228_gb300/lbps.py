@@ -29,11 +29,12 @@ LBPS_ERR_TIMEOUT = -5
 LBPS_ERR_STATE = -6
 
 LBPS_INTERIOR, LBPS_NEUMANN, LBPS_DIRICHLET = 0, 1, 2
-LBPS_STORAGE_F32, LBPS_STORAGE_F64 = 0, 1
+LBPS_STORAGE_F32, LBPS_STORAGE_F64, LBPS_STORAGE_BF16, LBPS_STORAGE_F16 = 0, 1, 2, 3
 LBPS_UX, LBPS_UY, LBPS_VX, LBPS_VY, LBPS_PHI, LBPS_PSI, LBPS_F_PHI, LBPS_F_PSI, LBPS_CONSISTENCY = range(9)
 FIELDS = {"ux": LBPS_UX, "uy": LBPS_UY, "vx": LBPS_VX, "vy": LBPS_VY, "phi": LBPS_PHI, "psi": LBPS_PSI,
           "f_phi": LBPS_F_PHI, "f_psi": LBPS_F_PSI, "consistency": LBPS_CONSISTENCY}
-STORAGES = {"f32": LBPS_STORAGE_F32, "f64": LBPS_STORAGE_F64}
+STORAGES = {"f32": LBPS_STORAGE_F32, "f64": LBPS_STORAGE_F64, "bf16": LBPS_STORAGE_BF16,
+            "f16": LBPS_STORAGE_F16}
 
 
 class lbps_params(ctypes.Structure):
@@ -42,7 +43,8 @@ class lbps_params(ctypes.Structure):
                 ("dh", ctypes.c_double), ("a0_phi", ctypes.c_double),
                 ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
                 ("bc_feq_mode", ctypes.c_int32), ("sync_every", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("cuda_stream", ctypes.c_void_p)]
+                ("storage", ctypes.c_int32), ("pop_scale_exp", ctypes.c_int32),
+                ("cuda_stream", ctypes.c_void_p)]
 
 
 class LbpsError(RuntimeError):
@@ -77,6 +79,7 @@ def _load():
         "lbps_norms": (ctypes.c_int, [vp, i32, vp, vp]),
         "lbps_norms_noalloc": (ctypes.c_int, [vp, vp, sz, vp, vp]),
         "lbps_info": (ctypes.c_int, [vp, vp, P(i64)]),
+        "lbps_scale_exp": (ctypes.c_int, [vp, P(i32)]),
         "lbps_check_report": (ctypes.c_int, [vp]),
         "lbps_last_cuda_error": (ctypes.c_int, [vp]),
         "lbps_set_tuning": (ctypes.c_int, [vp, i32, i32]),
@@ -202,6 +205,12 @@ def lbps_info(h):
     return out, int(steps.value)
 
 
+def lbps_scale_exp(h):
+    e = ctypes.c_int32(0)
+    _check(_lib.lbps_scale_exp(h, ctypes.byref(e)), "lbps_scale_exp")
+    return int(e.value)
+
+
 def lbps_check_report():
     out = np.zeros(2, np.uint64)
     rc = _lib.lbps_check_report(_p(out))
@@ -238,15 +247,17 @@ class Lattice:
     """One lattice on the current CUDA device, its state in a torch tensor."""
 
     def __init__(self, nx, ny, lam, mu, rho=1.0, dh=1.0, a0_phi=0.9999, periodic_x=False, periodic_y=False,
-                 node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0, storage="f32", stream=None):
+                 node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0, storage="f32", pop_scale_exp=0,
+                 stream=None):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
         self._torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.params = lbps_params(self.nx, self.ny, lam, mu, rho, dh, a0_phi, int(periodic_x), int(periodic_y),
-                                  int(bc_feq_mode), int(sync_every), STORAGES[storage],
+                                  int(bc_feq_mode), int(sync_every), STORAGES[storage], int(pop_scale_exp),
                                   ctypes.c_void_p(self.stream.cuda_stream))
+        self.storage = storage
         self.nbytes = lbps_state_bytes(self.params)
         with torch.cuda.stream(self.stream):
             self._mem = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
@@ -309,6 +320,10 @@ class Lattice:
     @property
     def steps(self):
         return lbps_info(self._h)[1]
+
+    @property
+    def scale_exp(self):
+        return lbps_scale_exp(self._h)
 
     def read(self, field):
         fid = FIELDS[field] if isinstance(field, str) else int(field)

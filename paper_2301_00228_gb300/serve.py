@@ -71,7 +71,7 @@ class Report:
 
 def _params(d, storage):
     return lbps.lbps_params(d.nx, d.ny, d.lam, d.mu, d.rho, 1.0, d.a0_phi, int(d.periodic_x), int(d.periodic_y),
-                            0, 0, lbps.STORAGES[storage], None)
+                            0, 0, lbps.STORAGES[storage], 0, None)
 
 
 def footprint(d, storage="f32"):

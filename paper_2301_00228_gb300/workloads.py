@@ -204,6 +204,22 @@ def crop(domain: Domain, x0, y0, w, h):
                   steps=domain.steps)
 
 
+def busiest_crop(domain: Domain, side):
+    """Origin (x0, y0) of the side x side window holding the most pulse
+    centres (windows start on a grid of side / 4; the first in row-major
+    order among equals).  With ``crop`` it makes a stand-alone problem of the
+    same kind: the domain's edge types on the window's edges, the pulses
+    centred inside."""
+    step = max(1, side // 4)
+    best = None
+    for y0 in range(0, domain.ny - side + 1, step):
+        for x0 in range(0, domain.nx - side + 1, step):
+            n = sum(1 for (cx, cy, *_r) in domain.pulses if x0 <= cx < x0 + side and y0 <= cy < y0 + side)
+            if best is None or n > best[0]:
+                best = (n, x0, y0)
+    return best[1], best[2]
+
+
 def poisson_requests(count=10000, seed=5, rate_hz=1.0, side_lo=128, side_hi=2048, steps_lo=500,
                      steps_hi=20000):
     """Arrival times and domains of a serving stream: Poisson arrivals at

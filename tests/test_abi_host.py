@@ -62,7 +62,7 @@ def test_rect_bc_rejects(lib):
 
 
 def test_state_bytes(lib):
-    p = lib.lbps_params(100, 37, 1.0, 1.0, 1.0, 1.0, 0.9999, 0, 0, 0, 0, lib.LBPS_STORAGE_F32, None)
+    p = lib.lbps_params(100, 37, 1.0, 1.0, 1.0, 1.0, 0.9999, 0, 0, 0, 0, lib.LBPS_STORAGE_F32, 0, None)
     n32 = lib.lbps_state_bytes(p)
     p.storage = lib.LBPS_STORAGE_F64
     n64 = lib.lbps_state_bytes(p)
@@ -70,9 +70,25 @@ def test_state_bytes(lib):
     assert n32 >= 2 * px * 37 * (10 * 4 + 4 * 8)
     assert n64 >= 2 * px * 37 * (10 * 8 + 4 * 8)
     assert n64 > n32
+    for code in (lib.LBPS_STORAGE_BF16, lib.LBPS_STORAGE_F16):
+        p.storage = code
+        n16 = lib.lbps_state_bytes(p)
+        # FP32 f^0, Jx, Jy + two 16-bit sums per set: 32 B per point and copy
+        assert 2 * px * 37 * (32 + 4 * 8) <= n16 < n32
+        assert n32 - n16 >= 2 * px * 37 * 8
+        # a lattice 3 wide along a non-periodic axis is rejected, a periodic one is not
+        for nx, ny, pxp, pyp, ok in ((3, 37, 0, 0, False), (100, 3, 0, 0, False), (3, 37, 1, 0, True),
+                                     (100, 3, 0, 1, True), (4, 4, 0, 0, True)):
+            q = lib.lbps_params(nx, ny, 1.0, 1.0, 1.0, 1.0, 0.9999, pxp, pyp, 0, 0, code, 0, None)
+            if ok:
+                assert lib.lbps_state_bytes(q) > 0
+            else:
+                with pytest.raises(lib.LbpsError):
+                    lib.lbps_state_bytes(q)
     for bad in (dict(nx=2), dict(mu=0.0), dict(rho=-1.0), dict(a0_phi=1.0), dict(bc_feq_mode=2),
-                dict(storage=7), dict(sync_every=-1), dict(dh=0.0)):
-        q = lib.lbps_params(100, 37, 1.0, 1.0, 1.0, 1.0, 0.9999, 0, 0, 0, 0, 0, None)
+                dict(storage=7), dict(storage=-1), dict(sync_every=-1), dict(dh=0.0), dict(pop_scale_exp=101),
+                dict(pop_scale_exp=-101)):
+        q = lib.lbps_params(100, 37, 1.0, 1.0, 1.0, 1.0, 0.9999, 0, 0, 0, 0, 0, 0, None)
         for k, v in bad.items():
             setattr(q, k, v)
         with pytest.raises(lib.LbpsError):

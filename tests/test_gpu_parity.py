@@ -2,7 +2,12 @@
 
 Tolerances: FP64 population storage must match the oracle to round-off
 (relative L2 <= 1e-10 per field); FP32 storage within relative L2 <= 1e-5 per
-field.  Relative L2 is taken per field against max(||ref||, 1e-2 ||ref group||)
+field.  The 16-bit formats (FP32 moments, 16-bit non-equilibrium sums) are
+held to what they deliver on these runs, which is not the 1e-3 target
+everywhere: FP16 stays below 1e-3 except on the a_0 = 0.9 periodic case
+(1.7e-3 in u), BF16 reaches 1.4e-2 there and about 1e-3 to 8e-3 elsewhere
+(its 8-bit significand).  The 1e-3 target on the precision workload is
+asserted in test_gpu_precision.py.  Relative L2 is taken per field against max(||ref||, 1e-2 ||ref group||)
 where the groups are (ux, uy), (vx, vy), (phi, psi), so a field that is zero
 by symmetry is compared on the scale of its partner.
 """
@@ -17,7 +22,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 GROUPS = (("ux", "uy"), ("vx", "vy"), ("phi", "psi"))
-TOL = {"f64": 1e-10, "f32": 1e-5}
+TOL = {"f64": 1e-10, "f32": 1e-5, "bf16": 2e-2, "f16": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -119,16 +124,21 @@ def run_gpu(L, cs, storage):
     return f
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
 @pytest.mark.parametrize("k", range(len(MIXED)))
 def test_mixed_rectangles(L, k, storage):
     cs = MIXED[k]
+    if storage in ("bf16", "f16") and ((cs["nx"] == 3 and not cs["px"]) or (cs["ny"] == 3 and not cs["py"])):
+        with pytest.raises(L.LbpsError) as e:       # 16-bit storage needs 4 points across
+            run_gpu(L, cs, storage)
+        assert e.value.code == L.LBPS_ERR_INVALID
+        return
     assert_parity(run_gpu(L, cs, storage), run_oracle(cs), TOL[storage], (k, storage))
 
 
 # ------------------------------------------------- the 64 x 64 problem
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
 def test_square_64_1000_steps(L, storage):
     """64 x 64, left edge clamped, others traction-free, centred dilatation pulse
     sigma = 4, lambda = mu = rho = 1, a_{0,phi} = 0.9999, 1000 steps."""
@@ -329,7 +339,7 @@ def test_device_init_equals_host_init(L):
 
 def test_library_owned_memory(L):
     """device_mem = NULL: the library allocates and frees the state itself."""
-    p = L.lbps_params(24, 20, 1.0, 1.0, 1.0, 1.0, 0.99, 1, 1, 0, 0, L.LBPS_STORAGE_F32, None)
+    p = L.lbps_params(24, 20, 1.0, 1.0, 1.0, 1.0, 0.99, 1, 1, 0, 0, L.LBPS_STORAGE_F32, 0, None)
     h = L.lbps_create(p, None, None, 0, 0)
     ux, uy = W.pulse_displacement(24, 20, 10.0, 9.0, 2.0, 1e-3, "dilatation")
     L.lbps_init(h, np.ascontiguousarray(ux), np.ascontiguousarray(uy))
@@ -382,20 +392,21 @@ def test_tunings_bit_identical(L):
     """Every launch shape of the interior kernel gives the same bits (ragged strip
     and row counts included)."""
     cs = mixed_case(21, 97, 83, steps=40)
-    ref = None
-    for variant in range(4):
-        for rows in (1, 7, 64, 4096):
-            lat = L.Lattice.rectangle(cs["nx"], cs["ny"], cs["lam"], 1.0, cs["et"], cs["ev"], a0_phi=cs["a0"],
-                                      storage="f32")
-            L.lbps_set_tuning(lat._h, variant, rows)
-            f = lat.init(cs["ux"], cs["uy"]).step(cs["steps"]).fields()
-            lat.close()
-            if ref is None:
-                ref = f
-                assert_parity(f, run_oracle(cs), TOL["f32"])
-            for k in f:
-                assert np.array_equal(f[k], ref[k]), (variant, rows, k)
+    for storage in ("f32", "f16"):
+        ref = None
+        for variant in range(8):
+            for rows in (1, 7, 64, 4096):
+                lat = L.Lattice.rectangle(cs["nx"], cs["ny"], cs["lam"], 1.0, cs["et"], cs["ev"], a0_phi=cs["a0"],
+                                          storage=storage)
+                L.lbps_set_tuning(lat._h, variant, rows)
+                f = lat.init(cs["ux"], cs["uy"]).step(cs["steps"]).fields()
+                lat.close()
+                if ref is None:
+                    ref = f
+                    assert_parity(f, run_oracle(cs), TOL[storage])
+                for k in f:
+                    assert np.array_equal(f[k], ref[k]), (storage, variant, rows, k)
     small = L.Lattice(8, 8, 1.0, 1.0, periodic_x=True, periodic_y=True)
-    for bad in ((4, 64), (-1, 64), (0, 0), (0, 5000)):
+    for bad in ((8, 64), (-1, 64), (0, 0), (0, 5000)):
         with pytest.raises(L.LbpsError):
             L.lbps_set_tuning(small._h, *bad)
