@@ -199,16 +199,16 @@ int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out
 int lbps_norms_noalloc(const double* d_x, const double* d_ref, size_t n, void* cuda_stream, double out[4]);
 
 /* ---- Batches: many lattices of different sizes, materials and edges
- * advanced together.  Each time step is one launch of the boundary kernel
- * over the boundary points of every lattice and one launch of the interior
- * kernel over a work list of strips of every lattice (the same per-point
- * arithmetic as lbps_step, so every lattice gets the same bits as when
- * stepped alone).  Pairs of steps are captured once into a CUDA graph and
+ * advanced together.  Each time step is one launch of each boundary pass
+ * (stress, Newmark, reset) over the boundary points of every lattice and one
+ * launch of the interior kernel over a work list of strips of every lattice
+ * (the same per-point arithmetic as lbps_step, so every lattice gets the
+ * same bits as when stepped alone).  Pairs of steps are captured once into a CUDA graph and
  * replayed.  The paper has no counterpart; this serves many solves at once. */
 typedef struct lbps_batch lbps_batch; /* opaque, library-owned */
 
-/* lats[count]: distinct, initialised lattices, all FP32 or all FP64, with
- * sync_every == 0.  The batch keeps the pointers (not the lattices): destroy
+/* lats[count]: distinct, initialised lattices, all of one storage format,
+ * with sync_every == 0.  The batch keeps the pointers (not the lattices): destroy
  * the batch before any of its lattices.  cuda_stream: stream for the batch's
  * work (NULL: a blocking stream of the batch's own, ordered with the legacy
  * default stream).  Allocates a small device block for descriptors and work

@@ -1,5 +1,5 @@
 // Batches of lattices (lbps_batch_* in include/lbps.h): every lattice of a
-// batch advances by one launch of the boundary kernel and one launch of the
+// batch advances by one launch of each boundary pass and one launch of the
 // interior kernel per time step, driven by device-side work lists; pairs of
 // steps are captured once in a CUDA graph and replayed.
 #include <algorithm>
@@ -29,6 +29,8 @@ struct lbps_batch {
     std::vector<int64_t> uploaded_gen;
     cudaGraphExec_t graph = nullptr;
     cudaEvent_t order = nullptr;  // orders the batch stream with the lattices' streams
+    cudaStream_t side = nullptr;  // boundary stress and Newmark passes, beside the interior kernel
+    cudaEvent_t fork = nullptr, join = nullptr;
     int last_cuda = 0;
 };
 
@@ -102,15 +104,23 @@ int upload(lbps_batch* b) {
 }
 
 // One time step of every lattice: parity 0 reads v[cur], parity 1 v[cur ^ 1].
-// Boundary stress and Newmark passes, the interior kernel, boundary reset.
+// The boundary stress and Newmark passes run on the side stream beside the
+// interior kernel: they read copy A and write only the boundary points' u,
+// du/dt of copy B and the stress scratch, none of which the interior kernel
+// touches.  The boundary reset waits for both (it reads the interior kernel's
+// new u and overwrites populations it wrote).
 cudaError_t launch_step(lbps_batch* b, int parity) {
     const BndTask* bt = reinterpret_cast<const BndTask*>(b->mem + b->off_bnd);
     const BulkTask* wt = reinterpret_cast<const BulkTask*>(b->mem + b->off_bulk);
     return lbps::with_policy(b->storage, [&](auto pol) {
         using P = decltype(pol);
         const DomDesc<P>* dd = reinterpret_cast<const DomDesc<P>*>(b->mem);
-        cudaError_t e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 0, 2, b->st);
+        cudaError_t e = cudaEventRecord(b->fork, b->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
+        if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 0, 2, b->side);
+        if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
         if (e == cudaSuccess) e = lbps::launch_bulk_batch<P>(dd, wt, b->nbulk, parity, b->variant, b->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->join, 0);
         if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 2, 3, b->st);
         return e;
     });
@@ -183,7 +193,10 @@ int lbps_batch_create(lbps_lattice* const* lats, int32_t count, void* cuda_strea
         }
         b->own_stream = true;
     }
-    if (cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) {
         lbps_batch_destroy(b);
         return LBPS_ERR_CUDA;
     }
@@ -326,9 +339,13 @@ int lbps_batch_last_cuda_error(const lbps_batch* b) { return b ? b->last_cuda : 
 void lbps_batch_destroy(lbps_batch* b) {
     if (!b) return;
     if (b->st) cudaStreamSynchronize(b->st);
+    if (b->side) cudaStreamSynchronize(b->side);
     drop_graph(b);
     if (b->mem) cudaFree(b->mem);
     if (b->order) cudaEventDestroy(b->order);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->side) cudaStreamDestroy(b->side);
     if (b->own_stream) cudaStreamDestroy(b->st);
     delete b;
 }
