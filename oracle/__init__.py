@@ -40,6 +40,7 @@ PINS = {
     "linearity / mirror symmetry": "tests/test_oracle_pins.py::test_linearity, ::test_mirror_symmetry",
     "synchronisation (Sec. 3.2)": "tests/test_oracle_pins.py::test_sync_*",
     "rectangle boundary helper": "tests/test_oracle_pins.py::test_rect_bc_*",
+    "time-dependent boundary data (readings R12, R13)": "tests/test_oracle_pins.py::test_load_ramp_*",
 }
 # Readings with no pin against the paper itself.
 PARITY_UNPINNED = (
@@ -85,6 +86,7 @@ def lib():
         L.ora_constants.argtypes = [vp, dp]
         L.ora_init.argtypes = [vp, vp, vp, vp, vp]
         L.ora_step.argtypes = [vp, ctypes.c_int64]
+        L.ora_set_load.argtypes = [vp, ctypes.c_int32, ctypes.c_double, ctypes.c_double]
         L.ora_sync.argtypes = [vp]
         L.ora_read.argtypes = [vp, ctypes.c_int32, vp]
         L.ora_steps_done.restype = ctypes.c_int64
@@ -148,6 +150,13 @@ class OracleLattice:
              for x in (ux0, uy0, vx0, vy0)]
         if lib().ora_init(self._h, *[_ptr(x) for x in a]) != 0:
             raise ValueError("non-finite initial data")
+        return self
+
+    def set_load(self, kind, t_ramp, t_hold=float("inf")):
+        """Ramp-then-hold factor on the boundary data of one kind (1 Neumann,
+        2 Dirichlet): s(t) = min(t, t_hold) / t_ramp; t_ramp = 0: constant."""
+        if lib().ora_set_load(self._h, int(kind), float(t_ramp), float(t_hold)) != 0:
+            raise ValueError("ora_set_load: bad arguments")
         return self
 
     def step(self, n=1):

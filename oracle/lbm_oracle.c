@@ -50,7 +50,14 @@
  *       modes whose acceleration feeds back on u (boundary points) grow by
  *       about 1 + (omega dt)^2 / 4 per step, which is why small a_phi (the
  *       paper's a_{0,phi} = 0.9999, Sec. 4) is needed for stability.
- *   R12 Dirichlet u* is constant in time, so u*(t) and u*(t+dt) coincide.
+ *   R12 Boundary data may vary in time as u*(t) = s_D(t) u*, F(t) = s_N(t) F
+ *       with a ramp-then-hold factor s(t) = min(t, t_hold) / t_ramp (s = 1
+ *       without a schedule; Sec. 4 ramps the traction of its tension and
+ *       shear examples this way).  R13 says at which times they are taken.
+ *   R13 The Neumann force enters the acceleration at t with its value at t
+ *       (like the stresses, Eq. acc_neumann); the Dirichlet target is
+ *       u*(t + dt), the displacement the point must have after the step
+ *       (Eq. acc_dirichlet lands u(t + dt) on it).
  */
 #include "lbm_oracle.h"
 
@@ -78,6 +85,8 @@ struct ora_lattice {
     double *ux1, *uy1, *vx1, *vy1;  /* u, du/dt at t + dt */
     double* s[2];         /* phi, psi at t */
     double *ax, *ay;      /* acceleration at t */
+    double load_rate[2];  /* 1 / t_ramp of the Neumann [0] and Dirichlet [1] data; 0 = constant */
+    double load_hold[2];  /* t_hold: the factor stays at t_hold / t_ramp from there on */
     int64_t steps;
     int initialised;
 };
@@ -318,6 +327,20 @@ static void accel_interior(const ora_lattice* L, int i, int j, double* ax, doubl
     *ay = cd2 * dphi_dy + cs2 * dpsi_dx;
 }
 
+/* Time factor of the boundary data of one kind (0 Neumann, 1 Dirichlet) at
+ * time t (reading R12). */
+static double load_factor(const ora_lattice* L, int kind, double t) {
+    if (!(L->load_rate[kind] > 0.0)) return 1.0;
+    return L->load_rate[kind] * fmin(t, L->load_hold[kind]);
+}
+
+int ora_set_load(ora_lattice* L, int32_t kind, double t_ramp, double t_hold) {
+    if (!L || (kind != 1 && kind != 2) || !(t_ramp >= 0.0) || !isfinite(t_ramp) || !(t_hold > 0.0)) return -1;
+    L->load_rate[kind - 1] = t_ramp > 0.0 ? 1.0 / t_ramp : 0.0;
+    L->load_hold[kind - 1] = t_hold;
+    return 0;
+}
+
 /* Neumann points: momentum balance of the boundary cell, Eq.
  * contBalanceOfMomentum simplified to Eq. acc_neumann (readings R5, R6). */
 static void accel_neumann(const ora_lattice* L, int i, int j, double* ax, double* ay) {
@@ -334,8 +357,10 @@ static void accel_neumann(const ora_lattice* L, int i, int j, double* ax, double
     double vol = wx * wy;
     double sk[3];
     stress(L, L->ux, L->uy, i, j, sk);
-    /* External part: integral of t* over dC_ext, supplied per point. */
-    double fx = L->bc[2 * k], fy = L->bc[2 * k + 1];
+    /* External part: integral of t* over dC_ext, supplied per point, at t
+     * (readings R12, R13). */
+    double sn = load_factor(L, 0, (double)L->steps * L->dt);
+    double fx = sn * L->bc[2 * k], fy = sn * L->bc[2 * k + 1];
     /* Internal part: one face per neighbour r, normal n_kr pointing to r,
      * length l_kr, stress sigma_kr = (sigma_k + sigma_r)/2. */
     for (int a = 1; a < 5; ++a) {
@@ -355,12 +380,14 @@ static void accel_neumann(const ora_lattice* L, int i, int j, double* ax, double
     *ay = fy / (L->p.rho * vol);
 }
 
-/* Dirichlet points: Eq. acc_dirichlet (reading R12). */
+/* Dirichlet points: Eq. acc_dirichlet with the target u*(t + dt) (readings
+ * R12, R13). */
 static void accel_dirichlet(const ora_lattice* L, int i, int j, double* ax, double* ay) {
     long k = at(L, i, j);
     double dt = L->dt;
-    *ax = 2.0 / (dt * dt) * (L->bc[2 * k] - L->ux[k]) - 2.0 / dt * L->vx[k];
-    *ay = 2.0 / (dt * dt) * (L->bc[2 * k + 1] - L->uy[k]) - 2.0 / dt * L->vy[k];
+    double s = load_factor(L, 1, (double)(L->steps + 1) * dt);
+    *ax = 2.0 / (dt * dt) * (s * L->bc[2 * k] - L->ux[k]) - 2.0 / dt * L->vx[k];
+    *ay = 2.0 / (dt * dt) * (s * L->bc[2 * k + 1] - L->uy[k]) - 2.0 / dt * L->vy[k];
 }
 
 /* Moments phi, psi of the current populations (Eq. interpretation). */

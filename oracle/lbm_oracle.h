@@ -57,6 +57,13 @@ void ora_constants(const ora_lattice* L, double out[6]);
 int ora_init(ora_lattice* L, const double* ux0, const double* uy0,
              const double* vx0, const double* vy0);
 
+/* Time-dependent boundary data (readings R12, R13): the values of one kind
+ * (1 Neumann forces, 2 Dirichlet targets) are multiplied by
+ * s(t) = min(t, t_hold) / t_ramp; t_ramp = 0 restores constant data.  The
+ * Neumann force at step n uses t = n dt, the Dirichlet target t = (n+1) dt.
+ * t_hold may be +infinity (a ramp without hold).  Returns -1 on bad input. */
+int ora_set_load(ora_lattice* L, int32_t kind, double t_ramp, double t_hold);
+
 /* Time loop of Fig. 3, n iterations. */
 int ora_step(ora_lattice* L, int64_t n);
 

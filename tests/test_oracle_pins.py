@@ -458,3 +458,69 @@ def test_rejects_bad_masks():
         O.OracleLattice(6, 5, 1.0, 1.0, node_type=nt, bc_value=bv)
     with pytest.raises(ValueError):
         O.OracleLattice(2, 5, 1.0, 1.0, periodic_x=True, periodic_y=True)
+
+
+# ------------------------------------------- time-dependent boundary data
+
+STATE_FIELDS = (O.UX, O.UY, O.VX, O.VY, O.F_PHI, O.F_PSI)
+
+
+def _loaded_lattice(et, ev, a0=0.99):
+    nt, bv = O.rect_bc(12, 10, et, ev)
+    return O.OracleLattice(12, 10, 1.7, 1.0, a0_phi=a0, node_type=nt, bc_value=bv)
+
+
+def _state(lat):
+    return [lat.read(f).copy() for f in STATE_FIELDS]
+
+
+@pytest.mark.parametrize("kind,et", [(1, (1, 1, 1, 1)), (2, (2, 1, 2, 1))])
+@pytest.mark.parametrize("ramp,hold", [(7, 7), (5, 13), (9, 1e9)])
+def test_load_ramp_superposition(kind, et, ramp, hold):
+    """The scheme is linear and time-invariant in the boundary data, so from a
+    body at rest the state after N steps under data s_n g is
+    sum_n s_n (y_{N-n} - y_{N-n-1}), with y_m the state after m steps under
+    constant data g.  The factor of step n is s(n dt) for Neumann forces and
+    s((n+1) dt) for Dirichlet targets (reading R13); a wrong time index, a
+    missing hold or a factor on the wrong kind of point breaks the identity."""
+    ev = np.array([3e-4, -2e-4, 1e-4, 5e-4, -4e-4, 2e-4, 1.5e-4, -1e-4])
+    # only the ramped kind carries data (the other kind's edges are traction-free)
+    ev = np.where(np.repeat(np.asarray(et) == kind, 2), ev, 0.0)
+    N = 24
+    zero = np.zeros((10, 12))
+    const = _loaded_lattice(et, ev).init(zero, zero)
+    y = [_state(const)]
+    for _ in range(N):
+        const.step(1)
+        y.append(_state(const))
+    ramped = _loaded_lattice(et, ev).init(zero, zero)
+    dt = ramped.dt
+    ramped.set_load(kind, ramp * dt, hold * dt)
+    ramped.step(N)
+    got = _state(ramped)
+    shift = 0 if kind == 1 else 1
+    s = [min((n + shift) * dt, hold * dt) / (ramp * dt) for n in range(N)]
+    for q, g in enumerate(got):
+        want = sum(s[n] * (y[N - n][q] - y[N - n - 1][q]) for n in range(N))
+        scale = max(np.abs(want).max(), 1e-300)
+        assert np.abs(g - want).max() <= 1e-11 * scale, (STATE_FIELDS[q], np.abs(g - want).max() / scale)
+    assert np.abs(got[0]).max() > 0
+
+
+def test_load_ramp_only_scales_its_kind():
+    """A schedule on one kind leaves the other kind's data constant: with
+    Dirichlet edges only, a Neumann schedule changes nothing; t_ramp = 0
+    restores constant data."""
+    ev = np.array([3e-4, -2e-4, 1e-4, 5e-4, -4e-4, 2e-4, 1.5e-4, -1e-4])
+    zero = np.zeros((10, 12))
+    a = _loaded_lattice((2, 2, 2, 2), ev).init(zero, zero).step(15)
+    b = _loaded_lattice((2, 2, 2, 2), ev).init(zero, zero)
+    b.set_load(1, 4 * b.dt, 4 * b.dt).step(15)
+    c = _loaded_lattice((2, 2, 2, 2), ev).init(zero, zero)
+    c.set_load(2, 4 * c.dt).set_load(2, 0.0).step(15)
+    for f in STATE_FIELDS:
+        assert np.array_equal(a.read(f), b.read(f)) and np.array_equal(a.read(f), c.read(f))
+    with pytest.raises(ValueError):
+        a.set_load(3, 1.0)
+    with pytest.raises(ValueError):
+        a.set_load(1, -1.0)
