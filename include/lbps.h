@@ -201,10 +201,11 @@ int lbps_norms_noalloc(const double* d_x, const double* d_ref, size_t n, void* c
 /* ---- Batches: many lattices of different sizes, materials and edges
  * advanced together.  Each time step is one launch of each boundary pass
  * (stress, Newmark, reset) over the boundary points of every lattice and one
- * launch of the interior kernel over a work list of strips of every lattice
- * (the same per-point arithmetic as lbps_step, so every lattice gets the
- * same bits as when stepped alone).  Pairs of steps are captured once into a CUDA graph and
- * replayed.  The paper has no counterpart; this serves many solves at once. */
+ * launch of the interior kernel, a persistent grid whose warps take strips
+ * of every lattice from a work list (the same per-point arithmetic as
+ * lbps_step, so every lattice gets the same bits as when stepped alone).
+ * Pairs of steps are captured once into a CUDA graph and replayed.  The
+ * paper has no counterpart; this serves many solves at once. */
 typedef struct lbps_batch lbps_batch; /* opaque, library-owned */
 
 /* lats[count]: distinct, initialised lattices, all of one storage format,
@@ -244,6 +245,19 @@ void lbps_batch_destroy(lbps_batch* b);
  * out[2] a_phi, out[3] a_psi, out[4] a_{0,psi}, out[5] Delta t; and the
  * number of completed time steps. */
 int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done);
+
+/* Time-dependent boundary data (Sec. 4: the tension example ramps its
+ * traction linearly to 0.005 mu at t = L/c_s and holds it; the shear example
+ * ramps without end).  The values of one kind (kind = LBPS_NEUMANN: the
+ * forces F, LBPS_DIRICHLET: the targets u*) given to lbps_create are
+ * multiplied by s(t) = min(t, t_hold) / t_ramp, with t = n dt after n steps:
+ * the Neumann force of a step is taken at its start t_n, the Dirichlet
+ * target at its end t_{n+1} (the displacement the point lands on).
+ * t_ramp = 0 restores constant data; t_hold may be +infinity.  The step
+ * count n is kept on the device (reset by init, advanced by every step of
+ * lbps_step or a batch).  LBPS_ERR_INVALID for another kind, t_ramp < 0 or
+ * not finite, or t_hold <= 0.  The paper gives no more general schedule. */
+int lbps_set_load(lbps_lattice* lat, int32_t kind, double t_ramp, double t_hold);
 
 /* The exponent e of the 16-bit storage scale in use (Nx, Ny are stored
  * times 2^e; fixed by pop_scale_exp or chosen by the last init); 0 for FP32

@@ -138,8 +138,8 @@ cudaError_t boundary_passes(lbps_lattice* lat, int a, int b, int pass_lo, int pa
         e = lbps::with_policy(lat->p.storage, [&](auto pol) {
             using P = decltype(pol);
             return lbps::launch_boundary<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(a), lat->view<P>(b),
-                                            lat->bn(), lat->L.nb, lat->sig(), lat->flag(), lat->st, pass_lo,
-                                            pass_hi);
+                                            lat->bn(), lat->L.nb, lat->sig(), lat->flag(), lat->tstep(), lat->st,
+                                            pass_lo, pass_hi);
         });
     if (e == cudaSuccess) e = prof_mark(lat);
     if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(1);
@@ -231,7 +231,8 @@ int init_from(lbps_lattice* lat, const double* ux0, const double* uy0, const dou
                                : cudaMemset2DAsync(dst, dp, 0, sp, g.ny, lat->st);
         if (e != cudaSuccess) return LBPS_ERR_CUDA;
     }
-    if (cudaMemsetAsync(lat->flag(), 0, sizeof(unsigned), lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
+    // the non-finite flag and the step counter beside it
+    if (cudaMemsetAsync(lat->flag(), 0, 16, lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
     if (lat->neq16()) {
         int rc = choose_scale(lat);
         if (rc != LBPS_OK) return rc;
@@ -551,6 +552,16 @@ int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done) {
         out[5] = lat->c.dt;
     }
     if (steps_done) *steps_done = lat->steps;
+    return LBPS_OK;
+}
+
+int lbps_set_load(lbps_lattice* lat, int32_t kind, double t_ramp, double t_hold) {
+    if (!lat || (kind != LBPS_NEUMANN && kind != LBPS_DIRICHLET)) return LBPS_ERR_INVALID;
+    if (!(t_ramp >= 0.0) || !std::isfinite(t_ramp) || !(t_hold > 0.0)) return LBPS_ERR_INVALID;
+    const int q = kind == LBPS_NEUMANN ? 0 : 1;
+    lat->c.load_rate[q] = t_ramp > 0.0 ? 1.0 / t_ramp : 0.0;
+    lat->c.load_hold[q] = t_hold;
+    lat->gen += 1;  // batches holding this lattice re-read its descriptor
     return LBPS_OK;
 }
 

@@ -22,7 +22,7 @@ struct lbps_batch {
     bool own_stream = false;
     char* mem = nullptr;          // descriptors | boundary tasks | bulk tasks
     size_t mem_bytes = 0;
-    size_t off_bnd = 0, off_bulk = 0;
+    size_t off_bnd = 0, off_bulk = 0, off_next = 0;
     int nbnd = 0, nbulk = 0;
     int variant = 0, rows = 32;
     std::vector<int> uploaded_cur;
@@ -49,6 +49,7 @@ DomDesc<P> make_desc(const lbps_lattice* lat) {
     d.bn = lat->bn();
     d.sig = lat->sig();
     d.flag = lat->flag();
+    d.tstep = lat->tstep();
     d.nb = lat->L.nb;
     d.cur = lat->cur;
     return d;
@@ -119,7 +120,8 @@ cudaError_t launch_step(lbps_batch* b, int parity) {
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
         if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 0, 2, b->side);
         if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
-        if (e == cudaSuccess) e = lbps::launch_bulk_batch<P>(dd, wt, b->nbulk, parity, b->variant, b->st);
+        unsigned* next = reinterpret_cast<unsigned*>(b->mem + b->off_next);
+        if (e == cudaSuccess) e = lbps::launch_bulk_batch<P>(dd, wt, b->nbulk, parity, b->variant, next, b->st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->join, 0);
         if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 2, 3, b->st);
         return e;
@@ -207,7 +209,8 @@ int lbps_batch_create(lbps_lattice* const* lats, int32_t count, void* cuda_strea
     for (auto* l : b->lats) nbnd += (size_t)l->L.nb;
     b->off_bnd = align256((size_t)count * desc_bytes(b));
     b->off_bulk = align256(b->off_bnd + nbnd * sizeof(BndTask));
-    b->mem_bytes = b->off_bulk + std::max<size_t>(max_bulk, 1) * sizeof(BulkTask);
+    b->off_next = align256(b->off_bulk + std::max<size_t>(max_bulk, 1) * sizeof(BulkTask));
+    b->mem_bytes = b->off_next + 256;
     if (cudaMalloc(&b->mem, b->mem_bytes) != cudaSuccess) {
         cudaGetLastError();
         lbps_batch_destroy(b);
@@ -322,6 +325,19 @@ int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* r
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    // the timed steps advanced the step counters (time of the boundary data):
+    // put back the count of steps actually taken
+    std::vector<unsigned long long> taken(b->lats.size());
+    for (size_t d = 0; d < b->lats.size() && rc == LBPS_OK; ++d) {
+        taken[d] = (unsigned long long)b->lats[d]->steps;
+        cudaError_t e = cudaMemcpyAsync(b->lats[d]->tstep(), &taken[d], sizeof(taken[d]), cudaMemcpyHostToDevice,
+                                        b->st);
+        if (e != cudaSuccess) rc = fail(b, e);
+    }
+    if (rc == LBPS_OK) {
+        cudaError_t e = cudaStreamSynchronize(b->st);
+        if (e != cudaSuccess) rc = fail(b, e);
+    }
     if (rc != LBPS_OK) return rc;
     b->variant = bv;
     b->rows = br;

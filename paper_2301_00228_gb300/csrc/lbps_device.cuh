@@ -57,8 +57,16 @@ struct Consts {
     double a[2], a0[2];         // a_phi, a_psi ; a_{0,phi}, a_{0,psi}
     double two_dt2, two_dt;     // 2 / dt^2, 2 / dt (Eq. acc_dirichlet)
     double inv_rho_dh2;         // 1 / (rho dh^2); a boundary cell's 1 / (rho V_C) is 1, 2 or 4 times it
+    double load_rate[2];        // 1 / t_ramp of the Neumann [0] / Dirichlet [1] data (0: constant)
+    double load_hold[2];        // t_hold: the factor is min(t, t_hold) / t_ramp
     int bc_feq_mode;            // Eq. LBE_mod reading
 };
+
+// Time factor of the boundary data of one kind (0 Neumann, 1 Dirichlet) at
+// time t: ramp then hold, 1 without a schedule (Sec. 4 loads).
+__device__ __forceinline__ double load_factor(const Consts& c, int kind, double t) {
+    return c.load_rate[kind] > 0.0 ? c.load_rate[kind] * fmin(t, c.load_hold[kind]) : 1.0;
+}
 
 // The same constants in the population arithmetic type T.
 template <typename T>

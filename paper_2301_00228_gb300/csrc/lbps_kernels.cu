@@ -196,13 +196,18 @@ __device__ inline void boundary_stress(const Geo& g, const Consts& c, const doub
     }
 }
 
+// tstep: the lattice's step counter n (device memory); time-dependent data
+// take the Neumann force at t_n and the Dirichlet target at t_{n+1}.
 template <typename P>
 __device__ inline void boundary_newmark(const Geo& g, const Consts& c, const View<P>& A, const View<P>& B,
                                         const BNode* __restrict__ bn, int nb,
-                                        const double* __restrict__ sig, int b) {
+                                        const double* __restrict__ sig,
+                                        const unsigned long long* __restrict__ tstep, int b) {
     int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
     const int btype = LBPS_LD(&bn[b].type);
-    const double bx = LBPS_LD(&bn[b].bx), by = LBPS_LD(&bn[b].by);
+    const double n = (double)LBPS_LD(tstep);
+    const double sc = btype == DIRICHLET ? load_factor(c, 1, (n + 1.0) * c.dt) : load_factor(c, 0, n * c.dt);
+    const double bx = sc * LBPS_LD(&bn[b].bx), by = sc * LBPS_LD(&bn[b].by);
     size_t p = (size_t)j * g.px + i;
     const double* ux = A.u;
     const double* uy = A.u + g.plane;
@@ -287,16 +292,21 @@ __global__ void __launch_bounds__(128) boundary_stress_kernel(Geo g, Consts c, V
 template <typename P>
 __global__ void __launch_bounds__(128) boundary_newmark_kernel(Geo g, Consts c, View<P> A, View<P> B,
                                                                const BNode* __restrict__ bn, int nb,
-                                                               const double* __restrict__ sig) {
+                                                               const double* __restrict__ sig,
+                                                               const unsigned long long* __restrict__ tstep) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb) boundary_newmark(g, c, A, B, bn, nb, sig, b);
+    if (b < nb) boundary_newmark(g, c, A, B, bn, nb, sig, tstep, b);
 }
 
+// The last pass of a step also advances the step counter (one thread; no
+// other thread of the pass reads it).
 template <typename P>
 __global__ void __launch_bounds__(128) boundary_reset_kernel(Geo g, Consts c, KCof<P> k, View<P> A, View<P> B,
-                                                             const BNode* __restrict__ bn, int nb, unsigned* flag) {
+                                                             const BNode* __restrict__ bn, int nb, unsigned* flag,
+                                                             unsigned long long* tstep) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nb && boundary_reset(g, c, k, A, B, bn, b)) atomicOr(flag, 1u);
+    if (b == 0) LBPS_ST(tstep, LBPS_LD(tstep) + 1ull);
 }
 
 // ---------------------------------------------------------------- bulk
@@ -467,34 +477,46 @@ __global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<P>* _
     if (pass == 0)
         boundary_stress(d.g, d.c, d.v[a].u, d.v[a].u + d.g.plane, d.bn, d.nb, d.sig, tk.b);
     else if (pass == 1)
-        boundary_newmark(d.g, d.c, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.sig, tk.b);
-    else if (boundary_reset(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, tk.b))
-        atomicOr(d.flag, 1u);
+        boundary_newmark(d.g, d.c, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.sig, d.tstep, tk.b);
+    else {
+        if (boundary_reset(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, tk.b)) atomicOr(d.flag, 1u);
+        if (tk.b == 0) LBPS_ST(d.tstep, LBPS_LD(d.tstep) + 1ull);
+    }
 }
 
-// One warp per strip task of every lattice in the batch.
+// The interior of every lattice in the batch: a persistent grid (as many
+// blocks as fit on the GPU at once) whose warps take strip tasks from the
+// work list through the counter *next (zero before the launch) until none is
+// left, so no wave of short tasks leaves the GPU half idle at the end.  Each
+// warp keeps the descriptor of the lattice it works on in shared memory and
+// copies a new one only when the next task belongs to another lattice.
 template <typename P, int MINB, int UVD>
 __global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<P>* __restrict__ dd,
                                                                const BulkTask* __restrict__ tasks, int ntasks,
-                                                               int parity) {
-    // Each warp copies its lattice's descriptor into shared memory, from where
-    // the strip code reloads fields as it needs them (instead of holding them
-    // in registers).
+                                                               int parity, unsigned* next) {
     __shared__ DomDesc<P> sd[kWarpsPerBlock];
+    const unsigned FULL = 0xffffffffu;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int w = blockIdx.x * kWarpsPerBlock + wid;
-    if (w >= ntasks) return;  // whole warp
-    const BulkTask tk = tasks[w];
-    {
-        const unsigned* src = reinterpret_cast<const unsigned*>(dd + tk.dom);
-        unsigned* dst = reinterpret_cast<unsigned*>(sd + wid);
-        for (int q = lane; q < (int)(sizeof(DomDesc<P>) / 4); q += 32) dst[q] = src[q];
-        __syncwarp();
+    int cached = -1;
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(next, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= (unsigned)ntasks) break;  // whole warp
+        const BulkTask tk = tasks[t];
+        if (tk.dom != cached) {
+            __syncwarp();  // every lane is done with the previous descriptor
+            const unsigned* src = reinterpret_cast<const unsigned*>(dd + tk.dom);
+            unsigned* dst = reinterpret_cast<unsigned*>(sd + wid);
+            for (int q = lane; q < (int)(sizeof(DomDesc<P>) / 4); q += 32) dst[q] = src[q];
+            __syncwarp();
+            cached = tk.dom;
+        }
+        const DomDesc<P>& d = sd[wid];
+        const int a = d.cur ^ parity;
+        bool bad = bulk_strip<P, UVD>(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], tk.xs, tk.j0, tk.j1);
+        if (__any_sync(FULL, bad) && lane == 0) atomicOr(d.flag, 1u);
     }
-    const DomDesc<P>& d = sd[wid];
-    const int a = d.cur ^ parity;
-    bool bad = bulk_strip<P, UVD>(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], tk.xs, tk.j0, tk.j1);
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(d.flag, 1u);
 }
 
 // ------------------------------------------------------------------ sync
@@ -653,22 +675,44 @@ cudaError_t launch_boundary_batch(const DomDesc<P>* dd, const BndTask* tasks, in
     return cudaGetLastError();
 }
 
+// Blocks of the persistent batch kernel: those resident on all SMs at once.
+template <typename K>
+int resident_blocks(K kernel) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * kWarpsPerBlock, 0) != cudaSuccess)
+        return -1;
+    return sms * (per_sm > 0 ? per_sm : 1);
+}
+
+template <typename P, int MINB, int UVD>
+cudaError_t launch_bulk_batch_v(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity,
+                                unsigned* next, cudaStream_t st) {
+    auto kern = bulk_batch_kernel<P, MINB, UVD>;
+    int blocks = resident_blocks(kern);
+    if (blocks < 0) return cudaGetLastError();
+    blocks = min(blocks, (ntasks + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, 32 * kWarpsPerBlock, 0, st>>>(dd, tasks, ntasks, parity, next);
+    return cudaGetLastError();
+}
+
 template <typename P>
 cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
-                              cudaStream_t st) {
+                              unsigned* next, cudaStream_t st) {
     if (ntasks <= 0) return cudaGetLastError();
-    dim3 grid((ntasks + kWarpsPerBlock - 1) / kWarpsPerBlock), blk(32 * kWarpsPerBlock);
     switch (variant) {
-    case 0: bulk_batch_kernel<P, 6, 2><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    case 1: bulk_batch_kernel<P, 5, 2><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    case 2: bulk_batch_kernel<P, 4, 2><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    case 3: bulk_batch_kernel<P, 8, 2><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    case 4: bulk_batch_kernel<P, 6, 1><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    case 5: bulk_batch_kernel<P, 5, 1><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    case 6: bulk_batch_kernel<P, 4, 1><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
-    default: bulk_batch_kernel<P, 8, 1><<<grid, blk, 0, st>>>(dd, tasks, ntasks, parity); break;
+    case 0: return launch_bulk_batch_v<P, 6, 2>(dd, tasks, ntasks, parity, next, st);
+    case 1: return launch_bulk_batch_v<P, 5, 2>(dd, tasks, ntasks, parity, next, st);
+    case 2: return launch_bulk_batch_v<P, 4, 2>(dd, tasks, ntasks, parity, next, st);
+    case 3: return launch_bulk_batch_v<P, 8, 2>(dd, tasks, ntasks, parity, next, st);
+    case 4: return launch_bulk_batch_v<P, 6, 1>(dd, tasks, ntasks, parity, next, st);
+    case 5: return launch_bulk_batch_v<P, 5, 1>(dd, tasks, ntasks, parity, next, st);
+    case 6: return launch_bulk_batch_v<P, 4, 1>(dd, tasks, ntasks, parity, next, st);
+    default: return launch_bulk_batch_v<P, 8, 1>(dd, tasks, ntasks, parity, next, st);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t set_check_range(const void* base, size_t bytes, cudaStream_t st) {
@@ -718,13 +762,14 @@ cudaError_t launch_init(const Geo& g, const Consts& c, const KCof<P>& k, View<P>
 
 template <typename P>
 cudaError_t launch_boundary(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, const BNode* bn,
-                            int nb, double* sig, unsigned* flag, cudaStream_t st, int pass_lo, int pass_hi) {
+                            int nb, double* sig, unsigned* flag, unsigned long long* tstep, cudaStream_t st,
+                            int pass_lo, int pass_hi) {
     if (nb > 0) {
         const int blocks = (nb + 127) / 128;
         for (int pass = pass_lo; pass < pass_hi; ++pass) {
             if (pass == 0) boundary_stress_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, bn, nb, sig);
-            if (pass == 1) boundary_newmark_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, B, bn, nb, sig);
-            if (pass == 2) boundary_reset_kernel<P><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb, flag);
+            if (pass == 1) boundary_newmark_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, B, bn, nb, sig, tstep);
+            if (pass == 2) boundary_reset_kernel<P><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb, flag, tstep);
         }
     }
     return cudaGetLastError();
@@ -778,7 +823,8 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, const KCof<P>& k, View<P
 #define LBPS_INSTANTIATE(P)                                                                                   \
     template cudaError_t launch_init<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, cudaStream_t);  \
     template cudaError_t launch_boundary<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>,      \
-                                            const BNode*, int, double*, unsigned*, cudaStream_t, int, int);   \
+                                            const BNode*, int, double*, unsigned*, unsigned long long*,       \
+                                            cudaStream_t, int, int);                                          \
     template cudaError_t launch_bulk<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>,          \
                                         unsigned*, cudaStream_t, const Tuning&);                              \
     template cudaError_t launch_sync<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, cudaStream_t);  \
@@ -788,7 +834,8 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, const KCof<P>& k, View<P
                                          const double*, double*, double*, cudaStream_t);                     \
     template cudaError_t launch_boundary_batch<P>(const DomDesc<P>*, const BndTask*, int, int, int, int,      \
                                                   cudaStream_t);                                              \
-    template cudaError_t launch_bulk_batch<P>(const DomDesc<P>*, const BulkTask*, int, int, int, cudaStream_t);
+    template cudaError_t launch_bulk_batch<P>(const DomDesc<P>*, const BulkTask*, int, int, int, unsigned*,      \
+                                              cudaStream_t);
 
 LBPS_INSTANTIATE(PopDirect<float>)
 LBPS_INSTANTIATE(PopDirect<double>)

@@ -25,11 +25,12 @@ cudaError_t launch_init(const Geo& g, const Consts& c, const KCof<P>& k, View<P>
 
 // One time step A (time t) -> B (time t + dt) on one stream: boundary passes
 // 0-1 (stress, Newmark), launch_bulk, boundary pass 2 (reset).  sig: scratch
-// of 2 * nb * 3 doubles (stresses of the boundary cells).
+// of 2 * nb * 3 doubles (stresses of the boundary cells); tstep: the
+// lattice's step counter, read by pass 1 and advanced by pass 2.
 template <typename P>
 cudaError_t launch_boundary(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B,
-                            const BNode* bn, int nb, double* sig, unsigned* flag, cudaStream_t st, int pass_lo,
-                            int pass_hi);
+                            const BNode* bn, int nb, double* sig, unsigned* flag, unsigned long long* tstep,
+                            cudaStream_t st, int pass_lo, int pass_hi);
 // Launch shape of the bulk kernel: variant selects the register budget (0: 6
 // blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8) with u, du/dt prefetched two
 // rows ahead like the populations; variants 4..7 the same budgets with u,
@@ -75,6 +76,7 @@ struct DomDesc {
     const BNode* bn;
     double* sig;
     unsigned* flag;
+    unsigned long long* tstep;  // step counter (time of the boundary data)
     int nb;
     int cur;
 };
@@ -92,9 +94,11 @@ constexpr int kBatchStripCols = 30;  // output columns per warp task
 template <typename P>
 cudaError_t launch_boundary_batch(const DomDesc<P>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
                                   int pass_hi, cudaStream_t st);
+// Interior of every lattice: a persistent grid whose warps take tasks through
+// the counter *next (device memory; the launcher zeroes it on the stream).
 template <typename P>
 cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
-                              cudaStream_t st);
+                              unsigned* next, cudaStream_t st);
 
 // Checked builds (LBPS_CHECKED): the device block every kernel access must
 // stay inside, and the first violation seen (source line, address); both are

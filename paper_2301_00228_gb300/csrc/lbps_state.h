@@ -78,6 +78,8 @@ struct lbps_lattice {
     const lbps::BNode* bn() const { return reinterpret_cast<const lbps::BNode*>(mem + L.off_bn); }
     double* sig() const { return reinterpret_cast<double*>(mem + L.off_sig); }
     unsigned* flag() const { return reinterpret_cast<unsigned*>(mem + L.off_flag); }
+    // device step counter (time of the boundary data), beside the flag
+    unsigned long long* tstep() const { return reinterpret_cast<unsigned long long*>(mem + L.off_flag + 8); }
     double* partials() const { return reinterpret_cast<double*>(mem + L.off_part); }
     double* out4() const { return reinterpret_cast<double*>(mem + L.off_out); }
     double* staging() const { return reinterpret_cast<double*>(mem + L.off_staging); }

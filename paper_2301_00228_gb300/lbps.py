@@ -80,6 +80,7 @@ def _load():
         "lbps_norms_noalloc": (ctypes.c_int, [vp, vp, sz, vp, vp]),
         "lbps_info": (ctypes.c_int, [vp, vp, P(i64)]),
         "lbps_scale_exp": (ctypes.c_int, [vp, P(i32)]),
+        "lbps_set_load": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.c_double]),
         "lbps_check_report": (ctypes.c_int, [vp]),
         "lbps_last_cuda_error": (ctypes.c_int, [vp]),
         "lbps_set_tuning": (ctypes.c_int, [vp, i32, i32]),
@@ -205,6 +206,10 @@ def lbps_info(h):
     return out, int(steps.value)
 
 
+def lbps_set_load(h, kind, t_ramp, t_hold=float("inf")):
+    _check(_lib.lbps_set_load(h, int(kind), float(t_ramp), float(t_hold)), "lbps_set_load")
+
+
 def lbps_scale_exp(h):
     e = ctypes.c_int32(0)
     _check(_lib.lbps_scale_exp(h, ctypes.byref(e)), "lbps_scale_exp")
@@ -324,6 +329,12 @@ class Lattice:
     @property
     def scale_exp(self):
         return lbps_scale_exp(self._h)
+
+    def set_load(self, kind, t_ramp, t_hold=float("inf")):
+        """Ramp-then-hold factor on the boundary data of one kind
+        (LBPS_NEUMANN or LBPS_DIRICHLET): s(t) = min(t, t_hold) / t_ramp."""
+        lbps_set_load(self._h, kind, t_ramp, t_hold)
+        return self
 
     def read(self, field):
         fid = FIELDS[field] if isinstance(field, str) else int(field)
