@@ -61,6 +61,22 @@ def aggregate(local_seconds, local_units, world, reduce_max, reduce_sum):
     return u / t, t, u
 
 
+def reducers(dist, device):
+    """(max, sum) over the ranks of a process group of one Python float each,
+    through a tensor on ``device`` ("cuda" under NCCL, "cpu" under gloo);
+    plain float() when there is no process group."""
+    if dist is None:
+        return float, float
+    import torch
+
+    def red(x, op):
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    return (lambda x: red(x, dist.ReduceOp.MAX)), (lambda x: red(x, dist.ReduceOp.SUM))
+
+
 def workload(name, size=None):
     """(config name, Domain) of a workload recipe."""
     from paper_2301_00228_gb300 import workloads as W
@@ -462,18 +478,7 @@ def run_gpu(args):
     seconds = e0.elapsed_time(e1) / 1000.0
     units = d.nx * d.ny * args.steps
 
-    if dist is not None:
-        def rmax(x):
-            t = torch.tensor([x], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-
-        def rsum(x):
-            t = torch.tensor([x], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.SUM)
-            return float(t.item())
-    else:
-        rmax = rsum = float
+    rmax, rsum = reducers(dist, "cuda")
     value_ups, t_max, units_all = aggregate(seconds, units, world, rmax, rsum)
     value = value_ups / 1e9
 

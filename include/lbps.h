@@ -246,6 +246,22 @@ void lbps_batch_destroy(lbps_batch* b);
  * number of completed time steps. */
 int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done);
 
+/* Checkpoint / resume (not in the paper).  A saved state is a small header
+ * (sizes, storage format, step count, 16-bit scale) and the raw current state
+ * copy: the populations in the storage format and u, du/dt, so a lattice that
+ * loads it continues bit-for-bit where the saved one was.  The parameters,
+ * boundary data and load schedule are the lattice's own and are not saved:
+ * load into a lattice created the same way.
+ *   lbps_state_size: bytes of a saved state.
+ *   lbps_state_save: copies it into dst (host or device memory, at least
+ *     lbps_state_size bytes); synchronises.  LBPS_ERR_STATE before init.
+ *   lbps_state_load: restores it (the lattice counts as initialised); returns
+ *     LBPS_ERR_INVALID if the header does not match this lattice (sizes,
+ *     storage format) or bytes is short.  Synchronises. */
+int lbps_state_size(const lbps_lattice* lat, size_t* bytes);
+int lbps_state_save(lbps_lattice* lat, void* dst, size_t bytes);
+int lbps_state_load(lbps_lattice* lat, const void* src, size_t bytes);
+
 /* Time-dependent boundary data (Sec. 4: the tension example ramps its
  * traction linearly to 0.005 mu at t = L/c_s and holds it; the shear example
  * ramps without end).  The values of one kind (kind = LBPS_NEUMANN: the

@@ -555,6 +555,87 @@ int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done) {
     return LBPS_OK;
 }
 
+namespace {
+
+// Header of a saved state; the raw current state copy follows it.
+struct SavedState {
+    char magic[8];          // "LBPSSTA1"
+    int32_t nx, ny, px, storage;
+    int32_t scale_exp, pad;
+    int64_t steps;
+    uint64_t copy_bytes;
+};
+
+constexpr char kMagic[8] = {'L', 'B', 'P', 'S', 'S', 'T', 'A', '1'};
+
+}  // namespace
+
+int lbps_state_size(const lbps_lattice* lat, size_t* bytes) {
+    if (!lat || !bytes) return LBPS_ERR_INVALID;
+    *bytes = sizeof(SavedState) + lat->L.copy_bytes;
+    return LBPS_OK;
+}
+
+int lbps_state_save(lbps_lattice* lat, void* dst, size_t bytes) {
+    if (!lat || !dst || bytes < sizeof(SavedState) + lat->L.copy_bytes) return LBPS_ERR_INVALID;
+    if (!lat->initialised) return LBPS_ERR_STATE;
+    SavedState h{};
+    std::memcpy(h.magic, kMagic, sizeof(kMagic));
+    h.nx = lat->L.g.nx;
+    h.ny = lat->L.g.ny;
+    h.px = lat->L.g.px;
+    h.storage = lat->p.storage;
+    h.scale_exp = lat->scale_exp;
+    h.steps = lat->steps;
+    h.copy_bytes = lat->L.copy_bytes;
+    // dst may be host or device memory: both copies go through the runtime
+    cudaError_t e = cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyDefault, lat->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(static_cast<char*>(dst) + sizeof(h), lat->mem + lat->L.off_copy[lat->cur],
+                            lat->L.copy_bytes, cudaMemcpyDefault, lat->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+    if (e != cudaSuccess) {
+        lat->last_cuda = (int)e;
+        return LBPS_ERR_CUDA;
+    }
+    return LBPS_OK;
+}
+
+int lbps_state_load(lbps_lattice* lat, const void* src, size_t bytes) {
+    if (!lat || !src || bytes < sizeof(SavedState)) return LBPS_ERR_INVALID;
+    SavedState h;
+    // src may be host or device memory
+    cudaError_t he = cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDefault, lat->st);
+    if (he == cudaSuccess) he = cudaStreamSynchronize(lat->st);
+    if (he != cudaSuccess) {
+        lat->last_cuda = (int)he;
+        return LBPS_ERR_CUDA;
+    }
+    if (std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.nx != lat->L.g.nx || h.ny != lat->L.g.ny ||
+        h.px != lat->L.g.px || h.storage != lat->p.storage || h.copy_bytes != lat->L.copy_bytes ||
+        bytes < sizeof(SavedState) + lat->L.copy_bytes || h.steps < 0 || h.scale_exp < -100 || h.scale_exp > 100)
+        return LBPS_ERR_INVALID;
+    lat->cur = 0;
+    cudaError_t e = cudaMemcpyAsync(lat->mem + lat->L.off_copy[0], static_cast<const char*>(src) + sizeof(h),
+                                    lat->L.copy_bytes, cudaMemcpyDefault, lat->st);
+    unsigned long long n = (unsigned long long)h.steps;
+    // the non-finite flag cleared, the device step counter set
+    if (e == cudaSuccess) e = cudaMemsetAsync(lat->flag(), 0, sizeof(unsigned), lat->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lat->tstep(), &n, sizeof(n), cudaMemcpyHostToDevice, lat->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+    if (e != cudaSuccess) {
+        lat->last_cuda = (int)e;
+        return LBPS_ERR_CUDA;
+    }
+    lat->steps = h.steps;
+    lat->scale_exp = h.scale_exp;
+    lat->kf.scale = std::ldexp(1.0f, h.scale_exp);
+    lat->kf.inv_scale = std::ldexp(1.0f, -h.scale_exp);
+    lat->initialised = true;
+    lat->gen += 1;  // batches holding this lattice re-read its descriptor
+    return LBPS_OK;
+}
+
 int lbps_set_load(lbps_lattice* lat, int32_t kind, double t_ramp, double t_hold) {
     if (!lat || (kind != LBPS_NEUMANN && kind != LBPS_DIRICHLET)) return LBPS_ERR_INVALID;
     if (!(t_ramp >= 0.0) || !std::isfinite(t_ramp) || !(t_hold > 0.0)) return LBPS_ERR_INVALID;

@@ -81,6 +81,9 @@ def _load():
         "lbps_info": (ctypes.c_int, [vp, vp, P(i64)]),
         "lbps_scale_exp": (ctypes.c_int, [vp, P(i32)]),
         "lbps_set_load": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.c_double]),
+        "lbps_state_size": (ctypes.c_int, [vp, P(sz)]),
+        "lbps_state_save": (ctypes.c_int, [vp, vp, sz]),
+        "lbps_state_load": (ctypes.c_int, [vp, vp, sz]),
         "lbps_check_report": (ctypes.c_int, [vp]),
         "lbps_last_cuda_error": (ctypes.c_int, [vp]),
         "lbps_set_tuning": (ctypes.c_int, [vp, i32, i32]),
@@ -210,6 +213,22 @@ def lbps_set_load(h, kind, t_ramp, t_hold=float("inf")):
     _check(_lib.lbps_set_load(h, int(kind), float(t_ramp), float(t_hold)), "lbps_set_load")
 
 
+def lbps_state_size(h):
+    n = ctypes.c_size_t(0)
+    _check(_lib.lbps_state_size(h, ctypes.byref(n)), "lbps_state_size")
+    return int(n.value)
+
+
+def lbps_state_save(h, dst):
+    _check(_lib.lbps_state_save(h, _p(dst), dst.nbytes), "lbps_state_save")
+    return dst
+
+
+def lbps_state_load(h, src):
+    src = np.ascontiguousarray(src, np.uint8)
+    _check(_lib.lbps_state_load(h, _p(src), src.nbytes), "lbps_state_load")
+
+
 def lbps_scale_exp(h):
     e = ctypes.c_int32(0)
     _check(_lib.lbps_scale_exp(h, ctypes.byref(e)), "lbps_scale_exp")
@@ -329,6 +348,14 @@ class Lattice:
     @property
     def scale_exp(self):
         return lbps_scale_exp(self._h)
+
+    def save_state(self):
+        """Checkpoint of the current state (host bytes, numpy uint8)."""
+        return lbps_state_save(self._h, np.empty(lbps_state_size(self._h), np.uint8))
+
+    def load_state(self, buf):
+        lbps_state_load(self._h, buf)
+        return self
 
     def set_load(self, kind, t_ramp, t_hold=float("inf")):
         """Ramp-then-hold factor on the boundary data of one kind

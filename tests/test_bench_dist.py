@@ -1,0 +1,71 @@
+"""The multi-rank path of bench.py on CPU: two gloo ranks (one process per
+rank, rendezvous on 127.0.0.1) combine their local timings the way the GPU
+ranks do under NCCL: the slowest rank's time and the sum of the units; the
+reference arm runs on rank 0 only."""
+import os
+import socket
+import sys
+from pathlib import Path
+
+import pytest
+
+torch = pytest.importorskip("torch")
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    sys.path.insert(0, str(ROOT))
+    import torch.distributed as dist
+
+    import bench
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    rmax, rsum = bench.reducers(dist, "cpu")
+    # rank r took (r + 1) s for 100 (r + 1) lattice updates
+    value, t, u = bench.aggregate(float(rank + 1), 100.0 * (rank + 1), world, rmax, rsum)
+    out.put((rank, value, t, u, bench.dist_env()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_aggregate():
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, value, t, u, env in res:
+        assert t == 2.0 and u == 300.0 and value == 150.0   # slowest rank, summed units
+        assert env == (rank, 2, rank)
+
+
+def test_reference_arm_other_ranks_exit(monkeypatch):
+    """Under torchrun only rank 0 times the oracle; the other ranks return 0
+    at once without work."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.main(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]) == 0
+
+
+def test_single_process_reducers_are_identity():
+    sys.path.insert(0, str(ROOT))
+    import bench
+
+    rmax, rsum = bench.reducers(None, "cpu")
+    assert bench.aggregate(2.0, 10.0, 1, rmax, rsum) == (5.0, 2.0, 10.0)
