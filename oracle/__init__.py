@@ -41,6 +41,9 @@ PINS = {
     "synchronisation (Sec. 3.2)": "tests/test_oracle_pins.py::test_sync_*",
     "rectangle boundary helper": "tests/test_oracle_pins.py::test_rect_bc_*",
     "time-dependent boundary data (readings R12, R13)": "tests/test_oracle_pins.py::test_load_ramp_*",
+    "general geometry: void points, clipped cells, one-sided stencils (reading R14)":
+        "tests/test_oracle_pins.py::test_hole_*, ::test_explicit_rectangle_cells_equal_default, "
+        "::test_geometry_rejected_without_stencil",
 }
 # Readings with no pin against the paper itself.
 PARITY_UNPINNED = (
@@ -82,6 +85,8 @@ def lib():
         vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
         L.ora_create.restype = vp
         L.ora_create.argtypes = [ctypes.POINTER(_Params), vp, vp]
+        L.ora_create_cells.restype = vp
+        L.ora_create_cells.argtypes = [ctypes.POINTER(_Params), vp, vp, vp]
         L.ora_destroy.argtypes = [vp]
         L.ora_constants.argtypes = [vp, dp]
         L.ora_init.argtypes = [vp, vp, vp, vp, vp]
@@ -124,7 +129,7 @@ class OracleLattice:
     """One lattice of the FP64 oracle."""
 
     def __init__(self, nx, ny, lam, mu, rho=1.0, dh=1.0, a0_phi=0.9999, periodic_x=False,
-                 periodic_y=False, node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0):
+                 periodic_y=False, node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0, cell=None):
         self.nx, self.ny = int(nx), int(ny)
         p = _Params(self.nx, self.ny, lam, mu, rho, dh, a0_phi, int(periodic_x), int(periodic_y),
                     int(bc_feq_mode), int(sync_every))
@@ -132,7 +137,8 @@ class OracleLattice:
             node_type = np.zeros((ny, nx), np.uint8)
         self._nt = np.ascontiguousarray(node_type, dtype=np.uint8)
         self._bv = None if bc_value is None else np.ascontiguousarray(bc_value, dtype=np.float64)
-        self._h = lib().ora_create(ctypes.byref(p), _ptr(self._nt), _ptr(self._bv))
+        self._cell = None if cell is None else np.ascontiguousarray(cell, dtype=np.float64)
+        self._h = lib().ora_create_cells(ctypes.byref(p), _ptr(self._nt), _ptr(self._bv), _ptr(self._cell))
         if not self._h:
             raise ValueError("oracle rejected the lattice description")
         c = np.zeros(6)

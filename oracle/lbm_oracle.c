@@ -54,6 +54,21 @@
  *       with a ramp-then-hold factor s(t) = min(t, t_hold) / t_ramp (s = 1
  *       without a schedule; Sec. 4 ramps the traction of its tension and
  *       shear examples this way).  R13 says at which times they are taken.
+ *   R14 General geometry (Sec. 3 preprocessing, not detailed in the paper):
+ *       points are interior (0), Neumann (1), Dirichlet (2) or void (3, not
+ *       in the body).  A body point with a neighbour outside the body (void,
+ *       or past a non-periodic edge) is a boundary point.  Its cell is the
+ *       square of side dh around it clipped to the body, given as data: the
+ *       area V_C and the length in the body of each side (E, N, W, S).  A
+ *       side facing a body neighbour r is shared with r's cell and carries
+ *       (sigma_k + sigma_r)/2; a side facing no body neighbour that still
+ *       lies partly in the body carries sigma_k (so a uniform stress is in
+ *       equilibrium); the rest of the cell boundary is dC_ext, whose force F
+ *       is supplied per point.  Without cell data the cells of R6 are used.
+ *       Differences (R4) are central where both neighbours are in the body,
+ *       otherwise one-sided towards the body; a body point without such a
+ *       stencil makes the geometry invalid.  A boundary point streams into
+ *       every interior neighbour (Eq. LBE_mod).
  *   R13 The Neumann force enters the acceleration at t with its value at t
  *       (like the stresses, Eq. acc_neumann); the Dirichlet target is
  *       u*(t + dt), the displacement the point must have after the step
@@ -76,8 +91,9 @@ static const int EY[5] = {0, 0, 1, 0, -1};
 struct ora_lattice {
     ora_params p;
     double cd, cs, a_phi, a_psi, a0_psi, dt, c;
-    uint8_t* type;        /* [ny*nx] */
+    uint8_t* type;        /* [ny*nx]: 0 interior, 1 Neumann, 2 Dirichlet, 3 void */
     double* bc;           /* [ny*nx*2] */
+    double* cell;         /* [ny*nx*5]: V_C and side lengths E, N, W, S of boundary cells */
     double* f[2][5];      /* populations at t: set 0 = phi, set 1 = psi */
     double* fn[2][5];     /* populations at t + dt */
     double* fc[2][5];     /* post-collision populations */
@@ -102,15 +118,8 @@ static long at(const ora_lattice* L, int i, int j) { return (long)j * L->p.nx + 
 static double w0_of(const ora_lattice* L, int set) { return set == 0 ? L->p.a0_phi : L->a0_psi; }
 static double w_of(const ora_lattice* L, int set) { return set == 0 ? L->a_phi : L->a_psi; }
 
-/* A point is a boundary lattice point when one of its four neighbours lies
- * outside a non-periodic edge. */
-static int is_boundary(const ora_lattice* L, int i, int j) {
-    if (!L->p.periodic_x && (i == 0 || i == L->p.nx - 1)) return 1;
-    if (!L->p.periodic_y && (j == 0 || j == L->p.ny - 1)) return 1;
-    return 0;
-}
-
-/* Neighbour of (i,j) in direction (di,dj); 0 if it lies outside the body. */
+/* Neighbour of (i,j) in direction (di,dj); 0 if it lies outside the body
+ * (past a non-periodic edge, or void). */
 static int neighbour(const ora_lattice* L, int i, int j, int di, int dj, int* oi, int* oj) {
     int ni = i + di, nj = j + dj;
     if (ni < 0 || ni >= L->p.nx) {
@@ -121,31 +130,45 @@ static int neighbour(const ora_lattice* L, int i, int j, int di, int dj, int* oi
         if (!L->p.periodic_y) return 0;
         nj = (nj + L->p.ny) % L->p.ny;
     }
+    if (L->type[at(L, ni, nj)] == 3) return 0;
     *oi = ni;
     *oj = nj;
     return 1;
 }
 
-/* Second-order finite differences (reading R4). */
-static double d_dx(const ora_lattice* L, const double* g, int i, int j) {
-    int nx = L->p.nx;
-    double h = L->p.dh;
-    if (L->p.periodic_x)
-        return (g[at(L, (i + 1) % nx, j)] - g[at(L, (i - 1 + nx) % nx, j)]) / (2.0 * h);
-    if (i > 0 && i < nx - 1) return (g[at(L, i + 1, j)] - g[at(L, i - 1, j)]) / (2.0 * h);
-    if (i == 0) return (-3.0 * g[at(L, 0, j)] + 4.0 * g[at(L, 1, j)] - g[at(L, 2, j)]) / (2.0 * h);
-    return (3.0 * g[at(L, nx - 1, j)] - 4.0 * g[at(L, nx - 2, j)] + g[at(L, nx - 3, j)]) / (2.0 * h);
+static int is_void(const ora_lattice* L, long k) { return L->type[k] == 3; }
+
+/* A body point is a boundary lattice point when one of its four neighbours
+ * lies outside the body (reading R14). */
+static int is_boundary(const ora_lattice* L, int i, int j) {
+    if (is_void(L, at(L, i, j))) return 0;
+    int oi, oj;
+    for (int a = 1; a < 5; ++a)
+        if (!neighbour(L, i, j, EX[a], EY[a], &oi, &oj)) return 1;
+    return 0;
 }
 
-static double d_dy(const ora_lattice* L, const double* g, int i, int j) {
-    int ny = L->p.ny;
+/* Second-order finite difference of g along (dx, dy) at (i, j) (readings R4,
+ * R14): central if both neighbours are in the body, else one-sided
+ * three-point towards the body.  Returns 0 and sets *ok = 0 when neither is
+ * possible. */
+static double fd1(const ora_lattice* L, const double* g, int i, int j, int dx, int dy, int* ok) {
     double h = L->p.dh;
-    if (L->p.periodic_y)
-        return (g[at(L, i, (j + 1) % ny)] - g[at(L, i, (j - 1 + ny) % ny)]) / (2.0 * h);
-    if (j > 0 && j < ny - 1) return (g[at(L, i, j + 1)] - g[at(L, i, j - 1)]) / (2.0 * h);
-    if (j == 0) return (-3.0 * g[at(L, i, 0)] + 4.0 * g[at(L, i, 1)] - g[at(L, i, 2)]) / (2.0 * h);
-    return (3.0 * g[at(L, i, ny - 1)] - 4.0 * g[at(L, i, ny - 2)] + g[at(L, i, ny - 3)]) / (2.0 * h);
+    int pi, pj, mi, mj, qi, qj;
+    int hp = neighbour(L, i, j, dx, dy, &pi, &pj);
+    int hm = neighbour(L, i, j, -dx, -dy, &mi, &mj);
+    if (ok) *ok = 1;
+    if (hp && hm) return (g[at(L, pi, pj)] - g[at(L, mi, mj)]) / (2.0 * h);
+    if (hp && neighbour(L, pi, pj, dx, dy, &qi, &qj))
+        return (-3.0 * g[at(L, i, j)] + 4.0 * g[at(L, pi, pj)] - g[at(L, qi, qj)]) / (2.0 * h);
+    if (hm && neighbour(L, mi, mj, -dx, -dy, &qi, &qj))
+        return (3.0 * g[at(L, i, j)] - 4.0 * g[at(L, mi, mj)] + g[at(L, qi, qj)]) / (2.0 * h);
+    if (ok) *ok = 0;
+    return 0.0;
 }
+
+static double d_dx(const ora_lattice* L, const double* g, int i, int j) { return fd1(L, g, i, j, 1, 0, NULL); }
+static double d_dy(const ora_lattice* L, const double* g, int i, int j) { return fd1(L, g, i, j, 0, 1, NULL); }
 
 /* Divergence and curl of u by finite differences (Eq. phi-psi). */
 static double fd_div(const ora_lattice* L, const double* ux, const double* uy, int i, int j) {
@@ -197,6 +220,11 @@ static void gather(double* const fs[5], long k, double g[5]) {
 static double* alloc0(long n) { return (double*)calloc((size_t)n, sizeof(double)); }
 
 ora_lattice* ora_create(const ora_params* p, const uint8_t* node_type, const double* bc_value) {
+    return ora_create_cells(p, node_type, bc_value, NULL);
+}
+
+ora_lattice* ora_create_cells(const ora_params* p, const uint8_t* node_type, const double* bc_value,
+                              const double* cell) {
     if (!p || p->nx < 3 || p->ny < 3) return NULL;
     if (!(p->mu > 0.0) || !(p->rho > 0.0) || !(p->lambda + 2.0 * p->mu > 0.0) || !(p->dh > 0.0)) return NULL;
     if (!(p->a0_phi >= 0.0 && p->a0_phi < 1.0)) return NULL;
@@ -217,6 +245,7 @@ ora_lattice* ora_create(const ora_params* p, const uint8_t* node_type, const dou
     long n = (long)p->nx * p->ny;
     L->type = (uint8_t*)calloc((size_t)n, 1);
     L->bc = alloc0(2 * n);
+    L->cell = alloc0(5 * n);
     for (int set = 0; set < 2; ++set) {
         for (int a = 0; a < 5; ++a) {
             L->f[set][a] = alloc0(n);
@@ -228,19 +257,55 @@ ora_lattice* ora_create(const ora_params* p, const uint8_t* node_type, const dou
     L->ux = alloc0(n); L->uy = alloc0(n); L->vx = alloc0(n); L->vy = alloc0(n);
     L->ux1 = alloc0(n); L->uy1 = alloc0(n); L->vx1 = alloc0(n); L->vy1 = alloc0(n);
     L->ax = alloc0(n); L->ay = alloc0(n);
+    /* Node types first (void points change who is a boundary point). */
+    for (long k = 0; k < n; ++k) {
+        uint8_t t = node_type ? node_type[k] : 0;
+        if (t > 3) {
+            ora_destroy(L);
+            return NULL;
+        }
+        L->type[k] = t;
+    }
     for (int j = 0; j < p->ny; ++j) {
         for (int i = 0; i < p->nx; ++i) {
             long k = at(L, i, j);
-            uint8_t t = node_type ? node_type[k] : 0;
-            int bnd = is_boundary(L, i, j);
-            if (t > 2 || (bnd && t == 0) || (!bnd && t != 0)) {
+            uint8_t t = L->type[k];
+            if (t == 3) continue;
+            int bnd = is_boundary(L, i, j), okx, oky;
+            fd1(L, L->ux, i, j, 1, 0, &okx);
+            fd1(L, L->ux, i, j, 0, 1, &oky);
+            if ((bnd && t == 0) || (!bnd && t != 0) || !okx || !oky) {
                 ora_destroy(L);
                 return NULL;
             }
-            L->type[k] = t;
+            if (!bnd) continue;
             if (bc_value) {
                 L->bc[2 * k] = bc_value[2 * k];
                 L->bc[2 * k + 1] = bc_value[2 * k + 1];
+            }
+            double* cd = L->cell + 5 * k;
+            if (t != 1) continue;  /* only Neumann points use a cell */
+            if (cell) {
+                for (int q = 0; q < 5; ++q) cd[q] = cell[5 * k + q];
+                int okc = isfinite(cd[0]) && cd[0] > 0.0;
+                for (int q = 1; q < 5; ++q) okc = okc && isfinite(cd[q]) && cd[q] >= 0.0;
+                if (!okc) {
+                    ora_destroy(L);
+                    return NULL;
+                }
+            } else {
+                /* Reading R6: the square of side dh clipped to the rectangle. */
+                double half = 0.5 * p->dh;
+                int ti, tj;
+                int has_e = neighbour(L, i, j, 1, 0, &ti, &tj), has_n = neighbour(L, i, j, 0, 1, &ti, &tj);
+                int has_w = neighbour(L, i, j, -1, 0, &ti, &tj), has_s = neighbour(L, i, j, 0, -1, &ti, &tj);
+                double wx = (has_w ? half : 0.0) + (has_e ? half : 0.0);
+                double wy = (has_s ? half : 0.0) + (has_n ? half : 0.0);
+                cd[0] = wx * wy;
+                cd[1] = has_e ? wy : 0.0;
+                cd[2] = has_n ? wx : 0.0;
+                cd[3] = has_w ? wy : 0.0;
+                cd[4] = has_s ? wx : 0.0;
             }
         }
     }
@@ -251,6 +316,7 @@ void ora_destroy(ora_lattice* L) {
     if (!L) return;
     free(L->type);
     free(L->bc);
+    free(L->cell);
     for (int set = 0; set < 2; ++set) {
         for (int a = 0; a < 5; ++a) {
             free(L->f[set][a]);
@@ -300,6 +366,7 @@ int ora_init(ora_lattice* L, const double* ux0, const double* uy0, const double*
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             long k = at(L, i, j);
+            if (is_void(L, k)) continue;  /* void points hold no state */
             double phi = fd_div(L, L->ux, L->uy, i, j);
             double psi = fd_curl(L, L->ux, L->uy, i, j);
             double jphi_x = -L->vx[k], jphi_y = -L->vy[k];
@@ -342,37 +409,32 @@ int ora_set_load(ora_lattice* L, int32_t kind, double t_ramp, double t_hold) {
 }
 
 /* Neumann points: momentum balance of the boundary cell, Eq.
- * contBalanceOfMomentum simplified to Eq. acc_neumann (readings R5, R6). */
+ * contBalanceOfMomentum simplified to Eq. acc_neumann (readings R5, R6, R14). */
 static void accel_neumann(const ora_lattice* L, int i, int j, double* ax, double* ay) {
     long k = at(L, i, j);
-    double half = 0.5 * L->p.dh;
-    int ti, tj;
-    int has_w = neighbour(L, i, j, -1, 0, &ti, &tj);
-    int has_e = neighbour(L, i, j, 1, 0, &ti, &tj);
-    int has_s = neighbour(L, i, j, 0, -1, &ti, &tj);
-    int has_n = neighbour(L, i, j, 0, 1, &ti, &tj);
-    /* Cell: square of side dh centred on x_k, clipped to the body. */
-    double wx = (has_w ? half : 0.0) + (has_e ? half : 0.0);
-    double wy = (has_s ? half : 0.0) + (has_n ? half : 0.0);
-    double vol = wx * wy;
+    const double* cd = L->cell + 5 * k;   /* V_C, side lengths E, N, W, S */
+    double vol = cd[0];
     double sk[3];
     stress(L, L->ux, L->uy, i, j, sk);
     /* External part: integral of t* over dC_ext, supplied per point, at t
      * (readings R12, R13). */
     double sn = load_factor(L, 0, (double)L->steps * L->dt);
     double fx = sn * L->bc[2 * k], fy = sn * L->bc[2 * k + 1];
-    /* Internal part: one face per neighbour r, normal n_kr pointing to r,
-     * length l_kr, stress sigma_kr = (sigma_k + sigma_r)/2. */
+    /* Internal part: one side per direction, normal n_kr = e_alpha, length
+     * l_kr; stress (sigma_k + sigma_r)/2 towards a body neighbour r, sigma_k
+     * on a side with no body neighbour that lies partly in the body. */
     for (int a = 1; a < 5; ++a) {
         int ri, rj;
-        if (!neighbour(L, i, j, EX[a], EY[a], &ri, &rj)) continue;
+        double len = cd[a];
+        int has = neighbour(L, i, j, EX[a], EY[a], &ri, &rj);
+        if (!has && !(len > 0.0)) continue;
         double sr[3];
-        stress(L, L->ux, L->uy, ri, rj, sr);
+        if (has) stress(L, L->ux, L->uy, ri, rj, sr);
+        else for (int q = 0; q < 3; ++q) sr[q] = sk[q];
         double sxx = 0.5 * (sk[0] + sr[0]);
         double syy = 0.5 * (sk[1] + sr[1]);
         double sxy = 0.5 * (sk[2] + sr[2]);
         double nx_ = (double)EX[a], ny_ = (double)EY[a];
-        double len = (EX[a] != 0) ? wy : wx;
         fx += (sxx * nx_ + sxy * ny_) * len;
         fy += (sxy * nx_ + syy * ny_) * len;
     }
@@ -441,6 +503,7 @@ static void synchronise(ora_lattice* L) {
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             long k = at(L, i, j);
+            if (is_void(L, k)) continue;
             double snew[2];
             snew[0] = fd_div(L, L->ux, L->uy, i, j);
             snew[1] = fd_curl(L, L->ux, L->uy, i, j);
@@ -484,7 +547,7 @@ static void one_step(ora_lattice* L) {
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             long k = at(L, i, j);
-            if (L->type[k] == 0) continue;
+            if (L->type[k] == 0 || is_void(L, k)) continue;
             double snew[2];
             snew[0] = fd_div(L, L->ux1, L->uy1, i, j);
             snew[1] = fd_curl(L, L->ux1, L->uy1, i, j);
@@ -505,6 +568,7 @@ static void one_step(ora_lattice* L) {
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             long k = at(L, i, j);
+            if (is_void(L, k)) continue;  /* no state, never a source */
             int bnd = L->type[k] != 0;
             for (int set = 0; set < 2; ++set) {
                 double fold[5], fhat[5], s, jx, jy;
@@ -591,6 +655,10 @@ int ora_read(ora_lattice* L, int32_t field, double* dst) {
         for (int j = 0; j < ny; ++j) {
             for (int i = 0; i < nx; ++i) {
                 long k = at(L, i, j);
+                if (is_void(L, k)) {
+                    dst[k] = 0.0;
+                    continue;
+                }
                 double d_psi = L->s[1][k] - fd_curl(L, L->ux, L->uy, i, j);
                 double d_phi = L->s[0][k] - fd_div(L, L->ux, L->uy, i, j);
                 dst[k] = sqrt(d_psi * d_psi + d_phi * d_phi);

@@ -41,12 +41,20 @@ typedef struct ora_params {
 typedef struct ora_lattice ora_lattice;
 
 /* node_type[ny][nx]: 0 interior, 1 Neumann, 2 Dirichlet.  Non-zero exactly on
- * the outer ring of non-periodic directions.  bc_value[ny][nx][2]: prescribed
+ * the outer ring of non-periodic directions (see ora_create_cells for void
+ * points).  bc_value[ny][nx][2]: prescribed
  * displacement u* at Dirichlet points, integrated external force
  * F = int_{dC_ext} t* da at Neumann points (Eq. acc_neumann), ignored at
  * interior points.  Returns NULL on invalid input. */
 ora_lattice* ora_create(const ora_params* p, const uint8_t* node_type,
                         const double* bc_value);
+
+/* As ora_create for a general geometry (reading R14): node_type may also
+ * hold 3 (void, not in the body); cell[ny][nx][5] gives, at boundary
+ * points, the cell area V_C and the length in the body of the cell's sides
+ * towards E, N, W, S (NULL: the clipped squares of a rectangle, R6). */
+ora_lattice* ora_create_cells(const ora_params* p, const uint8_t* node_type,
+                              const double* bc_value, const double* cell);
 void ora_destroy(ora_lattice* L);
 
 /* Derived constants of Eq. conditions-parameters: c_d, c_s, a_phi, a_psi,

@@ -240,6 +240,118 @@ def shear_square(n=64, a0_phi=0.9999, horizon=1.0, sync_every=50):
                   loads=((NEUMANN, T, math.inf),), steps=int(round(horizon * T / dt)), sync_every=sync_every)
 
 
+# ------------------------------------------------ plate with a circular hole
+
+def _disk_strip_area(x0, x1, y0, y1, cx, cy, r):
+    """Area of the rectangle [x0, x1] x [y0, y1] inside the disk of radius r
+    around (cx, cy): the chord overlap integrated in x piece by piece (between
+    the x where the circle crosses y0 or y1, or ends, each piece is a fixed
+    combination of straight lines and circle arcs, integrated exactly)."""
+    if x1 <= x0 or y1 <= y0:
+        return 0.0
+    F = lambda u: 0.5 * (u * math.sqrt(max(r * r - u * u, 0.0)) + r * r * math.asin(max(-1.0, min(1.0, u / r))))
+    cuts = {x0, x1, min(max(cx - r, x0), x1), min(max(cx + r, x0), x1)}
+    for y in (y0, y1):
+        if abs(y - cy) < r:
+            w = math.sqrt(r * r - (y - cy) ** 2)
+            for x in (cx - w, cx + w):
+                if x0 < x < x1:
+                    cuts.add(x)
+    xs = sorted(cuts)
+    area = 0.0
+    for a, b in zip(xs[:-1], xs[1:]):
+        if b <= a:
+            continue
+        m = 0.5 * (a + b)
+        if abs(m - cx) >= r:
+            continue
+        h = math.sqrt(r * r - (m - cx) ** 2)
+        top_arc, bot_arc = cy + h < y1, cy - h > y0
+        if (top_arc and cy + h <= y0) or (bot_arc and cy - h >= y1) or min(y1, cy + h) <= max(y0, cy - h):
+            continue
+        ia = F(b - cx) - F(a - cx)               # integral of h(x) over [a, b]
+        top = (cy * (b - a) + ia) if top_arc else y1 * (b - a)
+        bot = (cy * (b - a) - ia) if bot_arc else y0 * (b - a)
+        area += top - bot
+    return area
+
+
+def _segment_outside_disk(p0, p1, cx, cy, r):
+    """Length of the axis-parallel segment p0 -> p1 outside the disk."""
+    (ax, ay), (bx, by) = p0, p1
+    length = math.hypot(bx - ax, by - ay)
+    if length == 0.0:
+        return 0.0
+    if ay == by:                                  # horizontal
+        d = ay - cy
+        if abs(d) >= r:
+            return length
+        w = math.sqrt(r * r - d * d)
+        lo, hi = sorted((ax, bx))
+        inside = max(0.0, min(hi, cx + w) - max(lo, cx - w))
+    else:                                         # vertical
+        d = ax - cx
+        if abs(d) >= r:
+            return length
+        w = math.sqrt(r * r - d * d)
+        lo, hi = sorted((ay, by))
+        inside = max(0.0, min(hi, cy + w) - max(lo, cy - w))
+    return length - inside
+
+
+def hole_plate_bc(nx, ny, cx, cy, radius, edge_type, edge_value, dh=1.0):
+    """Node types, boundary values and cells of an nx x ny rectangle of
+    lattice points (body [0, (nx-1) dh] x [0, (ny-1) dh]) with a traction-free
+    circular hole of the given centre and radius (lattice units x dh).
+
+    node_type: 0 interior, 1 Neumann, 2 Dirichlet, 3 void (inside the hole).
+    The outer edges follow the rectangle rules (edge order bottom, right,
+    top, left; traction t* integrated over each cell's external faces; at
+    corners Dirichlet dominates).  Points whose neighbour lies in the hole are
+    Neumann points with F = 0.  cell[j, i] = (V_C, l_E, l_N, l_W, l_S): the
+    square of side dh around each boundary point clipped to the body, and
+    the length in the body of each of its sides (geometry only)."""
+    et = tuple(int(x) for x in edge_type)
+    ev = np.asarray(edge_value, float).reshape(4, 2)
+    X, Y = np.meshgrid(np.arange(nx) * dh, np.arange(ny) * dh)
+    void = np.hypot(X - cx * dh, Y - cy * dh) < radius * dh
+    nt = np.zeros((ny, nx), np.uint8)
+    bv = np.zeros((ny, nx, 2))
+    cell = np.zeros((ny, nx, 5))
+    Lx, Ly = (nx - 1) * dh, (ny - 1) * dh
+    R, CX, CY = radius * dh, cx * dh, cy * dh
+    half = 0.5 * dh
+    for j in range(ny):
+        for i in range(nx):
+            if void[j, i]:
+                nt[j, i] = 3
+                continue
+            on = [j == 0, i == nx - 1, j == ny - 1, i == 0]
+            nbr_void = any(0 <= i + di < nx and 0 <= j + dj < ny and void[j + dj, i + di]
+                           for di, dj in ((1, 0), (0, 1), (-1, 0), (0, -1)))
+            if not any(on) and not nbr_void:
+                continue
+            n_dir = sum(1 for e in range(4) if on[e] and et[e] == DIRICHLET)
+            if n_dir:
+                nt[j, i] = DIRICHLET
+                bv[j, i] = sum(ev[e] for e in range(4) if on[e] and et[e] == DIRICHLET) / n_dir
+                continue
+            nt[j, i] = NEUMANN
+            n_on = sum(on)
+            if n_on:
+                bv[j, i] = sum(ev[e] for e in range(4) if on[e]) * (dh if n_on == 1 else half)
+            x, y = i * dh, j * dh
+            x0, x1, y0, y1 = max(x - half, 0.0), min(x + half, Lx), max(y - half, 0.0), min(y + half, Ly)
+            cell[j, i, 0] = (x1 - x0) * (y1 - y0) - _disk_strip_area(x0, x1, y0, y1, CX, CY, R)
+            sides = [((x + half, y0), (x + half, y1)) if x + half <= Lx else None,
+                     ((x0, y + half), (x1, y + half)) if y + half <= Ly else None,
+                     ((x - half, y0), (x - half, y1)) if x - half >= 0.0 else None,
+                     ((x0, y - half), (x1, y - half)) if y - half >= 0.0 else None]
+            for q, sd in enumerate(sides):
+                cell[j, i, 1 + q] = 0.0 if sd is None else _segment_outside_disk(sd[0], sd[1], CX, CY, R)
+    return nt, bv, cell
+
+
 def busiest_crop(domain: Domain, side):
     """Origin (x0, y0) of the side x side window holding the most pulse
     centres (windows start on a grid of side / 4; the first in row-major

@@ -524,3 +524,120 @@ def test_load_ramp_only_scales_its_kind():
         a.set_load(3, 1.0)
     with pytest.raises(ValueError):
         a.set_load(1, -1.0)
+
+
+# ------------------------------------------ general geometry (plate with hole)
+
+def _hole_closure_force(nt, cell, sxx, syy, sxy):
+    """Per boundary point, the traction of a uniform stress integrated over
+    the cell's external boundary: by closure of the cell boundary, minus the
+    stress times the sum of e_d l_d over its sides (reading R14)."""
+    E = ((1, 0), (0, 1), (-1, 0), (0, -1))
+    fx = np.zeros(nt.shape)
+    fy = np.zeros(nt.shape)
+    for q, (ex, ey) in enumerate(E):
+        l = cell[..., 1 + q]
+        fx -= (sxx * ex + sxy * ey) * l
+        fy -= (sxy * ex + syy * ey) * l
+    bv = np.stack([fx, fy], axis=-1)
+    bv[nt != 1] = 0.0
+    return bv
+
+
+def test_hole_patch_uniform_strain():
+    """A uniform strain in a plate with a hole, loaded on every boundary cell
+    by the traction sigma n of the uniform stress, stays static: the
+    one-sided differences at the hole are exact for a linear field, and the
+    cell faces (with sigma_k on sides facing the hole) balance the external
+    force exactly (readings R4, R14)."""
+    nx, ny, lam, mu = 31, 27, 1.3, 1.0
+    nt, _, cell = W.hole_plate_bc(nx, ny, 14.6, 12.8, 4.4, (1, 1, 1, 1), np.zeros(8))
+    exx, eyy, exy = 2e-4, -1e-4, 0.5e-4
+    sxx = lam * (exx + eyy) + 2 * mu * exx
+    syy = lam * (exx + eyy) + 2 * mu * eyy
+    sxy = 2 * mu * exy
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    ux = exx * X + exy * Y
+    uy = exy * X + eyy * Y
+    ux[nt == 3] = 0.0
+    uy[nt == 3] = 0.0
+    bv = _hole_closure_force(nt, cell, sxx, syy, sxy)
+    lat = O.OracleLattice(nx, ny, lam, mu, a0_phi=0.99, node_type=nt, bc_value=bv, cell=cell)
+    lat.init(ux, uy).step(300)
+    body = nt != 3
+    assert np.abs(lat.read(O.UX) - ux)[body].max() <= 1e-13
+    assert np.abs(lat.read(O.UY) - uy)[body].max() <= 1e-13
+    assert np.abs(lat.read(O.UX)[~body]).max() == 0.0
+
+
+def test_explicit_rectangle_cells_equal_default():
+    """Cells from the general geometry generator on a rectangle without hole
+    are the clipped squares of R6; given explicitly they give the same bits
+    as the built-in rule."""
+    nx, ny = 17, 13
+    ev = np.array([1e-4, -2e-4, 0, 3e-4, -1e-4, 0, 2e-4, 1e-4])
+    et = (1, 2, 1, 1)
+    nt, bv, cell = W.hole_plate_bc(nx, ny, -50.0, -50.0, 1.0, et, ev)
+    nt0, bv0 = O.rect_bc(nx, ny, et, ev)
+    assert np.array_equal(nt, nt0) and np.array_equal(bv, bv0)
+    ux, uy = W.pulse_displacement(nx, ny, 7.0, 6.0, 2.5, 1e-3, "rotation")
+    a = O.OracleLattice(nx, ny, 1.2, 1.0, a0_phi=0.99, node_type=nt, bc_value=bv).init(ux, uy).step(40)
+    b = O.OracleLattice(nx, ny, 1.2, 1.0, a0_phi=0.99, node_type=nt, bc_value=bv, cell=cell).init(ux, uy).step(40)
+    for f in (O.UX, O.UY, O.VX, O.VY, O.F_PHI, O.F_PSI):
+        assert np.array_equal(a.read(f), b.read(f)), f
+
+
+def test_hole_mirror_symmetry():
+    """A centred hole and a centred dilatation pulse in a traction-free
+    plate: the solution is mirror-symmetric in x and in y."""
+    n = 33
+    nt, bv, cell = W.hole_plate_bc(n, n, 16.0, 16.0, 5.5, (1, 1, 1, 1), np.zeros(8))
+    ux, uy = W.pulse_displacement(n, n, 16.0, 16.0, 6.0, 1e-3, "dilatation")
+    ux[nt == 3] = 0.0
+    uy[nt == 3] = 0.0
+    lat = O.OracleLattice(n, n, 2.0, 1.0, a0_phi=0.999, node_type=nt, bc_value=bv, cell=cell).init(ux, uy)
+    lat.step(400)
+    gx, gy = lat.read(O.UX), lat.read(O.UY)
+    scale = np.abs(gx).max()
+    assert scale > 1e-5
+    assert np.abs(gx + gx[:, ::-1]).max() <= 1e-12 * scale
+    assert np.abs(gy - gy[:, ::-1]).max() <= 1e-12 * scale
+    assert np.abs(gx - gx[::-1, :]).max() <= 1e-12 * scale
+    assert np.abs(gx - gy.T).max() <= 1e-12 * scale                   # diagonal symmetry
+
+
+def test_geometry_rejected_without_stencil():
+    """A body point whose differences have no stencil (a one-point-thin
+    ligament next to the hole) or a wrong node type makes the lattice
+    invalid."""
+    nx, ny = 12, 9
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 1, 1), np.zeros(8))
+    bad = nt.copy()
+    bad[:, 2] = 3            # void column: column 1 is left with one neighbour column (0)
+    bad[:, 3] = 1
+    bad[0, 2] = bad[-1, 2] = 3
+    with pytest.raises(ValueError):
+        O.OracleLattice(nx, ny, 1.0, 1.0, node_type=bad, bc_value=bv)
+    wrong = nt.copy()
+    wrong[4, 5] = 1          # an interior point marked Neumann
+    with pytest.raises(ValueError):
+        O.OracleLattice(nx, ny, 1.0, 1.0, node_type=wrong, bc_value=bv)
+
+
+def test_hole_init_quadratic_exact():
+    """Initialisation of a plate with a hole from a quadratic u: phi, psi by
+    the differences of R4/R14 (one-sided three-point next to the hole) equal
+    the exact divergence and curl at every body point."""
+    nx, ny = 30, 26
+    nt, bv, cell = W.hole_plate_bc(nx, ny, 13.7, 12.2, 4.8, (1, 1, 1, 1), np.zeros(8))
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    ux = 1e-4 * (0.3 * X * X - 0.2 * X * Y + 0.1 * Y * Y + X)
+    uy = 1e-4 * (-0.1 * X * X + 0.4 * X * Y - 0.25 * Y * Y + 2 * Y)
+    div = 1e-4 * (0.6 * X - 0.2 * Y + 1) + 1e-4 * (0.4 * X - 0.5 * Y + 2)
+    curl = 1e-4 * (-0.2 * X + 0.4 * Y) - 1e-4 * (-0.2 * X + 0.2 * Y)
+    body = nt != 3
+    lat = O.OracleLattice(nx, ny, 1.0, 1.0, node_type=nt, bc_value=bv, cell=cell).init(ux * body, uy * body)
+    scale = np.abs(div).max()
+    assert np.abs(lat.read(O.PHI) - div)[body].max() <= 1e-12 * scale
+    assert np.abs(lat.read(O.PSI) - curl)[body].max() <= 1e-12 * scale
+    assert np.abs(lat.read(O.PHI)[~body]).max() == 0.0
