@@ -89,12 +89,23 @@ def workload(name, size=None):
         return f"waves_{size}", W.periodic_waves(size=size)
     if name == "square":
         return "square_64", W.square_64()
+    if name == "hole":
+        size = size or 8192
+        d, nt, bv, cell = W.hole_square(size)
+        d.geometry = (nt, bv, cell)
+        return f"hole_{size}", d
     raise SystemExit(f"unknown workload {name}")
 
 
 def describe(d):
     bc = {1: "N", 2: "D"}
     edges = "periodic" if d.periodic_x and d.periodic_y else "".join(bc[e] for e in d.edge_type)
+    if getattr(d, "geometry", None) is not None:
+        nt = d.geometry[0]
+        return {"nx": d.nx, "ny": d.ny, "lambda_over_mu": d.lam / d.mu, "a0_phi": d.a0_phi,
+                "edges_bottom_right_top_left": edges, "hole": "centred, diameter 0.266 L, traction-free",
+                "void_points": int((nt == 3).sum()), "boundary_points": int(((nt == 1) | (nt == 2)).sum()),
+                "loads": "tension ramp to 0.005 mu at L/c_s", "sync_every": d.sync_every}
     return {"nx": d.nx, "ny": d.ny, "lambda_over_mu": d.lam / d.mu, "a0_phi": d.a0_phi,
             "edges_bottom_right_top_left": edges, "pulses": len(d.pulses), "wave": d.wave}
 
@@ -194,6 +205,25 @@ def oracle_sample(d, target_seconds=15.0, side=1024):
 
     threads = os.cpu_count() or 1
     O.set_threads(threads)
+    if getattr(d, "geometry", None) is not None:
+        # the same plate with a hole at side x side, loads and synchronisation
+        n = min(side, d.nx)
+        dd, nt, bv, cell = W.hole_square(n, a0_phi=d.a0_phi, sync_every=d.sync_every)
+        lat = O.OracleLattice(n, n, dd.lam, dd.mu, dd.rho, a0_phi=dd.a0_phi, node_type=nt, bc_value=bv,
+                              cell=cell, sync_every=dd.sync_every)
+        for kind, t_ramp, t_hold in dd.loads:
+            lat.set_load(kind, t_ramp, t_hold)
+        lat.init(np.zeros((n, n)), np.zeros((n, n)))
+        t0 = time.perf_counter()
+        lat.step(2)
+        per = (time.perf_counter() - t0) / 2
+        steps = max(2, int(target_seconds / max(per, 1e-9)))
+        t0 = time.perf_counter()
+        lat.step(steps)
+        dt = time.perf_counter() - t0
+        return {"value": n * n * steps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+                "sample": f"{n}x{n} plate with the same hole, loads and synchronisation, {steps} FP64 steps "
+                          f"in {dt:.1f} s"}, dt, steps
     side_x, side_y = min(side, d.nx), min(side, d.ny)
     if d.periodic_x and d.periodic_y:
         c = W.Domain(side_x, side_y, d.lam, d.mu, d.rho, d.a0_phi, periodic_x=True, periodic_y=True)
@@ -440,8 +470,15 @@ def run_gpu(args):
     et = d.edge_type
     ev = np.asarray(d.edge_value, float).ravel()
     stream = torch.cuda.current_stream()
-    mk = dict(a0_phi=d.a0_phi, storage=args.storage, sync_every=args.sync_every)
-    if d.periodic_x and d.periodic_y:
+    geometry = getattr(d, "geometry", None)
+    sync_every = args.sync_every if args.sync_every or geometry is None else d.sync_every
+    mk = dict(a0_phi=d.a0_phi, storage=args.storage, sync_every=sync_every)
+    if geometry is not None:
+        nt, bv, cell = geometry
+        lat = lbps.Lattice(d.nx, d.ny, d.lam, d.mu, d.rho, node_type=nt, bc_value=bv, cell=cell, **mk)
+        for kind, t_ramp, t_hold in d.loads:
+            lat.set_load(kind, t_ramp, t_hold)
+    elif d.periodic_x and d.periodic_y:
         lat = lbps.Lattice(d.nx, d.ny, d.lam, d.mu, d.rho, periodic_x=True, periodic_y=True, **mk)
     else:
         lat = lbps.Lattice.rectangle(d.nx, d.ny, d.lam, d.mu, et, ev, **mk)
@@ -476,7 +513,9 @@ def run_gpu(args):
     prof = lbps.lbps_profile_read(lat._h)
     lbps.lbps_profile(lat._h, 0)
     seconds = e0.elapsed_time(e1) / 1000.0
-    units = d.nx * d.ny * args.steps
+    # lattice updates: body points (void points of a general geometry hold no state)
+    points = int((geometry[0] != 3).sum()) if geometry is not None else d.nx * d.ny
+    units = points * args.steps
 
     rmax, rsum = reducers(dist, "cuda")
     value_ups, t_max, units_all = aggregate(seconds, units, world, rmax, rsum)
@@ -484,8 +523,12 @@ def run_gpu(args):
 
     # roofline of the dominant (bulk) kernel
     bulk_ms, bulk_n, bnd_ms, bnd_n = (float(x) for x in prof)
-    interior = (d.nx - (0 if d.periodic_x else 2)) * (d.ny - (0 if d.periodic_y else 2))
-    alg_bytes = interior * BYTES_PER_UPDATE[args.storage]
+    if geometry is not None:  # interior points only; the kernel also reads one node-type byte per point
+        interior = int((geometry[0] == 0).sum())
+        alg_bytes = interior * (BYTES_PER_UPDATE[args.storage] + 1)
+    else:
+        interior = (d.nx - (0 if d.periodic_x else 2)) * (d.ny - (0 if d.periodic_y else 2))
+        alg_bytes = interior * BYTES_PER_UPDATE[args.storage]
     bulk_avg_s = bulk_ms / max(bulk_n, 1) / 1000.0
     peak, peak_kind = measured_peaks()
     achieved = alg_bytes / bulk_avg_s / 1e9
@@ -497,7 +540,7 @@ def run_gpu(args):
                 "share_of_step_kernel_time": bulk_ms / total_kernel_ms if total_kernel_ms else None,
                 "boundary_passes_ms_per_step": bnd_ms / args.steps}
     bounded = not (d.periodic_x and d.periodic_y)
-    gpu_launches = int(bulk_n) * (4 if bounded else 1) + (args.steps // args.sync_every if args.sync_every else 0)
+    gpu_launches = int(bulk_n) * (4 if bounded else 1) + (args.steps // sync_every if sync_every else 0)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -518,7 +561,7 @@ def run_gpu(args):
         barrier()
         if rc != 0:
             raise SystemExit(f"e2e step failed: {lbps.lbps_strerror(rc)}")
-        e2e_ups, _, _ = aggregate(t1 - t0, d.nx * d.ny * args.e2e_steps, world, rmax, rsum)
+        e2e_ups, _, _ = aggregate(t1 - t0, points * args.e2e_steps, world, rmax, rsum)
         e2e = {"value": e2e_ups / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 2 * d.nx * d.ny * 8, "d2h_bytes_per_step": 2 * d.nx * d.ny * 8,
                "step": f"one solve: lbps_init from pinned host u0, lbps_step({args.e2e_steps}), "
@@ -537,7 +580,7 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.storage == "f64" else "f32",
                 "data": "synthetic",
                 "config": {"workload": wname, **describe(d), "storage": args.storage,
-                           "displacement": "f64", "sync_every": args.sync_every,
+                           "displacement": "f64", "sync_every": sync_every,
                            "l2": "state larger than L2" if alg_bytes > 1.3e8 else "state fits L2",
                            "replicas_per_gpu": 1},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
@@ -557,7 +600,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="pulses", choices=["pulses", "waves", "square", "batch", "serve"])
+    ap.add_argument("--workload", default="pulses", choices=["pulses", "waves", "square", "hole", "batch", "serve"])
     ap.add_argument("--requests", type=int, default=64, help="serve: requests in the Poisson stream")
     ap.add_argument("--serve-sample", type=int, default=6, help="serve: solves timed to set the arrival rate")
     ap.add_argument("--rate-factor", type=float, default=0.8, help="serve: arrival rate / loop capacity")

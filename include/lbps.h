@@ -46,6 +46,7 @@ extern "C" {
 #define LBPS_INTERIOR 0
 #define LBPS_NEUMANN 1          /* traction t* prescribed: Eq. acc_neumann    */
 #define LBPS_DIRICHLET 2        /* displacement u* prescribed: Eq. acc_dirichlet */
+#define LBPS_VOID 3             /* not in the body (lbps_create_cells only)    */
 
 /* Storage of the populations (Eq. interpretation).  u and du/dt are FP64 in
  * every format.  The 16-bit formats store, per set, the conserved moments
@@ -127,6 +128,29 @@ int lbps_state_bytes(const lbps_params* params, size_t* bytes);
  * aligned, owned by the caller.  On success *out owns the lattice. */
 int lbps_create(const lbps_params* params, const uint8_t* node_type, const double* bc_value,
                 void* device_mem, size_t device_bytes, lbps_lattice** out);
+
+/* General geometry (Sec. 3 preprocessing, Sec. 4 plate with a hole; the
+ * paper does not detail its cells, this is the library's reading):
+ * node_type may also hold LBPS_VOID (points outside the body, e.g. inside a
+ * hole).  A body point with a neighbour outside the body is a boundary point
+ * and must be Neumann or Dirichlet; all others interior.  cell[ny][nx][5]
+ * (may be NULL) gives at Neumann points the cell of side dh around the point
+ * clipped to the body: its area V_C and the length in the body of its sides
+ * towards E, N, W, S; NULL uses the square clipped at missing neighbours.
+ * A side towards a body neighbour carries the averaged stress of Eq.
+ * acc_neumann, a side towards none that lies partly in the body the point's
+ * own stress (a uniform stress is then in equilibrium); bc_value gives the
+ * force on the rest of the cell boundary.  Differences are central where both
+ * neighbours are in the body, otherwise one-sided three-point towards it;
+ * LBPS_ERR_INVALID if a body point has no such stencil along x or y, if the
+ * node types do not match the body, or, with 16-bit storage, if a point has
+ * boundary neighbours on both sides along an axis.  The interior kernel then
+ * reads one byte of node type per point.  device_bytes: at least
+ * lbps_state_bytes_cells.  Otherwise as lbps_create. */
+int lbps_state_bytes_cells(const lbps_params* params, const uint8_t* node_type, const double* cell,
+                           size_t* bytes);
+int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const double* bc_value,
+                      const double* cell, void* device_mem, size_t device_bytes, lbps_lattice** out);
 
 /* Initialisation (Fig. 3; Sec. 3 before Eq. integration): u(x,0), du/dt(x,0)
  * from host arrays [ny][nx]; phi, psi by finite differences of u; the

@@ -360,6 +360,8 @@ int ora_init(ora_lattice* L, const double* ux0, const double* uy0, const double*
         memset(L->vx, 0, (size_t)n * sizeof(double));
         memset(L->vy, 0, (size_t)n * sizeof(double));
     }
+    for (long k = 0; k < n; ++k)  /* void points hold no state */
+        if (is_void(L, k)) L->ux[k] = L->uy[k] = L->vx[k] = L->vy[k] = 0.0;
     /* Fig. 3, initialisation: phi = div u, psi = curl u by finite differences,
      * then f = f_eq (Eq. feq); first moments from reading R9. */
 #pragma omp parallel for num_threads(g_threads) schedule(static)

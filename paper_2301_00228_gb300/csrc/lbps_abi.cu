@@ -48,20 +48,23 @@ int validate_params(const lbps_params* p) {
     return LBPS_OK;
 }
 
-Layout make_layout(const lbps_params* p) {
+// general: node types from a type plane (void points, given cells); nb_general:
+// the number of boundary points then (a rectangle's is its perimeter).
+Layout make_layout(const lbps_params* p, bool general = false, int nb_general = 0) {
     Layout L{};
     L.g.nx = p->nx;
     L.g.ny = p->ny;
     L.g.px = (p->nx + 31) / 32 * 32;
     L.g.periodic_x = p->periodic_x;
     L.g.periodic_y = p->periodic_y;
+    L.g.general = general ? 1 : 0;
     L.g.plane = (size_t)L.g.px * (size_t)p->ny;
     const size_t per_point =
         lbps::with_policy(p->storage, [](auto pol) { return (size_t)decltype(pol)::kBytesPerPoint; });
     L.f_bytes = align_up(L.g.plane * per_point);
     L.u_bytes = align_up(4 * L.g.plane * 8);
     L.copy_bytes = L.f_bytes + L.u_bytes;
-    L.nb = lbps::perim_count(L.g);
+    L.nb = general ? nb_general : lbps::perim_count(L.g);
     size_t off = 0;
     L.off_copy[0] = off;
     off += L.copy_bytes;
@@ -69,8 +72,10 @@ Layout make_layout(const lbps_params* p) {
     off += L.copy_bytes;
     L.off_bn = off;
     off += align_up((size_t)L.nb * sizeof(BNode));
-    L.off_sig = off;
-    off += align_up(2 * (size_t)L.nb * 3 * sizeof(double));
+    L.off_sig = off;  // stresses: 2 slots per boundary point (rectangle), 5 (general)
+    off += align_up((general ? 5 : 2) * (size_t)L.nb * 3 * sizeof(double));
+    L.off_type = off;
+    if (general) off += align_up(L.g.plane);
     L.off_part = off;
     off += align_up((size_t)lbps::kNormBlocks * 4 * sizeof(double));
     L.off_out = off;
@@ -103,6 +108,153 @@ KC<T> make_kc(double a_phi, double a_psi, double cd2, double cs2, double dh) {
     k.scale = (T)1;
     k.inv_scale = (T)1;
     return k;
+}
+
+// The boundary list of a lattice, checked against the node types.
+struct Boundary {
+    bool general = false;
+    std::vector<BNode> bn;
+};
+
+// Rectangle (no void points, no cells): the outer ring in perimeter order,
+// cells by reading R6 (computed in the kernel from the indices).  General
+// geometry (reading R14): every body point with a neighbour outside the body,
+// in row-major order, with its cell (given, or the clipped square of R6),
+// its body and interior neighbours; every body point must have a difference
+// stencil along both axes.
+int build_boundary(const lbps_params* p, const uint8_t* node_type, const double* bc_value, const double* cell,
+                   Boundary& out) {
+    const int nx = p->nx, ny = p->ny;
+    bool any_void = false;
+    if (node_type)
+        for (size_t k = 0; k < (size_t)nx * ny; ++k) {
+            if (node_type[k] > 3) return LBPS_ERR_INVALID;
+            any_void = any_void || node_type[k] == 3;
+        }
+    out.general = any_void || cell != nullptr;
+    out.bn.clear();
+    const int DX[4] = {1, 0, -1, 0};
+    const int DY[4] = {0, 1, 0, -1};
+    auto type_at = [&](int i, int j) { return node_type ? node_type[(size_t)j * nx + i] : (uint8_t)LBPS_INTERIOR; };
+    auto body = [&](int i, int j) {
+        if (i < 0 || i >= nx) {
+            if (!p->periodic_x) return false;
+            i = (i + nx) % nx;
+        }
+        if (j < 0 || j >= ny) {
+            if (!p->periodic_y) return false;
+            j = (j + ny) % ny;
+        }
+        return type_at(i, j) != 3;
+    };
+    auto boundary = [&](int i, int j) {
+        if (!body(i, j)) return false;
+        for (int d = 0; d < 4; ++d)
+            if (!body(i + DX[d], j + DY[d])) return true;
+        return false;
+    };
+    auto bvalue = [&](size_t k, double& bx, double& by) {
+        bx = bc_value ? bc_value[2 * k] : 0.0;
+        by = bc_value ? bc_value[2 * k + 1] : 0.0;
+        return std::isfinite(bx) && std::isfinite(by);
+    };
+    if (!out.general) {
+        Geo g{};
+        g.nx = nx;
+        g.ny = ny;
+        g.periodic_x = p->periodic_x;
+        g.periodic_y = p->periodic_y;
+        const int nb = lbps::perim_count(g);
+        out.bn.assign((size_t)nb, BNode{});
+        std::vector<char> seen((size_t)nb, 0);
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                size_t k = (size_t)j * nx + i;
+                int t = type_at(i, j);
+                if (!lbps::is_boundary(i, j, g)) {
+                    if (t != LBPS_INTERIOR) return LBPS_ERR_INVALID;
+                    continue;
+                }
+                if (t != LBPS_NEUMANN && t != LBPS_DIRICHLET) return LBPS_ERR_INVALID;
+                double bx, by;
+                if (!bvalue(k, bx, by)) return LBPS_ERR_INVALID;
+                int q = lbps::perim_index(i, j, g);
+                if (q < 0 || q >= nb || seen[q]) return LBPS_ERR_INVALID;
+                seen[q] = 1;
+                // the one interior neighbour of an edge point (none at corners)
+                bool l = !p->periodic_x && i == 0, r = !p->periodic_x && i == nx - 1;
+                bool b = !p->periodic_y && j == 0, tp = !p->periodic_y && j == ny - 1;
+                int smask = ((l || r) && (b || tp)) ? 0 : l ? 1 : r ? 4 : b ? 2 : 8;
+                BNode node{};
+                node.i = i;
+                node.j = j;
+                node.type = t;
+                node.smask = smask;
+                node.bx = bx;
+                node.by = by;
+                out.bn[q] = node;
+            }
+        }
+        return LBPS_OK;
+    }
+    const double half = 0.5 * p->dh;
+    const bool pairs16 = p->storage == LBPS_STORAGE_BF16 || p->storage == LBPS_STORAGE_F16;
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            size_t k = (size_t)j * nx + i;
+            int t = type_at(i, j);
+            if (t == 3) continue;
+            for (int ax = 0; ax < 2; ++ax) {  // a difference stencil along x and y
+                int dx = ax == 0, dy = ax == 1;
+                bool hp = body(i + dx, j + dy), hm = body(i - dx, j - dy);
+                bool ok = (hp && hm) || (hp && body(i + 2 * dx, j + 2 * dy)) || (hm && body(i - 2 * dx, j - 2 * dy));
+                if (!ok) return LBPS_ERR_INVALID;
+            }
+            const bool bnd = boundary(i, j);
+            if (!bnd) {
+                if (t != LBPS_INTERIOR) return LBPS_ERR_INVALID;
+                // 16-bit storage writes a population pair as a whole: no point
+                // may receive one pair from boundary sources on both sides
+                if (pairs16 && ((boundary(i - 1, j) && boundary(i + 1, j)) || (boundary(i, j - 1) && boundary(i, j + 1))))
+                    return LBPS_ERR_INVALID;
+                continue;
+            }
+            if (t != LBPS_NEUMANN && t != LBPS_DIRICHLET) return LBPS_ERR_INVALID;
+            BNode node{};
+            node.i = i;
+            node.j = j;
+            node.type = t;
+            if (!bvalue(k, node.bx, node.by)) return LBPS_ERR_INVALID;
+            bool has[4];
+            for (int d = 0; d < 4; ++d) {
+                has[d] = body(i + DX[d], j + DY[d]);
+                if (has[d]) node.nbmask |= 1 << d;
+                if (has[d] && !boundary(i + DX[d], j + DY[d])) node.smask |= 1 << d;
+            }
+            if (t == LBPS_NEUMANN) {
+                double vol;
+                if (cell) {
+                    vol = cell[5 * k];
+                    for (int d = 0; d < 4; ++d) node.l[d] = cell[5 * k + 1 + d];
+                    bool ok = std::isfinite(vol) && vol > 0.0;
+                    for (int d = 0; d < 4; ++d) ok = ok && std::isfinite(node.l[d]) && node.l[d] >= 0.0;
+                    if (!ok) return LBPS_ERR_INVALID;
+                } else {  // reading R6: the square of side dh clipped at missing neighbours
+                    double wx = (has[2] ? half : 0.0) + (has[0] ? half : 0.0);
+                    double wy = (has[3] ? half : 0.0) + (has[1] ? half : 0.0);
+                    vol = wx * wy;
+                    node.l[0] = has[0] ? wy : 0.0;
+                    node.l[1] = has[1] ? wx : 0.0;
+                    node.l[2] = has[2] ? wy : 0.0;
+                    node.l[3] = has[3] ? wx : 0.0;
+                    if (!(vol > 0.0)) return LBPS_ERR_INVALID;
+                }
+                node.inv_m = 1.0 / (p->rho * vol);
+            }
+            out.bn.push_back(node);
+        }
+    }
+    return LBPS_OK;
 }
 
 }  // namespace
@@ -335,35 +487,37 @@ int lbps_state_bytes(const lbps_params* params, size_t* bytes) {
     return LBPS_OK;
 }
 
+int lbps_state_bytes_cells(const lbps_params* params, const uint8_t* node_type, const double* cell, size_t* bytes) {
+    int rc = validate_params(params);
+    if (rc != LBPS_OK) return rc;
+    if (!bytes) return LBPS_ERR_INVALID;
+    if (!node_type && !cell) {  // a rectangle: the size does not depend on the node types
+        *bytes = make_layout(params).total;
+        return LBPS_OK;
+    }
+    Boundary bd;
+    rc = build_boundary(params, node_type, nullptr, cell, bd);
+    if (rc != LBPS_OK) return rc;
+    *bytes = make_layout(params, bd.general, (int)bd.bn.size()).total;
+    return LBPS_OK;
+}
+
 int lbps_create(const lbps_params* params, const uint8_t* node_type, const double* bc_value, void* device_mem,
                 size_t device_bytes, lbps_lattice** out) {
+    return lbps_create_cells(params, node_type, bc_value, nullptr, device_mem, device_bytes, out);
+}
+
+int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const double* bc_value,
+                      const double* cell, void* device_mem, size_t device_bytes, lbps_lattice** out) {
     if (!out) return LBPS_ERR_INVALID;
     *out = nullptr;
     int rc = validate_params(params);
     if (rc != LBPS_OK) return rc;
-    Layout L = make_layout(params);
-    const Geo& g = L.g;
-    // Boundary list in perimeter order, checked against the mask.
-    std::vector<BNode> bn((size_t)L.nb);
-    std::vector<char> seen((size_t)L.nb, 0);
-    for (int j = 0; j < g.ny; ++j) {
-        for (int i = 0; i < g.nx; ++i) {
-            size_t k = (size_t)j * g.nx + i;
-            int t = node_type ? node_type[k] : LBPS_INTERIOR;
-            bool bnd = lbps::is_boundary(i, j, g);
-            if (!bnd) {
-                if (t != LBPS_INTERIOR) return LBPS_ERR_INVALID;
-                continue;
-            }
-            if (t != LBPS_NEUMANN && t != LBPS_DIRICHLET) return LBPS_ERR_INVALID;
-            double bx = bc_value ? bc_value[2 * k] : 0.0, by = bc_value ? bc_value[2 * k + 1] : 0.0;
-            if (!std::isfinite(bx) || !std::isfinite(by)) return LBPS_ERR_INVALID;
-            int q = lbps::perim_index(i, j, g);
-            if (q < 0 || q >= L.nb || seen[q]) return LBPS_ERR_INVALID;
-            seen[q] = 1;
-            bn[q] = BNode{i, j, t, 0, bx, by};
-        }
-    }
+    Boundary bd;
+    rc = build_boundary(params, node_type, bc_value, cell, bd);
+    if (rc != LBPS_OK) return rc;
+    Layout L = make_layout(params, bd.general, (int)bd.bn.size());
+    const std::vector<BNode>& bn = bd.bn;
     lbps_lattice* lat = new (std::nothrow) lbps_lattice();
     if (!lat) return LBPS_ERR_OOM;
     lat->p = *params;
@@ -423,8 +577,12 @@ int lbps_create(const lbps_params* params, const uint8_t* node_type, const doubl
     lat->cur = 0;
     lat->steps = 0;
     lat->initialised = false;
+    if (L.g.general) lat->L.g.type = reinterpret_cast<const uint8_t*>(lat->mem + L.off_type);
     cudaError_t e = cudaMemsetAsync(lat->mem, 0, L.total, lat->st);
     if (e == cudaSuccess) e = lbps::set_check_range(lat->mem, L.total, lat->st);
+    if (e == cudaSuccess && L.g.general && node_type)
+        e = cudaMemcpy2DAsync(lat->mem + L.off_type, (size_t)L.g.px, node_type, (size_t)L.g.nx, (size_t)L.g.nx,
+                              (size_t)L.g.ny, cudaMemcpyHostToDevice, lat->st);
     if (e == cudaSuccess && L.nb > 0)
         e = cudaMemcpyAsync(lat->mem + L.off_bn, bn.data(), bn.size() * sizeof(BNode), cudaMemcpyHostToDevice,
                             lat->st);

@@ -41,11 +41,17 @@ __device__ __forceinline__ bool chk_ok(const P* p, int line) {
 #endif
 
 // Lattice geometry.  Planes are pitched: row j of a plane starts at j * px.
+// general = 0: a rectangle whose boundary points are its outer ring (node
+// classes from the indices).  general = 1: node types from the plane `type`
+// (0 interior, 1 Neumann, 2 Dirichlet, 3 void), cells given per boundary
+// point (reading R14: a plate with a hole).
 struct Geo {
     int nx, ny;
     int px;              // row pitch in elements (multiple of 32)
     int periodic_x, periodic_y;
+    int general;
     size_t plane;        // px * ny elements per plane
+    const uint8_t* type; // [ny][px] node types (general = 1 only)
 };
 
 // FP64 constants of the method (Eq. conditions-parameters, Eq. integration).
@@ -92,11 +98,15 @@ struct View {
 struct BNode {
     int i, j;
     int type;        // 1 Neumann, 2 Dirichlet
-    int pad;
+    int smask;       // bit d: the neighbour in direction d (E, N, W, S) is interior (Eq. LBE_mod target)
     double bx, by;   // u* (Dirichlet) or integrated external force (Neumann)
+    double inv_m;    // 1 / (rho V_C) of the cell (general geometry)
+    double l[4];     // in-body lengths of the cell's sides E, N, W, S (general geometry)
+    int nbmask;      // bit d: the neighbour in direction d is in the body (general geometry)
+    int pad;
 };
 
-enum { NEUMANN = 1, DIRICHLET = 2 };
+enum { NEUMANN = 1, DIRICHLET = 2, VOID = 3 };
 
 __host__ __device__ inline bool is_boundary(int i, int j, const Geo& g) {
     return (!g.periodic_x && (i == 0 || i == g.nx - 1)) || (!g.periodic_y && (j == 0 || j == g.ny - 1));
@@ -145,6 +155,19 @@ struct Sten {
     double w[3];
 };
 
+// Is (i, j) (wrapped along periodic axes) a point of the body?
+__device__ __forceinline__ bool body_at(const Geo& g, int i, int j) {
+    if (i < 0 || i >= g.nx) {
+        if (!g.periodic_x) return false;
+        i = wrap(i, g.nx);
+    }
+    if (j < 0 || j >= g.ny) {
+        if (!g.periodic_y) return false;
+        j = wrap(j, g.ny);
+    }
+    return !g.general || LBPS_LDG(&g.type[(size_t)j * g.px + i]) != VOID;
+}
+
 __device__ __forceinline__ Sten stencil(int i, int n, int periodic) {
     Sten s;
     if (periodic || (i > 0 && i < n - 1)) {
@@ -157,11 +180,34 @@ __device__ __forceinline__ Sten stencil(int i, int n, int periodic) {
     return s;
 }
 
+// The same choice from the node types (general geometry, reading R14):
+// central where both neighbours along (dx, dy) are in the body, else
+// one-sided towards the body (its existence is checked at creation).
+__device__ __forceinline__ Sten stencil_g(const Geo& g, int i, int j, int dx, int dy) {
+    Sten s;
+    const bool hp = body_at(g, i + dx, j + dy), hm = body_at(g, i - dx, j - dy);
+    if (hp && hm) {
+        s.n = 2; s.d[0] = -1; s.w[0] = -1.0; s.d[1] = 1; s.w[1] = 1.0; s.d[2] = 0; s.w[2] = 0.0;
+    } else if (hp) {
+        s.n = 3; s.d[0] = 0; s.w[0] = -3.0; s.d[1] = 1; s.w[1] = 4.0; s.d[2] = 2; s.w[2] = -1.0;
+    } else {
+        s.n = 3; s.d[0] = 0; s.w[0] = 3.0; s.d[1] = -1; s.w[1] = -4.0; s.d[2] = -2; s.w[2] = 1.0;
+    }
+    return s;
+}
+
+__device__ __forceinline__ Sten stencil_x(const Geo& G, int i, int j) {
+    return G.general ? stencil_g(G, i, j, 1, 0) : stencil(i, G.nx, G.periodic_x);
+}
+__device__ __forceinline__ Sten stencil_y(const Geo& G, int i, int j) {
+    return G.general ? stencil_g(G, i, j, 0, 1) : stencil(j, G.ny, G.periodic_y);
+}
+
 // d/dx and d/dy of a FP64 array with row stride `stride` (reading of the
 // paper's "second order accurate finite differences", Sec. 3.1.2).
 __device__ inline double ddx(const double* __restrict__ g, size_t stride, int i, int j, const Geo& G,
                              double inv2h) {
-    Sten s = stencil(i, G.nx, G.periodic_x);
+    Sten s = stencil_x(G, i, j);
     const double* r = g + (size_t)j * stride;
     double acc = 0.0;
     for (int q = 0; q < s.n; ++q) acc = fma_rn(s.w[q], LBPS_LD(&r[wrap(i + s.d[q], G.nx)]), acc);
@@ -170,7 +216,7 @@ __device__ inline double ddx(const double* __restrict__ g, size_t stride, int i,
 
 __device__ inline double ddy(const double* __restrict__ g, size_t stride, int i, int j, const Geo& G,
                              double inv2h) {
-    Sten s = stencil(j, G.ny, G.periodic_y);
+    Sten s = stencil_y(G, i, j);
     double acc = 0.0;
     for (int q = 0; q < s.n; ++q) acc = fma_rn(s.w[q], LBPS_LD(&g[(size_t)wrap(j + s.d[q], G.ny) * stride + i]), acc);
     return mul_rn(acc, inv2h);

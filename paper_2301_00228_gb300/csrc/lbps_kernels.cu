@@ -45,6 +45,12 @@ __global__ void init_kernel(Geo g, Consts c, KCof<P> k, View<P> A) {
     const double* ux = A.u;
     const double* uy = A.u + g.plane;
     size_t p = (size_t)j * g.px + i;
+    if (!body_at(g, i, j)) {  // void points hold no state: all zero
+        for (int q = 0; q < 4; ++q) LBPS_ST(&A.u[(size_t)q * g.plane + p], 0.0);
+        P::store_eq(A.f, g.plane, p, 0, c.a0[0], c.a[0], 0.0, 0.0, 0.0, k);
+        P::store_eq(A.f, g.plane, p, 1, c.a0[1], c.a[1], 0.0, 0.0, 0.0, k);
+        return;
+    }
     double phi = ddx(ux, g.px, i, j, g, c.inv2h) + ddy(uy, g.px, i, j, g, c.inv2h);
     double psi = ddx(uy, g.px, i, j, g, c.inv2h) - ddy(ux, g.px, i, j, g, c.inv2h);
     double vx = LBPS_LD(&A.u[2 * g.plane + p]), vy = LBPS_LD(&A.u[3 * g.plane + p]);
@@ -68,7 +74,7 @@ __global__ void scale_probe_kernel(Geo g, Consts c, const double* __restrict__ u
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     float est = 0.0f;
-    if (i < g.nx && j < g.ny) {
+    if (i < g.nx && j < g.ny && body_at(g, i, j)) {
         const double* ux = u;
         const double* uy = u + g.plane;
         size_t p = (size_t)j * g.px + i;
@@ -106,10 +112,36 @@ __device__ inline void stress_at(const Geo& g, const Consts& c, const double* ux
 // pointing to r, length l_kr, stress (sigma_k + sigma_r)/2; external force
 // F = int t* da supplied per point.  The stresses come from the stress pass:
 // sig0[b] at boundary point b, sig1[b] at its interior neighbour.
-__device__ inline void accel_neumann(const Geo& g, const Consts& c, const double* __restrict__ sig, int nb, int b,
-                                     int i, int j, double fx, double fy, double& ax, double& ay) {
+// General geometry (reading R14): the cell's side lengths and 1/(rho V_C)
+// come with the point; the stress pass left sigma at b in slot 5b and at
+// its body neighbour in direction d in slot 5b + 1 + d; a side facing no
+// body neighbour but lying partly in the body carries sigma_k.
+__device__ inline void accel_neumann(const Geo& g, const Consts& c, const BNode* __restrict__ bn,
+                                     const double* __restrict__ sig, int nb, int b, int i, int j, double fx,
+                                     double fy, double& ax, double& ay) {
     const int DX[4] = {1, 0, -1, 0};
     const int DY[4] = {0, 1, 0, -1};
+    if (g.general) {
+        const int nbm = LBPS_LD(&bn[b].nbmask);
+        double sk[3];
+        for (int q = 0; q < 3; ++q) sk[q] = LBPS_LD(&sig[(size_t)b * 15 + q]);
+        for (int d = 0; d < 4; ++d) {
+            const double len = LBPS_LD(&bn[b].l[d]);
+            const bool has = (nbm >> d) & 1;
+            if (!has && !(len > 0.0)) continue;
+            double sr[3];
+            for (int q = 0; q < 3; ++q) sr[q] = has ? LBPS_LD(&sig[(size_t)b * 15 + 3 * (1 + d) + q]) : sk[q];
+            double sxx = 0.5 * (sk[0] + sr[0]);
+            double syy = 0.5 * (sk[1] + sr[1]);
+            double sxy = 0.5 * (sk[2] + sr[2]);
+            fx += (sxx * DX[d] + sxy * DY[d]) * len;
+            fy += (sxy * DX[d] + syy * DY[d]) * len;
+        }
+        const double inv_m = LBPS_LD(&bn[b].inv_m);
+        ax = fx * inv_m;
+        ay = fy * inv_m;
+        return;
+    }
     bool has[4];
     has[0] = g.periodic_x || i < g.nx - 1;
     has[1] = g.periodic_y || j < g.ny - 1;
@@ -185,6 +217,19 @@ __device__ inline void boundary_stress(const Geo& g, const Consts& c, const doub
                                        const BNode* __restrict__ bn, int nb, double* __restrict__ sig, int b) {
     int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
     double s[3];
+    if (g.general) {  // slots 5b (the point) and 5b + 1 + d (its body neighbours)
+        const int DX[4] = {1, 0, -1, 0};
+        const int DY[4] = {0, 1, 0, -1};
+        const int nbm = LBPS_LD(&bn[b].nbmask);
+        stress_at(g, c, ux, uy, i, j, s);
+        for (int q = 0; q < 3; ++q) LBPS_ST(&sig[(size_t)b * 15 + q], s[q]);
+        for (int d = 0; d < 4; ++d) {
+            if (!((nbm >> d) & 1)) continue;
+            stress_at(g, c, ux, uy, wrap(i + DX[d], g.nx), wrap(j + DY[d], g.ny), s);
+            for (int q = 0; q < 3; ++q) LBPS_ST(&sig[(size_t)b * 15 + 3 * (1 + d) + q], s[q]);
+        }
+        return;
+    }
     stress_at(g, c, ux, uy, i, j, s);
     for (int q = 0; q < 3; ++q) LBPS_ST(&sig[(size_t)b * 3 + q], s[q]);
     const int dir = inward_dir(i, j, g);
@@ -218,7 +263,7 @@ __device__ inline void boundary_newmark(const Geo& g, const Consts& c, const Vie
         ax = c.two_dt2 * (bx - LBPS_LD(&ux[p])) - c.two_dt * LBPS_LD(&vx[p]);
         ay = c.two_dt2 * (by - LBPS_LD(&uy[p])) - c.two_dt * LBPS_LD(&vy[p]);
     } else {
-        accel_neumann(g, c, sig, nb, b, i, j, bx, by, ax, ay);
+        accel_neumann(g, c, bn, sig, nb, b, i, j, bx, by, ax, ay);
     }
     double ux1, uy1, vx1, vy1;
     newmark(LBPS_LD(&ux[p]), LBPS_LD(&vx[p]), ax, c, ux1, vx1);
@@ -238,7 +283,7 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<
     const double* ux1 = B.u;
     const double* uy1 = B.u + g.plane;
     // Eq. psi_phi_at_bound: differences of u(t + dt) at (i, j).
-    Sten sx = stencil(i, g.nx, g.periodic_x), sy = stencil(j, g.ny, g.periodic_y);
+    Sten sx = stencil_x(g, i, j), sy = stencil_y(g, i, j);
     double dux_dx = 0.0, duy_dx = 0.0, dux_dy = 0.0, duy_dy = 0.0;
     for (int q = 0; q < sx.n; ++q) {
         size_t o = (size_t)j * g.px + wrap(i + sx.d[q], g.nx);
@@ -253,32 +298,37 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<
     double phi = mul_rn(dux_dx, c.inv2h) + mul_rn(duy_dy, c.inv2h);
     double psi = mul_rn(duy_dx, c.inv2h) - mul_rn(dux_dy, c.inv2h);
     // Eq. correction-f with J(x_k, t) of the stored populations, then the value
-    // this point streams into its interior neighbour (Eq. LBE_mod): population
-    // dir of that neighbour, replacing what the interior kernel wrote there.
-    const int dir = inward_dir(i, j, g);
-    const int DX[5] = {0, 1, 0, -1, 0};
-    const int DY[5] = {0, 0, 1, 0, -1};
-    const size_t pin = dir ? (size_t)(j + DY[dir]) * g.px + (i + DX[dir]) : p;
-    V v[2] = {(V)0, (V)0};
+    // this point streams into each interior neighbour (Eq. LBE_mod): the
+    // population travelling that way, replacing what the interior kernel
+    // wrote there (a rectangle's edge point has one such neighbour, a corner
+    // none; next to a hole a point may have several).
+    const int smask = LBPS_LD(&bn[b].smask);
+    V a5s[2][5], b5s[2][5];
 #pragma unroll
     for (int set = 0; set < 2; ++set) {
-        V a5[5];
-        P::load5(A.f, g.plane, p, set, k, a5);
-        double jx = (double)a5[1] - (double)a5[3];
-        double jy = (double)a5[2] - (double)a5[4];
+        P::load5(A.f, g.plane, p, set, k, a5s[set]);
+        double jx = (double)a5s[set][1] - (double)a5s[set][3];
+        double jy = (double)a5s[set][2] - (double)a5s[set][4];
         P::store_eq(B.f, g.plane, p, set, c.a0[set], c.a[set], set == 0 ? phi : psi, jx, jy, k);
-        if (dir != 0) {
-            V b5[5];
-            P::load5(B.f, g.plane, p, set, k, b5);  // the reset values just stored
-            switch (dir) {
-            case 1: v[set] = stream_from_boundary<1, 3>(a5, b5, k, set, c.bc_feq_mode); break;
-            case 2: v[set] = stream_from_boundary<2, 4>(a5, b5, k, set, c.bc_feq_mode); break;
-            case 3: v[set] = stream_from_boundary<3, 1>(a5, b5, k, set, c.bc_feq_mode); break;
-            default: v[set] = stream_from_boundary<4, 2>(a5, b5, k, set, c.bc_feq_mode); break;
+        if (smask) P::load5(B.f, g.plane, p, set, k, b5s[set]);  // the reset values just stored
+    }
+    const int DXS[4] = {1, 0, -1, 0};
+    const int DYS[4] = {0, 1, 0, -1};
+    for (int d = 0; d < 4; ++d) {
+        if (!((smask >> d) & 1)) continue;
+        V v[2];
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+            switch (d) {
+            case 0: v[set] = stream_from_boundary<1, 3>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
+            case 1: v[set] = stream_from_boundary<2, 4>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
+            case 2: v[set] = stream_from_boundary<3, 1>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
+            default: v[set] = stream_from_boundary<4, 2>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
             }
         }
+        const size_t pin = (size_t)wrap(j + DYS[d], g.ny) * g.px + wrap(i + DXS[d], g.nx);
+        P::store1_both(B.f, g.plane, pin, d + 1, v, k);
     }
-    if (dir != 0) P::store1_both(B.f, g.plane, pin, dir, v, k);
     return !isfinite((V)phi + (V)psi);
 }
 
@@ -416,13 +466,15 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
                 out[s][2] = fma_rn(k.two_a[s], Ps[s], -Pf4[s]);
                 out[s][4] = fma_rn(k.two_a[s], Ns[s], -Nf[s][2]);
             }
-            if (out_lane) {
+            const size_t p = at(j);
+            // general geometry: only interior points (boundary and void points
+            // are the boundary passes' or stay zero)
+            if (out_lane && (!g.general || LBPS_LDG(&g.type[p]) == 0)) {
                 double ax, ay;
                 accel_interior<V>(sW[0], sE[0], Ps[0], Ns[0], sW[1], sE[1], Ps[1], Ns[1], k, ax, ay);
                 double u1[4];
                 newmark(Cu[0], Cu[2], ax, c, u1[0], u1[2]);
                 newmark(Cu[1], Cu[3], ay, c, u1[1], u1[3]);
-                const size_t p = at(j);
                 P::store_point(B.f, PL, p, out, k);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) LBPS_ST(&B.u[(size_t)q * PL + p], u1[q]);
@@ -528,7 +580,7 @@ __global__ void sync_kernel(Geo g, Consts c, KCof<P> k, View<P> A) {
     using V = typename P::V;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= g.nx || j >= g.ny) return;
+    if (i >= g.nx || j >= g.ny || !body_at(g, i, j)) return;
     const double* ux = A.u;
     const double* uy = A.u + g.plane;
     size_t p = (size_t)j * g.px + i;
@@ -563,7 +615,8 @@ __device__ inline double field_value(const Geo& g, const Consts& c, const KCof<P
     case FLD_PHI: return moment0_fp64(A, g.plane, p, 0, k);
     case FLD_PSI: return moment0_fp64(A, g.plane, p, 1, k);
     default: {
-        // consistency error e(x, t) of Sec. 4
+        // consistency error e(x, t) of Sec. 4 (0 at void points)
+        if (!body_at(g, i, j)) return 0.0;
         const double* ux = A.u;
         const double* uy = A.u + g.plane;
         double div = ddx(ux, g.px, i, j, g, c.inv2h) + ddy(uy, g.px, i, j, g, c.inv2h);

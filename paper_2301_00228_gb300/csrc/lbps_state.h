@@ -17,7 +17,7 @@ struct Layout {
     size_t u_bytes;     // 4 FP64 planes, aligned
     size_t copy_bytes;
     size_t off_copy[2];
-    size_t off_bn, off_sig, off_part, off_out, off_flag, off_staging;
+    size_t off_bn, off_sig, off_type, off_part, off_out, off_flag, off_staging;
     size_t staging_bytes;
     size_t total;
     int nb;

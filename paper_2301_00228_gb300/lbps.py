@@ -28,7 +28,7 @@ LBPS_ERR_NONFINITE = -4
 LBPS_ERR_TIMEOUT = -5
 LBPS_ERR_STATE = -6
 
-LBPS_INTERIOR, LBPS_NEUMANN, LBPS_DIRICHLET = 0, 1, 2
+LBPS_INTERIOR, LBPS_NEUMANN, LBPS_DIRICHLET, LBPS_VOID = 0, 1, 2, 3
 LBPS_STORAGE_F32, LBPS_STORAGE_F64, LBPS_STORAGE_BF16, LBPS_STORAGE_F16 = 0, 1, 2, 3
 LBPS_UX, LBPS_UY, LBPS_VX, LBPS_VY, LBPS_PHI, LBPS_PSI, LBPS_F_PHI, LBPS_F_PSI, LBPS_CONSISTENCY = range(9)
 FIELDS = {"ux": LBPS_UX, "uy": LBPS_UY, "vx": LBPS_VX, "vy": LBPS_VY, "phi": LBPS_PHI, "psi": LBPS_PSI,
@@ -68,6 +68,8 @@ def _load():
         "lbps_rect_bc": (ctypes.c_int, [i32, i32, i32, i32, ctypes.c_double, vp, vp, vp, vp]),
         "lbps_state_bytes": (ctypes.c_int, [P(lbps_params), P(sz)]),
         "lbps_create": (ctypes.c_int, [P(lbps_params), vp, vp, vp, sz, P(vp)]),
+        "lbps_state_bytes_cells": (ctypes.c_int, [P(lbps_params), vp, vp, P(sz)]),
+        "lbps_create_cells": (ctypes.c_int, [P(lbps_params), vp, vp, vp, vp, sz, P(vp)]),
         "lbps_init": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "lbps_init_device": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "lbps_step": (ctypes.c_int, [vp, i64]),
@@ -145,6 +147,21 @@ def lbps_create(params, node_type, bc_value, device_ptr, device_bytes):
     _check(_lib.lbps_create(ctypes.byref(params), _p(node_type), _p(bc_value),
                             ctypes.c_void_p(device_ptr) if device_ptr else None, device_bytes, ctypes.byref(h)),
            "lbps_create")
+    return h
+
+
+def lbps_state_bytes_cells(params, node_type, cell):
+    n = ctypes.c_size_t(0)
+    _check(_lib.lbps_state_bytes_cells(ctypes.byref(params), _p(node_type), _p(cell), ctypes.byref(n)),
+           "lbps_state_bytes_cells")
+    return int(n.value)
+
+
+def lbps_create_cells(params, node_type, bc_value, cell, device_ptr, device_bytes):
+    h = ctypes.c_void_p()
+    _check(_lib.lbps_create_cells(ctypes.byref(params), _p(node_type), _p(bc_value), _p(cell),
+                                  ctypes.c_void_p(device_ptr) if device_ptr else None, device_bytes,
+                                  ctypes.byref(h)), "lbps_create_cells")
     return h
 
 
@@ -272,7 +289,7 @@ class Lattice:
 
     def __init__(self, nx, ny, lam, mu, rho=1.0, dh=1.0, a0_phi=0.9999, periodic_x=False, periodic_y=False,
                  node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0, storage="f32", pop_scale_exp=0,
-                 stream=None):
+                 stream=None, cell=None):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
@@ -282,12 +299,13 @@ class Lattice:
                                   int(bc_feq_mode), int(sync_every), STORAGES[storage], int(pop_scale_exp),
                                   ctypes.c_void_p(self.stream.cuda_stream))
         self.storage = storage
-        self.nbytes = lbps_state_bytes(self.params)
-        with torch.cuda.stream(self.stream):
-            self._mem = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
         nt = None if node_type is None else np.ascontiguousarray(node_type, np.uint8)
         bv = None if bc_value is None else np.ascontiguousarray(bc_value, np.float64)
-        self._h = lbps_create(self.params, nt, bv, self._mem.data_ptr(), self.nbytes)
+        cl = None if cell is None else np.ascontiguousarray(cell, np.float64)
+        self.nbytes = lbps_state_bytes_cells(self.params, nt, cl)
+        with torch.cuda.stream(self.stream):
+            self._mem = torch.empty(self.nbytes, dtype=torch.uint8, device="cuda")
+        self._h = lbps_create_cells(self.params, nt, bv, cl, self._mem.data_ptr(), self.nbytes)
         c, _ = lbps_info(self._h)
         self.cd, self.cs, self.a_phi, self.a_psi, self.a0_psi, self.dt = (float(x) for x in c)
 

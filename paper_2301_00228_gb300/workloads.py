@@ -313,43 +313,63 @@ def hole_plate_bc(nx, ny, cx, cy, radius, edge_type, edge_value, dh=1.0):
     the length in the body of each of its sides (geometry only)."""
     et = tuple(int(x) for x in edge_type)
     ev = np.asarray(edge_value, float).reshape(4, 2)
-    X, Y = np.meshgrid(np.arange(nx) * dh, np.arange(ny) * dh)
-    void = np.hypot(X - cx * dh, Y - cy * dh) < radius * dh
+    R, CX, CY = radius * dh, cx * dh, cy * dh
+    xs, ys = np.arange(nx) * dh, np.arange(ny) * dh
+    # void points: the rows and columns the disk touches only
+    void = np.zeros((ny, nx), bool)
+    jlo, jhi = max(0, int(math.floor((CY - R) / dh)) - 1), min(ny, int(math.ceil((CY + R) / dh)) + 2)
+    ilo, ihi = max(0, int(math.floor((CX - R) / dh)) - 1), min(nx, int(math.ceil((CX + R) / dh)) + 2)
+    if jlo < jhi and ilo < ihi:
+        XX, YY = np.meshgrid(xs[ilo:ihi], ys[jlo:jhi])
+        void[jlo:jhi, ilo:ihi] = np.hypot(XX - CX, YY - CY) < R
+    nbr_void = np.zeros_like(void)
+    nbr_void[:, :-1] |= void[:, 1:]
+    nbr_void[:, 1:] |= void[:, :-1]
+    nbr_void[:-1, :] |= void[1:, :]
+    nbr_void[1:, :] |= void[:-1, :]
+    ring = np.zeros_like(void)
+    ring[[0, -1], :] = True
+    ring[:, [0, -1]] = True
     nt = np.zeros((ny, nx), np.uint8)
+    nt[void] = 3
     bv = np.zeros((ny, nx, 2))
     cell = np.zeros((ny, nx, 5))
     Lx, Ly = (nx - 1) * dh, (ny - 1) * dh
-    R, CX, CY = radius * dh, cx * dh, cy * dh
     half = 0.5 * dh
-    for j in range(ny):
-        for i in range(nx):
-            if void[j, i]:
-                nt[j, i] = 3
-                continue
-            on = [j == 0, i == nx - 1, j == ny - 1, i == 0]
-            nbr_void = any(0 <= i + di < nx and 0 <= j + dj < ny and void[j + dj, i + di]
-                           for di, dj in ((1, 0), (0, 1), (-1, 0), (0, -1)))
-            if not any(on) and not nbr_void:
-                continue
-            n_dir = sum(1 for e in range(4) if on[e] and et[e] == DIRICHLET)
-            if n_dir:
-                nt[j, i] = DIRICHLET
-                bv[j, i] = sum(ev[e] for e in range(4) if on[e] and et[e] == DIRICHLET) / n_dir
-                continue
-            nt[j, i] = NEUMANN
-            n_on = sum(on)
-            if n_on:
-                bv[j, i] = sum(ev[e] for e in range(4) if on[e]) * (dh if n_on == 1 else half)
-            x, y = i * dh, j * dh
-            x0, x1, y0, y1 = max(x - half, 0.0), min(x + half, Lx), max(y - half, 0.0), min(y + half, Ly)
-            cell[j, i, 0] = (x1 - x0) * (y1 - y0) - _disk_strip_area(x0, x1, y0, y1, CX, CY, R)
-            sides = [((x + half, y0), (x + half, y1)) if x + half <= Lx else None,
-                     ((x0, y + half), (x1, y + half)) if y + half <= Ly else None,
-                     ((x - half, y0), (x - half, y1)) if x - half >= 0.0 else None,
-                     ((x0, y - half), (x1, y - half)) if y - half >= 0.0 else None]
-            for q, sd in enumerate(sides):
-                cell[j, i, 1 + q] = 0.0 if sd is None else _segment_outside_disk(sd[0], sd[1], CX, CY, R)
+    for j, i in zip(*np.nonzero((ring | nbr_void) & ~void)):
+        on = [j == 0, i == nx - 1, j == ny - 1, i == 0]
+        n_dir = sum(1 for e in range(4) if on[e] and et[e] == DIRICHLET)
+        if n_dir:
+            nt[j, i] = DIRICHLET
+            bv[j, i] = sum(ev[e] for e in range(4) if on[e] and et[e] == DIRICHLET) / n_dir
+            continue
+        nt[j, i] = NEUMANN
+        n_on = sum(on)
+        if n_on:
+            bv[j, i] = sum(ev[e] for e in range(4) if on[e]) * (dh if n_on == 1 else half)
+        x, y = i * dh, j * dh
+        x0, x1, y0, y1 = max(x - half, 0.0), min(x + half, Lx), max(y - half, 0.0), min(y + half, Ly)
+        cell[j, i, 0] = (x1 - x0) * (y1 - y0) - _disk_strip_area(x0, x1, y0, y1, CX, CY, R)
+        sides = [((x + half, y0), (x + half, y1)) if x + half <= Lx else None,
+                 ((x0, y + half), (x1, y + half)) if y + half <= Ly else None,
+                 ((x - half, y0), (x - half, y1)) if x - half >= 0.0 else None,
+                 ((x0, y - half), (x1, y - half)) if y - half >= 0.0 else None]
+        for q, sd in enumerate(sides):
+            cell[j, i, 1 + q] = 0.0 if sd is None else _segment_outside_disk(sd[0], sd[1], CX, CY, R)
     return nt, bv, cell
+
+
+def hole_square(n=64, a0_phi=0.9999, horizon=1.0, sync_every=50):
+    """Sec. 4, plate with a hole: the tension square of tension_square with
+    a traction-free circular hole of diameter 0.266 L at its centre (taken
+    centred; the text places the probe point Q at (-0.175 L, 0.025 L) from the
+    hole's centre), synchronised every 50 steps as in the paper.  Returns
+    (Domain, node_type, bc_value, cell)."""
+    d = tension_square(n, a0_phi=a0_phi, horizon=horizon, sync_every=sync_every)
+    L = n - 1.0
+    nt, bv, cell = hole_plate_bc(n, n, 0.5 * L, 0.5 * L, 0.5 * 0.266 * L, d.edge_type,
+                                 np.asarray(d.edge_value, float).ravel())
+    return d, nt, bv, cell
 
 
 def busiest_crop(domain: Domain, side):

@@ -93,3 +93,46 @@ def test_state_bytes(lib):
             setattr(q, k, v)
         with pytest.raises(lib.LbpsError):
             lib.lbps_state_bytes(q)
+
+
+def test_general_geometry_host_checks(lib):
+    """Plate with a hole through the host-side checks of lbps_state_bytes_cells
+    (no GPU needed): a valid hole costs the node-type plane and five stress
+    slots per boundary point; invalid geometries are rejected."""
+    from paper_2301_00228_gb300 import workloads as W
+
+    nx, ny = 40, 36
+    p = lib.lbps_params(nx, ny, 1.0, 1.0, 1.0, 1.0, 0.999, 0, 0, 0, 0, lib.LBPS_STORAGE_F32, 0, None)
+    rect = lib.lbps_state_bytes(p)
+    nt, bv, cell = W.hole_plate_bc(nx, ny, 19.3, 17.6, 5.3, (1, 1, 1, 1), np.zeros(8))
+    hole = lib.lbps_state_bytes_cells(p, nt, cell)
+    assert hole >= rect + 64 * ny                       # + node types (pitched rows)
+    assert lib.lbps_state_bytes_cells(p, None, None) == rect
+    # a one-point ligament: column 1 then has no difference stencil along x
+    bad = nt.copy()
+    bad[:, 2] = lib.LBPS_VOID
+    bad[:, 3] = lib.LBPS_NEUMANN
+    with pytest.raises(lib.LbpsError):
+        lib.lbps_state_bytes_cells(p, bad, None)
+    wrong = nt.copy()
+    wrong[nt == lib.LBPS_NEUMANN] = lib.LBPS_INTERIOR   # boundary points must be Neumann or Dirichlet
+    with pytest.raises(lib.LbpsError):
+        lib.lbps_state_bytes_cells(p, wrong, cell)
+    badcell = cell.copy()
+    badcell[nt == lib.LBPS_NEUMANN, 0] = 0.0              # zero cell area
+    with pytest.raises(lib.LbpsError):
+        lib.lbps_state_bytes_cells(p, nt, badcell)
+    # 16-bit storage: a point between two boundary points along x is rejected
+    two = np.zeros((ny, nx), np.uint8)
+    two[:, [0, nx - 1]] = lib.LBPS_NEUMANN
+    two[[0, ny - 1], :] = lib.LBPS_NEUMANN
+    two[10:20, 12] = lib.LBPS_VOID                        # void column ...
+    two[10:20, 14] = lib.LBPS_VOID                        # ... and another one two points away
+    two[9:21, 11] = lib.LBPS_NEUMANN
+    two[9:21, 15] = lib.LBPS_NEUMANN
+    two[9, 12:15] = lib.LBPS_NEUMANN
+    two[20, 12:15] = lib.LBPS_NEUMANN
+    two[10:20, 13] = lib.LBPS_NEUMANN                     # the column between the voids
+    q = lib.lbps_params(nx, ny, 1.0, 1.0, 1.0, 1.0, 0.999, 0, 0, 0, 0, lib.LBPS_STORAGE_F16, 0, None)
+    with pytest.raises(lib.LbpsError):
+        lib.lbps_state_bytes_cells(q, two, None)
