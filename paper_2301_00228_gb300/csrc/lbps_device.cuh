@@ -256,7 +256,8 @@ __device__ __forceinline__ T sum5(T f0, T f1, T f2, T f3, T f4) {
 // at equilibrium (Eq. feq) each pair sum is 2 a s = 2 (a / a_0) f^0, so
 //   Nx = f^1 + f^3 - 2 r f^0,  Ny = f^2 + f^4 - 2 r f^0   (r = a / a_0)
 // vanish there and carry only the non-equilibrium part.  f^0, Jx, Jy are
-// stored in FP32, Nx, Ny in H multiplied by 2^e.  Decoding:
+// stored in FP32, Nx, Ny in H multiplied by 2^e (half: rounded to nearest;
+// bfloat16: deterministic stochastic rounding, f2bits_store).  Decoding:
 //   f^1 = r f^0 + (Nx + Jx) / 2,  f^3 = r f^0 + (Nx - Jx) / 2  (and y).
 // The first moment stays FP32 because with the small time steps of Sec. 4
 // (a_0 near 1) every rounding of J acts as a momentum kick whose effect on
@@ -358,6 +359,38 @@ __device__ __forceinline__ unsigned f2bits<__nv_bfloat16>(float v) {
     return __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
+// Integer mixing function (the 32-bit finaliser of MurmurHash3): spreads
+// every input bit over the output.
+__device__ __forceinline__ unsigned mix32(unsigned h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// 16-bit code of v with the rounding each format uses for the stored
+// non-equilibrium sums.  IEEE half: round to nearest.  bfloat16: stochastic
+// rounding (up with probability equal to the dropped fraction), with the
+// random bits a hash of the value and of `key` (the point and slot), so the
+// result is a deterministic function of the state.  With an 8-bit
+// significand and the tiny per-step changes of a_0 near 1, rounding to
+// nearest makes nearly the same error every step and the errors add up;
+// unbiased rounding lets them average out.
+template <typename H>
+__device__ __forceinline__ unsigned f2bits_store(float v, unsigned key);
+template <>
+__device__ __forceinline__ unsigned f2bits_store<__half>(float v, unsigned) { return f2bits<__half>(v); }
+template <>
+__device__ __forceinline__ unsigned f2bits_store<__nv_bfloat16>(float v, unsigned key) {
+    const unsigned u = __float_as_uint(v);
+    if (!isfinite(v)) return f2bits<__nv_bfloat16>(v);
+    // adding below the kept bits rounds the magnitude up with the dropped
+    // fraction's probability; a carry into the exponent is the next value up
+    return (u + (mix32(u ^ mix32(key)) & 0xffffu)) >> 16;
+}
+
 template <typename H>
 struct PopNeq16 {
     using V = float;
@@ -386,8 +419,10 @@ struct PopNeq16 {
         x[2] = fma_rn(0.5f, add_rn(ny, jy), rf0);
         x[4] = fma_rn(0.5f, sub_rn(ny, jy), rf0);
     }
-    __device__ __forceinline__ static unsigned enc_n(float pair_sum, float f0, float r, float scale) {
-        return f2bits<H>(mul_rn(fma_rn(-2.0f * r, f0, pair_sum), scale));
+    // key: the point's plane offset and the slot (set, pair) for the rounding
+    __device__ __forceinline__ static unsigned enc_n(float pair_sum, float f0, float r, float scale,
+                                                     unsigned key) {
+        return f2bits_store<H>(mul_rn(fma_rn(-2.0f * r, f0, pair_sum), scale), key);
     }
     __device__ __forceinline__ static void load_raw(const float* __restrict__ f, size_t plane, size_t p, bool ok,
                                                     Raw& r) {
@@ -435,8 +470,9 @@ struct PopNeq16 {
             LBPS_ST(f + (size_t)(s * 3) * plane + p, x[s][0]);
             LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, sub_rn(x[s][1], x[s][3]));
             LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, sub_rn(x[s][2], x[s][4]));
-            wx |= enc_n(add_rn(x[s][1], x[s][3]), x[s][0], k.r[s], k.scale) << (16 * s);
-            wy |= enc_n(add_rn(x[s][2], x[s][4]), x[s][0], k.r[s], k.scale) << (16 * s);
+            wx |= enc_n(add_rn(x[s][1], x[s][3]), x[s][0], k.r[s], k.scale, (unsigned)p * 4u + 2u * s) << (16 * s);
+            wy |= enc_n(add_rn(x[s][2], x[s][4]), x[s][0], k.r[s], k.scale, (unsigned)p * 4u + 2u * s + 1u)
+                  << (16 * s);
         }
         unsigned* w = words(f, plane);
         LBPS_ST(w + p, wx);
@@ -463,7 +499,8 @@ struct PopNeq16 {
             const float rf0 = mul_rn(k.r[s], f0);
             const float partner = plus ? fma_rn(0.5f, sub_rn(nn, j), rf0) : fma_rn(0.5f, add_rn(nn, j), rf0);
             LBPS_ST(jp, plus ? sub_rn(v[s], partner) : sub_rn(partner, v[s]));
-            out |= enc_n(add_rn(v[s], partner), f0, k.r[s], k.scale) << (16 * s);
+            out |= enc_n(add_rn(v[s], partner), f0, k.r[s], k.scale, (unsigned)p * 4u + 2u * s + (unsigned)ax)
+                   << (16 * s);
         }
         LBPS_ST(wp, out);
     }
@@ -477,7 +514,9 @@ struct PopNeq16 {
         LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, (float)jx);
         LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, (float)jy);
         unsigned short nv =
-            (unsigned short)f2bits<H>((float)((2.0 * a * sv - 2.0 * (double)k.r[s] * (double)f0) * (double)k.scale));
+            (unsigned short)f2bits_store<H>((float)((2.0 * a * sv - 2.0 * (double)k.r[s] * (double)f0) *
+                                                    (double)k.scale),
+                                            (unsigned)p * 4u + 2u * s);
         unsigned short* h = reinterpret_cast<unsigned short*>(words(f, plane));
         LBPS_ST(h + 2 * p + s, nv);
         LBPS_ST(h + 2 * (plane + p) + s, nv);

@@ -5,10 +5,11 @@ equilibrium in BF16 or FP16, FP32 arithmetic.
 Parity with the FP64 oracle, relative L2 per field (u_x, u_y, phi, psi)
 taken as in the FP32/FP64 parity tests (a field that vanishes by symmetry is
 measured on its partner's scale).  Targets: 1e-5 for FP32 storage, 1e-3 for
-16-bit storage.  FP16 meets 1e-3 on the many-pulse crop; BF16 does not (8-bit
-significand) and neither does FP16 on the 10^4-step periodic waves, so those
-runs assert the bound they do meet, stated beside each (measured values in
-the comments; the runs are deterministic).  Plus: the storage scale the
+16-bit storage.  FP16 meets 1e-3 on the many-pulse crop; BF16 (8-bit
+significand, stochastic rounding) misses it on the smaller 256^2 crop and
+neither format meets it on the 10^4-step periodic waves, so those runs
+assert the bound they do meet, stated beside each (measured values in the
+comments; the runs are deterministic).  Plus: the storage scale the
 library picks, overflow reported as a non-finite state, host and device
 initialisation identical, batches bit-identical to single lattices.
 """
@@ -22,10 +23,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"f32": 1e-5, "bf16": 1e-3, "f16": 1e-3}
-# bounds met where the target is not (measured: crop bf16 3.1e-3 in phi;
-# periodic 10^4 steps f16 4.7e-3, bf16 8.0e-2, both in u_y)
-CROP_BF16 = 5e-3
-WAVES = {"f16": 1e-2, "bf16": 1e-1}
+# bounds met where the target is not (measured: 256^2 crop bf16 1.7e-3 in
+# phi; periodic 10^4 steps f16 4.7e-3, bf16 9.0e-3, both in u_y).  On the
+# 1024^2 crop of the precision workload (5000 steps, bench.py --precision)
+# bf16 meets 1e-3 (9.0e-4) with its stochastic rounding.
+CROP_BF16 = 3e-3
+WAVES = {"f16": 1e-2, "bf16": 2e-2}
 GROUPS = (("ux", "uy"), ("phi", "psi"))
 
 
