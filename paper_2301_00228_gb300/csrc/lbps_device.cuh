@@ -205,12 +205,17 @@ __device__ __forceinline__ Sten stencil_y(const Geo& G, int i, int j) {
 
 // d/dx and d/dy of a FP64 array with row stride `stride` (reading of the
 // paper's "second order accurate finite differences", Sec. 3.1.2).
+// (A central difference, weights -1 and 1, is one subtraction: the same
+// bits as the weighted sum, fewer FP64 operations.)
 __device__ inline double ddx(const double* __restrict__ g, size_t stride, int i, int j, const Geo& G,
                              double inv2h) {
     Sten s = stencil_x(G, i, j);
     const double* r = g + (size_t)j * stride;
     double acc = 0.0;
-    for (int q = 0; q < s.n; ++q) acc = fma_rn(s.w[q], LBPS_LD(&r[wrap(i + s.d[q], G.nx)]), acc);
+    if (s.n == 2)
+        acc = sub_rn(LBPS_LD(&r[wrap(i + 1, G.nx)]), LBPS_LD(&r[wrap(i - 1, G.nx)]));
+    else
+        for (int q = 0; q < s.n; ++q) acc = fma_rn(s.w[q], LBPS_LD(&r[wrap(i + s.d[q], G.nx)]), acc);
     return mul_rn(acc, inv2h);
 }
 
@@ -218,7 +223,12 @@ __device__ inline double ddy(const double* __restrict__ g, size_t stride, int i,
                              double inv2h) {
     Sten s = stencil_y(G, i, j);
     double acc = 0.0;
-    for (int q = 0; q < s.n; ++q) acc = fma_rn(s.w[q], LBPS_LD(&g[(size_t)wrap(j + s.d[q], G.ny) * stride + i]), acc);
+    if (s.n == 2)
+        acc = sub_rn(LBPS_LD(&g[(size_t)wrap(j + 1, G.ny) * stride + i]),
+                     LBPS_LD(&g[(size_t)wrap(j - 1, G.ny) * stride + i]));
+    else
+        for (int q = 0; q < s.n; ++q)
+            acc = fma_rn(s.w[q], LBPS_LD(&g[(size_t)wrap(j + s.d[q], G.ny) * stride + i]), acc);
     return mul_rn(acc, inv2h);
 }
 
@@ -304,6 +314,13 @@ struct PopDirect {
 #pragma unroll
         for (int s = 0; s < 2; ++s) store5(f, plane, p, s, x[s], k);
     }
+    // Equilibria of both sets at one point (s[set], jx[set], jy[set]).
+    __device__ __forceinline__ static void store_eq_point(T* __restrict__ f, size_t plane, size_t p, const Consts& c,
+                                                          const double (&sv)[2], const double (&jx)[2],
+                                                          const double (&jy)[2], const KC<T>& k) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) store_eq(f, plane, p, s, c.a0[s], c.a[s], sv[s], jx[s], jy[s], k);
+    }
     // One moving population alpha (1..4) of both sets.
     __device__ __forceinline__ static void store1_both(T* __restrict__ f, size_t plane, size_t p, int alpha,
                                                        const T (&v)[2], const KC<T>&) {
@@ -317,9 +334,21 @@ struct PopDirect {
         for (int q = 0; q < 5; ++q) x[q] = (double)LBPS_LD(f + (size_t)(s * 5 + q) * plane + p);
     }
     // Equilibrium of Eq. feq for s and the lattice first moment (jx, jy) (FP64 in).
+    // FP32 storage evaluates it in FP32 (from a and a_0 of the FP32
+    // constants); FP64 storage in FP64.
     __device__ __forceinline__ static void store_eq(T* __restrict__ f, size_t plane, size_t p, int s, double a0,
-                                                    double a, double sv, double jx, double jy, const KC<T>&) {
+                                                    double a, double sv, double jx, double jy, const KC<T>& k) {
         T* b = f + (size_t)s * 5 * plane + p;
+        if constexpr (sizeof(T) == 4) {
+            const float sf = (float)sv, hx = mul_rn(0.5f, (float)jx), hy = mul_rn(0.5f, (float)jy);
+            const float as = mul_rn(k.a[s], sf);
+            LBPS_ST(&b[0], mul_rn(mul_rn(0.5f, k.two_a0[s]), sf));
+            LBPS_ST(&b[plane], add_rn(as, hx));
+            LBPS_ST(&b[2 * plane], add_rn(as, hy));
+            LBPS_ST(&b[3 * plane], sub_rn(as, hx));
+            LBPS_ST(&b[4 * plane], sub_rn(as, hy));
+            return;
+        }
         double as = a * sv;
         LBPS_ST(&b[0], (T)(a0 * sv));
         LBPS_ST(&b[plane], (T)(as + 0.5 * jx));
@@ -504,19 +533,39 @@ struct PopNeq16 {
         }
         LBPS_ST(wp, out);
     }
-    // Equilibrium of Eq. feq for set s: J = (jx, jy) (rounded to FP32), the
-    // pair sums' deviation 2 a s - 2 r f^0 formed in FP64 from the stored f^0,
+    // Equilibria of both sets at one point, each packed word written once.
+    __device__ __forceinline__ static void store_eq_point(float* __restrict__ f, size_t plane, size_t p,
+                                                          const Consts&, const double (&sv)[2],
+                                                          const double (&jx)[2], const double (&jy)[2],
+                                                          const KC<float>& k) {
+        unsigned w = 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float sf = (float)sv[s];
+            const float f0 = mul_rn(mul_rn(0.5f, k.two_a0[s]), sf);
+            LBPS_ST(f + (size_t)(s * 3) * plane + p, f0);
+            LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, (float)jx[s]);
+            LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, (float)jy[s]);
+            const float dev = mul_rn(fma_rn(-2.0f * k.r[s], f0, mul_rn(k.two_a[s], sf)), k.scale);
+            w |= f2bits_store<H>(dev, (unsigned)p * 4u + 2u * s) << (16 * s);
+        }
+        unsigned* wp = words(f, plane);
+        LBPS_ST(wp + p, w);
+        LBPS_ST(wp + plane + p, w);
+    }
+    // Equilibrium of Eq. feq for set s, in FP32: J = (jx, jy), the pair sums'
+    // deviation 2 a s - 2 r f^0 from the stored f^0 (zero up to rounding),
     // written into the set's halves of both words.
     __device__ __forceinline__ static void store_eq(float* __restrict__ f, size_t plane, size_t p, int s, double a0,
                                                     double a, double sv, double jx, double jy, const KC<float>& k) {
-        float f0 = (float)(a0 * sv);
+        const float sf = (float)sv;
+        const float f0 = mul_rn(mul_rn(0.5f, k.two_a0[s]), sf);
         LBPS_ST(f + (size_t)(s * 3) * plane + p, f0);
         LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, (float)jx);
         LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, (float)jy);
-        unsigned short nv =
-            (unsigned short)f2bits_store<H>((float)((2.0 * a * sv - 2.0 * (double)k.r[s] * (double)f0) *
-                                                    (double)k.scale),
-                                            (unsigned)p * 4u + 2u * s);
+        // 2 a s - 2 r f^0 (zero up to rounding), scaled
+        const float dev = mul_rn(fma_rn(-2.0f * k.r[s], f0, mul_rn(k.two_a[s], sf)), k.scale);
+        unsigned short nv = (unsigned short)f2bits_store<H>(dev, (unsigned)p * 4u + 2u * s);
         unsigned short* h = reinterpret_cast<unsigned short*>(words(f, plane));
         LBPS_ST(h + 2 * p + s, nv);
         LBPS_ST(h + 2 * (plane + p) + s, nv);

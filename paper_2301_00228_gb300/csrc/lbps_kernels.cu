@@ -47,8 +47,8 @@ __global__ void init_kernel(Geo g, Consts c, KCof<P> k, View<P> A) {
     size_t p = (size_t)j * g.px + i;
     if (!body_at(g, i, j)) {  // void points hold no state: all zero
         for (int q = 0; q < 4; ++q) LBPS_ST(&A.u[(size_t)q * g.plane + p], 0.0);
-        P::store_eq(A.f, g.plane, p, 0, c.a0[0], c.a[0], 0.0, 0.0, 0.0, k);
-        P::store_eq(A.f, g.plane, p, 1, c.a0[1], c.a[1], 0.0, 0.0, 0.0, k);
+        const double z[2] = {0.0, 0.0};
+        P::store_eq_point(A.f, g.plane, p, c, z, z, z, k);
         return;
     }
     double phi = ddx(ux, g.px, i, j, g, c.inv2h) + ddy(uy, g.px, i, j, g, c.inv2h);
@@ -57,8 +57,8 @@ __global__ void init_kernel(Geo g, Consts c, KCof<P> k, View<P> A) {
     // First moments from du/dt (J_phi = -v, J_psi = (-v_y, v_x)), in lattice
     // units Jbar = J dt / dh (c cancels: c^alpha . J / (2 c^2) = e_alpha . Jbar / 2).
     double q = c.dt / c.dh;
-    P::store_eq(A.f, g.plane, p, 0, c.a0[0], c.a[0], phi, -vx * q, -vy * q, k);
-    P::store_eq(A.f, g.plane, p, 1, c.a0[1], c.a[1], psi, -vy * q, vx * q, k);
+    const double sv[2] = {phi, psi}, jx[2] = {-vx * q, -vy * q}, jy[2] = {-vy * q, vx * q};
+    P::store_eq_point(A.f, g.plane, p, c, sv, jx, jy, k);
 }
 
 // Size of the lattice first moment J that the initial state implies, for the
@@ -587,13 +587,15 @@ __global__ void sync_kernel(Geo g, Consts c, KCof<P> k, View<P> A) {
     double s[2];
     s[0] = ddx(ux, g.px, i, j, g, c.inv2h) + ddy(uy, g.px, i, j, g, c.inv2h);
     s[1] = ddx(uy, g.px, i, j, g, c.inv2h) - ddy(ux, g.px, i, j, g, c.inv2h);
+    double jx[2], jy[2];
     for (int set = 0; set < 2; ++set) {
         V f[5];
         P::load5(A.f, g.plane, p, set, k, f);
-        double jx = (double)f[1] - (double)f[3];
-        double jy = (double)f[2] - (double)f[4];
-        P::store_eq(A.f, g.plane, p, set, c.a0[set], c.a[set], s[set], jx, jy, k);
+        // first moments in the arithmetic type of the storage
+        jx[set] = (double)sub_rn(f[1], f[3]);
+        jy[set] = (double)sub_rn(f[2], f[4]);
     }
+    P::store_eq_point(A.f, g.plane, p, c, s, jx, jy, k);
 }
 
 // ---------------------------------------------------------------- fields
