@@ -596,6 +596,7 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
 }
 
 int lbps_init(lbps_lattice* lat, const double* ux0, const double* uy0, const double* vx0, const double* vy0) {
+    lbps::NvtxRange nvtx("lbps_init");
     if (!lat || !ux0 || !uy0 || (!vx0) != (!vy0)) return LBPS_ERR_INVALID;
     size_t n = (size_t)lat->p.nx * (size_t)lat->p.ny;
     for (size_t k = 0; k < n; ++k) {
@@ -611,11 +612,13 @@ int lbps_init(lbps_lattice* lat, const double* ux0, const double* uy0, const dou
 
 int lbps_init_device(lbps_lattice* lat, const double* d_ux0, const double* d_uy0, const double* d_vx0,
                      const double* d_vy0) {
+    lbps::NvtxRange nvtx("lbps_init_device");
     if (!lat || !d_ux0 || !d_uy0 || (!d_vx0) != (!d_vy0)) return LBPS_ERR_INVALID;
     return init_from(lat, d_ux0, d_uy0, d_vx0, d_vy0, cudaMemcpyDeviceToDevice);
 }
 
 int lbps_step_async(lbps_lattice* lat, int64_t n) {
+    lbps::NvtxRange nvtx("lbps_step_async");
     if (!lat || n < 0) return LBPS_ERR_INVALID;
     if (!lat->initialised) return LBPS_ERR_STATE;
     for (int64_t s = 0; s < n; ++s) {
@@ -648,12 +651,14 @@ int lbps_step(lbps_lattice* lat, int64_t n) {
 }
 
 int lbps_sync(lbps_lattice* lat) {
+    lbps::NvtxRange nvtx("lbps_sync");
     if (!lat) return LBPS_ERR_INVALID;
     if (!lat->initialised) return LBPS_ERR_STATE;
     return run_sync(lat);
 }
 
 int lbps_read_device(lbps_lattice* lat, int32_t field, double* d_dst, size_t count) {
+    lbps::NvtxRange nvtx("lbps_read_device");
     if (!lat || !d_dst || !valid_field(field)) return LBPS_ERR_INVALID;
     if (!lat->initialised) return LBPS_ERR_STATE;
     if (count < field_count(lat, field)) return LBPS_ERR_INVALID;
@@ -661,6 +666,7 @@ int lbps_read_device(lbps_lattice* lat, int32_t field, double* d_dst, size_t cou
 }
 
 int lbps_read(lbps_lattice* lat, int32_t field, double* dst, size_t count) {
+    lbps::NvtxRange nvtx("lbps_read");
     if (!lat || !dst || !valid_field(field)) return LBPS_ERR_INVALID;
     if (!lat->initialised) return LBPS_ERR_STATE;
     if (count < field_count(lat, field)) return LBPS_ERR_INVALID;
@@ -686,6 +692,7 @@ int lbps_read(lbps_lattice* lat, int32_t field, double* dst, size_t count) {
 }
 
 int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out[4]) {
+    lbps::NvtxRange nvtx("lbps_norms");
     if (!lat || !out) return LBPS_ERR_INVALID;
     if (!(field >= LBPS_UX && field <= LBPS_PSI) && field != LBPS_CONSISTENCY) return LBPS_ERR_INVALID;
     if (!lat->initialised) return LBPS_ERR_STATE;
@@ -735,6 +742,7 @@ int lbps_state_size(const lbps_lattice* lat, size_t* bytes) {
 }
 
 int lbps_state_save(lbps_lattice* lat, void* dst, size_t bytes) {
+    lbps::NvtxRange nvtx("lbps_state_save");
     if (!lat || !dst || bytes < sizeof(SavedState) + lat->L.copy_bytes) return LBPS_ERR_INVALID;
     if (!lat->initialised) return LBPS_ERR_STATE;
     SavedState h{};
@@ -760,6 +768,7 @@ int lbps_state_save(lbps_lattice* lat, void* dst, size_t bytes) {
 }
 
 int lbps_state_load(lbps_lattice* lat, const void* src, size_t bytes) {
+    lbps::NvtxRange nvtx("lbps_state_load");
     if (!lat || !src || bytes < sizeof(SavedState)) return LBPS_ERR_INVALID;
     SavedState h;
     // src may be host or device memory

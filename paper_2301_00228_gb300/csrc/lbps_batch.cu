@@ -235,6 +235,7 @@ int lbps_batch_set_tuning(lbps_batch* b, int32_t variant, int32_t rows_per_warp)
 }
 
 int lbps_batch_step(lbps_batch* b, int64_t n) {
+    lbps::NvtxRange nvtx("lbps_batch_step");
     if (!b || n < 0) return LBPS_ERR_INVALID;
     if (n == 0) return LBPS_OK;
     // start after the work already queued on the lattices' own streams
@@ -284,6 +285,7 @@ int lbps_batch_check(lbps_batch* b) {
 }
 
 int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* rows_per_warp, double* ms_per_step) {
+    lbps::NvtxRange nvtx("lbps_batch_tune");
     if (!b || repeats < 1) return LBPS_ERR_INVALID;
     int rc = refresh(b);
     if (rc != LBPS_OK) return rc;

@@ -5,10 +5,22 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lbps.h"
 #include "lbps_launch.h"
 
 namespace lbps {
+
+// NVTX range around an entry point (named lbps_* after it), so profilers can
+// attribute GPU work to the call that enqueued it; costs nothing without a
+// tool attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Placement of everything in a lattice's device block.
 struct Layout {
