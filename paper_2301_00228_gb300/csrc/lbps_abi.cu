@@ -63,8 +63,10 @@ Layout make_layout(const lbps_params* p, bool general = false, int nb_general = 
         lbps::with_policy(p->storage, [](auto pol) { return (size_t)decltype(pol)::kBytesPerPoint; });
     L.f_bytes = align_up(L.g.plane * per_point);
     L.u_bytes = align_up(4 * L.g.plane * 8);
-    L.copy_bytes = L.f_bytes + L.u_bytes;
     L.nb = general ? nb_general : lbps::perim_count(L.g);
+    L.g.mplane = ((size_t)L.nb + 31) / 32 * 32;
+    L.m_bytes = align_up(L.g.mplane * per_point);
+    L.copy_bytes = L.f_bytes + L.u_bytes + L.m_bytes;
     size_t off = 0;
     L.off_copy[0] = off;
     off += L.copy_bytes;
@@ -326,7 +328,10 @@ int run_step(lbps_lattice* lat) {
 int run_sync(lbps_lattice* lat) {
     cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
         using P = decltype(pol);
-        return lbps::launch_sync<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(lat->cur), lat->st);
+        cudaError_t r = lbps::launch_sync<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(lat->cur), lat->st);
+        if (r == cudaSuccess)
+            r = lbps::launch_mirror<P>(lat->L.g, lat->view<P>(lat->cur), lat->bn(), lat->L.nb, lat->st);
+        return r;
     });
     return cuda_ok(e);
 }
@@ -334,7 +339,10 @@ int run_sync(lbps_lattice* lat) {
 int run_init_kernel(lbps_lattice* lat) {
     cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
         using P = decltype(pol);
-        return lbps::launch_init<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(lat->cur), lat->st);
+        cudaError_t r = lbps::launch_init<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(lat->cur), lat->st);
+        if (r == cudaSuccess)
+            r = lbps::launch_mirror<P>(lat->L.g, lat->view<P>(lat->cur), lat->bn(), lat->L.nb, lat->st);
+        return r;
     });
     return cuda_ok(e);
 }

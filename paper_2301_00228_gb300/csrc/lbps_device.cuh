@@ -52,6 +52,7 @@ struct Geo {
     int general;
     size_t plane;        // px * ny elements per plane
     const uint8_t* type; // [ny][px] node types (general = 1 only)
+    size_t mplane;       // plane of the boundary mirror (boundary points, rounded up to 32)
 };
 
 // FP64 constants of the method (Eq. conditions-parameters, Eq. integration).
@@ -86,12 +87,16 @@ struct KC {
     T scale, inv_scale;         // 2^e, 2^-e applied to the stored 16-bit Nx, Ny
 };
 
-// One state copy: the population planes (layout set by the storage policy P)
-// and 4 FP64 planes (u_x, u_y, v_x, v_y).
+// One state copy: the population planes (layout set by the storage policy P),
+// 4 FP64 planes (u_x, u_y, v_x, v_y), and the boundary mirror: the
+// populations of the boundary points again, in the order of the boundary
+// list (planes of Geo::mplane points, same policy layout), so that the
+// boundary reset reads and writes them coalesced.
 template <typename P>
 struct View {
     typename P::Base* f;
     double* u;
+    typename P::Base* m;
 };
 
 // A boundary lattice point (perimeter order, see perim_index).
@@ -314,12 +319,47 @@ struct PopDirect {
 #pragma unroll
         for (int s = 0; s < 2; ++s) store5(f, plane, p, s, x[s], k);
     }
-    // Equilibria of both sets at one point (s[set], jx[set], jy[set]).
+    // Every word of one point from its stored form.
+    __device__ __forceinline__ static void store_raw(T* __restrict__ f, size_t plane, size_t p, const Raw& r) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) LBPS_ST(f + (size_t)(s * 5 + q) * plane + p, r.f[s][q]);
+    }
+    // Equilibria of Eq. feq of both sets at lattice offset p for s[set] and
+    // the lattice first moments (jx[set], jy[set]) (FP64 in), in stored form.
+    // FP32 storage evaluates them in FP32 (from a and a_0 of the FP32
+    // constants); FP64 storage in FP64.
+    __device__ __forceinline__ static void eq_raw(size_t, const Consts& c, const double (&sv)[2],
+                                                  const double (&jx)[2], const double (&jy)[2], const KC<T>& k,
+                                                  Raw& r) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if constexpr (sizeof(T) == 4) {
+                const float sf = (float)sv[s], hx = mul_rn(0.5f, (float)jx[s]), hy = mul_rn(0.5f, (float)jy[s]);
+                const float as = mul_rn(k.a[s], sf);
+                r.f[s][0] = mul_rn(mul_rn(0.5f, k.two_a0[s]), sf);
+                r.f[s][1] = add_rn(as, hx);
+                r.f[s][2] = add_rn(as, hy);
+                r.f[s][3] = sub_rn(as, hx);
+                r.f[s][4] = sub_rn(as, hy);
+            } else {
+                const double as = c.a[s] * sv[s];
+                r.f[s][0] = (T)(c.a0[s] * sv[s]);
+                r.f[s][1] = (T)(as + 0.5 * jx[s]);
+                r.f[s][2] = (T)(as + 0.5 * jy[s]);
+                r.f[s][3] = (T)(as - 0.5 * jx[s]);
+                r.f[s][4] = (T)(as - 0.5 * jy[s]);
+            }
+        }
+    }
+    // The same equilibria stored at p.
     __device__ __forceinline__ static void store_eq_point(T* __restrict__ f, size_t plane, size_t p, const Consts& c,
                                                           const double (&sv)[2], const double (&jx)[2],
                                                           const double (&jy)[2], const KC<T>& k) {
-#pragma unroll
-        for (int s = 0; s < 2; ++s) store_eq(f, plane, p, s, c.a0[s], c.a[s], sv[s], jx[s], jy[s], k);
+        Raw r;
+        eq_raw(p, c, sv, jx, jy, k, r);
+        store_raw(f, plane, p, r);
     }
     // One moving population alpha (1..4) of both sets.
     __device__ __forceinline__ static void store1_both(T* __restrict__ f, size_t plane, size_t p, int alpha,
@@ -332,29 +372,6 @@ struct PopDirect {
                                                   const KC<T>&, double (&x)[5]) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) x[q] = (double)LBPS_LD(f + (size_t)(s * 5 + q) * plane + p);
-    }
-    // Equilibrium of Eq. feq for s and the lattice first moment (jx, jy) (FP64 in).
-    // FP32 storage evaluates it in FP32 (from a and a_0 of the FP32
-    // constants); FP64 storage in FP64.
-    __device__ __forceinline__ static void store_eq(T* __restrict__ f, size_t plane, size_t p, int s, double a0,
-                                                    double a, double sv, double jx, double jy, const KC<T>& k) {
-        T* b = f + (size_t)s * 5 * plane + p;
-        if constexpr (sizeof(T) == 4) {
-            const float sf = (float)sv, hx = mul_rn(0.5f, (float)jx), hy = mul_rn(0.5f, (float)jy);
-            const float as = mul_rn(k.a[s], sf);
-            LBPS_ST(&b[0], mul_rn(mul_rn(0.5f, k.two_a0[s]), sf));
-            LBPS_ST(&b[plane], add_rn(as, hx));
-            LBPS_ST(&b[2 * plane], add_rn(as, hy));
-            LBPS_ST(&b[3 * plane], sub_rn(as, hx));
-            LBPS_ST(&b[4 * plane], sub_rn(as, hy));
-            return;
-        }
-        double as = a * sv;
-        LBPS_ST(&b[0], (T)(a0 * sv));
-        LBPS_ST(&b[plane], (T)(as + 0.5 * jx));
-        LBPS_ST(&b[2 * plane], (T)(as + 0.5 * jy));
-        LBPS_ST(&b[3 * plane], (T)(as - 0.5 * jx));
-        LBPS_ST(&b[4 * plane], (T)(as - 0.5 * jy));
     }
 };
 
@@ -533,42 +550,44 @@ struct PopNeq16 {
         }
         LBPS_ST(wp, out);
     }
-    // Equilibria of both sets at one point, each packed word written once.
-    __device__ __forceinline__ static void store_eq_point(float* __restrict__ f, size_t plane, size_t p,
-                                                          const Consts&, const double (&sv)[2],
-                                                          const double (&jx)[2], const double (&jy)[2],
-                                                          const KC<float>& k) {
+    // Every word of one point from its stored form.
+    __device__ __forceinline__ static void store_raw(float* __restrict__ f, size_t plane, size_t p, const Raw& r) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) LBPS_ST(f + (size_t)(s * 3 + q) * plane + p, r.m[s][q]);
+        unsigned* w = words(f, plane);
+        LBPS_ST(w + p, r.w[0]);
+        LBPS_ST(w + plane + p, r.w[1]);
+    }
+    // Equilibria of Eq. feq of both sets at lattice offset p (the rounding key),
+    // in FP32 and in stored form: J = (jx, jy) and the pair sums' deviation
+    // 2 a s - 2 r f^0 from the stored f^0 (zero up to rounding), scaled.
+    __device__ __forceinline__ static void eq_raw(size_t p, const Consts&, const double (&sv)[2],
+                                                  const double (&jx)[2], const double (&jy)[2],
+                                                  const KC<float>& k, Raw& r) {
         unsigned w = 0;
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
             const float sf = (float)sv[s];
             const float f0 = mul_rn(mul_rn(0.5f, k.two_a0[s]), sf);
-            LBPS_ST(f + (size_t)(s * 3) * plane + p, f0);
-            LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, (float)jx[s]);
-            LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, (float)jy[s]);
+            r.m[s][0] = f0;
+            r.m[s][1] = (float)jx[s];
+            r.m[s][2] = (float)jy[s];
             const float dev = mul_rn(fma_rn(-2.0f * k.r[s], f0, mul_rn(k.two_a[s], sf)), k.scale);
             w |= f2bits_store<H>(dev, (unsigned)p * 4u + 2u * s) << (16 * s);
         }
-        unsigned* wp = words(f, plane);
-        LBPS_ST(wp + p, w);
-        LBPS_ST(wp + plane + p, w);
+        r.w[0] = w;
+        r.w[1] = w;
     }
-    // Equilibrium of Eq. feq for set s, in FP32: J = (jx, jy), the pair sums'
-    // deviation 2 a s - 2 r f^0 from the stored f^0 (zero up to rounding),
-    // written into the set's halves of both words.
-    __device__ __forceinline__ static void store_eq(float* __restrict__ f, size_t plane, size_t p, int s, double a0,
-                                                    double a, double sv, double jx, double jy, const KC<float>& k) {
-        const float sf = (float)sv;
-        const float f0 = mul_rn(mul_rn(0.5f, k.two_a0[s]), sf);
-        LBPS_ST(f + (size_t)(s * 3) * plane + p, f0);
-        LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, (float)jx);
-        LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, (float)jy);
-        // 2 a s - 2 r f^0 (zero up to rounding), scaled
-        const float dev = mul_rn(fma_rn(-2.0f * k.r[s], f0, mul_rn(k.two_a[s], sf)), k.scale);
-        unsigned short nv = (unsigned short)f2bits_store<H>(dev, (unsigned)p * 4u + 2u * s);
-        unsigned short* h = reinterpret_cast<unsigned short*>(words(f, plane));
-        LBPS_ST(h + 2 * p + s, nv);
-        LBPS_ST(h + 2 * (plane + p) + s, nv);
+    // The same equilibria stored at p, each packed word written once.
+    __device__ __forceinline__ static void store_eq_point(float* __restrict__ f, size_t plane, size_t p,
+                                                          const Consts& c, const double (&sv)[2],
+                                                          const double (&jx)[2], const double (&jy)[2],
+                                                          const KC<float>& k) {
+        Raw r;
+        eq_raw(p, c, sv, jx, jy, k, r);
+        store_raw(f, plane, p, r);
     }
 };
 

@@ -302,16 +302,27 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<
     // population travelling that way, replacing what the interior kernel
     // wrote there (a rectangle's edge point has one such neighbour, a corner
     // none; next to a hole a point may have several).
+    // The populations at t are read from copy A's boundary mirror (entry b,
+    // coalesced along the boundary list); the reset ones go to the lattice and
+    // to copy B's mirror.
     const int smask = LBPS_LD(&bn[b].smask);
+    typename P::Raw ra, rb;
+    P::load_raw(A.m, g.mplane, (size_t)b, true, ra);
     V a5s[2][5], b5s[2][5];
+    const double sv[2] = {phi, psi};
+    double jx[2], jy[2];
 #pragma unroll
     for (int set = 0; set < 2; ++set) {
-        P::load5(A.f, g.plane, p, set, k, a5s[set]);
-        double jx = (double)a5s[set][1] - (double)a5s[set][3];
-        double jy = (double)a5s[set][2] - (double)a5s[set][4];
-        P::store_eq(B.f, g.plane, p, set, c.a0[set], c.a[set], set == 0 ? phi : psi, jx, jy, k);
-        if (smask) P::load5(B.f, g.plane, p, set, k, b5s[set]);  // the reset values just stored
+        P::decode(ra, set, k, a5s[set]);
+        jx[set] = (double)a5s[set][1] - (double)a5s[set][3];
+        jy[set] = (double)a5s[set][2] - (double)a5s[set][4];
     }
+    P::eq_raw(p, c, sv, jx, jy, k, rb);
+    P::store_raw(B.f, g.plane, p, rb);
+    P::store_raw(B.m, g.mplane, (size_t)b, rb);
+    if (smask)
+#pragma unroll
+        for (int set = 0; set < 2; ++set) P::decode(rb, set, k, b5s[set]);
     const int DXS[4] = {1, 0, -1, 0};
     const int DYS[4] = {0, 1, 0, -1};
     for (int d = 0; d < 4; ++d) {
@@ -357,6 +368,20 @@ __global__ void __launch_bounds__(128) boundary_reset_kernel(Geo g, Consts c, KC
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nb && boundary_reset(g, c, k, A, B, bn, b)) atomicOr(flag, 1u);
     if (b == 0) LBPS_ST(tstep, LBPS_LD(tstep) + 1ull);
+}
+
+// Copies the populations of every boundary point of copy A into A's boundary
+// mirror.  Run after the kernels that write them in place (initialisation,
+// synchronisation); the reset pass keeps the mirror current otherwise.
+template <typename P>
+__global__ void __launch_bounds__(128) boundary_mirror_kernel(Geo g, View<P> A, const BNode* __restrict__ bn,
+                                                              int nb) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
+    typename P::Raw r;
+    P::load_raw(A.f, g.plane, (size_t)j * g.px + i, true, r);
+    P::store_raw(A.m, g.mplane, (size_t)b, r);
 }
 
 // ---------------------------------------------------------------- bulk
@@ -816,6 +841,12 @@ cudaError_t launch_init(const Geo& g, const Consts& c, const KCof<P>& k, View<P>
 }
 
 template <typename P>
+cudaError_t launch_mirror(const Geo& g, View<P> A, const BNode* bn, int nb, cudaStream_t st) {
+    if (nb > 0) boundary_mirror_kernel<P><<<(nb + 127) / 128, 128, 0, st>>>(g, A, bn, nb);
+    return cudaGetLastError();
+}
+
+template <typename P>
 cudaError_t launch_boundary(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, const BNode* bn,
                             int nb, double* sig, unsigned* flag, unsigned long long* tstep, cudaStream_t st,
                             int pass_lo, int pass_hi) {
@@ -877,6 +908,7 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, const KCof<P>& k, View<P
 
 #define LBPS_INSTANTIATE(P)                                                                                   \
     template cudaError_t launch_init<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, cudaStream_t);  \
+    template cudaError_t launch_mirror<P>(const Geo&, View<P>, const BNode*, int, cudaStream_t);            \
     template cudaError_t launch_boundary<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>,      \
                                             const BNode*, int, double*, unsigned*, unsigned long long*,       \
                                             cudaStream_t, int, int);                                          \

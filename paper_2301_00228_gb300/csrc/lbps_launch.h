@@ -22,6 +22,10 @@ cudaError_t launch_scale_probe(const Geo& g, const Consts& c, const double* u, d
 
 template <typename P>
 cudaError_t launch_init(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, cudaStream_t st);
+// Refreshes A's boundary mirror from the lattice (after launch_init and
+// launch_sync, which write boundary populations in place).
+template <typename P>
+cudaError_t launch_mirror(const Geo& g, View<P> A, const BNode* bn, int nb, cudaStream_t st);
 
 // One time step A (time t) -> B (time t + dt) on one stream: boundary passes
 // 0-1 (stress, Newmark), launch_bulk, boundary pass 2 (reset).  sig: scratch

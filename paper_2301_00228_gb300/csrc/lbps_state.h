@@ -27,6 +27,7 @@ struct Layout {
     Geo g;
     size_t f_bytes;     // population planes (layout of the storage policy), aligned
     size_t u_bytes;     // 4 FP64 planes, aligned
+    size_t m_bytes;     // boundary mirror (g.mplane points, storage layout), aligned
     size_t copy_bytes;
     size_t off_copy[2];
     size_t off_bn, off_sig, off_type, off_part, off_out, off_flag, off_staging;
@@ -77,6 +78,7 @@ struct lbps_lattice {
         lbps::View<P> v;
         v.f = reinterpret_cast<typename P::Base*>(mem + L.off_copy[q]);
         v.u = u(q);
+        v.m = reinterpret_cast<typename P::Base*>(mem + L.off_copy[q] + L.f_bytes + L.u_bytes);
         return v;
     }
     double* u(int q) const { return reinterpret_cast<double*>(mem + L.off_copy[q] + L.f_bytes); }
