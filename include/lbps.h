@@ -226,7 +226,7 @@ int lbps_norms_noalloc(const double* d_x, const double* d_ref, size_t n, void* c
 
 /* ---- Batches: many lattices of different sizes, materials and edges
  * advanced together.  Each time step is one launch of each boundary pass
- * (stress, Newmark, reset) over the boundary points of every lattice and one
+ * (Newmark, reset) over the boundary points of every lattice and one
  * launch of the interior kernel, a persistent grid whose warps take strips
  * of every lattice from a work list (the same per-point arithmetic as
  * lbps_step, so every lattice gets the same bits as when stepped alone).
@@ -330,8 +330,7 @@ int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);
 
 /* Per-kernel timing for roofline reports.  enable != 0 starts recording CUDA
  * events on the lattice's stream around the interior kernel of every step
- * and around each group of boundary passes (stress + Newmark before it,
- * reset after it); 0 stops.  lbps_profile_read waits for the stream and
+ * and around each boundary pass (Newmark before it, reset after it); 0 stops.  lbps_profile_read waits for the stream and
  * returns, since recording started: out[0] total milliseconds in the bulk
  * (interior) kernel, out[1] its launches, out[2] total milliseconds in the
  * boundary passes, out[3] the number of timed boundary groups (two per

@@ -66,7 +66,8 @@ Layout make_layout(const lbps_params* p, bool general = false, int nb_general = 
     L.nb = general ? nb_general : lbps::perim_count(L.g);
     L.g.mplane = ((size_t)L.nb + 31) / 32 * 32;
     L.m_bytes = align_up(L.g.mplane * per_point);
-    L.copy_bytes = L.f_bytes + L.u_bytes + L.m_bytes;
+    L.s_bytes = align_up((general ? 5 : 2) * (size_t)L.nb * 3 * sizeof(double));
+    L.copy_bytes = L.f_bytes + L.u_bytes + L.m_bytes + L.s_bytes;
     size_t off = 0;
     L.off_copy[0] = off;
     off += L.copy_bytes;
@@ -74,8 +75,6 @@ Layout make_layout(const lbps_params* p, bool general = false, int nb_general = 
     off += L.copy_bytes;
     L.off_bn = off;
     off += align_up((size_t)L.nb * sizeof(BNode));
-    L.off_sig = off;  // stresses: 2 slots per boundary point (rectangle), 5 (general)
-    off += align_up((general ? 5 : 2) * (size_t)L.nb * 3 * sizeof(double));
     L.off_type = off;
     if (general) off += align_up(L.g.plane);
     L.off_part = off;
@@ -284,7 +283,8 @@ cudaError_t prof_mark(lbps_lattice* lat) {
     return cudaEventRecord(e, lat->st);
 }
 
-// Boundary passes [pass_lo, pass_hi) of one step (0 stress, 1 Newmark, 2 reset).
+// Boundary passes [pass_lo, pass_hi) of one step (1 Newmark, 2 reset; 0, the
+// stresses of copy a, only after the initialisation).
 cudaError_t boundary_passes(lbps_lattice* lat, int a, int b, int pass_lo, int pass_hi) {
     if (lat->L.nb == 0) return cudaSuccess;
     cudaError_t e = prof_mark(lat);
@@ -292,7 +292,7 @@ cudaError_t boundary_passes(lbps_lattice* lat, int a, int b, int pass_lo, int pa
         e = lbps::with_policy(lat->p.storage, [&](auto pol) {
             using P = decltype(pol);
             return lbps::launch_boundary<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(a), lat->view<P>(b),
-                                            lat->bn(), lat->L.nb, lat->sig(), lat->flag(), lat->tstep(), lat->st,
+                                            lat->bn(), lat->L.nb, lat->flag(), lat->tstep(), lat->st,
                                             pass_lo, pass_hi);
         });
     if (e == cudaSuccess) e = prof_mark(lat);
@@ -300,12 +300,13 @@ cudaError_t boundary_passes(lbps_lattice* lat, int a, int b, int pass_lo, int pa
     return e;
 }
 
-// One time step: boundary stress and Newmark passes, the interior kernel, then
-// the boundary reset (which reads the interior kernel's new u and overwrites
-// the populations streamed from boundary points).
+// One time step: the boundary Newmark pass, the interior kernel, then the
+// boundary reset (which reads the interior kernel's new u, overwrites the
+// populations streamed from boundary points and leaves the stresses of the
+// new u for the next step).
 int run_step(lbps_lattice* lat) {
     int a = lat->cur, b = lat->cur ^ 1;
-    cudaError_t e = boundary_passes(lat, a, b, 0, 2);
+    cudaError_t e = boundary_passes(lat, a, b, 1, 2);
     if (e == cudaSuccess) e = prof_mark(lat);
     if (e == cudaSuccess)
         e = lbps::with_policy(lat->p.storage, [&](auto pol) {
@@ -339,9 +340,13 @@ int run_sync(lbps_lattice* lat) {
 int run_init_kernel(lbps_lattice* lat) {
     cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
         using P = decltype(pol);
-        cudaError_t r = lbps::launch_init<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(lat->cur), lat->st);
+        const lbps::View<P> v = lat->view<P>(lat->cur);
+        cudaError_t r = lbps::launch_init<P>(lat->L.g, lat->c, lat->kc<P>(), v, lat->st);
+        if (r == cudaSuccess) r = lbps::launch_mirror<P>(lat->L.g, v, lat->bn(), lat->L.nb, lat->st);
+        // the stresses of the initial u (later steps leave them with each copy)
         if (r == cudaSuccess)
-            r = lbps::launch_mirror<P>(lat->L.g, lat->view<P>(lat->cur), lat->bn(), lat->L.nb, lat->st);
+            r = lbps::launch_boundary<P>(lat->L.g, lat->c, lat->kc<P>(), v, v, lat->bn(), lat->L.nb, lat->flag(),
+                                         lat->tstep(), lat->st, 0, 1);
         return r;
     });
     return cuda_ok(e);

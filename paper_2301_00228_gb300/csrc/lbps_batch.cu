@@ -47,7 +47,6 @@ DomDesc<P> make_desc(const lbps_lattice* lat) {
     d.v[0] = lat->view<P>(0);
     d.v[1] = lat->view<P>(1);
     d.bn = lat->bn();
-    d.sig = lat->sig();
     d.flag = lat->flag();
     d.tstep = lat->tstep();
     d.nb = lat->L.nb;
@@ -105,11 +104,11 @@ int upload(lbps_batch* b) {
 }
 
 // One time step of every lattice: parity 0 reads v[cur], parity 1 v[cur ^ 1].
-// The boundary stress and Newmark passes run on the side stream beside the
-// interior kernel: they read copy A and write only the boundary points' u,
-// du/dt of copy B and the stress scratch, none of which the interior kernel
-// touches.  The boundary reset waits for both (it reads the interior kernel's
-// new u and overwrites populations it wrote).
+// The boundary Newmark pass runs on the side stream beside the interior
+// kernel: it reads copy A and writes only the boundary points' u, du/dt of
+// copy B, which the interior kernel does not touch.  The boundary reset waits
+// for both (it reads the interior kernel's new u and overwrites populations
+// it wrote).
 cudaError_t launch_step(lbps_batch* b, int parity) {
     const BndTask* bt = reinterpret_cast<const BndTask*>(b->mem + b->off_bnd);
     const BulkTask* wt = reinterpret_cast<const BulkTask*>(b->mem + b->off_bulk);
@@ -118,7 +117,7 @@ cudaError_t launch_step(lbps_batch* b, int parity) {
         const DomDesc<P>* dd = reinterpret_cast<const DomDesc<P>*>(b->mem);
         cudaError_t e = cudaEventRecord(b->fork, b->st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
-        if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 0, 2, b->side);
+        if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 1, 2, b->side);
         if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
         unsigned* next = reinterpret_cast<unsigned*>(b->mem + b->off_next);
         if (e == cudaSuccess) e = lbps::launch_bulk_batch<P>(dd, wt, b->nbulk, parity, b->variant, next, b->st);

@@ -91,12 +91,15 @@ struct KC {
 // 4 FP64 planes (u_x, u_y, v_x, v_y), and the boundary mirror: the
 // populations of the boundary points again, in the order of the boundary
 // list (planes of Geo::mplane points, same policy layout), so that the
-// boundary reset reads and writes them coalesced.
+// boundary reset reads and writes them coalesced; and the stresses of this
+// copy's u that Eq. acc_neumann reads (3 doubles per slot: 2 slots per
+// boundary point of a rectangle, 5 of a general geometry).
 template <typename P>
 struct View {
     typename P::Base* f;
     double* u;
     typename P::Base* m;
+    double* s;
 };
 
 // A boundary lattice point (perimeter order, see perim_index).

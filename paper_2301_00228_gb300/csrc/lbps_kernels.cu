@@ -95,26 +95,32 @@ __global__ void scale_probe_kernel(Geo g, Consts c, const double* __restrict__ u
 
 // ------------------------------------------------------------- boundary
 
-// Cauchy stress from differences of u (Eq. strain in Eq. hooke): s = {xx, yy, xy}.
-__device__ inline void stress_at(const Geo& g, const Consts& c, const double* ux, const double* uy, int i,
-                                 int j, double s[3]) {
-    double exx = ddx(ux, g.px, i, j, g, c.inv2h);
-    double eyy = ddy(uy, g.px, i, j, g, c.inv2h);
-    double exy = 0.5 * (ddy(ux, g.px, i, j, g, c.inv2h) + ddx(uy, g.px, i, j, g, c.inv2h));
+// Cauchy stress (Eq. hooke with the strain of Eq. strain) from the four
+// differences of u at a point: exx = du_x/dx, eyy = du_y/dy, uxy = du_x/dy,
+// uyx = du_y/dx; s = {xx, yy, xy}.
+__device__ inline void stress_of(const Consts& c, double exx, double eyy, double uxy, double uyx, double s[3]) {
+    double exy = 0.5 * (uxy + uyx);
     double tr = exx + eyy;
     s[0] = c.lam * tr + 2.0 * c.mu * exx;
     s[1] = c.lam * tr + 2.0 * c.mu * eyy;
     s[2] = 2.0 * c.mu * exy;
 }
 
+// The same from differences of u at (i, j).
+__device__ inline void stress_at(const Geo& g, const Consts& c, const double* ux, const double* uy, int i,
+                                 int j, double s[3]) {
+    stress_of(c, ddx(ux, g.px, i, j, g, c.inv2h), ddy(uy, g.px, i, j, g, c.inv2h), ddy(ux, g.px, i, j, g, c.inv2h),
+              ddx(uy, g.px, i, j, g, c.inv2h), s);
+}
+
 // Eq. acc_neumann for the boundary cell of (i, j): the square of side dh
 // clipped to the rectangle; one face per existing neighbour r with normal
 // pointing to r, length l_kr, stress (sigma_k + sigma_r)/2; external force
 // F = int t* da supplied per point.  The stresses come from the stress pass:
-// sig0[b] at boundary point b, sig1[b] at its interior neighbour.
+// slot b at boundary point b, slot nb + b at its interior neighbour.
 // General geometry (reading R14): the cell's side lengths and 1/(rho V_C)
-// come with the point; the stress pass left sigma at b in slot 5b and at
-// its body neighbour in direction d in slot 5b + 1 + d; a side facing no
+// come with the point; sigma at b is in slot 5b and at its body neighbour in
+// direction d in slot 5b + 1 + d; a side facing no
 // body neighbour but lying partly in the body carries sigma_k.
 __device__ inline void accel_neumann(const Geo& g, const Consts& c, const BNode* __restrict__ bn,
                                      const double* __restrict__ sig, int nb, int b, int i, int j, double fx,
@@ -202,27 +208,36 @@ __device__ inline int inward_dir(int i, int j, const Geo& g) {
     return 4;                             // -y (t)
 }
 
-// The boundary work of a step runs in three passes over the perimeter list,
+// The boundary work of a step runs in two passes over the perimeter list,
 // each one thread per boundary point b at (i, j):
-//   stress   sigma at b and at its interior neighbour (for Eq. acc_neumann);
-//   newmark  acceleration of b (Eq. acc_neumann or Eq. acc_dirichlet) and
-//            u(t + dt) at b;
+//   newmark  acceleration of b (Eq. acc_neumann, from the stresses of copy A,
+//            or Eq. acc_dirichlet) and u(t + dt) at b;
 //   (the interior kernel runs here: u(t + dt) at every interior point)
 //   reset    phi, psi from differences of u(t + dt) (Eq. psi_phi_at_bound),
-//            populations by Eq. correction-f, and the value b streams into its
+//            populations by Eq. correction-f, the value b streams into its
 //            interior neighbour (Eq. LBE_mod), written over the population the
-//            interior kernel put there.
+//            interior kernel put there, and the stresses of u(t + dt) that
+//            the next step's Eq. acc_neumann reads, into copy B.
+// Each copy thus carries the stresses of its own u; the stress pass below
+// computes them where u was set otherwise (initialisation).
 
-__device__ inline void boundary_stress(const Geo& g, const Consts& c, const double* ux, const double* uy,
-                                       const BNode* __restrict__ bn, int nb, double* __restrict__ sig, int b) {
-    int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
+// sigma at b (slot b of a rectangle, 5b of a general geometry).
+__device__ inline void store_point_stress(const Geo& g, double* __restrict__ sig, int b, const double s[3]) {
+    const size_t o = (size_t)b * (g.general ? 15 : 3);
+    for (int q = 0; q < 3; ++q) LBPS_ST(&sig[o + q], s[q]);
+}
+
+// sigma at the neighbours of b that its Eq. acc_neumann reads besides the
+// boundary points: the interior neighbour of a rectangle's edge point (slot
+// nb + b), the body neighbours of a general boundary point (slot 5b + 1 + d).
+__device__ inline void neighbour_stresses(const Geo& g, const Consts& c, const double* ux, const double* uy,
+                                          const BNode* __restrict__ bn, int nb, double* __restrict__ sig, int b,
+                                          int i, int j) {
     double s[3];
-    if (g.general) {  // slots 5b (the point) and 5b + 1 + d (its body neighbours)
+    if (g.general) {
         const int DX[4] = {1, 0, -1, 0};
         const int DY[4] = {0, 1, 0, -1};
         const int nbm = LBPS_LD(&bn[b].nbmask);
-        stress_at(g, c, ux, uy, i, j, s);
-        for (int q = 0; q < 3; ++q) LBPS_ST(&sig[(size_t)b * 15 + q], s[q]);
         for (int d = 0; d < 4; ++d) {
             if (!((nbm >> d) & 1)) continue;
             stress_at(g, c, ux, uy, wrap(i + DX[d], g.nx), wrap(j + DY[d], g.ny), s);
@@ -230,8 +245,6 @@ __device__ inline void boundary_stress(const Geo& g, const Consts& c, const doub
         }
         return;
     }
-    stress_at(g, c, ux, uy, i, j, s);
-    for (int q = 0; q < 3; ++q) LBPS_ST(&sig[(size_t)b * 3 + q], s[q]);
     const int dir = inward_dir(i, j, g);
     if (dir != 0) {
         const int DX[5] = {0, 1, 0, -1, 0};
@@ -239,6 +252,15 @@ __device__ inline void boundary_stress(const Geo& g, const Consts& c, const doub
         stress_at(g, c, ux, uy, i + DX[dir], j + DY[dir], s);
         for (int q = 0; q < 3; ++q) LBPS_ST(&sig[((size_t)nb + b) * 3 + q], s[q]);
     }
+}
+
+__device__ inline void boundary_stress(const Geo& g, const Consts& c, const double* ux, const double* uy,
+                                       const BNode* __restrict__ bn, int nb, double* __restrict__ sig, int b) {
+    const int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
+    double s[3];
+    stress_at(g, c, ux, uy, i, j, s);
+    store_point_stress(g, sig, b, s);
+    neighbour_stresses(g, c, ux, uy, bn, nb, sig, b, i, j);
 }
 
 // tstep: the lattice's step counter n (device memory); time-dependent data
@@ -276,7 +298,7 @@ __device__ inline void boundary_newmark(const Geo& g, const Consts& c, const Vie
 
 template <typename P>
 __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& A,
-                                      const View<P>& B, const BNode* __restrict__ bn, int b) {
+                                      const View<P>& B, const BNode* __restrict__ bn, int nb, int b) {
     using V = typename P::V;
     int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
     size_t p = (size_t)j * g.px + i;
@@ -295,8 +317,18 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<
         dux_dy = fma_rn(sy.w[q], LBPS_LD(&ux1[o]), dux_dy);
         duy_dy = fma_rn(sy.w[q], LBPS_LD(&uy1[o]), duy_dy);
     }
-    double phi = mul_rn(dux_dx, c.inv2h) + mul_rn(duy_dy, c.inv2h);
-    double psi = mul_rn(duy_dx, c.inv2h) - mul_rn(dux_dy, c.inv2h);
+    const double exx = mul_rn(dux_dx, c.inv2h), eyy = mul_rn(duy_dy, c.inv2h);
+    const double uxy = mul_rn(dux_dy, c.inv2h), uyx = mul_rn(duy_dx, c.inv2h);
+    const double phi = exx + eyy;
+    const double psi = uyx - uxy;
+    // sigma of u(t + dt) at b (from the same differences) and at the
+    // neighbours Eq. acc_neumann reads, into copy B for the next step
+    {
+        double s[3];
+        stress_of(c, exx, eyy, uxy, uyx, s);
+        store_point_stress(g, B.s, b, s);
+        neighbour_stresses(g, c, ux1, uy1, bn, nb, B.s, b, i, j);
+    }
     // Eq. correction-f with J(x_k, t) of the stored populations, then the value
     // this point streams into each interior neighbour (Eq. LBE_mod): the
     // population travelling that way, replacing what the interior kernel
@@ -345,18 +377,17 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<
 
 template <typename P>
 __global__ void __launch_bounds__(128) boundary_stress_kernel(Geo g, Consts c, View<P> A,
-                                                              const BNode* __restrict__ bn, int nb, double* sig) {
+                                                              const BNode* __restrict__ bn, int nb) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb) boundary_stress(g, c, A.u, A.u + g.plane, bn, nb, sig, b);
+    if (b < nb) boundary_stress(g, c, A.u, A.u + g.plane, bn, nb, A.s, b);
 }
 
 template <typename P>
 __global__ void __launch_bounds__(128) boundary_newmark_kernel(Geo g, Consts c, View<P> A, View<P> B,
                                                                const BNode* __restrict__ bn, int nb,
-                                                               const double* __restrict__ sig,
                                                                const unsigned long long* __restrict__ tstep) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb) boundary_newmark(g, c, A, B, bn, nb, sig, tstep, b);
+    if (b < nb) boundary_newmark(g, c, A, B, bn, nb, A.s, tstep, b);
 }
 
 // The last pass of a step also advances the step counter (one thread; no
@@ -366,7 +397,7 @@ __global__ void __launch_bounds__(128) boundary_reset_kernel(Geo g, Consts c, KC
                                                              const BNode* __restrict__ bn, int nb, unsigned* flag,
                                                              unsigned long long* tstep) {
     int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nb && boundary_reset(g, c, k, A, B, bn, b)) atomicOr(flag, 1u);
+    if (b < nb && boundary_reset(g, c, k, A, B, bn, nb, b)) atomicOr(flag, 1u);
     if (b == 0) LBPS_ST(tstep, LBPS_LD(tstep) + 1ull);
 }
 
@@ -540,8 +571,8 @@ __global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KCof<P
 
 // --------------------------------------------------------------- batches
 
-// The three boundary passes over the boundary points of every lattice in the
-// batch (one thread per point).
+// The boundary passes of a step (1 Newmark, 2 reset) over the boundary points
+// of every lattice in the batch (one thread per point).
 template <typename P>
 __global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<P>* __restrict__ dd,
                                                              const BndTask* __restrict__ tasks, int ntasks,
@@ -551,12 +582,10 @@ __global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<P>* _
     const BndTask tk = tasks[t];
     const DomDesc<P>& d = dd[tk.dom];
     const int a = d.cur ^ parity;
-    if (pass == 0)
-        boundary_stress(d.g, d.c, d.v[a].u, d.v[a].u + d.g.plane, d.bn, d.nb, d.sig, tk.b);
-    else if (pass == 1)
-        boundary_newmark(d.g, d.c, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.sig, d.tstep, tk.b);
+    if (pass == 1)
+        boundary_newmark(d.g, d.c, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.v[a].s, d.tstep, tk.b);
     else {
-        if (boundary_reset(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, tk.b)) atomicOr(d.flag, 1u);
+        if (boundary_reset(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, d.nb, tk.b)) atomicOr(d.flag, 1u);
         if (tk.b == 0) LBPS_ST(d.tstep, LBPS_LD(d.tstep) + 1ull);
     }
 }
@@ -848,13 +877,13 @@ cudaError_t launch_mirror(const Geo& g, View<P> A, const BNode* bn, int nb, cuda
 
 template <typename P>
 cudaError_t launch_boundary(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, const BNode* bn,
-                            int nb, double* sig, unsigned* flag, unsigned long long* tstep, cudaStream_t st,
+                            int nb, unsigned* flag, unsigned long long* tstep, cudaStream_t st,
                             int pass_lo, int pass_hi) {
     if (nb > 0) {
         const int blocks = (nb + 127) / 128;
         for (int pass = pass_lo; pass < pass_hi; ++pass) {
-            if (pass == 0) boundary_stress_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, bn, nb, sig);
-            if (pass == 1) boundary_newmark_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, B, bn, nb, sig, tstep);
+            if (pass == 0) boundary_stress_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, bn, nb);
+            if (pass == 1) boundary_newmark_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, B, bn, nb, tstep);
             if (pass == 2) boundary_reset_kernel<P><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb, flag, tstep);
         }
     }
@@ -910,7 +939,7 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, const KCof<P>& k, View<P
     template cudaError_t launch_init<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, cudaStream_t);  \
     template cudaError_t launch_mirror<P>(const Geo&, View<P>, const BNode*, int, cudaStream_t);            \
     template cudaError_t launch_boundary<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>,      \
-                                            const BNode*, int, double*, unsigned*, unsigned long long*,       \
+                                            const BNode*, int, unsigned*, unsigned long long*,                \
                                             cudaStream_t, int, int);                                          \
     template cudaError_t launch_bulk<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>,          \
                                         unsigned*, cudaStream_t, const Tuning&);                              \

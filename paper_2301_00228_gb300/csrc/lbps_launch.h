@@ -27,13 +27,14 @@ cudaError_t launch_init(const Geo& g, const Consts& c, const KCof<P>& k, View<P>
 template <typename P>
 cudaError_t launch_mirror(const Geo& g, View<P> A, const BNode* bn, int nb, cudaStream_t st);
 
-// One time step A (time t) -> B (time t + dt) on one stream: boundary passes
-// 0-1 (stress, Newmark), launch_bulk, boundary pass 2 (reset).  sig: scratch
-// of 2 * nb * 3 doubles (stresses of the boundary cells); tstep: the
-// lattice's step counter, read by pass 1 and advanced by pass 2.
+// One time step A (time t) -> B (time t + dt) on one stream: boundary pass 1
+// (Newmark, from A's stresses), launch_bulk, boundary pass 2 (reset, which
+// also writes B's stresses).  Pass 0 computes A's stresses from A's u, for
+// a copy whose u was set otherwise (initialisation).  tstep: the lattice's
+// step counter, read by pass 1 and advanced by pass 2.
 template <typename P>
 cudaError_t launch_boundary(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B,
-                            const BNode* bn, int nb, double* sig, unsigned* flag, unsigned long long* tstep,
+                            const BNode* bn, int nb, unsigned* flag, unsigned long long* tstep,
                             cudaStream_t st, int pass_lo, int pass_hi);
 // Launch shape of the bulk kernel: variant selects the register budget (0: 6
 // blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8) with u, du/dt prefetched two
@@ -78,7 +79,6 @@ struct DomDesc {
     KCof<P> k;
     View<P> v[2];
     const BNode* bn;
-    double* sig;
     unsigned* flag;
     unsigned long long* tstep;  // step counter (time of the boundary data)
     int nb;

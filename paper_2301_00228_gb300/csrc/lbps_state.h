@@ -28,9 +28,10 @@ struct Layout {
     size_t f_bytes;     // population planes (layout of the storage policy), aligned
     size_t u_bytes;     // 4 FP64 planes, aligned
     size_t m_bytes;     // boundary mirror (g.mplane points, storage layout), aligned
+    size_t s_bytes;     // stresses of the boundary cells (2 or 5 slots of 3 doubles per point), aligned
     size_t copy_bytes;
     size_t off_copy[2];
-    size_t off_bn, off_sig, off_type, off_part, off_out, off_flag, off_staging;
+    size_t off_bn, off_type, off_part, off_out, off_flag, off_staging;
     size_t staging_bytes;
     size_t total;
     int nb;
@@ -79,6 +80,7 @@ struct lbps_lattice {
         v.f = reinterpret_cast<typename P::Base*>(mem + L.off_copy[q]);
         v.u = u(q);
         v.m = reinterpret_cast<typename P::Base*>(mem + L.off_copy[q] + L.f_bytes + L.u_bytes);
+        v.s = reinterpret_cast<double*>(mem + L.off_copy[q] + L.f_bytes + L.u_bytes + L.m_bytes);
         return v;
     }
     double* u(int q) const { return reinterpret_cast<double*>(mem + L.off_copy[q] + L.f_bytes); }
@@ -90,7 +92,6 @@ struct lbps_lattice {
             return kf;
     }
     const lbps::BNode* bn() const { return reinterpret_cast<const lbps::BNode*>(mem + L.off_bn); }
-    double* sig() const { return reinterpret_cast<double*>(mem + L.off_sig); }
     unsigned* flag() const { return reinterpret_cast<unsigned*>(mem + L.off_flag); }
     // device step counter (time of the boundary data), beside the flag
     unsigned long long* tstep() const { return reinterpret_cast<unsigned long long*>(mem + L.off_flag + 8); }
