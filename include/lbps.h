@@ -252,7 +252,9 @@ int lbps_batch_step(lbps_batch* b, int64_t n);
 int lbps_batch_check(lbps_batch* b);
 
 /* Launch shape of the batch's interior kernel (as lbps_set_tuning;
- * rows_per_warp 8..4096).  Results do not depend on it. */
+ * rows_per_warp 8..4096).  Results do not depend on it.  Defaults: 5, 16
+ * (the batched kernel keeps each lattice's parameters in registers, so the
+ * 6-blocks-per-SM variants spill there). */
 int lbps_batch_set_tuning(lbps_batch* b, int32_t variant, int32_t rows_per_warp);
 
 /* Autotuner: times one step for each launch shape (variants 0, 1, 2, 4, 5,
