@@ -546,11 +546,11 @@ def run_gpu(args):
     e2e = None
     if args.e2e_steps > 0:
         pin_ux = torch.empty((d.ny, d.nx), dtype=torch.float64, pin_memory=True)
-        pin_uy = torch.empty_like(pin_ux)
+        pin_uy = torch.empty((d.ny, d.nx), dtype=torch.float64, pin_memory=True)
         pin_ux.copy_(ux.cpu())
         pin_uy.copy_(uy.cpu())
-        out_x = torch.empty_like(pin_ux)
-        out_y = torch.empty_like(pin_ux)
+        out_x = torch.empty((d.ny, d.nx), dtype=torch.float64, pin_memory=True)
+        out_y = torch.empty((d.ny, d.nx), dtype=torch.float64, pin_memory=True)
         barrier()
         t0 = time.perf_counter()
         lbps.lbps_init(lat._h, pin_ux.numpy(), pin_uy.numpy())

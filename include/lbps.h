@@ -158,7 +158,9 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
  * from host arrays [ny][nx]; phi, psi by finite differences of u; the
  * populations at equilibrium (Eq. feq).  vx0/vy0 may both be NULL (body at
  * rest); otherwise the first moments start at J_phi = -v, J_psi = (-v_y, v_x).
- * Rejects non-finite input with LBPS_ERR_INVALID.  Synchronises.  With
+ * The input is copied into the state copy that is not current and checked
+ * there on the device: non-finite input is rejected with LBPS_ERR_INVALID
+ * and leaves the lattice as it was.  Synchronises.  With
  * 16-bit storage and pop_scale_exp 0, the storage scale is chosen here from a
  * device reduction over the initial state (lbps_scale_exp reports it). */
 int lbps_init(lbps_lattice* lat, const double* ux0, const double* uy0,

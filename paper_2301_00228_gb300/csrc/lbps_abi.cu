@@ -383,19 +383,32 @@ int choose_scale(lbps_lattice* lat) {
 }
 
 // Copy four [ny][nx] arrays (v may be null) into the pitched u planes of the
-// current copy, then run the initialisation kernel.
-int init_from(lbps_lattice* lat, const double* ux0, const double* uy0, const double* vx0, const double* vy0,
-              cudaMemcpyKind kind) {
+// copy that is not current (the current state stays intact until the input
+// has been accepted).
+int stage_u(lbps_lattice* lat, const double* ux0, const double* uy0, const double* vx0, const double* vy0,
+            cudaMemcpyKind kind) {
     const Geo& g = lat->L.g;
-    double* u = lat->u(lat->cur);
+    double* u = lat->u(lat->cur ^ 1);
     size_t dp = (size_t)g.px * sizeof(double), sp = (size_t)g.nx * sizeof(double);
     const double* src[4] = {ux0, uy0, vx0, vy0};
     for (int q = 0; q < 4; ++q) {
         double* dst = u + (size_t)q * g.plane;
-        cudaError_t e = src[q] ? cudaMemcpy2DAsync(dst, dp, src[q], sp, sp, g.ny, kind, lat->st)
-                               : cudaMemset2DAsync(dst, dp, 0, sp, g.ny, lat->st);
+        cudaError_t e;
+        if (!src[q])
+            e = cudaMemset2DAsync(dst, dp, 0, sp, g.ny, lat->st);
+        else if (dp == sp)  // no row padding: one contiguous copy (a pitched one goes row by row from pageable memory)
+            e = cudaMemcpyAsync(dst, src[q], sp * g.ny, kind, lat->st);
+        else
+            e = cudaMemcpy2DAsync(dst, dp, src[q], sp, sp, g.ny, kind, lat->st);
         if (e != cudaSuccess) return LBPS_ERR_CUDA;
     }
+    return LBPS_OK;
+}
+
+// Make the staged copy current and initialise it: the initialisation kernel
+// (and the 16-bit scale choice before it).
+int init_staged(lbps_lattice* lat) {
+    lat->cur ^= 1;
     // the non-finite flag and the step counter beside it
     if (cudaMemsetAsync(lat->flag(), 0, 16, lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
     if (lat->neq16()) {
@@ -611,14 +624,33 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
 int lbps_init(lbps_lattice* lat, const double* ux0, const double* uy0, const double* vx0, const double* vy0) {
     lbps::NvtxRange nvtx("lbps_init");
     if (!lat || !ux0 || !uy0 || (!vx0) != (!vy0)) return LBPS_ERR_INVALID;
-    size_t n = (size_t)lat->p.nx * (size_t)lat->p.ny;
-    for (size_t k = 0; k < n; ++k) {
-        if (!std::isfinite(ux0[k]) || !std::isfinite(uy0[k])) return LBPS_ERR_INVALID;
-        if (vx0 && (!std::isfinite(vx0[k]) || !std::isfinite(vy0[k]))) return LBPS_ERR_INVALID;
-    }
-    int rc = init_from(lat, ux0, uy0, vx0, vy0, cudaMemcpyHostToDevice);
+    int rc = stage_u(lat, ux0, uy0, vx0, vy0, cudaMemcpyHostToDevice);
     if (rc != LBPS_OK) return rc;
-    cudaError_t e = cudaStreamSynchronize(lat->st);
+    // finiteness of the input, checked on the device over the staged planes
+    unsigned* bad = reinterpret_cast<unsigned*>(lat->out4());
+    unsigned h_bad = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(unsigned), lat->st);
+    if (e == cudaSuccess) e = lbps::launch_finite_check(lat->L.g, lat->u(lat->cur ^ 1), vx0 ? 4 : 2, bad, lat->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_bad, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, lat->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+    if (e != cudaSuccess) {
+        lat->last_cuda = (int)e;
+        return LBPS_ERR_CUDA;
+    }
+    if (h_bad) {
+        // rejected: the current state is untouched; clear the staging planes
+        // (points a step never writes, such as void points, must stay zero)
+        e = cudaMemsetAsync(lat->u(lat->cur ^ 1), 0, lat->L.u_bytes, lat->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+        if (e != cudaSuccess) {
+            lat->last_cuda = (int)e;
+            return LBPS_ERR_CUDA;
+        }
+        return LBPS_ERR_INVALID;
+    }
+    rc = init_staged(lat);
+    if (rc != LBPS_OK) return rc;
+    e = cudaStreamSynchronize(lat->st);
     if (e != cudaSuccess) lat->last_cuda = (int)e;
     return cuda_ok(e);
 }
@@ -627,7 +659,9 @@ int lbps_init_device(lbps_lattice* lat, const double* d_ux0, const double* d_uy0
                      const double* d_vy0) {
     lbps::NvtxRange nvtx("lbps_init_device");
     if (!lat || !d_ux0 || !d_uy0 || (!d_vx0) != (!d_vy0)) return LBPS_ERR_INVALID;
-    return init_from(lat, d_ux0, d_uy0, d_vx0, d_vy0, cudaMemcpyDeviceToDevice);
+    int rc = stage_u(lat, d_ux0, d_uy0, d_vx0, d_vy0, cudaMemcpyDeviceToDevice);
+    if (rc != LBPS_OK) return rc;
+    return init_staged(lat);
 }
 
 int lbps_step_async(lbps_lattice* lat, int64_t n) {
@@ -685,6 +719,17 @@ int lbps_read(lbps_lattice* lat, int32_t field, double* dst, size_t count) {
     if (count < field_count(lat, field)) return LBPS_ERR_INVALID;
     const Geo& g = lat->L.g;
     size_t nx = (size_t)g.nx, n = nx * (size_t)g.ny;
+    if (field >= LBPS_UX && field <= LBPS_VY && (size_t)g.px == nx) {
+        // a stored plane without row padding: one contiguous copy
+        cudaError_t e = cudaMemcpyAsync(dst, lat->u(lat->cur) + (size_t)field * g.plane, n * sizeof(double),
+                                        cudaMemcpyDeviceToHost, lat->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
+        if (e != cudaSuccess) {
+            lat->last_cuda = (int)e;
+            return LBPS_ERR_CUDA;
+        }
+        return LBPS_OK;
+    }
     int planes = (field == LBPS_F_PHI || field == LBPS_F_PSI) ? 5 : 1;
     size_t row_bytes = (size_t)planes * nx * sizeof(double);
     int chunk = (int)(lat->L.staging_bytes / row_bytes);
@@ -699,8 +744,9 @@ int lbps_read(lbps_lattice* lat, int32_t field, double* dst, size_t count) {
                                             (size_t)rows * nx * sizeof(double), cudaMemcpyDeviceToHost, lat->st);
             if (e != cudaSuccess) return LBPS_ERR_CUDA;
         }
-        if (cudaStreamSynchronize(lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
+        // no wait here: the next chunk's kernel runs after this copy on the stream
     }
+    if (cudaStreamSynchronize(lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
     return LBPS_OK;
 }
 

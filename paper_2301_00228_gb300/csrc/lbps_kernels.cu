@@ -61,6 +61,19 @@ __global__ void init_kernel(Geo g, Consts c, KCof<P> k, View<P> A) {
     P::store_eq_point(A.f, g.plane, p, c, sv, jx, jy, k);
 }
 
+// Sets *bad if any of the first `planes` FP64 planes of u holds a
+// non-finite value at a lattice point (the input check of the host
+// initialisation; the pitch padding is not looked at).
+__global__ void finite_check_kernel(Geo g, const double* __restrict__ u, int planes, unsigned* bad) {
+    const size_t n = (size_t)g.nx * (size_t)g.ny;
+    const size_t total = n * (size_t)planes;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t q = t / n, r = t - q * n;
+        const size_t j = r / (size_t)g.nx, i = r - j * (size_t)g.nx;
+        if (!isfinite(LBPS_LDG(&u[q * g.plane + j * (size_t)g.px + i]))) atomicOr(bad, 1u);
+    }
+}
+
 // Size of the lattice first moment J that the initial state implies, for the
 // choice of the 16-bit storage scale (the stored non-equilibrium sums are
 // smaller): per
@@ -853,6 +866,18 @@ int check_report(unsigned long long out[2]) {
     out[0] = out[1] = 0;
     return 0;
 #endif
+}
+
+cudaError_t launch_finite_check(const Geo& g, const double* u, int planes, unsigned* bad, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return cudaGetLastError();
+    const size_t total = (size_t)g.nx * (size_t)g.ny * (size_t)planes;
+    const size_t want = (total + 255) / 256;
+    const int blocks = (int)std::min<size_t>(want, (size_t)sms * 8);
+    finite_check_kernel<<<blocks, 256, 0, st>>>(g, u, planes, bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_scale_probe(const Geo& g, const Consts& c, const double* u, double sq, unsigned* out,

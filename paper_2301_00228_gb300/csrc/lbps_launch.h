@@ -15,6 +15,10 @@ using PolF64 = PopDirect<double>;
 using PolBF16 = PopNeq16<__nv_bfloat16>;
 using PolF16 = PopNeq16<__half>;
 
+// *bad |= 1 if one of the first `planes` u planes holds a non-finite value at
+// a lattice point (zero *bad first).
+cudaError_t launch_finite_check(const Geo& g, const double* u, int planes, unsigned* bad, cudaStream_t st);
+
 // Largest per-point estimate of |J| (scale_probe_kernel): FP32 bits
 // of a non-negative value, atomically maxed into *out (zero it first).
 cudaError_t launch_scale_probe(const Geo& g, const Consts& c, const double* u, double sq, unsigned* out,

@@ -410,3 +410,41 @@ def test_tunings_bit_identical(L):
     for bad in ((8, 64), (-1, 64), (0, 0), (0, 5000)):
         with pytest.raises(L.LbpsError):
             L.lbps_set_tuning(small._h, *bad)
+
+
+def test_rejected_init_keeps_state(L):
+    """lbps_init checks its input on the device after staging it in the copy
+    that is not current: a rejected input leaves the lattice exactly where it
+    was, and later steps (and void points of a general geometry) are
+    unaffected."""
+    ux, uy = W.pulse_displacement(47, 39, 20.0, 17.0, 3.0, 1e-3, "rotation")
+    a = L.Lattice.rectangle(47, 39, 1.2, 1.0, (1, 2, 1, 1), np.zeros(8), a0_phi=0.99).init(ux, uy).step(7)
+    b = L.Lattice.rectangle(47, 39, 1.2, 1.0, (1, 2, 1, 1), np.zeros(8), a0_phi=0.99).init(ux, uy).step(7)
+    before = {k: a.read(k) for k in ("ux", "uy", "vx", "vy", "phi", "psi")}
+    bad = np.full_like(ux, 3.0)
+    bad[5, 9] = np.nan
+    for args in ((bad, uy), (ux, uy, np.zeros_like(ux), np.where(ux > 1e-4, np.inf, 0.0))):
+        with pytest.raises(L.LbpsError) as e:
+            a.init(*args)
+        assert e.value.code == L.LBPS_ERR_INVALID
+    for k, v in before.items():
+        assert np.array_equal(a.read(k), v), k
+    a.step(13)
+    b.step(13)
+    for k in before:
+        assert np.array_equal(a.read(k), b.read(k)), k
+    # general geometry: garbage at void points of a rejected input never shows
+    n = 40
+    d, nt, bv, cell = W.hole_square(n, a0_phi=0.999, horizon=0.05, sync_every=0)
+    h = L.Lattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=nt, bc_value=bv, cell=cell)
+    z = np.zeros((n, n))
+    h.init(z, z)
+    junk = np.where(nt == L.LBPS_VOID, 7.0, 0.0)
+    junk[0, 0] = np.nan
+    with pytest.raises(L.LbpsError):
+        h.init(junk, junk)
+    h.init(*W.pulse_displacement(n, n, 10.0, 10.0, 3.0, 1e-3, "dilatation"))
+    h.step(5)
+    void = nt == L.LBPS_VOID
+    for k in ("ux", "uy", "vx", "vy"):
+        assert np.abs(h.read(k)[void]).max() == 0.0, k
