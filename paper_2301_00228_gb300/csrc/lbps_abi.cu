@@ -77,6 +77,9 @@ Layout make_layout(const lbps_params* p, bool general = false, int nb_general = 
     off += align_up((size_t)L.nb * sizeof(BNode));
     L.off_type = off;
     if (general) off += align_up(L.g.plane);
+    L.off_gap = off;  // general: 2 ints per strip of the interior kernel
+    if (general)
+        off += align_up((size_t)2 * (size_t)((p->nx + lbps::kBatchStripCols - 1) / lbps::kBatchStripCols) * sizeof(int));
     L.off_part = off;
     off += align_up((size_t)lbps::kNormBlocks * 4 * sizeof(double));
     L.off_out = off;
@@ -533,6 +536,34 @@ int lbps_create(const lbps_params* params, const uint8_t* node_type, const doubl
     return lbps_create_cells(params, node_type, bc_value, nullptr, device_mem, device_bytes, out);
 }
 
+// Per 30-column strip of the interior kernel, the longest run of rows [a, b)
+// in which none of the strip's columns holds an interior point (0, 0 if
+// there is none): the rows of a hole that the interior kernel can skip.  An
+// interior point's four neighbours are body points, so no interior point
+// outside the run reads the populations inside it.
+std::vector<int> strip_gaps(const lbps_params* p, const uint8_t* node_type) {
+    const int W = lbps::kBatchStripCols;  // = the interior kernel's strip width
+    const int nx = p->nx, ny = p->ny, strips = (nx + W - 1) / W;
+    std::vector<int> gap(2 * (size_t)strips, 0);
+    if (!node_type) return gap;
+    for (int s = 0; s < strips; ++s) {
+        int run = 0, best = 0, best_end = 0;
+        for (int j = 0; j < ny; ++j) {
+            bool any = false;
+            for (int i = W * s; i < std::min(nx, W * s + W) && !any; ++i)
+                any = node_type[(size_t)j * nx + i] == LBPS_INTERIOR;
+            run = any ? 0 : run + 1;
+            if (run > best) {
+                best = run;
+                best_end = j + 1;
+            }
+        }
+        gap[2 * (size_t)s] = best_end - best;
+        gap[2 * (size_t)s + 1] = best_end;
+    }
+    return gap;
+}
+
 int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const double* bc_value,
                       const double* cell, void* device_mem, size_t device_bytes, lbps_lattice** out) {
     if (!out) return LBPS_ERR_INVALID;
@@ -603,12 +634,19 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
     lat->cur = 0;
     lat->steps = 0;
     lat->initialised = false;
-    if (L.g.general) lat->L.g.type = reinterpret_cast<const uint8_t*>(lat->mem + L.off_type);
+    if (L.g.general) {
+        lat->L.g.type = reinterpret_cast<const uint8_t*>(lat->mem + L.off_type);
+        lat->L.g.gap = reinterpret_cast<const int*>(lat->mem + L.off_gap);
+        lat->gap = strip_gaps(params, node_type);
+    }
     cudaError_t e = cudaMemsetAsync(lat->mem, 0, L.total, lat->st);
     if (e == cudaSuccess) e = lbps::set_check_range(lat->mem, L.total, lat->st);
     if (e == cudaSuccess && L.g.general && node_type)
         e = cudaMemcpy2DAsync(lat->mem + L.off_type, (size_t)L.g.px, node_type, (size_t)L.g.nx, (size_t)L.g.nx,
                               (size_t)L.g.ny, cudaMemcpyHostToDevice, lat->st);
+    if (e == cudaSuccess && L.g.general)
+        e = cudaMemcpyAsync(lat->mem + L.off_gap, lat->gap.data(), lat->gap.size() * sizeof(int),
+                            cudaMemcpyHostToDevice, lat->st);
     if (e == cudaSuccess && L.nb > 0)
         e = cudaMemcpyAsync(lat->mem + L.off_bn, bn.data(), bn.size() * sizeof(BNode), cudaMemcpyHostToDevice,
                             lat->st);

@@ -24,6 +24,7 @@ struct lbps_batch {
     size_t mem_bytes = 0;
     size_t off_bnd = 0, off_bulk = 0, off_next = 0;
     int nbnd = 0, nbulk = 0;
+    size_t max_bulk = 0;  // capacity of the device work list (tasks)
     // default launch shape: 5 blocks per SM (no spills in the batched
     // kernel), u one row ahead, 16-row chunks; the fastest or within 3 % of
     // it on mixed batches of 64-2048-point sides (lbps_batch_tune refines it)
@@ -61,14 +62,37 @@ size_t desc_bytes(const lbps_batch* b) {
     return lbps::with_policy(b->storage, [](auto pol) { return sizeof(DomDesc<decltype(pol)>); });
 }
 
+// Work list of the interior kernel: every strip cut into chunks of `rows`
+// rows; in a general geometry the rows of a strip without interior points
+// (a hole, Geo::gap) are left out, splitting the chunk that spans them.
 std::vector<BulkTask> bulk_tasks(const lbps_batch* b, int rows) {
     std::vector<BulkTask> t;
     for (int d = 0; d < (int)b->lats.size(); ++d) {
-        const lbps::Geo& g = b->lats[d]->L.g;
-        for (int xs = 0; xs < g.nx; xs += lbps::kBatchStripCols)
-            for (int j0 = 0; j0 < g.ny; j0 += rows) t.push_back(BulkTask{d, xs, j0, std::min(j0 + rows, g.ny)});
+        const lbps_lattice* lat = b->lats[d];
+        const lbps::Geo& g = lat->L.g;
+        for (int xs = 0, s = 0; xs < g.nx; xs += lbps::kBatchStripCols, ++s) {
+            const int ga = lat->gap.empty() ? 0 : lat->gap[2 * (size_t)s];
+            const int gb = lat->gap.empty() ? 0 : lat->gap[2 * (size_t)s + 1];
+            for (int j0 = 0; j0 < g.ny; j0 += rows) {
+                const int j1 = std::min(j0 + rows, g.ny);
+                if (j0 < std::min(j1, ga)) t.push_back(BulkTask{d, xs, j0, std::min(j1, ga)});
+                if (std::max(j0, gb) < j1) t.push_back(BulkTask{d, xs, std::max(j0, gb), j1});
+            }
+        }
     }
     return t;
+}
+
+// Largest work list for any rows >= 8: ceil(ny / 8) chunks per strip, one of
+// them possibly split in two by the gap.
+size_t max_bulk_tasks(const lbps_batch* b) {
+    size_t n = 0;
+    for (const lbps_lattice* lat : b->lats) {
+        const lbps::Geo& g = lat->L.g;
+        const size_t strips = (size_t)(g.nx + lbps::kBatchStripCols - 1) / lbps::kBatchStripCols;
+        n += strips * ((size_t)(g.ny + 7) / 8 + 1);
+    }
+    return n;
 }
 
 int fail(lbps_batch* b, cudaError_t e) {
@@ -80,6 +104,7 @@ int fail(lbps_batch* b, cudaError_t e) {
 // block sized for the largest work list the tuner may ask for.
 int upload(lbps_batch* b) {
     std::vector<BulkTask> bt = bulk_tasks(b, b->rows);
+    if (bt.size() > b->max_bulk) return LBPS_ERR_INVALID;  // cannot happen (see max_bulk_tasks)
     std::vector<BndTask> nt;
     for (int d = 0; d < (int)b->lats.size(); ++d)
         for (int q = 0; q < b->lats[d]->L.nb; ++q) nt.push_back(BndTask{d, q});
@@ -204,9 +229,9 @@ int lbps_batch_create(lbps_lattice* const* lats, int32_t count, void* cuda_strea
         lbps_batch_destroy(b);
         return LBPS_ERR_CUDA;
     }
-    // Work lists: the bulk list is largest for the smallest tile height the
-    // tuner tries (8 rows).
-    size_t max_bulk = bulk_tasks(b, 8).size();
+    // Work lists: the bulk list sized for the longest any tile height gives.
+    size_t max_bulk = max_bulk_tasks(b);
+    b->max_bulk = max_bulk;
     size_t nbnd = 0;
     for (auto* l : b->lats) nbnd += (size_t)l->L.nb;
     b->off_bnd = align256((size_t)count * desc_bytes(b));

@@ -53,6 +53,10 @@ struct Geo {
     size_t plane;        // px * ny elements per plane
     const uint8_t* type; // [ny][px] node types (general = 1 only)
     size_t mplane;       // plane of the boundary mirror (boundary points, rounded up to 32)
+    // general geometry: per 30-column strip s of the interior kernel, gap[2s]
+    // .. gap[2s + 1] is the longest run of rows in which none of the strip's
+    // columns holds an interior point (empty run: 0, 0); null for rectangles
+    const int* gap;
 };
 
 // FP64 constants of the method (Eq. conditions-parameters, Eq. integration).

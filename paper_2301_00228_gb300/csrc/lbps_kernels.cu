@@ -438,6 +438,7 @@ __global__ void __launch_bounds__(128) boundary_mirror_kernel(Geo g, View<P> A, 
 // Every lattice point's words are read once per launch (plus the two halo
 // columns and two halo rows of each strip).
 constexpr int kStripCols = 30;
+static_assert(kStripCols == kBatchStripCols, "one strip width for the single-lattice and batched kernels");
 constexpr int kWarpsPerBlock = 4;
 
 template <typename P>
@@ -578,7 +579,11 @@ __global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KCof<P
     if (xs >= g.nx) return;  // whole warp
     const int j0 = blockIdx.y * rows_per_warp;
     const int j1 = min(j0 + rows_per_warp, g.ny);
-    bool bad = bulk_strip<P, UVD>(g, c, k, A, B, xs, j0, j1);
+    // General geometry: a warp whose rows all lie in its strip's run of rows
+    // without interior points (inside a hole) has nothing to write, and no
+    // interior point reads those rows: it returns before loading them.
+    if (g.gap && j0 >= LBPS_LD(&g.gap[2 * warp]) && j1 <= LBPS_LD(&g.gap[2 * warp + 1])) return;
+    const bool bad = bulk_strip<P, UVD>(g, c, k, A, B, xs, j0, j1);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 

@@ -31,7 +31,7 @@ struct Layout {
     size_t s_bytes;     // stresses of the boundary cells (2 or 5 slots of 3 doubles per point), aligned
     size_t copy_bytes;
     size_t off_copy[2];
-    size_t off_bn, off_type, off_part, off_out, off_flag, off_staging;
+    size_t off_bn, off_type, off_gap, off_part, off_out, off_flag, off_staging;
     size_t staging_bytes;
     size_t total;
     int nb;
@@ -60,6 +60,7 @@ struct lbps_lattice {
     double bc_est = 0.0;  // boundary values' share of the 16-bit scale estimate
     int scale_exp = 0;    // 16-bit storage: Nx, Ny are stored times 2^scale_exp
     int64_t gen = 0;      // incremented by every init (batches re-read descriptors)
+    std::vector<int> gap; // general geometry: rows without interior points per strip (Geo::gap, host copy)
     cudaStream_t st;
     char* mem;
     bool owns;
