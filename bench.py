@@ -196,15 +196,15 @@ def ncu_traffic(workload_name, storage):
 
 # ------------------------------------------------------------ CPU oracle
 
-def oracle_sample(d, target_seconds=15.0, side=1024):
-    """Time the FP64 oracle on a side x side crop of the workload (bottom-left
-    corner, same edge types) for as many steps as fill about target_seconds."""
+def oracle_lattice(d, side=1024):
+    """The FP64 oracle on a side x side crop of the workload (bottom-left
+    corner, same edge types; a plate with a hole is rebuilt at that size),
+    initialised.  Returns (lattice, points, description of the sample)."""
     import numpy as np
     import oracle as O
     from paper_2301_00228_gb300 import workloads as W
 
-    threads = os.cpu_count() or 1
-    O.set_threads(threads)
+    O.set_threads(os.cpu_count() or 1)
     if getattr(d, "geometry", None) is not None:
         # the same plate with a hole at side x side, loads and synchronisation
         n = min(side, d.nx)
@@ -214,16 +214,7 @@ def oracle_sample(d, target_seconds=15.0, side=1024):
         for kind, t_ramp, t_hold in dd.loads:
             lat.set_load(kind, t_ramp, t_hold)
         lat.init(np.zeros((n, n)), np.zeros((n, n)))
-        t0 = time.perf_counter()
-        lat.step(2)
-        per = (time.perf_counter() - t0) / 2
-        steps = max(2, int(target_seconds / max(per, 1e-9)))
-        t0 = time.perf_counter()
-        lat.step(steps)
-        dt = time.perf_counter() - t0
-        return {"value": n * n * steps / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
-                "sample": f"{n}x{n} plate with the same hole, loads and synchronisation, {steps} FP64 steps "
-                          f"in {dt:.1f} s"}, dt, steps
+        return lat, n * n, f"{n}x{n} plate with the same hole, loads and synchronisation"
     side_x, side_y = min(side, d.nx), min(side, d.ny)
     if d.periodic_x and d.periodic_y:
         c = W.Domain(side_x, side_y, d.lam, d.mu, d.rho, d.a0_phi, periodic_x=True, periodic_y=True)
@@ -239,77 +230,55 @@ def oracle_sample(d, target_seconds=15.0, side=1024):
     lat = O.OracleLattice(side_x, side_y, c.lam, c.mu, c.rho, a0_phi=c.a0_phi, periodic_x=c.periodic_x,
                           periodic_y=c.periodic_y, node_type=nt, bc_value=bv)
     lat.init(ux, uy)
-    t0 = time.perf_counter()
-    lat.step(2)
-    per = (time.perf_counter() - t0) / 2
-    steps = max(2, int(target_seconds / max(per, 1e-9)))
+    return lat, side_x * side_y, f"{side_x}x{side_y} corner crop of the workload (same material, edges of the corner kept)"
+
+
+def time_oracle(lat, target_seconds, per=None):
+    """Steps of the oracle lattice filling about target_seconds (the time per
+    step measured on two steps unless given): (seconds, steps, seconds per step)."""
+    if per is None:
+        t0 = time.perf_counter()
+        lat.step(2)
+        per = (time.perf_counter() - t0) / 2
+    steps = max(1, int(target_seconds / max(per, 1e-9)))
     t0 = time.perf_counter()
     lat.step(steps)
     dt = time.perf_counter() - t0
-    glups = side_x * side_y * steps / dt / 1e9
-    return {"value": glups, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{side_x}x{side_y} corner crop of the workload (same material, edges of the "
-                      f"corner kept), {steps} FP64 steps in {dt:.1f} s"}, dt, steps
+    return dt, steps, dt / steps
 
 
-def precision_report(d, side, steps):
-    """Relative L2 per field of every storage format against the FP64 oracle
-    on a side x side stand-alone crop of the workload (the window with the
-    most pulse centres; the workload's edge types on its edges; the pulses
-    centred inside), run for the given number of steps."""
-    import numpy as np
-    import oracle as O
-    from paper_2301_00228_gb300 import lbps
-    from paper_2301_00228_gb300 import workloads as W
-
-    x0, y0 = W.busiest_crop(d, side)
-    c = W.crop(d, x0, y0, side, side)
-    ux, uy = c.displacement()
-    ev = np.asarray(c.edge_value, float).ravel()
-    fields = ("ux", "uy", "phi", "psi")
-    got = {}
-    for st in ("f32", "bf16", "f16"):
-        lat = lbps.Lattice.rectangle(side, side, c.lam, c.mu, c.edge_type, ev, a0_phi=c.a0_phi, storage=st)
-        lat.init(ux, uy).step(steps)
-        got[st] = ({k: lat.read(k) for k in fields}, lat.scale_exp)
-        lat.close()
-    O.set_threads(os.cpu_count() or 1)
-    nt, bv = O.rect_bc(side, side, c.edge_type, ev)
-    t0 = time.perf_counter()
-    ref = O.OracleLattice(side, side, c.lam, c.mu, c.rho, a0_phi=c.a0_phi, node_type=nt, bc_value=bv)
-    ref.init(ux, uy).step(steps)
-    secs = time.perf_counter() - t0
-    rf = ref.fields()
-    out = {}
-    for st, (g, e) in got.items():
-        errs = {}
-        for grp in (("ux", "uy"), ("phi", "psi")):
-            gn = np.sqrt(sum(np.linalg.norm(rf[k]) ** 2 for k in grp))
-            for k in grp:
-                den = max(np.linalg.norm(rf[k]), 1e-2 * gn, 1e-300)
-                errs[k] = float(np.linalg.norm(g[k] - rf[k]) / den)
-        out[st] = {"rel_l2": errs, "max": max(errs.values()), "scale_exp": e,
-                   "bytes_per_update": BYTES_PER_UPDATE[st]}
-    return {"crop": f"{side}x{side} at ({x0}, {y0})", "pulses": len(c.pulses), "steps": steps,
-            "a0_phi": c.a0_phi, "oracle_seconds": secs, "oracle_threads": os.cpu_count() or 1, "formats": out}
+def oracle_sample(d, target_seconds=15.0, side=1024):
+    """Time the FP64 oracle on the crop of oracle_lattice for as many steps as
+    fill about target_seconds."""
+    lat, points, what = oracle_lattice(d, side)
+    dt, steps, _ = time_oracle(lat, target_seconds)
+    return {"value": points * steps / dt / 1e9, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": f"{what}, {steps} FP64 steps in {dt:.1f} s"}, dt, steps
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores, one bounded sample per timed step
+    (a crop of the workload, built once): each step runs as many oracle steps
+    as fill min(--ref-seconds, 150 s / steps), so the whole run stays within a
+    few minutes for any --steps."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     wname, d = workload(args.workload, args.size)
-    secs = []
+    lat, points, what = oracle_lattice(d)
+    target = min(args.ref_seconds, 150.0 / max(1, args.steps))
+    _, _, per = time_oracle(lat, 0.5)
     for _ in range(args.warmup):
-        oracle_sample(d, target_seconds=2.0)
-    vals = []
-    cb = None
+        time_oracle(lat, target, per)
+    secs, n_steps = [], []
     for _ in range(args.steps):
-        cb, dt, _ = oracle_sample(d, target_seconds=args.ref_seconds)
-        vals.append(cb["value"])
+        dt, steps, per = time_oracle(lat, target, per)
         secs.append(dt)
-    value = sum(vals) / len(vals)
-    cb["value"] = value
+        n_steps.append(steps)
+    value = points * sum(n_steps) / sum(secs) / 1e9
+    cb = {"value": value, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
+          "sample": f"{what}; {args.steps} timed samples of {min(n_steps)}-{max(n_steps)} FP64 steps, "
+                    f"{sum(secs):.1f} s in all"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

@@ -148,3 +148,31 @@ def test_invalid_geometry_rejected(L):
         with pytest.raises(L.LbpsError) as e:
             L.Lattice(nx, ny, 1.0, 1.0, node_type=nt_bad, bc_value=bv, cell=cl)
         assert e.value.code == L.LBPS_ERR_INVALID
+
+
+def test_hole_rows_skipped_same_bits(L):
+    """Warps whose rows lie inside the hole return without loading them. With
+    8-row chunks many do; every launch shape must give the same bits, and the
+    oracle's result within tolerance."""
+    n = 96
+    d, nt, bv, cell = W.hole_square(n, a0_phi=0.99, horizon=0.2, sync_every=0)
+    ux, uy = W.pulse_displacement(n, n, 20.0, 30.0, 5.0, 1e-3, "dilatation")
+    body = nt != 3
+    ux, uy = ux * body, uy * body
+    ref = O.OracleLattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=nt, bc_value=bv, cell=cell)
+    want = ref.init(ux, uy).step(150).fields()
+    first = None
+    for variant in range(8):
+        for rows in (8, 16, 64):
+            lat = L.Lattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=nt, bc_value=bv, cell=cell,
+                            storage="f32")
+            L.lbps_set_tuning(lat._h, variant, rows)
+            got = lat.init(ux, uy).step(150).fields()
+            if first is None:
+                first = got
+                errs = rel(got, want, body)
+                assert all(v <= TOL["f32"] for v in errs.values()), errs
+            else:
+                for k in FIELDS:
+                    assert np.array_equal(got[k], first[k]), (variant, rows, k)
+            lat.close()
