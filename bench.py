@@ -352,7 +352,7 @@ def run_batch(args):
                          "peak_source": peak_kind},
             "one_at_a_time": {"value": loop_value, "unit": UNIT, "steps": loop_steps,
                               "speedup_of_batch": value / loop_value},
-            "gpu_launches": 4 * args.steps, "clocks": clock}
+            "gpu_launches": 3 * args.steps, "clocks": clock}
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()
@@ -509,7 +509,11 @@ def run_gpu(args):
                 "share_of_step_kernel_time": bulk_ms / total_kernel_ms if total_kernel_ms else None,
                 "boundary_passes_ms_per_step": bnd_ms / args.steps}
     bounded = not (d.periodic_x and d.periodic_y)
-    gpu_launches = int(bulk_n) * (4 if bounded else 1) + (args.steps // sync_every if sync_every else 0)
+    # per step: boundary Newmark, interior, boundary reset (a periodic lattice
+    # has no boundary); per synchronisation: the sync kernel and the refresh
+    # of the boundary mirror
+    gpu_launches = int(bulk_n) * (3 if bounded else 1) + (
+        (args.steps // sync_every) * (2 if bounded else 1) if sync_every else 0)
 
     # end to end through the C ABI with host buffers
     e2e = None
