@@ -312,7 +312,12 @@ def run_batch(args):
     points = sum(d.nx * d.ny for d in ds)
     interior = sum((d.nx - 2) * (d.ny - 2) for d in ds)
     b = lbps.Batch(lats)
-    variant, rows, tuned_ms = b.tune(repeats=5)
+    if args.batch_tuning:  # a fixed launch shape (profiling), no tuner
+        variant, rows = (int(x) for x in args.batch_tuning.split(","))
+        b.set_tuning(variant, rows)
+        tuned_ms = None
+    else:
+        variant, rows, tuned_ms = b.tune(repeats=5)
     stream = torch.cuda.current_stream()
     b.step(args.warmup)
     torch.cuda.synchronize()
@@ -582,6 +587,8 @@ def main(argv=None):
     ap.add_argument("--max-chunk", type=int, default=500, help="serve: most steps between completions checks")
     ap.add_argument("--burst", type=int, default=32, help="serve: requests arriving at once for the capacity run")
     ap.add_argument("--batch-count", type=int, default=256, help="domains of the batch workload")
+    ap.add_argument("--batch-tuning", default=None,
+                    help="batch: launch shape 'variant,rows' instead of running the autotuner")
     ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--precision", action="store_true",
