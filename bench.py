@@ -175,9 +175,17 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    src = (ROOT / "paper_2301_00228_gb300" / "csrc" / "lbps_kernels.cu").read_bytes()
-    src += (ROOT / "paper_2301_00228_gb300" / "csrc" / "lbps_device.cuh").read_bytes()
-    return hashlib.sha256(src).hexdigest()[:16]
+    """sha256 (first 16 hex digits) of the kernel sources' code: the two files
+    with // comments and blank lines removed, so editing a comment keeps the
+    recorded ncu traffic valid and editing code does not."""
+    code = []
+    for name in ("lbps_kernels.cu", "lbps_device.cuh"):
+        text = (ROOT / "paper_2301_00228_gb300" / "csrc" / name).read_text()
+        for line in text.splitlines():
+            line = re.sub(r"//.*", "", line).rstrip()
+            if line.strip():
+                code.append(line)
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
 def ncu_traffic(workload_name, storage):

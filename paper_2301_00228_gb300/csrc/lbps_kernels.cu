@@ -1,11 +1,10 @@
 // CUDA kernels of the plane-strain lattice Boltzmann time loop
 // (arXiv:2301.00228, algorithm summary of Fig. 3), sm_103a.
 //
-// One time step is four launches on one stream:
-//   boundary stress   sigma at every boundary point and its interior
-//                     neighbour (Eq. strain, Eq. hooke), for Eq. acc_neumann;
-//   boundary newmark  acceleration of each boundary point (Eq. acc_neumann or
-//                     Eq. acc_dirichlet) and u, du/dt at t + dt (Eq.
+// One time step is three launches on one stream:
+//   boundary newmark  acceleration of each boundary point (Eq. acc_neumann,
+//                     from the stresses kept with the state copy, or Eq.
+//                     acc_dirichlet) and u, du/dt at t + dt (Eq.
 //                     integration);
 //   bulk              every interior point: acceleration (Eq. navier),
 //                     Newmark, and the pull form of the LBE (Eq. LBE).
@@ -13,8 +12,9 @@
 //                     once;
 //   boundary reset    phi, psi at boundary points from differences of the new
 //                     u (Eq. psi_phi_at_bound), their populations by Eq.
-//                     correction-f, and the value each streams into its
-//                     interior neighbour (Eq. LBE_mod).
+//                     correction-f, the value each streams into its
+//                     interior neighbour (Eq. LBE_mod), and the stresses of
+//                     the new u (Eq. strain, Eq. hooke) for the next step.
 // Copies A (time t) and B (time t + dt) swap after each step.  Every kernel is
 // a template over the population storage policy (lbps_device.cuh): FP32 or
 // FP64 planes, or FP32 moments (f^0, J) with the non-equilibrium pair sums in
