@@ -448,3 +448,20 @@ def test_rejected_init_keeps_state(L):
     void = nt == L.LBPS_VOID
     for k in ("ux", "uy", "vx", "vy"):
         assert np.abs(h.read(k)[void]).max() == 0.0, k
+
+
+def test_caller_block_too_small_or_misaligned(L):
+    """Host-side fault injection for allocation: a caller-provided device
+    block smaller than lbps_state_bytes, or not 256-byte aligned, is refused
+    with LBPS_ERR_OOM before anything is written to it."""
+    p = L.lbps_params(40, 30, 1.0, 1.0, 1.0, 1.0, 0.99, 0, 0, 0, 0, L.LBPS_STORAGE_F32, 0, None)
+    need = L.lbps_state_bytes(p)
+    nt, bv = L.lbps_rect_bc(40, 30, 0, 0, 1.0, (2, 1, 1, 1), np.zeros(8))
+    block = torch.zeros(need + 512, dtype=torch.uint8, device="cuda")
+    for ptr, size in ((block.data_ptr(), need - 1), (block.data_ptr() + 64, need)):
+        with pytest.raises(L.LbpsError) as e:
+            L.lbps_create(p, nt, bv, ptr, size)
+        assert e.value.code == L.LBPS_ERR_OOM
+    assert int(block.sum()) == 0                      # nothing written
+    h = L.lbps_create(p, nt, bv, block.data_ptr(), need)
+    L._lib.lbps_destroy(h)
