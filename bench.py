@@ -264,6 +264,48 @@ def oracle_sample(d, target_seconds=15.0, side=1024):
             "sample": f"{what}, {steps} FP64 steps in {dt:.1f} s"}, dt, steps
 
 
+def precision_report(d, side, steps):
+    """Relative L2 per field of every storage format against the FP64 oracle
+    on a side x side stand-alone crop of the workload (the window with the
+    most pulse centres; the workload's edge types on its edges; the pulses
+    centred inside), run for the given number of steps."""
+    import numpy as np
+    import oracle as O
+    from paper_2301_00228_gb300 import lbps
+    from paper_2301_00228_gb300 import workloads as W
+
+    x0, y0 = W.busiest_crop(d, side)
+    c = W.crop(d, x0, y0, side, side)
+    ux, uy = c.displacement()
+    ev = np.asarray(c.edge_value, float).ravel()
+    fields = ("ux", "uy", "phi", "psi")
+    got = {}
+    for st in ("f32", "bf16", "f16"):
+        lat = lbps.Lattice.rectangle(side, side, c.lam, c.mu, c.edge_type, ev, a0_phi=c.a0_phi, storage=st)
+        lat.init(ux, uy).step(steps)
+        got[st] = ({k: lat.read(k) for k in fields}, lat.scale_exp)
+        lat.close()
+    O.set_threads(os.cpu_count() or 1)
+    nt, bv = O.rect_bc(side, side, c.edge_type, ev)
+    t0 = time.perf_counter()
+    ref = O.OracleLattice(side, side, c.lam, c.mu, c.rho, a0_phi=c.a0_phi, node_type=nt, bc_value=bv)
+    ref.init(ux, uy).step(steps)
+    secs = time.perf_counter() - t0
+    rf = ref.fields()
+    out = {}
+    for st, (g, e) in got.items():
+        errs = {}
+        for grp in (("ux", "uy"), ("phi", "psi")):
+            gn = np.sqrt(sum(np.linalg.norm(rf[k]) ** 2 for k in grp))
+            for k in grp:
+                den = max(np.linalg.norm(rf[k]), 1e-2 * gn, 1e-300)
+                errs[k] = float(np.linalg.norm(g[k] - rf[k]) / den)
+        out[st] = {"rel_l2": errs, "max": max(errs.values()), "scale_exp": e,
+                   "bytes_per_update": BYTES_PER_UPDATE[st]}
+    return {"crop": f"{side}x{side} at ({x0}, {y0})", "pulses": len(c.pulses), "steps": steps,
+            "a0_phi": c.a0_phi, "oracle_seconds": secs, "oracle_threads": os.cpu_count() or 1, "formats": out}
+
+
 def run_reference(args):
     """The FP64 oracle on the host cores, one bounded sample per timed step
     (a crop of the workload, built once): each step runs as many oracle steps

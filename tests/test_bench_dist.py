@@ -69,3 +69,25 @@ def test_single_process_reducers_are_identity():
 
     rmax, rsum = bench.reducers(None, "cpu")
     assert bench.aggregate(2.0, 10.0, 1, rmax, rsum) == (5.0, 2.0, 10.0)
+
+
+def test_bench_calls_only_defined_functions():
+    """Every module-level function bench.py calls by bare name is defined in it
+    or imported (a static check: the GPU arms cannot run here)."""
+    import ast
+    import builtins
+
+    src = (Path(__file__).resolve().parents[1] / "bench.py").read_text()
+    tree = ast.parse(src)
+    known = set(dir(builtins))
+    for node in ast.walk(tree):
+        if isinstance(node, (ast.FunctionDef, ast.ClassDef)):
+            known.add(node.name)
+        elif isinstance(node, (ast.Import, ast.ImportFrom)):
+            known.update((a.asname or a.name).split(".")[0] for a in node.names)
+        elif isinstance(node, ast.Name) and isinstance(node.ctx, ast.Store):
+            known.add(node.id)
+        elif isinstance(node, ast.arg):
+            known.add(node.arg)
+    called = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
+    assert not called - known, sorted(called - known)
