@@ -53,10 +53,11 @@ extern "C" {
  * f^0, Jx = f^1 - f^3, Jy = f^2 - f^4 in FP32 and the two pair sums'
  * deviations from equilibrium (Eq. feq), Nx = f^1 + f^3 - 2 (a/a_0) f^0 and
  * Ny = f^2 + f^4 - 2 (a/a_0) f^0, in 16 bits multiplied by 2^scale_exp;
- * IEEE half rounds to nearest, bfloat16 rounds stochastically with random
- * bits hashed from the value and its position (deterministic, so results do
- * not depend on launch shape, batching or resumes); arithmetic is FP32.  32 bytes per point per state copy
- * instead of 40 (FP32).  They reject lattices 3 points wide along a
+ * with a0_phi >= 0.999 (slow waves) both formats round these stochastically,
+ * with random bits hashed from the value and its position (deterministic, so
+ * results do not depend on launch shape, batching or resumes), otherwise to
+ * nearest; arithmetic is FP32.  32 bytes per point per state copy instead of
+ * 40 (FP32).  They reject lattices 3 points wide along a
  * non-periodic axis (LBPS_ERR_INVALID). */
 #define LBPS_STORAGE_F32 0      /* FP32 populations, FP32 arithmetic          */
 #define LBPS_STORAGE_F64 1      /* FP64 populations, FP64 arithmetic          */

@@ -89,6 +89,7 @@ struct KC {
     T cd2h, cs2h;               // c_d^2 / (2 dh), c_s^2 / (2 dh)
     T r[2];                     // a / a_0 (16-bit storage: equilibrium pair sum 2 r f^0)
     T scale, inv_scale;         // 2^e, 2^-e applied to the stored 16-bit Nx, Ny
+    unsigned sr;                // 16-bit storage: round the stored sums stochastically (f2bits_store)
 };
 
 // One state copy: the population planes (layout set by the storage policy P),
@@ -423,22 +424,32 @@ __device__ __forceinline__ unsigned mix32(unsigned h) {
     return h;
 }
 
-// 16-bit code of v with the rounding each format uses for the stored
-// non-equilibrium sums.  IEEE half: round to nearest.  bfloat16: stochastic
-// rounding (up with probability equal to the dropped fraction), with the
-// random bits a hash of the value and of `key` (the point and slot), so the
-// result is a deterministic function of the state.  With an 8-bit
-// significand and the tiny per-step changes of a_0 near 1, rounding to
-// nearest makes nearly the same error every step and the errors add up;
-// unbiased rounding lets them average out.
+// 16-bit code of v for the stored non-equilibrium sums: rounded to nearest,
+// or (sr) stochastically, up with probability equal to the dropped fraction,
+// the random bits a hash of the value and of `key` (the point and slot), so
+// the result stays a deterministic function of the state.  When a_0 is near
+// 1 the per-step changes of the sums lie near or below half a 16-bit ulp:
+// rounding to nearest then makes nearly the same error every step and the
+// errors add up, while unbiased rounding lets them average out.  With faster
+// waves (a_0 further from 1) the errors of rounding to nearest decorrelate by
+// themselves and stochastic rounding only adds variance.  The library rounds
+// stochastically when a_{0,phi} >= 0.999 (KC::sr), for both formats.
 template <typename H>
-__device__ __forceinline__ unsigned f2bits_store(float v, unsigned key);
+__device__ __forceinline__ unsigned f2bits_store(float v, unsigned key, bool sr);
 template <>
-__device__ __forceinline__ unsigned f2bits_store<__half>(float v, unsigned) { return f2bits<__half>(v); }
-template <>
-__device__ __forceinline__ unsigned f2bits_store<__nv_bfloat16>(float v, unsigned key) {
+__device__ __forceinline__ unsigned f2bits_store<__half>(float v, unsigned key, bool sr) {
+    const float a = fabsf(v);
+    // nearest for overflow and for subnormal halves (below 2^-14 more than
+    // 13 bits are dropped)
+    if (!sr || !(a < 65504.0f) || a < 6.103515625e-05f) return f2bits<__half>(v);
     const unsigned u = __float_as_uint(v);
-    if (!isfinite(v)) return f2bits<__nv_bfloat16>(v);
+    // 13 random bits added below the kept ones, then the magnitude truncated
+    return __half_as_ushort(__float2half_rz(__uint_as_float(u + (mix32(u ^ mix32(key)) & 0x1fffu))));
+}
+template <>
+__device__ __forceinline__ unsigned f2bits_store<__nv_bfloat16>(float v, unsigned key, bool sr) {
+    if (!sr || !isfinite(v)) return f2bits<__nv_bfloat16>(v);
+    const unsigned u = __float_as_uint(v);
     // adding below the kept bits rounds the magnitude up with the dropped
     // fraction's probability; a carry into the exponent is the next value up
     return (u + (mix32(u ^ mix32(key)) & 0xffffu)) >> 16;
@@ -474,8 +485,8 @@ struct PopNeq16 {
     }
     // key: the point's plane offset and the slot (set, pair) for the rounding
     __device__ __forceinline__ static unsigned enc_n(float pair_sum, float f0, float r, float scale,
-                                                     unsigned key) {
-        return f2bits_store<H>(mul_rn(fma_rn(-2.0f * r, f0, pair_sum), scale), key);
+                                                     unsigned key, bool sr) {
+        return f2bits_store<H>(mul_rn(fma_rn(-2.0f * r, f0, pair_sum), scale), key, sr);
     }
     __device__ __forceinline__ static void load_raw(const float* __restrict__ f, size_t plane, size_t p, bool ok,
                                                     Raw& r) {
@@ -523,8 +534,9 @@ struct PopNeq16 {
             LBPS_ST(f + (size_t)(s * 3) * plane + p, x[s][0]);
             LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, sub_rn(x[s][1], x[s][3]));
             LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, sub_rn(x[s][2], x[s][4]));
-            wx |= enc_n(add_rn(x[s][1], x[s][3]), x[s][0], k.r[s], k.scale, (unsigned)p * 4u + 2u * s) << (16 * s);
-            wy |= enc_n(add_rn(x[s][2], x[s][4]), x[s][0], k.r[s], k.scale, (unsigned)p * 4u + 2u * s + 1u)
+            wx |= enc_n(add_rn(x[s][1], x[s][3]), x[s][0], k.r[s], k.scale, (unsigned)p * 4u + 2u * s, k.sr)
+                  << (16 * s);
+            wy |= enc_n(add_rn(x[s][2], x[s][4]), x[s][0], k.r[s], k.scale, (unsigned)p * 4u + 2u * s + 1u, k.sr)
                   << (16 * s);
         }
         unsigned* w = words(f, plane);
@@ -552,7 +564,7 @@ struct PopNeq16 {
             const float rf0 = mul_rn(k.r[s], f0);
             const float partner = plus ? fma_rn(0.5f, sub_rn(nn, j), rf0) : fma_rn(0.5f, add_rn(nn, j), rf0);
             LBPS_ST(jp, plus ? sub_rn(v[s], partner) : sub_rn(partner, v[s]));
-            out |= enc_n(add_rn(v[s], partner), f0, k.r[s], k.scale, (unsigned)p * 4u + 2u * s + (unsigned)ax)
+            out |= enc_n(add_rn(v[s], partner), f0, k.r[s], k.scale, (unsigned)p * 4u + 2u * s + (unsigned)ax, k.sr)
                    << (16 * s);
         }
         LBPS_ST(wp, out);
@@ -582,7 +594,7 @@ struct PopNeq16 {
             r.m[s][1] = (float)jx[s];
             r.m[s][2] = (float)jy[s];
             const float dev = mul_rn(fma_rn(-2.0f * k.r[s], f0, mul_rn(k.two_a[s], sf)), k.scale);
-            w |= f2bits_store<H>(dev, (unsigned)p * 4u + 2u * s) << (16 * s);
+            w |= f2bits_store<H>(dev, (unsigned)p * 4u + 2u * s, k.sr) << (16 * s);
         }
         r.w[0] = w;
         r.w[1] = w;

@@ -28,7 +28,7 @@ TOL = {"f32": 1e-5, "bf16": 1e-3, "f16": 1e-3}
 # 1024^2 crop of the precision workload (5000 steps, bench.py --precision)
 # bf16 meets 1e-3 (9.0e-4) with its stochastic rounding.
 CROP_BF16 = 3e-3
-WAVES = {"f16": 1e-2, "bf16": 2e-2}
+WAVES = {"f16": 2e-3, "bf16": 2e-2}   # measured 1.2e-3 and 9.0e-3 (stochastic rounding at a_0 = 0.9999)
 GROUPS = (("ux", "uy"), ("phi", "psi"))
 
 
