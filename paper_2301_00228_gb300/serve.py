@@ -12,7 +12,9 @@ times and serves them as they arrive:
   in chunks no longer than the shortest remaining solve, so every solve stops
   exactly at its step count;
 * completion: finished solves are read out (their u fields) and freed, and
-  the batch is rebuilt with the waiting requests that now fit.
+  the batch is rebuilt with the waiting requests that now fit;
+* cancellation: a request withdrawn by its client (``cancel_at``) leaves the
+  queue, or the batch at the next chunk boundary, and its memory is freed.
 
 ``serve_one_at_a_time`` is the plain baseline: the same kernels, one solve at
 a time in arrival order.  Both report per-request latency (completion minus
@@ -36,6 +38,10 @@ class Request:
     arrival: float          # seconds after the start of the run
     domain: object          # workloads.Domain
     steps: int
+    cancel_at: float | None = None  # the client withdraws the request at this time (None: never)
+
+    def cancelled_by(self, now):
+        return self.cancel_at is not None and self.cancel_at <= now
 
 
 @dataclass
@@ -60,13 +66,15 @@ class Report:
     rebuilds: int = 0
     max_active: int = 0
     peak_bytes: int = 0
+    cancelled: list = field(default_factory=list)   # rids withdrawn before completion
 
     def summary(self):
         lat = np.array([r.latency for r in self.results])
         return {"solves": len(self.results), "solves_per_s": len(self.results) / self.makespan,
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_latency_s": float(lat.mean()), "makespan_s": self.makespan, "chunks": self.chunks,
-                "batch_rebuilds": self.rebuilds, "max_active": self.max_active, "peak_state_bytes": self.peak_bytes}
+                "batch_rebuilds": self.rebuilds, "max_active": self.max_active, "peak_state_bytes": self.peak_bytes,
+                "cancelled": len(self.cancelled)}
 
 
 def _params(d, storage):
@@ -123,6 +131,16 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
         while nxt < len(reqs) and reqs[nxt].arrival <= now:
             waiting.append(reqs[nxt])
             nxt += 1
+        # withdrawn requests leave the queue, or the batch (at this chunk
+        # boundary), and give their memory back
+        for r in [r for r in waiting if r.cancelled_by(now)]:
+            waiting.remove(r)
+            rep.cancelled.append(r.rid)
+        for a in [a for a in active if a[0].cancelled_by(now)]:
+            active.remove(a)
+            a[1].close()
+            used -= footprint(a[0].domain, storage)
+            rep.cancelled.append(a[0].rid)
         # admit in arrival order while memory is left
         while waiting:
             need = footprint(waiting[0].domain, storage)
@@ -135,6 +153,9 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
         rep.peak_bytes = max(rep.peak_bytes, used)
         rep.max_active = max(rep.max_active, len(active))
         if not active:
+            if batch is not None:  # the last members were withdrawn
+                batch.close()
+                batch, batch_members = None, ()
             if nxt < len(reqs):
                 clk.wait_until(reqs[nxt].arrival)
             continue
@@ -178,12 +199,17 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
 
 
 def serve_one_at_a_time(requests, storage="f32", keep_fields=True, clock=time.perf_counter, prepared=None):
-    """Baseline: one solve at a time, in arrival order, with lbps_step."""
+    """Baseline: one solve at a time, in arrival order, with lbps_step.  A
+    request withdrawn before its turn is skipped; one running is not
+    interrupted (lbps_step runs it to the end)."""
     reqs = sorted(requests, key=lambda r: r.arrival)
     clk = _Clock(clock)
     rep = Report()
     for r in reqs:
         clk.wait_until(r.arrival)
+        if r.cancelled_by(clk.now()):
+            rep.cancelled.append(r.rid)
+            continue
         admitted = clk.now()
         u0 = prepared.get(r.rid) if prepared else None
         lat = _lattice(r.domain, storage, u0)

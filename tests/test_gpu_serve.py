@@ -68,3 +68,35 @@ def test_request_larger_than_budget_is_refused(S):
     reqs = stream(7, 2, rate_hz=10.0)
     with pytest.raises(ValueError):
         S.serve_batched(reqs, budget_bytes=1024)
+
+
+class StepClock:
+    """A clock that advances one second at every reading: the server's
+    timeline (arrivals, chunk boundaries, withdrawals) becomes deterministic."""
+
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1.0
+        return self.t
+
+
+def test_withdrawn_requests_leave_queue_and_batch(S):
+    """A request withdrawn before admission never runs; one withdrawn while
+    in the batch leaves it at the next chunk boundary and gives its memory
+    back; the others end with the same bits as alone."""
+    reqs = stream(8, 6, rate_hz=10.0, steps_lo=150, steps_hi=200)
+    for r in reqs:
+        r.arrival = 0.0
+    reqs[1].cancel_at = 0.0      # withdrawn while waiting
+    reqs[3].cancel_at = 3.5      # admitted at t = 1, withdrawn after its first chunk
+    rep = S.serve_batched(reqs, budget_bytes=8 << 30, max_chunk=20, clock=StepClock())
+    assert sorted(rep.cancelled) == [1, 3]
+    assert [r.rid for r in rep.results] == [0, 2, 4, 5]
+    assert rep.max_active == 5
+    for r in rep.results:
+        ux, uy = alone(S, reqs[r.rid])
+        assert np.array_equal(r.ux, ux) and np.array_equal(r.uy, uy), r.rid
+    base = S.serve_one_at_a_time(reqs, clock=StepClock())
+    assert 1 in base.cancelled and len(base.results) + len(base.cancelled) == 6
