@@ -465,3 +465,23 @@ def test_caller_block_too_small_or_misaligned(L):
     assert int(block.sum()) == 0                      # nothing written
     h = L.lbps_create(p, nt, bv, block.data_ptr(), need)
     L._lib.lbps_destroy(h)
+
+
+@pytest.mark.parametrize("size", [(3, 3), (4, 5), (7, 3)])
+@pytest.mark.parametrize("edges", range(16))
+def test_tiny_every_boundary_mix(L, size, edges):
+    """Every Dirichlet/Neumann combination of the four edges (with the corner
+    rule where a Dirichlet and a Neumann edge meet) on tiny lattices, from a
+    random state, FP64 and FP32 against the oracle."""
+    nx, ny = size
+    et = tuple(1 + ((edges >> q) & 1) for q in range(4))
+    rng = np.random.default_rng(1000 + 16 * nx + edges)
+    ev = rng.uniform(-2e-4, 2e-4, 8)
+    ux, uy = rng.uniform(-1e-4, 1e-4, (2, ny, nx))
+    nt, bv = O.rect_bc(nx, ny, et, ev)
+    ref = O.OracleLattice(nx, ny, 1.3, 1.0, a0_phi=0.9, node_type=nt, bc_value=bv).init(ux, uy).step(40).fields()
+    for storage in ("f64", "f32"):
+        lat = L.Lattice.rectangle(nx, ny, 1.3, 1.0, et, ev, a0_phi=0.9, storage=storage)
+        got = lat.init(ux, uy).step(40).fields()
+        lat.close()
+        assert_parity(got, ref, TOL[storage], (size, et, storage))
