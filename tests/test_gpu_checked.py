@@ -1,0 +1,68 @@
+"""The range-checked build (the stand-in for a memory sanitizer): every device
+access of the time-loop kernels is checked against the lattice's device block
+and for alignment, and the first violation is recorded instead of performed.
+A child process builds it, runs single-lattice cases through it (the check
+range is that of the last lattice created) and reads the record: no access may
+fall outside."""
+import os
+import subprocess
+import sys
+from pathlib import Path
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+ROOT = Path(__file__).resolve().parents[1]
+
+CHILD = r"""
+import os, sys
+sys.path.insert(0, ROOT); sys.path.insert(0, os.path.join(ROOT, "tests"))
+from paper_2301_00228_gb300 import build
+build.build(checked=True)
+os.environ["LBPS_CHECKED"] = "1"
+import numpy as np
+from paper_2301_00228_gb300 import lbps as L
+from paper_2301_00228_gb300 import workloads as W
+import test_gpu_fuzz as F
+
+runs = 0
+for seed in range(12):                       # random sizes, holes, periodic axes, storages, sync, ramps
+    c = F.make_case(seed)
+    lat = L.Lattice(c["nx"], c["ny"], c["lam"], c["mu"], c["rho"], a0_phi=c["a0"], periodic_x=c["px"],
+                    periodic_y=c["py"], node_type=c["nt"], bc_value=c["bv"], bc_feq_mode=c["mode"],
+                    sync_every=c["sync"], cell=c["cell"], storage=c["storage"])
+    if c["ramp"]:
+        lat.set_load(L.LBPS_NEUMANN, 30 * lat.dt, 60 * lat.dt)
+    lat.init(c["ux"], c["uy"]).step(40)
+    lat.fields()
+    lat.close()
+    runs += 1
+n = 40                                        # hole plate: every launch shape, row chunks inside the hole
+d, nt, bv, cell = W.hole_square(n, a0_phi=0.999, horizon=0.05, sync_every=0)
+for variant in range(8):
+    lat = L.Lattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=nt, bc_value=bv, cell=cell, storage="f32")
+    L.lbps_set_tuning(lat._h, variant, 8)
+    lat.init(*W.pulse_displacement(n, n, 12.0, 12.0, 3.0, 1e-3, "dilatation")).step(30)
+    bad = np.zeros((n, n)); bad[3, 3] = np.nan
+    try:
+        lat.init(bad, bad)                    # rejected input (device check in the idle copy)
+    except L.LbpsError:
+        pass
+    lat.step(5).close()
+    runs += 1
+rc, line, addr = L.lbps_check_report()
+print("REPORT", rc, line, addr, runs)
+"""
+
+
+def test_checked_build_records_no_violation():
+    env = dict(os.environ)
+    env.pop("LBPS_CHECKED", None)
+    out = subprocess.run([sys.executable, "-c", f"ROOT = {str(ROOT)!r}\n" + CHILD], capture_output=True, text=True,
+                         timeout=1200, env=env, cwd=str(ROOT))
+    report = [ln for ln in out.stdout.splitlines() if ln.startswith("REPORT")]
+    assert out.returncode == 0 and report, out.stdout[-2000:] + out.stderr[-3000:]
+    rc, line, addr, runs = (int(x) for x in report[-1].split()[1:])
+    assert rc == 1, "the checked build was not loaded"
+    assert (line, addr) == (0, 0), f"first violation at source line {line}, address {addr:#x}"
+    assert runs == 20
