@@ -39,7 +39,8 @@ extern "C" {
 #define LBPS_ERR_OOM (-2)       /* device allocation failed / block too small */
 #define LBPS_ERR_CUDA (-3)      /* a CUDA runtime call or launch failed       */
 #define LBPS_ERR_NONFINITE (-4) /* the state became non-finite (instability)  */
-#define LBPS_ERR_TIMEOUT (-5)   /* a bounded device wait gave up              */
+#define LBPS_ERR_TIMEOUT (-5)   /* reserved: no kernel waits on the device, so
+                                   no call returns it                        */
 #define LBPS_ERR_STATE (-6)     /* call out of order (e.g. step before init)  */
 
 /* Node types of the boundary mask (Sec. 2, Fig. 1). */
@@ -57,8 +58,8 @@ extern "C" {
  * with random bits hashed from the value and its position (deterministic, so
  * results do not depend on launch shape, batching or resumes), otherwise to
  * nearest; arithmetic is FP32.  32 bytes per point per state copy instead of
- * 40 (FP32).  They reject lattices 3 points wide along a
- * non-periodic axis (LBPS_ERR_INVALID). */
+ * 40 (FP32).  They reject lattices 3 points wide along a non-periodic axis
+ * (LBPS_ERR_INVALID). */
 #define LBPS_STORAGE_F32 0      /* FP32 populations, FP32 arithmetic          */
 #define LBPS_STORAGE_F64 1      /* FP64 populations, FP64 arithmetic          */
 #define LBPS_STORAGE_BF16 2     /* FP32 moments + bfloat16 Nx, Ny             */
@@ -118,7 +119,8 @@ int lbps_rect_bc(int32_t nx, int32_t ny, int32_t periodic_x, int32_t periodic_y,
                  uint8_t* node_type, double* bc_value);
 
 /* Device bytes that lbps_create needs for this lattice (two state copies,
- * boundary tables and reduction scratch). */
+ * each with its boundary mirror and boundary-cell stresses, the boundary
+ * table and reduction scratch). */
 int lbps_state_bytes(const lbps_params* params, size_t* bytes);
 
 /* Build the lattice (Fig. 3, preprocessing).
@@ -184,7 +186,7 @@ int lbps_step(lbps_lattice* lat, int64_t n);
 int lbps_step_async(lbps_lattice* lat, int64_t n);
 
 /* Waits for the stream; LBPS_ERR_NONFINITE if the state went non-finite
- * since creation. */
+ * since the last initialisation. */
 int lbps_check(lbps_lattice* lat);
 
 /* Periodic synchronisation of Sec. 3.2 applied now to the current state. */
