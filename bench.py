@@ -175,15 +175,31 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """sha256 (first 16 hex digits) of the kernel sources' code: the two files
-    with // comments and blank lines removed, so editing a comment keeps the
-    recorded ncu traffic valid and editing code does not."""
+    """sha256 (first 16 hex digits) of the code the normal build compiles
+    from the kernel sources: the two files without // comments, blank lines
+    and the branches only the range-checked build compiles (#ifdef
+    LBPS_CHECKED), so editing a comment or the checked build keeps the
+    recorded ncu traffic valid and editing the normal build's code does not."""
     code = []
     for name in ("lbps_kernels.cu", "lbps_device.cuh"):
         text = (ROOT / "paper_2301_00228_gb300" / "csrc" / name).read_text()
+        stack = []  # per open #if: True while its lines belong to the checked build only
         for line in text.splitlines():
             line = re.sub(r"//.*", "", line).rstrip()
-            if line.strip():
+            d = line.strip()
+            if d.startswith("#if"):
+                stack.append(d == "#ifdef LBPS_CHECKED")
+                if stack[-1]:
+                    continue
+            elif d.startswith("#else") and stack:
+                was = stack[-1]
+                stack[-1] = False
+                if was:
+                    continue
+            elif d.startswith("#endif") and stack:
+                if stack.pop():
+                    continue
+            if d and not any(stack):
                 code.append(line)
     return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 

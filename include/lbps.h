@@ -320,11 +320,12 @@ int lbps_scale_exp(const lbps_lattice* lat, int32_t* exp);
 int lbps_last_cuda_error(const lbps_lattice* lat);
 
 /* Diagnostics of a checked build (compiled with LBPS_CHECKED): every device
- * access of the time-loop kernels is checked against the lattice's device
- * block and for alignment, and the first violation is recorded instead of
- * performed.  Returns 1 and out[0] = source line, out[1] = address of that
- * first violation (0, 0 if none) in a checked build; returns 0 and zeros in
- * a normal build.  Waits for the device. */
+ * access of the time-loop kernels is checked for alignment and against the
+ * device blocks of the live lattices (at most 1024), and the first violation
+ * since the library was loaded is recorded instead of performed.  Returns 1
+ * and out[0] = source line, out[1] = address of that first violation (0, 0
+ * if none) in a checked build; returns 0 and zeros in a normal build.  Waits
+ * for the device. */
 int lbps_check_report(uint64_t out[2]);
 
 /* Launch shape of the interior kernel (performance only; results are

@@ -974,6 +974,7 @@ int lbps_set_stream(lbps_lattice* lat, void* cuda_stream) {
 
 void lbps_destroy(lbps_lattice* lat) {
     if (!lat) return;
+    if (lat->mem) lbps::set_check_range(lat->mem, 0, lat->st);  // checked builds: the block is no longer live
     if (lat->owns && lat->mem) {
         cudaStreamSynchronize(lat->st);
         cudaFree(lat->mem);

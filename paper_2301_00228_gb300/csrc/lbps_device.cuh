@@ -11,19 +11,26 @@
 namespace lbps {
 
 // Global-memory accessors of the kernels.  In a build with LBPS_CHECKED
-// defined, every access is checked against the lattice's device block and
-// for alignment; the first violation is recorded (source line and address)
-// and the access is skipped, so a bad index shows up as a report instead of
-// a fault.  Without LBPS_CHECKED they are plain loads and stores.
+// defined, every access is checked for alignment and against the device
+// blocks of the live lattices (a table of at most kChkRanges); the first
+// violation since the library was loaded is recorded (source line and
+// address) and the access is skipped, so a bad index shows up as a report
+// instead of a fault.  Without LBPS_CHECKED they are plain loads and stores.
 #ifdef LBPS_CHECKED
-__device__ const char* g_chk_lo;
-__device__ const char* g_chk_hi;
+constexpr int kChkRanges = 1024;
+__device__ const char* g_chk_lo[kChkRanges];
+__device__ const char* g_chk_hi[kChkRanges];
+__device__ int g_chk_n;
 __device__ unsigned long long g_chk_line;
 __device__ unsigned long long g_chk_addr;
 template <typename P>
 __device__ __forceinline__ bool chk_ok(const P* p, int line) {
     const char* c = reinterpret_cast<const char*>(p);
-    bool ok = c >= g_chk_lo && c + sizeof(P) <= g_chk_hi && (reinterpret_cast<uintptr_t>(c) % sizeof(P)) == 0;
+    bool ok = (reinterpret_cast<uintptr_t>(c) % sizeof(P)) == 0;
+    if (ok) {
+        ok = false;
+        for (int q = 0; q < g_chk_n && !ok; ++q) ok = c >= g_chk_lo[q] && c + sizeof(P) <= g_chk_hi[q];
+    }
     if (!ok && atomicCAS(&g_chk_line, 0ull, (unsigned long long)line) == 0ull)
         g_chk_addr = reinterpret_cast<unsigned long long>(c);
     return ok;

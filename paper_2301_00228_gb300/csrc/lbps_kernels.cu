@@ -20,6 +20,11 @@
 // FP64 planes, or FP32 moments (f^0, J) with the non-equilibrium pair sums in
 // 16 bits.
 #include "lbps_launch.h"
+#ifdef LBPS_CHECKED
+#include <algorithm>
+#include <utility>
+#include <vector>
+#endif
 
 namespace lbps {
 
@@ -844,14 +849,25 @@ cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int n
 
 cudaError_t set_check_range(const void* base, size_t bytes, cudaStream_t st) {
 #ifdef LBPS_CHECKED
+    // the table of live blocks, mirrored on the host and uploaded whole
+    static std::vector<std::pair<const char*, const char*>> ranges;
     const char* lo = static_cast<const char*>(base);
-    const char* hi = lo + bytes;
-    unsigned long long zero = 0;
-    cudaError_t e = cudaMemcpyToSymbolAsync(g_chk_lo, &lo, sizeof(lo), 0, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_chk_hi, &hi, sizeof(hi), 0, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_chk_line, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(g_chk_addr, &zero, sizeof(zero), 0, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    ranges.erase(std::remove_if(ranges.begin(), ranges.end(), [&](const auto& r) { return r.first == lo; }),
+                 ranges.end());
+    if (bytes > 0) {
+        if (ranges.size() >= (size_t)kChkRanges) return cudaErrorInvalidValue;
+        ranges.emplace_back(lo, lo + bytes);
+    }
+    std::vector<const char*> los, his;
+    for (const auto& r : ranges) {
+        los.push_back(r.first);
+        his.push_back(r.second);
+    }
+    const int n = (int)ranges.size();
+    cudaError_t e = cudaStreamSynchronize(st);  // no kernel in flight sees a half-written table
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyToSymbol(g_chk_lo, los.data(), n * sizeof(const char*));
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyToSymbol(g_chk_hi, his.data(), n * sizeof(const char*));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_chk_n, &n, sizeof(n));
     return e;
 #else
     (void)base;

@@ -108,9 +108,11 @@ template <typename P>
 cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
                               unsigned* next, cudaStream_t st);
 
-// Checked builds (LBPS_CHECKED): the device block every kernel access must
-// stay inside, and the first violation seen (source line, address); both are
-// no-ops returning 0 in normal builds.
+// Checked builds (LBPS_CHECKED): set_check_range adds a live lattice block
+// that kernel accesses may touch (bytes = 0 removes the block starting at
+// base); check_report returns the first violation since the library was
+// loaded (source line, address).  Both are no-ops returning 0 in normal
+// builds.
 cudaError_t set_check_range(const void* base, size_t bytes, cudaStream_t st);
 int check_report(unsigned long long out[2]);
 

@@ -1,9 +1,9 @@
 """The range-checked build (the stand-in for a memory sanitizer): every device
-access of the time-loop kernels is checked against the lattice's device block
-and for alignment, and the first violation is recorded instead of performed.
-A child process builds it, runs single-lattice cases through it (the check
-range is that of the last lattice created) and reads the record: no access may
-fall outside."""
+access of the time-loop kernels is checked for alignment and against the
+device blocks of the live lattices, and the first violation is recorded
+instead of performed.  A child process builds it, runs random single-lattice
+cases, hole plates under every launch shape and a batch of uneven lattices
+through it, and reads the record: no access may fall outside."""
 import os
 import subprocess
 import sys
@@ -50,6 +50,21 @@ for variant in range(8):
         pass
     lat.step(5).close()
     runs += 1
+lats = []                                     # a batch of uneven rectangles and hole plates
+for dom in W.mixed_batch(count=10)[::2]:
+    lats.append(L.Lattice.rectangle(dom.nx, dom.ny, dom.lam, dom.mu, dom.edge_type,
+                                    np.asarray(dom.edge_value, float).ravel(), a0_phi=dom.a0_phi)
+                .init(*dom.displacement()))
+for m in (40, 52):
+    dd, nt2, bv2, cell2 = W.hole_square(m, a0_phi=0.999, horizon=0.05, sync_every=0)
+    lats.append(L.Lattice(m, m, dd.lam, dd.mu, a0_phi=dd.a0_phi, node_type=nt2, bc_value=bv2, cell=cell2)
+                .init(*W.pulse_displacement(m, m, 10.0, 10.0, 3.0, 1e-3, "rotation")))
+b = L.Batch(lats)
+b.tune(repeats=1)
+b.step(25)
+assert b.check() == 0
+b.close()
+runs += 1
 rc, line, addr = L.lbps_check_report()
 print("REPORT", rc, line, addr, runs)
 """
@@ -65,4 +80,4 @@ def test_checked_build_records_no_violation():
     rc, line, addr, runs = (int(x) for x in report[-1].split()[1:])
     assert rc == 1, "the checked build was not loaded"
     assert (line, addr) == (0, 0), f"first violation at source line {line}, address {addr:#x}"
-    assert runs == 20
+    assert runs == 21
