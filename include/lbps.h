@@ -338,11 +338,14 @@ int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);
 
 /* Per-kernel timing for roofline reports.  enable != 0 starts recording CUDA
  * events on the lattice's stream around the interior kernel of every step
- * and around each boundary pass (Newmark before it, reset after it); 0 stops.  lbps_profile_read waits for the stream and
- * returns, since recording started: out[0] total milliseconds in the bulk
- * (interior) kernel, out[1] its launches, out[2] total milliseconds in the
- * boundary passes, out[3] the number of timed boundary groups (two per
- * step); then clears the record. */
+ * and around the boundary reset after it (the boundary Newmark pass runs on
+ * a second stream beside the interior kernel and is not timed); 0 stops.
+ * lbps_profile_read waits for the stream and returns, since recording
+ * started: out[0] total milliseconds in the bulk (interior) kernel, out[1]
+ * its launches, out[2] total milliseconds in the timed boundary passes,
+ * out[3] their number (one per step; two if the second stream could not be
+ * created, the Newmark pass then running, timed, on the lattice's stream);
+ * then clears the record. */
 int lbps_profile(lbps_lattice* lat, int32_t enable);
 int lbps_profile_read(lbps_lattice* lat, double out[4]);
 

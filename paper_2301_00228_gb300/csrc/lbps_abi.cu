@@ -282,39 +282,59 @@ cudaEvent_t next_event(lbps_lattice* lat) {
     return lat->ev_pool[lat->ev_used++];
 }
 
-// Records an event on the stream when profiling; the pair (start, end) of a
-// kernel is two consecutive pool entries.
-cudaError_t prof_mark(lbps_lattice* lat) {
+// Records an event on a stream (default: the lattice's) when profiling; the
+// pair (start, end) of a kernel is two consecutive pool entries.
+cudaError_t prof_mark(lbps_lattice* lat, cudaStream_t st = nullptr) {
     if (!lat->prof) return cudaSuccess;
     cudaEvent_t e = next_event(lat);
     if (!e) return cudaErrorMemoryAllocation;
-    return cudaEventRecord(e, lat->st);
+    return cudaEventRecord(e, st ? st : lat->st);
 }
 
 // Boundary passes [pass_lo, pass_hi) of one step (1 Newmark, 2 reset; 0, the
-// stresses of copy a, only after the initialisation).
-cudaError_t boundary_passes(lbps_lattice* lat, int a, int b, int pass_lo, int pass_hi) {
+// stresses of copy a, only after the initialisation), on stream st (default:
+// the lattice's).  timed = false leaves them out of lbps_profile (a pass
+// beside the interior kernel waits for free SMs, so events around it would
+// not measure it).
+cudaError_t boundary_passes(lbps_lattice* lat, int a, int b, int pass_lo, int pass_hi,
+                            cudaStream_t st = nullptr, bool timed = true) {
     if (lat->L.nb == 0) return cudaSuccess;
-    cudaError_t e = prof_mark(lat);
+    if (!st) st = lat->st;
+    const bool prof = lat->prof;
+    lat->prof = prof && timed;
+    cudaError_t e = prof_mark(lat, st);
     if (e == cudaSuccess)
         e = lbps::with_policy(lat->p.storage, [&](auto pol) {
             using P = decltype(pol);
             return lbps::launch_boundary<P>(lat->L.g, lat->c, lat->kc<P>(), lat->view<P>(a), lat->view<P>(b),
-                                            lat->bn(), lat->L.nb, lat->flag(), lat->tstep(), lat->st,
-                                            pass_lo, pass_hi);
+                                            lat->bn(), lat->L.nb, lat->flag(), lat->tstep(), st, pass_lo,
+                                            pass_hi);
         });
-    if (e == cudaSuccess) e = prof_mark(lat);
+    if (e == cudaSuccess) e = prof_mark(lat, st);
     if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(1);
+    lat->prof = prof;
     return e;
 }
 
 // One time step: the boundary Newmark pass, the interior kernel, then the
 // boundary reset (which reads the interior kernel's new u, overwrites the
 // populations streamed from boundary points and leaves the stresses of the
-// new u for the next step).
+// new u for the next step).  The Newmark pass runs on the side stream beside
+// the interior kernel: it reads copy A and writes only the boundary points'
+// u, du/dt of copy B, which the interior kernel does not touch; the reset
+// waits for both.
 int run_step(lbps_lattice* lat) {
     int a = lat->cur, b = lat->cur ^ 1;
-    cudaError_t e = boundary_passes(lat, a, b, 1, 2);
+    const bool overlap = lat->side && lat->L.nb > 0;
+    cudaError_t e = cudaSuccess;
+    if (overlap) {
+        e = cudaEventRecord(lat->fork, lat->st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(lat->side, lat->fork, 0);
+        if (e == cudaSuccess) e = boundary_passes(lat, a, b, 1, 2, lat->side, false);
+        if (e == cudaSuccess) e = cudaEventRecord(lat->join, lat->side);
+    } else {
+        e = boundary_passes(lat, a, b, 1, 2);
+    }
     if (e == cudaSuccess) e = prof_mark(lat);
     if (e == cudaSuccess)
         e = lbps::with_policy(lat->p.storage, [&](auto pol) {
@@ -324,6 +344,7 @@ int run_step(lbps_lattice* lat) {
         });
     if (e == cudaSuccess) e = prof_mark(lat);
     if (e == cudaSuccess && lat->prof) lat->ev_kind.push_back(0);
+    if (e == cudaSuccess && overlap) e = cudaStreamWaitEvent(lat->st, lat->join, 0);
     if (e == cudaSuccess) e = boundary_passes(lat, a, b, 2, 3);
     if (e != cudaSuccess) {
         lat->last_cuda = (int)e;
@@ -641,6 +662,18 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
     lat->cur = 0;
     lat->steps = 0;
     lat->initialised = false;
+    // the side stream of the boundary Newmark pass; if it cannot be had, the
+    // pass runs on the lattice's stream (same results, no overlap)
+    if (cudaStreamCreateWithFlags(&lat->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&lat->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&lat->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (lat->side) cudaStreamDestroy(lat->side);
+        if (lat->fork) cudaEventDestroy(lat->fork);
+        if (lat->join) cudaEventDestroy(lat->join);
+        lat->side = nullptr;
+        lat->fork = lat->join = nullptr;
+    }
     if (L.g.general) {
         lat->L.g.type = reinterpret_cast<const uint8_t*>(lat->mem + L.off_type);
         lat->L.g.gap = reinterpret_cast<const int*>(lat->mem + L.off_gap);
@@ -974,6 +1007,12 @@ int lbps_set_stream(lbps_lattice* lat, void* cuda_stream) {
 
 void lbps_destroy(lbps_lattice* lat) {
     if (!lat) return;
+    if (lat->side) {
+        cudaStreamSynchronize(lat->side);
+        cudaStreamDestroy(lat->side);
+    }
+    if (lat->fork) cudaEventDestroy(lat->fork);
+    if (lat->join) cudaEventDestroy(lat->join);
     if (lat->mem) lbps::set_check_range(lat->mem, 0, lat->st);  // checked builds: the block is no longer live
     if (lat->owns && lat->mem) {
         cudaStreamSynchronize(lat->st);

@@ -62,6 +62,10 @@ struct lbps_lattice {
     int64_t gen = 0;      // incremented by every init (batches re-read descriptors)
     std::vector<int> gap; // general geometry: rows without interior points per strip (Geo::gap, host copy)
     cudaStream_t st;
+    // second stream for the boundary Newmark pass beside the interior kernel,
+    // ordered by the fork/join events (null: the pass runs on st)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
     char* mem;
     bool owns;
     int cur;            // copy holding time t
