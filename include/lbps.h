@@ -333,7 +333,8 @@ int lbps_check_report(uint64_t out[2]);
  * (0: 6 blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8) with u, du/dt loaded
  * two rows ahead; 4..7 the same budgets loading them one row ahead.
  * rows_per_warp (1..4096) is the number of rows each warp marches over.
- * Defaults: 0, 32. */
+ * Defaults: variant 0; 32 rows, or 16 or 8 on lattices too small to give the
+ * interior kernel 16384 warps at 32 (below about 4096^2). */
 int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);
 
 /* Per-kernel timing for roofline reports.  enable != 0 starts recording CUDA

@@ -662,6 +662,18 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
     lat->cur = 0;
     lat->steps = 0;
     lat->initialised = false;
+    // default strip height: 32 rows, or 16 / 8 where the lattice is too small
+    // to give the interior kernel about 16 K warps (4-5 resident waves) at 32
+    {
+        const long long strips = (params->nx + lbps::kBatchStripCols - 1) / lbps::kBatchStripCols;
+        int rows = 8;
+        for (int r : {32, 16})
+            if (strips * ((params->ny + r - 1) / r) >= 16384) {
+                rows = r;
+                break;
+            }
+        lat->tuning.rows_per_warp = rows;
+    }
     // the side stream of the boundary Newmark pass; if it cannot be had, the
     // pass runs on the lattice's stream (same results, no overlap)
     if (cudaStreamCreateWithFlags(&lat->side, cudaStreamNonBlocking) != cudaSuccess ||
