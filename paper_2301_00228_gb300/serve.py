@@ -10,7 +10,8 @@ times and serves them as they arrive:
 * batching: all admitted solves advance together as one ``Batch`` (one launch
   of each kernel per time step for all of them, CUDA graphs for step pairs),
   in chunks no longer than the shortest remaining solve, so every solve stops
-  exactly at its step count;
+  exactly at its step count; a solve that is alone on the device is stepped
+  directly (lbps_step, the single-lattice kernels and their launch shape);
 * completion: finished solves are read out (their u fields) and freed, and
   the batch is rebuilt with the waiting requests that now fit;
 * cancellation: a request withdrawn by its client (``cancel_at``) leaves the
@@ -163,22 +164,28 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
         if members != batch_members:
             if batch is not None:
                 batch.close()
-            batch = lbps.Batch([a[1] for a in active])
-            if tuning is not None:
-                batch.set_tuning(*tuning)
+                batch = None
+            if len(active) > 1:
+                batch = lbps.Batch([a[1] for a in active])
+                if tuning is not None:
+                    batch.set_tuning(*tuning)
+                rep.rebuilds += 1
             batch_members = members
-            rep.rebuilds += 1
         k = min(max_chunk, min(a[2] for a in active))
-        batch.step(k)
-        rc = batch.check()  # waits for the chunk
+        if batch is not None:
+            batch.step(k)
+            rc = batch.check()  # waits for the chunk
+        else:  # alone on the device: the single-lattice path
+            rc = lbps.lbps_step(active[0][1]._h, k)
         if rc != lbps.LBPS_OK:
-            raise lbps.LbpsError(rc, "serve: batch check")
+            raise lbps.LbpsError(rc, "serve: chunk check")
         rep.chunks += 1
         done = [a for a in active if a[2] == k]
         for a in active:
             a[2] -= k
         if done:
-            batch.close()
+            if batch is not None:
+                batch.close()
             batch, batch_members = None, ()
             for r, lat, _, admitted in done:
                 res = Result(r.rid, r.arrival, admitted, 0.0)
