@@ -365,6 +365,10 @@ def run_batch(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:  # each rank advances its own copy of the batch (weak scaling)
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2301_00228_gb300 import lbps
     from paper_2301_00228_gb300 import workloads as W
 
@@ -390,16 +394,22 @@ def run_batch(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     b.step(args.steps)
     e1.record(stream)
     e1.synchronize()
+    if dist is not None:
+        dist.barrier()
     clock = clocks.stop()
     if b.check() != 0:
         raise SystemExit("state became non-finite")
-    seconds = e0.elapsed_time(e1) / 1000.0
-    value = points * args.steps / seconds / 1e9
+    rmax, rsum = reducers(dist, "cuda")
+    seconds = rmax(e0.elapsed_time(e1) / 1000.0)          # slowest rank
+    value = rsum(points * args.steps) / seconds / 1e9      # points of all ranks
     # the same lattices stepped one at a time (same kernels, one lattice per launch)
     loop_steps = max(2, args.steps // 10)
     torch.cuda.synchronize()
@@ -441,6 +451,10 @@ def run_serve(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    dist = None
+    if world > 1:  # each rank serves its own copy of the stream (replicas)
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2301_00228_gb300 import serve as S
     from paper_2301_00228_gb300 import workloads as W
 
@@ -463,7 +477,10 @@ def run_serve(args):
                             max_chunk=args.max_chunk) if args.small_budget_gb > 0 else None
     loop = S.serve_one_at_a_time(reqs, prepared=prepared)
     sv, lp = served.summary(), loop.summary()
-    line = {"metric": "served solves/s", "value": sv["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+    rmax, rsum = reducers(dist, "cuda")
+    total = rsum(sv["solves_per_s"])               # solves/s of all replicas
+    sv["p99_latency_s_max_over_ranks"] = rmax(sv["p99_latency_s"])
+    line = {"metric": "served solves/s", "value": total, "unit": "solves/s", "n_gpus": world,
             "steps": len(reqs), "warmup": 1, "ms_per_step": 1000.0 * served.makespan / len(reqs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"serve_poisson_{len(reqs)}", "requests": len(reqs), "sides": "log-U 128..2048",
