@@ -91,3 +91,23 @@ def test_bench_calls_only_defined_functions():
             known.add(node.arg)
     called = {n.func.id for n in ast.walk(tree) if isinstance(n, ast.Call) and isinstance(n.func, ast.Name)}
     assert not called - known, sorted(called - known)
+
+
+@pytest.mark.parametrize("workload", ["pulses", "hole"])
+def test_reference_arm_line(workload, capsys, monkeypatch):
+    """The reference arm (the FP64 oracle on the host cores) prints one JSON
+    line with the base contract's keys, on a small lattice."""
+    import json
+
+    sys.path.insert(0, str(ROOT))
+    import bench
+
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    assert bench.main(["--impl", "reference", "--workload", workload, "--size", "96", "--steps", "2",
+                       "--warmup", "1", "--ref-seconds", "0.2"]) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GLUPS" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == f"{workload}_96"
