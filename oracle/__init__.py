@@ -9,8 +9,8 @@ module only marshals arrays through ctypes.
 
 Parity status of each function is recorded in ``PINS`` below: every part of
 the time loop is pinned by a test against a closed form, an invariant, a
-hand-computed lattice or brute force, except the two readings listed as
-"parity unpinned" (they are pinned oracle-to-CUDA only).
+hand-computed lattice or brute force, except what is listed in
+``PARITY_UNPINNED`` (pinned oracle-to-CUDA only).
 """
 from __future__ import annotations
 
@@ -44,10 +44,18 @@ PINS = {
     "general geometry: void points, clipped cells, one-sided stencils (reading R14)":
         "tests/test_oracle_pins.py::test_hole_*, ::test_explicit_rectangle_cells_equal_default, "
         "::test_geometry_rejected_without_stencil",
+    "cells of the plate with a hole, areas by Green's theorem (reading R16)":
+        "tests/test_oracle_cells.py (hand-derived cells in tests/golden/disk_cells.json, tiling of the body, "
+        "closure of every cell boundary, sampling, symmetry)",
+    "initial first moments from du/dt (reading R9)":
+        "tests/test_oracle_pins.py::test_travelling_wave_from_initial_velocity (discrete travelling wave)",
+    "J of Eq. correction-f, both readings (R7, R15)":
+        "tests/test_oracle_pins.py::test_bc_j_mode_* (mode 1 against its definition; patch tests)",
 }
 # Readings with no pin against the paper itself.
 PARITY_UNPINNED = (
-    "initial first moments from du/dt (reading R9): no paper value; pinned oracle-to-CUDA only",
+    "J of Eq. correction-f with bc_j_mode 1 (reading R15): an alternative reading of the paper's J(x_k, t); "
+    "pinned to its own definition and oracle-to-CUDA only",
     "consistency-error magnitude of Fig. 9 (4.3e-12): lattice resolution not given",
 )
 
@@ -71,7 +79,8 @@ class _Params(ctypes.Structure):
                 ("lam", ctypes.c_double), ("mu", ctypes.c_double), ("rho", ctypes.c_double),
                 ("dh", ctypes.c_double), ("a0_phi", ctypes.c_double),
                 ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
-                ("bc_feq_mode", ctypes.c_int32), ("sync_every", ctypes.c_int32)]
+                ("bc_feq_mode", ctypes.c_int32), ("sync_every", ctypes.c_int32),
+                ("bc_j_mode", ctypes.c_int32)]
 
 
 _lib = None
@@ -98,6 +107,9 @@ def lib():
         L.ora_steps_done.argtypes = [vp]
         L.ora_rect_bc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_double, vp, vp, vp, vp]
+        L.ora_disk_cells.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, vp, vp, vp, vp, vp]
+        L.ora_clip_rect.argtypes = [ctypes.c_double] * 7 + [vp]
         L.ora_set_threads.argtypes = [ctypes.c_int32]
         L.ora_get_threads.restype = ctypes.c_int32
         _lib = L
@@ -125,14 +137,39 @@ def rect_bc(nx, ny, edge_type, edge_value, periodic_x=False, periodic_y=False, d
     return nt, bv
 
 
+def disk_cells(nx, ny, cx, cy, r, edge_type, edge_value, dh=1.0):
+    """Node types, boundary values and cells of an nx x ny rectangle of lattice
+    points with a traction-free circular hole of centre (cx, cy) and radius r
+    (lengths in the units of dh; reading R16, areas by Green's theorem)."""
+    et = np.ascontiguousarray(edge_type, dtype=np.int32).reshape(4)
+    ev = np.ascontiguousarray(edge_value, dtype=np.float64).reshape(8)
+    nt = np.zeros((ny, nx), np.uint8)
+    bv = np.zeros((ny, nx, 2), np.float64)
+    cell = np.zeros((ny, nx, 5), np.float64)
+    rc = lib().ora_disk_cells(int(nx), int(ny), float(dh), float(cx), float(cy), float(r), _ptr(et), _ptr(ev),
+                              _ptr(nt), _ptr(bv), _ptr(cell))
+    if rc != 0:
+        raise ValueError("invalid plate-with-hole description")
+    return nt, bv, cell
+
+
+def clip_rect(x0, x1, y0, y1, cx, cy, r):
+    """(area, lengths of the sides x = x1, y = y1, x = x0, y = y0) of the part of
+    the rectangle [x0, x1] x [y0, y1] outside the open disk."""
+    out = np.zeros(5, np.float64)
+    lib().ora_clip_rect(float(x0), float(x1), float(y0), float(y1), float(cx), float(cy), float(r), _ptr(out))
+    return float(out[0]), out[1:].copy()
+
+
 class OracleLattice:
     """One lattice of the FP64 oracle."""
 
     def __init__(self, nx, ny, lam, mu, rho=1.0, dh=1.0, a0_phi=0.9999, periodic_x=False,
-                 periodic_y=False, node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0, cell=None):
+                 periodic_y=False, node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0, cell=None,
+                 bc_j_mode=0):
         self.nx, self.ny = int(nx), int(ny)
         p = _Params(self.nx, self.ny, lam, mu, rho, dh, a0_phi, int(periodic_x), int(periodic_y),
-                    int(bc_feq_mode), int(sync_every))
+                    int(bc_feq_mode), int(sync_every), int(bc_j_mode))
         if node_type is None:
             node_type = np.zeros((ny, nx), np.uint8)
         self._nt = np.ascontiguousarray(node_type, dtype=np.uint8)

@@ -43,7 +43,8 @@
  *   R9  With du/dt(x,0) given, the first moments start at J_phi = -v and
  *       J_psi = (-v_y, v_x), from d(phi)/dt = -div J_phi (the zeroth-moment
  *       balance of the LBE) and d(phi)/dt = div v.  All inputs at rest give
- *       J = 0.
+ *       J = 0.  (A discrete travelling plane wave started this way stays a
+ *       pure travelling wave; the tests pin it so.)
  *   R10 tau = dt/2 in both Eq. LBE and Eq. LBE_mod (so dt/tau = 1/tau = 2).
  *   R11 The Newmark update is used as printed: beta = 0 and gamma = 0 (the
  *       velocity takes the acceleration at t only).  It is first order, and
@@ -73,6 +74,19 @@
  *       (like the stresses, Eq. acc_neumann); the Dirichlet target is
  *       u*(t + dt), the displacement the point must have after the step
  *       (Eq. acc_dirichlet lands u(t + dt) on it).
+ *   R15 Eq. correction-f takes J(x_k, t) without saying which populations it
+ *       is the moment of.  bc_j_mode 0 (default, R7): those stored at x_k.
+ *       bc_j_mode 1: Sec. 3.1.2 says boundary points "can only partially be
+ *       updated via the LBE"; J is then the first moment of that partial
+ *       update, the populations the plain LBE (Eq. LBE, from f(., t))
+ *       streams into x_k from its body neighbours, with f(x_k, t) kept for
+ *       the directions whose source lies outside the body.
+ *   R16 Cells of the plate with a circular hole (Sec. 4): the square of
+ *       side dh around a boundary point, clipped to the body rectangle,
+ *       minus the disk.  Its area and side lengths are computed here by
+ *       Green's theorem along the clipped boundary (ora_clip_rect); the
+ *       external faces on the outer edges carry the edge traction, the hole
+ *       is traction-free.
  */
 #include "lbm_oracle.h"
 
@@ -229,6 +243,7 @@ ora_lattice* ora_create_cells(const ora_params* p, const uint8_t* node_type, con
     if (!(p->mu > 0.0) || !(p->rho > 0.0) || !(p->lambda + 2.0 * p->mu > 0.0) || !(p->dh > 0.0)) return NULL;
     if (!(p->a0_phi >= 0.0 && p->a0_phi < 1.0)) return NULL;
     if (p->bc_feq_mode != 0 && p->bc_feq_mode != 1) return NULL;
+    if (p->bc_j_mode != 0 && p->bc_j_mode != 1) return NULL;
     if (p->sync_every < 0) return NULL;
     ora_lattice* L = (ora_lattice*)calloc(1, sizeof(ora_lattice));
     if (!L) return NULL;
@@ -521,6 +536,29 @@ static void synchronise(ora_lattice* L) {
         for (int a = 0; a < 5; ++a) swap_ptr(&L->f[set][a], &L->fn[set][a]);
 }
 
+/* Reading R15, bc_j_mode 1: the populations the plain LBE (Eq. LBE, tau =
+ * dt/2, from f(., t)) streams into the boundary point (i, j): direction alpha
+ * comes from the body neighbour at x - c^alpha dt after its collision; a
+ * direction whose source lies outside the body keeps f^alpha(x, t). */
+static void partial_stream(const ora_lattice* L, int set, int i, int j, double g[5]) {
+    long k = at(L, i, j);
+    double fk[5], s, jx, jy;
+    gather(L->f[set], k, fk);
+    moments(L, fk, &s, &jx, &jy);
+    g[0] = fk[0] - 2.0 * (fk[0] - f_eq(L, set, 0, s, jx, jy));  /* the point's own rest population */
+    for (int a = 1; a < 5; ++a) {
+        int si, sj;
+        if (!neighbour(L, i, j, -EX[a], -EY[a], &si, &sj)) {
+            g[a] = fk[a];
+            continue;
+        }
+        double fs[5], ss, sx, sy;
+        gather(L->f[set], at(L, si, sj), fs);
+        moments(L, fs, &ss, &sx, &sy);
+        g[a] = fs[a] - 2.0 * (fs[a] - f_eq(L, set, a, ss, sx, sy));
+    }
+}
+
 static void one_step(ora_lattice* L) {
     int nx = L->p.nx, ny = L->p.ny;
     double dt = L->dt;
@@ -555,7 +593,8 @@ static void one_step(ora_lattice* L) {
             snew[1] = fd_curl(L, L->ux1, L->uy1, i, j);
             for (int set = 0; set < 2; ++set) {
                 double g[5], s, jx, jy;
-                gather(L->f[set], k, g);
+                if (L->p.bc_j_mode == 1) partial_stream(L, set, i, j, g);
+                else gather(L->f[set], k, g);
                 moments(L, g, &s, &jx, &jy);
                 for (int a = 0; a < 5; ++a) L->fn[set][a][k] = f_eq(L, set, a, snew[set], jx, jy);
             }
@@ -727,6 +766,189 @@ int ora_rect_bc(int32_t nx, int32_t ny, int32_t periodic_x, int32_t periodic_y, 
                         bc_value[2 * k + 1] += edge_value[2 * e + 1] * len;
                     }
                 }
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------- plate with a circular hole */
+
+#define ORA_PI 3.14159265358979323846
+
+/* Contribution (x dy - y dx) / 2 of the straight segment p -> q to the area
+ * of the region on its left (Green's theorem). */
+static double green_segment(double px, double py, double qx, double qy) {
+    return 0.5 * (px * qy - py * qx);
+}
+
+/* The same for the arc of the circle of radius r from angle t1 down to t0
+ * (clockwise, t1 > t0), whose end points are p1 (at t1) and p0 (at t0): the
+ * chord p1 -> p0, less the circular segment between arc and chord, of area
+ * r^2 (dt - sin dt) / 2, which the clockwise arc leaves on its right. */
+static double green_arc_cw(double r, double t0, double t1, double p0x, double p0y, double p1x, double p1y) {
+    double dt = t1 - t0;
+    return green_segment(p1x, p1y, p0x, p0y) - 0.5 * r * r * (dt - sin(dt));
+}
+
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return (x > y) - (x < y);
+}
+
+/* Reading R16: the region A = S minus the open disk D, S = [x0, x1] x
+ * [y0, y1].  Its area is (1/2) times the integral of x dy - y dx around its
+ * boundary, which consists of the parts of the sides of S outside D,
+ * traversed counter-clockwise, and the arcs of the circle inside S,
+ * traversed clockwise (A lies outside the circle).  The pieces need not be
+ * joined into loops: the integral is a sum over them. */
+void ora_clip_rect(double x0, double x1, double y0, double y1, double cx, double cy, double r, double out[5]) {
+    /* coordinates relative to the rectangle's centre (the area does not
+     * depend on the origin, and small coordinates keep the sums exact) */
+    const double xm = 0.5 * (x0 + x1), ym = 0.5 * (y0 + y1);
+    x0 -= xm; x1 -= xm; cx -= xm;
+    y0 -= ym; y1 -= ym; cy -= ym;
+    /* sides in counter-clockwise order: S (y = y0), E (x = x1), N (y = y1),
+     * W (x = x0); out[] lists them E, N, W, S */
+    const double P[4][2] = {{x0, y0}, {x1, y0}, {x1, y1}, {x0, y1}};
+    const int slot[4] = {4, 1, 2, 3};
+    double area = 0.0;
+    for (int q = 1; q < 5; ++q) out[q] = 0.0;
+    for (int e = 0; e < 4; ++e) {
+        double ax = P[e][0], ay = P[e][1], bx = P[(e + 1) % 4][0], by = P[(e + 1) % 4][1];
+        double dx = bx - ax, dy = by - ay, len = sqrt(dx * dx + dy * dy);
+        if (!(len > 0.0)) continue;
+        /* |a + t (b - a) - c|^2 < r^2 for t in (t_in, t_out): a quadratic in t */
+        double ex = ax - cx, ey = ay - cy;
+        double qa = dx * dx + dy * dy, qb = 2.0 * (ex * dx + ey * dy), qc = ex * ex + ey * ey - r * r;
+        double disc = qb * qb - 4.0 * qa * qc;
+        double pieces[2][2];
+        int np = 0;
+        if (r > 0.0 && disc > 0.0) {
+            double sq = sqrt(disc);
+            double t_in = (-qb - sq) / (2.0 * qa), t_out = (-qb + sq) / (2.0 * qa);
+            if (t_in > 0.0) { pieces[np][0] = 0.0; pieces[np][1] = fmin(t_in, 1.0); ++np; }
+            if (t_out < 1.0) { pieces[np][0] = fmax(t_out, 0.0); pieces[np][1] = 1.0; ++np; }
+        } else {
+            pieces[0][0] = 0.0;
+            pieces[0][1] = 1.0;
+            np = 1;
+        }
+        for (int m = 0; m < np; ++m) {
+            double s0 = pieces[m][0], s1 = pieces[m][1];
+            if (!(s1 > s0)) continue;
+            area += green_segment(ax + s0 * dx, ay + s0 * dy, ax + s1 * dx, ay + s1 * dy);
+            out[slot[e]] += (s1 - s0) * len;
+        }
+    }
+    if (r > 0.0) {
+        /* angles where the circle crosses the four lines of the sides */
+        double th[9];
+        int n = 0;
+        const double lines_x[2] = {x0, x1}, lines_y[2] = {y0, y1};
+        for (int m = 0; m < 2; ++m) {
+            double u = (lines_x[m] - cx) / r;
+            if (fabs(u) < 1.0) {
+                double t = acos(u);
+                th[n++] = t;
+                th[n++] = 2.0 * ORA_PI - t;
+            }
+            double v = (lines_y[m] - cy) / r;
+            if (fabs(v) < 1.0) {
+                double t = asin(v);
+                th[n++] = t < 0.0 ? t + 2.0 * ORA_PI : t;
+                th[n++] = ORA_PI - t;
+            }
+        }
+        if (n == 0) {
+            /* no crossing: the whole circle lies inside S or outside it */
+            if (cx + r > x0 && cx + r < x1 && cy > y0 && cy < y1) area -= ORA_PI * r * r;
+        } else {
+            qsort(th, (size_t)n, sizeof(double), cmp_double);
+            th[n] = th[0] + 2.0 * ORA_PI;
+            for (int m = 0; m < n; ++m) {
+                double t0 = th[m], t1 = th[m + 1];
+                if (!(t1 > t0)) continue;
+                /* between two crossings the arc lies on one side of every
+                 * line; it may still touch a side where it is tangent to it,
+                 * so it counts as inside if any of three points along it lies
+                 * strictly inside */
+                int inside = 0;
+                for (int q = 1; q <= 3; ++q) {
+                    double tq = t0 + 0.25 * q * (t1 - t0);
+                    double mx = cx + r * cos(tq), my = cy + r * sin(tq);
+                    inside = inside || (mx > x0 && mx < x1 && my > y0 && my < y1);
+                }
+                if (inside)
+                    area += green_arc_cw(r, t0, t1, cx + r * cos(t0), cy + r * sin(t0), cx + r * cos(t1),
+                                         cy + r * sin(t1));
+            }
+        }
+    }
+    out[0] = area;
+}
+
+int ora_disk_cells(int32_t nx, int32_t ny, double dh, double cx, double cy, double r,
+                   const int32_t edge_type[4], const double edge_value[8],
+                   uint8_t* node_type, double* bc_value, double* cell) {
+    if (nx < 3 || ny < 3 || !(dh > 0.0) || !(r >= 0.0) || !isfinite(r) || !isfinite(cx) || !isfinite(cy))
+        return -1;
+    for (int e = 0; e < 4; ++e)
+        if (edge_type[e] != 1 && edge_type[e] != 2) return -1;
+    long n = (long)nx * ny;
+    double Lx = (nx - 1) * dh, Ly = (ny - 1) * dh, h2 = 0.5 * dh;
+    /* void points: strictly inside the circle */
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            double x = i * dh - cx, y = j * dh - cy;
+            node_type[(long)j * nx + i] = (x * x + y * y < r * r) ? 3 : 0;
+        }
+    for (long k = 0; k < 2 * n; ++k) bc_value[k] = 0.0;
+    for (long k = 0; k < 5 * n; ++k) cell[k] = 0.0;
+    const int DI[4] = {1, 0, -1, 0}, DJ[4] = {0, 1, 0, -1};
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            long k = (long)j * nx + i;
+            if (node_type[k] == 3) continue;
+            int bnd = 0;
+            for (int d = 0; d < 4; ++d) {
+                int ni = i + DI[d], nj = j + DJ[d];
+                if (ni < 0 || ni >= nx || nj < 0 || nj >= ny || node_type[(long)nj * nx + ni] == 3) bnd = 1;
+            }
+            if (!bnd) continue;
+            /* outer edges the point lies on: bottom, right, top, left */
+            int on[4] = {j == 0, i == nx - 1, j == ny - 1, i == 0};
+            int n_dir = 0;
+            for (int e = 0; e < 4; ++e) n_dir += on[e] && edge_type[e] == 2;
+            if (n_dir > 0) {
+                node_type[k] = 2;
+                for (int e = 0; e < 4; ++e)
+                    if (on[e] && edge_type[e] == 2) {
+                        bc_value[2 * k] += edge_value[2 * e] / n_dir;
+                        bc_value[2 * k + 1] += edge_value[2 * e + 1] / n_dir;
+                    }
+                continue;
+            }
+            node_type[k] = 1;
+            double x = i * dh, y = j * dh;
+            double sx0 = fmax(x - h2, 0.0), sx1 = fmin(x + h2, Lx);
+            double sy0 = fmax(y - h2, 0.0), sy1 = fmin(y + h2, Ly);
+            double c[5];
+            ora_clip_rect(sx0, sx1, sy0, sy1, cx, cy, r, c);
+            double* cd = cell + 5 * k;
+            cd[0] = c[0];
+            /* sides of the square inside the body rectangle; the sides of the
+             * clipped square on an outer edge are external faces instead */
+            int inside[4] = {x + h2 <= Lx, y + h2 <= Ly, x - h2 >= 0.0, y - h2 >= 0.0};
+            for (int q = 0; q < 4; ++q) cd[1 + q] = inside[q] ? c[1 + q] : 0.0;
+            /* external faces on the outer edges: E face on the right edge,
+             * N on the top, W on the left, S on the bottom */
+            const int edge_of_side[4] = {1, 2, 3, 0};
+            for (int q = 0; q < 4; ++q) {
+                if (inside[q]) continue;
+                int e = edge_of_side[q];
+                bc_value[2 * k] += edge_value[2 * e] * c[1 + q];
+                bc_value[2 * k + 1] += edge_value[2 * e + 1] * c[1 + q];
             }
         }
     }

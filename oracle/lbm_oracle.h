@@ -36,6 +36,12 @@ typedef struct ora_params {
                                 1 = moments of f(x_k, t)                   */
     int32_t sync_every;      /* periodic synchronisation interval l of
                                 Sec. 3.2; 0 disables it                    */
+    int32_t bc_j_mode;       /* first moment J(x_k, t) in Eq. correction-f:
+                                0 = of the populations stored at x_k,
+                                1 = of the populations the LBE streams into
+                                x_k from its body neighbours, the stored
+                                ones kept for directions from outside the
+                                body (reading R15)                          */
 } ora_params;
 
 typedef struct ora_lattice ora_lattice;
@@ -100,6 +106,29 @@ int ora_rect_bc(int32_t nx, int32_t ny, int32_t periodic_x, int32_t periodic_y,
                 double dh, const int32_t edge_type[4],
                 const double edge_value[8], uint8_t* node_type,
                 double* bc_value);
+
+/* A rectangle of lattice points (point (i, j) at (i dh, j dh), body
+ * [0, (nx-1) dh] x [0, (ny-1) dh]) with a traction-free circular hole of
+ * centre (cx, cy) and radius r (reading R14; the plate with a hole of
+ * Sec. 4).  Points strictly inside the circle are void (3); a body point with
+ * a neighbour outside the body is a boundary point: Dirichlet (2) on a
+ * Dirichlet outer edge (corner rules of ora_rect_bc), Neumann (1) otherwise.
+ * bc_value[ny][nx][2]: u* at Dirichlet points; at Neumann points the outer
+ * edges' traction t* times the length of the cell's faces on those edges
+ * outside the hole (the hole itself is traction-free).  cell[ny][nx][5]: at
+ * Neumann points the area of the cell (the square of side dh around the
+ * point, clipped to the body rectangle, minus the disk) and the lengths of
+ * its sides towards E, N, W, S that lie inside the body rectangle, outside
+ * the disk; zero elsewhere.  Returns -1 on bad input. */
+int ora_disk_cells(int32_t nx, int32_t ny, double dh, double cx, double cy, double r,
+                   const int32_t edge_type[4], const double edge_value[8],
+                   uint8_t* node_type, double* bc_value, double* cell);
+
+/* The part of the rectangle [x0, x1] x [y0, y1] outside the open disk of
+ * centre (cx, cy) and radius r: out[0] its area, out[1..4] the lengths of the
+ * rectangle's sides x = x1, y = y1, x = x0, y = y0 outside the disk. */
+void ora_clip_rect(double x0, double x1, double y0, double y1, double cx, double cy, double r,
+                   double out[5]);
 
 void ora_set_threads(int32_t n);
 int32_t ora_get_threads(void);

@@ -551,7 +551,7 @@ def test_hole_patch_uniform_strain():
     cell faces (with sigma_k on sides facing the hole) balance the external
     force exactly (readings R4, R14)."""
     nx, ny, lam, mu = 31, 27, 1.3, 1.0
-    nt, _, cell = W.hole_plate_bc(nx, ny, 14.6, 12.8, 4.4, (1, 1, 1, 1), np.zeros(8))
+    nt, _, cell = O.disk_cells(nx, ny, 14.6, 12.8, 4.4, (1, 1, 1, 1), np.zeros(8))
     exx, eyy, exy = 2e-4, -1e-4, 0.5e-4
     sxx = lam * (exx + eyy) + 2 * mu * exx
     syy = lam * (exx + eyy) + 2 * mu * eyy
@@ -577,7 +577,7 @@ def test_explicit_rectangle_cells_equal_default():
     nx, ny = 17, 13
     ev = np.array([1e-4, -2e-4, 0, 3e-4, -1e-4, 0, 2e-4, 1e-4])
     et = (1, 2, 1, 1)
-    nt, bv, cell = W.hole_plate_bc(nx, ny, -50.0, -50.0, 1.0, et, ev)
+    nt, bv, cell = O.disk_cells(nx, ny, -50.0, -50.0, 1.0, et, ev)
     nt0, bv0 = O.rect_bc(nx, ny, et, ev)
     assert np.array_equal(nt, nt0) and np.array_equal(bv, bv0)
     ux, uy = W.pulse_displacement(nx, ny, 7.0, 6.0, 2.5, 1e-3, "rotation")
@@ -591,7 +591,7 @@ def test_hole_mirror_symmetry():
     """A centred hole and a centred dilatation pulse in a traction-free
     plate: the solution is mirror-symmetric in x and in y."""
     n = 33
-    nt, bv, cell = W.hole_plate_bc(n, n, 16.0, 16.0, 5.5, (1, 1, 1, 1), np.zeros(8))
+    nt, bv, cell = O.disk_cells(n, n, 16.0, 16.0, 5.5, (1, 1, 1, 1), np.zeros(8))
     ux, uy = W.pulse_displacement(n, n, 16.0, 16.0, 6.0, 1e-3, "dilatation")
     ux[nt == 3] = 0.0
     uy[nt == 3] = 0.0
@@ -629,7 +629,7 @@ def test_hole_init_quadratic_exact():
     the differences of R4/R14 (one-sided three-point next to the hole) equal
     the exact divergence and curl at every body point."""
     nx, ny = 30, 26
-    nt, bv, cell = W.hole_plate_bc(nx, ny, 13.7, 12.2, 4.8, (1, 1, 1, 1), np.zeros(8))
+    nt, bv, cell = O.disk_cells(nx, ny, 13.7, 12.2, 4.8, (1, 1, 1, 1), np.zeros(8))
     X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
     ux = 1e-4 * (0.3 * X * X - 0.2 * X * Y + 0.1 * Y * Y + X)
     uy = 1e-4 * (-0.1 * X * X + 0.4 * X * Y - 0.25 * Y * Y + 2 * Y)
@@ -641,3 +641,117 @@ def test_hole_init_quadratic_exact():
     assert np.abs(lat.read(O.PHI) - div)[body].max() <= 1e-12 * scale
     assert np.abs(lat.read(O.PSI) - curl)[body].max() <= 1e-12 * scale
     assert np.abs(lat.read(O.PHI)[~body]).max() == 0.0
+
+
+# ------------------------------------------ travelling wave from du/dt (R9)
+
+@pytest.mark.parametrize("m,n,P", [(3, 2, (1e-3, 0.4e-3)), (1, -2, (-0.3e-3, 0.8e-3)), (2, 0, (0.0, 1e-3))])
+def test_travelling_wave_from_initial_velocity(m, n, P):
+    """Reading R9 (J_phi = -v, J_psi = (-v_y, v_x), in lattice units scaled by
+    dt/dh) against a closed form of the discrete scheme.  On a periodic
+    lattice with u0 = P sin(k.x) and du/dt(0) = Q cos(k.x):
+      phi0 = (P.s) cos(k.x), psi0 = (s x P) cos(k.x), s = (sin kx, sin ky)
+    (central differences).  The LBE's first step from f = f_eq(phi0, J) is
+      phi1 = phi0 + a lap5(phi0) - div_c(Jbar) = phi0 cos(w) - div_c(Jbar),
+    cos w = 1 - 2a(2 - cos kx - cos ky), and every later step is the
+    five-point leapfrog.  With Jbar_phi = -dt Q cos(k.x), -div_c Jbar_phi =
+    -dt (Q.s) sin(k.x), so phi_n = (P.s) cos(k.x - w_phi n) exactly when
+    -dt (Q.s) = (P.s) sin(w_phi); likewise Jbar_psi = dt (-Q_y, Q_x) cos(k.x)
+    gives psi_n = (s x P) cos(k.x - w_psi n) when -dt (s x Q) = (s x P) sin(w_psi).
+    Q is chosen so: a pure travelling wave in both fields, which runs at
+    w/(|k| dt) -> c_d, c_s.  A wrong sign of J_psi makes psi travel backwards,
+    a wrong dt scaling mixes in the opposite wave; both fail here."""
+    nx, ny, lam, mu, steps = 48, 40, 2.0, 1.0, 120
+    lat = periodic_lattice(nx, ny, lam, mu, 1.0, a0=0.6)
+    kx, ky = 2 * math.pi * m / nx, 2 * math.pi * n / ny
+    s = np.array([math.sin(kx), math.sin(ky)])
+    Pv = np.array(P, float)
+    A_phi = float(Pv @ s)
+    A_psi = float(s[0] * Pv[1] - s[1] * Pv[0])
+    K = 2 - math.cos(kx) - math.cos(ky)
+    w_phi = math.acos(1 - 2 * lat.a_phi * K)
+    w_psi = math.acos(1 - 2 * lat.a_psi * K)
+    sn = float(np.linalg.norm(s))
+    shat, sperp = s / sn, np.array([-s[1], s[0]]) / sn
+    q1 = -A_phi * math.sin(w_phi) / (lat.dt * sn)      # Q.s = q1 |s|
+    q2 = -A_psi * math.sin(w_psi) / (lat.dt * sn)      # s x Q = q2 |s|
+    Q = q1 * shat + q2 * sperp
+    X, Y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    ph = kx * X + ky * Y
+    ux0, uy0 = Pv[0] * np.sin(ph), Pv[1] * np.sin(ph)
+    vx0, vy0 = Q[0] * np.cos(ph), Q[1] * np.cos(ph)
+    lat.init(ux0, uy0, vx0, vy0)
+    scale = max(abs(A_phi), abs(A_psi))
+    for done in (1, 2, 7, 40, steps):
+        lat.step(done - lat.steps)
+        assert np.abs(lat.read(O.PHI) - A_phi * np.cos(ph - w_phi * done)).max() <= 1e-12 * scale, ("phi", done)
+        assert np.abs(lat.read(O.PSI) - A_psi * np.cos(ph - w_psi * done)).max() <= 1e-12 * scale, ("psi", done)
+
+
+# ------------------------------------------- J of Eq. correction-f (R15)
+
+def test_bc_j_mode_partial_stream():
+    """Reading R15, bc_j_mode 1: after a step the boundary populations are
+    f^0 = a0 s, f^alpha = a s + e_alpha.Jbar/2 (Eq. correction-f), so their
+    first moment is the Jbar used; it must be the first moment of what the
+    LBE streams into the point from its body neighbours (2 a s - f^opp there)
+    with the point's own populations kept for directions from outside.  This
+    evaluates that definition from the populations before the step.  (The
+    reading is not pinned against the paper: it is one of two readings.)"""
+    nx, ny = 9, 7
+    rng = np.random.default_rng(5)
+    et, ev = (1, 2, 1, 1), rng.uniform(-2e-4, 2e-4, 8)
+    nt, bv = O.rect_bc(nx, ny, et, ev)
+    ux, uy = rng.uniform(-1e-4, 1e-4, (2, ny, nx))
+    lat = O.OracleLattice(nx, ny, 1.4, 1.0, a0_phi=0.9, node_type=nt, bc_value=bv, bc_j_mode=1)
+    lat.init(ux, uy).step(6)
+    a = {0: lat.a_phi, 1: lat.a_psi}
+    before = {0: lat.read(O.F_PHI), 1: lat.read(O.F_PSI)}
+    lat.step(1)
+    after = {0: lat.read(O.F_PHI), 1: lat.read(O.F_PSI)}
+    EX, EY, OPP = (0, 1, 0, -1, 0), (0, 0, 1, 0, -1), (0, 3, 4, 1, 2)
+    checked = 0
+    for set_ in (0, 1):
+        f = before[set_]
+        for j in range(ny):
+            for i in range(nx):
+                if nt[j, i] == 0:
+                    continue
+                g = [f[q, j, i] for q in range(5)]
+                for q in range(1, 5):
+                    si, sj = i - EX[q], j - EY[q]
+                    if 0 <= si < nx and 0 <= sj < ny:
+                        g[q] = 2 * a[set_] * f[:, sj, si].sum() - f[OPP[q], sj, si]
+                jx, jy = g[1] - g[3], g[2] - g[4]
+                h = after[set_][:, j, i]
+                assert h[1] - h[3] == pytest.approx(jx, abs=1e-18), (set_, i, j)
+                assert h[2] - h[4] == pytest.approx(jy, abs=1e-18), (set_, i, j)
+                checked += 1
+    assert checked == 2 * (2 * nx + 2 * (ny - 2))
+
+
+@pytest.mark.parametrize("jmode", [0, 1])
+def test_bc_j_mode_patch_static(jmode):
+    """Both readings of J keep the uniform-strain patch test static (a body
+    in equilibrium has J = 0 everywhere, and so has every partial stream)."""
+    nx, ny, lam, mu = 11, 8, 2.0, 0.7
+    G = [[4e-4, 1.5e-4], [-0.5e-4, -2e-4]]
+    sig = hooke(G, lam, mu)
+    normals = ((0, -1), (1, 0), (0, 1), (-1, 0))
+    ev = np.concatenate([sig @ np.array(nn, float) for nn in normals])
+    nt, bv = O.rect_bc(nx, ny, (1, 1, 1, 1), ev)
+    ux0, uy0 = linear_field(nx, ny, G, (1e-4, 0.0))
+    lat = O.OracleLattice(nx, ny, lam, mu, a0_phi=0.9, node_type=nt, bc_value=bv, bc_j_mode=jmode)
+    lat.init(ux0, uy0)
+    assert_static(lat, ux0, uy0)
+
+
+def test_bc_j_mode_changes_boundary_moments():
+    """The two readings give different boundary populations once a wave has
+    reached the boundary (so the parity cases of both modes test something)."""
+    nx, ny = 21, 17
+    nt, bv = O.rect_bc(nx, ny, (2, 1, 1, 1), np.zeros(8))
+    ux, uy = W.pulse_displacement(nx, ny, 10.0, 8.0, 2.0, 1e-3, "dilatation")
+    res = [O.OracleLattice(nx, ny, 1.0, 1.0, a0_phi=0.9, node_type=nt, bc_value=bv, bc_j_mode=jm)
+           .init(ux, uy).step(40).read(O.F_PHI) for jm in (0, 1)]
+    assert np.abs(res[0] - res[1]).max() > 1e-3 * np.abs(res[0]).max()
