@@ -91,21 +91,21 @@ def workload(name, size=None):
         return "square_64", W.square_64()
     if name == "hole":
         size = size or 8192
-        d, nt, bv, cell = W.hole_square(size)
-        d.geometry = (nt, bv, cell)
-        return f"hole_{size}", d
+        return f"hole_{size}", W.hole_square(size)
     raise SystemExit(f"unknown workload {name}")
 
 
 def describe(d):
     bc = {1: "N", 2: "D"}
     edges = "periodic" if d.periodic_x and d.periodic_y else "".join(bc[e] for e in d.edge_type)
-    if getattr(d, "geometry", None) is not None:
-        nt = d.geometry[0]
-        return {"nx": d.nx, "ny": d.ny, "lambda_over_mu": d.lam / d.mu, "a0_phi": d.a0_phi,
-                "edges_bottom_right_top_left": edges, "hole": "centred, diameter 0.266 L, traction-free",
-                "void_points": int((nt == 3).sum()), "boundary_points": int(((nt == 1) | (nt == 2)).sum()),
-                "loads": "tension ramp to 0.005 mu at L/c_s", "sync_every": d.sync_every}
+    if d.hole is not None:
+        out = {"nx": d.nx, "ny": d.ny, "lambda_over_mu": d.lam / d.mu, "a0_phi": d.a0_phi,
+               "edges_bottom_right_top_left": edges, "hole": "centred, diameter 0.266 L, traction-free",
+               "loads": "tension ramp to 0.005 mu at L/c_s", "sync_every": d.sync_every}
+        nt = getattr(d, "node_type", None)
+        if nt is not None:
+            out.update(void_points=int((nt == 3).sum()), boundary_points=int(((nt == 1) | (nt == 2)).sum()))
+        return out
     return {"nx": d.nx, "ny": d.ny, "lambda_over_mu": d.lam / d.mu, "a0_phi": d.a0_phi,
             "edges_bottom_right_top_left": edges, "pulses": len(d.pulses), "wave": d.wave}
 
@@ -229,10 +229,12 @@ def oracle_lattice(d, side=1024):
     from paper_2301_00228_gb300 import workloads as W
 
     O.set_threads(os.cpu_count() or 1)
-    if getattr(d, "geometry", None) is not None:
+    if d.hole is not None:
         # the same plate with a hole at side x side, loads and synchronisation
+        # (the oracle builds the plate's cells itself)
         n = min(side, d.nx)
-        dd, nt, bv, cell = W.hole_square(n, a0_phi=d.a0_phi, sync_every=d.sync_every)
+        dd = W.hole_square(n, a0_phi=d.a0_phi, sync_every=d.sync_every)
+        nt, bv, cell = O.disk_cells(n, n, *dd.hole, dd.edge_type, np.asarray(dd.edge_value, float).ravel())
         lat = O.OracleLattice(n, n, dd.lam, dd.mu, dd.rho, a0_phi=dd.a0_phi, node_type=nt, bc_value=bv,
                               cell=cell, sync_every=dd.sync_every)
         for kind, t_ramp, t_hold in dd.loads:
@@ -527,7 +529,10 @@ def run_gpu(args):
     et = d.edge_type
     ev = np.asarray(d.edge_value, float).ravel()
     stream = torch.cuda.current_stream()
-    geometry = getattr(d, "geometry", None)
+    geometry = None
+    if d.hole is not None:  # the plate's node types and cells, built by the library
+        geometry = lbps.lbps_disk_cells(d.nx, d.ny, 1.0, *d.hole, et, ev)
+        d.node_type = geometry[0]
     sync_every = args.sync_every if args.sync_every or geometry is None else d.sync_every
     mk = dict(a0_phi=d.a0_phi, storage=args.storage, sync_every=sync_every)
     if geometry is not None:

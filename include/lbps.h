@@ -97,6 +97,15 @@ typedef struct lbps_params {
                                    lands near 2^10 (Nx, Ny are smaller; half's
                                    limit is 65504).  Ignored for FP32 / FP64.  */
     void* cuda_stream;          /* cudaStream_t for all work of this lattice  */
+    int32_t bc_j_mode;          /* J(x_k, t) of Eq. correction-f (Sec. 3.1.2):
+                                   0 = first moment of the populations stored
+                                   at the boundary point; 1 = of the
+                                   populations the LBE (Eq. LBE, from f(., t))
+                                   streams into it from its body neighbours,
+                                   its own stored ones kept for directions
+                                   coming from outside the body (the paper's
+                                   boundary points "can only partially be
+                                   updated via the LBE")                      */
 } lbps_params;
 
 typedef struct lbps_lattice lbps_lattice; /* opaque, library-owned */
@@ -156,6 +165,37 @@ int lbps_state_bytes_cells(const lbps_params* params, const uint8_t* node_type, 
                            size_t* bytes);
 int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const double* bc_value,
                       const double* cell, void* device_mem, size_t device_bytes, lbps_lattice** out);
+
+/* Plate with a circular hole (Sec. 4, third example; Sec. 3 preprocessing:
+ * the cell of a boundary point is the square of side dh around it "modified
+ * to match the boundary geometry", which gives V_C, the face lengths l_kr and
+ * the external boundary of Eq. acc_neumann).  Fills the inputs of
+ * lbps_create_cells for an nx x ny rectangle of lattice points (point (i, j)
+ * at (i dh, j dh); body [0, (nx-1) dh] x [0, (ny-1) dh]) with a traction-free
+ * hole, the open disk of centre (cx, cy) and radius r (caller's length
+ * units):
+ *   node_type[ny][nx]: LBPS_VOID strictly inside the circle; a body point
+ *     with a neighbour outside the body is LBPS_DIRICHLET if it lies on a
+ *     Dirichlet outer edge (corner rules of lbps_rect_bc), else
+ *     LBPS_NEUMANN; all others LBPS_INTERIOR;
+ *   cell[ny][nx][5] at Neumann points: the area of the square around the
+ *     point clipped to the body rectangle, minus the disk, and the lengths of
+ *     its sides towards E, N, W, S that lie inside the body rectangle,
+ *     outside the disk (sides on an outer edge are external faces: 0);
+ *     zero elsewhere;
+ *   bc_value[ny][nx][2]: u* at Dirichlet points (mean of the Dirichlet edges
+ *     through the point); at Neumann points the traction t* of each outer
+ *     edge (edge_type/edge_value as lbps_rect_bc, no periodic axes) times the
+ *     length of the cell's face on that edge outside the disk; the hole
+ *     itself carries no traction.
+ * Host only, no device work.  The caller owns all arrays.  LBPS_ERR_INVALID
+ * for sides < 3, dh <= 0, r < 0, non-finite input or an edge type other
+ * than LBPS_NEUMANN / LBPS_DIRICHLET.  Whether the geometry is valid for the
+ * method (a difference stencil at every body point) is checked by
+ * lbps_create_cells. */
+int lbps_disk_cells(int32_t nx, int32_t ny, double dh, double cx, double cy, double r,
+                    const int32_t edge_type[4], const double edge_value[8], uint8_t* node_type,
+                    double* bc_value, double* cell);
 
 /* Initialisation (Fig. 3; Sec. 3 before Eq. integration): u(x,0), du/dt(x,0)
  * from host arrays [ny][nx]; phi, psi by finite differences of u; the
@@ -218,10 +258,12 @@ int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out
  * Scratch: a fixed device array inside the library (2 MiB + 32 B per device
  * that loads it, held until the process exits), so n may be at most
  * LBPS_NOALLOC_MAX_POINTS; larger n returns LBPS_ERR_INVALID before any
- * device work.  The first call on a device looks up the array's address with
- * that device current; make that first call before any stream capture.  All
- * calls on a device share the array: calls whose work overlaps on the GPU
- * (other streams, other threads) race and must be serialised by the caller.
+ * device work.  Each call looks up the array's address on the current device.
+ * The call ends by copying into the caller's host memory and waiting for the
+ * stream, so it returns LBPS_ERR_INVALID, before any device work, when
+ * cuda_stream is capturing.  All calls on a device share the array: calls
+ * whose work overlaps on the GPU (other streams, other threads) race and must
+ * be serialised by the caller.  out[3] is NaN if any x is NaN.
  * Each call overwrites every scratch slot it reads, so nothing in it needs
  * clearing between calls.  Calls no cudaMalloc, cudaFree or other allocating
  * routine. */
@@ -280,17 +322,20 @@ void lbps_batch_destroy(lbps_batch* b);
 int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done);
 
 /* Checkpoint / resume (not in the paper).  A saved state is a small header
- * (sizes, storage format, step count, 16-bit scale) and the raw current state
- * copy: the populations in the storage format and u, du/dt, so a lattice that
+ * (sizes, storage format, step count, 16-bit scale, a 64-bit fingerprint of
+ * the parameters and boundary description) and the raw current state copy:
+ * the populations in the storage format and u, du/dt, so a lattice that
  * loads it continues bit-for-bit where the saved one was.  The parameters,
  * boundary data and load schedule are the lattice's own and are not saved:
- * load into a lattice created the same way.
+ * load into a lattice created the same way (same parameters, node types,
+ * boundary values and cells; the load schedule is not checked).
  *   lbps_state_size: bytes of a saved state.
  *   lbps_state_save: copies it into dst (host or device memory, at least
  *     lbps_state_size bytes); synchronises.  LBPS_ERR_STATE before init.
  *   lbps_state_load: restores it (the lattice counts as initialised); returns
  *     LBPS_ERR_INVALID if the header does not match this lattice (sizes,
- *     storage format) or bytes is short.  Synchronises. */
+ *     storage format, or the fingerprint of parameters and boundary
+ *     description) or bytes is short.  Synchronises. */
 int lbps_state_size(const lbps_lattice* lat, size_t* bytes);
 int lbps_state_save(lbps_lattice* lat, void* dst, size_t bytes);
 int lbps_state_load(lbps_lattice* lat, const void* src, size_t bytes);

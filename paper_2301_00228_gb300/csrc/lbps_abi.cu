@@ -38,6 +38,7 @@ int validate_params(const lbps_params* p) {
     if (!(p->lambda + 2.0 * p->mu > 0.0) || !finite_positive(p->dh)) return LBPS_ERR_INVALID;
     if (!(p->a0_phi >= 0.0 && p->a0_phi < 1.0)) return LBPS_ERR_INVALID;
     if (p->bc_feq_mode != 0 && p->bc_feq_mode != 1) return LBPS_ERR_INVALID;
+    if (p->bc_j_mode != 0 && p->bc_j_mode != 1) return LBPS_ERR_INVALID;
     if (p->sync_every < 0) return LBPS_ERR_INVALID;
     if (p->storage < LBPS_STORAGE_F32 || p->storage > LBPS_STORAGE_F16) return LBPS_ERR_INVALID;
     if (p->pop_scale_exp < -100 || p->pop_scale_exp > 100) return LBPS_ERR_INVALID;
@@ -264,6 +265,55 @@ int build_boundary(const lbps_params* p, const uint8_t* node_type, const double*
         }
     }
     return LBPS_OK;
+}
+
+// 64-bit FNV-1a over bytes, for the set-up fingerprint of saved states.
+struct Fnv {
+    uint64_t h = 1469598103934665603ull;
+    void add(const void* p, size_t n) {
+        const unsigned char* b = static_cast<const unsigned char*>(p);
+        for (size_t q = 0; q < n; ++q) {
+            h ^= b[q];
+            h *= 1099511628211ull;
+        }
+    }
+    template <typename T>
+    void add(const T& v) {
+        add(&v, sizeof(T));
+    }
+};
+
+// Fingerprint of what a state's meaning depends on besides its own bytes:
+// the parameters of the method and the boundary description (boundary list
+// with its values and cells; for a general geometry also the node types).
+uint64_t setup_hash(const lbps_params* p, const Boundary& bd, const uint8_t* node_type) {
+    Fnv f;
+    f.add(p->nx);
+    f.add(p->ny);
+    f.add(p->lambda);
+    f.add(p->mu);
+    f.add(p->rho);
+    f.add(p->dh);
+    f.add(p->a0_phi);
+    f.add(p->periodic_x);
+    f.add(p->periodic_y);
+    f.add(p->bc_feq_mode);
+    f.add(p->bc_j_mode);
+    f.add(p->sync_every);
+    f.add(p->storage);
+    for (const BNode& q : bd.bn) {
+        f.add(q.i);
+        f.add(q.j);
+        f.add(q.type);
+        f.add(q.smask);
+        f.add(q.bx);
+        f.add(q.by);
+        f.add(q.inv_m);
+        f.add(q.l);
+        f.add(q.nbmask);
+    }
+    if (bd.general && node_type) f.add(node_type, (size_t)p->nx * (size_t)p->ny);
+    return f.h;
 }
 
 }  // namespace
@@ -605,6 +655,7 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
     if (!lat) return LBPS_ERR_OOM;
     lat->p = *params;
     lat->L = L;
+    lat->setup_hash = setup_hash(params, bd, node_type);
     lat->st = reinterpret_cast<cudaStream_t>(params->cuda_stream);
     if (device_mem) {
         if (device_bytes < L.total || (reinterpret_cast<uintptr_t>(device_mem) % kAlign) != 0) {
@@ -647,6 +698,7 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
     c.two_dt = 2.0 / dt;
     c.inv_rho_dh2 = 1.0 / (rho * dh * dh);
     c.bc_feq_mode = params->bc_feq_mode;
+    c.bc_j_mode = params->bc_j_mode;
     // Strain scale the boundary values impose (|u*| / dh at Dirichlet points,
     // |F| / (dh mu) at Neumann points), for the 16-bit scale estimate.
     double eps = 0.0;
@@ -873,14 +925,15 @@ namespace {
 
 // Header of a saved state; the raw current state copy follows it.
 struct SavedState {
-    char magic[8];          // "LBPSSTA1"
+    char magic[8];          // "LBPSSTA2"
     int32_t nx, ny, px, storage;
     int32_t scale_exp, pad;
     int64_t steps;
     uint64_t copy_bytes;
+    uint64_t setup_hash;    // parameters and boundary description of the saving lattice
 };
 
-constexpr char kMagic[8] = {'L', 'B', 'P', 'S', 'S', 'T', 'A', '1'};
+constexpr char kMagic[8] = {'L', 'B', 'P', 'S', 'S', 'T', 'A', '2'};
 
 }  // namespace
 
@@ -903,6 +956,7 @@ int lbps_state_save(lbps_lattice* lat, void* dst, size_t bytes) {
     h.scale_exp = lat->scale_exp;
     h.steps = lat->steps;
     h.copy_bytes = lat->L.copy_bytes;
+    h.setup_hash = lat->setup_hash;
     // dst may be host or device memory: both copies go through the runtime
     cudaError_t e = cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyDefault, lat->st);
     if (e == cudaSuccess)
@@ -929,7 +983,8 @@ int lbps_state_load(lbps_lattice* lat, const void* src, size_t bytes) {
     }
     if (std::memcmp(h.magic, kMagic, sizeof(kMagic)) != 0 || h.nx != lat->L.g.nx || h.ny != lat->L.g.ny ||
         h.px != lat->L.g.px || h.storage != lat->p.storage || h.copy_bytes != lat->L.copy_bytes ||
-        bytes < sizeof(SavedState) + lat->L.copy_bytes || h.steps < 0 || h.scale_exp < -100 || h.scale_exp > 100)
+        bytes < sizeof(SavedState) + lat->L.copy_bytes || h.steps < 0 || h.scale_exp < -100 || h.scale_exp > 100 ||
+        h.setup_hash != lat->setup_hash)
         return LBPS_ERR_INVALID;
     lat->cur = 0;
     cudaError_t e = cudaMemcpyAsync(lat->mem + lat->L.off_copy[0], static_cast<const char*>(src) + sizeof(h),

@@ -78,6 +78,7 @@ struct Consts {
     double load_rate[2];        // 1 / t_ramp of the Neumann [0] / Dirichlet [1] data (0: constant)
     double load_hold[2];        // t_hold: the factor is min(t, t_hold) / t_ramp
     int bc_feq_mode;            // Eq. LBE_mod reading
+    int bc_j_mode;              // J of Eq. correction-f: 0 stored, 1 partial LBE update
 };
 
 // Time factor of the boundary data of one kind (0 Neumann, 1 Dirichlet) at

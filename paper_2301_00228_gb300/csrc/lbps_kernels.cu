@@ -314,6 +314,43 @@ __device__ inline void boundary_newmark(const Geo& g, const Consts& c, const Vie
     LBPS_ST(&B.u[3 * g.plane + p], vy1);
 }
 
+// bc_j_mode 1: J(x_k, t) of Eq. correction-f is the first moment of the
+// populations the plain LBE (Eq. LBE, from copy A) streams into (i, j):
+// direction alpha arrives from the body neighbour at x - e_alpha as
+// 2 a s - f^opp there (tau = dt/2); a direction whose source is outside the
+// body keeps the point's own stored population (own5).
+template <typename P>
+__device__ inline void partial_stream_moment(const Geo& g, const KCof<P>& k, const View<P>& A, int i, int j,
+                                             const typename P::V (&own5)[2][5], double (&jx)[2],
+                                             double (&jy)[2]) {
+    using V = typename P::V;
+    const int SX[5] = {0, -1, 0, 1, 0};  // source offset x - e_alpha
+    const int SY[5] = {0, 0, -1, 0, 1};
+    const int OPP[5] = {0, 3, 4, 1, 2};
+    V in5[2][5];
+#pragma unroll
+    for (int set = 0; set < 2; ++set)
+#pragma unroll
+        for (int q = 1; q < 5; ++q) in5[set][q] = own5[set][q];
+    for (int q = 1; q < 5; ++q) {
+        const int si = i + SX[q], sj = j + SY[q];
+        if (!body_at(g, si, sj)) continue;
+        typename P::Raw r;
+        P::load_raw(A.f, g.plane, (size_t)wrap(sj, g.ny) * g.px + wrap(si, g.nx), true, r);
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+            V f5[5];
+            P::decode(r, set, k, f5);
+            in5[set][q] = fma_rn(k.two_a[set], sum5(f5[0], f5[1], f5[2], f5[3], f5[4]), -f5[OPP[q]]);
+        }
+    }
+#pragma unroll
+    for (int set = 0; set < 2; ++set) {
+        jx[set] = (double)in5[set][1] - (double)in5[set][3];
+        jy[set] = (double)in5[set][2] - (double)in5[set][4];
+    }
+}
+
 template <typename P>
 __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& A,
                                       const View<P>& B, const BNode* __restrict__ bn, int nb, int b) {
@@ -367,6 +404,7 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<
         jx[set] = (double)a5s[set][1] - (double)a5s[set][3];
         jy[set] = (double)a5s[set][2] - (double)a5s[set][4];
     }
+    if (c.bc_j_mode == 1) partial_stream_moment<P>(g, k, A, i, j, a5s, jx, jy);
     P::eq_raw(p, c, sv, jx, jy, k, rb);
     P::store_raw(B.f, g.plane, p, rb);
     P::store_raw(B.m, g.mplane, (size_t)b, rb);

@@ -12,7 +12,6 @@
 // takes its scratch from a fixed array in this file instead, so it allocates
 // nothing.  The paper has no counterpart; it is a service routine.
 #include <cmath>
-#include <mutex>
 
 #include "lbps.h"
 
@@ -27,10 +26,8 @@ constexpr size_t kPointsPerBlock = (size_t)kThreads * kPointsPerThread;
 // library until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[(LBPS_NOALLOC_MAX_BLOCKS + 1) * 4];
 
-// Device address of g_noalloc_scratch, looked up once per device.
-constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_setup_mutex;
+// max that keeps a NaN (fmax drops it)
+__device__ __forceinline__ double nan_max(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
 
 __global__ void __launch_bounds__(kThreads) noalloc_partial_kernel(const double* __restrict__ x,
                                                                    const double* __restrict__ ref, size_t n,
@@ -47,7 +44,7 @@ __global__ void __launch_bounds__(kThreads) noalloc_partial_kernel(const double*
             s0 += e * e;
             s1 += r * r;
             s2 += v;
-            mx = fmax(mx, fabs(v));
+            mx = nan_max(mx, fabs(v));
         }
     }
     sh[0][threadIdx.x] = s0;
@@ -60,7 +57,7 @@ __global__ void __launch_bounds__(kThreads) noalloc_partial_kernel(const double*
             sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
             sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
             sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
-            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+            sh[3][threadIdx.x] = nan_max(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
         }
         __syncthreads();
     }
@@ -78,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) noalloc_final_kernel(double* scratch
         s[0] += scratch[(size_t)b * 4];
         s[1] += scratch[(size_t)b * 4 + 1];
         s[2] += scratch[(size_t)b * 4 + 2];
-        s[3] = fmax(s[3], scratch[(size_t)b * 4 + 3]);
+        s[3] = nan_max(s[3], scratch[(size_t)b * 4 + 3]);
     }
     for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = s[q];
     __syncthreads();
@@ -87,7 +84,7 @@ __global__ void __launch_bounds__(kThreads) noalloc_final_kernel(double* scratch
             sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
             sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
             sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
-            sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
+            sh[3][threadIdx.x] = nan_max(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
         }
         __syncthreads();
     }
@@ -95,21 +92,17 @@ __global__ void __launch_bounds__(kThreads) noalloc_final_kernel(double* scratch
         for (int q = 0; q < 4; ++q) scratch[(size_t)LBPS_NOALLOC_MAX_BLOCKS * 4 + q] = sh[q][0];
 }
 
-// Device address of the scratch on the current device.  The first call on a
-// device takes the address with that device current; later calls reuse it.
+// Device address of the scratch on the current device, looked up on every
+// call (a lookup allocates nothing, and a cached address would go stale if
+// the module were reloaded after a device reset).  The host-side name of the
+// array is not a device address and is never passed to a kernel.
 int scratch_for_current_device(double** out) {
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBPS_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return LBPS_ERR_CUDA;
-        }
-        g_scratch_ptr[dev] = static_cast<double*>(p);
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return LBPS_ERR_CUDA;
     }
-    *out = g_scratch_ptr[dev];
+    *out = static_cast<double*>(p);
     return LBPS_OK;
 }
 
@@ -119,10 +112,19 @@ extern "C" int lbps_norms_noalloc(const double* d_x, const double* d_ref, size_t
                                   double out[4]) {
     if (!d_x || !out || n == 0) return LBPS_ERR_INVALID;
     if (n > LBPS_NOALLOC_MAX_POINTS) return LBPS_ERR_INVALID;  // more blocks than scratch slots
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    // the call ends with a copy into pageable host memory and a wait for the
+    // stream, neither of which a capturing stream allows
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return LBPS_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return LBPS_ERR_INVALID;
     double* scratch = nullptr;
     int rc = scratch_for_current_device(&scratch);
     if (rc != LBPS_OK) return rc;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    cudaGetLastError();  // an error left by earlier, unrelated work is not this call's
     int nblk = (int)((n + kPointsPerBlock - 1) / kPointsPerBlock);
     noalloc_partial_kernel<<<nblk, kThreads, 0, st>>>(d_x, d_ref, n, scratch);
     noalloc_final_kernel<<<1, kThreads, 0, st>>>(scratch, nblk);

@@ -60,6 +60,7 @@ struct lbps_lattice {
     double bc_est = 0.0;  // boundary values' share of the 16-bit scale estimate
     int scale_exp = 0;    // 16-bit storage: Nx, Ny are stored times 2^scale_exp
     int64_t gen = 0;      // incremented by every init (batches re-read descriptors)
+    uint64_t setup_hash = 0;  // parameters and boundary description (checked by lbps_state_load)
     std::vector<int> gap; // general geometry: rows without interior points per strip (Geo::gap, host copy)
     cudaStream_t st;
     // second stream for the boundary Newmark pass beside the interior kernel,

@@ -44,7 +44,7 @@ class lbps_params(ctypes.Structure):
                 ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
                 ("bc_feq_mode", ctypes.c_int32), ("sync_every", ctypes.c_int32),
                 ("storage", ctypes.c_int32), ("pop_scale_exp", ctypes.c_int32),
-                ("cuda_stream", ctypes.c_void_p)]
+                ("cuda_stream", ctypes.c_void_p), ("bc_j_mode", ctypes.c_int32)]
 
 
 class LbpsError(RuntimeError):
@@ -70,6 +70,8 @@ def _load():
         "lbps_create": (ctypes.c_int, [P(lbps_params), vp, vp, vp, sz, P(vp)]),
         "lbps_state_bytes_cells": (ctypes.c_int, [P(lbps_params), vp, vp, P(sz)]),
         "lbps_create_cells": (ctypes.c_int, [P(lbps_params), vp, vp, vp, vp, sz, P(vp)]),
+        "lbps_disk_cells": (ctypes.c_int, [i32, i32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, vp, vp, vp, vp, vp]),
         "lbps_init": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "lbps_init_device": (ctypes.c_int, [vp, vp, vp, vp, vp]),
         "lbps_step": (ctypes.c_int, [vp, i64]),
@@ -163,6 +165,18 @@ def lbps_create_cells(params, node_type, bc_value, cell, device_ptr, device_byte
                                   ctypes.c_void_p(device_ptr) if device_ptr else None, device_bytes,
                                   ctypes.byref(h)), "lbps_create_cells")
     return h
+
+
+def lbps_disk_cells(nx, ny, dh, cx, cy, r, edge_type, edge_value):
+    """(node_type, bc_value, cell) of a rectangle with a circular hole."""
+    et = np.ascontiguousarray(edge_type, np.int32).reshape(4)
+    ev = np.ascontiguousarray(edge_value, np.float64).reshape(8)
+    nt = np.zeros((ny, nx), np.uint8)
+    bv = np.zeros((ny, nx, 2), np.float64)
+    cell = np.zeros((ny, nx, 5), np.float64)
+    _check(_lib.lbps_disk_cells(int(nx), int(ny), float(dh), float(cx), float(cy), float(r), _p(et), _p(ev),
+                                _p(nt), _p(bv), _p(cell)), "lbps_disk_cells")
+    return nt, bv, cell
 
 
 def lbps_init(h, ux0, uy0, vx0=None, vy0=None):
@@ -289,7 +303,7 @@ class Lattice:
 
     def __init__(self, nx, ny, lam, mu, rho=1.0, dh=1.0, a0_phi=0.9999, periodic_x=False, periodic_y=False,
                  node_type=None, bc_value=None, bc_feq_mode=0, sync_every=0, storage="f32", pop_scale_exp=0,
-                 stream=None, cell=None):
+                 stream=None, cell=None, bc_j_mode=0):
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
@@ -297,7 +311,7 @@ class Lattice:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.params = lbps_params(self.nx, self.ny, lam, mu, rho, dh, a0_phi, int(periodic_x), int(periodic_y),
                                   int(bc_feq_mode), int(sync_every), STORAGES[storage], int(pop_scale_exp),
-                                  ctypes.c_void_p(self.stream.cuda_stream))
+                                  ctypes.c_void_p(self.stream.cuda_stream), int(bc_j_mode))
         self.storage = storage
         nt = None if node_type is None else np.ascontiguousarray(node_type, np.uint8)
         bv = None if bc_value is None else np.ascontiguousarray(bc_value, np.float64)

@@ -16,6 +16,9 @@ Recipes (lattice units, dh = 1):
   along k rotated by 90 degrees.  Started at rest they are standing waves.
 * Random rectangles draw each edge Dirichlet or Neumann with values in
   U(-1e-3, 1e-3)^2 and lambda/mu from U(0.5, 4) with mu = rho = 1.
+* A plate with a hole is described by its rectangle, edges and the hole's
+  centre and radius only; its node types and boundary cells are the
+  method's preprocessing and are computed by the library or the oracle.
 """
 from __future__ import annotations
 
@@ -96,6 +99,7 @@ class Domain:
     steps: int = 0
     loads: tuple = ()                              # (kind, t_ramp, t_hold): ramped boundary data
     sync_every: int = 0
+    hole: tuple | None = None                      # (cx, cy, r): traction-free circular hole
 
     def displacement(self, window=None):
         """u(x, 0) on the whole lattice, or on window = (x0, y0, w, h)."""
@@ -242,134 +246,18 @@ def shear_square(n=64, a0_phi=0.9999, horizon=1.0, sync_every=50):
 
 # ------------------------------------------------ plate with a circular hole
 
-def _disk_strip_area(x0, x1, y0, y1, cx, cy, r):
-    """Area of the rectangle [x0, x1] x [y0, y1] inside the disk of radius r
-    around (cx, cy): the chord overlap integrated in x piece by piece (between
-    the x where the circle crosses y0 or y1, or ends, each piece is a fixed
-    combination of straight lines and circle arcs, integrated exactly)."""
-    if x1 <= x0 or y1 <= y0:
-        return 0.0
-    F = lambda u: 0.5 * (u * math.sqrt(max(r * r - u * u, 0.0)) + r * r * math.asin(max(-1.0, min(1.0, u / r))))
-    cuts = {x0, x1, min(max(cx - r, x0), x1), min(max(cx + r, x0), x1)}
-    for y in (y0, y1):
-        if abs(y - cy) < r:
-            w = math.sqrt(r * r - (y - cy) ** 2)
-            for x in (cx - w, cx + w):
-                if x0 < x < x1:
-                    cuts.add(x)
-    xs = sorted(cuts)
-    area = 0.0
-    for a, b in zip(xs[:-1], xs[1:]):
-        if b <= a:
-            continue
-        m = 0.5 * (a + b)
-        if abs(m - cx) >= r:
-            continue
-        h = math.sqrt(r * r - (m - cx) ** 2)
-        top_arc, bot_arc = cy + h < y1, cy - h > y0
-        if (top_arc and cy + h <= y0) or (bot_arc and cy - h >= y1) or min(y1, cy + h) <= max(y0, cy - h):
-            continue
-        ia = F(b - cx) - F(a - cx)               # integral of h(x) over [a, b]
-        top = (cy * (b - a) + ia) if top_arc else y1 * (b - a)
-        bot = (cy * (b - a) - ia) if bot_arc else y0 * (b - a)
-        area += top - bot
-    return area
-
-
-def _segment_outside_disk(p0, p1, cx, cy, r):
-    """Length of the axis-parallel segment p0 -> p1 outside the disk."""
-    (ax, ay), (bx, by) = p0, p1
-    length = math.hypot(bx - ax, by - ay)
-    if length == 0.0:
-        return 0.0
-    if ay == by:                                  # horizontal
-        d = ay - cy
-        if abs(d) >= r:
-            return length
-        w = math.sqrt(r * r - d * d)
-        lo, hi = sorted((ax, bx))
-        inside = max(0.0, min(hi, cx + w) - max(lo, cx - w))
-    else:                                         # vertical
-        d = ax - cx
-        if abs(d) >= r:
-            return length
-        w = math.sqrt(r * r - d * d)
-        lo, hi = sorted((ay, by))
-        inside = max(0.0, min(hi, cy + w) - max(lo, cy - w))
-    return length - inside
-
-
-def hole_plate_bc(nx, ny, cx, cy, radius, edge_type, edge_value, dh=1.0):
-    """Node types, boundary values and cells of an nx x ny rectangle of
-    lattice points (body [0, (nx-1) dh] x [0, (ny-1) dh]) with a traction-free
-    circular hole of the given centre and radius (lattice units x dh).
-
-    node_type: 0 interior, 1 Neumann, 2 Dirichlet, 3 void (inside the hole).
-    The outer edges follow the rectangle rules (edge order bottom, right,
-    top, left; traction t* integrated over each cell's external faces; at
-    corners Dirichlet dominates).  Points whose neighbour lies in the hole are
-    Neumann points with F = 0.  cell[j, i] = (V_C, l_E, l_N, l_W, l_S): the
-    square of side dh around each boundary point clipped to the body, and
-    the length in the body of each of its sides (geometry only)."""
-    et = tuple(int(x) for x in edge_type)
-    ev = np.asarray(edge_value, float).reshape(4, 2)
-    R, CX, CY = radius * dh, cx * dh, cy * dh
-    xs, ys = np.arange(nx) * dh, np.arange(ny) * dh
-    # void points: the rows and columns the disk touches only
-    void = np.zeros((ny, nx), bool)
-    jlo, jhi = max(0, int(math.floor((CY - R) / dh)) - 1), min(ny, int(math.ceil((CY + R) / dh)) + 2)
-    ilo, ihi = max(0, int(math.floor((CX - R) / dh)) - 1), min(nx, int(math.ceil((CX + R) / dh)) + 2)
-    if jlo < jhi and ilo < ihi:
-        XX, YY = np.meshgrid(xs[ilo:ihi], ys[jlo:jhi])
-        void[jlo:jhi, ilo:ihi] = np.hypot(XX - CX, YY - CY) < R
-    nbr_void = np.zeros_like(void)
-    nbr_void[:, :-1] |= void[:, 1:]
-    nbr_void[:, 1:] |= void[:, :-1]
-    nbr_void[:-1, :] |= void[1:, :]
-    nbr_void[1:, :] |= void[:-1, :]
-    ring = np.zeros_like(void)
-    ring[[0, -1], :] = True
-    ring[:, [0, -1]] = True
-    nt = np.zeros((ny, nx), np.uint8)
-    nt[void] = 3
-    bv = np.zeros((ny, nx, 2))
-    cell = np.zeros((ny, nx, 5))
-    Lx, Ly = (nx - 1) * dh, (ny - 1) * dh
-    half = 0.5 * dh
-    for j, i in zip(*np.nonzero((ring | nbr_void) & ~void)):
-        on = [j == 0, i == nx - 1, j == ny - 1, i == 0]
-        n_dir = sum(1 for e in range(4) if on[e] and et[e] == DIRICHLET)
-        if n_dir:
-            nt[j, i] = DIRICHLET
-            bv[j, i] = sum(ev[e] for e in range(4) if on[e] and et[e] == DIRICHLET) / n_dir
-            continue
-        nt[j, i] = NEUMANN
-        n_on = sum(on)
-        if n_on:
-            bv[j, i] = sum(ev[e] for e in range(4) if on[e]) * (dh if n_on == 1 else half)
-        x, y = i * dh, j * dh
-        x0, x1, y0, y1 = max(x - half, 0.0), min(x + half, Lx), max(y - half, 0.0), min(y + half, Ly)
-        cell[j, i, 0] = (x1 - x0) * (y1 - y0) - _disk_strip_area(x0, x1, y0, y1, CX, CY, R)
-        sides = [((x + half, y0), (x + half, y1)) if x + half <= Lx else None,
-                 ((x0, y + half), (x1, y + half)) if y + half <= Ly else None,
-                 ((x - half, y0), (x - half, y1)) if x - half >= 0.0 else None,
-                 ((x0, y - half), (x1, y - half)) if y - half >= 0.0 else None]
-        for q, sd in enumerate(sides):
-            cell[j, i, 1 + q] = 0.0 if sd is None else _segment_outside_disk(sd[0], sd[1], CX, CY, R)
-    return nt, bv, cell
-
-
 def hole_square(n=64, a0_phi=0.9999, horizon=1.0, sync_every=50):
     """Sec. 4, plate with a hole: the tension square of tension_square with
     a traction-free circular hole of diameter 0.266 L at its centre (taken
     centred; the text places the probe point Q at (-0.175 L, 0.025 L) from the
-    hole's centre), synchronised every 50 steps as in the paper.  Returns
-    (Domain, node_type, bc_value, cell)."""
+    hole's centre), synchronised every 50 steps as in the paper.  The hole is
+    described by ``Domain.hole`` = (centre x, centre y, radius) in lattice
+    units; the node types and boundary cells are the method's preprocessing
+    and are built from it by the library (lbps_disk_cells) or the oracle."""
     d = tension_square(n, a0_phi=a0_phi, horizon=horizon, sync_every=sync_every)
     L = n - 1.0
-    nt, bv, cell = hole_plate_bc(n, n, 0.5 * L, 0.5 * L, 0.5 * 0.266 * L, d.edge_type,
-                                 np.asarray(d.edge_value, float).ravel())
-    return d, nt, bv, cell
+    d.hole = (0.5 * L, 0.5 * L, 0.5 * 0.266 * L)
+    return d
 
 
 def busiest_crop(domain: Domain, side):

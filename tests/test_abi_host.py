@@ -99,12 +99,10 @@ def test_general_geometry_host_checks(lib):
     """Plate with a hole through the host-side checks of lbps_state_bytes_cells
     (no GPU needed): a valid hole costs the node-type plane and five stress
     slots per boundary point; invalid geometries are rejected."""
-    from paper_2301_00228_gb300 import workloads as W
-
     nx, ny = 40, 36
     p = lib.lbps_params(nx, ny, 1.0, 1.0, 1.0, 1.0, 0.999, 0, 0, 0, 0, lib.LBPS_STORAGE_F32, 0, None)
     rect = lib.lbps_state_bytes(p)
-    nt, bv, cell = W.hole_plate_bc(nx, ny, 19.3, 17.6, 5.3, (1, 1, 1, 1), np.zeros(8))
+    nt, bv, cell = lib.lbps_disk_cells(nx, ny, 1.0, 19.3, 17.6, 5.3, (1, 1, 1, 1), np.zeros(8))
     hole = lib.lbps_state_bytes_cells(p, nt, cell)
     assert hole >= rect + 64 * ny                       # + node types (pitched rows)
     assert lib.lbps_state_bytes_cells(p, None, None) == rect

@@ -38,7 +38,8 @@ for seed in range(12):                       # random sizes, holes, periodic axe
     lat.close()
     runs += 1
 n = 40                                        # hole plate: every launch shape, row chunks inside the hole
-d, nt, bv, cell = W.hole_square(n, a0_phi=0.999, horizon=0.05, sync_every=0)
+d = W.hole_square(n, a0_phi=0.999, horizon=0.05, sync_every=0)
+nt, bv, cell = L.lbps_disk_cells(n, n, 1.0, *d.hole, d.edge_type, np.asarray(d.edge_value, float).ravel())
 for variant in range(8):
     lat = L.Lattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=nt, bc_value=bv, cell=cell, storage="f32")
     L.lbps_set_tuning(lat._h, variant, 8)
@@ -56,7 +57,8 @@ for dom in W.mixed_batch(count=10)[::2]:
                                     np.asarray(dom.edge_value, float).ravel(), a0_phi=dom.a0_phi)
                 .init(*dom.displacement()))
 for m in (40, 52):
-    dd, nt2, bv2, cell2 = W.hole_square(m, a0_phi=0.999, horizon=0.05, sync_every=0)
+    dd = W.hole_square(m, a0_phi=0.999, horizon=0.05, sync_every=0)
+    nt2, bv2, cell2 = L.lbps_disk_cells(m, m, 1.0, *dd.hole, dd.edge_type, np.asarray(dd.edge_value, float).ravel())
     lats.append(L.Lattice(m, m, dd.lam, dd.mu, a0_phi=dd.a0_phi, node_type=nt2, bc_value=bv2, cell=cell2)
                 .init(*W.pulse_displacement(m, m, 10.0, 10.0, 3.0, 1e-3, "rotation")))
 b = L.Batch(lats)

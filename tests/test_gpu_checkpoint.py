@@ -81,3 +81,25 @@ def test_load_rejects_mismatch(L):
     with pytest.raises(L.LbpsError) as e:
         make(L, "f32", init=False).save_state()
     assert e.value.code == L.LBPS_ERR_STATE
+
+
+def test_load_rejects_other_setup(L):
+    """A state saved by one lattice does not load into a lattice of the same
+    size and storage created otherwise: another material, another edge value,
+    another reading of the boundary rules, or a plate with a hole."""
+    nx, ny = 45, 38
+    buf = make(L, "f32").step(3).save_state()
+    d = W.tension_square(24, a0_phi=0.999)
+    ev = np.asarray(d.edge_value, float).ravel()
+    others = [L.Lattice.rectangle(nx, ny, 1.4, 1.0, (1, 2, 1, 1), ev, a0_phi=0.99),
+              L.Lattice.rectangle(nx, ny, 1.3, 1.0, (1, 2, 1, 1), ev * 1.5, a0_phi=0.99),
+              L.Lattice.rectangle(nx, ny, 1.3, 1.0, (1, 2, 1, 1), ev, a0_phi=0.99, bc_j_mode=1),
+              L.Lattice.rectangle(nx, ny, 1.3, 1.0, (1, 2, 1, 1), ev, a0_phi=0.99, bc_feq_mode=1)]
+    nt, bv, cell = L.lbps_disk_cells(nx, ny, 1.0, 22.0, 19.0, 6.0, (1, 2, 1, 1), ev)
+    others.append(L.Lattice(nx, ny, 1.3, 1.0, a0_phi=0.99, node_type=nt, bc_value=bv, cell=cell))
+    for q, o in enumerate(others):
+        with pytest.raises(L.LbpsError) as e:
+            o.load_state(buf)
+        assert e.value.code == L.LBPS_ERR_INVALID, q
+    same_again = make(L, "f32", init=False).load_state(buf)
+    assert same_again.steps == 3

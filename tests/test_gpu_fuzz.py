@@ -38,16 +38,19 @@ def make_case(seed):
                 mu=float(rng.uniform(0.7, 1.5)), rho=float(rng.uniform(0.8, 1.6)),
                 a0=float(rng.choice([0.99, 0.999])), mode=int(rng.integers(0, 2)),
                 sync=int(rng.choice([0, 0, 13])), storage=storage, steps=int(rng.integers(20, 160)),
-                ramp=bool(rng.random() < 0.3), cell=None)
+                ramp=bool(rng.random() < 0.3), cell=None, jmode=int(seed % 3 == 2))
     if hole:
+        from paper_2301_00228_gb300 import lbps
+
         r = float(rng.uniform(2.5, min(nx, ny) / 5))
         cx = float(rng.uniform(r + 4, nx - 1 - r - 4))
         cy = float(rng.uniform(r + 4, ny - 1 - r - 4))
-        nt, bv, cell = W.hole_plate_bc(nx, ny, cx, cy, r, et, ev)
-        case.update(nt=nt, bv=bv, cell=cell)
+        # each side builds the plate's node types and cells itself
+        nt, bv, cell = lbps.lbps_disk_cells(nx, ny, 1.0, cx, cy, r, et, ev)
+        case.update(nt=nt, bv=bv, cell=cell, ora=O.disk_cells(nx, ny, cx, cy, r, et, ev))
     else:
         nt, bv = O.rect_bc(nx, ny, et, ev, periodic_x=px, periodic_y=py)
-        case.update(nt=nt, bv=bv)
+        case.update(nt=nt, bv=bv, ora=(nt, bv, None))
     body = case["nt"] != 3
     ux, uy = W.pulse_displacement(nx, ny, float(rng.uniform(0, nx - 1)), float(rng.uniform(0, ny - 1)),
                                   float(rng.uniform(2.0, max(2.5, min(nx, ny) / 5))), 1e-3,
@@ -69,10 +72,14 @@ def rel(got, ref, body):
 @pytest.mark.parametrize("seed", range(N_CASES))
 def test_random_case(L, seed):
     c = make_case(seed)
-    kw = dict(a0_phi=c["a0"], periodic_x=c["px"], periodic_y=c["py"], node_type=c["nt"], bc_value=c["bv"],
-              bc_feq_mode=c["mode"], sync_every=c["sync"], cell=c["cell"])
-    ref = O.OracleLattice(c["nx"], c["ny"], c["lam"], c["mu"], c["rho"], **kw)
-    lat = L.Lattice(c["nx"], c["ny"], c["lam"], c["mu"], c["rho"], storage=c["storage"], **kw)
+    kw = dict(a0_phi=c["a0"], periodic_x=c["px"], periodic_y=c["py"], bc_feq_mode=c["mode"], bc_j_mode=c["jmode"],
+              sync_every=c["sync"])
+    ont, obv, ocell = c["ora"]
+    assert np.array_equal(ont, c["nt"])
+    ref = O.OracleLattice(c["nx"], c["ny"], c["lam"], c["mu"], c["rho"], node_type=ont, bc_value=obv, cell=ocell,
+                          **kw)
+    lat = L.Lattice(c["nx"], c["ny"], c["lam"], c["mu"], c["rho"], storage=c["storage"], node_type=c["nt"],
+                    bc_value=c["bv"], cell=c["cell"], **kw)
     if c["ramp"]:
         ref.set_load(1, 30 * ref.dt, 60 * ref.dt)
         ref.set_load(2, 40 * ref.dt)

@@ -43,11 +43,22 @@ def gpu(L, n, d, nt, bv, cell, storage, sync=None):
     return lat
 
 
+def plate(L, d, n):
+    """The plate's node types and cells, built by the library and, separately,
+    by the oracle (the two must classify every point alike)."""
+    ev = np.asarray(d.edge_value, float).ravel()
+    lib = L.lbps_disk_cells(n, n, 1.0, *d.hole, d.edge_type, ev)
+    ora = O.disk_cells(n, n, *d.hole, d.edge_type, ev)
+    assert np.array_equal(lib[0], ora[0])
+    return lib, ora
+
+
 @pytest.fixture(scope="module")
-def hole_case():
+def hole_case(L):
     n = 40
-    d, nt, bv, cell = W.hole_square(n, a0_phi=0.9999, horizon=0.4)
-    ref = O.OracleLattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=nt, bc_value=bv, cell=cell,
+    d = W.hole_square(n, a0_phi=0.9999, horizon=0.4)
+    (nt, bv, cell), (ont, obv, ocell) = plate(L, d, n)
+    ref = O.OracleLattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=ont, bc_value=obv, cell=ocell,
                           sync_every=d.sync_every)
     for kind, t_ramp, t_hold in d.loads:
         ref.set_load(kind, t_ramp, t_hold)
@@ -81,7 +92,7 @@ def test_patch_uniform_strain_around_hole(L):
     traction of the uniform stress (closure of the cell boundary), stays
     static on the GPU as in the oracle."""
     nx, ny, lam, mu = 33, 29, 1.3, 1.0
-    nt, _, cell = W.hole_plate_bc(nx, ny, 15.6, 13.8, 4.6, (1, 1, 1, 1), np.zeros(8))
+    nt, _, cell = L.lbps_disk_cells(nx, ny, 1.0, 15.6, 13.8, 4.6, (1, 1, 1, 1), np.zeros(8))
     exx, eyy, exy = 2e-4, -1e-4, 0.5e-4
     sxx, syy, sxy = lam * (exx + eyy) + 2 * mu * exx, lam * (exx + eyy) + 2 * mu * eyy, 2 * mu * exy
     fx = np.zeros((ny, nx))
@@ -107,7 +118,7 @@ def test_explicit_rectangle_cells(L):
     nx, ny = 47, 39
     ev = np.array([1e-4, -2e-4, 0, 3e-4, -1e-4, 0, 2e-4, 1e-4])
     et = (1, 2, 1, 1)
-    nt, bv, cell = W.hole_plate_bc(nx, ny, -50.0, -50.0, 1.0, et, ev)
+    nt, bv, cell = L.lbps_disk_cells(nx, ny, 1.0, -50.0, -50.0, 1.0, et, ev)
     ux, uy = W.pulse_displacement(nx, ny, 20.0, 17.0, 3.0, 1e-3, "rotation")
     a = L.Lattice.rectangle(nx, ny, 1.2, 1.0, et, ev, a0_phi=0.99, storage="f64").init(ux, uy).step(120)
     b = L.Lattice(nx, ny, 1.2, 1.0, a0_phi=0.99, node_type=nt, bc_value=bv, cell=cell, storage="f64")
@@ -121,7 +132,8 @@ def test_batch_with_holes_equals_single(L):
     shapes = [(40, 0.9999), (33, 0.9999), (51, 0.9999)]
     lats, solo = [], []
     for n, a0 in shapes:
-        d, nt, bv, cell = W.hole_square(n, a0_phi=a0, horizon=0.05, sync_every=0)
+        d = W.hole_square(n, a0_phi=a0, horizon=0.05, sync_every=0)
+        nt, bv, cell = L.lbps_disk_cells(n, n, 1.0, *d.hole, d.edge_type, np.asarray(d.edge_value, float).ravel())
         z = np.zeros((n, n))
         one = gpu(L, n, d, nt, bv, cell, "f32").init(z, z).step(211)
         solo.append({k: one.read(k) for k in FIELDS})
@@ -140,7 +152,7 @@ def test_batch_with_holes_equals_single(L):
 
 def test_invalid_geometry_rejected(L):
     nx, ny = 30, 28
-    nt, bv, cell = W.hole_plate_bc(nx, ny, 14.0, 13.0, 5.0, (1, 1, 1, 1), np.zeros(8))
+    nt, bv, cell = L.lbps_disk_cells(nx, ny, 1.0, 14.0, 13.0, 5.0, (1, 1, 1, 1), np.zeros(8))
     bad = nt.copy()
     bad[:, 2] = L.LBPS_VOID           # column 1 left without a stencil along x
     bad[:, 3] = L.LBPS_NEUMANN
@@ -155,11 +167,12 @@ def test_hole_rows_skipped_same_bits(L):
     8-row chunks many do; every launch shape must give the same bits, and the
     oracle's result within tolerance."""
     n = 96
-    d, nt, bv, cell = W.hole_square(n, a0_phi=0.99, horizon=0.2, sync_every=0)
+    d = W.hole_square(n, a0_phi=0.99, horizon=0.2, sync_every=0)
+    (nt, bv, cell), (ont, obv, ocell) = plate(L, d, n)
     ux, uy = W.pulse_displacement(n, n, 20.0, 30.0, 5.0, 1e-3, "dilatation")
     body = nt != 3
     ux, uy = ux * body, uy * body
-    ref = O.OracleLattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=nt, bc_value=bv, cell=cell)
+    ref = O.OracleLattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=ont, bc_value=obv, cell=ocell)
     want = ref.init(ux, uy).step(150).fields()
     first = None
     for variant in range(8):

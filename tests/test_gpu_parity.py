@@ -78,9 +78,31 @@ def test_hand_cases(L, name, mode, storage, tol):
     assert not fails, fails
 
 
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-5)])
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("name", [c["name"] for c in H.load()["cases"]])
+def test_hand_inputs_partial_stream_j(L, name, mode, storage, tol):
+    """The hand-computed lattices' inputs with J of Eq. correction-f taken
+    from the partial LBE update (bc_j_mode 1), 12 steps, against the oracle."""
+    g = H.load()
+    c = g["common"]
+    case = next(x for x in g["cases"] if x["name"] == name)
+    ux, uy = H.initial_u(c)
+    nt, bv = O.rect_bc(c["nx"], c["ny"], case["edges"]["type"], H.edge_values(case))
+    ref = O.OracleLattice(c["nx"], c["ny"], c["lambda"], c["mu"], c["rho"], c["dh"], c["a0_phi"], node_type=nt,
+                          bc_value=bv, bc_feq_mode=mode, bc_j_mode=1).init(ux, uy).step(12).fields()
+    lat = L.Lattice.rectangle(c["nx"], c["ny"], c["lambda"], c["mu"], case["edges"]["type"], H.edge_values(case),
+                              rho=c["rho"], a0_phi=c["a0_phi"], bc_feq_mode=mode, bc_j_mode=1, storage=storage)
+    got = lat.init(ux, uy).step(12).fields()
+    lat.close()
+    for k in ref:
+        scale = max(np.abs(ref[k]).max(), 1e-30)
+        assert np.abs(got[k] - ref[k]).max() <= tol * scale, (k, storage)
+
+
 # ------------------------------------------------------- mixed rectangles
 
-def mixed_case(seed, nx, ny, periodic=(0, 0), a0=0.99, mode=0, sync=0, steps=200):
+def mixed_case(seed, nx, ny, periodic=(0, 0), a0=0.99, mode=0, sync=0, steps=200, jmode=0):
     rng = np.random.default_rng(seed)
     et = tuple(int(x) for x in rng.choice([1, 2], 4))
     ev = rng.uniform(-2e-4, 2e-4, 8)
@@ -89,7 +111,7 @@ def mixed_case(seed, nx, ny, periodic=(0, 0), a0=0.99, mode=0, sync=0, steps=200
     kind = "dilatation" if seed % 2 else "rotation"
     ux, uy = W.pulse_displacement(nx, ny, cx, cy, max(1.5, min(nx, ny) / 8), 1e-3, kind)
     return dict(nx=nx, ny=ny, et=et, ev=ev, lam=lam, px=periodic[0], py=periodic[1], a0=a0, mode=mode,
-                sync=sync, steps=steps, ux=ux, uy=uy)
+                sync=sync, steps=steps, ux=ux, uy=uy, jmode=jmode)
 
 
 MIXED = [
@@ -111,23 +133,25 @@ def run_oracle(cs):
     nt, bv = O.rect_bc(cs["nx"], cs["ny"], cs["et"], cs["ev"], periodic_x=cs["px"], periodic_y=cs["py"])
     lat = O.OracleLattice(cs["nx"], cs["ny"], cs["lam"], 1.0, a0_phi=cs["a0"], periodic_x=cs["px"],
                           periodic_y=cs["py"], node_type=nt, bc_value=bv, bc_feq_mode=cs["mode"],
-                          sync_every=cs["sync"])
+                          sync_every=cs["sync"], bc_j_mode=cs["jmode"])
     return lat.init(cs["ux"], cs["uy"]).step(cs["steps"]).fields()
 
 
 def run_gpu(L, cs, storage):
     lat = L.Lattice.rectangle(cs["nx"], cs["ny"], cs["lam"], 1.0, cs["et"], cs["ev"], periodic_x=cs["px"],
                               periodic_y=cs["py"], a0_phi=cs["a0"], bc_feq_mode=cs["mode"], sync_every=cs["sync"],
-                              storage=storage)
+                              storage=storage, bc_j_mode=cs["jmode"])
     f = lat.init(cs["ux"], cs["uy"]).step(cs["steps"]).fields()
     lat.close()
     return f
 
 
+@pytest.mark.parametrize("jmode", [0, 1])
 @pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
 @pytest.mark.parametrize("k", range(len(MIXED)))
-def test_mixed_rectangles(L, k, storage):
-    cs = MIXED[k]
+def test_mixed_rectangles(L, k, storage, jmode):
+    """Both readings of J in Eq. correction-f (bc_j_mode 0 and 1)."""
+    cs = dict(MIXED[k], jmode=jmode)
     if storage in ("bf16", "f16") and ((cs["nx"] == 3 and not cs["px"]) or (cs["ny"] == 3 and not cs["py"])):
         with pytest.raises(L.LbpsError) as e:       # 16-bit storage needs 4 points across
             run_gpu(L, cs, storage)
@@ -435,7 +459,8 @@ def test_rejected_init_keeps_state(L):
         assert np.array_equal(a.read(k), b.read(k)), k
     # general geometry: garbage at void points of a rejected input never shows
     n = 40
-    d, nt, bv, cell = W.hole_square(n, a0_phi=0.999, horizon=0.05, sync_every=0)
+    d = W.hole_square(n, a0_phi=0.999, horizon=0.05, sync_every=0)
+    nt, bv, cell = L.lbps_disk_cells(n, n, 1.0, *d.hole, d.edge_type, np.asarray(d.edge_value, float).ravel())
     h = L.Lattice(n, n, d.lam, d.mu, a0_phi=d.a0_phi, node_type=nt, bc_value=bv, cell=cell)
     z = np.zeros((n, n))
     h.init(z, z)
@@ -467,21 +492,24 @@ def test_caller_block_too_small_or_misaligned(L):
     L._lib.lbps_destroy(h)
 
 
+@pytest.mark.parametrize("jmode", [0, 1])
 @pytest.mark.parametrize("size", [(3, 3), (4, 5), (7, 3)])
 @pytest.mark.parametrize("edges", range(16))
-def test_tiny_every_boundary_mix(L, size, edges):
+def test_tiny_every_boundary_mix(L, size, edges, jmode):
     """Every Dirichlet/Neumann combination of the four edges (with the corner
     rule where a Dirichlet and a Neumann edge meet) on tiny lattices, from a
-    random state, FP64 and FP32 against the oracle."""
+    random state, FP64 and FP32 against the oracle, in both readings of J in
+    Eq. correction-f."""
     nx, ny = size
     et = tuple(1 + ((edges >> q) & 1) for q in range(4))
     rng = np.random.default_rng(1000 + 16 * nx + edges)
     ev = rng.uniform(-2e-4, 2e-4, 8)
     ux, uy = rng.uniform(-1e-4, 1e-4, (2, ny, nx))
     nt, bv = O.rect_bc(nx, ny, et, ev)
-    ref = O.OracleLattice(nx, ny, 1.3, 1.0, a0_phi=0.9, node_type=nt, bc_value=bv).init(ux, uy).step(40).fields()
+    ref = O.OracleLattice(nx, ny, 1.3, 1.0, a0_phi=0.9, node_type=nt, bc_value=bv, bc_j_mode=jmode)
+    ref = ref.init(ux, uy).step(40).fields()
     for storage in ("f64", "f32"):
-        lat = L.Lattice.rectangle(nx, ny, 1.3, 1.0, et, ev, a0_phi=0.9, storage=storage)
+        lat = L.Lattice.rectangle(nx, ny, 1.3, 1.0, et, ev, a0_phi=0.9, storage=storage, bc_j_mode=jmode)
         got = lat.init(ux, uy).step(40).fields()
         lat.close()
         assert_parity(got, ref, TOL[storage], (size, et, storage))

@@ -70,3 +70,23 @@ def test_noalloc_rejects_oversize_and_bad_args(L):
         assert e.value.code == L.LBPS_ERR_INVALID
     got = L.lbps_norms_noalloc(x.data_ptr(), 0, 16)
     assert list(got) == [0.0, 0.0, 0.0, 0.0]
+
+
+def test_noalloc_keeps_nan_and_refuses_a_capturing_stream(L):
+    """A NaN in x shows in the max slot; a call on a stream that is being
+    captured into a graph is refused before any device work (it would end
+    with a host copy and a wait), and the capture stays valid."""
+    x = torch.arange(1000, dtype=torch.float64, device="cuda")
+    x[17] = float("nan")
+    got = L.lbps_norms_noalloc(x.data_ptr(), 0, x.numel())
+    assert np.isnan(got[3]) and np.isnan(got[0])
+    g = torch.cuda.CUDAGraph()
+    y = torch.zeros_like(x)
+    with torch.cuda.graph(g):
+        with pytest.raises(L.LbpsError) as e:
+            L.lbps_norms_noalloc(x.data_ptr(), 0, x.numel(), torch.cuda.current_stream().cuda_stream)
+        y.copy_(x * 2.0)
+    assert e.value.code == L.LBPS_ERR_INVALID
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(y[3]) == 6.0
