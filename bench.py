@@ -92,6 +92,9 @@ def workload(name, size=None):
     if name == "hole":
         size = size or 8192
         return f"hole_{size}", W.hole_square(size)
+    if name == "slab":
+        size = size or 16384
+        return f"slab_pulses_{size}", W.many_pulses(size=size)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -444,11 +447,60 @@ def run_batch(args):
     return 0
 
 
+def serve_measure(requests=64, rate_factor=1.2, burst=32, budget_gb=64.0, small_budget=None, max_chunk=500,
+                  sample=6):
+    """Serving measurements on one GPU: a Poisson stream of solves (sides
+    log-uniform 128..2048, steps U{500..20000}, edges and lambda/mu as in the
+    mixed batch) at rate_factor x the capacity of the one-solve-at-a-time
+    loop (measured first on a sample of the same recipe), served by
+    continuous batching and by that loop; a second batched run under a small
+    device-memory budget (default 1.5 x the largest request's footprint, so
+    admission binds); and a burst of the first requests arriving at once
+    (capacity).  Latency = completion - arrival."""
+    from paper_2301_00228_gb300 import serve as S
+    from paper_2301_00228_gb300 import workloads as W
+
+    smp = [S.Request(i, 0.0, d, d.steps)
+           for i, (_, d) in enumerate(W.poisson_requests(count=sample, seed=55, rate_hz=1.0))]
+    prep = {r.rid: r.domain.displacement() for r in smp}
+    S.serve_one_at_a_time(smp[:1], prepared=prep)  # warm-up
+    t0 = time.perf_counter()
+    S.serve_one_at_a_time(smp, prepared=prep)
+    service = (time.perf_counter() - t0) / len(smp)
+    rate = rate_factor / service
+    reqs = [S.Request(i, t, d, d.steps)
+            for i, (t, d) in enumerate(W.poisson_requests(count=requests, seed=5, rate_hz=rate))]
+    prepared = {r.rid: r.domain.displacement() for r in reqs}
+    work = sum(r.domain.nx * r.domain.ny * r.steps for r in reqs)
+    budget = int(budget_gb * (1 << 30))
+    biggest = max(S.footprint(r.domain) for r in reqs)
+    small_bytes = int(small_budget * (1 << 30)) if small_budget else int(1.5 * biggest)
+    served = S.serve_batched(reqs, budget, prepared=prepared, max_chunk=max_chunk)
+    small = S.serve_batched(reqs, small_bytes, prepared=prepared, max_chunk=max_chunk)
+    loop = S.serve_one_at_a_time(reqs, prepared=prepared)
+    sv, lp = served.summary(), loop.summary()
+    out = {"config": {"requests": len(reqs), "sides": "log-U 128..2048", "steps": "U{500..20000}",
+                      "rate_hz": rate, "rate_factor": rate_factor, "loop_service_s_mean": service,
+                      "budget_gb": budget_gb, "lattice_updates": work},
+           "served": {**sv, "glups": work / served.makespan / 1e9},
+           "one_at_a_time": {**lp, "glups": work / loop.makespan / 1e9},
+           "speedup_solves_per_s": sv["solves_per_s"] / lp["solves_per_s"],
+           "p99_latency_ratio": lp["p99_latency_s"] / sv["p99_latency_s"],
+           "served_small_budget": {**small.summary(), "budget_gb": small_bytes / (1 << 30),
+                                   "largest_request_gb": biggest / (1 << 30)}}
+    bst = [S.Request(r.rid, 0.0, r.domain, r.steps) for r in reqs[:burst]]
+    bwork = sum(r.domain.nx * r.domain.ny * r.steps for r in bst)
+    bs = S.serve_batched(bst, budget, prepared=prepared, max_chunk=max_chunk)
+    bl = S.serve_one_at_a_time(bst, prepared=prepared)
+    out["capacity_burst"] = {"requests": len(bst), "served_solves_per_s": bs.summary()["solves_per_s"],
+                             "loop_solves_per_s": bl.summary()["solves_per_s"],
+                             "served_glups": bwork / bs.makespan / 1e9, "loop_glups": bwork / bl.makespan / 1e9,
+                             "speedup": bl.makespan / bs.makespan, "served_max_active": bs.max_active}
+    return out, served
+
+
 def run_serve(args):
-    """Serving: a Poisson stream of solves (sides log-uniform 128..2048, steps
-    U{500..20000}, edges and lambda/mu as in the mixed batch) at 0.8 x the
-    capacity of a one-solve-at-a-time loop, served by continuous batching and
-    by that loop; latency = completion - arrival."""
+    """Serving as its own JSON line (metric: served solves/s); see serve_measure."""
     import torch
 
     rank, world, local = dist_env()
@@ -457,56 +509,106 @@ def run_serve(args):
     if world > 1:  # each rank serves its own copy of the stream (replicas)
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_2301_00228_gb300 import serve as S
-    from paper_2301_00228_gb300 import workloads as W
-
-    # capacity of the one-at-a-time loop, from a sample of the same recipe
-    sample = [S.Request(i, 0.0, d, d.steps)
-              for i, (_, d) in enumerate(W.poisson_requests(count=args.serve_sample, seed=55, rate_hz=1.0))]
-    prep = {r.rid: r.domain.displacement() for r in sample}
-    S.serve_one_at_a_time(sample[:1], prepared=prep)  # warm-up
-    t0 = time.perf_counter()
-    base = S.serve_one_at_a_time(sample, prepared=prep)
-    service = (time.perf_counter() - t0) / len(sample)
-    rate = args.rate_factor / service
-    reqs = [S.Request(i, t, d, d.steps)
-            for i, (t, d) in enumerate(W.poisson_requests(count=args.requests, seed=5, rate_hz=rate))]
-    prepared = {r.rid: r.domain.displacement() for r in reqs}
-    work = sum(r.domain.nx * r.domain.ny * r.steps for r in reqs)
-    budget = int(args.budget_gb * (1 << 30))
-    served = S.serve_batched(reqs, budget, prepared=prepared, max_chunk=args.max_chunk)
-    small = S.serve_batched(reqs, int(args.small_budget_gb * (1 << 30)), prepared=prepared,
-                            max_chunk=args.max_chunk) if args.small_budget_gb > 0 else None
-    loop = S.serve_one_at_a_time(reqs, prepared=prepared)
-    sv, lp = served.summary(), loop.summary()
+    m, served = serve_measure(args.requests, args.rate_factor, args.burst, args.budget_gb,
+                              args.small_budget_gb or None, args.max_chunk, args.serve_sample)
+    sv = m["served"]
     rmax, rsum = reducers(dist, "cuda")
     total = rsum(sv["solves_per_s"])               # solves/s of all replicas
     sv["p99_latency_s_max_over_ranks"] = rmax(sv["p99_latency_s"])
     line = {"metric": "served solves/s", "value": total, "unit": "solves/s", "n_gpus": world,
-            "steps": len(reqs), "warmup": 1, "ms_per_step": 1000.0 * served.makespan / len(reqs),
+            "steps": m["config"]["requests"], "warmup": 1,
+            "ms_per_step": 1000.0 * served.makespan / m["config"]["requests"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"serve_poisson_{len(reqs)}", "requests": len(reqs), "sides": "log-U 128..2048",
-                       "steps": "U{500..20000}", "rate_hz": rate, "rate_factor": args.rate_factor,
-                       "loop_service_s_mean": service, "budget_gb": args.budget_gb,
-                       "lattice_updates": work},
-            "served": {**sv, "glups": work / served.makespan / 1e9},
-            "one_at_a_time": {**lp, "glups": work / loop.makespan / 1e9},
-            "speedup_solves_per_s": sv["solves_per_s"] / lp["solves_per_s"],
-            "p99_latency_ratio": lp["p99_latency_s"] / sv["p99_latency_s"]}
-    if small is not None:
-        line["served_small_budget"] = {**small.summary(), "budget_gb": args.small_budget_gb}
-    # capacity: the first requests all arriving at once (throughput, no idle time)
-    burst = [S.Request(r.rid, 0.0, r.domain, r.steps) for r in reqs[:args.burst]]
-    bwork = sum(r.domain.nx * r.domain.ny * r.steps for r in burst)
-    bs = S.serve_batched(burst, budget, prepared=prepared, max_chunk=args.max_chunk)
-    bl = S.serve_one_at_a_time(burst, prepared=prepared)
-    line["capacity_burst"] = {"requests": len(burst),
-                              "served_solves_per_s": bs.summary()["solves_per_s"],
-                              "loop_solves_per_s": bl.summary()["solves_per_s"],
-                              "served_glups": bwork / bs.makespan / 1e9, "loop_glups": bwork / bl.makespan / 1e9,
-                              "speedup": bl.makespan / bs.makespan, "served_max_active": bs.max_active}
+            "config": {"workload": f"serve_poisson_{m['config']['requests']}", **m["config"]},
+            **{k: v for k, v in m.items() if k != "config"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_slab(args):
+    """One lattice split into slabs of rows, one per rank (strong scaling:
+    the lattice is the same for every N), ghost rows exchanged through NCCL
+    after every step (paper_2301_00228_gb300.slab).  Default: the 16384^2
+    many-pulse lattice (same recipe as the pulses workload).  At N = 1 the one
+    slab is the whole lattice and nothing is exchanged."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2301_00228_gb300 import lbps
+    from paper_2301_00228_gb300 import slab as S
+    from paper_2301_00228_gb300 import workloads as W
+
+    size = args.size or 16384
+    d = W.many_pulses(size=size)
+    ev = np.asarray(d.edge_value, float).ravel()
+    nt, bv = lbps.lbps_rect_bc(d.nx, d.ny, 0, 0, 1.0, d.edge_type, ev)
+    p = S.plan(d.ny, world, rank)
+    eng = S.CudaSlab(p, d.nx, d.lam, d.mu, d.rho, node_type=nt, bc_value=bv, a0_phi=d.a0_phi, storage=args.storage)
+    run = S.SlabRun(eng, p, dist)
+    ux, uy = d.displacement_torch("cuda", rows=(p.first, p.rows))
+    run.init_rows(ux, uy)
+    del ux, uy
+    stream = torch.cuda.current_stream()
+    run.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    lbps.lbps_profile(eng.lat._h, 1)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    run.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clock = clocks.stop()
+    if eng.lat.check() != 0:
+        raise SystemExit("state became non-finite")
+    prof = lbps.lbps_profile_read(eng.lat._h)
+    lbps.lbps_profile(eng.lat._h, 0)
+    seconds = e0.elapsed_time(e1) / 1000.0
+    owned = (p.y1 - p.y0) * d.nx
+    rmax, rsum = reducers(dist, "cuda")
+    value_ups, t_max, units_all = aggregate(seconds, owned * args.steps, world, rmax, rsum)
+    bulk_ms, bulk_n = float(prof[0]), float(prof[1])
+    interior = (d.nx - 2) * (p.rows - 2)
+    alg = interior * BYTES_PER_UPDATE[args.storage]
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (bulk_ms / max(bulk_n, 1) / 1000.0) / 1e9
+    halo = lbps.lbps_halo_bytes(eng.lat._h, S.HALO)
+    line = {"metric": METRIC, "value": value_ups / 1e9, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64" if args.storage == "f64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": f"slab_pulses_{size}", **describe(d), "storage": args.storage,
+                       "displacement": "f64", "parallelism": f"slab{world}", "halo_rows": S.HALO,
+                       "rows_per_rank": [p.y1 - p.y0], "halo_bytes_per_message": halo if world > 1 else 0,
+                       "l2": "state larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "bulk_kernel (rank 0's slab)", "peak_source": peak_kind},
+            # per step: boundary Newmark, interior, reset; per neighbour one pack and
+            # one unpack (copy, boundary mirror, boundary stresses)
+            "gpu_launches": int(bulk_n) * 3 + args.steps * 4 * ((p.down is not None) + (p.up is not None)),
+            "clocks": clock}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 
@@ -639,6 +741,11 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _, _ = oracle_sample(d, target_seconds=args.ref_seconds)
+    serving = None
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        lat.close()  # its device memory back before the serving runs
+        serving, _ = serve_measure(args.serve_requests, args.rate_factor, args.serve_burst, args.budget_gb, None,
+                                   args.max_chunk, args.serve_sample)
     precision = None
     if rank == 0 and args.precision and not (d.periodic_x and d.periodic_y):
         precision = precision_report(d, args.precision_side, args.precision_steps)
@@ -656,6 +763,8 @@ def run_gpu(args):
                 "clocks": clock}
         if precision is not None:
             line["precision"] = precision
+        if serving is not None:
+            line["serving"] = serving
         print(json.dumps(line), flush=True)
     lat.close()
     if dist is not None:
@@ -669,14 +778,19 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="pulses", choices=["pulses", "waves", "square", "hole", "batch", "serve"])
+    ap.add_argument("--workload", default="pulses",
+                    choices=["pulses", "waves", "square", "hole", "batch", "serve", "slab"])
     ap.add_argument("--requests", type=int, default=64, help="serve: requests in the Poisson stream")
     ap.add_argument("--serve-sample", type=int, default=6, help="serve: solves timed to set the arrival rate")
-    ap.add_argument("--rate-factor", type=float, default=0.8, help="serve: arrival rate / loop capacity")
+    ap.add_argument("--rate-factor", type=float, default=1.2, help="serve: arrival rate / loop capacity")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device-memory admission budget")
-    ap.add_argument("--small-budget-gb", type=float, default=2.0, help="serve: second run with a small budget")
+    ap.add_argument("--small-budget-gb", type=float, default=0.0,
+                    help="serve: budget of the second run (0: 1.5 x the largest request's footprint)")
     ap.add_argument("--max-chunk", type=int, default=500, help="serve: most steps between completions checks")
     ap.add_argument("--burst", type=int, default=32, help="serve: requests arriving at once for the capacity run")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="serving section of the lattice workloads' line: requests (0: none)")
+    ap.add_argument("--serve-burst", type=int, default=24, help="serving section: burst requests")
     ap.add_argument("--batch-count", type=int, default=256, help="domains of the batch workload")
     ap.add_argument("--batch-tuning", default=None,
                     help="batch: launch shape 'variant,rows' instead of running the autotuner")
@@ -699,6 +813,8 @@ def main(argv=None):
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "slab":
+        return run_slab(args)
     return run_gpu(args)
 
 

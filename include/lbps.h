@@ -395,6 +395,32 @@ int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);
 int lbps_profile(lbps_lattice* lat, int32_t enable);
 int lbps_profile_read(lbps_lattice* lat, double out[4]);
 
+/* ---- Domain decomposition (not in the paper, whose only remark on
+ * parallelism is that it is easy with most LBMs, Sec. 1).  A large lattice
+ * split into slabs of rows, each a lattice of its own with a few ghost rows
+ * beyond each cut, exchanges those rows with its neighbours after every
+ * step; see paper_2301_00228_gb300/slab.py for the plan.
+ *   lbps_halo_bytes: bytes of `rows` rows of the current state: every
+ *     population plane (storage layout) and u_x, u_y, v_x, v_y, plane after
+ *     plane, rows x (nx rounded up to 32) elements each.
+ *   lbps_halo_pack: rows [row0, row0 + rows) of the current state into d_buf
+ *     (device memory, 16-byte aligned, at least lbps_halo_bytes bytes, owned
+ *     by the caller); asynchronous on the lattice's stream.
+ *   lbps_halo_unpack: the same rows from d_buf into the current state, then
+ *     recomputes what the state carries besides them (boundary stresses and
+ *     the boundary mirror); asynchronous.
+ * LBPS_ERR_INVALID for a bad row range, a short or misaligned buffer;
+ * LBPS_ERR_STATE before init. */
+int lbps_halo_bytes(const lbps_lattice* lat, int32_t rows, size_t* bytes);
+int lbps_halo_pack(lbps_lattice* lat, int32_t row0, int32_t rows, void* d_buf, size_t bytes);
+int lbps_halo_unpack(lbps_lattice* lat, int32_t row0, int32_t rows, const void* d_buf, size_t bytes);
+
+/* The lattice is rows [row0, row0 + ny) of a larger one (a slab): the 16-bit
+ * formats' stochastic rounding then draws its random bits from the global
+ * position, so a slab rounds its rows as the whole lattice does.  Call before
+ * lbps_init.  No effect for FP32 / FP64 storage. */
+int lbps_set_origin(lbps_lattice* lat, int64_t row0);
+
 /* Switch the stream used by later calls. */
 int lbps_set_stream(lbps_lattice* lat, void* cuda_stream);
 

@@ -110,6 +110,8 @@ def lib():
         L.ora_disk_cells.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, vp, vp, vp, vp, vp]
         L.ora_clip_rect.argtypes = [ctypes.c_double] * 7 + [vp]
+        L.ora_get_rows.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp]
+        L.ora_set_rows.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp]
         L.ora_set_threads.argtypes = [ctypes.c_int32]
         L.ora_get_threads.restype = ctypes.c_int32
         _lib = L
@@ -221,6 +223,20 @@ class OracleLattice:
         if lib().ora_read(self._h, int(field), _ptr(out)) != 0:
             raise ValueError("bad field id")
         return out if planes == 5 else out[0]
+
+    def get_rows(self, row0, rows):
+        """Rows [row0, row0 + rows) of the state: (14, rows, nx) doubles (the five
+        populations of each set, u_x, u_y, v_x, v_y)."""
+        out = np.zeros((14, rows, self.nx), np.float64)
+        if lib().ora_get_rows(self._h, int(row0), int(rows), _ptr(out)) != 0:
+            raise ValueError("bad row range or lattice not initialised")
+        return out
+
+    def set_rows(self, row0, block):
+        block = np.ascontiguousarray(block, np.float64)
+        if lib().ora_set_rows(self._h, int(row0), int(block.shape[1]), _ptr(block)) != 0:
+            raise ValueError("bad row range or lattice not initialised")
+        return self
 
     def fields(self):
         return {name: self.read(fid) for name, fid in

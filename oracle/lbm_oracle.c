@@ -718,6 +718,30 @@ int ora_read(ora_lattice* L, int32_t field, double* dst) {
     }
 }
 
+/* ------------------------------------------------------------ state rows */
+
+static double* row_plane(const ora_lattice* L, int q) {
+    if (q < 10) return L->f[q / 5][q % 5];
+    double* u[4] = {L->ux, L->uy, L->vx, L->vy};
+    return u[q - 10];
+}
+
+int ora_get_rows(const ora_lattice* L, int32_t row0, int32_t rows, double* dst) {
+    if (!L->initialised || row0 < 0 || rows < 0 || row0 + rows > L->p.ny) return -1;
+    long blk = (long)rows * L->p.nx;
+    for (int q = 0; q < 14; ++q)
+        memcpy(dst + q * blk, row_plane(L, q) + (long)row0 * L->p.nx, (size_t)blk * sizeof(double));
+    return 0;
+}
+
+int ora_set_rows(ora_lattice* L, int32_t row0, int32_t rows, const double* src) {
+    if (!L->initialised || row0 < 0 || rows < 0 || row0 + rows > L->p.ny) return -1;
+    long blk = (long)rows * L->p.nx;
+    for (int q = 0; q < 14; ++q)
+        memcpy(row_plane(L, q) + (long)row0 * L->p.nx, src + q * blk, (size_t)blk * sizeof(double));
+    return 0;
+}
+
 /* ------------------------------------------------------ rectangle helper */
 
 int ora_rect_bc(int32_t nx, int32_t ny, int32_t periodic_x, int32_t periodic_y, double dh,

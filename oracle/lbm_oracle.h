@@ -130,6 +130,13 @@ int ora_disk_cells(int32_t nx, int32_t ny, double dh, double cx, double cy, doub
 void ora_clip_rect(double x0, double x1, double y0, double y1, double cx, double cy, double r,
                    double out[5]);
 
+/* State rows for a domain decomposition test: rows [row0, row0 + rows) of
+ * the current state, as 14 blocks of rows x nx doubles in the order
+ * f_phi^0..4, f_psi^0..4, u_x, u_y, v_x, v_y.  get copies out, set copies in
+ * (the lattice must be initialised).  Return -1 on a bad row range. */
+int ora_get_rows(const ora_lattice* L, int32_t row0, int32_t rows, double* dst);
+int ora_set_rows(ora_lattice* L, int32_t row0, int32_t rows, const double* src);
+
 void ora_set_threads(int32_t n);
 int32_t ora_get_threads(void);
 

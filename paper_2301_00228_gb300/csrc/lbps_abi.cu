@@ -117,6 +117,7 @@ KC<T> make_kc(double a_phi, double a_psi, double cd2, double cs2, double dh) {
     k.scale = (T)1;
     k.sr = 0;
     k.inv_scale = (T)1;
+    k.key0 = 0;
     return k;
 }
 
@@ -1062,6 +1063,99 @@ int lbps_profile_read(lbps_lattice* lat, double out[4]) {
     }
     lat->ev_kind.clear();
     lat->ev_used = 0;
+    return LBPS_OK;
+}
+
+// ---- rows of the state for a domain decomposition
+
+namespace {
+
+// The copy of rows [row0, row0 + rows) of every plane of the current state
+// (populations in the storage layout, then u_x, u_y, v_x, v_y) to or from
+// buf, plane after plane, each rows x px elements (row padding included).
+int halo_segments(lbps_lattice* lat, int32_t row0, int32_t rows, char* buf, bool pack, lbps::CopySegs& s) {
+    const Layout& L = lat->L;
+    const size_t px = (size_t)L.g.px;
+    const size_t base = lbps::with_policy(lat->p.storage, [](auto pol) { return sizeof(typename decltype(pol)::Base); });
+    const int planes = lbps::with_policy(lat->p.storage, [](auto pol) { return decltype(pol)::kBytesPerPoint; }) /
+                       (int)base;
+    if (planes + 4 > lbps::kMaxCopySegs) return LBPS_ERR_INVALID;
+    char* copy = lat->mem + L.off_copy[lat->cur];
+    char* u = reinterpret_cast<char*>(lat->u(lat->cur));
+    size_t off = 0;
+    s.n = 0;
+    s.pack = pack ? 1 : 0;
+    auto add = [&](char* lattice_side, size_t bytes) {
+        s.src[s.n] = pack ? lattice_side : buf + off;
+        s.dst[s.n] = pack ? buf + off : lattice_side;
+        s.bytes[s.n] = bytes;
+        ++s.n;
+        off += bytes;
+    };
+    for (int q = 0; q < planes; ++q) add(copy + ((size_t)q * L.g.plane + (size_t)row0 * px) * base, (size_t)rows * px * base);
+    for (int q = 0; q < 4; ++q) add(u + ((size_t)q * L.g.plane + (size_t)row0 * px) * sizeof(double), (size_t)rows * px * 8);
+    return LBPS_OK;
+}
+
+size_t halo_bytes_of(const lbps_lattice* lat, int32_t rows) {
+    const size_t per = lbps::with_policy(lat->p.storage, [](auto pol) { return (size_t)decltype(pol)::kBytesPerPoint; });
+    return (size_t)rows * (size_t)lat->L.g.px * (per + 32);
+}
+
+int halo_check(const lbps_lattice* lat, int32_t row0, int32_t rows, const void* buf, size_t bytes) {
+    if (!lat || !buf || rows < 1 || row0 < 0 || row0 + rows > lat->L.g.ny) return LBPS_ERR_INVALID;
+    if (reinterpret_cast<uintptr_t>(buf) % 16 != 0 || bytes < halo_bytes_of(lat, rows)) return LBPS_ERR_INVALID;
+    if (!lat->initialised) return LBPS_ERR_STATE;
+    return LBPS_OK;
+}
+
+}  // namespace
+
+int lbps_halo_bytes(const lbps_lattice* lat, int32_t rows, size_t* bytes) {
+    if (!lat || !bytes || rows < 1 || rows > lat->L.g.ny) return LBPS_ERR_INVALID;
+    *bytes = halo_bytes_of(lat, rows);
+    return LBPS_OK;
+}
+
+int lbps_halo_pack(lbps_lattice* lat, int32_t row0, int32_t rows, void* d_buf, size_t bytes) {
+    lbps::NvtxRange nvtx("lbps_halo_pack");
+    int rc = halo_check(lat, row0, rows, d_buf, bytes);
+    if (rc != LBPS_OK) return rc;
+    lbps::CopySegs s;
+    rc = halo_segments(lat, row0, rows, static_cast<char*>(d_buf), true, s);
+    if (rc != LBPS_OK) return rc;
+    cudaError_t e = lbps::launch_copy_segments(s, lat->st);
+    if (e != cudaSuccess) lat->last_cuda = (int)e;
+    return cuda_ok(e);
+}
+
+int lbps_halo_unpack(lbps_lattice* lat, int32_t row0, int32_t rows, const void* d_buf, size_t bytes) {
+    lbps::NvtxRange nvtx("lbps_halo_unpack");
+    int rc = halo_check(lat, row0, rows, d_buf, bytes);
+    if (rc != LBPS_OK) return rc;
+    lbps::CopySegs s;
+    rc = halo_segments(lat, row0, rows, const_cast<char*>(static_cast<const char*>(d_buf)), false, s);
+    if (rc != LBPS_OK) return rc;
+    cudaError_t e = lbps::launch_copy_segments(s, lat->st);
+    // the copy's derived boundary data: stresses of its u and the boundary mirror
+    if (e == cudaSuccess)
+        e = lbps::with_policy(lat->p.storage, [&](auto pol) {
+            using P = decltype(pol);
+            const lbps::View<P> v = lat->view<P>(lat->cur);
+            cudaError_t r = lbps::launch_mirror<P>(lat->L.g, v, lat->bn(), lat->L.nb, lat->st);
+            if (r == cudaSuccess)
+                r = lbps::launch_boundary<P>(lat->L.g, lat->c, lat->kc<P>(), v, v, lat->bn(), lat->L.nb, lat->flag(),
+                                             lat->tstep(), lat->st, 0, 1);
+            return r;
+        });
+    if (e != cudaSuccess) lat->last_cuda = (int)e;
+    return cuda_ok(e);
+}
+
+int lbps_set_origin(lbps_lattice* lat, int64_t row0) {
+    if (!lat) return LBPS_ERR_INVALID;
+    lat->kf.key0 = (unsigned)((uint64_t)row0 * (uint64_t)lat->L.g.px);
+    lat->gen += 1;  // batches holding this lattice re-read its descriptor
     return LBPS_OK;
 }
 

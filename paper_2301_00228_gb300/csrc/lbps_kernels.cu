@@ -19,9 +19,10 @@
 // a template over the population storage policy (lbps_device.cuh): FP32 or
 // FP64 planes, or FP32 moments (f^0, J) with the non-equilibrium pair sums in
 // 16 bits.
+#include <algorithm>
+
 #include "lbps_launch.h"
 #ifdef LBPS_CHECKED
-#include <algorithm>
 #include <utility>
 #include <vector>
 #endif
@@ -830,6 +831,25 @@ __global__ void __launch_bounds__(kNormThreads) norms_final_kernel(const double*
         for (int q = 0; q < 4; ++q) out[q] = sh[q][0];
 }
 
+// Rows of a state copy to or from a caller buffer, 16 bytes per thread and
+// step; segment blockIdx.y.  The lattice side of each copy goes through the
+// checked accessors, the caller's buffer is not part of a lattice block.
+__global__ void copy_segments_kernel(CopySegs s) {
+    const int q = blockIdx.y;
+    if (q >= s.n) return;
+    const uint4* a = reinterpret_cast<const uint4*>(s.src[q]);
+    uint4* b = reinterpret_cast<uint4*>(s.dst[q]);
+    const size_t n16 = s.bytes[q] / 16;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n16; t += (size_t)gridDim.x * blockDim.x) {
+        if (s.pack) {
+            const uint4 v = LBPS_LD(&a[t]);
+            b[t] = v;
+        } else {
+            LBPS_ST(&b[t], a[t]);
+        }
+    }
+}
+
 dim3 grid2d(int nx, int ny, dim3 blk) { return dim3((nx + blk.x - 1) / blk.x, (ny + blk.y - 1) / blk.y); }
 
 }  // namespace
@@ -883,6 +903,15 @@ cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int n
     case 6: return launch_bulk_batch_v<P, 4, 1>(dd, tasks, ntasks, parity, next, st);
     default: return launch_bulk_batch_v<P, 8, 1>(dd, tasks, ntasks, parity, next, st);
     }
+}
+
+cudaError_t launch_copy_segments(const CopySegs& s, cudaStream_t st) {
+    if (s.n <= 0) return cudaSuccess;
+    size_t most = 0;
+    for (int q = 0; q < s.n; ++q) most = std::max(most, s.bytes[q] / 16);
+    const int bx = (int)std::min<size_t>((most + 255) / 256, 1024);
+    copy_segments_kernel<<<dim3(std::max(bx, 1), s.n), 256, 0, st>>>(s);
+    return cudaGetLastError();
 }
 
 cudaError_t set_check_range(const void* base, size_t bytes, cudaStream_t st) {

@@ -108,6 +108,20 @@ template <typename P>
 cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
                               unsigned* next, cudaStream_t st);
 
+// Rows of a state copy to or from a caller buffer (domain decomposition):
+// up to kMaxCopySegs contiguous byte ranges, each a multiple of 16 bytes and
+// 16-byte aligned at both ends.  pack: lattice -> buffer; otherwise buffer ->
+// lattice.
+constexpr int kMaxCopySegs = 16;
+struct CopySegs {
+    const char* src[kMaxCopySegs];
+    char* dst[kMaxCopySegs];
+    size_t bytes[kMaxCopySegs];
+    int n;
+    int pack;
+};
+cudaError_t launch_copy_segments(const CopySegs& s, cudaStream_t st);
+
 // Checked builds (LBPS_CHECKED): set_check_range adds a live lattice block
 // that kernel accesses may touch (bytes = 0 removes the block starting at
 // base); check_report returns the first violation since the library was

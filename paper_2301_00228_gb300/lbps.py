@@ -94,6 +94,10 @@ def _load():
         "lbps_profile": (ctypes.c_int, [vp, i32]),
         "lbps_profile_read": (ctypes.c_int, [vp, vp]),
         "lbps_set_stream": (ctypes.c_int, [vp, vp]),
+        "lbps_halo_bytes": (ctypes.c_int, [vp, i32, P(sz)]),
+        "lbps_halo_pack": (ctypes.c_int, [vp, i32, i32, vp, sz]),
+        "lbps_halo_unpack": (ctypes.c_int, [vp, i32, i32, vp, sz]),
+        "lbps_set_origin": (ctypes.c_int, [vp, i64]),
         "lbps_destroy": (None, [vp]),
         "lbps_batch_create": (ctypes.c_int, [vp, i32, vp, P(vp)]),
         "lbps_batch_step": (ctypes.c_int, [vp, i64]),
@@ -294,6 +298,24 @@ def lbps_set_stream(h, stream_ptr):
 
 def lbps_destroy(h):
     _lib.lbps_destroy(h)
+
+
+def lbps_halo_bytes(h, rows):
+    n = ctypes.c_size_t(0)
+    _check(_lib.lbps_halo_bytes(h, int(rows), ctypes.byref(n)), "lbps_halo_bytes")
+    return int(n.value)
+
+
+def lbps_halo_pack(h, row0, rows, d_buf, nbytes):
+    _check(_lib.lbps_halo_pack(h, int(row0), int(rows), ctypes.c_void_p(d_buf), int(nbytes)), "lbps_halo_pack")
+
+
+def lbps_halo_unpack(h, row0, rows, d_buf, nbytes):
+    _check(_lib.lbps_halo_unpack(h, int(row0), int(rows), ctypes.c_void_p(d_buf), int(nbytes)), "lbps_halo_unpack")
+
+
+def lbps_set_origin(h, row0):
+    _check(_lib.lbps_set_origin(h, int(row0)), "lbps_set_origin")
 
 
 # ---- convenience wrapper --------------------------------------------------

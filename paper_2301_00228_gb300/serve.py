@@ -12,8 +12,10 @@ times and serves them as they arrive:
   in chunks no longer than the shortest remaining solve, so every solve stops
   exactly at its step count; a solve that is alone on the device is stepped
   directly (lbps_step, the single-lattice kernels and their launch shape);
-* completion: finished solves are read out (their u fields) and freed, and
-  the batch is rebuilt with the waiting requests that now fit;
+* completion: finished solves leave the batch at the chunk boundary; they
+  are read out (their u fields) and freed while the next chunk runs, and
+  requests that arrive meanwhile are created and initialised then too (on
+  streams of their own, beside the batch's), joining at the next boundary;
 * cancellation: a request withdrawn by its client (``cancel_at``) leaves the
   queue, or the batch at the next chunk boundary, and its memory is freed.
 
@@ -88,10 +90,10 @@ def footprint(d, storage="f32"):
     return lbps.lbps_state_bytes(_params(d, storage))
 
 
-def _lattice(d, storage, u0=None):
+def _lattice(d, storage, u0=None, stream=None):
     lat = lbps.Lattice.rectangle(d.nx, d.ny, d.lam, d.mu, d.edge_type, np.asarray(d.edge_value, float).ravel(),
                                  periodic_x=d.periodic_x, periodic_y=d.periodic_y, a0_phi=d.a0_phi,
-                                 storage=storage)
+                                 storage=storage, stream=stream)
     ux, uy = u0 if u0 is not None else d.displacement()
     return lat.init(ux, uy)
 
@@ -112,53 +114,101 @@ class _Clock:
             time.sleep(min(dt, 0.01))
 
 
+def _streams():
+    """(a function giving each new lattice a stream, the batch stream):
+    non-blocking CUDA streams from torch's pool, so that new solves are
+    created, initialised and read out, and a lone solve is stepped, while a
+    chunk of the batch runs (the legacy default stream would wait for it);
+    no streams without a GPU."""
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.Stream, torch.cuda.Stream()
+    except ImportError:
+        pass
+    return (lambda: None), None
+
+
 def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fields=True, tuning=None,
                   clock=time.perf_counter, prepared=None):
     """Continuous batching.  ``prepared[rid]`` may hold (ux, uy) host arrays
-    computed beforehand (input generation kept out of the timed run)."""
+    computed beforehand (input generation kept out of the timed run).
+
+    While a chunk runs on the device the host admits the requests that have
+    arrived and fit (creating and initialising their lattices on a stream of
+    their own; they join the batch at the next chunk boundary) and reads out
+    the solves that finished in the chunk before."""
     reqs = sorted(requests, key=lambda r: r.arrival)
     for r in reqs:
         if footprint(r.domain, storage) > budget_bytes:
             raise ValueError(f"request {r.rid} needs more device memory than the whole budget")
+    new_stream, batch_stream = _streams()
     clk = _Clock(clock)
     rep = Report()
-    waiting, active = [], []     # active: [request, lattice, remaining, admitted]
-    nxt = 0
-    used = 0
+    waiting = []                 # arrived, not admitted
+    ready = []                   # admitted and initialised: [request, lattice, remaining, admitted]
+    active = []                  # advancing together (the batch, or one lattice alone)
+    finished = []                # stepped to the end, not read out yet
+    state = {"next": 0, "used": 0}
     batch = None
     batch_members = ()
-    while nxt < len(reqs) or waiting or active:
+
+    def arrivals():
         now = clk.now()
-        while nxt < len(reqs) and reqs[nxt].arrival <= now:
-            waiting.append(reqs[nxt])
-            nxt += 1
-        # withdrawn requests leave the queue, or the batch (at this chunk
+        while state["next"] < len(reqs) and reqs[state["next"]].arrival <= now:
+            waiting.append(reqs[state["next"]])
+            state["next"] += 1
+        # withdrawn requests leave the queue, or the device (at a chunk
         # boundary), and give their memory back
         for r in [r for r in waiting if r.cancelled_by(now)]:
             waiting.remove(r)
             rep.cancelled.append(r.rid)
-        for a in [a for a in active if a[0].cancelled_by(now)]:
-            active.remove(a)
-            a[1].close()
-            used -= footprint(a[0].domain, storage)
-            rep.cancelled.append(a[0].rid)
-        # admit in arrival order while memory is left
+
+    def admit():
         while waiting:
             need = footprint(waiting[0].domain, storage)
-            if used + need > budget_bytes:
+            if state["used"] + need > budget_bytes:
                 break
             r = waiting.pop(0)
             u0 = prepared.get(r.rid) if prepared else None
-            active.append([r, _lattice(r.domain, storage, u0), r.steps, clk.now()])
-            used += need
-        rep.peak_bytes = max(rep.peak_bytes, used)
+            ready.append([r, _lattice(r.domain, storage, u0, stream=new_stream()), r.steps, clk.now()])
+            state["used"] += need
+            rep.peak_bytes = max(rep.peak_bytes, state["used"])
+
+    def read_out():
+        for r, lat, _, admitted in finished:
+            res = Result(r.rid, r.arrival, admitted, 0.0)
+            if keep_fields:
+                res.ux, res.uy = lat.read("ux"), lat.read("uy")
+            else:
+                lat.norms("ux")
+            res.completed = clk.now()
+            rep.results.append(res)
+            state["used"] -= footprint(r.domain, storage)
+            lat.close()
+        finished.clear()
+
+    while state["next"] < len(reqs) or waiting or ready or active or finished:
+        arrivals()
+        now = clk.now()
+        for group in (ready, active):
+            for a in [a for a in group if a[0].cancelled_by(now)]:
+                group.remove(a)
+                a[1].close()
+                state["used"] -= footprint(a[0].domain, storage)
+                rep.cancelled.append(a[0].rid)
+        admit()
+        active.extend(ready)
+        ready.clear()
         rep.max_active = max(rep.max_active, len(active))
         if not active:
+            read_out()
             if batch is not None:  # the last members were withdrawn
                 batch.close()
                 batch, batch_members = None, ()
-            if nxt < len(reqs):
-                clk.wait_until(reqs[nxt].arrival)
+            if state["next"] < len(reqs) and not waiting:
+                clk.wait_until(reqs[state["next"]].arrival)
             continue
         members = tuple(id(a[1]) for a in active)
         if members != batch_members:
@@ -166,7 +216,7 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
                 batch.close()
                 batch = None
             if len(active) > 1:
-                batch = lbps.Batch([a[1] for a in active])
+                batch = lbps.Batch([a[1] for a in active], stream=batch_stream)
                 if tuning is not None:
                     batch.set_tuning(*tuning)
                 rep.rebuilds += 1
@@ -174,30 +224,26 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
         k = min(max_chunk, min(a[2] for a in active))
         if batch is not None:
             batch.step(k)
-            rc = batch.check()  # waits for the chunk
         else:  # alone on the device: the single-lattice path
-            rc = lbps.lbps_step(active[0][1]._h, k)
+            rc = lbps.lbps_step_async(active[0][1]._h, k)
+            if rc != lbps.LBPS_OK:
+                raise lbps.LbpsError(rc, "serve: lone step")
+        # host work while the chunk runs: results of the previous chunk, new arrivals
+        read_out()
+        arrivals()
+        admit()
+        rc = batch.check() if batch is not None else lbps.lbps_check(active[0][1]._h)  # waits for the chunk
         if rc != lbps.LBPS_OK:
             raise lbps.LbpsError(rc, "serve: chunk check")
         rep.chunks += 1
-        done = [a for a in active if a[2] == k]
         for a in active:
             a[2] -= k
+        done = [a for a in active if a[2] == 0]
         if done:
-            if batch is not None:
-                batch.close()
-            batch, batch_members = None, ()
-            for r, lat, _, admitted in done:
-                res = Result(r.rid, r.arrival, admitted, 0.0)
-                if keep_fields:
-                    res.ux, res.uy = lat.read("ux"), lat.read("uy")
-                else:
-                    lat.norms("ux")
-                res.completed = clk.now()
-                rep.results.append(res)
-                used -= footprint(r.domain, storage)
-                lat.close()
+            finished.extend(done)
             active = [a for a in active if a[2] > 0]
+            if not active and not ready and not waiting:
+                read_out()       # nothing to overlap with
     if batch is not None:
         batch.close()
     rep.makespan = clk.now()

@@ -118,13 +118,20 @@ class Domain:
             uy += dy
         return ux, uy
 
-    def displacement_torch(self, device="cuda"):
-        """u(x, 0) as FP64 torch tensors on ``device`` (same recipe as displacement())."""
+    def displacement_torch(self, device="cuda", rows=None):
+        """u(x, 0) as FP64 torch tensors on ``device`` (same recipe as
+        displacement()); ``rows`` = (first, count): only those rows (wrapped
+        modulo ny, e.g. the rows of one slab of the lattice)."""
         import torch
 
         x = torch.arange(self.nx, dtype=torch.float64, device=device)
-        y = torch.arange(self.ny, dtype=torch.float64, device=device)
-        ux = torch.zeros((self.ny, self.nx), dtype=torch.float64, device=device)
+        if rows is None:
+            y = torch.arange(self.ny, dtype=torch.float64, device=device)
+        else:
+            if self.wave is not None:
+                raise ValueError("plane waves are sampled on the whole lattice")
+            y = torch.remainder(torch.arange(rows[0], rows[0] + rows[1], device=device), self.ny).to(torch.float64)
+        ux = torch.zeros((y.numel(), self.nx), dtype=torch.float64, device=device)
         uy = torch.zeros_like(ux)
         for (cx, cy, sg, amp, kind) in self.pulses:
             X = (x - cx)[None, :]

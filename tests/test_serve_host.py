@@ -31,7 +31,7 @@ class FakeLattice:
 class FakeBatch:
     built = []
 
-    def __init__(self, lats):
+    def __init__(self, lats, stream=None):
         assert len(lats) > 1, "a lone solve is stepped directly"
         self.lats = list(lats)
         FakeBatch.built.append(tuple(l.d.rid for l in lats))
@@ -64,7 +64,7 @@ class StepClock:
 def fakes(monkeypatch):
     lats = []
 
-    def make(d, storage, u0=None):
+    def make(d, storage, u0=None, stream=None):
         lats.append(FakeLattice(d))
         return lats[-1]
 
@@ -76,7 +76,8 @@ def fakes(monkeypatch):
     monkeypatch.setattr(S, "_lattice", make)
     monkeypatch.setattr(S, "footprint", lambda d, storage="f32": d.bytes)
     monkeypatch.setattr(S.lbps, "Batch", FakeBatch)
-    monkeypatch.setattr(S.lbps, "lbps_step", lone_step)
+    monkeypatch.setattr(S.lbps, "lbps_step_async", lone_step)
+    monkeypatch.setattr(S.lbps, "lbps_check", lambda h: 0)
     return lats
 
 
