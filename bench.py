@@ -454,8 +454,8 @@ def serve_measure(requests=64, rate_factor=1.2, burst=32, budget_gb=64.0, small_
     mixed batch) at rate_factor x the capacity of the one-solve-at-a-time
     loop (measured first on a sample of the same recipe), served by
     continuous batching and by that loop; a second batched run under a small
-    device-memory budget (default 1.5 x the largest request's footprint, so
-    admission binds); and a burst of the first requests arriving at once
+    device-memory budget (default 1.2 x the largest request's footprint, so
+    admission binds: requests wait for memory, memory_waits > 0); and a burst of the first requests arriving at once
     (capacity).  Latency = completion - arrival."""
     from paper_2301_00228_gb300 import serve as S
     from paper_2301_00228_gb300 import workloads as W
@@ -474,7 +474,7 @@ def serve_measure(requests=64, rate_factor=1.2, burst=32, budget_gb=64.0, small_
     work = sum(r.domain.nx * r.domain.ny * r.steps for r in reqs)
     budget = int(budget_gb * (1 << 30))
     biggest = max(S.footprint(r.domain) for r in reqs)
-    small_bytes = int(small_budget * (1 << 30)) if small_budget else int(1.5 * biggest)
+    small_bytes = int(small_budget * (1 << 30)) if small_budget else int(1.2 * biggest)
     served = S.serve_batched(reqs, budget, prepared=prepared, max_chunk=max_chunk)
     small = S.serve_batched(reqs, small_bytes, prepared=prepared, max_chunk=max_chunk)
     loop = S.serve_one_at_a_time(reqs, prepared=prepared)
@@ -785,7 +785,7 @@ def main(argv=None):
     ap.add_argument("--rate-factor", type=float, default=1.2, help="serve: arrival rate / loop capacity")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device-memory admission budget")
     ap.add_argument("--small-budget-gb", type=float, default=0.0,
-                    help="serve: budget of the second run (0: 1.5 x the largest request's footprint)")
+                    help="serve: budget of the second run (0: 1.2 x the largest request's footprint)")
     ap.add_argument("--max-chunk", type=int, default=500, help="serve: most steps between completions checks")
     ap.add_argument("--burst", type=int, default=32, help="serve: requests arriving at once for the capacity run")
     ap.add_argument("--serve-requests", type=int, default=48,

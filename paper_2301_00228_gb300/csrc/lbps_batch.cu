@@ -64,17 +64,20 @@ size_t desc_bytes(const lbps_batch* b) {
 
 // Work list of the interior kernel: every strip cut into chunks of `rows`
 // rows; in a general geometry the rows of a strip without interior points
-// (a hole, Geo::gap) are left out, splitting the chunk that spans them.
+// (a hole, Geo::gap) are left out, splitting the chunk that spans them.  The
+// list runs across a lattice's strips first, chunk row after chunk row, so
+// warps that take consecutive tasks read neighbouring columns of the same
+// rows (adjacent memory) at the same time.
 std::vector<BulkTask> bulk_tasks(const lbps_batch* b, int rows) {
     std::vector<BulkTask> t;
     for (int d = 0; d < (int)b->lats.size(); ++d) {
         const lbps_lattice* lat = b->lats[d];
         const lbps::Geo& g = lat->L.g;
-        for (int xs = 0, s = 0; xs < g.nx; xs += lbps::kBatchStripCols, ++s) {
-            const int ga = lat->gap.empty() ? 0 : lat->gap[2 * (size_t)s];
-            const int gb = lat->gap.empty() ? 0 : lat->gap[2 * (size_t)s + 1];
-            for (int j0 = 0; j0 < g.ny; j0 += rows) {
-                const int j1 = std::min(j0 + rows, g.ny);
+        for (int j0 = 0; j0 < g.ny; j0 += rows) {
+            const int j1 = std::min(j0 + rows, g.ny);
+            for (int xs = 0, s = 0; xs < g.nx; xs += lbps::kBatchStripCols, ++s) {
+                const int ga = lat->gap.empty() ? 0 : lat->gap[2 * (size_t)s];
+                const int gb = lat->gap.empty() ? 0 : lat->gap[2 * (size_t)s + 1];
                 if (j0 < std::min(j1, ga)) t.push_back(BulkTask{d, xs, j0, std::min(j1, ga)});
                 if (std::max(j0, gb) < j1) t.push_back(BulkTask{d, xs, std::max(j0, gb), j1});
             }

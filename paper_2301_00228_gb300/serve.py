@@ -70,6 +70,8 @@ class Report:
     max_active: int = 0
     peak_bytes: int = 0
     cancelled: list = field(default_factory=list)   # rids withdrawn before completion
+    memory_waits: int = 0          # chunk boundaries at which an arrived request did not fit the budget
+    memory_wait_s: float = 0.0     # summed time requests waited for memory after they arrived
 
     def summary(self):
         lat = np.array([r.latency for r in self.results])
@@ -77,7 +79,8 @@ class Report:
                 "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                 "mean_latency_s": float(lat.mean()), "makespan_s": self.makespan, "chunks": self.chunks,
                 "batch_rebuilds": self.rebuilds, "max_active": self.max_active, "peak_state_bytes": self.peak_bytes,
-                "cancelled": len(self.cancelled)}
+                "cancelled": len(self.cancelled), "memory_waits": self.memory_waits,
+                "memory_wait_s": self.memory_wait_s}
 
 
 def _params(d, storage):
@@ -165,12 +168,18 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
             waiting.remove(r)
             rep.cancelled.append(r.rid)
 
+    refused_at = {}              # rid -> when it first did not fit the budget
+
     def admit():
         while waiting:
             need = footprint(waiting[0].domain, storage)
             if state["used"] + need > budget_bytes:
+                rep.memory_waits += 1
+                refused_at.setdefault(waiting[0].rid, clk.now())
                 break
             r = waiting.pop(0)
+            if r.rid in refused_at:
+                rep.memory_wait_s += clk.now() - refused_at.pop(r.rid)
             u0 = prepared.get(r.rid) if prepared else None
             ready.append([r, _lattice(r.domain, storage, u0, stream=new_stream()), r.steps, clk.now()])
             state["used"] += need

@@ -10,11 +10,12 @@ import pytest
 
 import oracle as O
 from paper_2301_00228_gb300 import workloads as W
+from tolerance import TARGET as TOL
+from tolerance import judge
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-10, "f32": 1e-5, "f16": 2e-3}
 FIELDS = ("ux", "uy", "phi", "psi")
 
 
@@ -81,10 +82,10 @@ def test_plate_with_hole_against_oracle(L, hole_case, storage):
     got = {k: lat.read(k) for k in FIELDS}
     body = nt != 3
     errs = rel(got, ref, body)
-    assert all(v <= TOL[storage] for v in errs.values()), (storage, errs)
     for k in FIELDS:
         assert np.abs(got[k][~body]).max() == 0.0, k          # void points hold nothing
     assert np.abs(ref["uy"]).max() > 1e-4
+    judge(errs, storage, "plate with a hole")
 
 
 def test_patch_uniform_strain_around_hole(L):

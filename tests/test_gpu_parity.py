@@ -1,13 +1,11 @@
 """Parity of the CUDA time loop with the FP64 oracle, through the C ABI.
 
-Tolerances: FP64 population storage must match the oracle to round-off
-(relative L2 <= 1e-10 per field); FP32 storage within relative L2 <= 1e-5 per
-field.  The 16-bit formats (FP32 moments, 16-bit non-equilibrium sums) are
-held to what they deliver on these runs, which is not the 1e-3 target
-everywhere: FP16 stays below 1e-3 except on the a_0 = 0.9 periodic case
-(1.7e-3 in u), BF16 reaches 1.4e-2 there and about 1e-3 to 8e-3 elsewhere
-(its 8-bit significand).  The 1e-3 target on the precision workload is
-asserted in test_gpu_precision.py.  Relative L2 is taken per field against max(||ref||, 1e-2 ||ref group||)
+Tolerances (tests/tolerance.py): FP64 population storage must match the
+oracle to round-off (relative L2 <= 1e-10 per field); FP32 storage within
+relative L2 <= 1e-5 per field; the 16-bit formats within 1e-3, a run that
+misses it being reported as an expected failure with its measured error (the
+format's precision limit) as long as it stays below a regression bound.
+Relative L2 is taken per field against max(||ref||, 1e-2 ||ref group||)
 where the groups are (ux, uy), (vx, vy), (phi, psi), so a field that is zero
 by symmetry is compared on the scale of its partner.
 """
@@ -17,12 +15,13 @@ import pytest
 import oracle as O
 import hand_cases as H
 from paper_2301_00228_gb300 import workloads as W
+from tolerance import TARGET as TOL
+from tolerance import judge
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 GROUPS = (("ux", "uy"), ("vx", "vy"), ("phi", "psi"))
-TOL = {"f64": 1e-10, "f32": 1e-5, "bf16": 2e-2, "f16": 2e-3}
 
 
 @pytest.fixture(scope="module")
@@ -42,8 +41,12 @@ def rel_errors(got, ref):
     return out
 
 
-def assert_parity(got, ref, tol, what=""):
+def assert_parity(got, ref, tol, what="", storage=None):
+    """Every field within tol; with a 16-bit storage named, a miss within the
+    format's known limit is an expected failure (tests/tolerance.py)."""
     errs = rel_errors(got, ref)
+    if storage in ("bf16", "f16"):
+        return judge(errs, storage, what)
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, (what, bad, errs)
     return errs
@@ -157,7 +160,7 @@ def test_mixed_rectangles(L, k, storage, jmode):
             run_gpu(L, cs, storage)
         assert e.value.code == L.LBPS_ERR_INVALID
         return
-    assert_parity(run_gpu(L, cs, storage), run_oracle(cs), TOL[storage], (k, storage))
+    assert_parity(run_gpu(L, cs, storage), run_oracle(cs), TOL[storage], (k, storage), storage)
 
 
 # ------------------------------------------------- the 64 x 64 problem
@@ -173,7 +176,7 @@ def test_square_64_1000_steps(L, storage):
     ref = O.OracleLattice(64, 64, 1.0, 1.0, node_type=nt, bc_value=bv).init(ux, uy).step(d.steps).fields()
     lat = L.Lattice.rectangle(64, 64, 1.0, 1.0, d.edge_type, ev, storage=storage)
     got = lat.init(ux, uy).step(d.steps).fields()
-    assert_parity(got, ref, TOL[storage])
+    assert_parity(got, ref, TOL[storage], "square_64", storage)
 
 
 # ------------------------------------------- full size: periodic waves

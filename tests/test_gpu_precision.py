@@ -4,31 +4,26 @@ equilibrium in BF16 or FP16, FP32 arithmetic.
 
 Parity with the FP64 oracle, relative L2 per field (u_x, u_y, phi, psi)
 taken as in the FP32/FP64 parity tests (a field that vanishes by symmetry is
-measured on its partner's scale).  Targets: 1e-5 for FP32 storage, 1e-3 for
-16-bit storage.  FP16 meets 1e-3 on the many-pulse crop; BF16 (8-bit
-significand, stochastic rounding) misses it on the smaller 256^2 crop and
-neither format meets it on the 10^4-step periodic waves, so those runs
-assert the bound they do meet, stated beside each (measured values in the
-comments; the runs are deterministic).  Plus: the storage scale the
-library picks, overflow reported as a non-finite state, host and device
-initialisation identical, batches bit-identical to single lattices.
+measured on its partner's scale).  Targets (tests/tolerance.py): 1e-5 for
+FP32 storage, 1e-3 for 16-bit storage.  A 16-bit run that misses 1e-3 is an
+expected failure with its measured error (the format's precision limit; the
+runs are deterministic): BF16 (8-bit significand) on the 256^2 crop
+(1.7e-3) and on the 10^4-step periodic waves (9.0e-3), FP16 on the waves
+(1.2e-3).  BF16 meets 1e-3 on the 1024^2 crop of the precision workload
+(bench.py --precision).  Plus: the storage scale the library picks,
+overflow reported as a non-finite state, host and device initialisation
+identical.
 """
 import numpy as np
 import pytest
 
 import oracle as O
 from paper_2301_00228_gb300 import workloads as W
+from tolerance import judge
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {"f32": 1e-5, "bf16": 1e-3, "f16": 1e-3}
-# bounds met where the target is not (measured: 256^2 crop bf16 1.7e-3 in
-# phi; periodic 10^4 steps f16 4.7e-3, bf16 9.0e-3, both in u_y).  On the
-# 1024^2 crop of the precision workload (5000 steps, bench.py --precision)
-# bf16 meets 1e-3 (9.0e-4) with its stochastic rounding.
-CROP_BF16 = 3e-3
-WAVES = {"f16": 2e-3, "bf16": 2e-2}   # measured 1.2e-3 and 9.0e-3 (stochastic rounding at a_0 = 0.9999)
 GROUPS = (("ux", "uy"), ("phi", "psi"))
 
 
@@ -49,10 +44,12 @@ def rel_errors(got, ref):
     return out
 
 
-def check(got, ref, tol, what):
+def check(got, ref, storage, what):
+    """FP32 within 1e-5; a 16-bit format within 1e-3, or an expected failure
+    within its known limit (tests/tolerance.py)."""
     errs = rel_errors(got, ref)
-    assert all(v <= tol for v in errs.values()), (what, errs)
-    return errs
+    print(f"{what}: rel-L2 {errs}")
+    return judge(errs, storage, what)
 
 
 def pulse_crop(side, steps):
@@ -83,9 +80,9 @@ def test_pulse_crop_against_oracle(L, crop_case, storage):
                               storage=storage)
     lat.init(ux, uy).step(c.steps)
     assert lat.check() == 0
-    errs = check({k: lat.read(k) for k in ref}, ref, CROP_BF16 if storage == "bf16" else TOL[storage], storage)
-    print(f"256^2 pulse crop, {c.steps} steps, {storage}: rel-L2 {errs}, scale 2^{lat.scale_exp}")
+    got = {k: lat.read(k) for k in ref}
     lat.close()
+    check(got, ref, storage, f"256^2 pulse crop, {c.steps} steps, {storage}")
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
@@ -101,8 +98,7 @@ def test_periodic_waves_16bit(L, storage):
     lat.init(ux, uy).step(d.steps)
     ex = standing_wave_expected(d.nx, d.ny, m, n, amp_d, amp_s, d.lam, d.mu, d.rho, lat.a_phi, lat.a_psi, lat.dt,
                                 d.steps)
-    errs = check({k: lat.read(k) for k in ("ux", "uy", "phi", "psi")}, ex, WAVES[storage], storage)
-    print(f"periodic 1024^2 x 1e4 steps, {storage}: rel-L2 {errs}")
+    check({k: lat.read(k) for k in ("ux", "uy", "phi", "psi")}, ex, storage, f"periodic 1024^2 x 1e4 steps, {storage}")
 
 
 @pytest.mark.parametrize("storage", ["bf16", "f16"])
@@ -113,11 +109,11 @@ def test_sync_16bit(L, storage):
     ref = O.OracleLattice(nx, ny, 1.5, 1.0, a0_phi=0.99, node_type=nt, bc_value=bv).init(ux, uy).step(13).sync()
     lat = L.Lattice.rectangle(nx, ny, 1.5, 1.0, (2, 1, 1, 1), np.zeros(8), a0_phi=0.99, storage=storage)
     lat.init(ux, uy).step(13).sync()
-    check({k: lat.read(k) for k in ("ux", "uy", "phi", "psi")}, ref.fields(), TOL[storage], storage)
     # after a synchronisation phi, psi are the differences of u up to the
     # rounding of the stored deviations
     scale = np.abs(ref.fields()["phi"]).max()
     assert lat.read("consistency").max() <= 1e-3 * scale
+    check({k: lat.read(k) for k in ("ux", "uy", "phi", "psi")}, ref.fields(), storage, f"sync, {storage}")
 
 
 def test_scale_choice(L):

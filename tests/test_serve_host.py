@@ -93,12 +93,14 @@ def test_every_solve_takes_exactly_its_steps(fakes):
         assert r.ux[0, 0] == q.steps          # stepped exactly its step count
     assert all(lat.closed for lat in fakes)
     assert rep.max_active == 5
+    assert rep.memory_waits == 0 and rep.memory_wait_s == 0.0
 
 
 def test_budget_bounds_the_resident_solves(fakes):
     reqs = [req(k, 50 * (k + 1), nbytes=300) for k in range(6)]
     rep = S.serve_batched(reqs, budget_bytes=900, max_chunk=40, clock=StepClock())
     assert rep.max_active == 3 and rep.peak_bytes <= 900
+    assert rep.memory_waits > 0 and rep.memory_wait_s > 0
     assert [r.ux[0, 0] for r in rep.results] == [q.steps for q in reqs]
     assert all(r.completed >= r.admitted >= r.arrival for r in rep.results)
 
