@@ -661,7 +661,10 @@ def run_gpu(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    lbps.lbps_profile(lat._h, 1)
+    # per-kernel CUDA events around every launch of the timed steps; with
+    # --graphs the timed steps replay captured step pairs instead (no events
+    # inside), and the kernel timings come from a window of steps after them
+    lbps.lbps_profile(lat._h, 0 if args.graphs else 1)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -674,6 +677,9 @@ def run_gpu(args):
         raise SystemExit(f"step failed: {lbps.lbps_strerror(rc)}")
     if lat.check() != 0:
         raise SystemExit("state became non-finite")
+    if args.graphs:
+        lbps.lbps_profile(lat._h, 1)
+        lat.step(min(args.steps, 200))
     prof = lbps.lbps_profile_read(lat._h)
     lbps.lbps_profile(lat._h, 0)
     seconds = e0.elapsed_time(e1) / 1000.0
@@ -703,14 +709,16 @@ def run_gpu(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "bulk_kernel", "peak_source": peak_kind,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": bulk_avg_s * 1000.0,
-                "share_of_step_time": bulk_ms / args.steps / (1000.0 * seconds / args.steps),
+                "share_of_step_time": bulk_ms / bulk_n / (1000.0 * seconds / args.steps),
+                "kernel_timing": "a window after the timed steps (--graphs)" if args.graphs
+                else "CUDA events around every launch of the timed steps",
                 "timed_boundary_passes_ms_per_step": bnd_ms / args.steps,
                 "boundary_newmark_pass": "beside the interior kernel on a second stream, not timed"}
     bounded = not (d.periodic_x and d.periodic_y)
     # per step: boundary Newmark, interior, boundary reset (a periodic lattice
     # has no boundary); per synchronisation: the sync kernel and the refresh
     # of the boundary mirror
-    gpu_launches = int(bulk_n) * (3 if bounded else 1) + (
+    gpu_launches = args.steps * (3 if bounded else 1) + (
         (args.steps // sync_every) * (2 if bounded else 1) if sync_every else 0)
 
     # end to end through the C ABI with host buffers
@@ -802,6 +810,9 @@ def main(argv=None):
     ap.add_argument("--precision-steps", type=int, default=5000)
     ap.add_argument("--sync-every", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1000)
+    ap.add_argument("--graphs", action="store_true",
+                    help="time the steps as lbps_step runs them for a caller (pairs replayed from CUDA graphs) "
+                         "and take the per-kernel timings from a window after them")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)

@@ -406,6 +406,60 @@ int run_step(lbps_lattice* lat) {
     return LBPS_OK;
 }
 
+void drop_graphs(lbps_lattice* lat) {
+    for (int q = 0; q < 2; ++q) {
+        if (lat->graph[q]) cudaGraphExecDestroy(lat->graph[q]);
+        lat->graph[q] = nullptr;
+        lat->graph_gen[q] = -1;
+    }
+}
+
+// The graph of two steps starting from the current copy: captured once (for
+// the current parameters, launch shape and storage scale: anything that
+// changes them bumps lat->gen), then replayed.  The capture runs run_step
+// twice on the capture stream; the host-side copy index and step count it
+// advances are put back.
+int pair_graph(lbps_lattice* lat, cudaGraphExec_t* out) {
+    const int q = lat->cur;
+    if (lat->graph[q] && lat->graph_gen[q] == lat->gen) {
+        *out = lat->graph[q];
+        return LBPS_OK;
+    }
+    if (lat->graph[q]) cudaGraphExecDestroy(lat->graph[q]);
+    lat->graph[q] = nullptr;
+    if (!lat->cap && cudaStreamCreateWithFlags(&lat->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        lat->cap = nullptr;
+        cudaGetLastError();
+        return LBPS_ERR_CUDA;
+    }
+    cudaStream_t saved = lat->st;
+    const int64_t steps = lat->steps;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(lat->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        lat->last_cuda = (int)e;
+        return LBPS_ERR_CUDA;
+    }
+    lat->st = lat->cap;
+    int rc = run_step(lat);
+    if (rc == LBPS_OK) rc = run_step(lat);
+    lat->st = saved;
+    lat->cur = q;
+    lat->steps = steps;
+    e = cudaStreamEndCapture(lat->cap, &g);
+    if (rc == LBPS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&lat->graph[q], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (rc != LBPS_OK || e != cudaSuccess) {
+        lat->graph[q] = nullptr;
+        if (e != cudaSuccess) lat->last_cuda = (int)e;
+        cudaGetLastError();
+        return LBPS_ERR_CUDA;
+    }
+    lat->graph_gen[q] = lat->gen;
+    *out = lat->graph[q];
+    return LBPS_OK;
+}
+
 int run_sync(lbps_lattice* lat) {
     cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
         using P = decltype(pol);
@@ -811,11 +865,28 @@ int lbps_step_async(lbps_lattice* lat, int64_t n) {
     lbps::NvtxRange nvtx("lbps_step_async");
     if (!lat || n < 0) return LBPS_ERR_INVALID;
     if (!lat->initialised) return LBPS_ERR_STATE;
-    for (int64_t s = 0; s < n; ++s) {
-        int rc = run_step(lat);
-        if (rc != LBPS_OK) return rc;
-        if (lat->p.sync_every > 0 && lat->steps % lat->p.sync_every == 0) {
-            rc = run_sync(lat);
+    const int l = lat->p.sync_every;
+    for (int64_t s = 0; s < n;) {
+        // two steps at once from a graph, unless per-kernel timing is on or a
+        // synchronisation falls after the first of them
+        if (n - s >= 2 && !lat->prof && !(l > 0 && (lat->steps + 1) % l == 0)) {
+            cudaGraphExec_t g = nullptr;
+            int rc = pair_graph(lat, &g);
+            if (rc != LBPS_OK) return rc;
+            cudaError_t e = cudaGraphLaunch(g, lat->st);
+            if (e != cudaSuccess) {
+                lat->last_cuda = (int)e;
+                return LBPS_ERR_CUDA;
+            }
+            lat->steps += 2;
+            s += 2;
+        } else {
+            int rc = run_step(lat);
+            if (rc != LBPS_OK) return rc;
+            s += 1;
+        }
+        if (l > 0 && lat->steps % l == 0) {
+            int rc = run_sync(lat);
             if (rc != LBPS_OK) return rc;
         }
     }
@@ -1040,6 +1111,7 @@ int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp) {
         return LBPS_ERR_INVALID;
     lat->tuning.variant = variant;
     lat->tuning.rows_per_warp = rows_per_warp;
+    lat->gen += 1;  // captured step graphs use the old launch shape
     return LBPS_OK;
 }
 
@@ -1168,6 +1240,8 @@ int lbps_set_stream(lbps_lattice* lat, void* cuda_stream) {
 
 void lbps_destroy(lbps_lattice* lat) {
     if (!lat) return;
+    drop_graphs(lat);
+    if (lat->cap) cudaStreamDestroy(lat->cap);
     if (lat->side) {
         cudaStreamSynchronize(lat->side);
         cudaStreamDestroy(lat->side);

@@ -841,12 +841,10 @@ __global__ void copy_segments_kernel(CopySegs s) {
     uint4* b = reinterpret_cast<uint4*>(s.dst[q]);
     const size_t n16 = s.bytes[q] / 16;
     for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < n16; t += (size_t)gridDim.x * blockDim.x) {
-        if (s.pack) {
-            const uint4 v = LBPS_LD(&a[t]);
-            b[t] = v;
-        } else {
-            LBPS_ST(&b[t], a[t]);
-        }
+#ifdef LBPS_CHECKED
+        if (!chk_ok(s.pack ? &a[t] : &b[t], __LINE__)) continue;
+#endif
+        b[t] = a[t];
     }
 }
 

@@ -67,6 +67,13 @@ struct lbps_lattice {
     // ordered by the fork/join events (null: the pass runs on st)
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // two time steps captured as a CUDA graph, one per starting copy, replayed
+    // by lbps_step for pairs of steps (captured on `cap`, a stream of the
+    // lattice's own, since the legacy default stream cannot be captured);
+    // valid while graph_gen == gen
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_gen[2] = {-1, -1};
     char* mem;
     bool owns;
     int cur;            // copy holding time t

@@ -134,3 +134,13 @@ def test_general_geometry_host_checks(lib):
     q = lib.lbps_params(nx, ny, 1.0, 1.0, 1.0, 1.0, 0.999, 0, 0, 0, 0, lib.LBPS_STORAGE_F16, 0, None)
     with pytest.raises(lib.LbpsError):
         lib.lbps_state_bytes_cells(q, two, None)
+
+
+def test_checked_build_compiles():
+    """The range-checked build (LBPS_CHECKED, the sanitizer stand-in the GPU
+    tests run) compiles from the same sources (host-side cross-compilation,
+    no GPU)."""
+    from paper_2301_00228_gb300 import build as B
+
+    lib = B.build(checked=True)
+    assert lib.exists() and lib.name == "liblbps_checked.so"

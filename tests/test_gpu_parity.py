@@ -516,3 +516,33 @@ def test_tiny_every_boundary_mix(L, size, edges, jmode):
         got = lat.init(ux, uy).step(40).fields()
         lat.close()
         assert_parity(got, ref, TOL[storage], (size, et, storage))
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_step_graphs_same_bits(L, storage):
+    """lbps_step replays pairs of steps from captured CUDA graphs (one per
+    starting copy); with per-kernel timing on it launches every kernel
+    itself.  Both give the same bits, across synchronisation points (every
+    7th step), a changed launch shape and a load schedule set between calls
+    (which make the graphs be captured again)."""
+    cs = mixed_case(31, 71, 53, steps=0, a0=0.99)
+    ev = cs["ev"]
+
+    def run(timed):
+        lat = L.Lattice.rectangle(cs["nx"], cs["ny"], cs["lam"], 1.0, cs["et"], ev, a0_phi=cs["a0"], storage=storage,
+                                  sync_every=7)
+        L.lbps_profile(lat._h, int(timed))
+        lat.init(cs["ux"], cs["uy"])
+        lat.step(1).step(10).step(5)
+        L.lbps_set_tuning(lat._h, 5, 16)
+        lat.step(9)
+        lat.set_load(L.LBPS_NEUMANN, 20 * lat.dt, 40 * lat.dt)
+        lat.step(30).step(2)
+        out = {k: lat.read(k) for k in ("ux", "uy", "vx", "vy", "f_phi", "f_psi")}
+        assert lat.steps == 57
+        lat.close()
+        return out
+
+    a, b = run(False), run(True)
+    for k in a:
+        assert np.array_equal(a[k], b[k]), (storage, k)
