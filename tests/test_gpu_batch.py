@@ -87,6 +87,26 @@ def test_batch_tuning_and_interleaved_single_steps(L):
     b.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "f64", "f16"])
+def test_batch_every_launch_shape_same_bits(L, storage):
+    """Register pipelines and shared-memory rings, with short and long row
+    chunks: the same bits as the lattices stepped on their own."""
+    ds = domains(11, 6, lo=5, hi=90)
+    solo = [make(L, d, storage).step(21) for d in ds]
+    for variant in range(8):
+        for rows in (8, 40):
+            lats = [make(L, d, storage) for d in ds]
+            b = L.Batch(lats)
+            b.set_tuning(variant, rows)
+            b.step(21)
+            assert b.check() == 0
+            for q, (x, y) in enumerate(zip(lats, solo)):
+                assert_same(x, y, (storage, variant, rows, q))
+            b.close()
+            for x in lats:
+                x.close()
+
+
 def test_batch_against_oracle(L):
     ds = domains(9, 5, lo=12, hi=60, periodic=False)
     lats = [make(L, d, "f64") for d in ds]
