@@ -49,6 +49,23 @@ def pulse_displacement(nx, ny, cx, cy, sigma, amp, kind="dilatation", dh=1.0, x0
     raise ValueError(kind)
 
 
+def bump_displacement(nx, ny, cx, cy, radius, amp, kind="dilatation", x0=0, y0=0):
+    """A displacement bump of compact support centred at (cx, cy): magnitude
+    amp (r/R)(1 - (r/R)^2)^3 for r < R = radius, zero beyond, along e_r
+    (dilatation) or e_theta (rotation); sampled on the nx x ny window whose
+    first point is (x0, y0)."""
+    x = np.arange(x0, x0 + nx, dtype=np.float64) - cx
+    y = np.arange(y0, y0 + ny, dtype=np.float64) - cy
+    X, Y = np.meshgrid(x, y)
+    q = np.hypot(X, Y) / radius
+    g = np.where(q < 1.0, amp * (1.0 - q * q) ** 3, 0.0) / radius  # magnitude / r
+    if kind == "dilatation":
+        return g * X, g * Y
+    if kind == "rotation":
+        return -g * Y, g * X
+    raise ValueError(kind)
+
+
 def plane_wave_displacement(nx, ny, m, n, amp_d, amp_s):
     """u = amp_d khat sin(k.x) + amp_s khat_perp sin(k.x), k = 2 pi (m/nx, n/ny)."""
     kx, ky = 2.0 * math.pi * m / nx, 2.0 * math.pi * n / ny

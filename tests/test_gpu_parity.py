@@ -240,6 +240,57 @@ def test_many_pulses_full_size_sampled(L):
             assert np.abs(g[k] - e[k]).max() <= 2e-6 * scale + 1e-18, ((si, sj), k)
 
 
+def test_full_size_corner_bumps_long_run(L):
+    """8192 x 8192 (clamped bottom, traction-free other edges, lambda/mu = 3) from
+    three bumps of compact support: two at corners, one on the top edge.  After
+    S = 120 steps the state can differ from zero only within 5 S points of a
+    bump (the widening bound of the sampled test above), so (a) every point
+    outside those regions is exactly zero on the GPU, over the whole lattice,
+    and (b) inside them the GPU equals the oracle run on a crop around each
+    region (cut edges traction-free, beyond the reach of the bumps), point for
+    point: the boundary reset and the corners after many steps at full size."""
+    d = W.many_pulses(steps=120)
+    S, rad = d.steps, 6
+    reach = 5 * S + rad + 8
+    centres = [(rad, rad, "dilatation"), (d.nx - 1 - rad, d.ny - 1 - rad, "rotation"),
+               (4000, d.ny - 1 - rad, "dilatation")]
+    ux = np.zeros((d.ny, d.nx))
+    uy = np.zeros((d.ny, d.nx))
+    boxes = []
+    for cx, cy, kind in centres:
+        x0, x1 = max(0, cx - reach), min(d.nx, cx + reach + 1)
+        y0, y1 = max(0, cy - reach), min(d.ny, cy + reach + 1)
+        bx, by = W.bump_displacement(x1 - x0, y1 - y0, cx, cy, rad, 1e-3, kind, x0=x0, y0=y0)
+        ux[y0:y1, x0:x1] += bx
+        uy[y0:y1, x0:x1] += by
+        boxes.append((x0, x1, y0, y1))
+    ev = np.asarray(d.edge_value, float).ravel()
+    lat = L.Lattice.rectangle(d.nx, d.ny, d.lam, d.mu, d.edge_type, ev, storage="f32")
+    lat.init(ux, uy).step(S)
+    inside = torch.zeros((d.ny, d.nx), dtype=torch.bool, device="cuda")
+    for x0, x1, y0, y1 in boxes:
+        inside[y0:y1, x0:x1] = True
+    got = {}
+    for k in ("ux", "uy", "phi", "psi"):
+        t = lat.read_device(k)
+        assert int(torch.count_nonzero(t[~inside])) == 0, k
+        got[k] = [t[y0:y1, x0:x1].cpu().numpy() for x0, x1, y0, y1 in boxes]
+        del t
+    lat.close()
+    for b, (x0, x1, y0, y1) in enumerate(boxes):
+        w, h = x1 - x0, y1 - y0
+        et = [d.edge_type[0] if y0 == 0 else 1, d.edge_type[1] if x1 == d.nx else 1,
+              d.edge_type[2] if y1 == d.ny else 1, d.edge_type[3] if x0 == 0 else 1]
+        nt, bv = O.rect_bc(w, h, et, ev)
+        ref = O.OracleLattice(w, h, d.lam, d.mu, node_type=nt, bc_value=bv).init(
+            ux[y0:y1, x0:x1], uy[y0:y1, x0:x1]).step(S).fields()
+        keys = ("ux", "uy", "phi", "psi")
+        assert all(np.abs(ref[k]).max() > 0 for k in keys), b
+        assert_parity({k: got[k][b] for k in keys}, {k: ref[k] for k in keys}, TOL["f32"], what=("bump", b))
+        for k in keys:
+            assert np.abs(got[k][b] - ref[k]).max() <= TOL["f32"] * np.abs(ref[k]).max(), (b, k)
+
+
 # ----------------------------------------------------------- edge cases
 
 def _small(L, **kw):
