@@ -388,8 +388,11 @@ def run_batch(args):
     interior = sum((d.nx - 2) * (d.ny - 2) for d in ds)
     b = lbps.Batch(lats)
     if args.batch_tuning:  # a fixed launch shape (profiling), no tuner
-        variant, rows = (int(x) for x in args.batch_tuning.split(","))
+        shape = [int(x) for x in args.batch_tuning.split(",")]
+        variant, rows = shape[:2]
         b.set_tuning(variant, rows)
+        if len(shape) > 2:
+            b.set_graph_steps(shape[2])
         tuned_ms = None
     else:
         variant, rows, tuned_ms = b.tune(repeats=5)
@@ -432,7 +435,8 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f64" if args.storage == "f64" else "f32", "data": "synthetic",
             "config": {"workload": f"mixed_batch_{len(ds)}", "domains": len(ds), "sides": "U{64..512}",
                        "points": points, "storage": args.storage, "l2": "state larger than L2",
-                       "tuned": {"variant": variant, "rows_per_warp": rows, "ms_per_step": tuned_ms}},
+                       "tuned": {"variant": variant, "rows_per_warp": rows, "graph_steps": b.graph_steps,
+                                 "ms_per_step": tuned_ms}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "whole batched step",
                          "peak_source": peak_kind},
@@ -646,6 +650,9 @@ def run_gpu(args):
         lat = lbps.Lattice(d.nx, d.ny, d.lam, d.mu, d.rho, periodic_x=True, periodic_y=True, **mk)
     else:
         lat = lbps.Lattice.rectangle(d.nx, d.ny, d.lam, d.mu, et, ev, **mk)
+    if args.tuning:  # a fixed launch shape of the interior kernel (profiling a smaller lattice like a larger)
+        variant, rows = (int(x) for x in args.tuning.split(","))
+        lbps.lbps_set_tuning(lat._h, variant, rows)
     ux, uy = d.displacement_torch("cuda")
     lat.init(ux, uy)
     torch.cuda.synchronize()
@@ -766,7 +773,7 @@ def run_gpu(args):
                 "config": {"workload": wname, **describe(d), "storage": args.storage,
                            "displacement": "f64", "sync_every": sync_every,
                            "l2": "state larger than L2" if alg_bytes > 1.3e8 else "state fits L2",
-                           "replicas_per_gpu": 1},
+                           "replicas_per_gpu": 1, **({"tuning": args.tuning} if args.tuning else {})},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clock}
         if precision is not None:
@@ -801,7 +808,9 @@ def main(argv=None):
     ap.add_argument("--serve-burst", type=int, default=24, help="serving section: burst requests")
     ap.add_argument("--batch-count", type=int, default=256, help="domains of the batch workload")
     ap.add_argument("--batch-tuning", default=None,
-                    help="batch: launch shape 'variant,rows' instead of running the autotuner")
+                    help="batch: launch shape 'variant,rows[,steps per graph]' instead of running the autotuner")
+    ap.add_argument("--tuning", default=None,
+                    help="lattice workloads: interior-kernel launch shape 'variant,rows' instead of the default")
     ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")
     ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16", "f16"])
     ap.add_argument("--precision", action="store_true",

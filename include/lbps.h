@@ -277,8 +277,9 @@ int lbps_norms_noalloc(const double* d_x, const double* d_ref, size_t n, void* c
  * launch of the interior kernel, a persistent grid whose warps take strips
  * of every lattice from a work list (the same per-point arithmetic as
  * lbps_step, so every lattice gets the same bits as when stepped alone).
- * Pairs of steps are captured once into a CUDA graph and replayed.  The
- * paper has no counterpart; this serves many solves at once. */
+ * Blocks of k steps (k even; 2 unless set or tuned) are captured once into
+ * a CUDA graph and replayed.  The paper has no counterpart; this serves many
+ * solves at once. */
 typedef struct lbps_batch lbps_batch; /* opaque, library-owned */
 
 /* lats[count]: distinct, initialised lattices, all of one storage format,
@@ -304,10 +305,20 @@ int lbps_batch_check(lbps_batch* b);
  * 6-blocks-per-SM variants spill there). */
 int lbps_batch_set_tuning(lbps_batch* b, int32_t variant, int32_t rows_per_warp);
 
+/* Steps per replayed CUDA graph: k even, 2..64 (LBPS_ERR_INVALID
+ * otherwise).  lbps_batch_step(n) replays floor(n / k) graphs of k steps,
+ * then pairs, then launches a last odd step directly.  Results do not depend
+ * on it.  lbps_batch_graph_steps returns the current k. */
+int lbps_batch_set_graph_steps(lbps_batch* b, int32_t k);
+int lbps_batch_graph_steps(const lbps_batch* b);
+
 /* Autotuner: times one step for each launch shape (variants 0, 1, 2, 4, 5,
- * 6 x rows 8, 16, 32, 64, 128), repeats times each, keeps the fastest and
- * reports it.  Leaves every lattice's state unchanged (a step is a pure function of
- * the copy it reads; the timed steps only rewrite the same next state). */
+ * 6 x rows 8, 16, 32, 64, 128), repeats times each, keeps the fastest; then,
+ * for that shape, times graphs of k = 2, 4, 8, 16, 32 steps (a longer graph
+ * must be 1 % faster per step) and keeps the fastest k.  ms_per_step is the
+ * time per step replayed from that graph.  Leaves every lattice's state
+ * unchanged (a step is a pure function of the copy it reads; the timed steps
+ * only rewrite the same next state, and the step counters are put back). */
 int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* rows_per_warp,
                     double* ms_per_step);
 
@@ -378,9 +389,18 @@ int lbps_check_report(uint64_t out[2]);
  * (0: 6 blocks of 128 threads per SM, 1: 5, 2: 4, 3: 8) with u, du/dt loaded
  * two rows ahead; 4..7 the same budgets loading them one row ahead.
  * rows_per_warp (1..4096) is the number of rows each warp marches over.
- * Defaults: variant 0; 32 rows, or 16 or 8 on lattices too small to give the
+ * Defaults: variant 0 (variant 2 for FP64 storage, which needs more
+ * registers); 32 rows, or 16 or 8 on lattices too small to give the
  * interior kernel 16384 warps at 32 (below about 4096^2). */
 int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);
+
+/* Steps per CUDA graph of lbps_step: k even, 2..64 (LBPS_ERR_INVALID
+ * otherwise; default 32).  lbps_step captures k consecutive steps once per
+ * starting state copy and replays them; what is left of n (or a block a
+ * synchronisation would split) runs as pairs from a 2-step graph or as
+ * direct launches.  Results do not depend on it; a larger k saves launch
+ * time on small lattices. */
+int lbps_set_graph_steps(lbps_lattice* lat, int32_t k);
 
 /* Per-kernel timing for roofline reports.  enable != 0 starts recording CUDA
  * events on the lattice's stream around the interior kernel of every step

@@ -117,7 +117,7 @@ KC<T> make_kc(double a_phi, double a_psi, double cd2, double cs2, double dh) {
     k.scale = (T)1;
     k.sr = 0;
     k.inv_scale = (T)1;
-    k.key0 = 0;
+    k.key4 = 0;
     return k;
 }
 
@@ -407,26 +407,29 @@ int run_step(lbps_lattice* lat) {
 }
 
 void drop_graphs(lbps_lattice* lat) {
-    for (int q = 0; q < 2; ++q) {
-        if (lat->graph[q]) cudaGraphExecDestroy(lat->graph[q]);
-        lat->graph[q] = nullptr;
-        lat->graph_gen[q] = -1;
-    }
+    for (int w = 0; w < 2; ++w)
+        for (int q = 0; q < 2; ++q) {
+            if (lat->graph[w][q]) cudaGraphExecDestroy(lat->graph[w][q]);
+            lat->graph[w][q] = nullptr;
+            lat->graph_gen[w][q] = -1;
+        }
 }
 
-// The graph of two steps starting from the current copy: captured once (for
-// the current parameters, launch shape and storage scale: anything that
-// changes them bumps lat->gen), then replayed.  The capture runs run_step
-// twice on the capture stream; the host-side copy index and step count it
-// advances are put back.
-int pair_graph(lbps_lattice* lat, cudaGraphExec_t* out) {
+// The graph of k steps (2, or lat->graph_k) starting from the current copy:
+// captured once (for the current parameters, launch shape, storage scale and
+// graph_k: anything that changes them bumps lat->gen), then replayed.  The
+// capture runs run_step k times on the capture stream; the host-side copy
+// index and step count it advances are put back.
+int step_graph(lbps_lattice* lat, int k, cudaGraphExec_t* out) {
     const int q = lat->cur;
-    if (lat->graph[q] && lat->graph_gen[q] == lat->gen) {
-        *out = lat->graph[q];
+    const int w = k == 2 ? 0 : 1;
+    cudaGraphExec_t& slot = lat->graph[w][q];
+    if (slot && lat->graph_gen[w][q] == lat->gen) {
+        *out = slot;
         return LBPS_OK;
     }
-    if (lat->graph[q]) cudaGraphExecDestroy(lat->graph[q]);
-    lat->graph[q] = nullptr;
+    if (slot) cudaGraphExecDestroy(slot);
+    slot = nullptr;
     if (!lat->cap && cudaStreamCreateWithFlags(&lat->cap, cudaStreamNonBlocking) != cudaSuccess) {
         lat->cap = nullptr;
         cudaGetLastError();
@@ -441,22 +444,22 @@ int pair_graph(lbps_lattice* lat, cudaGraphExec_t* out) {
         return LBPS_ERR_CUDA;
     }
     lat->st = lat->cap;
-    int rc = run_step(lat);
-    if (rc == LBPS_OK) rc = run_step(lat);
+    int rc = LBPS_OK;
+    for (int s = 0; s < k && rc == LBPS_OK; ++s) rc = run_step(lat);
     lat->st = saved;
     lat->cur = q;
     lat->steps = steps;
     e = cudaStreamEndCapture(lat->cap, &g);
-    if (rc == LBPS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&lat->graph[q], g, 0);
+    if (rc == LBPS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&slot, g, 0);
     if (g) cudaGraphDestroy(g);
     if (rc != LBPS_OK || e != cudaSuccess) {
-        lat->graph[q] = nullptr;
+        slot = nullptr;
         if (e != cudaSuccess) lat->last_cuda = (int)e;
         cudaGetLastError();
         return LBPS_ERR_CUDA;
     }
-    lat->graph_gen[q] = lat->gen;
-    *out = lat->graph[q];
+    lat->graph_gen[w][q] = lat->gen;
+    *out = slot;
     return LBPS_OK;
 }
 
@@ -780,6 +783,10 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
                 break;
             }
         lat->tuning.rows_per_warp = rows;
+        // FP64 populations need 128 registers a thread: the 6-blocks-per-SM
+        // variant spills there, the 4-blocks one does not (8192^2: 12.2
+        // against 9.6 GLUPS; the FP64 arithmetic bounds either)
+        if (params->storage == LBPS_STORAGE_F64) lat->tuning.variant = 2;
     }
     // the side stream of the boundary Newmark pass; if it cannot be had, the
     // pass runs on the lattice's stream (same results, no overlap)
@@ -867,19 +874,22 @@ int lbps_step_async(lbps_lattice* lat, int64_t n) {
     if (!lat->initialised) return LBPS_ERR_STATE;
     const int l = lat->p.sync_every;
     for (int64_t s = 0; s < n;) {
-        // two steps at once from a graph, unless per-kernel timing is on or a
-        // synchronisation falls after the first of them
-        if (n - s >= 2 && !lat->prof && !(l > 0 && (lat->steps + 1) % l == 0)) {
+        // graph_k steps at once from a graph, else 2, unless per-kernel timing
+        // is on or a synchronisation falls after one of the first k - 1 of them
+        int k = 0;
+        for (int c : {lat->graph_k, 2})
+            if (k == 0 && n - s >= c && !lat->prof && !(l > 0 && l - lat->steps % l < c)) k = c;
+        if (k > 0) {
             cudaGraphExec_t g = nullptr;
-            int rc = pair_graph(lat, &g);
+            int rc = step_graph(lat, k, &g);
             if (rc != LBPS_OK) return rc;
             cudaError_t e = cudaGraphLaunch(g, lat->st);
             if (e != cudaSuccess) {
                 lat->last_cuda = (int)e;
                 return LBPS_ERR_CUDA;
             }
-            lat->steps += 2;
-            s += 2;
+            lat->steps += k;
+            s += k;
         } else {
             int rc = run_step(lat);
             if (rc != LBPS_OK) return rc;
@@ -1115,6 +1125,13 @@ int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp) {
     return LBPS_OK;
 }
 
+int lbps_set_graph_steps(lbps_lattice* lat, int32_t k) {
+    if (!lat || k < 2 || k > 64 || (k & 1)) return LBPS_ERR_INVALID;
+    lat->graph_k = k;
+    lat->gen += 1;  // captured step graphs hold the old number of steps
+    return LBPS_OK;
+}
+
 int lbps_profile(lbps_lattice* lat, int32_t enable) {
     if (!lat) return LBPS_ERR_INVALID;
     lat->prof = enable != 0;
@@ -1226,7 +1243,7 @@ int lbps_halo_unpack(lbps_lattice* lat, int32_t row0, int32_t rows, const void* 
 
 int lbps_set_origin(lbps_lattice* lat, int64_t row0) {
     if (!lat) return LBPS_ERR_INVALID;
-    lat->kf.key0 = (unsigned)((uint64_t)row0 * (uint64_t)lat->L.g.px);
+    lat->kf.key4 = (unsigned)((uint64_t)row0 * (uint64_t)lat->L.g.px * 4u);
     lat->gen += 1;  // batches holding this lattice re-read its descriptor
     return LBPS_OK;
 }

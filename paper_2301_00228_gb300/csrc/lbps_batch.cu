@@ -1,7 +1,7 @@
 // Batches of lattices (lbps_batch_* in include/lbps.h): every lattice of a
 // batch advances by one launch of each boundary pass and one launch of the
-// interior kernel per time step, driven by device-side work lists; pairs of
-// steps are captured once in a CUDA graph and replayed.
+// interior kernel per time step, driven by device-side work lists; blocks of
+// k steps (k even, tuned) are captured once in a CUDA graph and replayed.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -29,9 +29,11 @@ struct lbps_batch {
     // kernel), u one row ahead, 16-row chunks; the fastest or within 3 % of
     // it on mixed batches of 64-2048-point sides (lbps_batch_tune refines it)
     int variant = 5, rows = 16;
+    int graph_k = 2;              // steps per replayed graph (even)
     std::vector<int> uploaded_cur;
     std::vector<int64_t> uploaded_gen;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;    // graph_k steps
+    cudaGraphExec_t pair = nullptr;     // 2 steps (what is left of n after the k-step blocks)
     cudaEvent_t order = nullptr;  // orders the batch stream with the lattices' streams
     cudaStream_t side = nullptr;  // boundary stress and Newmark passes, beside the interior kernel
     cudaEvent_t fork = nullptr, join = nullptr;
@@ -160,23 +162,26 @@ cudaError_t launch_step(lbps_batch* b, int parity) {
 
 void drop_graph(lbps_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->pair) cudaGraphExecDestroy(b->pair);
     b->graph = nullptr;
+    b->pair = nullptr;
 }
 
-// Captures two steps (parity 0 then 1) as one graph.
-int capture(lbps_batch* b) {
-    drop_graph(b);
+// Captures k steps as one graph: parities 0, 1, 0, 1, ... (k even, so the
+// current copy is the same after it), or with `repeat` the parity-0 step k
+// times (the autotuner's timing graph, which rewrites the same next state).
+int capture(lbps_batch* b, int k, bool repeat, cudaGraphExec_t* out) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail(b, e);
-    cudaError_t e1 = launch_step(b, 0);
-    if (e1 == cudaSuccess) e1 = launch_step(b, 1);
+    cudaError_t e1 = cudaSuccess;
+    for (int q = 0; q < k && e1 == cudaSuccess; ++q) e1 = launch_step(b, repeat ? 0 : q & 1);
     e = cudaStreamEndCapture(b->st, &g);
     if (e1 != cudaSuccess) e = e1;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        b->graph = nullptr;
+        *out = nullptr;
         return fail(b, e);
     }
     return LBPS_OK;
@@ -277,15 +282,23 @@ int lbps_batch_step(lbps_batch* b, int64_t n) {
     }
     int rc = refresh(b);
     if (rc != LBPS_OK) return rc;
-    if (n >= 2 && !b->graph) {
-        rc = capture(b);
-        if (rc != LBPS_OK) return rc;
+    // blocks of graph_k steps, then pairs, then a last single step
+    int64_t q = 0;
+    if (b->graph_k > 2 && n >= b->graph_k) {
+        if (!b->graph && (rc = capture(b, b->graph_k, false, &b->graph)) != LBPS_OK) return rc;
+        for (; q + b->graph_k <= n; q += b->graph_k) {
+            cudaError_t e = cudaGraphLaunch(b->graph, b->st);
+            if (e != cudaSuccess) return fail(b, e);
+        }
     }
-    for (int64_t q = 0; q + 1 < n; q += 2) {
-        cudaError_t e = cudaGraphLaunch(b->graph, b->st);
-        if (e != cudaSuccess) return fail(b, e);
+    if (n - q >= 2) {
+        if (!b->pair && (rc = capture(b, 2, false, &b->pair)) != LBPS_OK) return rc;
+        for (; q + 2 <= n; q += 2) {
+            cudaError_t e = cudaGraphLaunch(b->pair, b->st);
+            if (e != cudaSuccess) return fail(b, e);
+        }
     }
-    if (n & 1) {
+    if (q < n) {
         cudaError_t e = launch_step(b, 0);
         if (e != cudaSuccess) return fail(b, e);
     }
@@ -313,6 +326,15 @@ int lbps_batch_check(lbps_batch* b) {
         if (f) return LBPS_ERR_NONFINITE;
     return LBPS_OK;
 }
+
+int lbps_batch_set_graph_steps(lbps_batch* b, int32_t k) {
+    if (!b || k < 2 || k > 64 || (k & 1)) return LBPS_ERR_INVALID;
+    b->graph_k = k;
+    drop_graph(b);
+    return LBPS_OK;
+}
+
+int lbps_batch_graph_steps(const lbps_batch* b) { return b ? b->graph_k : LBPS_ERR_INVALID; }
 
 int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* rows_per_warp, double* ms_per_step) {
     lbps::NvtxRange nvtx("lbps_batch_tune");
@@ -376,9 +398,50 @@ int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* r
     drop_graph(b);
     rc = upload(b);
     if (rc != LBPS_OK) return rc;
+    // Steps per graph for that launch shape: k repeats of the parity-0 step
+    // captured as one graph, replayed `repeats` times (the same next state
+    // again; the step counters are put back below).
+    float best_g = -1.0f;
+    int bk = b->graph_k;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(b, cudaGetLastError());
+    for (int k : {2, 4, 8, 16, 32}) {
+        cudaGraphExec_t g = nullptr;
+        rc = capture(b, k, true, &g);
+        if (rc != LBPS_OK) break;
+        cudaError_t e = cudaGraphLaunch(g, b->st);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->st);
+        for (int q = 0; q < repeats && e == cudaSuccess; ++q) e = cudaGraphLaunch(g, b->st);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        cudaGraphExecDestroy(g);
+        if (e != cudaSuccess) {
+            rc = fail(b, e);
+            break;
+        }
+        ms /= (float)(repeats * k);
+        if (best_g < 0.0f || ms < 0.99f * best_g) {  // a longer graph must win by 1 %
+            best_g = ms;
+            bk = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (size_t d = 0; d < b->lats.size() && rc == LBPS_OK; ++d) {
+        cudaError_t e = cudaMemcpyAsync(b->lats[d]->tstep(), &taken[d], sizeof(taken[d]), cudaMemcpyHostToDevice,
+                                        b->st);
+        if (e != cudaSuccess) rc = fail(b, e);
+    }
+    if (rc == LBPS_OK) {
+        cudaError_t e = cudaStreamSynchronize(b->st);
+        if (e != cudaSuccess) rc = fail(b, e);
+    }
+    if (rc != LBPS_OK) return rc;
+    b->graph_k = bk;
     if (variant) *variant = bv;
     if (rows_per_warp) *rows_per_warp = br;
-    if (ms_per_step) *ms_per_step = best;
+    if (ms_per_step) *ms_per_step = best_g;
     return LBPS_OK;
 }
 

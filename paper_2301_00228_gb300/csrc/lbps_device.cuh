@@ -98,8 +98,9 @@ struct KC {
     T r[2];                     // a / a_0 (16-bit storage: equilibrium pair sum 2 r f^0)
     T scale, inv_scale;         // 2^e, 2^-e applied to the stored 16-bit Nx, Ny
     unsigned sr;                // 16-bit storage: round the stored sums stochastically (f2bits_store)
-    unsigned key0;              // added to a point's plane offset to form its rounding key (a
-                                // sub-lattice of a larger one sets its first row's offset there)
+    unsigned key4;              // 4 x the offset added to a point's plane offset to form its
+                                // rounding key (a sub-lattice of a larger one sets its first
+                                // row's offset there)
 };
 
 // One state copy: the population planes (layout set by the storage policy P),
@@ -498,6 +499,16 @@ struct PopNeq16 {
                                                      unsigned key, bool sr) {
         return f2bits_store<H>(mul_rn(fma_rn(-2.0f * r, f0, pair_sum), scale), key, sr);
     }
+    // Rounding key of slot (0..3: 2 set + pair) at plane offset p:
+    // 4 (p + offset) + slot.  The empty asm keeps the compiler from folding
+    // the offset into loop-invariant sums held in registers (which made the
+    // 6-blocks-per-SM interior kernel spill); the offset stays a kernel
+    // parameter read where it is added.
+    __device__ __forceinline__ static unsigned key_of(size_t p, unsigned slot, const KC<float>& k) {
+        unsigned x = (unsigned)p * 4u + slot;
+        asm("" : "+r"(x));
+        return x + k.key4;
+    }
     __device__ __forceinline__ static void load_raw(const float* __restrict__ f, size_t plane, size_t p, bool ok,
                                                     Raw& r) {
         const unsigned* w = words(f, plane);
@@ -544,11 +555,11 @@ struct PopNeq16 {
             LBPS_ST(f + (size_t)(s * 3) * plane + p, x[s][0]);
             LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, sub_rn(x[s][1], x[s][3]));
             LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, sub_rn(x[s][2], x[s][4]));
-            wx |= enc_n(add_rn(x[s][1], x[s][3]), x[s][0], k.r[s], k.scale, ((unsigned)p + k.key0) * 4u + 2u * s,
+            wx |= enc_n(add_rn(x[s][1], x[s][3]), x[s][0], k.r[s], k.scale, key_of(p, 2u * s, k),
                         k.sr)
                   << (16 * s);
             wy |= enc_n(add_rn(x[s][2], x[s][4]), x[s][0], k.r[s], k.scale,
-                        ((unsigned)p + k.key0) * 4u + 2u * s + 1u, k.sr)
+                        key_of(p, 2u * s + 1u, k), k.sr)
                   << (16 * s);
         }
         unsigned* w = words(f, plane);
@@ -577,7 +588,7 @@ struct PopNeq16 {
             const float partner = plus ? fma_rn(0.5f, sub_rn(nn, j), rf0) : fma_rn(0.5f, add_rn(nn, j), rf0);
             LBPS_ST(jp, plus ? sub_rn(v[s], partner) : sub_rn(partner, v[s]));
             out |= enc_n(add_rn(v[s], partner), f0, k.r[s], k.scale,
-                         ((unsigned)p + k.key0) * 4u + 2u * s + (unsigned)ax, k.sr)
+                         key_of(p, 2u * s + (unsigned)ax, k), k.sr)
                    << (16 * s);
         }
         LBPS_ST(wp, out);
@@ -607,7 +618,7 @@ struct PopNeq16 {
             r.m[s][1] = (float)jx[s];
             r.m[s][2] = (float)jy[s];
             const float dev = mul_rn(fma_rn(-2.0f * k.r[s], f0, mul_rn(k.two_a[s], sf)), k.scale);
-            w |= f2bits_store<H>(dev, ((unsigned)p + k.key0) * 4u + 2u * s, k.sr) << (16 * s);
+            w |= f2bits_store<H>(dev, key_of(p, 2u * s, k), k.sr) << (16 * s);
         }
         r.w[0] = w;
         r.w[1] = w;

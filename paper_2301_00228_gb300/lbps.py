@@ -91,6 +91,7 @@ def _load():
         "lbps_check_report": (ctypes.c_int, [vp]),
         "lbps_last_cuda_error": (ctypes.c_int, [vp]),
         "lbps_set_tuning": (ctypes.c_int, [vp, i32, i32]),
+        "lbps_set_graph_steps": (ctypes.c_int, [vp, i32]),
         "lbps_profile": (ctypes.c_int, [vp, i32]),
         "lbps_profile_read": (ctypes.c_int, [vp, vp]),
         "lbps_set_stream": (ctypes.c_int, [vp, vp]),
@@ -103,6 +104,8 @@ def _load():
         "lbps_batch_step": (ctypes.c_int, [vp, i64]),
         "lbps_batch_check": (ctypes.c_int, [vp]),
         "lbps_batch_set_tuning": (ctypes.c_int, [vp, i32, i32]),
+        "lbps_batch_set_graph_steps": (ctypes.c_int, [vp, i32]),
+        "lbps_batch_graph_steps": (ctypes.c_int, [vp]),
         "lbps_batch_tune": (ctypes.c_int, [vp, i32, P(i32), P(i32), P(ctypes.c_double)]),
         "lbps_batch_last_cuda_error": (ctypes.c_int, [vp]),
         "lbps_batch_destroy": (None, [vp]),
@@ -276,6 +279,10 @@ def lbps_check_report():
     if rc < 0:
         raise LbpsError(rc, "lbps_check_report")
     return rc, int(out[0]), int(out[1])
+
+
+def lbps_set_graph_steps(h, k):
+    _check(_lib.lbps_set_graph_steps(h, int(k)), "lbps_set_graph_steps")
 
 
 def lbps_set_tuning(h, variant, rows_per_warp):
@@ -466,6 +473,14 @@ def lbps_batch_set_tuning(b, variant, rows_per_warp):
     _check(_lib.lbps_batch_set_tuning(b, int(variant), int(rows_per_warp)), "lbps_batch_set_tuning")
 
 
+def lbps_batch_set_graph_steps(b, k):
+    _check(_lib.lbps_batch_set_graph_steps(b, int(k)), "lbps_batch_set_graph_steps")
+
+
+def lbps_batch_graph_steps(b):
+    return int(_lib.lbps_batch_graph_steps(b))
+
+
 def lbps_batch_tune(b, repeats=3):
     v, r, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0)
     _check(_lib.lbps_batch_tune(b, int(repeats), ctypes.byref(v), ctypes.byref(r), ctypes.byref(ms)),
@@ -499,6 +514,13 @@ class Batch:
 
     def set_tuning(self, variant, rows_per_warp):
         lbps_batch_set_tuning(self._h, variant, rows_per_warp)
+
+    @property
+    def graph_steps(self):
+        return lbps_batch_graph_steps(self._h)
+
+    def set_graph_steps(self, k):
+        lbps_batch_set_graph_steps(self._h, k)
 
     def close(self):
         if getattr(self, "_h", None):

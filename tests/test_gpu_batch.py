@@ -71,6 +71,7 @@ def test_batch_tuning_and_interleaved_single_steps(L):
     b = L.Batch(lats)
     v, r, ms = b.tune(repeats=2)
     assert v in (0, 1, 2, 4, 5, 6) and r in (8, 16, 32, 64, 128) and ms > 0
+    assert b.graph_steps in (2, 4, 8, 16, 32)
     b.step(9)
     lats[2].step(1)        # one lattice stepped on its own in between
     lats[5].step(2)
@@ -145,4 +146,28 @@ def test_batch_rejects_and_reports(L):
     b.step(3)
     assert b.check() == L.LBPS_ERR_NONFINITE
     assert a.check() == 0
+    b.close()
+
+
+@pytest.mark.parametrize("k", [4, 8, 32])
+def test_batch_graph_steps_same_bits(L, k):
+    """Blocks of k steps per graph, then pairs, then an odd step: the same bits
+    as stepping alone, for step counts around and below k."""
+    ds = domains(12, 5, lo=6, hi=70)
+    for n in (1, k - 1, k, 2 * k + 3):
+        solo = [make(L, d, "f32").step(n) for d in ds]
+        lats = [make(L, d, "f32") for d in ds]
+        b = L.Batch(lats)
+        b.set_graph_steps(k)
+        assert b.graph_steps == k
+        b.step(n)
+        assert b.check() == 0
+        for q, (x, y) in enumerate(zip(lats, solo)):
+            assert x.steps == n
+            assert_same(x, y, (k, n, q))
+        b.close()
+    b = L.Batch([make(L, ds[0], "f32")])
+    for bad in (0, 3, 66, -2):
+        with pytest.raises(L.LbpsError):
+            b.set_graph_steps(bad)
     b.close()

@@ -271,7 +271,8 @@ def test_full_size_corner_bumps_long_run(L):
     for x0, x1, y0, y1 in boxes:
         inside[y0:y1, x0:x1] = True
     got = {}
-    for k in ("ux", "uy", "phi", "psi"):
+    keys = ("ux", "uy", "vx", "vy", "phi", "psi")
+    for k in keys:
         t = lat.read_device(k)
         assert int(torch.count_nonzero(t[~inside])) == 0, k
         got[k] = [t[y0:y1, x0:x1].cpu().numpy() for x0, x1, y0, y1 in boxes]
@@ -284,7 +285,6 @@ def test_full_size_corner_bumps_long_run(L):
         nt, bv = O.rect_bc(w, h, et, ev)
         ref = O.OracleLattice(w, h, d.lam, d.mu, node_type=nt, bc_value=bv).init(
             ux[y0:y1, x0:x1], uy[y0:y1, x0:x1]).step(S).fields()
-        keys = ("ux", "uy", "phi", "psi")
         assert all(np.abs(ref[k]).max() > 0 for k in keys), b
         assert_parity({k: got[k][b] for k in keys}, {k: ref[k] for k in keys}, TOL["f32"], what=("bump", b))
         for k in keys:
@@ -571,29 +571,40 @@ def test_tiny_every_boundary_mix(L, size, edges, jmode):
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_step_graphs_same_bits(L, storage):
-    """lbps_step replays pairs of steps from captured CUDA graphs (one per
-    starting copy); with per-kernel timing on it launches every kernel
-    itself.  Both give the same bits, across synchronisation points (every
-    7th step), a changed launch shape and a load schedule set between calls
-    (which make the graphs be captured again)."""
+    """lbps_step replays blocks of k steps (and pairs) from captured CUDA
+    graphs (one per starting copy); with per-kernel timing on it launches
+    every kernel itself.  All give the same bits, for several k, across
+    synchronisation points (every 7th step), a changed launch shape, a load
+    schedule and a changed k set between calls (which make the graphs be
+    captured again)."""
     cs = mixed_case(31, 71, 53, steps=0, a0=0.99)
     ev = cs["ev"]
 
-    def run(timed):
+    def run(timed, k=2):
         lat = L.Lattice.rectangle(cs["nx"], cs["ny"], cs["lam"], 1.0, cs["et"], ev, a0_phi=cs["a0"], storage=storage,
                                   sync_every=7)
         L.lbps_profile(lat._h, int(timed))
+        L.lbps_set_graph_steps(lat._h, k)
         lat.init(cs["ux"], cs["uy"])
         lat.step(1).step(10).step(5)
         L.lbps_set_tuning(lat._h, 5, 16)
         lat.step(9)
         lat.set_load(L.LBPS_NEUMANN, 20 * lat.dt, 40 * lat.dt)
         lat.step(30).step(2)
+        L.lbps_set_graph_steps(lat._h, 2 if k > 2 else 4)
+        lat.step(13)
         out = {k: lat.read(k) for k in ("ux", "uy", "vx", "vy", "f_phi", "f_psi")}
-        assert lat.steps == 57
+        assert lat.steps == 70
         lat.close()
         return out
 
-    a, b = run(False), run(True)
-    for k in a:
-        assert np.array_equal(a[k], b[k]), (storage, k)
+    a = run(True)
+    for k in (2, 4, 6, 16):   # blocks of k steps, split by the synchronisation every 7th step or not
+        b = run(False, k)
+        for f in a:
+            assert np.array_equal(a[f], b[f]), (storage, k, f)
+    lat = L.Lattice(8, 8, 1.0, 1.0, periodic_x=True, periodic_y=True)
+    for bad in (0, 1, 3, 66):
+        with pytest.raises(L.LbpsError):
+            L.lbps_set_graph_steps(lat._h, bad)
+    lat.close()
