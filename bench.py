@@ -737,6 +737,12 @@ def run_gpu(args):
         pin_uy.copy_(uy.cpu())
         out_x = torch.empty((d.ny, d.nx), dtype=torch.float64, pin_memory=True)
         out_y = torch.empty((d.ny, d.nx), dtype=torch.float64, pin_memory=True)
+        # untimed warm-up of the same calls: each init swaps the state copies,
+        # so two passes capture the step graphs of both starting copies
+        for _ in range(2):
+            lbps.lbps_init(lat._h, pin_ux.numpy(), pin_uy.numpy())
+            lbps.lbps_step(lat._h, 64)
+            lbps.lbps_read(lat._h, lbps.LBPS_UX, out_x.numpy())
         barrier()
         t0 = time.perf_counter()
         lbps.lbps_init(lat._h, pin_ux.numpy(), pin_uy.numpy())
@@ -751,7 +757,7 @@ def run_gpu(args):
         e2e = {"value": e2e_ups / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 2 * d.nx * d.ny * 8, "d2h_bytes_per_step": 2 * d.nx * d.ny * 8,
                "step": f"one solve: lbps_init from pinned host u0, lbps_step({args.e2e_steps}), "
-                       f"lbps_read of u_x and u_y into pinned host memory"}
+                       f"lbps_read of u_x and u_y into pinned host memory (after two untimed solves of 64 steps)"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

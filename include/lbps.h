@@ -75,6 +75,10 @@ extern "C" {
 #define LBPS_F_PHI 6            /* the 5 phi populations, [5][ny][nx]          */
 #define LBPS_F_PSI 7            /* the 5 psi populations, [5][ny][nx]          */
 #define LBPS_CONSISTENCY 8      /* error measure e(x,t) of Sec. 4              */
+#define LBPS_KINETIC_ENERGY 9   /* rho |du/dt|^2 / 2 per unit area (0 at void points) */
+#define LBPS_STRAIN_ENERGY 10   /* sigma : eps / 2 = lambda tr(eps)^2 / 2 + mu eps : eps
+                                   (Eq. hooke, eps by the finite differences of
+                                   Sec. 3.1.2; 0 at void points)              */
 
 typedef struct lbps_params {
     int32_t nx, ny;             /* lattice points along x, y; each >= 3       */
@@ -240,10 +244,19 @@ int lbps_read(lbps_lattice* lat, int32_t field, double* dst, size_t count);
 int lbps_read_device(lbps_lattice* lat, int32_t field, double* d_dst, size_t count);
 
 /* FP64 reductions over the lattice for one scalar field (LBPS_UX ..
- * LBPS_PSI, LBPS_CONSISTENCY): out[0] = sum (x - ref)^2, out[1] = sum ref^2,
- * out[2] = sum x, out[3] = max |x|.  d_ref is a device array [ny][nx] or
- * NULL (ref = 0).  Deterministic order.  Synchronises. */
+ * LBPS_PSI, LBPS_CONSISTENCY .. LBPS_STRAIN_ENERGY): out[0] = sum (x - ref)^2,
+ * out[1] = sum ref^2, out[2] = sum x, out[3] = max |x|.  d_ref is a device
+ * array [ny][nx] or NULL (ref = 0).  Deterministic order.  Synchronises. */
 int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out[4]);
+
+/* Energy of the current state in FP64 on the device (a diagnostic; the paper
+ * states the material law, Eq. hooke, and the strain, Eq. strain, but
+ * reports no energy): out[0] = kinetic, out[1] = strain, out[2] = their sum,
+ * each the sum over the body points of the density (LBPS_KINETIC_ENERGY,
+ * LBPS_STRAIN_ENERGY) times dh^2, per unit thickness.  Every body point
+ * counts one square of side dh; boundary cells are not clipped.  Waits for
+ * the lattice's stream. */
+int lbps_energy(lbps_lattice* lat, double out[3]);
 
 /* lbps_norms without any allocation.  The paper has no counterpart: this is
  * a service routine for callers that cannot call cudaMalloc or cudaFree,

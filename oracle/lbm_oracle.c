@@ -714,6 +714,32 @@ int ora_read(ora_lattice* L, int32_t field, double* dst) {
         memcpy(dst, field == ORA_AX ? L->ax : L->ay, (size_t)n * sizeof(double));
         return 0;
     }
+    case ORA_EKIN:
+    case ORA_ESTRAIN: {
+        /* Energy densities per unit area, 0 at void points: rho |v|^2 / 2, and
+         * half the double contraction of the stress (Eq. hooke) with the
+         * strain (Eq. strain), both from the finite differences of u. */
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                long k = at(L, i, j);
+                if (is_void(L, k)) {
+                    dst[k] = 0.0;
+                    continue;
+                }
+                if (field == ORA_EKIN) {
+                    dst[k] = 0.5 * L->p.rho * (L->vx[k] * L->vx[k] + L->vy[k] * L->vy[k]);
+                    continue;
+                }
+                double sig[3];
+                stress(L, L->ux, L->uy, i, j, sig);
+                double exx = d_dx(L, L->ux, i, j);
+                double eyy = d_dy(L, L->uy, i, j);
+                double exy = 0.5 * (d_dy(L, L->ux, i, j) + d_dx(L, L->uy, i, j));
+                dst[k] = 0.5 * (sig[0] * exx + sig[1] * eyy + 2.0 * sig[2] * exy);
+            }
+        }
+        return 0;
+    }
     default: return -1;
     }
 }

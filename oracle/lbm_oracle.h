@@ -90,7 +90,10 @@ enum {
     ORA_PHI = 4, ORA_PSI = 5,
     ORA_F_PHI = 6, ORA_F_PSI = 7,   /* 5 planes each, alpha-major          */
     ORA_ERR = 8,                    /* consistency error e of Sec. 4       */
-    ORA_AX = 9, ORA_AY = 10         /* acceleration the next step would use */
+    ORA_AX = 9, ORA_AY = 10,        /* acceleration the next step would use */
+    ORA_EKIN = 11,                  /* kinetic energy density rho |v|^2 / 2  */
+    ORA_ESTRAIN = 12                /* strain energy density sigma : eps / 2 (Eq. hooke,
+                                       Eq. strain by the finite differences of Sec. 3.1.2) */
 };
 /* Copies a field into dst (nx*ny doubles, 5*nx*ny for population sets). */
 int ora_read(ora_lattice* L, int32_t field, double* dst);

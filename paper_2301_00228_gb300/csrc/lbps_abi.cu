@@ -565,7 +565,7 @@ size_t field_count(const lbps_lattice* lat, int32_t field) {
     return (field == LBPS_F_PHI || field == LBPS_F_PSI) ? 5 * n : n;
 }
 
-bool valid_field(int32_t f) { return f >= LBPS_UX && f <= LBPS_CONSISTENCY; }
+bool valid_field(int32_t f) { return f >= LBPS_UX && f <= LBPS_STRAIN_ENERGY; }
 
 int extract_rows(lbps_lattice* lat, int32_t field, int j0, int rows, double* dst) {
     cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
@@ -977,7 +977,8 @@ int lbps_read(lbps_lattice* lat, int32_t field, double* dst, size_t count) {
 int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out[4]) {
     lbps::NvtxRange nvtx("lbps_norms");
     if (!lat || !out) return LBPS_ERR_INVALID;
-    if (!(field >= LBPS_UX && field <= LBPS_PSI) && field != LBPS_CONSISTENCY) return LBPS_ERR_INVALID;
+    if (!(field >= LBPS_UX && field <= LBPS_PSI) && !(field >= LBPS_CONSISTENCY && field <= LBPS_STRAIN_ENERGY))
+        return LBPS_ERR_INVALID;
     if (!lat->initialised) return LBPS_ERR_STATE;
     cudaError_t e = lbps::with_policy(lat->p.storage, [&](auto pol) {
         using P = decltype(pol);
@@ -987,6 +988,22 @@ int lbps_norms(lbps_lattice* lat, int32_t field, const double* d_ref, double out
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, lat->out4(), 4 * sizeof(double), cudaMemcpyDeviceToHost, lat->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->st);
     return cuda_ok(e);
+}
+
+int lbps_energy(lbps_lattice* lat, double out[3]) {
+    lbps::NvtxRange nvtx("lbps_energy");
+    if (!lat || !out) return LBPS_ERR_INVALID;
+    if (!lat->initialised) return LBPS_ERR_STATE;
+    double n[2][4];
+    for (int q = 0; q < 2; ++q) {
+        int rc = lbps_norms(lat, q == 0 ? LBPS_KINETIC_ENERGY : LBPS_STRAIN_ENERGY, nullptr, n[q]);
+        if (rc != LBPS_OK) return rc;
+    }
+    const double area = lat->p.dh * lat->p.dh;
+    out[0] = n[0][2] * area;
+    out[1] = n[1][2] * area;
+    out[2] = out[0] + out[1];
+    return LBPS_OK;
 }
 
 int lbps_info(const lbps_lattice* lat, double out[6], int64_t* steps_done) {

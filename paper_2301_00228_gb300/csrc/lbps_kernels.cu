@@ -33,7 +33,7 @@ namespace {
 
 enum {
     FLD_UX = 0, FLD_UY = 1, FLD_VX = 2, FLD_VY = 3, FLD_PHI = 4, FLD_PSI = 5,
-    FLD_FPHI = 6, FLD_FPSI = 7, FLD_CONS = 8
+    FLD_FPHI = 6, FLD_FPSI = 7, FLD_CONS = 8, FLD_KIN = 9, FLD_STRAIN = 10
 };
 
 template <typename T>
@@ -732,6 +732,24 @@ __device__ inline double field_value(const Geo& g, const Consts& c, const KCof<P
     case FLD_UX: case FLD_UY: case FLD_VX: case FLD_VY: return A.u[(size_t)field * g.plane + p];
     case FLD_PHI: return moment0_fp64(A, g.plane, p, 0, k);
     case FLD_PSI: return moment0_fp64(A, g.plane, p, 1, k);
+    case FLD_KIN: {
+        // kinetic energy density rho |du/dt|^2 / 2 (0 at void points)
+        if (!body_at(g, i, j)) return 0.0;
+        const double vx = A.u[2 * g.plane + p], vy = A.u[3 * g.plane + p];
+        return 0.5 * c.rho * (vx * vx + vy * vy);
+    }
+    case FLD_STRAIN: {
+        // strain energy density sigma : eps / 2 = lambda tr(eps)^2 / 2 + mu eps : eps
+        // (Eq. hooke with eps of Eq. strain by the finite differences of Sec. 3.1.2)
+        if (!body_at(g, i, j)) return 0.0;
+        const double* ux = A.u;
+        const double* uy = A.u + g.plane;
+        const double exx = ddx(ux, g.px, i, j, g, c.inv2h);
+        const double eyy = ddy(uy, g.px, i, j, g, c.inv2h);
+        const double exy = 0.5 * (ddy(ux, g.px, i, j, g, c.inv2h) + ddx(uy, g.px, i, j, g, c.inv2h));
+        const double tr = exx + eyy;
+        return 0.5 * c.lam * tr * tr + c.mu * (exx * exx + eyy * eyy + 2.0 * exy * exy);
+    }
     default: {
         // consistency error e(x, t) of Sec. 4 (0 at void points)
         if (!body_at(g, i, j)) return 0.0;

@@ -30,9 +30,11 @@ LBPS_ERR_STATE = -6
 
 LBPS_INTERIOR, LBPS_NEUMANN, LBPS_DIRICHLET, LBPS_VOID = 0, 1, 2, 3
 LBPS_STORAGE_F32, LBPS_STORAGE_F64, LBPS_STORAGE_BF16, LBPS_STORAGE_F16 = 0, 1, 2, 3
-LBPS_UX, LBPS_UY, LBPS_VX, LBPS_VY, LBPS_PHI, LBPS_PSI, LBPS_F_PHI, LBPS_F_PSI, LBPS_CONSISTENCY = range(9)
+(LBPS_UX, LBPS_UY, LBPS_VX, LBPS_VY, LBPS_PHI, LBPS_PSI, LBPS_F_PHI, LBPS_F_PSI, LBPS_CONSISTENCY,
+ LBPS_KINETIC_ENERGY, LBPS_STRAIN_ENERGY) = range(11)
 FIELDS = {"ux": LBPS_UX, "uy": LBPS_UY, "vx": LBPS_VX, "vy": LBPS_VY, "phi": LBPS_PHI, "psi": LBPS_PSI,
-          "f_phi": LBPS_F_PHI, "f_psi": LBPS_F_PSI, "consistency": LBPS_CONSISTENCY}
+          "f_phi": LBPS_F_PHI, "f_psi": LBPS_F_PSI, "consistency": LBPS_CONSISTENCY,
+          "kinetic_energy": LBPS_KINETIC_ENERGY, "strain_energy": LBPS_STRAIN_ENERGY}
 STORAGES = {"f32": LBPS_STORAGE_F32, "f64": LBPS_STORAGE_F64, "bf16": LBPS_STORAGE_BF16,
             "f16": LBPS_STORAGE_F16}
 
@@ -81,6 +83,7 @@ def _load():
         "lbps_read": (ctypes.c_int, [vp, i32, vp, sz]),
         "lbps_read_device": (ctypes.c_int, [vp, i32, vp, sz]),
         "lbps_norms": (ctypes.c_int, [vp, i32, vp, vp]),
+        "lbps_energy": (ctypes.c_int, [vp, vp]),
         "lbps_norms_noalloc": (ctypes.c_int, [vp, vp, sz, vp, vp]),
         "lbps_info": (ctypes.c_int, [vp, vp, P(i64)]),
         "lbps_scale_exp": (ctypes.c_int, [vp, P(i32)]),
@@ -219,6 +222,12 @@ def lbps_read(h, field, dst):
 
 def lbps_read_device(h, field, d_dst, count):
     _check(_lib.lbps_read_device(h, int(field), ctypes.c_void_p(d_dst), int(count)), "lbps_read_device")
+
+
+def lbps_energy(h):
+    out = np.zeros(3, np.float64)
+    _check(_lib.lbps_energy(h, _p(out)), "lbps_energy")
+    return out
 
 
 def lbps_norms(h, field, d_ref=0):
@@ -446,6 +455,10 @@ class Lattice:
             ref = ref.contiguous()
             return lbps_norms(self._h, fid, ref.data_ptr())
         return lbps_norms(self._h, fid)
+
+    def energy(self):
+        """(kinetic, strain, total) energy of the current state (FP64, on the device)."""
+        return lbps_energy(self._h)
 
     def fields(self):
         return {k: self.read(k) for k in ("ux", "uy", "vx", "vy", "phi", "psi")}

@@ -755,3 +755,68 @@ def test_bc_j_mode_changes_boundary_moments():
     res = [O.OracleLattice(nx, ny, 1.0, 1.0, a0_phi=0.9, node_type=nt, bc_value=bv, bc_j_mode=jm)
            .init(ux, uy).step(40).read(O.F_PHI) for jm in (0, 1)]
     assert np.abs(res[0] - res[1]).max() > 1e-3 * np.abs(res[0]).max()
+
+
+# ------------------------------------------------- energy densities (diagnostic)
+
+def _closed_form_strain_energy(G, lam, mu):
+    """Strain energy density of the uniform displacement gradient G (plane strain):
+    eps = sym(G), W = lambda tr(eps)^2 / 2 + mu eps : eps, written out by hand."""
+    exx, eyy = G[0][0], G[1][1]
+    exy = 0.5 * (G[0][1] + G[1][0])
+    return 0.5 * lam * (exx + eyy) ** 2 + mu * (exx * exx + eyy * eyy + 2.0 * exy * exy)
+
+
+@pytest.mark.parametrize("geometry", ["rectangle", "hole"])
+def test_energy_density_linear_fields(geometry):
+    """For a linear displacement field the finite differences are exact at every
+    body point (central and one-sided alike), so the strain energy density
+    equals the closed form of the uniform strain everywhere, 0 at void points;
+    an infinitesimal rigid rotation stores none (only the symmetric part of the
+    gradient counts); a uniform velocity gives rho |v|^2 / 2 at every body point."""
+    nx, ny, lam, mu, rho = 23, 19, 1.7, 0.8, 1.3
+    if geometry == "rectangle":
+        nt, bv = O.rect_bc(nx, ny, (2, 1, 1, 1), np.zeros(8))
+        cell = None
+    else:
+        nt, bv, cell = O.disk_cells(nx, ny, 11.3, 9.6, 3.7, (1, 1, 1, 1), np.zeros(8))
+    body = nt != 3
+    G = [[3e-4, -1.2e-4], [2.1e-4, -0.7e-4]]
+    ux, uy = linear_field(nx, ny, G, (1e-4, -2e-4))
+    ux[~body] = 0.0
+    uy[~body] = 0.0
+    vx, vy = np.full((ny, nx), 2e-3), np.full((ny, nx), -1e-3)
+    lat = O.OracleLattice(nx, ny, lam, mu, rho, node_type=nt, bc_value=bv, cell=cell)
+    lat.init(ux, uy, vx, vy)
+    w = lat.read(O.ESTRAIN)
+    want = _closed_form_strain_energy(G, lam, mu)
+    assert want > 0
+    assert np.abs(w[body] - want).max() <= 1e-12 * want
+    assert np.all(w[~body] == 0.0)
+    k = lat.read(O.EKIN)
+    assert np.abs(k[body] - 0.5 * rho * (4e-6 + 1e-6)).max() <= 1e-18
+    assert np.all(k[~body] == 0.0)
+    rot = [[0.0, -4e-4], [4e-4, 0.0]]
+    rx, ry = linear_field(nx, ny, rot)
+    rx[~body] = 0.0
+    ry[~body] = 0.0
+    lat.init(rx, ry)
+    assert np.abs(lat.read(O.ESTRAIN)).max() <= 1e-22
+
+
+def test_energy_density_plane_wave():
+    """u = A e_x sin(k x) on a periodic lattice: the central difference gives
+    eps_xx = A sin(k dh) / dh cos(k x) exactly, so the strain energy density is
+    (lambda / 2 + mu) eps_xx^2 point by point, and its lattice sum is
+    (lambda / 2 + mu) (A sin(k dh) / dh)^2 N / 2 (a full number of periods)."""
+    nx, ny, lam, mu, A = 64, 8, 2.0, 1.0, 1e-3
+    m = 3
+    k = 2 * math.pi * m / nx
+    X = np.tile(np.arange(nx, dtype=float), (ny, 1))
+    lat = O.OracleLattice(nx, ny, lam, mu, periodic_x=True, periodic_y=True)
+    lat.init(A * np.sin(k * X), np.zeros((ny, nx)))
+    w = lat.read(O.ESTRAIN)
+    exx = A * math.sin(k) * np.cos(k * X)
+    assert np.abs(w - (0.5 * lam + mu) * exx ** 2).max() <= 1e-12 * (0.5 * lam + mu) * A * A
+    total = (0.5 * lam + mu) * (A * math.sin(k)) ** 2 * nx * ny / 2
+    assert abs(w.sum() - total) <= 1e-12 * total
