@@ -285,11 +285,12 @@ int lbps_energy(lbps_lattice* lat, double out[3]);
 int lbps_norms_noalloc(const double* d_x, const double* d_ref, size_t n, void* cuda_stream, double out[4]);
 
 /* ---- Batches: many lattices of different sizes, materials and edges
- * advanced together.  Each time step is one launch of each boundary pass
- * (Newmark, reset) over the boundary points of every lattice and one
- * launch of the interior kernel, a persistent grid whose warps take strips
- * of every lattice from a work list (the same per-point arithmetic as
- * lbps_step, so every lattice gets the same bits as when stepped alone).
+ * advanced together.  Each time step is two launches: a persistent grid
+ * whose warps take tasks from one work list (strips of the interior of every
+ * lattice, and groups of 32 boundary points for the Newmark pass), then the
+ * boundary reset over the boundary points of every lattice (the same
+ * per-point arithmetic as lbps_step, so every lattice gets the same bits as
+ * when stepped alone).
  * Blocks of k steps (k even; 2 unless set or tuned) are captured once into
  * a CUDA graph and replayed.  The paper has no counterpart; this serves many
  * solves at once. */

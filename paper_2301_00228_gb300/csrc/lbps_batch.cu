@@ -1,7 +1,8 @@
 // Batches of lattices (lbps_batch_* in include/lbps.h): every lattice of a
-// batch advances by one launch of each boundary pass and one launch of the
-// interior kernel per time step, driven by device-side work lists; blocks of
-// k steps (k even, tuned) are captured once in a CUDA graph and replayed.
+// batch advances by two launches per time step, the persistent kernel (the
+// interior strips and the boundary Newmark pass of every lattice, from one
+// device-side work list) and the boundary reset; blocks of k steps (k even,
+// tuned) are captured once in a CUDA graph and replayed.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -35,8 +36,6 @@ struct lbps_batch {
     cudaGraphExec_t graph = nullptr;    // graph_k steps
     cudaGraphExec_t pair = nullptr;     // 2 steps (what is left of n after the k-step blocks)
     cudaEvent_t order = nullptr;  // orders the batch stream with the lattices' streams
-    cudaStream_t side = nullptr;  // boundary stress and Newmark passes, beside the interior kernel
-    cudaEvent_t fork = nullptr, join = nullptr;
     int last_cuda = 0;
 };
 
@@ -88,16 +87,37 @@ std::vector<BulkTask> bulk_tasks(const lbps_batch* b, int rows) {
     return t;
 }
 
+// The Newmark pass of the boundary points as tasks of the persistent kernel:
+// 32 consecutive entries of the boundary work list each, spread evenly
+// through the strip tasks, so that warps gathering boundary data (latency
+// bound) run among warps streaming the interior (bandwidth bound).
+std::vector<BulkTask> with_newmark_tasks(const std::vector<BulkTask>& strips, int nbnd) {
+    const size_t nn = (size_t)(nbnd + 31) / 32;
+    std::vector<BulkTask> t;
+    t.reserve(strips.size() + nn);
+    size_t q = 0;
+    for (size_t k = 0; k < nn; ++k) {
+        // the k-th Newmark task goes before strip task k * strips / nn
+        const size_t until = nn ? k * strips.size() / nn : 0;
+        for (; q < until; ++q) t.push_back(strips[q]);
+        const int b0 = (int)(32 * k);
+        t.push_back(BulkTask{0, b0, -1, std::min(32, nbnd - b0)});
+    }
+    for (; q < strips.size(); ++q) t.push_back(strips[q]);
+    return t;
+}
+
 // Largest work list for any rows >= 8: ceil(ny / 8) chunks per strip, one of
-// them possibly split in two by the gap.
+// them possibly split in two by the gap, and the Newmark tasks.
 size_t max_bulk_tasks(const lbps_batch* b) {
-    size_t n = 0;
+    size_t n = 0, nbnd = 0;
     for (const lbps_lattice* lat : b->lats) {
         const lbps::Geo& g = lat->L.g;
         const size_t strips = (size_t)(g.nx + lbps::kBatchStripCols - 1) / lbps::kBatchStripCols;
         n += strips * ((size_t)(g.ny + 7) / 8 + 1);
+        nbnd += (size_t)lat->L.nb;
     }
-    return n;
+    return n + (nbnd + 31) / 32;
 }
 
 int fail(lbps_batch* b, cudaError_t e) {
@@ -108,11 +128,11 @@ int fail(lbps_batch* b, cudaError_t e) {
 // (Re)builds the bulk work list for b->rows and the descriptors, in a device
 // block sized for the largest work list the tuner may ask for.
 int upload(lbps_batch* b) {
-    std::vector<BulkTask> bt = bulk_tasks(b, b->rows);
-    if (bt.size() > b->max_bulk) return LBPS_ERR_INVALID;  // cannot happen (see max_bulk_tasks)
     std::vector<BndTask> nt;
     for (int d = 0; d < (int)b->lats.size(); ++d)
         for (int q = 0; q < b->lats[d]->L.nb; ++q) nt.push_back(BndTask{d, q});
+    std::vector<BulkTask> bt = with_newmark_tasks(bulk_tasks(b, b->rows), (int)nt.size());
+    if (bt.size() > b->max_bulk) return LBPS_ERR_INVALID;  // cannot happen (see max_bulk_tasks)
     std::vector<char> host(b->off_bnd + nt.size() * sizeof(BndTask));
     size_t db = desc_bytes(b);
     for (int d = 0; d < (int)b->lats.size(); ++d) {
@@ -137,24 +157,19 @@ int upload(lbps_batch* b) {
 }
 
 // One time step of every lattice: parity 0 reads v[cur], parity 1 v[cur ^ 1].
-// The boundary Newmark pass runs on the side stream beside the interior
-// kernel: it reads copy A and writes only the boundary points' u, du/dt of
-// copy B, which the interior kernel does not touch.  The boundary reset waits
-// for both (it reads the interior kernel's new u and overwrites populations
-// it wrote).
+// Two launches: the persistent kernel runs the interior strips and, among
+// them, the boundary Newmark tasks (those read copy A and write only the
+// boundary points' u, du/dt of copy B, which no strip touches); the boundary
+// reset follows (it reads the new u and overwrites populations the strips
+// wrote).
 cudaError_t launch_step(lbps_batch* b, int parity) {
     const BndTask* bt = reinterpret_cast<const BndTask*>(b->mem + b->off_bnd);
     const BulkTask* wt = reinterpret_cast<const BulkTask*>(b->mem + b->off_bulk);
     return lbps::with_policy(b->storage, [&](auto pol) {
         using P = decltype(pol);
         const DomDesc<P>* dd = reinterpret_cast<const DomDesc<P>*>(b->mem);
-        cudaError_t e = cudaEventRecord(b->fork, b->st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->side, b->fork, 0);
-        if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 1, 2, b->side);
-        if (e == cudaSuccess) e = cudaEventRecord(b->join, b->side);
         unsigned* next = reinterpret_cast<unsigned*>(b->mem + b->off_next);
-        if (e == cudaSuccess) e = lbps::launch_bulk_batch<P>(dd, wt, b->nbulk, parity, b->variant, next, b->st);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->join, 0);
+        cudaError_t e = lbps::launch_bulk_batch<P>(dd, wt, b->nbulk, bt, parity, b->variant, next, b->st);
         if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 2, 3, b->st);
         return e;
     });
@@ -230,10 +245,7 @@ int lbps_batch_create(lbps_lattice* const* lats, int32_t count, void* cuda_strea
         }
         b->own_stream = true;
     }
-    if (cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaEventCreateWithFlags(&b->order, cudaEventDisableTiming) != cudaSuccess) {
         lbps_batch_destroy(b);
         return LBPS_ERR_CUDA;
     }
@@ -450,13 +462,9 @@ int lbps_batch_last_cuda_error(const lbps_batch* b) { return b ? b->last_cuda : 
 void lbps_batch_destroy(lbps_batch* b) {
     if (!b) return;
     if (b->st) cudaStreamSynchronize(b->st);
-    if (b->side) cudaStreamSynchronize(b->side);
     drop_graph(b);
     if (b->mem) cudaFree(b->mem);
     if (b->order) cudaEventDestroy(b->order);
-    if (b->fork) cudaEventDestroy(b->fork);
-    if (b->join) cudaEventDestroy(b->join);
-    if (b->side) cudaStreamDestroy(b->side);
     if (b->own_stream) cudaStreamDestroy(b->st);
     delete b;
 }

@@ -661,7 +661,8 @@ __global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<P>* _
 template <typename P, int MINB, int UVD>
 __global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<P>* __restrict__ dd,
                                                                const BulkTask* __restrict__ tasks, int ntasks,
-                                                               int parity, unsigned* next) {
+                                                               const BndTask* __restrict__ btasks, int parity,
+                                                               unsigned* next) {
     __shared__ DomDesc<P> sd[kWarpsPerBlock];
     const unsigned FULL = 0xffffffffu;
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -672,6 +673,19 @@ __global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<P>*
         t = __shfl_sync(FULL, t, 0);
         if (t >= (unsigned)ntasks) break;  // whole warp
         const BulkTask tk = tasks[t];
+        if (tk.j0 < 0) {
+            // Newmark task (warp-uniform): boundary points tk.xs .. tk.xs +
+            // tk.j1 - 1 of the boundary work list, one per lane.  It reads
+            // copy A and writes only boundary u, du/dt of copy B, which no
+            // strip task touches; the reset pass after this kernel reads them.
+            if (lane < tk.j1) {
+                const BndTask bt = btasks[tk.xs + lane];
+                const DomDesc<P>& d = dd[bt.dom];
+                const int a = d.cur ^ parity;
+                boundary_newmark(d.g, d.c, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.v[a].s, d.tstep, bt.b);
+            }
+            continue;
+        }
         if (tk.dom != cached) {
             __syncwarp();  // every lane is done with the previous descriptor
             const unsigned* src = reinterpret_cast<const unsigned*>(dd + tk.dom);
@@ -893,31 +907,31 @@ int resident_blocks(K kernel) {
 }
 
 template <typename P, int MINB, int UVD>
-cudaError_t launch_bulk_batch_v(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity,
-                                unsigned* next, cudaStream_t st) {
+cudaError_t launch_bulk_batch_v(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, const BndTask* btasks,
+                                int parity, unsigned* next, cudaStream_t st) {
     auto kern = bulk_batch_kernel<P, MINB, UVD>;
     int blocks = resident_blocks(kern);
     if (blocks < 0) return cudaGetLastError();
     blocks = min(blocks, (ntasks + kWarpsPerBlock - 1) / kWarpsPerBlock);
     cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    kern<<<blocks, 32 * kWarpsPerBlock, 0, st>>>(dd, tasks, ntasks, parity, next);
+    kern<<<blocks, 32 * kWarpsPerBlock, 0, st>>>(dd, tasks, ntasks, btasks, parity, next);
     return cudaGetLastError();
 }
 
 template <typename P>
-cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
-                              unsigned* next, cudaStream_t st) {
+cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, const BndTask* btasks,
+                              int parity, int variant, unsigned* next, cudaStream_t st) {
     if (ntasks <= 0) return cudaGetLastError();
     switch (variant) {
-    case 0: return launch_bulk_batch_v<P, 6, 2>(dd, tasks, ntasks, parity, next, st);
-    case 1: return launch_bulk_batch_v<P, 5, 2>(dd, tasks, ntasks, parity, next, st);
-    case 2: return launch_bulk_batch_v<P, 4, 2>(dd, tasks, ntasks, parity, next, st);
-    case 3: return launch_bulk_batch_v<P, 8, 2>(dd, tasks, ntasks, parity, next, st);
-    case 4: return launch_bulk_batch_v<P, 6, 1>(dd, tasks, ntasks, parity, next, st);
-    case 5: return launch_bulk_batch_v<P, 5, 1>(dd, tasks, ntasks, parity, next, st);
-    case 6: return launch_bulk_batch_v<P, 4, 1>(dd, tasks, ntasks, parity, next, st);
-    default: return launch_bulk_batch_v<P, 8, 1>(dd, tasks, ntasks, parity, next, st);
+    case 0: return launch_bulk_batch_v<P, 6, 2>(dd, tasks, ntasks, btasks, parity, next, st);
+    case 1: return launch_bulk_batch_v<P, 5, 2>(dd, tasks, ntasks, btasks, parity, next, st);
+    case 2: return launch_bulk_batch_v<P, 4, 2>(dd, tasks, ntasks, btasks, parity, next, st);
+    case 3: return launch_bulk_batch_v<P, 8, 2>(dd, tasks, ntasks, btasks, parity, next, st);
+    case 4: return launch_bulk_batch_v<P, 6, 1>(dd, tasks, ntasks, btasks, parity, next, st);
+    case 5: return launch_bulk_batch_v<P, 5, 1>(dd, tasks, ntasks, btasks, parity, next, st);
+    case 6: return launch_bulk_batch_v<P, 4, 1>(dd, tasks, ntasks, btasks, parity, next, st);
+    default: return launch_bulk_batch_v<P, 8, 1>(dd, tasks, ntasks, btasks, parity, next, st);
     }
 }
 
@@ -1079,8 +1093,8 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, const KCof<P>& k, View<P
                                          const double*, double*, double*, cudaStream_t);                     \
     template cudaError_t launch_boundary_batch<P>(const DomDesc<P>*, const BndTask*, int, int, int, int,      \
                                                   cudaStream_t);                                              \
-    template cudaError_t launch_bulk_batch<P>(const DomDesc<P>*, const BulkTask*, int, int, int, unsigned*,      \
-                                              cudaStream_t);
+    template cudaError_t launch_bulk_batch<P>(const DomDesc<P>*, const BulkTask*, int, const BndTask*, int, int, \
+                                              unsigned*, cudaStream_t);
 
 LBPS_INSTANTIATE(PopDirect<float>)
 LBPS_INSTANTIATE(PopDirect<double>)

@@ -89,8 +89,8 @@ struct DomDesc {
     int cur;
 };
 
-struct BulkTask {  // one warp: output columns [xs, xs + 30) of rows [j0, j1) of lattice dom
-    int dom, xs, j0, j1;
+struct BulkTask {  // one warp: output columns [xs, xs + 30) of rows [j0, j1) of lattice dom;
+    int dom, xs, j0, j1;  // j0 < 0: the Newmark pass of boundary tasks [xs, xs + j1), j1 <= 32
 };
 
 struct BndTask {   // one thread: boundary point b of lattice dom
@@ -102,11 +102,13 @@ constexpr int kBatchStripCols = 30;  // output columns per warp task
 template <typename P>
 cudaError_t launch_boundary_batch(const DomDesc<P>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
                                   int pass_hi, cudaStream_t st);
-// Interior of every lattice: a persistent grid whose warps take tasks through
-// the counter *next (device memory; the launcher zeroes it on the stream).
+// Interior of every lattice and the Newmark pass of their boundary points: a
+// persistent grid whose warps take tasks (strips, or 32 boundary points of
+// btasks) through the counter *next (device memory; the launcher zeroes it on
+// the stream).
 template <typename P>
-cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, int parity, int variant,
-                              unsigned* next, cudaStream_t st);
+cudaError_t launch_bulk_batch(const DomDesc<P>* dd, const BulkTask* tasks, int ntasks, const BndTask* btasks,
+                              int parity, int variant, unsigned* next, cudaStream_t st);
 
 // Rows of a state copy to or from a caller buffer (domain decomposition):
 // up to kMaxCopySegs contiguous byte ranges, each a multiple of 16 bytes and
