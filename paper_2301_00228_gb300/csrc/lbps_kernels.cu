@@ -360,6 +360,13 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<
     size_t p = (size_t)j * g.px + i;
     const double* ux1 = B.u;
     const double* uy1 = B.u + g.plane;
+    // The populations at t (copy A's boundary mirror, entry b, coalesced
+    // along the boundary list) and the streaming mask, loaded first: nothing
+    // below writes them, and issued here their latency overlaps the
+    // differences and the stress stores instead of following them.
+    const int smask = LBPS_LD(&bn[b].smask);
+    typename P::Raw ra, rb;
+    P::load_raw(A.m, g.mplane, (size_t)b, true, ra);
     // Eq. psi_phi_at_bound: differences of u(t + dt) at (i, j).
     Sten sx = stencil_x(g, i, j), sy = stencil_y(g, i, j);
     double dux_dx = 0.0, duy_dx = 0.0, dux_dy = 0.0, duy_dy = 0.0;
@@ -390,12 +397,7 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<
     // population travelling that way, replacing what the interior kernel
     // wrote there (a rectangle's edge point has one such neighbour, a corner
     // none; next to a hole a point may have several).
-    // The populations at t are read from copy A's boundary mirror (entry b,
-    // coalesced along the boundary list); the reset ones go to the lattice and
-    // to copy B's mirror.
-    const int smask = LBPS_LD(&bn[b].smask);
-    typename P::Raw ra, rb;
-    P::load_raw(A.m, g.mplane, (size_t)b, true, ra);
+    // The reset populations go to the lattice and to copy B's mirror.
     V a5s[2][5], b5s[2][5];
     const double sv[2] = {phi, psi};
     double jx[2], jy[2];
