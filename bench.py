@@ -746,7 +746,9 @@ def run_gpu(args):
         barrier()
         t0 = time.perf_counter()
         lbps.lbps_init(lat._h, pin_ux.numpy(), pin_uy.numpy())
+        ti = time.perf_counter()
         rc = lbps.lbps_step(lat._h, args.e2e_steps)
+        ts = time.perf_counter()
         lbps.lbps_read(lat._h, lbps.LBPS_UX, out_x.numpy())
         lbps.lbps_read(lat._h, lbps.LBPS_UY, out_y.numpy())
         t1 = time.perf_counter()
@@ -756,6 +758,7 @@ def run_gpu(args):
         e2e_ups, _, _ = aggregate(t1 - t0, points * args.e2e_steps, world, rmax, rsum)
         e2e = {"value": e2e_ups / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": 2 * d.nx * d.ny * 8, "d2h_bytes_per_step": 2 * d.nx * d.ny * 8,
+               "seconds": {"init": ti - t0, "steps": ts - ti, "read": t1 - ts},
                "step": f"one solve: lbps_init from pinned host u0, lbps_step({args.e2e_steps}), "
                        f"lbps_read of u_x and u_y into pinned host memory (after two untimed solves of 64 steps)"}
 
