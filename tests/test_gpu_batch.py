@@ -90,8 +90,8 @@ def test_batch_tuning_and_interleaved_single_steps(L):
 
 @pytest.mark.parametrize("storage", ["f32", "f64", "f16"])
 def test_batch_every_launch_shape_same_bits(L, storage):
-    """Register pipelines and shared-memory rings, with short and long row
-    chunks: the same bits as the lattices stepped on their own."""
+    """Every launch shape, with short and long row chunks: the same bits as
+    the lattices stepped on their own."""
     ds = domains(11, 6, lo=5, hi=90)
     solo = [make(L, d, storage).step(21) for d in ds]
     for variant in range(8):
@@ -122,6 +122,37 @@ def test_batch_against_oracle(L):
             scale = max(np.abs(want["ux"]).max(), np.abs(want["uy"]).max()) if k[0] == "u" else \
                 max(np.abs(want["phi"]).max(), np.abs(want["psi"]).max())
             assert np.abs(got[k] - want[k]).max() <= 1e-10 * scale, k
+    b.close()
+
+
+def test_batch_fp32_mixed_recipe_against_oracle(L):
+    """The batching workload's recipe (random edges and values in
+    U(-1e-3, 1e-3), lambda/mu in U(0.5, 4), a sigma = 4 pulse at a random
+    point), scaled to sides 64..160 so the oracle finishes: FP32 storage,
+    autotuned shape and graphs, 400 steps, every domain within the FP32
+    tolerance (relative L2 per field, 1e-5) of the FP64 oracle."""
+    def rel_errors(got, ref):
+        # relative L2 per field against max(|ref|, 1e-2 |group|), groups (u), (v), (phi, psi)
+        out = {}
+        for g in (("ux", "uy"), ("vx", "vy"), ("phi", "psi")):
+            gn = np.sqrt(sum(np.linalg.norm(ref[k]) ** 2 for k in g))
+            for k in g:
+                out[k] = float(np.linalg.norm(got[k] - ref[k]) / max(np.linalg.norm(ref[k]), 1e-2 * gn, 1e-300))
+        return out
+
+    ds = W.mixed_batch(count=6, seed=17, side_lo=64, side_hi=160)
+    lats = [L.Lattice.rectangle(d.nx, d.ny, d.lam, d.mu, d.edge_type, np.asarray(d.edge_value, float).ravel(),
+                                a0_phi=d.a0_phi, storage="f32").init(*d.displacement()) for d in ds]
+    b = L.Batch(lats)
+    b.tune(repeats=1)
+    b.step(400)
+    assert b.check() == 0
+    for q, (d, lat) in enumerate(zip(ds, lats)):
+        nt, bv = O.rect_bc(d.nx, d.ny, d.edge_type, np.asarray(d.edge_value, float).ravel())
+        ref = O.OracleLattice(d.nx, d.ny, d.lam, d.mu, a0_phi=d.a0_phi, node_type=nt, bc_value=bv)
+        ref.init(*d.displacement()).step(400)
+        errs = rel_errors(lat.fields(), ref.fields())
+        assert max(errs.values()) <= 1e-5, (q, errs)
     b.close()
 
 
