@@ -405,7 +405,8 @@ int lbps_check_report(uint64_t out[2]);
  * rows_per_warp (1..4096) is the number of rows each warp marches over.
  * Defaults: variant 0 (variant 2 for FP64 storage, which needs more
  * registers); 32 rows, or 16 or 8 on lattices too small to give the
- * interior kernel 16384 warps at 32 (below about 4096^2). */
+ * interior kernel 16384 warps at 32 (below about 4096^2); 16 rows from
+ * 640000 to 2000000 points and 4 rows below 640000 (measured best). */
 int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);
 
 /* Steps per CUDA graph of lbps_step: k even, 2..64 (LBPS_ERR_INVALID

@@ -773,15 +773,21 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
     lat->steps = 0;
     lat->initialised = false;
     // default strip height: 32 rows, or 16 / 8 where the lattice is too small
-    // to give the interior kernel about 16 K warps (4-5 resident waves) at 32
+    // to give the interior kernel about 16 K warps (4-5 resident waves) at 32;
+    // below about 1400^2 points a sweep of 2..16 rows (FP32, CUDA graphs) put
+    // 16 rows first from about 800^2 (1024^2: 29.0 GLUPS against 25.8 at 8)
+    // and 4 rows first below it (512^2: 16.4 against 15.5)
     {
         const long long strips = (params->nx + lbps::kBatchStripCols - 1) / lbps::kBatchStripCols;
+        const long long points = (long long)params->nx * params->ny;
         int rows = 8;
         for (int r : {32, 16})
             if (strips * ((params->ny + r - 1) / r) >= 16384) {
                 rows = r;
                 break;
             }
+        if (points < 640000) rows = 4;
+        else if (points < 2000000) rows = 16;
         lat->tuning.rows_per_warp = rows;
         // FP64 populations need 128 registers a thread: the 6-blocks-per-SM
         // variant spills there, the 4-blocks one does not (8192^2: 12.2
