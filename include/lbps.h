@@ -417,6 +417,19 @@ int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);
  * time on small lattices. */
 int lbps_set_graph_steps(lbps_lattice* lat, int32_t k);
 
+/* Two time steps per sweep of the interior (on != 0) or one (0, the default).
+ * Applies to rectangles without periodic axes and at least 16 points a side
+ * (other lattices keep single steps): the points at least 3 from every edge
+ * advance two steps in one pass of a kernel that reads the state once and
+ * writes it once; the boundary rules and the points up to 3 from the edges
+ * run step by step through a scratch state copy, beside it.  Results are the
+ * same bits as single steps.  Allocates the scratch copy (cudaMalloc, the
+ * size of one state copy; LBPS_ERR_OOM if that fails) and frees it when
+ * turned off or at lbps_destroy.  Per-kernel timing (lbps_profile) and
+ * synchronisation points that fall between the two steps of a pair use single
+ * steps. */
+int lbps_set_step_pairs(lbps_lattice* lat, int32_t on);
+
 /* Per-kernel timing for roofline reports.  enable != 0 starts recording CUDA
  * events on the lattice's stream around the interior kernel of every step
  * and around the boundary reset after it (the boundary Newmark pass runs on

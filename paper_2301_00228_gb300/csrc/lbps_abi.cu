@@ -406,6 +406,73 @@ int run_step(lbps_lattice* lat) {
     return LBPS_OK;
 }
 
+// Two steps per sweep apply to rectangles without periodic axes, at least
+// 16 points a side, with the scratch copy allocated and per-kernel timing off.
+bool pair_ok(const lbps_lattice* lat) {
+    const lbps::Geo& g = lat->L.g;
+    return lat->xmem && lat->side && !g.general && !g.periodic_x && !g.periodic_y && g.nx >= 16 && g.ny >= 16 &&
+           lat->L.nb > 0 && !lat->prof;
+}
+
+// Steps n and n + 1 in one sweep of the interior.  Copy A (current) holds
+// step n, copy B receives step n + 2, the scratch copy X step n + 1 where the
+// boundary rules need it:
+//   side stream: Newmark(n) A -> X; the interior kernel on the points 1..3
+//   from the edges, A -> X; reset(n) A, X -> X; Newmark(n + 1) X -> B; the
+//   interior kernel on the points 1..2 from the edges, X -> B; reset(n + 1)
+//   X, B -> B (the order of two single steps, on X and B);
+//   main stream, beside it: pair_kernel, A -> B, the points at least 3 from
+//   the edges.
+// The two streams write disjoint parts of X and B and read A, X, B only where
+// the other does not write, so they run concurrently; the join ends the pair.
+int run_pair(lbps_lattice* lat) {
+    const int a = lat->cur, b = lat->cur ^ 1;
+    cudaError_t e = cudaEventRecord(lat->fork, lat->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(lat->side, lat->fork, 0);
+    if (e == cudaSuccess)
+        e = lbps::with_policy(lat->p.storage, [&](auto pol) {
+            using P = decltype(pol);
+            const auto& g = lat->L.g;
+            const auto A = lat->view<P>(a), B = lat->view<P>(b), X = lat->copy_view<P>(lat->xmem);
+            cudaError_t r = lbps::launch_pair<P>(g, lat->c, lat->kc<P>(), A, B, lat->flag(), lat->st, 32);
+            auto bnd = [&](lbps::View<P> s, lbps::View<P> d, int pass) {
+                return lbps::launch_boundary<P>(g, lat->c, lat->kc<P>(), s, d, lat->bn(), lat->L.nb, lat->flag(),
+                                                lat->tstep(), lat->side, pass, pass + 1);
+            };
+            if (r == cudaSuccess) r = bnd(A, X, 1);
+            if (r == cudaSuccess) r = lbps::launch_frame<P>(g, lat->c, lat->kc<P>(), A, X, lat->flag(), lat->side, 3);
+            if (r == cudaSuccess) r = bnd(A, X, 2);
+            if (r == cudaSuccess) r = bnd(X, B, 1);
+            if (r == cudaSuccess) r = lbps::launch_frame<P>(g, lat->c, lat->kc<P>(), X, B, lat->flag(), lat->side, 2);
+            if (r == cudaSuccess) r = bnd(X, B, 2);
+            return r;
+        });
+    if (e == cudaSuccess) e = cudaEventRecord(lat->join, lat->side);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(lat->st, lat->join, 0);
+    if (e != cudaSuccess) {
+        lat->last_cuda = (int)e;
+        return LBPS_ERR_CUDA;
+    }
+    lat->cur = b;
+    lat->steps += 2;
+    return LBPS_OK;
+}
+
+// k steps: pairs in one sweep where they apply, else single steps
+int run_steps(lbps_lattice* lat, int k) {
+    int rc = LBPS_OK;
+    for (int s = 0; s < k && rc == LBPS_OK;) {
+        if (k - s >= 2 && pair_ok(lat)) {
+            rc = run_pair(lat);
+            s += 2;
+        } else {
+            rc = run_step(lat);
+            s += 1;
+        }
+    }
+    return rc;
+}
+
 void drop_graphs(lbps_lattice* lat) {
     for (int w = 0; w < 2; ++w)
         for (int q = 0; q < 2; ++q) {
@@ -420,12 +487,13 @@ void drop_graphs(lbps_lattice* lat) {
 // graph_k: anything that changes them bumps lat->gen), then replayed.  The
 // capture runs run_step k times on the capture stream; the host-side copy
 // index and step count it advances are put back.
-int step_graph(lbps_lattice* lat, int k, cudaGraphExec_t* out) {
+int step_graph(lbps_lattice* lat, int k, cudaGraphExec_t* out, int* end_cur) {
     const int q = lat->cur;
     const int w = k == 2 ? 0 : 1;
     cudaGraphExec_t& slot = lat->graph[w][q];
     if (slot && lat->graph_gen[w][q] == lat->gen) {
         *out = slot;
+        *end_cur = lat->graph_cur[w][q];
         return LBPS_OK;
     }
     if (slot) cudaGraphExecDestroy(slot);
@@ -444,9 +512,9 @@ int step_graph(lbps_lattice* lat, int k, cudaGraphExec_t* out) {
         return LBPS_ERR_CUDA;
     }
     lat->st = lat->cap;
-    int rc = LBPS_OK;
-    for (int s = 0; s < k && rc == LBPS_OK; ++s) rc = run_step(lat);
+    int rc = run_steps(lat, k);
     lat->st = saved;
+    lat->graph_cur[w][q] = lat->cur;  // a pair in one sweep moves the state to the other copy once
     lat->cur = q;
     lat->steps = steps;
     e = cudaStreamEndCapture(lat->cap, &g);
@@ -460,6 +528,7 @@ int step_graph(lbps_lattice* lat, int k, cudaGraphExec_t* out) {
     }
     lat->graph_gen[w][q] = lat->gen;
     *out = slot;
+    *end_cur = lat->graph_cur[w][q];
     return LBPS_OK;
 }
 
@@ -887,7 +956,8 @@ int lbps_step_async(lbps_lattice* lat, int64_t n) {
             if (k == 0 && n - s >= c && !lat->prof && !(l > 0 && l - lat->steps % l < c)) k = c;
         if (k > 0) {
             cudaGraphExec_t g = nullptr;
-            int rc = step_graph(lat, k, &g);
+            int end_cur = lat->cur;
+            int rc = step_graph(lat, k, &g, &end_cur);
             if (rc != LBPS_OK) return rc;
             cudaError_t e = cudaGraphLaunch(g, lat->st);
             if (e != cudaSuccess) {
@@ -895,6 +965,7 @@ int lbps_step_async(lbps_lattice* lat, int64_t n) {
                 return LBPS_ERR_CUDA;
             }
             lat->steps += k;
+            lat->cur = end_cur;
             s += k;
         } else {
             int rc = run_step(lat);
@@ -1148,6 +1219,33 @@ int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp) {
     return LBPS_OK;
 }
 
+int lbps_set_step_pairs(lbps_lattice* lat, int32_t on) {
+    if (!lat || on < 0 || on > 1) return LBPS_ERR_INVALID;
+    if ((on != 0) == (lat->xmem != nullptr)) return LBPS_OK;
+    if (cudaStreamSynchronize(lat->st) != cudaSuccess) return LBPS_ERR_CUDA;
+    if (on) {
+        void* x = nullptr;
+        if (cudaMalloc(&x, lat->L.copy_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return LBPS_ERR_OOM;
+        }
+        // zeroed once: parts of it the frame passes read but do not use then hold finite values
+        if (cudaMemset(x, 0, lat->L.copy_bytes) != cudaSuccess ||
+            lbps::set_check_range(x, lat->L.copy_bytes, lat->st) != cudaSuccess) {
+            cudaFree(x);
+            cudaGetLastError();
+            return LBPS_ERR_CUDA;
+        }
+        lat->xmem = static_cast<char*>(x);
+    } else {
+        lbps::set_check_range(lat->xmem, 0, lat->st);
+        cudaFree(lat->xmem);
+        lat->xmem = nullptr;
+    }
+    lat->gen += 1;  // captured step graphs hold the other kind of step
+    return LBPS_OK;
+}
+
 int lbps_set_graph_steps(lbps_lattice* lat, int32_t k) {
     if (!lat || k < 2 || k > 64 || (k & 1)) return LBPS_ERR_INVALID;
     lat->graph_k = k;
@@ -1289,6 +1387,11 @@ void lbps_destroy(lbps_lattice* lat) {
     if (lat->fork) cudaEventDestroy(lat->fork);
     if (lat->join) cudaEventDestroy(lat->join);
     if (lat->mem) lbps::set_check_range(lat->mem, 0, lat->st);  // checked builds: the block is no longer live
+    if (lat->xmem) {
+        lbps::set_check_range(lat->xmem, 0, lat->st);
+        cudaStreamSynchronize(lat->st);
+        cudaFree(lat->xmem);
+    }
     if (lat->owns && lat->mem) {
         cudaStreamSynchronize(lat->st);
         cudaFree(lat->mem);

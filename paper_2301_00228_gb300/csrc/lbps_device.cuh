@@ -345,6 +345,13 @@ struct PopDirect {
 #pragma unroll
             for (int q = 0; q < 5; ++q) LBPS_ST(f + (size_t)(s * 5 + q) * plane + p, r.f[s][q]);
     }
+    // The stored form store_point would write at p, in registers.
+    __device__ __forceinline__ static void pack(size_t, const T (&x)[2][5], const KC<T>&, Raw& r) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int q = 0; q < 5; ++q) r.f[s][q] = x[s][q];
+    }
     // Equilibria of Eq. feq of both sets at lattice offset p for s[set] and
     // the lattice first moments (jx[set], jy[set]) (FP64 in), in stored form.
     // FP32 storage evaluates them in FP32 (from a and a_0 of the FP32
@@ -592,6 +599,22 @@ struct PopNeq16 {
                    << (16 * s);
         }
         LBPS_ST(wp, out);
+    }
+    // The stored form store_point would write at p, in registers.
+    __device__ __forceinline__ static void pack(size_t p, const float (&x)[2][5], const KC<float>& k, Raw& r) {
+        unsigned wx = 0, wy = 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            r.m[s][0] = x[s][0];
+            r.m[s][1] = sub_rn(x[s][1], x[s][3]);
+            r.m[s][2] = sub_rn(x[s][2], x[s][4]);
+            wx |= enc_n(add_rn(x[s][1], x[s][3]), x[s][0], k.r[s], k.scale, key_of(p, 2u * s, k), k.sr)
+                  << (16 * s);
+            wy |= enc_n(add_rn(x[s][2], x[s][4]), x[s][0], k.r[s], k.scale, key_of(p, 2u * s + 1u, k), k.sr)
+                  << (16 * s);
+        }
+        r.w[0] = wx;
+        r.w[1] = wy;
     }
     // Every word of one point from its stored form.
     __device__ __forceinline__ static void store_raw(float* __restrict__ f, size_t plane, size_t p, const Raw& r) {

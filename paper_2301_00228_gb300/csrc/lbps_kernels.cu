@@ -500,13 +500,19 @@ __device__ __forceinline__ void load_uv(const double* __restrict__ U, size_t pla
     for (int q = 0; q < 4; ++q) u[q] = ok ? ld(U + (size_t)q * plane + p) : 0.0;
 }
 
+// An output window of the interior kernel: columns [x0, x1), rows [y0, y1).
+struct Win {
+    int x0, x1, y0, y1;
+};
+
 // One warp's strip: output columns [xs, xs + kStripCols) of rows [j0, j1).
 // Returns true in lanes that produced a non-finite value.  All 32 lanes of
 // the warp must call it together (warp shuffles).  UVD: how many rows ahead u
-// and du/dt are prefetched (1 or 2; the populations always 2).
-template <typename P, int UVD>
+// and du/dt are prefetched (1 or 2; the populations always 2).  WIN: writes
+// only points inside the window w (the frame passes of a two-step sweep).
+template <typename P, int UVD, bool WIN = false>
 __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& A,
-                                           const View<P>& B, int xs, int j0, int j1) {
+                                           const View<P>& B, int xs, int j0, int j1, Win w = Win{0, 0, 0, 0}) {
     using V = typename P::V;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -514,7 +520,7 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
     const bool col_ok = g.periodic_x ? (xl <= g.nx) : (xl >= 0 && xl < g.nx);
     const int col = col_ok ? wrap(xl, g.nx) : 0;
     const bool out_lane = lane >= 1 && lane <= kStripCols && xl < g.nx &&
-                          (g.periodic_x || (xl > 0 && xl < g.nx - 1));
+                          (g.periodic_x || (xl > 0 && xl < g.nx - 1)) && (!WIN || (xl >= w.x0 && xl < w.x1));
     const size_t PL = g.plane;
 
     auto row_ok = [&](int j) { return g.periodic_y || (j >= 0 && j < g.ny); };
@@ -564,7 +570,7 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
             Nm[s] = add_rn(add_rn(Nf[s][1], Nf[s][2]), add_rn(Nf[s][3], Nf[s][4]));
             Ns[s] = add_rn(Nf[s][0], Nm[s]);
         }
-        const bool row_interior = g.periodic_y || (j > 0 && j < g.ny - 1);
+        const bool row_interior = (g.periodic_y || (j > 0 && j < g.ny - 1)) && (!WIN || (j >= w.y0 && j < w.y1));
         if (row_interior) {  // warp-uniform
             V sW[2], sE[2], out[2][5];
 #pragma unroll
@@ -630,6 +636,193 @@ __global__ void __launch_bounds__(128, MINB) bulk_kernel(Geo g, Consts c, KCof<P
     // interior point reads those rows: it returns before loading them.
     if (g.gap && j0 >= LBPS_LD(&g.gap[2 * warp]) && j1 <= LBPS_LD(&g.gap[2 * warp + 1])) return;
     const bool bad = bulk_strip<P, UVD>(g, c, k, A, B, xs, j0, j1);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+// ------------------------------------------------- two steps per sweep
+
+// The interior kernel restricted to the window w: strips s0 .. s0 + nstrips - 1,
+// rows [jb, je) in chunks of `rows` (the frame passes of a two-step sweep).
+template <typename P, int MINB, int UVD>
+__global__ void __launch_bounds__(128, MINB) frame_kernel(Geo g, Consts c, KCof<P> k, View<P> A, View<P> B,
+                                                          unsigned* flag, int s0, int nstrips, int jb, int je,
+                                                          int rows, Win w) {
+    const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    if (warp >= nstrips) return;  // whole warp
+    const int xs = (s0 + warp) * kStripCols;
+    const int j0 = jb + blockIdx.y * rows;
+    const int j1 = min(j0 + rows, je);
+    if (j0 >= j1) return;
+    const bool bad = bulk_strip<P, UVD, true>(g, c, k, A, B, xs, j0, j1, w);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
+constexpr int kPairCols = 28;  // output columns of a warp in the two-step kernel
+constexpr int kDeep = 3;       // the two-step kernel writes points at least this far from every edge
+
+// Two time steps of the deep interior of a rectangle (no periodic axis, no
+// void points) in one sweep: the warp marches its strip's rows computing step
+// n + 1 from copy A (state n) exactly as bulk_strip does, rounds it to its
+// stored form as a store and reload would, and from those values step n + 2,
+// which it writes to copy B.  Lanes are columns xs - 2 .. xs + 29: step n + 1
+// is valid in lanes 1..30, step n + 2 in lanes 2..29 (output columns xs ..
+// xs + 27).  Rows [j0, j1) need step n + 1 at rows j0 - 1 .. j1 and state n
+// at rows j0 - 2 .. j1 + 1.  A point at least kDeep from every edge depends
+// at step n + 2 only on interior points at step n + 1 that are at least 2
+// from the edges, which the boundary reset of step n does not touch, so
+// nothing here needs the boundary passes.
+template <typename P>
+__device__ __forceinline__ bool pair_strip(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& A,
+                                           const View<P>& B, int xs, int j0, int j1) {
+    using V = typename P::V;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int xl = xs - 2 + lane;
+    const bool col_ok = xl < g.nx;             // xl >= 1 always (xs >= kDeep)
+    const int col = col_ok ? xl : g.nx - 1;
+    const bool out_lane = lane >= 2 && lane < 2 + kPairCols && xl < g.nx - kDeep;
+    const size_t PL = g.plane;
+    auto at = [&](int j) { return (size_t)j * (size_t)g.px + (size_t)col; };
+
+    // step n (state n, read): rows r - 1, r, r + 1 and r + 2 in flight
+    V P0s[2], P0f4[2];
+    V C0f[2][5], C0s[2], C0m[2];
+    V N0f[2][5];
+    typename P::Raw Qr;
+    double C0u[4], N0u[4];
+    // step n + 1: rows r - 2 (moment, f^4), r - 1 (all); filled by the first
+    // two iterations, which write nothing
+    V P1s[2] = {}, P1f4[2] = {};
+    V C1f[2][5] = {}, C1s[2] = {}, C1m[2] = {};
+    double C1u[4] = {};
+
+    {
+        V t[2][5];
+        P::load_raw(A.f, PL, at(j0 - 2), col_ok, Qr);
+        decode_row<P>(Qr, k, t);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            P0s[s] = sum5(t[s][0], t[s][1], t[s][2], t[s][3], t[s][4]);
+            P0f4[s] = t[s][4];
+        }
+    }
+    P::load_raw(A.f, PL, at(j0 - 1), col_ok, Qr);
+    decode_row<P>(Qr, k, C0f);
+    P::load_raw(A.f, PL, at(j0), col_ok, Qr);
+    decode_row<P>(Qr, k, N0f);
+    load_uv(A.u, PL, at(j0 - 1), col_ok, C0u);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        C0m[s] = add_rn(add_rn(C0f[s][1], C0f[s][2]), add_rn(C0f[s][3], C0f[s][4]));
+        C0s[s] = add_rn(C0f[s][0], C0m[s]);
+    }
+    bool bad = false;
+    // r: the row of step n + 1 computed this iteration; step n + 2 at r - 1
+    for (int r = j0 - 1; r <= j1; ++r) {
+        P::load_raw(A.f, PL, at(r + 2), col_ok && r + 2 <= j1 + 1, Qr);
+        load_uv(A.u, PL, at(r + 1), col_ok && r + 1 <= j1, N0u);
+        V N0m[2], N0s[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            N0m[s] = add_rn(add_rn(N0f[s][1], N0f[s][2]), add_rn(N0f[s][3], N0f[s][4]));
+            N0s[s] = add_rn(N0f[s][0], N0m[s]);
+        }
+        // step n + 1 at row r (bulk_strip's arithmetic)
+        V N1f[2][5];
+        double N1u[4];
+        {
+            V sW[2], sE[2], out[2][5];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                sW[s] = __shfl_up_sync(FULL, C0s[s], 1);
+                sE[s] = __shfl_down_sync(FULL, C0s[s], 1);
+                V f3W = __shfl_up_sync(FULL, C0f[s][3], 1);
+                V f1E = __shfl_down_sync(FULL, C0f[s][1], 1);
+                out[s][0] = add_rn(C0f[s][0], fma_rn(k.two_a0[s], C0m[s], -mul_rn(k.eight_a[s], C0f[s][0])));
+                out[s][1] = fma_rn(k.two_a[s], sW[s], -f3W);
+                out[s][3] = fma_rn(k.two_a[s], sE[s], -f1E);
+                out[s][2] = fma_rn(k.two_a[s], P0s[s], -P0f4[s]);
+                out[s][4] = fma_rn(k.two_a[s], N0s[s], -N0f[s][2]);
+            }
+            double ax, ay;
+            accel_interior<V>(sW[0], sE[0], P0s[0], N0s[0], sW[1], sE[1], P0s[1], N0s[1], k, ax, ay);
+            newmark(C0u[0], C0u[2], ax, c, N1u[0], N1u[2]);
+            newmark(C0u[1], C0u[3], ay, c, N1u[1], N1u[3]);
+            // as stored at row r and read back
+            typename P::Raw q;
+            P::pack(at(r), out, k, q);
+            decode_row<P>(q, k, N1f);
+        }
+        V N1m[2], N1s[2];
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            N1m[s] = add_rn(add_rn(N1f[s][1], N1f[s][2]), add_rn(N1f[s][3], N1f[s][4]));
+            N1s[s] = add_rn(N1f[s][0], N1m[s]);
+        }
+        // step n + 2 at row r - 1
+        if (r - 1 >= j0) {  // warp-uniform
+            V sW[2], sE[2], out[2][5];
+#pragma unroll
+            for (int s = 0; s < 2; ++s) {
+                sW[s] = __shfl_up_sync(FULL, C1s[s], 1);
+                sE[s] = __shfl_down_sync(FULL, C1s[s], 1);
+                V f3W = __shfl_up_sync(FULL, C1f[s][3], 1);
+                V f1E = __shfl_down_sync(FULL, C1f[s][1], 1);
+                out[s][0] = add_rn(C1f[s][0], fma_rn(k.two_a0[s], C1m[s], -mul_rn(k.eight_a[s], C1f[s][0])));
+                out[s][1] = fma_rn(k.two_a[s], sW[s], -f3W);
+                out[s][3] = fma_rn(k.two_a[s], sE[s], -f1E);
+                out[s][2] = fma_rn(k.two_a[s], P1s[s], -P1f4[s]);
+                out[s][4] = fma_rn(k.two_a[s], N1s[s], -N1f[s][2]);
+            }
+            if (out_lane) {
+                const size_t p = at(r - 1);
+                double ax, ay;
+                accel_interior<V>(sW[0], sE[0], P1s[0], N1s[0], sW[1], sE[1], P1s[1], N1s[1], k, ax, ay);
+                double u2[4];
+                newmark(C1u[0], C1u[2], ax, c, u2[0], u2[2]);
+                newmark(C1u[1], C1u[3], ay, c, u2[1], u2[3]);
+                P::store_point(B.f, PL, p, out, k);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) LBPS_ST(&B.u[(size_t)q * PL + p], u2[q]);
+                bad |= !isfinite(out[0][0] + out[1][0]);
+            }
+        }
+        // shift both windows
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            P1s[s] = C1s[s];
+            P1f4[s] = C1f[s][4];
+            C1s[s] = N1s[s];
+            C1m[s] = N1m[s];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) C1f[s][q] = N1f[s][q];
+            P0s[s] = C0s[s];
+            P0f4[s] = C0f[s][4];
+            C0s[s] = N0s[s];
+            C0m[s] = N0m[s];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) C0f[s][q] = N0f[s][q];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            C1u[q] = N1u[q];
+            C0u[q] = N0u[q];
+        }
+        decode_row<P>(Qr, k, N0f);
+    }
+    return bad;
+}
+
+template <typename P, int MINB>
+__global__ void __launch_bounds__(128, MINB) pair_kernel(Geo g, Consts c, KCof<P> k, View<P> A, View<P> B,
+                                                         unsigned* flag, int rows_per_warp) {
+    const int warp = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int xs = kDeep + warp * kPairCols;
+    if (xs >= g.nx - kDeep) return;  // whole warp
+    const int j0 = kDeep + blockIdx.y * rows_per_warp;
+    const int j1 = min(j0 + rows_per_warp, g.ny - kDeep);
+    if (j0 >= j1) return;
+    const bool bad = pair_strip<P>(g, c, k, A, B, xs, j0, j1);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
 }
 
@@ -1055,6 +1248,43 @@ cudaError_t launch_bulk(const Geo& g, const Consts& c, const KCof<P>& k, View<P>
 }
 
 template <typename P>
+cudaError_t launch_frame(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, unsigned* flag,
+                         cudaStream_t st, int fw) {
+    // FP64 populations need the 4-blocks shape (the others spill there)
+    constexpr int minb = sizeof(typename P::V) == 8 ? 4 : 6;
+    auto kern = frame_kernel<P, minb, 2>;
+    const int nx = g.nx, ny = g.ny, rows = 32;
+    const int all = (nx + kStripCols - 1) / kStripCols;
+    const dim3 blk(32 * kWarpsPerBlock);
+    auto blocks = [](int strips) { return (strips + kWarpsPerBlock - 1) / kWarpsPerBlock; };
+    // top and bottom bands: every strip, fw rows
+    kern<<<dim3(blocks(all), 1), blk, 0, st>>>(g, c, k, A, B, flag, 0, all, 1, 1 + fw, fw,
+                                                Win{1, nx - 1, 1, 1 + fw});
+    kern<<<dim3(blocks(all), 1), blk, 0, st>>>(g, c, k, A, B, flag, 0, all, ny - 1 - fw, ny - 1, fw,
+                                                Win{1, nx - 1, ny - 1 - fw, ny - 1});
+    // left and right bands between them: the strips holding columns 1 .. fw and
+    // nx - 1 - fw .. nx - 2
+    const int jb = 1 + fw, je = ny - 1 - fw, chunks = (je - jb + rows - 1) / rows;
+    const int ls0 = 1 / kStripCols, ls1 = fw / kStripCols;
+    const int rs0 = (nx - 1 - fw) / kStripCols, rs1 = (nx - 2) / kStripCols;
+    kern<<<dim3(blocks(ls1 - ls0 + 1), chunks), blk, 0, st>>>(g, c, k, A, B, flag, ls0, ls1 - ls0 + 1, jb, je, rows,
+                                                             Win{1, 1 + fw, jb, je});
+    kern<<<dim3(blocks(rs1 - rs0 + 1), chunks), blk, 0, st>>>(g, c, k, A, B, flag, rs0, rs1 - rs0 + 1, jb, je, rows,
+                                                             Win{nx - 1 - fw, nx - 1, jb, je});
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t launch_pair(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, unsigned* flag,
+                        cudaStream_t st, int rows) {
+    const int warps = (g.nx - 2 * kDeep + kPairCols - 1) / kPairCols;
+    const dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, (g.ny - 2 * kDeep + rows - 1) / rows);
+    constexpr int minb = sizeof(typename P::V) == 8 ? 2 : 4;  // FP64 needs 168 registers a thread
+    pair_kernel<P, minb><<<grid, 32 * kWarpsPerBlock, 0, st>>>(g, c, k, A, B, flag, rows);
+    return cudaGetLastError();
+}
+
+template <typename P>
 cudaError_t launch_sync(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, cudaStream_t st) {
     dim3 blk(32, 8);
     sync_kernel<P><<<grid2d(g.nx, g.ny, blk), blk, 0, st>>>(g, c, k, A);
@@ -1082,6 +1312,10 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, const KCof<P>& k, View<P
 
 #define LBPS_INSTANTIATE(P)                                                                                   \
     template cudaError_t launch_init<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, cudaStream_t);  \
+    template cudaError_t launch_frame<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>, unsigned*,  \
+                                         cudaStream_t, int);                                                  \
+    template cudaError_t launch_pair<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>, unsigned*,   \
+                                        cudaStream_t, int);                                                   \
     template cudaError_t launch_mirror<P>(const Geo&, View<P>, const BNode*, int, cudaStream_t);            \
     template cudaError_t launch_boundary<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, View<P>,      \
                                             const BNode*, int, unsigned*, unsigned long long*,                \

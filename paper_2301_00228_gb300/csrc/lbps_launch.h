@@ -54,6 +54,16 @@ constexpr int kTuningVariants = 8;
 template <typename P>
 cudaError_t launch_bulk(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, unsigned* flag,
                         cudaStream_t st, const Tuning& tu);
+// Two steps per sweep of a rectangle without periodic axes (min side >= 16):
+// launch_pair writes step n + 2 of the points at least 3 from every edge
+// (copy A holds step n); launch_frame runs the interior kernel on the points
+// 1 .. fw from the edges only (four bands).
+template <typename P>
+cudaError_t launch_pair(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, unsigned* flag,
+                        cudaStream_t st, int rows);
+template <typename P>
+cudaError_t launch_frame(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, unsigned* flag,
+                         cudaStream_t st, int fw);
 
 template <typename P>
 cudaError_t launch_sync(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, cudaStream_t st);

@@ -75,9 +75,14 @@ struct lbps_lattice {
     int graph_k = 32;   // 5-14 % faster than pairs below 1024^2, 3 % at 2048^2 (FP32)
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     int64_t graph_gen[2][2] = {{-1, -1}, {-1, -1}};
+    int graph_cur[2][2] = {{0, 1}, {0, 1}};  // the current copy after a replay
     char* mem;
     bool owns;
     int cur;            // copy holding time t
+    // two steps per sweep (lbps_set_step_pairs): the scratch state copy that
+    // holds step n + 1 on the boundary and the points up to 3 from it
+    // (cudaMalloc'd, copy_bytes), null when off
+    char* xmem = nullptr;
     lbps::Tuning tuning;  // bulk-kernel launch shape
     int last_cuda = 0;    // cudaError_t of the last failing CUDA call
     int64_t steps;
@@ -90,11 +95,17 @@ struct lbps_lattice {
 
     template <typename P>
     lbps::View<P> view(int q) const {
+        return copy_view<P>(mem + L.off_copy[q]);
+    }
+    // A state copy laid out at base (the two copies of the block, or the
+    // scratch copy of two-step sweeps).
+    template <typename P>
+    lbps::View<P> copy_view(char* base) const {
         lbps::View<P> v;
-        v.f = reinterpret_cast<typename P::Base*>(mem + L.off_copy[q]);
-        v.u = u(q);
-        v.m = reinterpret_cast<typename P::Base*>(mem + L.off_copy[q] + L.f_bytes + L.u_bytes);
-        v.s = reinterpret_cast<double*>(mem + L.off_copy[q] + L.f_bytes + L.u_bytes + L.m_bytes);
+        v.f = reinterpret_cast<typename P::Base*>(base);
+        v.u = reinterpret_cast<double*>(base + L.f_bytes);
+        v.m = reinterpret_cast<typename P::Base*>(base + L.f_bytes + L.u_bytes);
+        v.s = reinterpret_cast<double*>(base + L.f_bytes + L.u_bytes + L.m_bytes);
         return v;
     }
     double* u(int q) const { return reinterpret_cast<double*>(mem + L.off_copy[q] + L.f_bytes); }

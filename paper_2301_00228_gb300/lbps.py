@@ -95,6 +95,7 @@ def _load():
         "lbps_last_cuda_error": (ctypes.c_int, [vp]),
         "lbps_set_tuning": (ctypes.c_int, [vp, i32, i32]),
         "lbps_set_graph_steps": (ctypes.c_int, [vp, i32]),
+        "lbps_set_step_pairs": (ctypes.c_int, [vp, i32]),
         "lbps_profile": (ctypes.c_int, [vp, i32]),
         "lbps_profile_read": (ctypes.c_int, [vp, vp]),
         "lbps_set_stream": (ctypes.c_int, [vp, vp]),
@@ -288,6 +289,10 @@ def lbps_check_report():
     if rc < 0:
         raise LbpsError(rc, "lbps_check_report")
     return rc, int(out[0]), int(out[1])
+
+
+def lbps_set_step_pairs(h, on):
+    _check(_lib.lbps_set_step_pairs(h, int(on)), "lbps_set_step_pairs")
 
 
 def lbps_set_graph_steps(h, k):

@@ -2,8 +2,9 @@
 access of the time-loop kernels is checked for alignment and against the
 device blocks of the live lattices, and the first violation is recorded
 instead of performed.  A child process builds it, runs random single-lattice
-cases, hole plates under every launch shape and a batch of uneven lattices
-through it, and reads the record: no access may fall outside."""
+cases, hole plates under every launch shape, lattices taking two steps per
+sweep (their scratch copy registered as a live block) and a batch of uneven
+lattices through it, and reads the record: no access may fall outside."""
 import os
 import subprocess
 import sys
@@ -51,6 +52,13 @@ for variant in range(8):
         pass
     lat.step(5).close()
     runs += 1
+for storage, (nx, ny) in (("f32", (16, 16)), ("f16", (67, 45)), ("f64", (131, 37))):  # two steps per sweep
+    lat = L.Lattice.rectangle(nx, ny, 1.7, 1.0, (2, 1, 1, 2), np.full(8, 1e-4), a0_phi=0.99, storage=storage,
+                              sync_every=7)
+    L.lbps_set_step_pairs(lat._h, 1)
+    lat.init(*W.pulse_displacement(nx, ny, nx / 3, ny / 2, 3.0, 1e-3, "dilatation")).step(41)
+    lat.close()
+    runs += 1
 lats = []                                     # a batch of uneven rectangles and hole plates
 for dom in W.mixed_batch(count=10)[::2]:
     lats.append(L.Lattice.rectangle(dom.nx, dom.ny, dom.lam, dom.mu, dom.edge_type,
@@ -82,4 +90,4 @@ def test_checked_build_records_no_violation():
     rc, line, addr, runs = (int(x) for x in report[-1].split()[1:])
     assert rc == 1, "the checked build was not loaded"
     assert (line, addr) == (0, 0), f"first violation at source line {line}, address {addr:#x}"
-    assert runs == 21
+    assert runs == 24
