@@ -207,10 +207,10 @@ def kernel_source_hash():
     return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
-def ncu_traffic(workload_name, storage):
-    """DRAM bytes per bulk-kernel launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    f = ROOT / "profiles" / f"bulk_kernel_{workload_name}_{storage}.md"
+def ncu_traffic(workload_name, storage, kernel="bulk_kernel"):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    f = ROOT / "profiles" / f"{kernel}_{workload_name}_{storage}.md"
     if not f.exists():
         return None
     text = f.read_text()
@@ -616,6 +616,79 @@ def run_slab(args):
     return 0
 
 
+def bulk_roofline(prof, d, args, seconds, geometry, peak, peak_kind, wname):
+    """The interior kernel of single steps: the state read and written once per
+    step at every interior point (events around every launch)."""
+    bulk_ms, bulk_n, bnd_ms, bnd_n = (float(x) for x in prof)
+    if geometry is not None:  # interior points only; the kernel also reads one node-type byte per point
+        interior = int((geometry[0] == 0).sum())
+        alg_bytes = interior * (BYTES_PER_UPDATE[args.storage] + 1)
+    else:
+        interior = (d.nx - (0 if d.periodic_x else 2)) * (d.ny - (0 if d.periodic_y else 2))
+        alg_bytes = interior * BYTES_PER_UPDATE[args.storage]
+    bulk_avg_s = bulk_ms / max(bulk_n, 1) / 1000.0
+    achieved = alg_bytes / bulk_avg_s / 1e9
+    # timed on the lattice's stream: the interior kernel and the boundary
+    # reset; the boundary Newmark pass runs beside the interior kernel on a
+    # second stream and is not timed (lbps_profile)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic(wname, args.storage), "kernel": "bulk_kernel", "peak_source": peak_kind,
+            "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": bulk_avg_s * 1000.0,
+            "share_of_step_time": bulk_ms / (1000.0 * seconds),
+            "kernel_timing": "a window after the timed steps (--graphs)" if args.graphs
+            else "CUDA events around every launch of the timed steps",
+            "timed_boundary_passes_ms_per_step": bnd_ms / args.steps,
+            "boundary_newmark_pass": "beside the interior kernel on a second stream, not timed"}
+
+
+def pair_roofline(prof, d, args, seconds, peak, peak_kind, wname):
+    """The two-step kernel: it reads the state of the points at least 3 from
+    every edge once and writes it once per launch, for two steps of updates
+    (events around every launch).  The FP64 Newmark update of u, du/dt, not
+    HBM, bounds it."""
+    pair_ms, pair_n = float(prof[0]), float(prof[1])
+    deep = (d.nx - 6) * (d.ny - 6)
+    alg_bytes = deep * BYTES_PER_UPDATE[args.storage]
+    avg_s = pair_ms / max(pair_n, 1) / 1000.0
+    achieved = alg_bytes / avg_s / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": ncu_traffic(wname, args.storage, kernel="pair_kernel"), "kernel": "pair_kernel",
+            "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1000.0,
+            "steps_per_launch": 2, "updates_per_launch": 2 * deep,
+            "bytes_per_update": alg_bytes / (2 * deep),
+            "limiter": "FP64 pipe (the Newmark update of u, du/dt, twice per point per launch)",
+            "share_of_step_time": pair_ms / (1000.0 * seconds),
+            "kernel_timing": "CUDA events around every two-step launch of the timed steps",
+            "frame_and_boundary_passes": "beside the two-step kernel on a second stream, not timed"}
+
+
+def single_step_window(lbps, lat, d, args, points, peak, stream):
+    """The same lattice with single steps, timed over a shorter window (for
+    comparison with two steps per sweep); the lattice keeps its state."""
+    import torch
+
+    lbps.lbps_set_step_pairs(lat._h, 0)
+    n = min(args.steps, 300)
+    lat.step(4)
+    lbps.lbps_profile(lat._h, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc = lbps.lbps_step_async(lat._h, n)
+    e1.record(stream)
+    e1.synchronize()
+    prof = lbps.lbps_profile_read(lat._h)
+    lbps.lbps_profile(lat._h, 0)
+    lbps.lbps_set_step_pairs(lat._h, 1)
+    if rc != 0:
+        raise SystemExit(f"step failed: {lbps.lbps_strerror(rc)}")
+    s = e0.elapsed_time(e1) / 1000.0
+    bulk_avg_s = float(prof[0]) / max(float(prof[1]), 1) / 1000.0
+    alg = (d.nx - 2) * (d.ny - 2) * BYTES_PER_UPDATE[args.storage]
+    return {"value": points * n / s / 1e9, "unit": UNIT, "steps": n, "ms_per_step": 1000.0 * s / n,
+            "bulk_kernel_frac": alg / bulk_avg_s / 1e9 / peak, "bulk_kernel_avg_ms": bulk_avg_s * 1000.0}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -640,7 +713,8 @@ def run_gpu(args):
         geometry = lbps.lbps_disk_cells(d.nx, d.ny, 1.0, *d.hole, et, ev)
         d.node_type = geometry[0]
     sync_every = args.sync_every if args.sync_every or geometry is None else d.sync_every
-    mk = dict(a0_phi=d.a0_phi, storage=args.storage, sync_every=sync_every)
+    mk = dict(a0_phi=d.a0_phi, storage=args.storage, sync_every=sync_every,
+              step_pairs={"auto": "auto", "on": True, "off": False}[args.pairs])
     if geometry is not None:
         nt, bv, cell = geometry
         lat = lbps.Lattice(d.nx, d.ny, d.lam, d.mu, d.rho, node_type=nt, bc_value=bv, cell=cell, **mk)
@@ -653,6 +727,7 @@ def run_gpu(args):
     if args.tuning:  # a fixed launch shape of the interior kernel (profiling a smaller lattice like a larger)
         variant, rows = (int(x) for x in args.tuning.split(","))
         lbps.lbps_set_tuning(lat._h, variant, rows)
+    pairs = bool(lbps.lbps_step_pairs(lat._h))  # two steps per sweep (large rectangles)
     ux, uy = d.displacement_torch("cuda")
     lat.init(ux, uy)
     torch.cuda.synchronize()
@@ -698,35 +773,23 @@ def run_gpu(args):
     value_ups, t_max, units_all = aggregate(seconds, units, world, rmax, rsum)
     value = value_ups / 1e9
 
-    # roofline of the dominant (bulk) kernel
-    bulk_ms, bulk_n, bnd_ms, bnd_n = (float(x) for x in prof)
-    if geometry is not None:  # interior points only; the kernel also reads one node-type byte per point
-        interior = int((geometry[0] == 0).sum())
-        alg_bytes = interior * (BYTES_PER_UPDATE[args.storage] + 1)
-    else:
-        interior = (d.nx - (0 if d.periodic_x else 2)) * (d.ny - (0 if d.periodic_y else 2))
-        alg_bytes = interior * BYTES_PER_UPDATE[args.storage]
-    bulk_avg_s = bulk_ms / max(bulk_n, 1) / 1000.0
+    # roofline of the dominant kernel
     peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / bulk_avg_s / 1e9
-    traffic = ncu_traffic(wname, args.storage)
-    # timed on the lattice's stream: the interior kernel and the boundary
-    # reset; the boundary Newmark pass runs beside the interior kernel on a
-    # second stream and is not timed (lbps_profile)
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "bulk_kernel", "peak_source": peak_kind,
-                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": bulk_avg_s * 1000.0,
-                "share_of_step_time": bulk_ms / bulk_n / (1000.0 * seconds / args.steps),
-                "kernel_timing": "a window after the timed steps (--graphs)" if args.graphs
-                else "CUDA events around every launch of the timed steps",
-                "timed_boundary_passes_ms_per_step": bnd_ms / args.steps,
-                "boundary_newmark_pass": "beside the interior kernel on a second stream, not timed"}
-    bounded = not (d.periodic_x and d.periodic_y)
-    # per step: boundary Newmark, interior, boundary reset (a periodic lattice
-    # has no boundary); per synchronisation: the sync kernel and the refresh
-    # of the boundary mirror
-    gpu_launches = args.steps * (3 if bounded else 1) + (
-        (args.steps // sync_every) * (2 if bounded else 1) if sync_every else 0)
+    if pairs:
+        roofline = pair_roofline(prof, d, args, seconds, peak, peak_kind, wname)
+        # per pair of steps: the two-step kernel; beside it the boundary
+        # Newmark and reset of each step and two frame passes of four launches
+        gpu_launches = (args.steps // 2) * 13 + (args.steps % 2) * 3
+        single = single_step_window(lbps, lat, d, args, points, peak, stream)
+    else:
+        roofline = bulk_roofline(prof, d, args, seconds, geometry, peak, peak_kind, wname)
+        bounded = not (d.periodic_x and d.periodic_y)
+        # per step: boundary Newmark, interior, boundary reset (a periodic lattice
+        # has no boundary); per synchronisation: the sync kernel and the refresh
+        # of the boundary mirror
+        gpu_launches = args.steps * (3 if bounded else 1) + (
+            (args.steps // sync_every) * (2 if bounded else 1) if sync_every else 0)
+        single = None
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -781,10 +844,13 @@ def run_gpu(args):
                 "data": "synthetic",
                 "config": {"workload": wname, **describe(d), "storage": args.storage,
                            "displacement": "f64", "sync_every": sync_every,
-                           "l2": "state larger than L2" if alg_bytes > 1.3e8 else "state fits L2",
+                           "l2": "state larger than L2" if roofline["alg_bytes_per_launch"] > 1.3e8 else "state fits L2",
                            "replicas_per_gpu": 1, **({"tuning": args.tuning} if args.tuning else {})},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clock}
+        line["config"]["steps_per_sweep"] = 2 if pairs else 1
+        if single is not None:
+            line["single_step"] = single
         if precision is not None:
             line["precision"] = precision
         if serving is not None:
@@ -818,6 +884,8 @@ def main(argv=None):
     ap.add_argument("--batch-count", type=int, default=256, help="domains of the batch workload")
     ap.add_argument("--batch-tuning", default=None,
                     help="batch: launch shape 'variant,rows[,steps per graph]' instead of running the autotuner")
+    ap.add_argument("--pairs", default="auto", choices=["auto", "on", "off"],
+                    help="lattice workloads: two time steps per sweep (auto: on from 12M points where they apply)")
     ap.add_argument("--tuning", default=None,
                     help="lattice workloads: interior-kernel launch shape 'variant,rows' instead of the default")
     ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")

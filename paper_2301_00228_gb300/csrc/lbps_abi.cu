@@ -411,7 +411,7 @@ int run_step(lbps_lattice* lat) {
 bool pair_ok(const lbps_lattice* lat) {
     const lbps::Geo& g = lat->L.g;
     return lat->xmem && lat->side && !g.general && !g.periodic_x && !g.periodic_y && g.nx >= 16 && g.ny >= 16 &&
-           lat->L.nb > 0 && !lat->prof;
+           lat->L.nb > 0;
 }
 
 // Steps n and n + 1 in one sweep of the interior.  Copy A (current) holds
@@ -434,7 +434,12 @@ int run_pair(lbps_lattice* lat) {
             using P = decltype(pol);
             const auto& g = lat->L.g;
             const auto A = lat->view<P>(a), B = lat->view<P>(b), X = lat->copy_view<P>(lat->xmem);
-            cudaError_t r = lbps::launch_pair<P>(g, lat->c, lat->kc<P>(), A, B, lat->flag(), lat->st, 32);
+            // per-kernel timing: events around the two-step kernel (the passes
+            // beside it are not timed, as the Newmark pass of a single step)
+            cudaError_t r = prof_mark(lat);
+            if (r == cudaSuccess) r = lbps::launch_pair<P>(g, lat->c, lat->kc<P>(), A, B, lat->flag(), lat->st, 32);
+            if (r == cudaSuccess) r = prof_mark(lat);
+            if (r == cudaSuccess && lat->prof) lat->ev_kind.push_back(0);
             auto bnd = [&](lbps::View<P> s, lbps::View<P> d, int pass) {
                 return lbps::launch_boundary<P>(g, lat->c, lat->kc<P>(), s, d, lat->bn(), lat->L.nb, lat->flag(),
                                                 lat->tstep(), lat->side, pass, pass + 1);
@@ -967,6 +972,10 @@ int lbps_step_async(lbps_lattice* lat, int64_t n) {
             lat->steps += k;
             lat->cur = end_cur;
             s += k;
+        } else if (n - s >= 2 && pair_ok(lat) && !(l > 0 && (lat->steps + 1) % l == 0)) {
+            int rc = run_pair(lat);
+            if (rc != LBPS_OK) return rc;
+            s += 2;
         } else {
             int rc = run_step(lat);
             if (rc != LBPS_OK) return rc;
@@ -1244,6 +1253,11 @@ int lbps_set_step_pairs(lbps_lattice* lat, int32_t on) {
     }
     lat->gen += 1;  // captured step graphs hold the other kind of step
     return LBPS_OK;
+}
+
+int lbps_step_pairs(const lbps_lattice* lat) {
+    if (!lat) return LBPS_ERR_INVALID;
+    return pair_ok(lat) ? 1 : 0;
 }
 
 int lbps_set_graph_steps(lbps_lattice* lat, int32_t k) {

@@ -262,9 +262,10 @@ class CudaSlab:
 
     def _make(self):
         a = self.args
+        # single steps: the ghost rows are exchanged after every step
         self.lat = self.L.Lattice(a["nx"], a["ny"], a["lam"], a["mu"], a["rho"], a["dh"],
                                   periodic_y=a["periodic_y"], node_type=a["node_type"], bc_value=a["bc_value"],
-                                  cell=a["cell"], **self.kw)
+                                  cell=a["cell"], step_pairs=False, **self.kw)
         self.L.lbps_set_origin(self.lat._h, self.p.first)
         for kind, t_ramp, t_hold in self.loads:
             self.lat.set_load(kind, t_ramp, t_hold)
