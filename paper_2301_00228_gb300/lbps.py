@@ -347,8 +347,9 @@ def lbps_set_origin(h, row0):
 # ---- convenience wrapper --------------------------------------------------
 
 # From about this many points two time steps per sweep are faster than one
-# (8192^2 FP32: 51.7 against 42.9 GLUPS; 4096^2: 45.2 against 42.0; 2048^2:
-# 29.6 against 37.5).
+# (FP32: 16384^2 54.2 against 43.3 GLUPS, 8192^2 51.6 against 42.9, 4096^2
+# 44.3 against 40.7, 2048^2 29.6 against 37.5; FP16/BF16 8192^2 51.2 / 50.9
+# against 47.6; FP64 storage 11.5 against 12.2, so not there).
 PAIRS_AUTO_POINTS = 12_000_000
 
 
@@ -360,8 +361,9 @@ class Lattice:
                  stream=None, cell=None, bc_j_mode=0, step_pairs="auto"):
         """step_pairs: two time steps per sweep (lbps_set_step_pairs); "auto"
         turns them on for lattices of at least PAIRS_AUTO_POINTS points where
-        they apply (rectangles without periodic axes), where they are
-        faster (the scratch state copy they need is allocated then)."""
+        they apply (rectangles without periodic axes) and the storage is not
+        FP64, where they are faster (the scratch state copy they need is
+        allocated then)."""
         import torch
 
         self.nx, self.ny = int(nx), int(ny)
@@ -380,8 +382,8 @@ class Lattice:
         self._h = lbps_create_cells(self.params, nt, bv, cl, self._mem.data_ptr(), self.nbytes)
         c, _ = lbps_info(self._h)
         self.cd, self.cs, self.a_phi, self.a_psi, self.a0_psi, self.dt = (float(x) for x in c)
-        if step_pairs == "auto":
-            step_pairs = self.nx * self.ny >= PAIRS_AUTO_POINTS
+        if step_pairs == "auto":  # FP64 storage is FP64-bound with single steps already
+            step_pairs = self.nx * self.ny >= PAIRS_AUTO_POINTS and storage != "f64"
         if step_pairs:
             lbps_set_step_pairs(self._h, 1)
             if not lbps_step_pairs(self._h):  # does not apply here: free the scratch copy
