@@ -20,6 +20,7 @@
 // FP64 planes, or FP32 moments (f^0, J) with the non-equilibrium pair sums in
 // 16 bits.
 #include <algorithm>
+#include <type_traits>
 
 #include "lbps_launch.h"
 #ifdef LBPS_CHECKED
@@ -1279,7 +1280,9 @@ cudaError_t launch_pair(const Geo& g, const Consts& c, const KCof<P>& k, View<P>
                         cudaStream_t st, int rows) {
     const int warps = (g.nx - 2 * kDeep + kPairCols - 1) / kPairCols;
     const dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, (g.ny - 2 * kDeep + rows - 1) / rows);
-    constexpr int minb = sizeof(typename P::V) == 8 ? 2 : 4;  // FP64 needs 168 registers a thread
+    // blocks per SM that fit without spilling: FP32 populations 5 (96
+    // registers), the 16-bit formats 4 (about 120), FP64 2 (168)
+    constexpr int minb = sizeof(typename P::V) == 8 ? 2 : (std::is_same<P, PopDirect<float>>::value ? 5 : 4);
     pair_kernel<P, minb><<<grid, 32 * kWarpsPerBlock, 0, st>>>(g, c, k, A, B, flag, rows);
     return cudaGetLastError();
 }
