@@ -12,9 +12,9 @@ Prints one JSON line (rank 0).  Metric: two-field lattice updates per second
 (GLUPS = lattice points x time steps / s / 1e9), whole job.
   --impl reference  times the FP64 CPU oracle on the host cores instead
                     (bounded sample of the same workload).
-  --storage bf16|f16  populations in the 16-bit formats (FP32 moments, 16-bit
-                    non-equilibrium sums); dtype stays the arithmetic type.
-  --precision       adds the relative L2 error of FP32, BF16 and FP16 storage
+  --storage bf16|f16|bfp13  populations in the 16-bit formats (FP32 moments,
+                    16-bit non-equilibrium sums); dtype stays the arithmetic type.
+  --precision       adds the relative L2 error of FP32, BF16, FP16 and BFP13 storage
                     against the FP64 oracle on a 1024^2 crop rerun (5000
                     steps; about a minute of oracle time on the host cores).
 """
@@ -42,7 +42,8 @@ UNIT = "GLUPS"
 # of u, du/dt (FP64); the 16-bit formats hold per set f^0, Jx, Jy in FP32 and
 # two 16-bit non-equilibrium sums
 BYTES_PER_UPDATE = {"f32": 2 * (10 * 4 + 4 * 8), "f64": 2 * (10 * 8 + 4 * 8),
-                    "bf16": 2 * (6 * 4 + 4 * 2 + 4 * 8), "f16": 2 * (6 * 4 + 4 * 2 + 4 * 8)}
+                    "bf16": 2 * (6 * 4 + 4 * 2 + 4 * 8), "f16": 2 * (6 * 4 + 4 * 2 + 4 * 8),
+                    "bfp13": 2 * (6 * 4 + 4 * 2 + 4 * 8)}
 
 
 # ----------------------------------------------------------------- helpers
@@ -301,7 +302,7 @@ def precision_report(d, side, steps):
     ev = np.asarray(c.edge_value, float).ravel()
     fields = ("ux", "uy", "phi", "psi")
     got = {}
-    for st in ("f32", "bf16", "f16"):
+    for st in ("f32", "bf16", "f16", "bfp13"):
         lat = lbps.Lattice.rectangle(side, side, c.lam, c.mu, c.edge_type, ev, a0_phi=c.a0_phi, storage=st)
         lat.init(ux, uy).step(steps)
         got[st] = ({k: lat.read(k) for k in fields}, lat.scale_exp)
@@ -442,7 +443,8 @@ def run_batch(args):
                          "peak_source": peak_kind},
             "one_at_a_time": {"value": loop_value, "unit": UNIT, "steps": loop_steps,
                               "speedup_of_batch": value / loop_value},
-            "gpu_launches": 3 * args.steps, "clocks": clock}
+            # per step: the persistent kernel (strips and Newmark tasks) and the reset
+            "gpu_launches": (3 if args.storage == "bfp13" else 2) * args.steps, "clocks": clock}
     if rank == 0:
         print(json.dumps(line), flush=True)
     b.close()
@@ -606,7 +608,8 @@ def run_slab(args):
                          "traffic": None, "kernel": "bulk_kernel (rank 0's slab)", "peak_source": peak_kind},
             # per step: boundary Newmark, interior, reset; per neighbour one pack and
             # one unpack (copy, boundary mirror, boundary stresses)
-            "gpu_launches": int(bulk_n) * 3 + args.steps * 4 * ((p.down is not None) + (p.up is not None)),
+            "gpu_launches": int(bulk_n) * (4 if args.storage == "bfp13" else 3) +
+            args.steps * 4 * ((p.down is not None) + (p.up is not None)),
             "clocks": clock}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -779,7 +782,9 @@ def run_gpu(args):
         roofline = pair_roofline(prof, d, args, seconds, peak, peak_kind, wname)
         # per pair of steps: the two-step kernel; beside it the boundary
         # Newmark and reset of each step and two frame passes of four launches
-        gpu_launches = (args.steps // 2) * 13 + (args.steps % 2) * 3
+        # (BFP13 storage: one more launch per reset, its y streams)
+        split = 1 if args.storage == "bfp13" else 0
+        gpu_launches = (args.steps // 2) * (13 + 2 * split) + (args.steps % 2) * (3 + split)
         single = single_step_window(lbps, lat, d, args, points, peak, stream)
     else:
         roofline = bulk_roofline(prof, d, args, seconds, geometry, peak, peak_kind, wname)
@@ -787,7 +792,8 @@ def run_gpu(args):
         # per step: boundary Newmark, interior, boundary reset (a periodic lattice
         # has no boundary); per synchronisation: the sync kernel and the refresh
         # of the boundary mirror
-        gpu_launches = args.steps * (3 if bounded else 1) + (
+        split = 1 if args.storage == "bfp13" else 0
+        gpu_launches = args.steps * ((3 + split) if bounded else 1) + (
             (args.steps // sync_every) * (2 if bounded else 1) if sync_every else 0)
         single = None
 
@@ -889,7 +895,7 @@ def main(argv=None):
     ap.add_argument("--tuning", default=None,
                     help="lattice workloads: interior-kernel launch shape 'variant,rows' instead of the default")
     ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")
-    ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16", "f16"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f64", "bf16", "f16", "bfp13"])
     ap.add_argument("--precision", action="store_true",
                     help="pulses: add rel-L2 of every storage format against the FP64 oracle on a crop rerun")
     ap.add_argument("--precision-side", type=int, default=1024)

@@ -53,8 +53,8 @@ extern "C" {
  * every format.  The 16-bit formats store, per set, the conserved moments
  * f^0, Jx = f^1 - f^3, Jy = f^2 - f^4 in FP32 and the two pair sums'
  * deviations from equilibrium (Eq. feq), Nx = f^1 + f^3 - 2 (a/a_0) f^0 and
- * Ny = f^2 + f^4 - 2 (a/a_0) f^0, in 16 bits multiplied by 2^scale_exp;
- * with a0_phi >= 0.999 (slow waves) both formats round these stochastically,
+ * Ny = f^2 + f^4 - 2 (a/a_0) f^0, in 16 bits a value multiplied by
+ * 2^scale_exp; with a0_phi >= 0.999 (slow waves) BF16 and FP16 round them stochastically,
  * with random bits hashed from the value and its position (deterministic, so
  * results do not depend on launch shape, batching or resumes), otherwise to
  * nearest; arithmetic is FP32.  32 bytes per point per state copy instead of
@@ -64,6 +64,15 @@ extern "C" {
 #define LBPS_STORAGE_F64 1      /* FP64 populations, FP64 arithmetic          */
 #define LBPS_STORAGE_BF16 2     /* FP32 moments + bfloat16 Nx, Ny             */
 #define LBPS_STORAGE_F16 3      /* FP32 moments + IEEE half Nx, Ny            */
+#define LBPS_STORAGE_BFP13 4    /* FP32 moments + Nx, Ny of each set in one
+                                   32-bit block-floating-point word: a shared
+                                   4-bit exponent E and two sign + 13-bit
+                                   magnitudes m, value m 2^(E-13) (bits 31..28
+                                   E, 27 sign of Nx, 26..14 m of Nx, 13 sign of
+                                   Ny, 12..0 m of Ny; E = 15 with m = 8191:
+                                   infinity).  Rounded to nearest (ties to
+                                   even), never stochastically.  The boundary
+                                   reset takes one more launch per step.      */
 
 /* Fields for lbps_read / lbps_read_device. */
 #define LBPS_UX 0               /* displacement u_x                            */
@@ -384,6 +393,25 @@ int lbps_set_load(lbps_lattice* lat, int32_t kind, double t_ramp, double t_hold)
  * compressed formats are this library's. */
 int lbps_scale_exp(const lbps_lattice* lat, int32_t* exp);
 
+/* The value codec of a 16-bit storage format (storage = LBPS_STORAGE_BF16,
+ * _F16 or _BFP13) on n values in caller-owned device arrays d_x (FP32) and
+ * d_code (n 16-bit slots), enqueued on cuda_stream (NULL = legacy default
+ * stream), not waited for.  encode = 1 writes the codes of d_x as the time
+ * step rounds stored pair sums (d_x already multiplied by 2^e); encode = 0
+ * writes into d_x the values of d_code.  BF16, FP16: d_code[i] is the code
+ * of d_x[i], rounded to nearest (ties to even) with stochastic = 0, else
+ * stochastically with the random bits hashed from d_x[i] and the key
+ * 4 i + key0 (a point at plane offset i, slot key0 of 0..3, on a lattice with
+ * no row offset).  BFP13: the values pair up, (d_x[2i], d_x[2i+1]) = (Nx, Ny)
+ * in the 32-bit word d_code[2i] | d_code[2i+1] << 16 (n even, d_x 8-byte
+ * and d_code 4-byte aligned; key0 and stochastic are not used).  Non-finite values and overflow give the format's
+ * infinity.  Lets a caller read or reproduce stored sums.  LBPS_ERR_INVALID
+ * for another storage, n < 0, a BFP13 call breaking those conditions, a null
+ * array with n > 0, or encode or stochastic not 0 or 1; LBPS_ERR_CUDA if the
+ * launch fails. */
+int lbps_codec16(int32_t storage, int32_t encode, float* d_x, uint16_t* d_code, int64_t n, uint32_t key0,
+                 int32_t stochastic, void* cuda_stream);
+
 /* The CUDA runtime error code (a cudaError_t value) of the most recent
  * step, check or initialisation of this lattice that returned
  * LBPS_ERR_CUDA; 0 if none. */
@@ -404,7 +432,7 @@ int lbps_check_report(uint64_t out[2]);
  * two rows ahead; 4..7 the same budgets loading them one row ahead.
  * rows_per_warp (1..4096) is the number of rows each warp marches over.
  * Defaults: variant 0 (variant 2 for FP64 storage, which needs more
- * registers); 32 rows, or 16 or 8 on lattices too small to give the
+ * registers, and 4 for BFP13, whose codec does); 32 rows, or 16 or 8 on lattices too small to give the
  * interior kernel 16384 warps at 32 (below about 4096^2); 16 rows from
  * 640000 to 2000000 points and 4 rows below 640000 (measured best). */
 int lbps_set_tuning(lbps_lattice* lat, int32_t variant, int32_t rows_per_warp);

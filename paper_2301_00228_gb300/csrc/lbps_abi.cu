@@ -40,14 +40,14 @@ int validate_params(const lbps_params* p) {
     if (p->bc_feq_mode != 0 && p->bc_feq_mode != 1) return LBPS_ERR_INVALID;
     if (p->bc_j_mode != 0 && p->bc_j_mode != 1) return LBPS_ERR_INVALID;
     if (p->sync_every < 0) return LBPS_ERR_INVALID;
-    if (p->storage < LBPS_STORAGE_F32 || p->storage > LBPS_STORAGE_F16) return LBPS_ERR_INVALID;
+    if (p->storage < LBPS_STORAGE_F32 || p->storage > LBPS_STORAGE_BFP13) return LBPS_ERR_INVALID;
     if (p->pop_scale_exp < -100 || p->pop_scale_exp > 100) return LBPS_ERR_INVALID;
     if ((p->periodic_x != 0 && p->periodic_x != 1) || (p->periodic_y != 0 && p->periodic_y != 1))
         return LBPS_ERR_INVALID;
     // 16-bit storage rewrites a population pair as a whole; on a lattice 3 points
     // wide along a non-periodic axis two boundary sources stream into the same
     // pair of one point, which that cannot express.
-    if ((p->storage == LBPS_STORAGE_BF16 || p->storage == LBPS_STORAGE_F16) &&
+    if (lbps::storage_is16(p->storage) &&
         ((!p->periodic_x && p->nx == 3) || (!p->periodic_y && p->ny == 3)))
         return LBPS_ERR_INVALID;
     return LBPS_OK;
@@ -209,7 +209,7 @@ int build_boundary(const lbps_params* p, const uint8_t* node_type, const double*
         return LBPS_OK;
     }
     const double half = 0.5 * p->dh;
-    const bool pairs16 = p->storage == LBPS_STORAGE_BF16 || p->storage == LBPS_STORAGE_F16;
+    const bool pairs16 = lbps::storage_is16(p->storage);
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             size_t k = (size_t)j * nx + i;
@@ -867,6 +867,9 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
         // variant spills there, the 4-blocks one does not (8192^2: 12.2
         // against 9.6 GLUPS; the FP64 arithmetic bounds either)
         if (params->storage == LBPS_STORAGE_F64) lat->tuning.variant = 2;
+        // BFP13's codec spills in the shape that prefetches u two rows ahead
+        // at 6 blocks per SM; one row ahead fits in 80 registers
+        if (params->storage == LBPS_STORAGE_BFP13) lat->tuning.variant = 4;
     }
     // the side stream of the boundary Newmark pass; if it cannot be had, the
     // pass runs on the lattice's stream (same results, no overlap)

@@ -290,8 +290,8 @@ __device__ __forceinline__ T sum5(T f0, T f1, T f2, T f3, T f4) {
 // at equilibrium (Eq. feq) each pair sum is 2 a s = 2 (a / a_0) f^0, so
 //   Nx = f^1 + f^3 - 2 r f^0,  Ny = f^2 + f^4 - 2 r f^0   (r = a / a_0)
 // vanish there and carry only the non-equilibrium part.  f^0, Jx, Jy are
-// stored in FP32, Nx, Ny in H multiplied by 2^e (half: rounded to nearest;
-// bfloat16: deterministic stochastic rounding, f2bits_store).  Decoding:
+// stored in FP32, Nx, Ny in H multiplied by 2^e (rounded by
+// f2bits_store: to nearest, or stochastically with a_0 near 1).  Decoding:
 //   f^1 = r f^0 + (Nx + Jx) / 2,  f^3 = r f^0 + (Nx - Jx) / 2  (and y).
 // The first moment stays FP32 because with the small time steps of Sec. 4
 // (a_0 near 1) every rounding of J acts as a momentum kick whose effect on
@@ -309,6 +309,9 @@ struct PopDirect {
     using V = T;
     using Base = T;
     static constexpr int kBytesPerPoint = 10 * (int)sizeof(T);
+    // false: the boundary reset may write the x pair and the y pair of one
+    // point from two threads at once (true for PopBfp13, whose words hold both)
+    static constexpr bool kSplitStream = false;
     struct Raw {
         T f[2][5];
     };
@@ -401,18 +404,6 @@ struct PopDirect {
     }
 };
 
-template <typename H>
-__device__ __forceinline__ float h2f(H v);
-template <>
-__device__ __forceinline__ float h2f<__half>(__half v) { return __half2float(v); }
-template <>
-__device__ __forceinline__ float h2f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
-template <typename H>
-__device__ __forceinline__ H f2h(float v);
-template <>
-__device__ __forceinline__ __half f2h<__half>(float v) { return __float2half_rn(v); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 f2h<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
 // 16-bit value <-> its bits (the low or high half of a packed word)
 template <typename H>
 __device__ __forceinline__ float bits2f(unsigned b);
@@ -473,11 +464,25 @@ __device__ __forceinline__ unsigned f2bits_store<__nv_bfloat16>(float v, unsigne
     return (u + (mix32(u ^ mix32(key)) & 0xffffu)) >> 16;
 }
 
+// Populations of one set from f^0, J and the pair sums' deviations N
+// (PopNeq16, PopBfp13): f^1 = r f^0 + (Nx + Jx) / 2, f^3 = r f^0 + (Nx - Jx) / 2
+// and the same along y.
+__device__ __forceinline__ void expand_pairs(float f0, float jx, float jy, float nx, float ny, float r,
+                                             float (&x)[5]) {
+    const float rf0 = mul_rn(r, f0);
+    x[0] = f0;
+    x[1] = fma_rn(0.5f, add_rn(nx, jx), rf0);
+    x[3] = fma_rn(0.5f, sub_rn(nx, jx), rf0);
+    x[2] = fma_rn(0.5f, add_rn(ny, jy), rf0);
+    x[4] = fma_rn(0.5f, sub_rn(ny, jy), rf0);
+}
+
 template <typename H>
 struct PopNeq16 {
     using V = float;
     using Base = float;
     static constexpr int kBytesPerPoint = 6 * 4 + 2 * 4;
+    static constexpr bool kSplitStream = false;
     struct Raw {
         float m[2][3];   // f^0, Jx, Jy of each set
         unsigned w[2];   // packed Nx, Ny words (scaled)
@@ -490,16 +495,6 @@ struct PopNeq16 {
     }
     __device__ __forceinline__ static float half_of(unsigned w, int s, const KC<float>& k) {
         return mul_rn(bits2f<H>(s ? (w >> 16) : (w & 0xffffu)), k.inv_scale);
-    }
-    // populations from the moments of one set
-    __device__ __forceinline__ static void expand(float f0, float jx, float jy, float nx, float ny, float r,
-                                                  float (&x)[5]) {
-        const float rf0 = mul_rn(r, f0);
-        x[0] = f0;
-        x[1] = fma_rn(0.5f, add_rn(nx, jx), rf0);
-        x[3] = fma_rn(0.5f, sub_rn(nx, jx), rf0);
-        x[2] = fma_rn(0.5f, add_rn(ny, jy), rf0);
-        x[4] = fma_rn(0.5f, sub_rn(ny, jy), rf0);
     }
     // key: the point's plane offset and the slot (set, pair) for the rounding
     __device__ __forceinline__ static unsigned enc_n(float pair_sum, float f0, float r, float scale,
@@ -527,7 +522,7 @@ struct PopNeq16 {
         for (int q = 0; q < 2; ++q) r.w[q] = ok ? LBPS_LDG(w + (size_t)q * plane + p) : 0u;
     }
     __device__ __forceinline__ static void decode(const Raw& r, int s, const KC<float>& k, float (&x)[5]) {
-        expand(r.m[s][0], r.m[s][1], r.m[s][2], half_of(r.w[0], s, k), half_of(r.w[1], s, k), k.r[s], x);
+        expand_pairs(r.m[s][0], r.m[s][1], r.m[s][2], half_of(r.w[0], s, k), half_of(r.w[1], s, k), k.r[s], x);
     }
     __device__ __forceinline__ static void load5(const float* __restrict__ f, size_t plane, size_t p, int s,
                                                  const KC<float>& k, float (&x)[5]) {
@@ -535,7 +530,7 @@ struct PopNeq16 {
         float m[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) m[q] = LBPS_LD(f + (size_t)(s * 3 + q) * plane + p);
-        expand(m[0], m[1], m[2], half_of(LBPS_LD(w + p), s, k), half_of(LBPS_LD(w + plane + p), s, k), k.r[s], x);
+        expand_pairs(m[0], m[1], m[2], half_of(LBPS_LD(w + p), s, k), half_of(LBPS_LD(w + plane + p), s, k), k.r[s], x);
     }
     // The same in FP64 (field output).
     __device__ __forceinline__ static void load5d(const float* __restrict__ f, size_t plane, size_t p, int s,
@@ -647,6 +642,234 @@ struct PopNeq16 {
         r.w[1] = w;
     }
     // The same equilibria stored at p, each packed word written once.
+    __device__ __forceinline__ static void store_eq_point(float* __restrict__ f, size_t plane, size_t p,
+                                                          const Consts& c, const double (&sv)[2],
+                                                          const double (&jx)[2], const double (&jy)[2],
+                                                          const KC<float>& k) {
+        Raw r;
+        eq_raw(p, c, sv, jx, jy, k, r);
+        store_raw(f, plane, p, r);
+    }
+};
+
+// ---- BFP13: block floating point, two values per 32-bit word
+//
+// Both values of a word share a 4-bit exponent E; each has a sign and a
+// 13-bit magnitude m (no hidden bit), value = m 2^(E-13):
+//   bits 31..28 E, bit 27 sign of a, 26..14 m of a, bit 13 sign of b,
+//   12..0 m of b.
+// E is the smallest exponent at which the larger magnitude rounds to at most
+// 8191, so the larger value keeps 13 significant bits (IEEE half has 11) and
+// the smaller one the same absolute step; the range is m 2^-13 .. 32761.99.
+// E = 15 with m = 8191 is infinity (overflow; non-finite input).  Rounding
+// is to nearest, ties to even.
+__device__ __forceinline__ void bfp13_decode(unsigned w, float& a, float& b) {
+    // FP32 2^E (1 + m 2^-13) less 2^E: m 2^(E-13), exactly; the magnitudes
+    // moved into the top of the FP32 fraction field
+    const unsigned eb = ((w >> 28) + 127u) << 23;
+    const float base = __uint_as_float(eb);
+    float xa = __uint_as_float(eb | ((w >> 4) & 0x7ffc00u)) - base;
+    float xb = __uint_as_float(eb | ((w << 10) & 0x7ffc00u)) - base;
+    if ((w & 0xf7ffc000u) == 0xf7ffc000u) xa = __uint_as_float(0x7f800000u);
+    if ((w & 0xf0001fffu) == 0xf0001fffu) xb = __uint_as_float(0x7f800000u);
+    a = __uint_as_float(__float_as_uint(xa) | ((w << 4) & 0x80000000u));
+    b = __uint_as_float(__float_as_uint(xb) | ((w << 18) & 0x80000000u));
+}
+__device__ __forceinline__ unsigned bfp13_encode(float a, float b) {
+    const unsigned sa = __float_as_uint(a) >> 31, sb = __float_as_uint(b) >> 31;
+    const float xa = fabsf(a), xb = fabsf(b);
+    const unsigned signs = (sa << 27) | (sb << 13);
+    // overflow (and NaN): both values infinite
+    if (!(xa < 32762.0f) || !(xb < 32762.0f)) return 0xf7ffdfffu | signs;
+    // E = floor(log2 big) + 1 from the FP32 exponent field, at least 0 (zero,
+    // subnormals), and one more where big 2^(13-E) would round to 2^13: where
+    // the fraction field is at least 2^23 - 2^10, which adding 2^10 to the
+    // bits carries into the exponent field
+    const int E = max((int)((__float_as_uint(fmaxf(xa, xb)) + 0x400u) >> 23) - 126, 0);
+    const float sc = __uint_as_float((unsigned)(140 - E) << 23);   // 2^(13-E)
+    const unsigned ma = __float2uint_rn(xa * sc), mb = __float2uint_rn(xb * sc);
+    return ((unsigned)E << 28) | signs | (ma << 14) | mb;
+}
+
+// PopBfp13: per set f^0, Jx, Jy in FP32 as in PopNeq16, and the set's two
+// non-equilibrium pair sums Nx, Ny times 2^e in one BFP13 word (a = Nx,
+// b = Ny): plane 6 holds phi's word, plane 7 psi's; 32 bytes per point, as
+// PopNeq16, with 13-bit magnitudes instead of 11 significant bits.  Always
+// rounded to nearest (KC::sr is not used).  Writing one streamed pair of a
+// point rewrites the word of each set, which also holds the other pair, so
+// the boundary reset writes its x and its y streams in two passes
+// (kSplitStream); re-encoding the other pair is exact unless the new value
+// raises the shared exponent.
+struct PopBfp13 {
+    using V = float;
+    using Base = float;
+    static constexpr int kBytesPerPoint = 6 * 4 + 2 * 4;
+    static constexpr bool kSplitStream = true;
+    struct Raw {
+        float m[2][3];   // f^0, Jx, Jy of each set
+        unsigned w[2];   // the BFP13 word (Nx, Ny scaled) of each set
+    };
+    __device__ __forceinline__ static const unsigned* words(const float* f, size_t plane) {
+        return reinterpret_cast<const unsigned*>(f + 6 * plane);
+    }
+    __device__ __forceinline__ static unsigned* words(float* f, size_t plane) {
+        return reinterpret_cast<unsigned*>(f + 6 * plane);
+    }
+    // Nx, Ny of one set from its word
+    __device__ __forceinline__ static void n_of(unsigned w, const KC<float>& k, float& nx, float& ny) {
+        bfp13_decode(w, nx, ny);
+        nx = mul_rn(nx, k.inv_scale);
+        ny = mul_rn(ny, k.inv_scale);
+    }
+    // the scaled deviation of a pair sum from 2 r f^0
+    __device__ __forceinline__ static float scaled_n(float pair_sum, float f0, float r, float scale) {
+        return mul_rn(fma_rn(-2.0f * r, f0, pair_sum), scale);
+    }
+    __device__ __forceinline__ static unsigned enc_set(const float (&x)[5], float r, float scale) {
+        return bfp13_encode(scaled_n(add_rn(x[1], x[3]), x[0], r, scale), scaled_n(add_rn(x[2], x[4]), x[0], r, scale));
+    }
+    __device__ __forceinline__ static void load_raw(const float* __restrict__ f, size_t plane, size_t p, bool ok,
+                                                    Raw& r) {
+        const unsigned* w = words(f, plane);
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) r.m[s][q] = ok ? LBPS_LDG(f + (size_t)(s * 3 + q) * plane + p) : 0.0f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) r.w[q] = ok ? LBPS_LDG(w + (size_t)q * plane + p) : 0u;
+    }
+    __device__ __forceinline__ static void decode(const Raw& r, int s, const KC<float>& k, float (&x)[5]) {
+        float nx, ny;
+        n_of(r.w[s], k, nx, ny);
+        expand_pairs(r.m[s][0], r.m[s][1], r.m[s][2], nx, ny, k.r[s], x);
+    }
+    __device__ __forceinline__ static void load5(const float* __restrict__ f, size_t plane, size_t p, int s,
+                                                 const KC<float>& k, float (&x)[5]) {
+        float m[3], nx, ny;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) m[q] = LBPS_LD(f + (size_t)(s * 3 + q) * plane + p);
+        n_of(LBPS_LD(words(f, plane) + (size_t)s * plane + p), k, nx, ny);
+        expand_pairs(m[0], m[1], m[2], nx, ny, k.r[s], x);
+    }
+    // The same in FP64 (field output).
+    __device__ __forceinline__ static void load5d(const float* __restrict__ f, size_t plane, size_t p, int s,
+                                                  const KC<float>& k, double (&x)[5]) {
+        double f0 = LBPS_LD(f + (size_t)(s * 3) * plane + p);
+        double jx = LBPS_LD(f + (size_t)(s * 3 + 1) * plane + p);
+        double jy = LBPS_LD(f + (size_t)(s * 3 + 2) * plane + p);
+        float ax, ay;
+        bfp13_decode(LBPS_LD(words(f, plane) + (size_t)s * plane + p), ax, ay);
+        double nx = (double)ax * (double)k.inv_scale, ny = (double)ay * (double)k.inv_scale;
+        double rf0 = (double)k.r[s] * f0;
+        x[0] = f0;
+        x[1] = rf0 + 0.5 * (nx + jx);
+        x[3] = rf0 + 0.5 * (nx - jx);
+        x[2] = rf0 + 0.5 * (ny + jy);
+        x[4] = rf0 + 0.5 * (ny - jy);
+    }
+    __device__ __forceinline__ static void store_point(float* __restrict__ f, size_t plane, size_t p,
+                                                       const float (&x)[2][5], const KC<float>& k) {
+        unsigned* w = words(f, plane);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            LBPS_ST(f + (size_t)(s * 3) * plane + p, x[s][0]);
+            LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, sub_rn(x[s][1], x[s][3]));
+            LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, sub_rn(x[s][2], x[s][4]));
+            LBPS_ST(w + (size_t)s * plane + p, enc_set(x[s], k.r[s], k.scale));
+        }
+    }
+    // store_point for an interior point whose moving populations flagged in
+    // prov (1: f^1, 2: f^3, 4: f^2, 8: f^4) streamed in from boundary points:
+    // the reset overwrites each of them and keeps only its pair partner
+    // (store1_both).  Such a pair is stored as N = 0 and the J that gives the
+    // partner back, J = 2 (r f^0 - f^3) or 2 (f^1 - r f^0), so that the
+    // provisional value neither sets the word's exponent (and costs the other
+    // pair its precision) nor passes through the 13-bit rounding.
+    __device__ __forceinline__ static void store_point_pins(float* __restrict__ f, size_t plane, size_t p,
+                                                            const float (&x)[2][5], const KC<float>& k, int prov) {
+        unsigned* w = words(f, plane);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float f0 = x[s][0], rf0 = mul_rn(k.r[s], f0);
+            float jx = sub_rn(x[s][1], x[s][3]), jy = sub_rn(x[s][2], x[s][4]);
+            float nx = scaled_n(add_rn(x[s][1], x[s][3]), f0, k.r[s], k.scale);
+            float ny = scaled_n(add_rn(x[s][2], x[s][4]), f0, k.r[s], k.scale);
+            if (prov & 3) {
+                jx = mul_rn(2.0f, (prov & 1) ? sub_rn(rf0, x[s][3]) : sub_rn(x[s][1], rf0));
+                nx = 0.0f;
+            }
+            if (prov & 12) {
+                jy = mul_rn(2.0f, (prov & 4) ? sub_rn(rf0, x[s][4]) : sub_rn(x[s][2], rf0));
+                ny = 0.0f;
+            }
+            LBPS_ST(f + (size_t)(s * 3) * plane + p, f0);
+            LBPS_ST(f + (size_t)(s * 3 + 1) * plane + p, jx);
+            LBPS_ST(f + (size_t)(s * 3 + 2) * plane + p, jy);
+            LBPS_ST(w + (size_t)s * plane + p, bfp13_encode(nx, ny));
+        }
+    }
+    // One moving population alpha (1..4) of both sets: the pair partner keeps
+    // its value, so the pair's J and N are rewritten together, and each set's
+    // word with the N of the other pair (decoded and encoded again).  The
+    // call owns both words of the point: the reset writes x streams and y
+    // streams in separate passes, and the library rejects lattices 3 points
+    // wide along a non-periodic axis (two sources into one pair).
+    __device__ __forceinline__ static void store1_both(float* __restrict__ f, size_t plane, size_t p, int alpha,
+                                                       const float (&v)[2], const KC<float>& k) {
+        const int ax = (alpha == 1 || alpha == 3) ? 0 : 1;        // 0: x pair, 1: y pair
+        const bool plus = alpha <= 2;                              // alpha = 1, 2: J = v - partner
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            unsigned* wp = words(f, plane) + (size_t)s * plane + p;
+            float n[2];
+            bfp13_decode(LBPS_LD(wp), n[0], n[1]);
+            float* jp = f + (size_t)(s * 3 + 1 + ax) * plane + p;
+            const float f0 = LBPS_LD(f + (size_t)(s * 3) * plane + p);
+            const float j = LBPS_LD(jp);
+            const float nn = mul_rn(ax ? n[1] : n[0], k.inv_scale);
+            const float rf0 = mul_rn(k.r[s], f0);
+            const float partner = plus ? fma_rn(0.5f, sub_rn(nn, j), rf0) : fma_rn(0.5f, add_rn(nn, j), rf0);
+            LBPS_ST(jp, plus ? sub_rn(v[s], partner) : sub_rn(partner, v[s]));
+            const float nv = scaled_n(add_rn(v[s], partner), f0, k.r[s], k.scale);
+            LBPS_ST(wp, ax ? bfp13_encode(n[0], nv) : bfp13_encode(nv, n[1]));
+        }
+    }
+    // The stored form store_point would write at p, in registers.
+    __device__ __forceinline__ static void pack(size_t, const float (&x)[2][5], const KC<float>& k, Raw& r) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            r.m[s][0] = x[s][0];
+            r.m[s][1] = sub_rn(x[s][1], x[s][3]);
+            r.m[s][2] = sub_rn(x[s][2], x[s][4]);
+            r.w[s] = enc_set(x[s], k.r[s], k.scale);
+        }
+    }
+    // Every word of one point from its stored form.
+    __device__ __forceinline__ static void store_raw(float* __restrict__ f, size_t plane, size_t p, const Raw& r) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) LBPS_ST(f + (size_t)(s * 3 + q) * plane + p, r.m[s][q]);
+        unsigned* w = words(f, plane);
+        LBPS_ST(w + p, r.w[0]);
+        LBPS_ST(w + plane + p, r.w[1]);
+    }
+    // Equilibria of Eq. feq of both sets, in FP32 and in stored form (as
+    // PopNeq16::eq_raw; p unused, no rounding keys).
+    __device__ __forceinline__ static void eq_raw(size_t, const Consts&, const double (&sv)[2],
+                                                  const double (&jx)[2], const double (&jy)[2],
+                                                  const KC<float>& k, Raw& r) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            const float sf = (float)sv[s];
+            const float f0 = mul_rn(mul_rn(0.5f, k.two_a0[s]), sf);
+            r.m[s][0] = f0;
+            r.m[s][1] = (float)jx[s];
+            r.m[s][2] = (float)jy[s];
+            const float dev = mul_rn(fma_rn(-2.0f * k.r[s], f0, mul_rn(k.two_a[s], sf)), k.scale);
+            r.w[s] = bfp13_encode(dev, dev);
+        }
+    }
     __device__ __forceinline__ static void store_eq_point(float* __restrict__ f, size_t plane, size_t p,
                                                           const Consts& c, const double (&sv)[2],
                                                           const double (&jx)[2], const double (&jy)[2],

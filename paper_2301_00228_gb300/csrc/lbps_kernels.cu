@@ -353,6 +353,32 @@ __device__ inline void partial_stream_moment(const Geo& g, const KCof<P>& k, con
     }
 }
 
+// The populations boundary point (i, j) streams into its interior
+// neighbours, the directions d (0: +x, 1: +y, 2: -x, 3: -y) set in mask, from
+// its populations at t (a5s) and after the reset (b5s) (Eq. LBE_mod).
+template <typename P>
+__device__ inline void stream_out(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& B, int i, int j,
+                                  int mask, const typename P::V (&a5s)[2][5], const typename P::V (&b5s)[2][5]) {
+    using V = typename P::V;
+    const int DXS[4] = {1, 0, -1, 0};
+    const int DYS[4] = {0, 1, 0, -1};
+    for (int d = 0; d < 4; ++d) {
+        if (!((mask >> d) & 1)) continue;
+        V v[2];
+#pragma unroll
+        for (int set = 0; set < 2; ++set) {
+            switch (d) {
+            case 0: v[set] = stream_from_boundary<1, 3>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
+            case 1: v[set] = stream_from_boundary<2, 4>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
+            case 2: v[set] = stream_from_boundary<3, 1>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
+            default: v[set] = stream_from_boundary<4, 2>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
+            }
+        }
+        const size_t pin = (size_t)wrap(j + DYS[d], g.ny) * g.px + wrap(i + DXS[d], g.nx);
+        P::store1_both(B.f, g.plane, pin, d + 1, v, k);
+    }
+}
+
 template <typename P>
 __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& A,
                                       const View<P>& B, const BNode* __restrict__ bn, int nb, int b) {
@@ -415,24 +441,34 @@ __device__ inline bool boundary_reset(const Geo& g, const Consts& c, const KCof<
     if (smask)
 #pragma unroll
         for (int set = 0; set < 2; ++set) P::decode(rb, set, k, b5s[set]);
-    const int DXS[4] = {1, 0, -1, 0};
-    const int DYS[4] = {0, 1, 0, -1};
-    for (int d = 0; d < 4; ++d) {
-        if (!((smask >> d) & 1)) continue;
-        V v[2];
-#pragma unroll
-        for (int set = 0; set < 2; ++set) {
-            switch (d) {
-            case 0: v[set] = stream_from_boundary<1, 3>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
-            case 1: v[set] = stream_from_boundary<2, 4>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
-            case 2: v[set] = stream_from_boundary<3, 1>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
-            default: v[set] = stream_from_boundary<4, 2>(a5s[set], b5s[set], k, set, c.bc_feq_mode); break;
-            }
-        }
-        const size_t pin = (size_t)wrap(j + DYS[d], g.ny) * g.px + wrap(i + DXS[d], g.nx);
-        P::store1_both(B.f, g.plane, pin, d + 1, v, k);
-    }
+    // a policy whose words hold both pairs of a point leaves the y streams to
+    // a second pass (boundary_stream_y): two boundary points may stream into
+    // one point along x and along y
+    stream_out<P>(g, c, k, B, i, j, P::kSplitStream ? (smask & 5) : smask, a5s, b5s);
     return !isfinite((V)phi + (V)psi);
+}
+
+// The y streams of the reset for PopBfp13 (P::kSplitStream), in a pass after
+// the one that wrote everything else: the values depend only on the boundary
+// point's populations at t (copy A's mirror) and those the reset stored for
+// t + dt (copy B's mirror), which that pass left as they are.
+template <typename P>
+__device__ inline void boundary_stream_y(const Geo& g, const Consts& c, const KCof<P>& k, const View<P>& A,
+                                         const View<P>& B, const BNode* __restrict__ bn, int b) {
+    using V = typename P::V;
+    const int smask = LBPS_LD(&bn[b].smask) & 10;
+    if (!smask) return;
+    const int i = LBPS_LD(&bn[b].i), j = LBPS_LD(&bn[b].j);
+    typename P::Raw ra, rb;
+    P::load_raw(A.m, g.mplane, (size_t)b, true, ra);
+    P::load_raw(B.m, g.mplane, (size_t)b, true, rb);
+    V a5s[2][5], b5s[2][5];
+#pragma unroll
+    for (int set = 0; set < 2; ++set) {
+        P::decode(ra, set, k, a5s[set]);
+        P::decode(rb, set, k, b5s[set]);
+    }
+    stream_out<P>(g, c, k, B, i, j, smask, a5s, b5s);
 }
 
 template <typename P>
@@ -459,6 +495,13 @@ __global__ void __launch_bounds__(128) boundary_reset_kernel(Geo g, Consts c, KC
     int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b < nb && boundary_reset(g, c, k, A, B, bn, nb, b)) atomicOr(flag, 1u);
     if (b == 0) LBPS_ST(tstep, LBPS_LD(tstep) + 1ull);
+}
+
+template <typename P>
+__global__ void __launch_bounds__(128) boundary_stream_y_kernel(Geo g, Consts c, KCof<P> k, View<P> A, View<P> B,
+                                                                const BNode* __restrict__ bn, int nb) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b < nb) boundary_stream_y(g, c, k, A, B, bn, b);
 }
 
 // Copies the populations of every boundary point of copy A into A's boundary
@@ -505,6 +548,28 @@ __device__ __forceinline__ void load_uv(const double* __restrict__ U, size_t pla
 struct Win {
     int x0, x1, y0, y1;
 };
+
+// The moving populations of interior point (i, j) (plane offset p) that
+// stream in from boundary points and that the reset pass overwrites: 1 f^1
+// (from i - 1), 2 f^3 (from i + 1), 4 f^2 (from j - 1), 8 f^4 (from j + 1).
+// A rectangle's boundary points are its non-periodic edges; a general
+// geometry marks them in its node-type plane.
+__device__ __forceinline__ int streamed_in(const Geo& g, int i, int j, size_t p) {
+    if (!g.general) {
+        int m = 0;
+        if (!g.periodic_x) m |= (i == 1 ? 1 : 0) | (i == g.nx - 2 ? 2 : 0);
+        if (!g.periodic_y) m |= (j == 1 ? 4 : 0) | (j == g.ny - 2 ? 8 : 0);
+        return m;
+    }
+    auto bnd = [&](size_t q) {
+        const int t = LBPS_LDG(&g.type[q]);
+        return t == NEUMANN || t == DIRICHLET;
+    };
+    const size_t row = p - (size_t)i;
+    return (bnd(row + (size_t)wrap(i - 1, g.nx)) ? 1 : 0) | (bnd(row + (size_t)wrap(i + 1, g.nx)) ? 2 : 0) |
+           (bnd((size_t)wrap(j - 1, g.ny) * g.px + (size_t)i) ? 4 : 0) |
+           (bnd((size_t)wrap(j + 1, g.ny) * g.px + (size_t)i) ? 8 : 0);
+}
 
 // One warp's strip: output columns [xs, xs + kStripCols) of rows [j0, j1).
 // Returns true in lanes that produced a non-finite value.  All 32 lanes of
@@ -598,7 +663,10 @@ __device__ __forceinline__ bool bulk_strip(const Geo& g, const Consts& c, const 
                 double u1[4];
                 newmark(Cu[0], Cu[2], ax, c, u1[0], u1[2]);
                 newmark(Cu[1], Cu[3], ay, c, u1[1], u1[3]);
-                P::store_point(B.f, PL, p, out, k);
+                if constexpr (P::kSplitStream)
+                    P::store_point_pins(B.f, PL, p, out, k, streamed_in(g, col, j, p));
+                else
+                    P::store_point(B.f, PL, p, out, k);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) LBPS_ST(&B.u[(size_t)q * PL + p], u1[q]);
                 bad |= !isfinite(out[0][0] + out[1][0]);
@@ -829,8 +897,9 @@ __global__ void __launch_bounds__(128, MINB) pair_kernel(Geo g, Consts c, KCof<P
 
 // --------------------------------------------------------------- batches
 
-// The boundary passes of a step (1 Newmark, 2 reset) over the boundary points
-// of every lattice in the batch (one thread per point).
+// The boundary passes of a step (1 Newmark, 2 reset, 3 the y streams of the
+// reset where P::kSplitStream) over the boundary points of every lattice in
+// the batch (one thread per point).
 template <typename P>
 __global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<P>* __restrict__ dd,
                                                              const BndTask* __restrict__ tasks, int ntasks,
@@ -842,6 +911,8 @@ __global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<P>* _
     const int a = d.cur ^ parity;
     if (pass == 1)
         boundary_newmark(d.g, d.c, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.v[a].s, d.tstep, tk.b);
+    else if (pass == 3)
+        boundary_stream_y(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, tk.b);
     else {
         if (boundary_reset(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, d.nb, tk.b)) atomicOr(d.flag, 1u);
         if (tk.b == 0) LBPS_ST(d.tstep, LBPS_LD(d.tstep) + 1ull);
@@ -1086,8 +1157,11 @@ template <typename P>
 cudaError_t launch_boundary_batch(const DomDesc<P>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
                                   int pass_hi, cudaStream_t st) {
     if (ntasks > 0)
-        for (int pass = pass_lo; pass < pass_hi; ++pass)
+        for (int pass = pass_lo; pass < pass_hi; ++pass) {
             boundary_batch_kernel<P><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity, pass);
+            if (pass == 2 && P::kSplitStream)
+                boundary_batch_kernel<P><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity, 3);
+        }
     return cudaGetLastError();
 }
 
@@ -1224,6 +1298,8 @@ cudaError_t launch_boundary(const Geo& g, const Consts& c, const KCof<P>& k, Vie
             if (pass == 0) boundary_stress_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, bn, nb);
             if (pass == 1) boundary_newmark_kernel<P><<<blocks, 128, 0, st>>>(g, c, A, B, bn, nb, tstep);
             if (pass == 2) boundary_reset_kernel<P><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb, flag, tstep);
+            if (pass == 2 && P::kSplitStream)
+                boundary_stream_y_kernel<P><<<blocks, 128, 0, st>>>(g, c, k, A, B, bn, nb);
         }
     }
     return cudaGetLastError();
@@ -1251,9 +1327,11 @@ cudaError_t launch_bulk(const Geo& g, const Consts& c, const KCof<P>& k, View<P>
 template <typename P>
 cudaError_t launch_frame(const Geo& g, const Consts& c, const KCof<P>& k, View<P> A, View<P> B, unsigned* flag,
                          cudaStream_t st, int fw) {
-    // FP64 populations need the 4-blocks shape (the others spill there)
+    // FP64 populations need the 4-blocks shape (the others spill there);
+    // BFP13 fits 6 blocks with u prefetched one row ahead, not two
     constexpr int minb = sizeof(typename P::V) == 8 ? 4 : 6;
-    auto kern = frame_kernel<P, minb, 2>;
+    constexpr int uvd = std::is_same<P, PopBfp13>::value ? 1 : 2;
+    auto kern = frame_kernel<P, minb, uvd>;
     const int nx = g.nx, ny = g.ny, rows = 32;
     const int all = (nx + kStripCols - 1) / kStripCols;
     const dim3 blk(32 * kWarpsPerBlock);
@@ -1339,5 +1417,6 @@ LBPS_INSTANTIATE(PopDirect<float>)
 LBPS_INSTANTIATE(PopDirect<double>)
 LBPS_INSTANTIATE(PopNeq16<__nv_bfloat16>)
 LBPS_INSTANTIATE(PopNeq16<__half>)
+LBPS_INSTANTIATE(PopBfp13)
 
 }  // namespace lbps

@@ -14,6 +14,7 @@ using PolF32 = PopDirect<float>;
 using PolF64 = PopDirect<double>;
 using PolBF16 = PopNeq16<__nv_bfloat16>;
 using PolF16 = PopNeq16<__half>;
+using PolBfp13 = PopBfp13;
 
 // *bad |= 1 if one of the first `planes` u planes holds a non-finite value at
 // a lattice point (zero *bad first).

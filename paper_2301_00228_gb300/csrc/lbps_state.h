@@ -22,6 +22,12 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// The storage codes whose pair sums are held in 16 bits a value (PopNeq16,
+// PopBfp13).
+inline bool storage_is16(int32_t storage) {
+    return storage == LBPS_STORAGE_BF16 || storage == LBPS_STORAGE_F16 || storage == LBPS_STORAGE_BFP13;
+}
+
 // Placement of everything in a lattice's device block.
 struct Layout {
     Geo g;
@@ -44,6 +50,7 @@ auto with_policy(int32_t storage, Fn&& fn) {
     case LBPS_STORAGE_F64: return fn(PolF64{});
     case LBPS_STORAGE_BF16: return fn(PolBF16{});
     case LBPS_STORAGE_F16: return fn(PolF16{});
+    case LBPS_STORAGE_BFP13: return fn(PolBfp13{});
     default: return fn(PolF32{});
     }
 }
@@ -123,5 +130,5 @@ struct lbps_lattice {
     double* partials() const { return reinterpret_cast<double*>(mem + L.off_part); }
     double* out4() const { return reinterpret_cast<double*>(mem + L.off_out); }
     double* staging() const { return reinterpret_cast<double*>(mem + L.off_staging); }
-    bool neq16() const { return p.storage == LBPS_STORAGE_BF16 || p.storage == LBPS_STORAGE_F16; }
+    bool neq16() const { return lbps::storage_is16(p.storage); }
 };

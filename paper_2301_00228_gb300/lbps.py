@@ -29,14 +29,14 @@ LBPS_ERR_TIMEOUT = -5
 LBPS_ERR_STATE = -6
 
 LBPS_INTERIOR, LBPS_NEUMANN, LBPS_DIRICHLET, LBPS_VOID = 0, 1, 2, 3
-LBPS_STORAGE_F32, LBPS_STORAGE_F64, LBPS_STORAGE_BF16, LBPS_STORAGE_F16 = 0, 1, 2, 3
+LBPS_STORAGE_F32, LBPS_STORAGE_F64, LBPS_STORAGE_BF16, LBPS_STORAGE_F16, LBPS_STORAGE_BFP13 = 0, 1, 2, 3, 4
 (LBPS_UX, LBPS_UY, LBPS_VX, LBPS_VY, LBPS_PHI, LBPS_PSI, LBPS_F_PHI, LBPS_F_PSI, LBPS_CONSISTENCY,
  LBPS_KINETIC_ENERGY, LBPS_STRAIN_ENERGY) = range(11)
 FIELDS = {"ux": LBPS_UX, "uy": LBPS_UY, "vx": LBPS_VX, "vy": LBPS_VY, "phi": LBPS_PHI, "psi": LBPS_PSI,
           "f_phi": LBPS_F_PHI, "f_psi": LBPS_F_PSI, "consistency": LBPS_CONSISTENCY,
           "kinetic_energy": LBPS_KINETIC_ENERGY, "strain_energy": LBPS_STRAIN_ENERGY}
 STORAGES = {"f32": LBPS_STORAGE_F32, "f64": LBPS_STORAGE_F64, "bf16": LBPS_STORAGE_BF16,
-            "f16": LBPS_STORAGE_F16}
+            "f16": LBPS_STORAGE_F16, "bfp13": LBPS_STORAGE_BFP13}
 
 
 class lbps_params(ctypes.Structure):
@@ -87,6 +87,7 @@ def _load():
         "lbps_norms_noalloc": (ctypes.c_int, [vp, vp, sz, vp, vp]),
         "lbps_info": (ctypes.c_int, [vp, vp, P(i64)]),
         "lbps_scale_exp": (ctypes.c_int, [vp, P(i32)]),
+        "lbps_codec16": (ctypes.c_int, [i32, i32, vp, vp, i64, ctypes.c_uint32, i32, vp]),
         "lbps_set_load": (ctypes.c_int, [vp, i32, ctypes.c_double, ctypes.c_double]),
         "lbps_state_size": (ctypes.c_int, [vp, P(sz)]),
         "lbps_state_save": (ctypes.c_int, [vp, vp, sz]),
@@ -249,6 +250,15 @@ def lbps_norms_noalloc(d_x, d_ref, n, stream_ptr=0):
                                    ctypes.c_void_p(stream_ptr) if stream_ptr else None, _p(out)),
            "lbps_norms_noalloc")
     return out
+
+
+def lbps_codec16(storage, encode, d_x, d_code, n, key0=0, stochastic=False, stream_ptr=0):
+    """The value codec of a 16-bit storage format on device arrays (FP32
+    values d_x, 16-bit codes d_code; see include/lbps.h)."""
+    _check(_lib.lbps_codec16(STORAGES[storage] if isinstance(storage, str) else int(storage), int(encode),
+                             ctypes.c_void_p(d_x), ctypes.c_void_p(d_code), int(n), int(key0) & 0xffffffff,
+                             int(bool(stochastic)), ctypes.c_void_p(stream_ptr) if stream_ptr else None),
+           "lbps_codec16")
 
 
 def lbps_info(h):

@@ -274,7 +274,7 @@ class CudaSlab:
         self.lat.init(ux, uy, vx, vy)
 
     def scale_exp(self):
-        return self.lat.scale_exp if self.lat.storage in ("bf16", "f16") else None
+        return self.lat.scale_exp if self.lat.storage in ("bf16", "f16", "bfp13") else None
 
     def rescale(self, e):
         self.lat.close()

@@ -70,7 +70,7 @@ def test_state_bytes(lib):
     assert n32 >= 2 * px * 37 * (10 * 4 + 4 * 8)
     assert n64 >= 2 * px * 37 * (10 * 8 + 4 * 8)
     assert n64 > n32
-    for code in (lib.LBPS_STORAGE_BF16, lib.LBPS_STORAGE_F16):
+    for code in (lib.LBPS_STORAGE_BF16, lib.LBPS_STORAGE_F16, lib.LBPS_STORAGE_BFP13):
         p.storage = code
         n16 = lib.lbps_state_bytes(p)
         # FP32 f^0, Jx, Jy + two 16-bit sums per set: 32 B per point and copy
@@ -86,7 +86,7 @@ def test_state_bytes(lib):
                 with pytest.raises(lib.LbpsError):
                     lib.lbps_state_bytes(q)
     for bad in (dict(nx=2), dict(mu=0.0), dict(rho=-1.0), dict(a0_phi=1.0), dict(bc_feq_mode=2),
-                dict(storage=7), dict(storage=-1), dict(sync_every=-1), dict(dh=0.0), dict(pop_scale_exp=101),
+                dict(storage=5), dict(storage=7), dict(storage=-1), dict(sync_every=-1), dict(dh=0.0), dict(pop_scale_exp=101),
                 dict(pop_scale_exp=-101)):
         q = lib.lbps_params(100, 37, 1.0, 1.0, 1.0, 1.0, 0.9999, 0, 0, 0, 0, 0, 0, None)
         for k, v in bad.items():

@@ -50,7 +50,7 @@ def assert_same(a, b, what):
         assert np.array_equal(fa[k], fb[k]), (what, k)
 
 
-@pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f64", "bf16", "f16", "bfp13"])
 def test_batch_equals_single(L, storage):
     ds = domains(7, 14, lo=3 if storage in ("f32", "f64") else 4)
     solo = [make(L, d, storage).step(37) for d in ds]
@@ -88,7 +88,7 @@ def test_batch_tuning_and_interleaved_single_steps(L):
     b.close()
 
 
-@pytest.mark.parametrize("storage", ["f32", "f64", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f64", "f16", "bfp13"])
 def test_batch_every_launch_shape_same_bits(L, storage):
     """Every launch shape, with short and long row chunks: the same bits as
     the lattices stepped on their own."""

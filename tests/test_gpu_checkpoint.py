@@ -36,7 +36,7 @@ def same(a, b, what):
         assert np.array_equal(a.read(k), b.read(k)), (what, k)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16", "bfp13"])
 def test_resume_is_bit_exact(L, storage):
     n, k = 130, 47
     a = make(L, storage).step(n)

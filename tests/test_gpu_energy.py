@@ -34,7 +34,7 @@ def rect_case(seed=3, nx=61, ny=47):
     return dict(nx=nx, ny=ny, lam=1.9, mu=1.0, rho=1.2, et=et, ev=ev, u=(ux + rx, uy + ry))
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16", "bfp13"])
 def test_energy_matches_oracle(L, storage):
     c = rect_case()
     steps = 150
@@ -56,7 +56,7 @@ def test_energy_matches_oracle(L, storage):
     # the densities are quadratic in the fields: their relative error is about
     # twice that of the fields, so half of it is held to the fields' tolerance
     errs = {k: rel(got[k], want[k]) / 2 for k in want}
-    if storage in ("f16", "bf16"):
+    if storage in ("f16", "bf16", "bfp13"):
         judge(errs, storage, "energy densities")
     else:
         assert all(v <= TOL[storage] for v in errs.values()), errs

@@ -33,7 +33,7 @@ def make_case(seed):
     et = tuple(int(x) for x in rng.choice([1, 2], 4))
     ev = rng.uniform(-2e-4, 2e-4, 8)
     hole = (not px and not py and min(nx, ny) >= 24 and rng.random() < 0.5)
-    storage = str(rng.choice(["f64", "f32", "f16", "bf16"]))
+    storage = str(rng.choice(["f64", "f32", "f16", "bf16", "bfp13"]))
     case = dict(nx=nx, ny=ny, px=px, py=py, et=et, ev=ev, lam=float(rng.uniform(0.5, 3.0)),
                 mu=float(rng.uniform(0.7, 1.5)), rho=float(rng.uniform(0.8, 1.6)),
                 a0=float(rng.choice([0.99, 0.999])), mode=int(rng.integers(0, 2)),

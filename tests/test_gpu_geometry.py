@@ -68,7 +68,7 @@ def hole_case(L):
     return n, d, nt, bv, cell, ref.fields()
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bfp13"])
 def test_plate_with_hole_against_oracle(L, hole_case, storage):
     """The Sec. 4 plate with a hole (tension ramp, synchronised every 50
     steps) over 0.4 L/c_s, in uneven step chunks."""

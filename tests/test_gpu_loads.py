@@ -51,7 +51,7 @@ def gpu_lattice(L, d, storage):
     return lat.init(*d.displacement())
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bfp13"])
 @pytest.mark.parametrize("example", ["tension", "shear"])
 def test_paper_examples_against_oracle(L, example, storage):
     """The tension (ramp to 0.005 mu at L/c_s, then held) and shear (ramp

@@ -55,7 +55,7 @@ def assert_same(a, b, what):
         assert np.array_equal(a[k], b[k]), (what, k)
 
 
-@pytest.mark.parametrize("storage", ["f32", "f64", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "f64", "f16", "bf16", "bfp13"])
 @pytest.mark.parametrize("size", [(16, 16), (37, 53), (67, 45), (131, 97), (256, 200)])
 def test_pairs_equal_single_steps(L, storage, size):
     c = case(sum(size), *size)
@@ -70,7 +70,7 @@ def test_pairs_equal_single_steps_variants(L, variant):
     kw = {"feq1": dict(feq=1), "jmode1": dict(jmode=1), "sync7": dict(sync=7), "loads": dict(load=True),
           "chunks": dict(chunks=[1, 2, 3, 5, 8, 13, 21, 34]), "graphs2": dict(graph_k=2),
           "graphs4": dict(graph_k=4), "nographs": dict(chunks=[1] * 9 + [3] * 3)}[variant]
-    for storage in ("f32", "f16"):
+    for storage in ("f32", "f16", "bfp13"):
         want = run(L, c, storage, 87, pairs=False, **kw)
         got = run(L, c, storage, 87, pairs=True, **kw)
         assert_same(got, want, (variant, storage))

@@ -45,7 +45,7 @@ def assert_parity(got, ref, tol, what="", storage=None):
     """Every field within tol; with a 16-bit storage named, a miss within the
     format's known limit is an expected failure (tests/tolerance.py)."""
     errs = rel_errors(got, ref)
-    if storage in ("bf16", "f16"):
+    if storage in ("bf16", "f16", "bfp13"):
         return judge(errs, storage, what)
     bad = {k: v for k, v in errs.items() if not v <= tol}
     assert not bad, (what, bad, errs)
@@ -150,12 +150,12 @@ def run_gpu(L, cs, storage):
 
 
 @pytest.mark.parametrize("jmode", [0, 1])
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16", "bfp13"])
 @pytest.mark.parametrize("k", range(len(MIXED)))
 def test_mixed_rectangles(L, k, storage, jmode):
     """Both readings of J in Eq. correction-f (bc_j_mode 0 and 1)."""
     cs = dict(MIXED[k], jmode=jmode)
-    if storage in ("bf16", "f16") and ((cs["nx"] == 3 and not cs["px"]) or (cs["ny"] == 3 and not cs["py"])):
+    if storage in ("bf16", "f16", "bfp13") and ((cs["nx"] == 3 and not cs["px"]) or (cs["ny"] == 3 and not cs["py"])):
         with pytest.raises(L.LbpsError) as e:       # 16-bit storage needs 4 points across
             run_gpu(L, cs, storage)
         assert e.value.code == L.LBPS_ERR_INVALID
@@ -165,7 +165,7 @@ def test_mixed_rectangles(L, k, storage, jmode):
 
 # ------------------------------------------------- the 64 x 64 problem
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16", "bfp13"])
 def test_square_64_1000_steps(L, storage):
     """64 x 64, left edge clamped, others traction-free, centred dilatation pulse
     sigma = 4, lambda = mu = rho = 1, a_{0,phi} = 0.9999, 1000 steps."""
@@ -470,7 +470,7 @@ def test_tunings_bit_identical(L):
     """Every launch shape of the interior kernel gives the same bits (ragged strip
     and row counts included)."""
     cs = mixed_case(21, 97, 83, steps=40)
-    for storage in ("f32", "f16"):
+    for storage in ("f32", "f16", "bfp13"):
         ref = None
         for variant in range(8):
             for rows in (1, 7, 64, 4096):
@@ -569,7 +569,7 @@ def test_tiny_every_boundary_mix(L, size, edges, jmode):
         assert_parity(got, ref, TOL[storage], (size, et, storage))
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bfp13"])
 def test_step_graphs_same_bits(L, storage):
     """lbps_step replays blocks of k steps (and pairs) from captured CUDA
     graphs (one per starting copy); with per-kernel timing on it launches

@@ -73,7 +73,7 @@ def crop_case():
     return c, ux, uy, {k: ref.fields()[k] for k in ("ux", "uy", "phi", "psi")}
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16", "bfp13"])
 def test_pulse_crop_against_oracle(L, crop_case, storage):
     c, ux, uy, ref = crop_case
     lat = L.Lattice.rectangle(c.nx, c.ny, c.lam, c.mu, c.edge_type, np.asarray(c.edge_value, float).ravel(),
@@ -85,7 +85,7 @@ def test_pulse_crop_against_oracle(L, crop_case, storage):
     check(got, ref, storage, f"256^2 pulse crop, {c.steps} steps, {storage}")
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("storage", ["bf16", "f16", "bfp13"])
 def test_periodic_waves_16bit(L, storage):
     """1024^2 periodic superposed dilatational and shear waves (wavelength 64),
     10^4 steps, against the scheme's closed form."""
@@ -101,7 +101,7 @@ def test_periodic_waves_16bit(L, storage):
     check({k: lat.read(k) for k in ("ux", "uy", "phi", "psi")}, ex, storage, f"periodic 1024^2 x 1e4 steps, {storage}")
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("storage", ["bf16", "f16", "bfp13"])
 def test_sync_16bit(L, storage):
     nx, ny = 40, 30
     ux, uy = W.pulse_displacement(nx, ny, 15.0, 12.0, 3.0, 1e-3, "dilatation")
@@ -138,20 +138,21 @@ def test_scale_choice(L):
     assert L.Lattice.rectangle(nx, ny, 2.0, 1.0, (1, 1, 1, 1), np.zeros(8)).init(ux, uy).scale_exp == 0
 
 
-def test_overflow_is_reported(L):
-    """A scale far too large for IEEE half overflows the stored
-    non-equilibrium sums; the step reports a non-finite state instead of
-    returning garbage."""
+@pytest.mark.parametrize("storage", ["f16", "bfp13"])
+def test_overflow_is_reported(L, storage):
+    """A scale far too large for the format (IEEE half, BFP13) overflows the
+    stored non-equilibrium sums; the step reports a non-finite state instead
+    of returning garbage."""
     nx, ny = 30, 24
     ux, uy = W.pulse_displacement(nx, ny, 12.0, 10.0, 3.0, 1e-3, "rotation")
-    lat = L.Lattice.rectangle(nx, ny, 1.0, 1.0, (1, 1, 1, 1), np.zeros(8), storage="f16", pop_scale_exp=100)
+    lat = L.Lattice.rectangle(nx, ny, 1.0, 1.0, (1, 1, 1, 1), np.zeros(8), storage=storage, pop_scale_exp=100)
     lat.init(ux, uy)
     with pytest.raises(L.LbpsError) as e:
         lat.step(3)
     assert e.value.code == L.LBPS_ERR_NONFINITE
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
+@pytest.mark.parametrize("storage", ["bf16", "f16", "bfp13"])
 def test_device_init_equals_host_init(L, storage):
     ux, uy = W.pulse_displacement(40, 33, 15.0, 12.0, 3.0, 1e-3, "dilatation")
     vx, vy = 1e-2 * uy, -1e-2 * ux

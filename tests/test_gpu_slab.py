@@ -100,7 +100,7 @@ def whole(L, c, storage, steps):
 
 
 @pytest.mark.parametrize("world", [2, 3])
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16", "bfp13"])
 def test_slabs_equal_whole_rectangle(L, storage, world):
     c = case_rect(L)
     steps = 150

@@ -3,8 +3,9 @@
 The interior kernel is bound by HBM bandwidth only while enough warps are in
 flight; its default launch shapes are sized so that their registers fit
 (variant 0: 6 blocks of 128 threads per SM, at most 80 registers; FP64
-storage's variant 2: 4 blocks, 128 registers; the batched kernel's variant
-5: 5 blocks, 96 registers).  A spill to local memory inside the row loop
+storage's variant 2: 4 blocks, 128 registers; BFP13 storage's variant 4: 6
+blocks with u one row ahead; the batched kernel's variant 5: 5 blocks, 96
+registers; the frame kernel of two steps per sweep: 6 blocks).  A spill to local memory inside the row loop
 costs far more than the bytes it saves (a 20-byte spill once took the BF16
 kernel from 1.38 to 2.02 ms per 8192^2 launch), so every default shape must
 compile without one.  ptxas prints, per kernel, the registers it used and
@@ -21,10 +22,14 @@ DEFAULTS = [
     ("bulk_kernel", "PopDirectIfE", (6, 2)),
     ("bulk_kernel", "PopNeq16I6__halfE", (6, 2)),
     ("bulk_kernel", "PopNeq16I13__nv_bfloat16E", (6, 2)),
+    ("bulk_kernel", "PopBfp13", (6, 1)),
     ("bulk_kernel", "PopDirectIdE", (4, 2)),
     ("bulk_batch_kernel", "PopDirectIfE", (5, 1)),
     ("bulk_batch_kernel", "PopNeq16I6__halfE", (5, 1)),
     ("bulk_batch_kernel", "PopNeq16I13__nv_bfloat16E", (5, 1)),
+    ("bulk_batch_kernel", "PopBfp13", (5, 1)),
+    ("frame_kernel", "PopBfp13", (6, 1)),
+    ("frame_kernel", "PopDirectIfE", (6, 2)),
 ]
 
 
