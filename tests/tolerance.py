@@ -22,6 +22,7 @@ def judge(errs, storage, what=""):
     """Pass if every field meets the target; for a 16-bit format that misses
     it but stays within LIMIT_16, xfail with the measured error; else fail."""
     worst = max(errs.values())
+    print(f"rel-L2 {storage} {worst:.3e} {what}")
     if worst <= TARGET[storage]:
         return errs
     if storage in LIMIT_16 and worst <= LIMIT_16[storage]:
