@@ -1,6 +1,7 @@
 """Compressed population storage: per set the conserved moments (f^0 and the
 lattice first moment J) in FP32 and the two pair sums' deviations from
-equilibrium in BF16 or FP16, FP32 arithmetic.
+equilibrium in BF16, FP16 or BFP13 (one block-floating-point word per set,
+the two sums sharing an exponent), FP32 arithmetic.
 
 Parity with the FP64 oracle, relative L2 per field (u_x, u_y, phi, psi)
 taken as in the FP32/FP64 parity tests (a field that vanishes by symmetry is
@@ -10,7 +11,8 @@ expected failure with its measured error (the format's precision limit; the
 runs are deterministic): BF16 (8-bit significand) on the 256^2 crop
 (1.7e-3) and on the 10^4-step periodic waves (9.0e-3), FP16 on the waves
 (1.2e-3).  BF16 meets 1e-3 on the 1024^2 crop of the precision workload
-(bench.py --precision).  Plus: the storage scale the library picks,
+(bench.py --precision).  BFP13 meets 1e-3 on every case (no expected
+failures: a miss fails).  Plus: the storage scale the library picks,
 overflow reported as a non-finite state, host and device initialisation
 identical.
 """
