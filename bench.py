@@ -647,8 +647,8 @@ def bulk_roofline(prof, d, args, seconds, geometry, peak, peak_kind, wname):
 def pair_roofline(prof, d, args, seconds, peak, peak_kind, wname):
     """The two-step kernel: it reads the state of the points at least 3 from
     every edge once and writes it once per launch, for two steps of updates
-    (events around every launch).  The FP64 Newmark update of u, du/dt, not
-    HBM, bounds it."""
+    (events around every launch), with u, du/dt integrated over both steps
+    in one composed Newmark update."""
     pair_ms, pair_n = float(prof[0]), float(prof[1])
     deep = (d.nx - 6) * (d.ny - 6)
     alg_bytes = deep * BYTES_PER_UPDATE[args.storage]
@@ -659,7 +659,7 @@ def pair_roofline(prof, d, args, seconds, peak, peak_kind, wname):
             "peak_source": peak_kind, "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_s * 1000.0,
             "steps_per_launch": 2, "updates_per_launch": 2 * deep,
             "bytes_per_update": alg_bytes / (2 * deep),
-            "limiter": "FP64 pipe (the Newmark update of u, du/dt, twice per point per launch)",
+            "limiter": "latency at 20 warps/SM with the FP64 pipe about 2/3 busy (one composed Newmark update of u, du/dt per point per launch)",
             "share_of_step_time": pair_ms / (1000.0 * seconds),
             "kernel_timing": "CUDA events around every two-step launch of the timed steps",
             "frame_and_boundary_passes": "beside the two-step kernel on a second stream, not timed"}

@@ -260,18 +260,54 @@ __device__ inline double ddy(const double* __restrict__ g, size_t stride, int i,
 // with central differences of the neighbours' moments.  Evaluated in the
 // population type T and widened to FP64 for the Newmark update.
 template <typename T>
-__device__ __forceinline__ void accel_interior(T phiW, T phiE, T phiS, T phiN, T psiW, T psiE, T psiS,
-                                               T psiN, const KC<T>& k, double& ax, double& ay) {
+__device__ __forceinline__ void accel_interior_v(T phiW, T phiE, T phiS, T phiN, T psiW, T psiE, T psiS,
+                                                 T psiN, const KC<T>& k, T& ax, T& ay) {
     T dphix = sub_rn(phiE, phiW), dphiy = sub_rn(phiN, phiS);
     T dpsix = sub_rn(psiE, psiW), dpsiy = sub_rn(psiN, psiS);
-    ax = (double)fma_rn(k.cd2h, dphix, -mul_rn(k.cs2h, dpsiy));
-    ay = (double)fma_rn(k.cd2h, dphiy, mul_rn(k.cs2h, dpsix));
+    ax = fma_rn(k.cd2h, dphix, -mul_rn(k.cs2h, dpsiy));
+    ay = fma_rn(k.cd2h, dphiy, mul_rn(k.cs2h, dpsix));
+}
+template <typename T>
+__device__ __forceinline__ void accel_interior(T phiW, T phiE, T phiS, T phiN, T psiW, T psiE, T psiS,
+                                               T psiN, const KC<T>& k, double& ax, double& ay) {
+    T x, y;
+    accel_interior_v<T>(phiW, phiE, phiS, phiN, psiW, psiE, psiS, psiN, k, x, y);
+    ax = (double)x;
+    ay = (double)y;
 }
 
 // Eq. integration (explicit Newmark as printed).
 __device__ __forceinline__ void newmark(double u, double v, double a, const Consts& c, double& u1, double& v1) {
     u1 = fma_rn(c.half_dt2, a, fma_rn(c.dt, v, u));
     v1 = fma_rn(c.dt, a, v);
+}
+
+// Two steps of Eq. integration at once, from the accelerations a0 at t and
+// a1 at t + dt: u(t + 2 dt) = u + 2 dt v + dt^2/2 (3 a0 + a1) and
+// v(t + 2 dt) = v + dt (a0 + a1), the two explicit updates composed.  The
+// sums of the accelerations are taken in their own type (FP32 for the FP32
+// and 16-bit storages, as the accelerations themselves), so u and v take 3
+// FP64 fused multiply-adds each instead of 6; they differ from two calls of
+// newmark by rounding only.
+// FP32 -> FP64 exactly by integer operations (the FP64 pipe, which the
+// conversion instruction would take, is busy with the update): the binary32
+// sign, exponent (rebased from 127 to 1023) and fraction (shifted up 29 bits)
+// placed in binary64's fields; zero too; subnormal, infinite and NaN inputs
+// take the conversion instruction.
+__device__ __forceinline__ double widen(double x) { return x; }
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if ((e == 0u && (u << 9) != 0u) || e == 255u) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | (e ? (e + 896u) << 20 : 0u) | ((u >> 3) & 0xfffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+template <typename T>
+__device__ __forceinline__ void newmark2(double u, double v, T a0, T a1, const Consts& c, double& u2, double& v2) {
+    const double sa = widen(fma_rn((T)3, a0, a1)), sb = widen(add_rn(a0, a1));
+    u2 = fma_rn(c.half_dt2, sa, fma_rn(c.dt + c.dt, v, u));
+    v2 = fma_rn(c.dt, sb, v);
 }
 
 template <typename T>

@@ -758,12 +758,12 @@ __device__ __forceinline__ bool pair_strip(const Geo& g, const Consts& c, const 
     V C0f[2][5], C0s[2], C0m[2];
     V N0f[2][5];
     typename P::Raw Qr;
-    double C0u[4], N0u[4];
     // step n + 1: rows r - 2 (moment, f^4), r - 1 (all); filled by the first
     // two iterations, which write nothing
     V P1s[2] = {}, P1f4[2] = {};
     V C1f[2][5] = {}, C1s[2] = {}, C1m[2] = {};
-    double C1u[4] = {};
+    double C1u[4] = {};   // u, du/dt of row r - 1 at step n (loaded one iteration ahead)
+    V C1a[2] = {};        // the accelerations of row r - 1 at step n
 
     {
         V t[2][5];
@@ -779,7 +779,6 @@ __device__ __forceinline__ bool pair_strip(const Geo& g, const Consts& c, const 
     decode_row<P>(Qr, k, C0f);
     P::load_raw(A.f, PL, at(j0), col_ok, Qr);
     decode_row<P>(Qr, k, N0f);
-    load_uv(A.u, PL, at(j0 - 1), col_ok, C0u);
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
         C0m[s] = add_rn(add_rn(C0f[s][1], C0f[s][2]), add_rn(C0f[s][3], C0f[s][4]));
@@ -789,7 +788,10 @@ __device__ __forceinline__ bool pair_strip(const Geo& g, const Consts& c, const 
     // r: the row of step n + 1 computed this iteration; step n + 2 at r - 1
     for (int r = j0 - 1; r <= j1; ++r) {
         P::load_raw(A.f, PL, at(r + 2), col_ok && r + 2 <= j1 + 1, Qr);
-        load_uv(A.u, PL, at(r + 1), col_ok && r + 1 <= j1, N0u);
+        // u, du/dt only where a point is written: row r, used by the next
+        // iteration's second stage
+        double Nu[4];
+        load_uv(A.u, PL, at(r), out_lane && r >= j0 && r < j1, Nu);
         V N0m[2], N0s[2];
 #pragma unroll
         for (int s = 0; s < 2; ++s) {
@@ -797,8 +799,7 @@ __device__ __forceinline__ bool pair_strip(const Geo& g, const Consts& c, const 
             N0s[s] = add_rn(N0f[s][0], N0m[s]);
         }
         // step n + 1 at row r (bulk_strip's arithmetic)
-        V N1f[2][5];
-        double N1u[4];
+        V N1f[2][5], N1a[2];
         {
             V sW[2], sE[2], out[2][5];
 #pragma unroll
@@ -813,10 +814,9 @@ __device__ __forceinline__ bool pair_strip(const Geo& g, const Consts& c, const 
                 out[s][2] = fma_rn(k.two_a[s], P0s[s], -P0f4[s]);
                 out[s][4] = fma_rn(k.two_a[s], N0s[s], -N0f[s][2]);
             }
-            double ax, ay;
-            accel_interior<V>(sW[0], sE[0], P0s[0], N0s[0], sW[1], sE[1], P0s[1], N0s[1], k, ax, ay);
-            newmark(C0u[0], C0u[2], ax, c, N1u[0], N1u[2]);
-            newmark(C0u[1], C0u[3], ay, c, N1u[1], N1u[3]);
+            // the accelerations at step n, for the second stage, which
+            // integrates both steps at once
+            accel_interior_v<V>(sW[0], sE[0], P0s[0], N0s[0], sW[1], sE[1], P0s[1], N0s[1], k, N1a[0], N1a[1]);
             // as stored at row r and read back
             typename P::Raw q;
             P::pack(at(r), out, k, q);
@@ -845,11 +845,11 @@ __device__ __forceinline__ bool pair_strip(const Geo& g, const Consts& c, const 
             }
             if (out_lane) {
                 const size_t p = at(r - 1);
-                double ax, ay;
-                accel_interior<V>(sW[0], sE[0], P1s[0], N1s[0], sW[1], sE[1], P1s[1], N1s[1], k, ax, ay);
+                V ax, ay;
+                accel_interior_v<V>(sW[0], sE[0], P1s[0], N1s[0], sW[1], sE[1], P1s[1], N1s[1], k, ax, ay);
                 double u2[4];
-                newmark(C1u[0], C1u[2], ax, c, u2[0], u2[2]);
-                newmark(C1u[1], C1u[3], ay, c, u2[1], u2[3]);
+                newmark2(C1u[0], C1u[2], C1a[0], ax, c, u2[0], u2[2]);
+                newmark2(C1u[1], C1u[3], C1a[1], ay, c, u2[1], u2[3]);
                 P::store_point(B.f, PL, p, out, k);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) LBPS_ST(&B.u[(size_t)q * PL + p], u2[q]);
@@ -873,10 +873,9 @@ __device__ __forceinline__ bool pair_strip(const Geo& g, const Consts& c, const 
             for (int q = 0; q < 5; ++q) C0f[s][q] = N0f[s][q];
         }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            C1u[q] = N1u[q];
-            C0u[q] = N0u[q];
-        }
+        for (int q = 0; q < 4; ++q) C1u[q] = Nu[q];
+        C1a[0] = N1a[0];
+        C1a[1] = N1a[1];
         decode_row<P>(Qr, k, N0f);
     }
     return bad;
@@ -1358,9 +1357,10 @@ cudaError_t launch_pair(const Geo& g, const Consts& c, const KCof<P>& k, View<P>
                         cudaStream_t st, int rows) {
     const int warps = (g.nx - 2 * kDeep + kPairCols - 1) / kPairCols;
     const dim3 grid((warps + kWarpsPerBlock - 1) / kWarpsPerBlock, (g.ny - 2 * kDeep + rows - 1) / rows);
-    // blocks per SM that fit without spilling: FP32 populations 5 (96
-    // registers), the 16-bit formats 4 (about 120), FP64 2 (168)
-    constexpr int minb = sizeof(typename P::V) == 8 ? 2 : (std::is_same<P, PopDirect<float>>::value ? 5 : 4);
+    // blocks per SM that fit without spilling: 5 for FP32 and the 16-bit
+    // formats (96 registers; 8192^2 FP32: 70.2 against 67.1 GLUPS at 4),
+    // 2 for FP64
+    constexpr int minb = sizeof(typename P::V) == 8 ? 2 : 5;
     pair_kernel<P, minb><<<grid, 32 * kWarpsPerBlock, 0, st>>>(g, c, k, A, B, flag, rows);
     return cudaGetLastError();
 }

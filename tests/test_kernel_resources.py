@@ -5,7 +5,8 @@ flight; its default launch shapes are sized so that their registers fit
 (variant 0: 6 blocks of 128 threads per SM, at most 80 registers; FP64
 storage's variant 2: 4 blocks, 128 registers; BFP13 storage's variant 4: 6
 blocks with u one row ahead; the batched kernel's variant 5: 5 blocks, 96
-registers; the frame kernel of two steps per sweep: 6 blocks).  A spill to local memory inside the row loop
+registers; the frame kernel of two steps per sweep: 6 blocks; the two-step
+kernel: 5 blocks, 96 registers).  A spill to local memory inside the row loop
 costs far more than the bytes it saves (a 20-byte spill once took the BF16
 kernel from 1.38 to 2.02 ms per 8192^2 launch), so every default shape must
 compile without one.  ptxas prints, per kernel, the registers it used and
@@ -30,6 +31,9 @@ DEFAULTS = [
     ("bulk_batch_kernel", "PopBfp13", (5, 1)),
     ("frame_kernel", "PopBfp13", (6, 1)),
     ("frame_kernel", "PopDirectIfE", (6, 2)),
+    ("pair_kernel", "PopDirectIfE", (5, None)),
+    ("pair_kernel", "PopNeq16I6__halfE", (5, None)),
+    ("pair_kernel", "PopBfp13", (5, None)),
 ]
 
 
@@ -63,7 +67,8 @@ def ptxas_report(tmp_path_factory):
 @pytest.mark.parametrize("kernel,policy,shape", DEFAULTS)
 def test_default_shapes_do_not_spill(ptxas_report, kernel, policy, shape):
     minb, uvd = shape
-    pat = re.compile(rf"\d{kernel}INS_\d+{policy}ELi{minb}ELi{uvd}E")
+    tail = f"ELi{minb}EE" if uvd is None else f"ELi{minb}ELi{uvd}E"
+    pat = re.compile(rf"\d{kernel}INS_\d+{policy}{tail}")
     hits = [(k, v) for k, v in ptxas_report.items() if pat.search(k)]
     assert len(hits) == 1, (kernel, policy, shape, len(hits))
     name, (regs, st, ld) = hits[0]
