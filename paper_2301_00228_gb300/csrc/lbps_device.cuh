@@ -289,18 +289,31 @@ __device__ __forceinline__ void newmark(double u, double v, double a, const Cons
 // and 16-bit storages, as the accelerations themselves), so u and v take 3
 // FP64 fused multiply-adds each instead of 6; they differ from two calls of
 // newmark by rounding only.
-// FP32 -> FP64 exactly by integer operations (the FP64 pipe, which the
-// conversion instruction would take, is busy with the update): the binary32
-// sign, exponent (rebased from 127 to 1023) and fraction (shifted up 29 bits)
-// placed in binary64's fields; zero too; subnormal, infinite and NaN inputs
-// take the conversion instruction.
+// FP32 -> FP64 exactly by integer operations only (the conversion
+// instruction runs on the FP64 pipe, which the update keeps busy): the
+// binary32 sign, exponent and fraction placed in binary64's fields.  Normal
+// numbers: exponent rebased from 127 to 1023, fraction shifted up 29 bits.
+// Zero: zero.  Subnormals m 2^-149 (m < 2^23, leading one at bit k):
+// exponent k - 149 + 1023, the bits below the leading one as the fraction.
+// Infinity and NaN: exponent 2047, the fraction (a NaN's payload) kept.
 __device__ __forceinline__ double widen(double x) { return x; }
 __device__ __forceinline__ double widen(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu;
-    if ((e == 0u && (u << 9) != 0u) || e == 255u) return (double)f;
-    const unsigned hi = (u & 0x80000000u) | (e ? (e + 896u) << 20 : 0u) | ((u >> 3) & 0xfffffu);
-    return __hiloint2double((int)hi, (int)(u << 29));
+    unsigned m = u & 0x7fffffu, E;
+    if (e == 255u) {
+        E = 2047u;
+    } else if (e != 0u) {
+        E = e + 896u;
+    } else if (m != 0u) {
+        const unsigned k = 31u - (unsigned)__clz(m);   // bit of the leading one, 0..22
+        E = k + 874u;
+        m = (m << (23u - k)) & 0x7fffffu;
+    } else {
+        E = 0u;
+    }
+    const unsigned hi = (u & 0x80000000u) | (E << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)(m << 29));
 }
 
 template <typename T>

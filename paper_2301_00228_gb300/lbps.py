@@ -357,10 +357,11 @@ def lbps_set_origin(h, row0):
 # ---- convenience wrapper --------------------------------------------------
 
 # From about this many points two time steps per sweep are faster than one
-# (FP32: 16384^2 54.2 against 43.3 GLUPS, 8192^2 51.6 against 42.9, 4096^2
-# 44.3 against 40.7, 2048^2 29.6 against 37.5; FP16/BF16 8192^2 51.2 / 50.9
-# against 47.6; FP64 storage 11.5 against 12.2, so not there).
-PAIRS_AUTO_POINTS = 12_000_000
+# (FP32: 8192^2 71.8 against 42.9 GLUPS, 4096^2 55.8 against 40.6, 2048^2
+# 32.5 against 32.4, 1024^2 12.2 against 20.8; BFP13 8192^2 73.3 against
+# 47.6; FP64 storage is bound by its FP64 population arithmetic, so not
+# there).
+PAIRS_AUTO_POINTS = 6_000_000
 
 
 class Lattice:
