@@ -450,15 +450,18 @@ int lbps_set_graph_steps(lbps_lattice* lat, int32_t k);
  * (other lattices keep single steps): the points at least 3 from every edge
  * advance two steps in one pass of a kernel that reads the state once and
  * writes it once; the boundary rules and the points up to 3 from the edges
- * run step by step through a scratch state copy, beside it.  Results are the
- * same bits as single steps.  Allocates the scratch copy (cudaMalloc, the
+ * run step by step through a scratch state copy, beside it.  The kernel
+ * integrates u, du/dt of its points over both steps in one composed Newmark
+ * update (Eq. integration applied twice, the sums of the two accelerations
+ * taken in the populations' arithmetic type): the populations are the same
+ * bits as single steps between synchronisations, u and du/dt the same up to
+ * rounding.  Allocates the scratch copy (cudaMalloc, the
  * size of one state copy; LBPS_ERR_OOM if that fails) and frees it when
  * turned off or at lbps_destroy.  A synchronisation point that falls between
  * the two steps of a pair makes that pair two single steps.  With
  * lbps_profile on, the events of each pair bracket the two-step kernel only.
- * The kernel is bound by the FP64 Newmark update rather than by HBM; it pays
- * from about 3500^2 points (8192^2 FP32: 51.7 against 42.9 GLUPS; 2048^2:
- * 29.6 against 37.5). */
+ * It pays from about 2048^2 points (8192^2 FP32: 71.8 against 42.9 GLUPS;
+ * 4096^2: 55.8 against 40.6; 2048^2: 32.5 against 32.4). */
 int lbps_set_step_pairs(lbps_lattice* lat, int32_t on);
 
 /* 1 if lbps_step takes two steps per sweep on this lattice (turned on and
