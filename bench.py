@@ -397,6 +397,9 @@ def run_batch(args):
         tuned_ms = None
     else:
         variant, rows, tuned_ms = b.tune(repeats=5)
+    pairs = args.batch_pairs == "on"
+    if pairs:  # two steps per sweep for every lattice
+        b.set_step_pairs(True)
     stream = torch.cuda.current_stream()
     b.step(args.warmup)
     torch.cuda.synchronize()
@@ -430,12 +433,23 @@ def run_batch(args):
     loop_value = points * loop_steps / loop_s / 1e9
     peak, peak_kind = measured_peaks()
     step_s = seconds / args.steps
-    achieved = interior * BYTES_PER_UPDATE[args.storage] / step_s / 1e9
+    per_update = BYTES_PER_UPDATE[args.storage]
+    if pairs:
+        # per pair of steps: the points at least 3 from every edge read and
+        # written once, the first step on the points 1..3 from the edges and
+        # the second on those 1..2 from them read and written once each
+        deep = sum(max(d.nx - 6, 0) * max(d.ny - 6, 0) for d in ds)
+        band = lambda w: sum((d.nx - 2) * (d.ny - 2) - max(d.nx - 2 - 2 * w, 0) * max(d.ny - 2 - 2 * w, 0) for d in ds)
+        alg_pair = (deep + band(3) + band(2)) * per_update
+        achieved = alg_pair / (2 * step_s) / 1e9
+    else:
+        achieved = interior * per_update / step_s / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * step_s, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.storage == "f64" else "f32", "data": "synthetic",
             "config": {"workload": f"mixed_batch_{len(ds)}", "domains": len(ds), "sides": "U{64..512}",
                        "points": points, "storage": args.storage, "l2": "state larger than L2",
+                       "steps_per_sweep": 2 if pairs else 1,
                        "tuned": {"variant": variant, "rows_per_warp": rows, "graph_steps": b.graph_steps,
                                  "ms_per_step": tuned_ms}},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -444,6 +458,7 @@ def run_batch(args):
             "one_at_a_time": {"value": loop_value, "unit": UNIT, "steps": loop_steps,
                               "speedup_of_batch": value / loop_value},
             # per step: the persistent kernel (strips and Newmark tasks) and the reset
+            # (two steps per sweep: two persistent kernels and two resets a pair)
             "gpu_launches": (3 if args.storage == "bfp13" else 2) * args.steps, "clocks": clock}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -888,10 +903,12 @@ def main(argv=None):
                     help="serving section of the lattice workloads' line: requests (0: none)")
     ap.add_argument("--serve-burst", type=int, default=24, help="serving section: burst requests")
     ap.add_argument("--batch-count", type=int, default=256, help="domains of the batch workload")
+    ap.add_argument("--batch-pairs", default="on", choices=["on", "off"],
+                    help="batch: two time steps per sweep for every lattice")
     ap.add_argument("--batch-tuning", default=None,
                     help="batch: launch shape 'variant,rows[,steps per graph]' instead of running the autotuner")
     ap.add_argument("--pairs", default="auto", choices=["auto", "on", "off"],
-                    help="lattice workloads: two time steps per sweep (auto: on from 12M points where they apply)")
+                    help="lattice workloads: two time steps per sweep (auto: on from 6M points where they apply)")
     ap.add_argument("--tuning", default=None,
                     help="lattice workloads: interior-kernel launch shape 'variant,rows' instead of the default")
     ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")

@@ -335,6 +335,24 @@ int lbps_batch_set_tuning(lbps_batch* b, int32_t variant, int32_t rows_per_warp)
 int lbps_batch_set_graph_steps(lbps_batch* b, int32_t k);
 int lbps_batch_graph_steps(const lbps_batch* b);
 
+/* Two time steps per sweep for every lattice of the batch (on != 0) or one
+ * (0, the default), as lbps_set_step_pairs does for one lattice: each pair
+ * of steps is four launches, a persistent kernel that advances the points at
+ * least 3 from every edge of every lattice by two steps and runs the first
+ * step on the points 1..3 from the edges and its boundary Newmark pass into
+ * each lattice's scratch copy, the first step's reset, a persistent kernel
+ * for the second step on the points 1..2 from the edges and its Newmark pass,
+ * and the second step's reset.  Every lattice gets the same bits as when it
+ * takes two steps per sweep on its own.  Turning it on calls
+ * lbps_set_step_pairs(lat, 1) for every lattice (a scratch state copy each;
+ * its error code if that fails) and returns LBPS_ERR_INVALID, changing
+ * nothing, if a lattice is not a rectangle without periodic axes and at least
+ * 16 points a side.  lbps_batch_step then runs n / 2 pairs and an odd last
+ * step as a single step; no CUDA graph (the launches are few per pair).
+ * lbps_batch_step_pairs returns 1 if on, 0 if off. */
+int lbps_batch_set_step_pairs(lbps_batch* b, int32_t on);
+int lbps_batch_step_pairs(const lbps_batch* b);
+
 /* Autotuner: times one step for each launch shape (variants 0, 1, 2, 4, 5,
  * 6 x rows 8, 16, 32, 64, 128), repeats times each, keeps the fastest; then,
  * for that shape, times graphs of k = 2, 4, 8, 16, 32 steps (a longer graph

@@ -15,6 +15,7 @@
 using lbps::BndTask;
 using lbps::BulkTask;
 using lbps::DomDesc;
+using lbps::PairTask;
 
 struct lbps_batch {
     std::vector<lbps_lattice*> lats;
@@ -37,6 +38,11 @@ struct lbps_batch {
     cudaGraphExec_t pair = nullptr;     // 2 steps (what is left of n after the k-step blocks)
     cudaEvent_t order = nullptr;  // orders the batch stream with the lattices' streams
     int last_cuda = 0;
+    // two steps per sweep (lbps_batch_set_step_pairs): the task lists of the
+    // two stages of a pair, stage 1 then stage 2, in their own device block
+    bool pairs = false;
+    char* pmem = nullptr;
+    int np1 = 0, np2 = 0;
 };
 
 namespace {
@@ -51,6 +57,7 @@ DomDesc<P> make_desc(const lbps_lattice* lat) {
     d.k = lat->kc<P>();
     d.v[0] = lat->view<P>(0);
     d.v[1] = lat->view<P>(1);
+    d.x = lat->xmem ? lat->copy_view<P>(lat->xmem) : lbps::View<P>{};
     d.bn = lat->bn();
     d.flag = lat->flag();
     d.tstep = lat->tstep();
@@ -120,6 +127,54 @@ size_t max_bulk_tasks(const lbps_batch* b) {
     return n + (nbnd + 31) / 32;
 }
 
+// The tasks of one stage of a pair of steps (two steps per sweep), as
+// run_pair runs them on a single lattice: stage 1 the two-step strips
+// (pair_kernel's 28 columns by 32 rows over the points at least 3 from every
+// edge) and the frame strips on the points 1..3 from the edges; stage 2 the
+// frame strips on the points 1..2 from the edges (frame_kernel's bands);
+// both with the Newmark pass of every boundary point spread evenly among them.
+std::vector<PairTask> pair_stage_tasks(const lbps_batch* b, int stage) {
+    constexpr int kDeep = 3, kPairCols = 28, kRows = 32, kCols = lbps::kBatchStripCols;
+    const int fw = stage == 1 ? 3 : 2;
+    std::vector<PairTask> work;
+    int nbnd = 0;
+    for (int d = 0; d < (int)b->lats.size(); ++d) {
+        const lbps::Geo& g = b->lats[d]->L.g;
+        const int nx = g.nx, ny = g.ny;
+        nbnd += b->lats[d]->L.nb;
+        if (stage == 1)
+            for (int j0 = kDeep; j0 < ny - kDeep; j0 += kRows)
+                for (int xs = kDeep; xs < nx - kDeep; xs += kPairCols)
+                    work.push_back(PairTask{d, lbps::kPairStrip, xs, j0, std::min(j0 + kRows, ny - kDeep), 0, 0, 0, 0});
+        const int all = (nx + kCols - 1) / kCols;
+        for (int q = 0; q < all; ++q) {   // top and bottom bands, fw rows each
+            work.push_back(PairTask{d, lbps::kFrameStrip, q * kCols, 1, 1 + fw, 1, nx - 1, 1, 1 + fw});
+            work.push_back(PairTask{d, lbps::kFrameStrip, q * kCols, ny - 1 - fw, ny - 1, 1, nx - 1, ny - 1 - fw,
+                                    ny - 1});
+        }
+        const int jb = 1 + fw, je = ny - 1 - fw;   // left and right bands between them
+        for (int j0 = jb; j0 < je; j0 += kRows) {
+            const int j1 = std::min(j0 + kRows, je);
+            for (int q = 1 / kCols; q <= fw / kCols; ++q)
+                work.push_back(PairTask{d, lbps::kFrameStrip, q * kCols, j0, j1, 1, 1 + fw, jb, je});
+            for (int q = (nx - 1 - fw) / kCols; q <= (nx - 2) / kCols; ++q)
+                work.push_back(PairTask{d, lbps::kFrameStrip, q * kCols, j0, j1, nx - 1 - fw, nx - 1, jb, je});
+        }
+    }
+    const size_t nn = (size_t)(nbnd + 31) / 32;
+    std::vector<PairTask> t;
+    t.reserve(work.size() + nn);
+    size_t q = 0;
+    for (size_t k = 0; k < nn; ++k) {
+        const size_t until = k * work.size() / nn;
+        for (; q < until; ++q) t.push_back(work[q]);
+        const int b0 = (int)(32 * k);
+        t.push_back(PairTask{0, lbps::kNewmarkTask, b0, 0, std::min(32, nbnd - b0), 0, 0, 0, 0});
+    }
+    for (; q < work.size(); ++q) t.push_back(work[q]);
+    return t;
+}
+
 int fail(lbps_batch* b, cudaError_t e) {
     b->last_cuda = (int)e;
     return LBPS_ERR_CUDA;
@@ -171,6 +226,26 @@ cudaError_t launch_step(lbps_batch* b, int parity) {
         unsigned* next = reinterpret_cast<unsigned*>(b->mem + b->off_next);
         cudaError_t e = lbps::launch_bulk_batch<P>(dd, wt, b->nbulk, bt, parity, b->variant, next, b->st);
         if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 2, 3, b->st);
+        return e;
+    });
+}
+
+// Two steps of every lattice (two steps per sweep; parity as for launch_step,
+// per pair): stage 1, the reset of the first step (v[a], x -> x), stage 2,
+// the reset of the second (x, v[a ^ 1] -> v[a ^ 1]).
+cudaError_t launch_pair_step(lbps_batch* b, int parity) {
+    const BndTask* bt = reinterpret_cast<const BndTask*>(b->mem + b->off_bnd);
+    const PairTask* p1 = reinterpret_cast<const PairTask*>(b->pmem);
+    const PairTask* p2 = p1 + b->np1;
+    return lbps::with_policy(b->storage, [&](auto pol) {
+        using P = decltype(pol);
+        const DomDesc<P>* dd = reinterpret_cast<const DomDesc<P>*>(b->mem);
+        unsigned* next = reinterpret_cast<unsigned*>(b->mem + b->off_next) + 1;   // the two stages' counters
+        cudaError_t e = cudaMemsetAsync(next, 0, 2 * sizeof(unsigned), b->st);
+        if (e == cudaSuccess) e = lbps::launch_pair_batch<P>(dd, p1, b->np1, bt, parity, 1, next, b->st);
+        if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 2, 3, b->st, 1);
+        if (e == cudaSuccess) e = lbps::launch_pair_batch<P>(dd, p2, b->np2, bt, parity, 2, next + 1, b->st);
+        if (e == cudaSuccess) e = lbps::launch_boundary_batch<P>(dd, bt, b->nbnd, parity, 2, 3, b->st, 2);
         return e;
     });
 }
@@ -294,9 +369,26 @@ int lbps_batch_step(lbps_batch* b, int64_t n) {
     }
     int rc = refresh(b);
     if (rc != LBPS_OK) return rc;
-    // blocks of graph_k steps, then pairs, then a last single step
+    int flips = (int)(n & 1);   // how the current copy of every lattice moves
     int64_t q = 0;
-    if (b->graph_k > 2 && n >= b->graph_k) {
+    if (b->pairs) {
+        // two steps per sweep: every pair writes the other copy (parity
+        // alternating); an odd last step starts from the copy they leave
+        const int64_t np = n / 2;
+        for (int64_t k = 0; k < np; ++k) {
+            cudaError_t e = launch_pair_step(b, (int)(k & 1));
+            if (e != cudaSuccess) return fail(b, e);
+        }
+        q = 2 * np;
+        flips = (int)((np & 1) ^ (n & 1));
+        if (q < n) {
+            cudaError_t e = launch_step(b, (int)(np & 1));
+            if (e != cudaSuccess) return fail(b, e);
+            q = n;
+        }
+    }
+    // blocks of graph_k steps, then pairs, then a last single step
+    if (b->graph_k > 2 && n - q >= b->graph_k) {
         if (!b->graph && (rc = capture(b, b->graph_k, false, &b->graph)) != LBPS_OK) return rc;
         for (; q + b->graph_k <= n; q += b->graph_k) {
             cudaError_t e = cudaGraphLaunch(b->graph, b->st);
@@ -321,7 +413,7 @@ int lbps_batch_step(lbps_batch* b, int64_t n) {
     if (e != cudaSuccess) return fail(b, e);
     for (auto* l : b->lats) {
         l->steps += n;
-        l->cur ^= (int)(n & 1);
+        l->cur ^= flips;
     }
     return LBPS_OK;
 }
@@ -347,6 +439,44 @@ int lbps_batch_set_graph_steps(lbps_batch* b, int32_t k) {
 }
 
 int lbps_batch_graph_steps(const lbps_batch* b) { return b ? b->graph_k : LBPS_ERR_INVALID; }
+
+int lbps_batch_set_step_pairs(lbps_batch* b, int32_t on) {
+    if (!b || (on != 0 && on != 1)) return LBPS_ERR_INVALID;
+    if (b->st) cudaStreamSynchronize(b->st);
+    if (b->pmem) cudaFree(b->pmem);
+    b->pmem = nullptr;
+    b->pairs = false;
+    b->np1 = b->np2 = 0;
+    if (!on) return LBPS_OK;
+    for (lbps_lattice* l : b->lats) {
+        const lbps::Geo& g = l->L.g;
+        if (g.general || g.periodic_x || g.periodic_y || g.nx < 16 || g.ny < 16 || l->L.nb <= 0)
+            return LBPS_ERR_INVALID;
+    }
+    for (lbps_lattice* l : b->lats) {   // the scratch copy of each lattice
+        const int rc = lbps_set_step_pairs(l, 1);
+        if (rc != LBPS_OK) return rc;
+    }
+    const std::vector<PairTask> t1 = pair_stage_tasks(b, 1), t2 = pair_stage_tasks(b, 2);
+    if (cudaMalloc(&b->pmem, (t1.size() + t2.size()) * sizeof(PairTask)) != cudaSuccess) {
+        cudaGetLastError();
+        b->pmem = nullptr;
+        return LBPS_ERR_OOM;
+    }
+    cudaError_t e = cudaMemcpyAsync(b->pmem, t1.data(), t1.size() * sizeof(PairTask), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->pmem + t1.size() * sizeof(PairTask), t2.data(), t2.size() * sizeof(PairTask),
+                            cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return fail(b, e);
+    b->np1 = (int)t1.size();
+    b->np2 = (int)t2.size();
+    b->pairs = true;
+    drop_graph(b);
+    return upload(b);   // the descriptors with the scratch copies
+}
+
+int lbps_batch_step_pairs(const lbps_batch* b) { return b ? (int)b->pairs : LBPS_ERR_INVALID; }
 
 int lbps_batch_tune(lbps_batch* b, int32_t repeats, int32_t* variant, int32_t* rows_per_warp, double* ms_per_step) {
     lbps::NvtxRange nvtx("lbps_batch_tune");
@@ -464,6 +594,7 @@ void lbps_batch_destroy(lbps_batch* b) {
     if (b->st) cudaStreamSynchronize(b->st);
     drop_graph(b);
     if (b->mem) cudaFree(b->mem);
+    if (b->pmem) cudaFree(b->pmem);
     if (b->order) cudaEventDestroy(b->order);
     if (b->own_stream) cudaStreamDestroy(b->st);
     delete b;

@@ -902,18 +902,21 @@ __global__ void __launch_bounds__(128, MINB) pair_kernel(Geo g, Consts c, KCof<P
 template <typename P>
 __global__ void __launch_bounds__(128) boundary_batch_kernel(const DomDesc<P>* __restrict__ dd,
                                                              const BndTask* __restrict__ tasks, int ntasks,
-                                                             int parity, int pass) {
+                                                             int parity, int pass, int stage) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ntasks) return;
     const BndTask tk = tasks[t];
     const DomDesc<P>& d = dd[tk.dom];
     const int a = d.cur ^ parity;
+    // the copies the pass reads and writes (stage: see launch_boundary_batch)
+    const View<P>& S = stage == 2 ? d.x : d.v[a];
+    const View<P>& D = stage == 1 ? d.x : d.v[a ^ 1];
     if (pass == 1)
-        boundary_newmark(d.g, d.c, d.v[a], d.v[a ^ 1], d.bn, d.nb, d.v[a].s, d.tstep, tk.b);
+        boundary_newmark(d.g, d.c, S, D, d.bn, d.nb, S.s, d.tstep, tk.b);
     else if (pass == 3)
-        boundary_stream_y(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, tk.b);
+        boundary_stream_y(d.g, d.c, d.k, S, D, d.bn, tk.b);
     else {
-        if (boundary_reset(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], d.bn, d.nb, tk.b)) atomicOr(d.flag, 1u);
+        if (boundary_reset(d.g, d.c, d.k, S, D, d.bn, d.nb, tk.b)) atomicOr(d.flag, 1u);
         if (tk.b == 0) LBPS_ST(d.tstep, LBPS_LD(d.tstep) + 1ull);
     }
 }
@@ -963,6 +966,59 @@ __global__ void __launch_bounds__(128, MINB) bulk_batch_kernel(const DomDesc<P>*
         const DomDesc<P>& d = sd[wid];
         const int a = d.cur ^ parity;
         bool bad = bulk_strip<P, UVD>(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], tk.xs, tk.j0, tk.j1);
+        if (__any_sync(FULL, bad) && lane == 0) atomicOr(d.flag, 1u);
+    }
+}
+
+// Two steps per sweep for every lattice of a batch: one stage of a pair (see
+// launch_pair_batch).  The tasks are those of pair_kernel, frame_kernel and
+// boundary_newmark_kernel on each lattice, so each lattice gets the same bits
+// as run on its own with two steps per sweep.  Frame strips take the shape
+// that loads u one row ahead (the results do not depend on it).
+template <typename P, int MINB>
+__global__ void __launch_bounds__(128, MINB) pair_batch_kernel(const DomDesc<P>* __restrict__ dd,
+                                                               const PairTask* __restrict__ tasks, int ntasks,
+                                                               const BndTask* __restrict__ btasks, int parity,
+                                                               int stage, unsigned* next) {
+    __shared__ DomDesc<P> sd[kWarpsPerBlock];
+    const unsigned FULL = 0xffffffffu;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int cached = -1;
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(next, 1u);
+        t = __shfl_sync(FULL, t, 0);
+        if (t >= (unsigned)ntasks) break;  // whole warp
+        const PairTask tk = tasks[t];
+        if (tk.kind == kNewmarkTask) {
+            if (lane < tk.j1) {
+                const BndTask bt = btasks[tk.xs + lane];
+                const DomDesc<P>& d = dd[bt.dom];
+                const int a = d.cur ^ parity;
+                const View<P>& S = stage == 2 ? d.x : d.v[a];
+                const View<P>& D = stage == 1 ? d.x : d.v[a ^ 1];
+                boundary_newmark(d.g, d.c, S, D, d.bn, d.nb, S.s, d.tstep, bt.b);
+            }
+            continue;
+        }
+        if (tk.dom != cached) {
+            __syncwarp();  // every lane is done with the previous descriptor
+            const unsigned* src = reinterpret_cast<const unsigned*>(dd + tk.dom);
+            unsigned* dst = reinterpret_cast<unsigned*>(sd + wid);
+            for (int q = lane; q < (int)(sizeof(DomDesc<P>) / 4); q += 32) dst[q] = src[q];
+            __syncwarp();
+            cached = tk.dom;
+        }
+        const DomDesc<P>& d = sd[wid];
+        const int a = d.cur ^ parity;
+        bool bad;
+        if (tk.kind == kPairStrip) {
+            bad = pair_strip<P>(d.g, d.c, d.k, d.v[a], d.v[a ^ 1], tk.xs, tk.j0, tk.j1);
+        } else {
+            const View<P>& S = stage == 2 ? d.x : d.v[a];
+            const View<P>& D = stage == 1 ? d.x : d.v[a ^ 1];
+            bad = bulk_strip<P, 1, true>(d.g, d.c, d.k, S, D, tk.xs, tk.j0, tk.j1, Win{tk.x0, tk.x1, tk.y0, tk.y1});
+        }
         if (__any_sync(FULL, bad) && lane == 0) atomicOr(d.flag, 1u);
     }
 }
@@ -1154,12 +1210,12 @@ dim3 grid2d(int nx, int ny, dim3 blk) { return dim3((nx + blk.x - 1) / blk.x, (n
 
 template <typename P>
 cudaError_t launch_boundary_batch(const DomDesc<P>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
-                                  int pass_hi, cudaStream_t st) {
+                                  int pass_hi, cudaStream_t st, int stage) {
     if (ntasks > 0)
         for (int pass = pass_lo; pass < pass_hi; ++pass) {
-            boundary_batch_kernel<P><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity, pass);
+            boundary_batch_kernel<P><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity, pass, stage);
             if (pass == 2 && P::kSplitStream)
-                boundary_batch_kernel<P><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity, 3);
+                boundary_batch_kernel<P><<<(ntasks + 127) / 128, 128, 0, st>>>(dd, tasks, ntasks, parity, 3, stage);
         }
     return cudaGetLastError();
 }
@@ -1185,6 +1241,19 @@ cudaError_t launch_bulk_batch_v(const DomDesc<P>* dd, const BulkTask* tasks, int
     cudaError_t e = cudaMemsetAsync(next, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
     kern<<<blocks, 32 * kWarpsPerBlock, 0, st>>>(dd, tasks, ntasks, btasks, parity, next);
+    return cudaGetLastError();
+}
+
+template <typename P>
+cudaError_t launch_pair_batch(const DomDesc<P>* dd, const PairTask* tasks, int ntasks, const BndTask* btasks,
+                              int parity, int stage, unsigned* next, cudaStream_t st) {
+    if (ntasks <= 0) return cudaGetLastError();
+    // 4 blocks per SM (at 5 the two kinds of strips together spill)
+    auto kern = pair_batch_kernel<P, sizeof(typename P::V) == 8 ? 2 : 4>;
+    int blocks = resident_blocks(kern);
+    if (blocks < 0) return cudaGetLastError();
+    blocks = min(blocks, (ntasks + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    kern<<<blocks, 32 * kWarpsPerBlock, 0, st>>>(dd, tasks, ntasks, btasks, parity, stage, next);
     return cudaGetLastError();
 }
 
@@ -1409,7 +1478,9 @@ cudaError_t launch_norms(const Geo& g, const Consts& c, const KCof<P>& k, View<P
     template cudaError_t launch_norms<P>(const Geo&, const Consts&, const KCof<P>&, View<P>, int,            \
                                          const double*, double*, double*, cudaStream_t);                     \
     template cudaError_t launch_boundary_batch<P>(const DomDesc<P>*, const BndTask*, int, int, int, int,      \
-                                                  cudaStream_t);                                              \
+                                                  cudaStream_t, int);                                         \
+    template cudaError_t launch_pair_batch<P>(const DomDesc<P>*, const PairTask*, int, const BndTask*, int, int, \
+                                              unsigned*, cudaStream_t);                                       \
     template cudaError_t launch_bulk_batch<P>(const DomDesc<P>*, const BulkTask*, int, const BndTask*, int, int, \
                                               unsigned*, cudaStream_t);
 

@@ -93,6 +93,7 @@ struct DomDesc {
     Consts c;
     KCof<P> k;
     View<P> v[2];
+    View<P> x;  // scratch state copy of two steps per sweep (unset without)
     const BNode* bn;
     unsigned* flag;
     unsigned long long* tstep;  // step counter (time of the boundary data)
@@ -108,11 +109,34 @@ struct BndTask {   // one thread: boundary point b of lattice dom
     int dom, b;
 };
 
+// One warp's task of the two-steps-per-sweep batch kernel: kind kPairStrip,
+// output columns [xs, xs + 28) of rows [j0, j1) of lattice dom advanced two
+// steps; kFrameStrip, the interior kernel on strip xs, rows [j0, j1), writing
+// only inside the window [x0, x1) x [y0, y1); kNewmarkTask, the Newmark pass
+// of boundary tasks [xs, xs + j1).
+constexpr int kPairStrip = 0;
+constexpr int kFrameStrip = 1;
+constexpr int kNewmarkTask = 2;
+struct PairTask {
+    int dom, kind, xs, j0, j1;
+    int x0, x1, y0, y1;
+};
+
 constexpr int kBatchStripCols = 30;  // output columns per warp task
 
+// stage 0: copy v[a] -> v[a ^ 1] (a = cur ^ parity); with two steps per
+// sweep, stage 1: v[a] -> x and stage 2: x -> v[a ^ 1].
 template <typename P>
 cudaError_t launch_boundary_batch(const DomDesc<P>* dd, const BndTask* tasks, int ntasks, int parity, int pass_lo,
-                                  int pass_hi, cudaStream_t st);
+                                  int pass_hi, cudaStream_t st, int stage = 0);
+// One stage of a pair of steps of every lattice (two steps per sweep): a
+// persistent grid whose warps take PairTasks through the counter *next
+// (zeroed by the caller).  Stage 1: two-step strips v[a] -> v[a ^ 1], frame
+// strips and Newmark tasks v[a] -> x; stage 2: frame strips and Newmark tasks
+// x -> v[a ^ 1].
+template <typename P>
+cudaError_t launch_pair_batch(const DomDesc<P>* dd, const PairTask* tasks, int ntasks, const BndTask* btasks,
+                              int parity, int stage, unsigned* next, cudaStream_t st);
 // Interior of every lattice and the Newmark pass of their boundary points: a
 // persistent grid whose warps take tasks (strips, or 32 boundary points of
 // btasks) through the counter *next (device memory; the launcher zeroes it on

@@ -112,6 +112,8 @@ def _load():
         "lbps_batch_set_tuning": (ctypes.c_int, [vp, i32, i32]),
         "lbps_batch_set_graph_steps": (ctypes.c_int, [vp, i32]),
         "lbps_batch_graph_steps": (ctypes.c_int, [vp]),
+        "lbps_batch_set_step_pairs": (ctypes.c_int, [vp, i32]),
+        "lbps_batch_step_pairs": (ctypes.c_int, [vp]),
         "lbps_batch_tune": (ctypes.c_int, [vp, i32, P(i32), P(i32), P(ctypes.c_double)]),
         "lbps_batch_last_cuda_error": (ctypes.c_int, [vp]),
         "lbps_batch_destroy": (None, [vp]),
@@ -533,6 +535,14 @@ def lbps_batch_graph_steps(b):
     return int(_lib.lbps_batch_graph_steps(b))
 
 
+def lbps_batch_set_step_pairs(b, on):
+    _check(_lib.lbps_batch_set_step_pairs(b, int(on)), "lbps_batch_set_step_pairs")
+
+
+def lbps_batch_step_pairs(b):
+    return int(_lib.lbps_batch_step_pairs(b))
+
+
 def lbps_batch_tune(b, repeats=3):
     v, r, ms = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_double(0)
     _check(_lib.lbps_batch_tune(b, int(repeats), ctypes.byref(v), ctypes.byref(r), ctypes.byref(ms)),
@@ -573,6 +583,14 @@ class Batch:
 
     def set_graph_steps(self, k):
         lbps_batch_set_graph_steps(self._h, k)
+
+    @property
+    def step_pairs(self):
+        return bool(lbps_batch_step_pairs(self._h))
+
+    def set_step_pairs(self, on):
+        """Two time steps per sweep for every lattice (lbps_batch_set_step_pairs)."""
+        lbps_batch_set_step_pairs(self._h, on)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -202,3 +202,83 @@ def test_batch_graph_steps_same_bits(L, k):
         with pytest.raises(L.LbpsError):
             b.set_graph_steps(bad)
     b.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "f16", "bfp13"])
+def test_batch_pairs_equal_lattices_alone(L, storage):
+    """Two steps per sweep in the batch: every lattice ends with the same bits
+    as the same lattice taking two steps per sweep on its own, over an odd
+    step count in chunks (pairs, then a single step), and single steps taken
+    again after turning the mode off continue alike."""
+    ds = domains(17, 12, lo=16, hi=150, periodic=False)
+    solo = []
+    for d in ds:
+        lat = make(L, d, storage)
+        L.lbps_set_step_pairs(lat._h, 1)
+        solo.append(lat.step(10).step(27))
+    lats = [make(L, d, storage) for d in ds]
+    b = L.Batch(lats)
+    assert not b.step_pairs
+    b.set_step_pairs(True)
+    assert b.step_pairs
+    b.step(10).step(27)
+    assert b.check() == 0
+    for q, (x, y) in enumerate(zip(lats, solo)):
+        assert x.steps == 37
+        assert_same(x, y, (storage, q))
+    b.set_step_pairs(False)
+    b.step(5)
+    for y in solo:
+        L.lbps_set_step_pairs(y._h, 0)
+        y.step(5)
+    for q, (x, y) in enumerate(zip(lats, solo)):
+        assert_same(x, y, ("single after pairs", storage, q))
+    b.close()
+
+
+def test_batch_pairs_against_single_steps_and_oracle(L):
+    """Against the batch's single steps: populations the same bits, u and
+    du/dt within the rounding of the composed update; and against the FP64
+    oracle within the FP32 tolerance."""
+    ds = domains(23, 6, lo=16, hi=90, periodic=False)
+    one = [make(L, d, "f32") for d in ds]
+    two = [make(L, d, "f32") for d in ds]
+    b1, b2 = L.Batch(one), L.Batch(two)
+    b2.set_step_pairs(True)
+    b1.step(40)
+    b2.step(40)
+    for q, (x, y) in enumerate(zip(two, one)):
+        fx, fy = x.fields(), y.fields()
+        for k in fx:
+            if k in ("f_phi", "f_psi", "phi", "psi"):
+                assert np.array_equal(fx[k], fy[k]), (q, k)
+            else:
+                scale = max(float(np.abs(fy[k]).max()), 1e-300)
+                assert float(np.abs(fx[k] - fy[k]).max()) <= 1e-7 * scale, (q, k)
+        d = ds[q]
+        nt, bv = O.rect_bc(d["nx"], d["ny"], d["et"], d["ev"])
+        ref = O.OracleLattice(d["nx"], d["ny"], d["lam"], 1.0, a0_phi=d["a0"], node_type=nt, bc_value=bv)
+        ref = ref.init(d["ux"], d["uy"]).step(40).fields()
+        for grp in (("ux", "uy"), ("phi", "psi")):
+            gn = np.sqrt(sum(np.linalg.norm(ref[k]) ** 2 for k in grp))
+            for k in grp:
+                err = np.linalg.norm(fx[k] - ref[k]) / max(np.linalg.norm(ref[k]), 1e-2 * gn)
+                assert err <= 1e-5, (q, k, err)
+    b1.close()
+    b2.close()
+
+
+def test_batch_pairs_rejected_where_they_do_not_apply(L):
+    """A periodic lattice or one under 16 points a side: LBPS_ERR_INVALID, the
+    batch keeps single steps."""
+    for d in (dict(domains(3, 1, lo=20, hi=40, periodic=False)[0], px=True),
+              dict(domains(4, 1, lo=10, hi=12, periodic=False)[0])):
+        good = make(L, domains(5, 1, lo=20, hi=40, periodic=False)[0], "f32")
+        b = L.Batch([good, make(L, d, "f32")])
+        with pytest.raises(L.LbpsError) as e:
+            b.set_step_pairs(True)
+        assert e.value.code == L.LBPS_ERR_INVALID
+        assert not b.step_pairs
+        b.step(3)
+        assert b.check() == 0
+        b.close()
