@@ -422,7 +422,11 @@ def run_batch(args):
     rmax, rsum = reducers(dist, "cuda")
     seconds = rmax(e0.elapsed_time(e1) / 1000.0)          # slowest rank
     value = rsum(points * args.steps) / seconds / 1e9      # points of all ranks
-    # the same lattices stepped one at a time (same kernels, one lattice per launch)
+    # the same lattices stepped one at a time (same kernels, one lattice per
+    # launch), each with single steps, its faster mode at these sizes
+    if pairs:
+        for lat in lats:
+            lbps.lbps_set_step_pairs(lat._h, 0)
     loop_steps = max(2, args.steps // 10)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
