@@ -473,7 +473,7 @@ def run_batch(args):
 
 
 def serve_measure(requests=64, rate_factor=1.2, burst=32, budget_gb=64.0, small_budget=None, max_chunk=500,
-                  sample=6):
+                  sample=6, pairs=True):
     """Serving measurements on one GPU: a Poisson stream of solves (sides
     log-uniform 128..2048, steps U{500..20000}, edges and lambda/mu as in the
     mixed batch) at rate_factor x the capacity of the one-solve-at-a-time
@@ -481,7 +481,8 @@ def serve_measure(requests=64, rate_factor=1.2, burst=32, budget_gb=64.0, small_
     continuous batching and by that loop; a second batched run under a small
     device-memory budget (default 1.2 x the largest request's footprint, so
     admission binds: requests wait for memory, memory_waits > 0); and a burst of the first requests arriving at once
-    (capacity).  Latency = completion - arrival."""
+    (capacity).  With pairs the batched server takes two time steps per sweep
+    (each solve charged its scratch copy).  Latency = completion - arrival."""
     from paper_2301_00228_gb300 import serve as S
     from paper_2301_00228_gb300 import workloads as W
 
@@ -498,15 +499,15 @@ def serve_measure(requests=64, rate_factor=1.2, burst=32, budget_gb=64.0, small_
     prepared = {r.rid: r.domain.displacement() for r in reqs}
     work = sum(r.domain.nx * r.domain.ny * r.steps for r in reqs)
     budget = int(budget_gb * (1 << 30))
-    biggest = max(S.footprint(r.domain) for r in reqs)
+    biggest = max(S.footprint(r.domain, pairs=pairs) for r in reqs)
     small_bytes = int(small_budget * (1 << 30)) if small_budget else int(1.2 * biggest)
-    served = S.serve_batched(reqs, budget, prepared=prepared, max_chunk=max_chunk)
-    small = S.serve_batched(reqs, small_bytes, prepared=prepared, max_chunk=max_chunk)
+    served = S.serve_batched(reqs, budget, prepared=prepared, max_chunk=max_chunk, pairs=pairs)
+    small = S.serve_batched(reqs, small_bytes, prepared=prepared, max_chunk=max_chunk, pairs=pairs)
     loop = S.serve_one_at_a_time(reqs, prepared=prepared)
     sv, lp = served.summary(), loop.summary()
     out = {"config": {"requests": len(reqs), "sides": "log-U 128..2048", "steps": "U{500..20000}",
                       "rate_hz": rate, "rate_factor": rate_factor, "loop_service_s_mean": service,
-                      "budget_gb": budget_gb, "lattice_updates": work},
+                      "budget_gb": budget_gb, "lattice_updates": work, "batch_steps_per_sweep": 2 if pairs else 1},
            "served": {**sv, "glups": work / served.makespan / 1e9},
            "one_at_a_time": {**lp, "glups": work / loop.makespan / 1e9},
            "speedup_solves_per_s": sv["solves_per_s"] / lp["solves_per_s"],
@@ -515,7 +516,7 @@ def serve_measure(requests=64, rate_factor=1.2, burst=32, budget_gb=64.0, small_
                                    "largest_request_gb": biggest / (1 << 30)}}
     bst = [S.Request(r.rid, 0.0, r.domain, r.steps) for r in reqs[:burst]]
     bwork = sum(r.domain.nx * r.domain.ny * r.steps for r in bst)
-    bs = S.serve_batched(bst, budget, prepared=prepared, max_chunk=max_chunk)
+    bs = S.serve_batched(bst, budget, prepared=prepared, max_chunk=max_chunk, pairs=pairs)
     bl = S.serve_one_at_a_time(bst, prepared=prepared)
     out["capacity_burst"] = {"requests": len(bst), "served_solves_per_s": bs.summary()["solves_per_s"],
                              "loop_solves_per_s": bl.summary()["solves_per_s"],

@@ -23,7 +23,11 @@ times and serves them as they arrive:
 a time in arrival order.  Both report per-request latency (completion minus
 arrival) and throughput.  A solve gets the same bits alone, in the batch, or
 in the baseline loop, because the batched kernels run the per-point
-arithmetic of the single-lattice ones.
+arithmetic of the single-lattice ones.  With ``pairs`` the batch takes two
+time steps per sweep (lbps_batch_set_step_pairs) when every member allows
+it: the populations are the same bits, u and du/dt the same up to the
+rounding of the composed two-step update, and each admitted solve is
+charged one more state copy (its scratch copy).
 """
 from __future__ import annotations
 
@@ -88,9 +92,18 @@ def _params(d, storage):
                             0, 0, lbps.STORAGES[storage], 0, None)
 
 
-def footprint(d, storage="f32"):
-    """Device bytes one solve holds while admitted."""
-    return lbps.lbps_state_bytes(_params(d, storage))
+def pairs_apply(d):
+    """Two steps per sweep apply to the domain: a rectangle without periodic
+    axes, at least 16 points a side."""
+    return not d.periodic_x and not d.periodic_y and min(d.nx, d.ny) >= 16
+
+
+def footprint(d, storage="f32", pairs=False):
+    """Device bytes one solve holds while admitted; with two steps per sweep
+    also the scratch state copy, counted as half the lattice's block (which
+    holds two copies and more: an upper bound)."""
+    b = lbps.lbps_state_bytes(_params(d, storage))
+    return b + b // 2 if pairs and pairs_apply(d) else b
 
 
 def _lattice(d, storage, u0=None, stream=None):
@@ -134,7 +147,7 @@ def _streams():
 
 
 def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fields=True, tuning=None,
-                  clock=time.perf_counter, prepared=None):
+                  clock=time.perf_counter, prepared=None, pairs=False):
     """Continuous batching.  ``prepared[rid]`` may hold (ux, uy) host arrays
     computed beforehand (input generation kept out of the timed run).
 
@@ -143,8 +156,9 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
     their own; they join the batch at the next chunk boundary) and reads out
     the solves that finished in the chunk before."""
     reqs = sorted(requests, key=lambda r: r.arrival)
+    foot = (lambda d: footprint(d, storage, pairs=True)) if pairs else (lambda d: footprint(d, storage))
     for r in reqs:
-        if footprint(r.domain, storage) > budget_bytes:
+        if foot(r.domain) > budget_bytes:
             raise ValueError(f"request {r.rid} needs more device memory than the whole budget")
     new_stream, batch_stream = _streams()
     clk = _Clock(clock)
@@ -172,7 +186,7 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
 
     def admit():
         while waiting:
-            need = footprint(waiting[0].domain, storage)
+            need = foot(waiting[0].domain)
             if state["used"] + need > budget_bytes:
                 rep.memory_waits += 1
                 refused_at.setdefault(waiting[0].rid, clk.now())
@@ -194,7 +208,7 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
                 lat.norms("ux")
             res.completed = clk.now()
             rep.results.append(res)
-            state["used"] -= footprint(r.domain, storage)
+            state["used"] -= foot(r.domain)
             lat.close()
         finished.clear()
 
@@ -205,7 +219,7 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
             for a in [a for a in group if a[0].cancelled_by(now)]:
                 group.remove(a)
                 a[1].close()
-                state["used"] -= footprint(a[0].domain, storage)
+                state["used"] -= foot(a[0].domain)
                 rep.cancelled.append(a[0].rid)
         admit()
         active.extend(ready)
@@ -228,7 +242,14 @@ def serve_batched(requests, budget_bytes, storage="f32", max_chunk=500, keep_fie
                 batch = lbps.Batch([a[1] for a in active], stream=batch_stream)
                 if tuning is not None:
                     batch.set_tuning(*tuning)
+                if pairs and all(pairs_apply(a[0].domain) for a in active):
+                    batch.set_step_pairs(True)
                 rep.rebuilds += 1
+            elif pairs:
+                # alone: two steps per sweep only where they pay on one lattice
+                d = active[0][0].domain
+                lbps.lbps_set_step_pairs(active[0][1]._h,
+                                         int(pairs_apply(d) and d.nx * d.ny >= lbps.PAIRS_AUTO_POINTS))
             batch_members = members
         k = min(max_chunk, min(a[2] for a in active))
         if batch is not None:

@@ -100,3 +100,19 @@ def test_withdrawn_requests_leave_queue_and_batch(S):
         assert np.array_equal(r.ux, ux) and np.array_equal(r.uy, uy), r.rid
     base = S.serve_one_at_a_time(reqs, clock=StepClock())
     assert 1 in base.cancelled and len(base.results) + len(base.cancelled) == 6
+
+
+def test_results_with_two_steps_per_sweep(S):
+    """With pairs the batch takes two steps per sweep: every result matches
+    the solve alone up to the rounding of the composed two-step update of u,
+    and the admission charge includes the scratch copy."""
+    reqs = stream(8, 16, rate_hz=400.0, side_lo=16, side_hi=80)
+    rep = S.serve_batched(reqs, budget_bytes=8 << 30, max_chunk=64, pairs=True)
+    assert len(rep.results) == len(reqs) and rep.max_active > 1
+    for req, r in zip(reqs, rep.results):
+        ux, uy = alone(S, req)
+        for got, want in ((r.ux, ux), (r.uy, uy)):
+            scale = max(float(np.abs(want).max()), 1e-300)
+            assert float(np.abs(got - want).max()) <= 1e-7 * scale, req.rid
+    d = reqs[0].domain
+    assert S.footprint(d, pairs=True) == S.footprint(d) + S.footprint(d) // 2
