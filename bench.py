@@ -913,7 +913,7 @@ def main(argv=None):
     ap.add_argument("--batch-tuning", default=None,
                     help="batch: launch shape 'variant,rows[,steps per graph]' instead of running the autotuner")
     ap.add_argument("--pairs", default="auto", choices=["auto", "on", "off"],
-                    help="lattice workloads: two time steps per sweep (auto: on from 6M points where they apply)")
+                    help="lattice workloads: two time steps per sweep (auto: on from 3M points where they apply)")
     ap.add_argument("--tuning", default=None,
                     help="lattice workloads: interior-kernel launch shape 'variant,rows' instead of the default")
     ap.add_argument("--size", type=int, default=None, help="lattice side (pulses: 8192, waves: 1024)")

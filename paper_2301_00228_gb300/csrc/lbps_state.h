@@ -90,6 +90,9 @@ struct lbps_lattice {
     // holds step n + 1 on the boundary and the points up to 3 from it
     // (cudaMalloc'd, copy_bytes), null when off
     char* xmem = nullptr;
+    // pairs of steps of a lattice below lbps_solo_pairs_max points run as a
+    // batch of this one lattice (lbps_step_async)
+    lbps_batch* solo = nullptr;
     lbps::Tuning tuning;  // bulk-kernel launch shape
     int last_cuda = 0;    // cudaError_t of the last failing CUDA call
     int64_t steps;

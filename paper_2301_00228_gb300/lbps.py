@@ -359,11 +359,10 @@ def lbps_set_origin(h, row0):
 # ---- convenience wrapper --------------------------------------------------
 
 # From about this many points two time steps per sweep are faster than one
-# (FP32: 8192^2 71.8 against 42.9 GLUPS, 4096^2 55.8 against 40.6, 2048^2
-# 32.5 against 32.4, 1024^2 12.2 against 20.8; BFP13 8192^2 73.3 against
-# 47.6; FP64 storage is bound by its FP64 population arithmetic, so not
-# there).
-PAIRS_AUTO_POINTS = 6_000_000
+# (FP32, lbps_step with CUDA graphs: 8192^2 72.1 against 43.2 GLUPS, 4096^2
+# 63.1 against 41.9, 2048^2 46.6 against 37.1, 1536^2 32.5 against 33.6;
+# FP64 storage is bound by its FP64 population arithmetic, so not there).
+PAIRS_AUTO_POINTS = 3_000_000
 
 
 class Lattice:

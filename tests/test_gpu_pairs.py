@@ -175,3 +175,22 @@ def test_pairs_report_nonfinite(L):
         lat.step(10)
     assert e.value.code == L.LBPS_ERR_NONFINITE
     lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bfp13"])
+def test_pair_implementations_same_bits(L, storage):
+    """A lattice below 2^25 points takes its pairs as a batch of itself; with
+    per-kernel timing on it takes them through the two-step kernel and the
+    frame chain on the second stream.  Both give the same bits."""
+    c = case(13, 131, 97)
+    out = []
+    for timed in (False, True):
+        lat = L.Lattice.rectangle(c["nx"], c["ny"], c["lam"], 1.0, c["et"], c["ev"], a0_phi=0.99, storage=storage)
+        L.lbps_set_step_pairs(lat._h, 1)
+        L.lbps_profile(lat._h, int(timed))
+        lat.init(*c["u"]).step(9).step(32)
+        out.append({k: lat.read(k) for k in FIELDS})
+        assert lat.check() == 0 and lat.steps == 41
+        lat.close()
+    for k in FIELDS:
+        assert np.array_equal(out[0][k], out[1][k]), k
