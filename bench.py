@@ -682,7 +682,9 @@ def pair_roofline(prof, d, args, seconds, peak, peak_kind, wname):
             "limiter": "latency at 20 warps/SM with the FP64 pipe about 2/3 busy (one composed Newmark update of u, du/dt per point per launch)",
             "share_of_step_time": pair_ms / (1000.0 * seconds),
             "kernel_timing": "CUDA events around every two-step launch of the timed steps",
-            "frame_and_boundary_passes": "beside the two-step kernel on a second stream, not timed"}
+            "frame_and_boundary_passes": "beside the two-step kernel on a second stream of greatest priority, "
+                                          "not timed; they run on SM slots the kernel's retiring blocks free, so "
+                                          "the kernel's launch time includes them"}
 
 
 def single_step_window(lbps, lat, d, args, points, peak, stream):

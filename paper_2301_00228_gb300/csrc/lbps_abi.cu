@@ -541,7 +541,8 @@ int step_graph(lbps_lattice* lat, int k, cudaGraphExec_t* out, int* end_cur) {
     lat->cur = q;
     lat->steps = steps;
     e = cudaStreamEndCapture(lat->cap, &g);
-    if (rc == LBPS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&slot, g, 0);
+    // the kernels captured from the side stream keep its priority in the graph
+    if (rc == LBPS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&slot, g, cudaGraphInstantiateFlagUseNodePriority);
     if (g) cudaGraphDestroy(g);
     if (rc != LBPS_OK || e != cudaSuccess) {
         slot = nullptr;
@@ -890,8 +891,16 @@ int lbps_create_cells(const lbps_params* params, const uint8_t* node_type, const
         if (params->storage == LBPS_STORAGE_BFP13) lat->tuning.variant = 4;
     }
     // the side stream of the boundary Newmark pass; if it cannot be had, the
-    // pass runs on the lattice's stream (same results, no overlap)
-    if (cudaStreamCreateWithFlags(&lat->side, cudaStreamNonBlocking) != cudaSuccess ||
+    // pass runs on the lattice's stream (same results, no overlap).  It has
+    // the greatest priority: its short dependent launches then take SM slots
+    // as the interior kernel's blocks retire, instead of waiting behind all of
+    // that kernel's blocks and running in its tail.
+    int prio_least = 0, prio_greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest) != cudaSuccess) {
+        cudaGetLastError();
+        prio_greatest = 0;
+    }
+    if (cudaStreamCreateWithPriority(&lat->side, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
         cudaEventCreateWithFlags(&lat->fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&lat->join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
