@@ -478,13 +478,13 @@ int lbps_set_graph_steps(lbps_lattice* lat, int32_t k);
  * turned off or at lbps_destroy.  A synchronisation point that falls between
  * the two steps of a pair makes that pair two single steps.  With
  * lbps_profile on, the events of each pair bracket the two-step kernel only.
- * Below 2^25 points (and without per-kernel timing or synchronisation) the
- * pairs run as a batch of this one lattice (lbps_batch_set_step_pairs: four
- * launches a pair), from there on as the two-step kernel beside a chain of
- * boundary and frame launches on a second stream; both give the same bits.
- * It pays from about 1700^2 points (FP32: 8192^2 72.1 against 43.2 GLUPS;
- * 4096^2 63.1 against 41.9; 2048^2 46.6 against 37.1; 1536^2 32.5 against
- * 33.6). */
+ * Below 12 x 2^20 points (and without per-kernel timing or synchronisation)
+ * the pairs run as a batch of this one lattice (lbps_batch_set_step_pairs:
+ * four launches a pair), from there on as the two-step kernel beside a chain
+ * of boundary and frame launches on a second stream of greatest priority;
+ * both give the same bits.  It pays from about 1700^2 points (FP32: 8192^2
+ * 75.1 against 43.2 GLUPS; 4096^2 68.8 against 41.9; 2048^2 46.3 against
+ * 37.1; 1536^2 32.5 against 33.6). */
 int lbps_set_step_pairs(lbps_lattice* lat, int32_t on);
 
 /* 1 if lbps_step takes two steps per sweep on this lattice (turned on and

@@ -418,9 +418,10 @@ bool pair_ok(const lbps_lattice* lat) {
 // itself (lbps_batch_set_step_pairs): four launches a pair, the two-step
 // strips and the first step's frame strips in one persistent kernel, where
 // run_pair's concurrent chain on the second stream costs thirteen launches.
-// Measured (FP32 pulses): 2048^2 46.6 against 35.9 GLUPS, 4096^2 63.1
-// against 58.7; at 8192^2 run_pair is faster (72.1 against 68.1).
-constexpr int64_t kSoloPairsMaxPoints = 32ll << 20;
+// Measured (FP32 pulses, CUDA graphs, run_pair's second stream at the
+// greatest priority): 2048^2 46.3 against 37.9 GLUPS, 3072^2 56.8 against
+// 56.9; from 4096^2 run_pair is faster (68.8 against 63.0).
+constexpr int64_t kSoloPairsMaxPoints = 12ll << 20;
 
 bool solo_pairs(const lbps_lattice* lat) {
     return pair_ok(lat) && !lat->prof && lat->p.sync_every == 0 &&
